@@ -1,0 +1,131 @@
+"""Mesh complex K = {N, E, F, T} and degree-of-freedom numbering.
+
+Follows Section III-A ("Discretization in Space"): the domain is a collection
+of tetrahedra with N_n nodes, N_e edges, N_f faces and N_t tets; each tet
+carries W0/W1/W2 basis functions of order k (DOF counts in Section III-A and
+the Appendix).
+
+Canonical numbering (a reading: the paper states none):
+
+* every tet's four vertices are sorted by global node id; local vertex i is the
+  i-th smallest.  Edges and faces are oriented from the smaller to the larger
+  global id, so local and global orientations agree and all signs are +1;
+* edges are the unique sorted pairs, faces the unique sorted triples, both in
+  lexicographic order;
+* local edge j is ``LOCAL_EDGES[j]``; local face i is the face opposite local
+  vertex i (``LOCAL_FACES[i]``);
+* order 1: W1 DOF = edge id, W2 DOF = face id, W0 DOF = node id;
+* order 2: W1 DOFs are ``2*edge + v`` (v=0: multiplier attached to the lower
+  vertex, v=1: to the upper) then ``2*N_e + 2*face + v``; W2 DOFs are
+  ``3*face + v`` then ``3*N_f + 3*tet + i``; W0 DOFs are nodes then
+  ``N_n + edge`` (mid-edge Lagrange nodes).
+"""
+
+import numpy as np
+
+LOCAL_EDGES = ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))
+LOCAL_FACES = ((1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2))
+
+
+class MeshError(ValueError):
+    pass
+
+
+class Topology:
+    """Entities, adjacency and DOF maps of a tet mesh for a given order."""
+
+    def __init__(self, xyz, tets, order):
+        if order not in (1, 2):
+            raise ValueError("order must be 1 or 2")
+        xyz = np.asarray(xyz, dtype=np.float64)
+        t = np.sort(np.asarray(tets, dtype=np.int64), axis=1)
+        if t.size and (t.min() < 0 or t.max() >= len(xyz)):
+            raise MeshError("tet references a node out of range")
+        if np.any(t[:, 1:] == t[:, :-1]):
+            raise MeshError("tet with a repeated vertex")
+        self.order = order
+        self.xyz = xyz
+        self.tets = t
+        nt = len(t)
+        self.n_nodes, self.n_tets = len(xyz), nt
+
+        e_all = t[:, LOCAL_EDGES].reshape(-1, 2)
+        self.edges, inv = np.unique(e_all, axis=0, return_inverse=True)
+        self.tet_edges = inv.reshape(nt, 6)
+        f_all = t[:, LOCAL_FACES].reshape(-1, 3)
+        self.faces, inv = np.unique(f_all, axis=0, return_inverse=True)
+        self.tet_faces = inv.reshape(nt, 4)
+        self.n_edges, self.n_faces = len(self.edges), len(self.faces)
+
+        # face -> the (at most two) tets that own it
+        owners = np.full((self.n_faces, 2), -1, dtype=np.int64)
+        owner_face = np.full((self.n_faces, 2), -1, dtype=np.int64)
+        count = np.zeros(self.n_faces, dtype=np.int64)
+        for tt in range(nt):
+            for i in range(4):
+                f = self.tet_faces[tt, i]
+                if count[f] >= 2:
+                    raise MeshError("face shared by more than two tets")
+                owners[f, count[f]] = tt
+                owner_face[f, count[f]] = i
+                count[f] += 1
+        self.tet2tet = np.full((nt, 4), -1, dtype=np.int64)
+        self.tet2face = np.full((nt, 4), -1, dtype=np.int64)  # local face index in the neighbour
+        for f in np.nonzero(count == 2)[0]:
+            a, b = owners[f]
+            ia, ib = owner_face[f]
+            self.tet2tet[a, ia], self.tet2face[a, ia] = b, ib
+            self.tet2tet[b, ib], self.tet2face[b, ib] = a, ia
+        self.boundary_face = count == 1
+        bf = self.faces[self.boundary_face]
+        self.boundary_node = np.zeros(self.n_nodes, dtype=bool)
+        self.boundary_node[bf.ravel()] = True
+        bedge = set()
+        for (a, b, c) in bf:
+            bedge.update([(a, b), (a, c), (b, c)])
+        self.boundary_edge = np.zeros(self.n_edges, dtype=bool)
+        if bedge:
+            be = np.array(sorted(bedge), dtype=np.int64)
+            key = self.edges[:, 0] * self.n_nodes + self.edges[:, 1]
+            bkey = be[:, 0] * self.n_nodes + be[:, 1]
+            self.boundary_edge = np.isin(key, bkey)
+        self._dofs()
+
+    def _dofs(self):
+        ne, nf, nt, nn = self.n_edges, self.n_faces, self.n_tets, self.n_nodes
+        te, tf = self.tet_edges, self.tet_faces
+        if self.order == 1:
+            self.n1, self.n2, self.n0 = ne, nf, nn
+            self.dof1 = te.copy()
+            self.dof2 = tf.copy()
+            self.dof0 = self.tets.copy()
+            self.pec1 = self.boundary_edge.copy()
+            self.bnd0 = self.boundary_node.copy()
+        else:
+            self.n1 = 2 * ne + 2 * nf
+            self.n2 = 3 * nf + 3 * nt
+            self.n0 = nn + ne
+            d1 = np.zeros((nt, 20), dtype=np.int64)
+            d1[:, 0:12:2] = 2 * te
+            d1[:, 1:12:2] = 2 * te + 1
+            d1[:, 12:20:2] = 2 * ne + 2 * tf
+            d1[:, 13:20:2] = 2 * ne + 2 * tf + 1
+            self.dof1 = d1
+            d2 = np.zeros((nt, 15), dtype=np.int64)
+            for v in range(3):
+                d2[:, v:12:3] = 3 * tf + v
+            for i in range(3):
+                d2[:, 12 + i] = 3 * nf + 3 * np.arange(nt) + i
+            self.dof2 = d2
+            self.dof0 = np.concatenate([self.tets, nn + te], axis=1)
+            pec = np.zeros(self.n1, dtype=bool)
+            be = np.nonzero(self.boundary_edge)[0]
+            pec[2 * be] = True
+            pec[2 * be + 1] = True
+            bfid = np.nonzero(self.boundary_face)[0]
+            pec[2 * ne + 2 * bfid] = True
+            pec[2 * ne + 2 * bfid + 1] = True
+            self.pec1 = pec
+            self.bnd0 = np.concatenate([self.boundary_node, self.boundary_edge])
+        self.free1 = ~self.pec1
+        self.interior0 = ~self.bnd0
