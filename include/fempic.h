@@ -1,0 +1,235 @@
+/*
+ * fempic.h -- C ABI of the GB300 EM-FEMPIC library.
+ *
+ * The library advances one charged species and the electromagnetic field on an
+ * unstructured tetrahedral mesh with the higher-order, charge-conserving
+ * finite-element particle-in-cell method of Crawford, Ramachandran, O'Connor,
+ * Luginsland and Shanker, "Higher Order Charge Conserving Electromagnetic
+ * Finite Element Particle in Cell Method" (arXiv 2111.12411):
+ *
+ *   - E is expanded in order-p interpolatory Whitney edge functions W1 and B in
+ *     face functions W2 (Section III-A, Appendix), p = 1 or 2;
+ *   - each step gathers E and B at every particle, applies the Lorentz force
+ *     (Section II), moves the particle on a straight chord, walks the chord
+ *     through the tets by ray-face intersection, and deposits the exact path
+ *     integral q w int W1_i . dr of every edge function into the current DOFs
+ *     g (Section III-B, g_i = <W1_i, G>), which conserves charge;
+ *   - the fields advance with the implicit Newmark (average acceleration)
+ *     scheme, gamma = 1/2, beta = 1/4 (Section III-B), solved on the device by
+ *     preconditioned conjugate gradients;
+ *   - charge is measured with the order-p nodal functions W0 (Section III-A).
+ *
+ * Conventions shared by every entry point:
+ *   - All pointers named *_host are host memory owned by the caller; the
+ *     library copies from/to them and never keeps them.  All device memory is
+ *     owned by the library and released by femPIC_destroy.
+ *   - Every function returns FEMPIC_OK (0) or one of the FEMPIC_ERR_* codes and
+ *     never exits, aborts or traps; femPIC_last_error gives a message.
+ *   - Device-side failures (crossing cap, CG iteration cap, barrier timeout)
+ *     are latched in a device status word and reported by the next call that
+ *     synchronises (femPIC_step, femPIC_sync, femPIC_get).
+ *   - DOF numbering: tet vertices are sorted by global node id; edges (sorted
+ *     node pairs) and faces (sorted triples) are numbered in lexicographic
+ *     order.  Order 1: W1 DOF = edge, W2 DOF = face, W0 DOF = node.  Order 2:
+ *     W1 DOFs 2*edge+v (v=0: (3 l_lo - 1) w, v=1: (3 l_hi - 1) w) then
+ *     2*N_e + 2*face + v (v=0: 3 l_u w_st, v=1: 3 l_t w_su for face s<t<u);
+ *     W2 DOFs 3*face + v ((4 l_v - 1) w_stu for the v-th face vertex) then
+ *     3*N_f + 3*tet + i (4 l_i w_(face opposite local vertex i), i = 0..2);
+ *     W0 DOFs nodes then N_n + edge (mid-edge Lagrange nodes).
+ *   - Units are SI.  The boundary is a perfect electric conductor: W1 DOFs on
+ *     boundary edges/faces are held at 0 and particles reflect specularly.
+ */
+#ifndef FEMPIC_H
+#define FEMPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+enum {
+  FEMPIC_OK = 0,
+  FEMPIC_ERR_ARG = 1,    /* bad argument (NULL, size, order, option)            */
+  FEMPIC_ERR_MESH = 2,   /* degenerate tet, node out of range, non-manifold face */
+  FEMPIC_ERR_OOM = 3,    /* device allocation failed                             */
+  FEMPIC_ERR_CUDA = 4,   /* a CUDA call failed (message has the CUDA error)      */
+  FEMPIC_ERR_CG = 5,     /* CG hit its iteration cap before the tolerance        */
+  FEMPIC_ERR_WALK = 6,   /* a particle hit the face-crossing cap in one step     */
+  FEMPIC_ERR_SIZE = 7,   /* caller buffer size does not match the quantity       */
+  FEMPIC_ERR_STATE = 8,  /* call not valid in the current state                  */
+  FEMPIC_ERR_BARRIER = 9 /* a device grid barrier timed out                      */
+};
+
+/* ---- precision modes (set at create) ------------------------------------ */
+enum {
+  FEMPIC_FP64_STRICT = 0, /* all FP64, every operation rounded separately in the
+                             order the reference evaluation uses (no FMA): the
+                             walk's decisions are bit-reproducible             */
+  FEMPIC_FP64 = 1,        /* all FP64, fused multiply-add and factored forms   */
+  FEMPIC_MIXED = 2        /* FP32 gather and push; FP64 positions, walk,
+                             deposit, charge and CG                            */
+};
+
+/* ---- field time schemes ------------------------------------------------- */
+enum {
+  FEMPIC_SCHEME_TRAPEZOID = 0, /* gamma = 1/2, beta = 1/4 on the [b; e] system */
+  FEMPIC_SCHEME_WAVE = 1       /* second-order e form with free gamma, beta    */
+};
+
+/* ---- quantities for femPIC_get / femPIC_set ----------------------------- */
+enum {
+  FEMPIC_E = 0,        /* double[N1]  electric field DOFs e^n                   */
+  FEMPIC_B = 1,        /* double[N2]  magnetic flux DOFs b^n (self field only;
+                          the uniform impressed B0 is added at the gather)      */
+  FEMPIC_DG = 2,       /* double[N1]  g^n - g^{n-1} deposited by the last step  */
+  FEMPIC_RHO = 3,      /* double[N0]  rho_k = q w sum_p W0_k(x_p)               */
+  FEMPIC_X = 4,        /* double[3*Np] positions, particle-id order, xyz interleaved */
+  FEMPIC_V = 5,        /* double[3*Np] velocities v^{n-1/2}                     */
+  FEMPIC_TET = 6,      /* int32[Np]   owning tet                                */
+  FEMPIC_NCROSS = 7,   /* int32[Np]   face crossings (incl. wall hits), last step */
+  FEMPIC_HASH = 8,     /* uint64[Np]  FNV-1a style hash of the last step's crossing
+                          events: h = (h ^ code) * 1099511628211 from
+                          14695981039346656037, code = new tet id, or
+                          0x80000000 | local face for a wall reflection        */
+  FEMPIC_E_PREV = 9,   /* double[N1]  e^{n-1} (wave scheme, CG initial guess)    */
+  FEMPIC_DG_PREV = 10, /* double[N1]  Delta g of the step before (wave scheme)   */
+  FEMPIC_DIAG = 11,    /* femPIC_diag (get only)                                */
+  FEMPIC_PHI = 12      /* double[N0]  potential of the electrostatic start (get) */
+};
+
+/* ---- operators for femPIC_apply ----------------------------------------- */
+enum {
+  FEMPIC_OP_M1 = 0,  /* [*eps]    N1 x N1 (PEC rows/cols removed)              */
+  FEMPIC_OP_K = 1,   /* K = C^T [*mu^-1] C, N1 x N1 (PEC rows/cols removed)    */
+  FEMPIC_OP_C = 2,   /* curl map C, N2 x N1: curl W1_j = sum_f C_fj W2_f        */
+  FEMPIC_OP_D = 3,   /* grad map D, N1 x N0: grad W0_k = sum_i D_ik W1_i        */
+  FEMPIC_OP_DT = 4,  /* D^T, N0 x N1                                            */
+  FEMPIC_OP_M2 = 5,  /* [*mu^-1], N2 x N2                                       */
+  FEMPIC_OP_A = 6,   /* system matrix of the last dt, N1 x N1                   */
+  FEMPIC_OP_L = 7    /* nodal Laplacian D^T [*eps] D on interior W0 DOFs        */
+};
+
+typedef struct FemPIC FemPIC; /* opaque handle */
+
+/* Mesh (Section III-A: K = {N, E, F, T}).  Vertex order inside a tet is free. */
+typedef struct {
+  int32_t n_nodes;
+  int32_t n_tets;
+  const double* xyz_host;   /* [3*n_nodes] node coordinates (m)               */
+  const int32_t* tets_host; /* [4*n_tets] node ids                             */
+} femPIC_mesh;
+
+/* One species of macro particles (Section II: a single species). */
+typedef struct {
+  double q;                 /* charge of one physical particle (C)             */
+  double m;                 /* mass of one physical particle (kg)              */
+  double weight;            /* physical particles per macro particle           */
+  int64_t n;                /* number of macro particles (>= 0)                */
+  const double* x_host;     /* [3n] positions                                  */
+  const double* v_host;     /* [3n] velocities, taken as v^{-1/2}              */
+  const int32_t* tet_host;  /* [n] tet containing each position (checked)      */
+} femPIC_species;
+
+typedef struct {
+  int32_t precision;    /* FEMPIC_FP64_STRICT / FEMPIC_FP64 / FEMPIC_MIXED     */
+  int32_t scheme;       /* FEMPIC_SCHEME_*                                     */
+  double gamma, beta;   /* Newmark parameters of the wave scheme               */
+  double cg_rtol;       /* stop when ||r|| <= cg_rtol ||rhs||                   */
+  int32_t cg_max_it;    /* iteration cap (FEMPIC_ERR_CG when reached)          */
+  int32_t max_cross;    /* face crossings per particle per step (FEMPIC_ERR_WALK) */
+  int32_t sort_period;  /* re-sort particles by tet every this many steps (0 = never) */
+  double B0[3];         /* uniform impressed magnetic flux density (T)         */
+  double rho_ion;       /* uniform neutralising charge density (C/m^3)         */
+  int32_t es_init;      /* 1: solve the electrostatic start at create          */
+  int32_t diagnostics;  /* 1: compute continuity/Gauss residuals every step    */
+  int32_t device;       /* CUDA device ordinal                                  */
+  void* stream;         /* cudaStream_t to run on; NULL = library-owned stream */
+} femPIC_opts;
+
+/* Per-step diagnostics (Section IV-D): continuity and Gauss residuals. */
+typedef struct {
+  int64_t steps;            /* steps taken since create                        */
+  int32_t status;           /* latched FEMPIC_* status of the device            */
+  int32_t cg_iterations;    /* iterations of the last field solve              */
+  double cg_residual;       /* ||r|| / ||rhs|| of the last field solve          */
+  double continuity_abs;    /* ||rho^{n+1} - rho^n - D^T Delta g||_2, interior W0 */
+  double continuity_ref;    /* ||rho^{n+1} - rho^n||_2, interior W0             */
+  double gauss_abs;         /* ||D^T [*eps] e + rho + rho_ion <W0,1>||_2, interior */
+  double gauss_ref;         /* ||rho||_2, interior                             */
+  double crossings;         /* face crossings in the last step (all particles) */
+} femPIC_diag;
+
+typedef struct {
+  int32_t n_nodes, n_tets, n_edges, n_faces;
+  int32_t order;
+  int32_t n0, n1, n2;       /* global W0, W1, W2 DOF counts                     */
+  int32_t nl0, nl1, nl2;    /* local DOFs per tet                               */
+  int64_t n_particles;
+  int64_t nnz_A, nnz_C, nnz_Q;
+  int32_t n_boundary_faces;
+  size_t device_bytes;      /* device memory held by the handle                */
+} femPIC_info;
+
+/* Fill *opts with defaults: FP64, trapezoid, cg_rtol 1e-12, cg_max_it 2000,
+ * max_cross 4096, sort_period 1, B0 = 0, rho_ion = 0, es_init 1,
+ * diagnostics 0, device 0, stream NULL. */
+void femPIC_default_opts(femPIC_opts* opts);
+
+/* Build the mesh complex, DOF numbering, Hodge/curl/gradient matrices (Section
+ * III-A) and upload mesh, matrices and particles to the device.  order is p
+ * (1 or 2).  opts may be NULL for defaults.  On success *out holds a handle.
+ * On failure *out may still hold a handle that only carries the error message
+ * (femPIC_last_error); release it with femPIC_destroy. */
+int femPIC_create(const femPIC_mesh* mesh, int32_t order, const femPIC_species* species,
+                  const femPIC_opts* opts, FemPIC** out);
+
+/* Advance n_steps PIC steps of size dt (s): gather, Lorentz push, walk,
+ * charge-conserving deposit, Newmark field solve, b update, rho measurement
+ * (Section III-B).  Returns after the device finished; the return value is
+ * the latched device status. */
+int femPIC_step(FemPIC* h, double dt, int32_t n_steps);
+
+/* Same as femPIC_step but returns as soon as the work is enqueued on the
+ * handle's stream; femPIC_sync collects the status. */
+int femPIC_step_async(FemPIC* h, double dt, int32_t n_steps);
+int femPIC_sync(FemPIC* h);
+
+/* Copy a quantity to/from caller memory; bytes must equal its size. */
+int femPIC_get(FemPIC* h, int32_t what, void* host_dst, size_t bytes);
+int femPIC_set(FemPIC* h, int32_t what, const void* host_src, size_t bytes);
+
+/* Copy the same quantities to/from device memory the caller owns (same
+ * device, ordered on the handle's stream; synchronous on return).  Unlike
+ * femPIC_set, femPIC_set_device does not range-check tet ids: the caller
+ * guarantees 0 <= tet < n_tets. */
+int femPIC_get_device(FemPIC* h, int32_t what, void* dev_dst, size_t bytes);
+int femPIC_set_device(FemPIC* h, int32_t what, const void* dev_src, size_t bytes);
+
+/* y = Op x for one of the FEMPIC_OP_* operators (host vectors). */
+int femPIC_apply(FemPIC* h, int32_t op, const double* x_host, size_t nx,
+                 double* y_host, size_t ny);
+
+/* E(x) and B(x) (B includes B0) at n points with known owning tets, evaluated
+ * with the handle's precision mode (Section III-A field expansions). */
+int femPIC_eval_fields(FemPIC* h, int64_t n, const double* x_host, const int32_t* tet_host,
+                       double* E_host, double* B_host);
+
+int femPIC_get_info(const FemPIC* h, femPIC_info* info);
+
+/* Time (ms) of the device work of the last femPIC_step call split into the
+ * particle loop (sort, gather, push, walk, deposit, charge) and the field
+ * update (right-hand side, CG, b update), measured with CUDA events on the
+ * handle's stream; times[2] = kernel launches in that call. */
+int femPIC_last_timing(const FemPIC* h, double* times, int32_t n);
+
+void femPIC_destroy(FemPIC* h);
+const char* femPIC_last_error(const FemPIC* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEMPIC_H */

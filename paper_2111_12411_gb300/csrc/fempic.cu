@@ -1,0 +1,1062 @@
+// C-ABI entry points of the EM-FEMPIC library (see include/fempic.h): handle
+// life cycle, the per-step launch sequence, state transfer and operators.
+//
+// Step sequence (Section III-B; the PIC cycle of Section II):
+//   [sort particles by tet] -> zero Delta g, rho ->
+//   k_particle: gather E^n, B^n; Boris push; walk; deposit Delta g^{n+1}; rho^{n+1}
+//   -> k_rhs: Newmark right-hand side -> k_pcg: ([*eps] + dt^2/4 K) e^{n+1} = rhs
+//   -> k_bupdate: b^{n+1} = b^n - dt/2 C (e^{n+1} + e^n) -> [diagnostics]
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fempic.h"
+#include "internal.h"
+#include "kernels.cuh"
+#include "linalg.cuh"
+
+using namespace fempic;
+using namespace fempic::dev;
+
+namespace {
+
+struct DevCSR {
+  int32_t n_rows = 0, n_cols = 0;
+  int64_t nnz = 0;
+  int32_t* rp = nullptr;
+  int32_t* ci = nullptr;
+  double* v = nullptr;
+  CsrView view(const double* vals = nullptr) const { return CsrView{n_rows, rp, ci, vals ? vals : v}; }
+};
+
+}  // namespace
+
+struct FemPIC {
+  femPIC_opts opts;
+  std::string err;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  // model sizes
+  int order = 1, nl0 = 4, nl1 = 6, nl2 = 4;
+  int32_t n_nodes = 0, n_tets = 0, n_edges = 0, n_faces = 0, n0 = 0, n1 = 0, n2 = 0, n_bfaces = 0;
+  // species
+  double q = 0, m = 0, weight = 0;
+  int64_t np = 0;
+  // device mesh
+  double* geom = nullptr;
+  int32_t *nbr = nullptr, *dof0 = nullptr, *dof1 = nullptr, *dof2 = nullptr;
+  uint8_t *pec1 = nullptr, *int0 = nullptr;
+  double* load0 = nullptr;
+  // matrices
+  DevCSR M, K, Q, C, M2, D, DT, L;
+  double *Aval = nullptr, *R1val = nullptr, *R2val = nullptr, *dinvA = nullptr, *dinvL = nullptr;
+  // fields
+  double *e = nullptr, *e_prev = nullptr, *e_new = nullptr, *b = nullptr, *dg = nullptr, *dg_prev = nullptr;
+  double *rho = nullptr, *rho_prev = nullptr, *phi = nullptr, *rhs = nullptr;
+  // CG scratch
+  double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *partials = nullptr;
+  GridBarrier* bar = nullptr;
+  int pcg_blocks_w1 = 0, pcg_blocks_w0 = 0;
+  // particles (device order), SoA
+  double* px[3] = {nullptr, nullptr, nullptr};
+  double* pv[3] = {nullptr, nullptr, nullptr};
+  double* alt[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* stage = nullptr;  // [3*np] staging for particle-id ordered transfers
+  int32_t *ptet = nullptr, *pid = nullptr, *ptet_alt = nullptr, *pid_alt = nullptr;
+  int32_t *pncross = nullptr;
+  unsigned long long* phash = nullptr;
+  int32_t *sort_cnt = nullptr, *sort_off = nullptr, *sort_sums = nullptr, *sort_sums2 = nullptr;
+  // status / counters
+  int32_t* d_status = nullptr;
+  int32_t* d_cg_iters = nullptr;
+  double* d_cg_res = nullptr;
+  double* d_norms = nullptr;  // [4]: continuity abs^2, ref^2, gauss abs^2, ref^2
+  unsigned long long* d_cross = nullptr;
+  double* d_tmp1 = nullptr;  // N1 scratch
+  double* d_tmp0 = nullptr;  // N0 scratch
+  double dt_cur = -1.0;
+  int64_t steps = 0;
+  int64_t since_sort = 0;
+  // timing of the last femPIC_step call
+  std::vector<cudaEvent_t> ev;
+  double t_particle_ms = 0, t_field_ms = 0;
+  int launches = 0;
+  int pending_steps = 0;
+};
+
+namespace {
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+      return FEMPIC_ERR_CUDA;                                                      \
+    }                                                                              \
+  } while (0)
+
+template <class T>
+int dalloc(FemPIC* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    h->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? FEMPIC_ERR_OOM : FEMPIC_ERR_CUDA;
+  }
+  h->allocs.push_back(*p);
+  h->bytes += count * sizeof(T);
+  return FEMPIC_OK;
+}
+
+template <class T>
+int upload(FemPIC* h, T** p, const std::vector<T>& src) {
+  int rc = dalloc(h, p, src.size());
+  if (rc) return rc;
+  if (!src.empty()) CK(cudaMemcpy(*p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return FEMPIC_OK;
+}
+
+int upload_csr(FemPIC* h, DevCSR* d, const HostCSR& s) {
+  d->n_rows = s.n_rows;
+  d->n_cols = s.n_cols;
+  d->nnz = s.nnz();
+  int rc = upload(h, &d->rp, s.rowptr);
+  if (!rc) rc = upload(h, &d->ci, s.col);
+  if (!rc) rc = upload(h, &d->v, s.val);
+  return rc;
+}
+
+inline int grid_for(int64_t work, int block, int cap) {
+  int64_t g = (work + block - 1) / block;
+  if (g < 1) g = 1;
+  return (int)std::min<int64_t>(g, cap);
+}
+
+int lpr_w1(const FemPIC* h) { return h->order == 1 ? 4 : 8; }
+
+int latch_status(FemPIC* h) {
+  int32_t st = 0;
+  CK(cudaMemcpyAsync(&st, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (st & kStatusBarrier) {
+    h->err = "device grid barrier timed out";
+    return FEMPIC_ERR_BARRIER;
+  }
+  if (st & kStatusWalk) {
+    h->err = "a particle reached the face-crossing cap (max_cross)";
+    return FEMPIC_ERR_WALK;
+  }
+  if (st & kStatusCG) {
+    h->err = "CG reached its iteration cap before the tolerance";
+    return FEMPIC_ERR_CG;
+  }
+  return FEMPIC_OK;
+}
+
+template <int LPR>
+int launch_spmv(FemPIC* h, const CsrView& A, const double* x, double* y, double alpha, double beta) {
+  int grid = grid_for((int64_t)A.n_rows * LPR, 256, h->num_sms * 16);
+  k_spmv<LPR><<<grid, 256, 0, h->stream>>>(A, x, y, alpha, beta);
+  h->launches++;
+  CK(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+int spmv(FemPIC* h, const CsrView& A, const double* x, double* y, double alpha = 1.0, double beta = 0.0) {
+  return h->order == 1 ? launch_spmv<4>(h, A, x, y, alpha, beta) : launch_spmv<8>(h, A, x, y, alpha, beta);
+}
+
+// co-resident blocks of the persistent PCG kernel, or -1 on error
+template <int LPR>
+int pcg_blocks(FemPIC* h) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<LPR>, 256, 0);
+  if (e != cudaSuccess) {
+    h->err = std::string("occupancy query: ") + cudaGetErrorString(e);
+    return -1;
+  }
+  return std::max(1, per_sm) * h->num_sms;
+}
+
+// Solve A x = rhs (x holds the initial guess) on the device; with nodal, the
+// preconditioner adds the auxiliary nodal correction D L_diag^-1 D^T.
+int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, double* x, int blocks,
+            bool nodal) {
+  PcgArgs a;
+  a.A = A;
+  a.dinv = dinv;
+  a.D = nodal ? h->D.view() : CsrView{0, nullptr, nullptr, nullptr};
+  a.DT = nodal ? h->DT.view() : CsrView{0, nullptr, nullptr, nullptr};
+  a.dinvL = h->dinvL;
+  a.t = h->d_tmp0;
+  a.rhs = rhs;
+  a.x = x;
+  a.r = h->cg_r;
+  a.z = h->cg_z;
+  a.p = h->cg_p;
+  a.q = h->cg_q;
+  a.partials = h->partials;
+  a.bar = h->bar;
+  a.status = h->d_status;
+  a.iters_out = h->d_cg_iters;
+  a.res_out = h->d_cg_res;
+  a.rtol = h->opts.cg_rtol;
+  a.max_it = h->opts.cg_max_it;
+  CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), h->stream));
+  void* args[] = {&a};
+  if (h->order == 1)
+    CK(cudaLaunchCooperativeKernel((void*)k_pcg<4>, blocks, 256, args, 0, h->stream));
+  else
+    CK(cudaLaunchCooperativeKernel((void*)k_pcg<8>, blocks, 256, args, 0, h->stream));
+  h->launches++;
+  return FEMPIC_OK;
+}
+
+int form_system(FemPIC* h, double dt) {
+  double c1;
+  double cr1, cr2 = 0.0;
+  if (h->opts.scheme == FEMPIC_SCHEME_TRAPEZOID) {
+    c1 = 0.25 * dt * dt;
+    cr1 = -0.25 * dt * dt;  // R1 = M - dt^2/4 K
+  } else {
+    double g = h->opts.gamma, be = h->opts.beta;
+    c1 = be * dt * dt;
+    double c2 = 0.5 + g - 2.0 * be, c3 = 0.5 - g + be;
+    cr1 = -c2 * dt * dt;  // R1 = 2M - c2 dt^2 K  (M part doubled below)
+    cr2 = c3 * dt * dt;   // R2 = M + c3 dt^2 K
+  }
+  int grid = grid_for(h->n1, 256, 1 << 30);
+  k_form_system<<<grid, 256, 0, h->stream>>>(h->n1, h->M.rp, h->M.ci, h->M.v, h->K.v, c1, cr1, h->Aval, h->R1val,
+                                             h->dinvA);
+  h->launches++;
+  CK(cudaGetLastError());
+  if (h->opts.scheme == FEMPIC_SCHEME_WAVE) {
+    // R1 = 2M - c2 dt^2 K = (M - c2 dt^2 K) + M: form as M*2 via a second pass
+    // using R2 scratch: R2 <- M + cr2 K; R1 <- R1 + M
+    k_form_system<<<grid, 256, 0, h->stream>>>(h->n1, h->M.rp, h->M.ci, h->M.v, h->K.v, cr2, 0.0, h->R2val, nullptr,
+                                               h->d_tmp1);
+    h->launches++;
+    CK(cudaGetLastError());
+    // R1 += M (reuse k_form_system with a = R1 + 1*M by passing m=R1 and k=M)
+    k_form_system<<<grid, 256, 0, h->stream>>>(h->n1, h->M.rp, h->M.ci, h->R1val, h->M.v, 1.0, 0.0, h->R1val,
+                                               nullptr, h->d_tmp1);
+    h->launches++;
+    CK(cudaGetLastError());
+  }
+  h->dt_cur = dt;
+  return FEMPIC_OK;
+}
+
+int measure_rho(FemPIC* h, double* rho_out) {
+  CK(cudaMemsetAsync(rho_out, 0, sizeof(double) * h->n0, h->stream));
+  if (h->np == 0) return FEMPIC_OK;
+  int grid = grid_for(h->np, 256, 1 << 30);
+  double qw = h->q * h->weight;
+  if (h->order == 1)
+    k_rho<1><<<grid, 256, 0, h->stream>>>(h->np, h->px[0], h->px[1], h->px[2], h->ptet, h->geom, h->dof0, qw,
+                                          rho_out);
+  else
+    k_rho<2><<<grid, 256, 0, h->stream>>>(h->np, h->px[0], h->px[1], h->px[2], h->ptet, h->geom, h->dof0, qw,
+                                          rho_out);
+  h->launches++;
+  CK(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+// exclusive scan of cnt[0..n) into off (recursive over 1024-element tiles)
+int scan_excl(FemPIC* h, int32_t n, const int32_t* in, int32_t* out, int32_t* sums, int32_t* sums2) {
+  int tiles = (n + 1023) / 1024;
+  k_scan_tiles<<<tiles, 1024, 0, h->stream>>>(n, in, out, tiles > 1 ? sums : nullptr);
+  h->launches++;
+  CK(cudaGetLastError());
+  if (tiles > 1) {
+    if (tiles > 1024 * 1024) {
+      h->err = "too many tets for the scan";
+      return FEMPIC_ERR_ARG;
+    }
+    int t2 = (tiles + 1023) / 1024;
+    k_scan_tiles<<<t2, 1024, 0, h->stream>>>(tiles, sums, sums, t2 > 1 ? sums2 : nullptr);
+    h->launches++;
+    if (t2 > 1) {
+      k_scan_tiles<<<1, 1024, 0, h->stream>>>(t2, sums2, sums2, nullptr);
+      k_scan_add<<<t2, 1024, 0, h->stream>>>(tiles, sums, sums2);
+      h->launches += 2;
+    }
+    k_scan_add<<<tiles, 1024, 0, h->stream>>>(n, out, sums);
+    h->launches++;
+    CK(cudaGetLastError());
+  }
+  return FEMPIC_OK;
+}
+
+int sort_particles(FemPIC* h) {
+  if (h->np == 0) return FEMPIC_OK;
+  CK(cudaMemsetAsync(h->sort_cnt, 0, sizeof(int32_t) * h->n_tets, h->stream));
+  int grid = grid_for(h->np, 256, 1 << 30);
+  k_hist<<<grid, 256, 0, h->stream>>>(h->np, h->ptet, h->sort_cnt);
+  h->launches++;
+  CK(cudaGetLastError());
+  int rc = scan_excl(h, h->n_tets, h->sort_cnt, h->sort_off, h->sort_sums, h->sort_sums2);
+  if (rc) return rc;
+  SortArgs a;
+  a.n = h->np;
+  a.tet_in = h->ptet;
+  a.cursor = h->sort_off;
+  for (int k = 0; k < 3; ++k) {
+    a.src[k] = h->px[k];
+    a.src[3 + k] = h->pv[k];
+    a.dst[k] = h->alt[k];
+    a.dst[3 + k] = h->alt[3 + k];
+  }
+  a.ti[0] = h->ptet;
+  a.ti[1] = h->pid;
+  a.to[0] = h->ptet_alt;
+  a.to[1] = h->pid_alt;
+  k_sort_scatter<<<grid, 256, 0, h->stream>>>(a);
+  h->launches++;
+  CK(cudaGetLastError());
+  for (int k = 0; k < 3; ++k) {
+    std::swap(h->px[k], h->alt[k]);
+    std::swap(h->pv[k], h->alt[3 + k]);
+  }
+  std::swap(h->ptet, h->ptet_alt);
+  std::swap(h->pid, h->pid_alt);
+  return FEMPIC_OK;
+}
+
+int launch_particles(FemPIC* h, double dt) {
+  ParticleArgs a;
+  a.n = h->np;
+  for (int k = 0; k < 3; ++k) {
+    a.x[k] = h->px[k];
+    a.v[k] = h->pv[k];
+  }
+  a.tet = h->ptet;
+  a.ncross = h->pncross;
+  a.hash = h->phash;
+  a.geom = h->geom;
+  a.nbr = h->nbr;
+  a.dof0 = h->dof0;
+  a.dof1 = h->dof1;
+  a.dof2 = h->dof2;
+  a.e = h->e;
+  a.b = h->b;
+  a.dg = h->dg;
+  a.rho = h->rho;
+  for (int k = 0; k < 3; ++k) a.B0[k] = h->opts.B0[k];
+  a.h = ((h->q / h->m) * dt) * 0.5;
+  a.dt = dt;
+  a.qw = h->q * h->weight;
+  a.max_cross = h->opts.max_cross;
+  a.status = h->d_status;
+  a.crossings = h->d_cross;
+  if (h->np == 0) return FEMPIC_OK;
+  int grid = grid_for(h->np, 256, 1 << 30);
+  bool strict = h->opts.precision == FEMPIC_FP64_STRICT;
+  if (h->order == 1) {
+    if (strict)
+      k_particle<1, Strict><<<grid, 256, 0, h->stream>>>(a);
+    else
+      k_particle<1, Fast><<<grid, 256, 0, h->stream>>>(a);
+  } else {
+    if (strict)
+      k_particle<2, Strict><<<grid, 256, 0, h->stream>>>(a);
+    else
+      k_particle<2, Fast><<<grid, 256, 0, h->stream>>>(a);
+  }
+  h->launches++;
+  CK(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+int field_update(FemPIC* h, double dt) {
+  bool trap = h->opts.scheme == FEMPIC_SCHEME_TRAPEZOID;
+  // initial guess: linear extrapolation 2 e^n - e^{n-1}
+  {
+    int g = grid_for(h->n1, 256, h->num_sms * 8);
+    k_lincomb<<<g, 256, 0, h->stream>>>(h->n1, h->e, h->e_prev, 2.0, -1.0, h->e_new);
+    h->launches++;
+    CK(cudaGetLastError());
+  }
+  CsrView R1 = h->M.view(h->R1val);
+  CsrView Qv = h->Q.view();
+  int grid = grid_for((int64_t)h->n1 * lpr_w1(h), 256, h->num_sms * 16);
+  if (h->order == 1)
+    k_rhs<4><<<grid, 256, 0, h->stream>>>(R1, trap ? nullptr : h->R2val, Qv, h->e, h->e_prev, h->b, trap ? dt : 0.0,
+                                          h->dg, h->dg_prev, trap ? 0.0 : 1.0, h->pec1, h->rhs);
+  else
+    k_rhs<8><<<grid, 256, 0, h->stream>>>(R1, trap ? nullptr : h->R2val, Qv, h->e, h->e_prev, h->b, trap ? dt : 0.0,
+                                          h->dg, h->dg_prev, trap ? 0.0 : 1.0, h->pec1, h->rhs);
+  h->launches++;
+  CK(cudaGetLastError());
+  int rc = run_pcg(h, h->M.view(h->Aval), h->dinvA, h->rhs, h->e_new, h->pcg_blocks_w1, true);
+  if (rc) return rc;
+  int gridc = grid_for((int64_t)h->n2 * 4, 256, h->num_sms * 16);
+  k_bupdate<4><<<gridc, 256, 0, h->stream>>>(h->C.view(), h->e_new, h->e, 0.5 * dt, h->b);
+  h->launches++;
+  CK(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+int diagnostics(FemPIC* h) {
+  // continuity: (rho - rho_prev) - D^T dg ; Gauss: D^T M e + rho + rho_ion load
+  CK(cudaMemsetAsync(h->d_norms, 0, sizeof(double) * 4, h->stream));
+  int rc = spmv(h, h->DT.view(), h->dg, h->d_tmp0);
+  if (rc) return rc;
+  int grid = grid_for(h->n0, 256, h->num_sms * 8);
+  k_norms2<<<grid, 256, 0, h->stream>>>(h->n0, h->int0, h->rho, h->rho_prev, h->d_tmp0, -1.0, 0.0, nullptr,
+                                        h->d_norms);
+  h->launches++;
+  rc = spmv(h, h->M.view(), h->e, h->d_tmp1);
+  if (rc) return rc;
+  rc = spmv(h, h->DT.view(), h->d_tmp1, h->d_tmp0);
+  if (rc) return rc;
+  k_norms2<<<grid, 256, 0, h->stream>>>(h->n0, h->int0, h->rho, nullptr, h->d_tmp0, 1.0, h->opts.rho_ion, h->load0,
+                                        h->d_norms + 2);
+  h->launches++;
+  CK(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+cudaEvent_t event_at(FemPIC* h, size_t i) {
+  while (h->ev.size() <= i) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->ev.push_back(e);
+  }
+  return h->ev[i];
+}
+
+int do_steps(FemPIC* h, double dt, int32_t n) {
+  if (!(dt > 0.0) || !std::isfinite(dt) || n < 0) {
+    h->err = "dt must be positive and finite, n_steps >= 0";
+    return FEMPIC_ERR_ARG;
+  }
+  CK(cudaSetDevice(h->device));
+  h->launches = 0;
+  if (dt != h->dt_cur) {
+    int rc = form_system(h, dt);
+    if (rc) return rc;
+  }
+  CK(cudaMemsetAsync(h->d_cross, 0, sizeof(unsigned long long), h->stream));
+  for (int32_t s = 0; s < n; ++s) {
+    cudaEvent_t e0 = event_at(h, 3 * s), e1 = event_at(h, 3 * s + 1), e2 = event_at(h, 3 * s + 2);
+    if (!e0 || !e1 || !e2) {
+      h->err = "cudaEventCreate failed";
+      return FEMPIC_ERR_CUDA;
+    }
+    CK(cudaEventRecord(e0, h->stream));
+    if (h->opts.sort_period > 0 && h->since_sort >= h->opts.sort_period) {
+      int rc = sort_particles(h);
+      if (rc) return rc;
+      h->since_sort = 0;
+    }
+    std::swap(h->dg, h->dg_prev);
+    std::swap(h->rho, h->rho_prev);
+    CK(cudaMemsetAsync(h->dg, 0, sizeof(double) * h->n1, h->stream));
+    CK(cudaMemsetAsync(h->rho, 0, sizeof(double) * h->n0, h->stream));
+    int rc = launch_particles(h, dt);
+    if (rc) return rc;
+    CK(cudaEventRecord(e1, h->stream));
+    rc = field_update(h, dt);
+    if (rc) return rc;
+    CK(cudaEventRecord(e2, h->stream));
+    // rotate e: e_prev <- e, e <- e_new
+    double* old_prev = h->e_prev;
+    h->e_prev = h->e;
+    h->e = h->e_new;
+    h->e_new = old_prev;
+    if (h->opts.diagnostics) {
+      rc = diagnostics(h);
+      if (rc) return rc;
+    }
+    h->steps++;
+    h->since_sort++;
+  }
+  h->pending_steps = n;
+  return FEMPIC_OK;
+}
+
+int collect_timing(FemPIC* h) {
+  h->t_particle_ms = h->t_field_ms = 0.0;
+  for (int s = 0; s < h->pending_steps; ++s) {
+    float a = 0.f, b = 0.f;
+    CK(cudaEventElapsedTime(&a, h->ev[3 * s], h->ev[3 * s + 1]));
+    CK(cudaEventElapsedTime(&b, h->ev[3 * s + 1], h->ev[3 * s + 2]));
+    h->t_particle_ms += a;
+    h->t_field_ms += b;
+  }
+  h->pending_steps = 0;
+  return FEMPIC_OK;
+}
+
+size_t what_bytes(const FemPIC* h, int32_t what) {
+  switch (what) {
+    case FEMPIC_E:
+    case FEMPIC_DG:
+    case FEMPIC_E_PREV:
+    case FEMPIC_DG_PREV:
+      return sizeof(double) * (size_t)h->n1;
+    case FEMPIC_B:
+      return sizeof(double) * (size_t)h->n2;
+    case FEMPIC_RHO:
+    case FEMPIC_PHI:
+      return sizeof(double) * (size_t)h->n0;
+    case FEMPIC_X:
+    case FEMPIC_V:
+      return sizeof(double) * 3 * (size_t)h->np;
+    case FEMPIC_TET:
+    case FEMPIC_NCROSS:
+      return sizeof(int32_t) * (size_t)h->np;
+    case FEMPIC_HASH:
+      return sizeof(uint64_t) * (size_t)h->np;
+    case FEMPIC_DIAG:
+      return sizeof(femPIC_diag);
+    default:
+      return 0;
+  }
+}
+
+double* field_ptr(FemPIC* h, int32_t what) {
+  switch (what) {
+    case FEMPIC_E:
+      return h->e;
+    case FEMPIC_B:
+      return h->b;
+    case FEMPIC_DG:
+      return h->dg;
+    case FEMPIC_RHO:
+      return h->rho;
+    case FEMPIC_E_PREV:
+      return h->e_prev;
+    case FEMPIC_DG_PREV:
+      return h->dg_prev;
+    case FEMPIC_PHI:
+      return h->phi;
+    default:
+      return nullptr;
+  }
+}
+
+// move a quantity between the handle and a buffer (host or device)
+int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, bool buf_on_device) {
+  if (!h) return FEMPIC_ERR_ARG;
+  size_t need = what_bytes(h, what);
+  if (need == 0 || (to_handle && (what == FEMPIC_DIAG || what == FEMPIC_PHI || what == FEMPIC_NCROSS ||
+                                  what == FEMPIC_HASH))) {
+    h->err = "unknown or read-only quantity";
+    return FEMPIC_ERR_ARG;
+  }
+  if (bytes != need) {
+    h->err = "buffer is " + std::to_string(bytes) + " bytes, quantity needs " + std::to_string(need);
+    return FEMPIC_ERR_SIZE;
+  }
+  if (!buf && need) {
+    h->err = "NULL buffer";
+    return FEMPIC_ERR_ARG;
+  }
+  if (to_handle && what == FEMPIC_TET && !buf_on_device) {
+    const int32_t* t = static_cast<const int32_t*>(buf);
+    for (int64_t i = 0; i < h->np; ++i)
+      if (t[i] < 0 || t[i] >= h->n_tets) {
+        h->err = "tet id out of range at particle " + std::to_string(i);
+        return FEMPIC_ERR_ARG;
+      }
+  }
+  CK(cudaSetDevice(h->device));
+  cudaMemcpyKind up = buf_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaMemcpyKind down = buf_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (what == FEMPIC_DIAG) {
+    femPIC_diag d;
+    memset(&d, 0, sizeof(d));
+    double norms[4];
+    CK(cudaMemcpyAsync(norms, h->d_norms, sizeof(norms), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&d.cg_iterations, h->d_cg_iters, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&d.cg_residual, h->d_cg_res, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    unsigned long long cr = 0;
+    CK(cudaMemcpyAsync(&cr, h->d_cross, sizeof(cr), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&d.status, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    d.steps = h->steps;
+    d.continuity_abs = std::sqrt(norms[0]);
+    d.continuity_ref = std::sqrt(norms[1]);
+    d.gauss_abs = std::sqrt(norms[2]);
+    d.gauss_ref = std::sqrt(norms[3]);
+    d.crossings = (double)cr;
+    if (buf_on_device)
+      CK(cudaMemcpy(buf, &d, sizeof(d), cudaMemcpyHostToDevice));
+    else
+      memcpy(buf, &d, sizeof(d));
+    return FEMPIC_OK;
+  }
+  if (double* f = field_ptr(h, what)) {
+    if (to_handle)
+      CK(cudaMemcpyAsync(f, buf, need, up, h->stream));
+    else
+      CK(cudaMemcpyAsync(buf, f, need, down, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FEMPIC_OK;
+  }
+  if (h->np == 0) return FEMPIC_OK;
+  int grid = grid_for(h->np, 256, 1 << 30);
+  double* stage = h->stage;
+  if (what == FEMPIC_X || what == FEMPIC_V) {
+    double** dst = what == FEMPIC_X ? h->px : h->pv;
+    if (to_handle) {
+      CK(cudaMemcpyAsync(stage, buf, need, up, h->stream));
+      k_gather_by_id<<<grid, 256, 0, h->stream>>>(h->np, h->pid, stage, dst[0], dst[1], dst[2]);
+    } else {
+      k_scatter_by_id<<<grid, 256, 0, h->stream>>>(h->np, h->pid, dst[0], dst[1], dst[2], stage);
+      CK(cudaMemcpyAsync(buf, stage, need, down, h->stream));
+    }
+  } else if (what == FEMPIC_TET || what == FEMPIC_NCROSS) {
+    int32_t* src = what == FEMPIC_TET ? h->ptet : h->pncross;
+    int32_t* st = reinterpret_cast<int32_t*>(stage);
+    if (to_handle) {
+      CK(cudaMemcpyAsync(st, buf, need, up, h->stream));
+      k_gather1_by_id<int32_t><<<grid, 256, 0, h->stream>>>(h->np, h->pid, st, src);
+    } else {
+      k_scatter1_by_id<int32_t><<<grid, 256, 0, h->stream>>>(h->np, h->pid, src, st);
+      CK(cudaMemcpyAsync(buf, st, need, down, h->stream));
+    }
+  } else if (what == FEMPIC_HASH) {
+    auto* st = reinterpret_cast<unsigned long long*>(stage);
+    k_scatter1_by_id<unsigned long long><<<grid, 256, 0, h->stream>>>(h->np, h->pid, h->phash, st);
+    CK(cudaMemcpyAsync(buf, st, need, down, h->stream));
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  if (to_handle && (what == FEMPIC_X || what == FEMPIC_TET)) {
+    int rc = measure_rho(h, h->rho);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return FEMPIC_OK;
+}
+
+int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp, const femPIC_opts* opts,
+                FemPIC* h) {
+  if (opts)
+    h->opts = *opts;
+  else
+    femPIC_default_opts(&h->opts);
+  const femPIC_opts& o = h->opts;
+  if (!mesh || !sp) {
+    h->err = "NULL mesh or species";
+    return FEMPIC_ERR_ARG;
+  }
+  if (order != 1 && order != 2) {
+    h->err = "order must be 1 or 2";
+    return FEMPIC_ERR_ARG;
+  }
+  if (o.precision < 0 || o.precision > 2 || o.scheme < 0 || o.scheme > 1 || !(o.cg_rtol > 0) ||
+      o.cg_max_it < 1 || o.max_cross < 1 || o.sort_period < 0) {
+    h->err = "invalid option";
+    return FEMPIC_ERR_ARG;
+  }
+  if (sp->n < 0 || (sp->n > 0 && (!sp->x_host || !sp->v_host || !sp->tet_host)) || !(sp->m > 0) ||
+      sp->n > INT32_MAX) {
+    h->err = "invalid species";
+    return FEMPIC_ERR_ARG;
+  }
+  HostModel hm;
+  std::string err;
+  int code = build_model(mesh->xyz_host, mesh->n_nodes, mesh->tets_host, mesh->n_tets, order, &hm, &err);
+  if (code) {
+    h->err = err;
+    return code == 2 ? FEMPIC_ERR_MESH : FEMPIC_ERR_ARG;
+  }
+  // particle ownership check on the host: lambda >= -1e-9 in the given tet
+  for (int64_t i = 0; i < sp->n; ++i) {
+    int32_t t = sp->tet_host[i];
+    if (t < 0 || t >= hm.n_tets) {
+      h->err = "particle " + std::to_string(i) + " has a tet id out of range";
+      return FEMPIC_ERR_ARG;
+    }
+    const double* g = &hm.geom[(size_t)t * 16];
+    const double* x = sp->x_host + 3 * i;
+    for (int k = 0; k < 4; ++k) {
+      double l = ((g[3 * k] * x[0] + g[3 * k + 1] * x[1]) + g[3 * k + 2] * x[2]) + g[12 + k];
+      if (!(l >= -1e-9)) {
+        h->err = "particle " + std::to_string(i) + " is not inside its tet";
+        return FEMPIC_ERR_ARG;
+      }
+    }
+  }
+  h->order = order;
+  h->nl0 = hm.nl0;
+  h->nl1 = hm.nl1;
+  h->nl2 = hm.nl2;
+  h->n_nodes = hm.n_nodes;
+  h->n_tets = hm.n_tets;
+  h->n_edges = hm.n_edges;
+  h->n_faces = hm.n_faces;
+  h->n0 = hm.n0;
+  h->n1 = hm.n1;
+  h->n2 = hm.n2;
+  h->n_bfaces = hm.n_bfaces;
+  h->q = sp->q;
+  h->m = sp->m;
+  h->weight = sp->weight;
+  h->np = sp->n;
+
+  h->device = o.device;
+  CK(cudaSetDevice(h->device));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, h->device));
+  h->num_sms = prop.multiProcessorCount;
+  if (o.stream) {
+    h->stream = (cudaStream_t)o.stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  int rc = 0;
+#define UP(dst, src)             \
+  rc = upload(h, &(dst), (src)); \
+  if (rc) return rc;
+  UP(h->geom, hm.geom);
+  UP(h->nbr, hm.nbr);
+  UP(h->dof0, hm.dof0);
+  UP(h->dof1, hm.dof1);
+  UP(h->dof2, hm.dof2);
+  UP(h->pec1, hm.pec1);
+  {
+    std::vector<uint8_t> i0(hm.n0);
+    for (int32_t i = 0; i < hm.n0; ++i) i0[i] = !hm.bnd0[i];
+    UP(h->int0, i0);
+  }
+  UP(h->load0, hm.load0);
+#undef UP
+  if ((rc = upload_csr(h, &h->M, hm.M)) || (rc = upload_csr(h, &h->K, hm.K)) || (rc = upload_csr(h, &h->Q, hm.Q)) ||
+      (rc = upload_csr(h, &h->C, hm.C)) || (rc = upload_csr(h, &h->M2, hm.M2)) || (rc = upload_csr(h, &h->D, hm.D)) ||
+      (rc = upload_csr(h, &h->DT, hm.DT)) || (rc = upload_csr(h, &h->L, hm.L)))
+    return rc;
+  const size_t nnz = hm.M.col.size();
+  if ((rc = dalloc(h, &h->Aval, nnz)) || (rc = dalloc(h, &h->R1val, nnz)) ||
+      (rc = dalloc(h, &h->R2val, o.scheme == FEMPIC_SCHEME_WAVE ? nnz : 1)) || (rc = dalloc(h, &h->dinvA, h->n1)) ||
+      (rc = dalloc(h, &h->dinvL, h->n0)))
+    return rc;
+  double** vec1[] = {&h->e, &h->e_prev, &h->e_new, &h->dg, &h->dg_prev, &h->d_tmp1};
+  for (auto p : vec1)
+    if ((rc = dalloc(h, p, h->n1))) return rc;
+  double** vec0[] = {&h->rho, &h->rho_prev, &h->phi, &h->d_tmp0};
+  for (auto p : vec0)
+    if ((rc = dalloc(h, p, h->n0))) return rc;
+  if ((rc = dalloc(h, &h->b, h->n2))) return rc;
+  int32_t nmax = std::max(h->n1, h->n0);
+  if ((rc = dalloc(h, &h->rhs, nmax))) return rc;
+  double** cgv[] = {&h->cg_r, &h->cg_z, &h->cg_p, &h->cg_q};
+  for (auto p : cgv)
+    if ((rc = dalloc(h, p, nmax))) return rc;
+  if (order == 1) {
+    int bl = pcg_blocks<4>(h);
+    if (bl < 0) return FEMPIC_ERR_CUDA;
+    h->pcg_blocks_w1 = h->pcg_blocks_w0 = bl;
+  } else {
+    int bl = pcg_blocks<8>(h);
+    if (bl < 0) return FEMPIC_ERR_CUDA;
+    h->pcg_blocks_w1 = h->pcg_blocks_w0 = bl;
+  }
+  if ((rc = dalloc(h, &h->partials, 4 * (size_t)h->pcg_blocks_w1)) || (rc = dalloc(h, &h->bar, 1)) ||
+      (rc = dalloc(h, &h->d_status, 1)) || (rc = dalloc(h, &h->d_cg_iters, 1)) || (rc = dalloc(h, &h->d_cg_res, 1)) ||
+      (rc = dalloc(h, &h->d_norms, 4)) || (rc = dalloc(h, &h->d_cross, 1)))
+    return rc;
+  for (void* p : std::vector<void*>{h->e, h->e_prev, h->e_new, h->dg, h->dg_prev})
+    CK(cudaMemset(p, 0, sizeof(double) * h->n1));
+  CK(cudaMemset(h->b, 0, sizeof(double) * h->n2));
+  CK(cudaMemset(h->phi, 0, sizeof(double) * h->n0));
+  CK(cudaMemset(h->rho_prev, 0, sizeof(double) * h->n0));
+  CK(cudaMemset(h->d_status, 0, sizeof(int32_t)));
+  CK(cudaMemset(h->d_cg_iters, 0, sizeof(int32_t)));
+  CK(cudaMemset(h->d_cg_res, 0, sizeof(double)));
+  CK(cudaMemset(h->d_norms, 0, 4 * sizeof(double)));
+  CK(cudaMemset(h->d_cross, 0, sizeof(unsigned long long)));
+  // particles
+  const int64_t n = h->np;
+  for (int k = 0; k < 3; ++k) {
+    if ((rc = dalloc(h, &h->px[k], n)) || (rc = dalloc(h, &h->pv[k], n))) return rc;
+  }
+  double* altblock = nullptr;
+  if ((rc = dalloc(h, &altblock, 6 * (size_t)std::max<int64_t>(n, 1)))) return rc;
+  for (int k = 0; k < 6; ++k) h->alt[k] = altblock + (size_t)k * std::max<int64_t>(n, 1);
+  if ((rc = dalloc(h, &h->stage, 3 * (size_t)std::max<int64_t>(n, 1)))) return rc;
+  if ((rc = dalloc(h, &h->ptet, n)) || (rc = dalloc(h, &h->pid, n)) || (rc = dalloc(h, &h->ptet_alt, n)) ||
+      (rc = dalloc(h, &h->pid_alt, n)) || (rc = dalloc(h, &h->pncross, n)) || (rc = dalloc(h, &h->phash, n)) ||
+      (rc = dalloc(h, &h->sort_cnt, h->n_tets)) || (rc = dalloc(h, &h->sort_off, h->n_tets)) ||
+      (rc = dalloc(h, &h->sort_sums, (h->n_tets + 1023) / 1024 + 1)) ||
+      (rc = dalloc(h, &h->sort_sums2, (h->n_tets + 1023) / 1024 / 1024 + 2)))
+    return rc;
+  if (n > 0) {
+    std::vector<double> tmp((size_t)n);
+    for (int k = 0; k < 3; ++k) {
+      for (int64_t i = 0; i < n; ++i) tmp[i] = sp->x_host[3 * i + k];
+      CK(cudaMemcpy(h->px[k], tmp.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+      for (int64_t i = 0; i < n; ++i) tmp[i] = sp->v_host[3 * i + k];
+      CK(cudaMemcpy(h->pv[k], tmp.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(h->ptet, sp->tet_host, n * sizeof(int32_t), cudaMemcpyHostToDevice));
+    std::vector<int32_t> ids((size_t)n);
+    for (int64_t i = 0; i < n; ++i) ids[i] = (int32_t)i;
+    CK(cudaMemcpy(h->pid, ids.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemset(h->pncross, 0, n * sizeof(int32_t)));
+    CK(cudaMemset(h->phash, 0, n * sizeof(unsigned long long)));
+  }
+  h->since_sort = h->opts.sort_period;  // sort before the first step
+  rc = measure_rho(h, h->rho);
+  if (rc) return rc;
+  {
+    int grid = grid_for(h->n0, 256, 1 << 30);
+    k_inv_diag<<<grid, 256, 0, h->stream>>>(h->n0, h->L.rp, h->L.ci, h->L.v, h->dinvL);
+    CK(cudaGetLastError());
+  }
+  // electrostatic start: L phi = rho + rho_ion <W0, 1> on interior DOFs, e = -D phi
+  if (o.es_init) {
+    // rhs0 = (rho + rho_ion load) masked to interior: use k_norms2-free path on the host side
+    CK(cudaStreamSynchronize(h->stream));
+    std::vector<double> rho_h(h->n0), rhs0(h->n0);
+    CK(cudaMemcpy(rho_h.data(), h->rho, sizeof(double) * h->n0, cudaMemcpyDeviceToHost));
+    for (int32_t i = 0; i < h->n0; ++i) rhs0[i] = hm.bnd0[i] ? 0.0 : rho_h[i] + o.rho_ion * hm.load0[i];
+    CK(cudaMemcpy(h->d_tmp0, rhs0.data(), sizeof(double) * h->n0, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(h->rhs, h->d_tmp0, sizeof(double) * h->n0, cudaMemcpyDeviceToDevice, h->stream));
+    rc = run_pcg(h, h->L.view(), h->dinvL, h->rhs, h->phi, h->pcg_blocks_w0, false);
+    if (rc) return rc;
+    rc = spmv(h, h->D.view(), h->phi, h->e, -1.0, 0.0);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->e_prev, h->e, sizeof(double) * h->n1, cudaMemcpyDeviceToDevice, h->stream));
+    rc = latch_status(h);
+    if (rc) {
+      h->err = "electrostatic start: " + h->err;
+      return rc;
+    }
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return FEMPIC_OK;
+}
+
+}  // namespace
+
+// =============================================================================
+extern "C" {
+
+void femPIC_default_opts(femPIC_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = FEMPIC_FP64;
+  o->scheme = FEMPIC_SCHEME_TRAPEZOID;
+  o->gamma = 0.5;
+  o->beta = 0.25;
+  o->cg_rtol = 1e-12;
+  o->cg_max_it = 2000;
+  o->max_cross = 4096;
+  o->sort_period = 1;
+  o->es_init = 1;
+  o->diagnostics = 0;
+  o->device = 0;
+  o->stream = nullptr;
+}
+
+int femPIC_create(const femPIC_mesh* mesh, int32_t order, const femPIC_species* species, const femPIC_opts* opts,
+                  FemPIC** out) {
+  if (!out) return FEMPIC_ERR_ARG;
+  *out = nullptr;
+  FemPIC* h = new (std::nothrow) FemPIC();
+  if (!h) return FEMPIC_ERR_OOM;
+  int rc = create_impl(mesh, order, species, opts, h);
+  *out = h;  // the handle carries the error message even on failure
+  return rc;
+}
+
+int femPIC_step_async(FemPIC* h, double dt, int32_t n) {
+  if (!h) return FEMPIC_ERR_ARG;
+  if (!h->stream) {
+    h->err = "handle was not created";
+    return FEMPIC_ERR_STATE;
+  }
+  return do_steps(h, dt, n);
+}
+
+int femPIC_sync(FemPIC* h) {
+  if (!h) return FEMPIC_ERR_ARG;
+  if (!h->stream) return FEMPIC_ERR_STATE;
+  CK(cudaSetDevice(h->device));
+  CK(cudaStreamSynchronize(h->stream));
+  int rc = collect_timing(h);
+  if (rc) return rc;
+  return latch_status(h);
+}
+
+int femPIC_step(FemPIC* h, double dt, int32_t n) {
+  int rc = femPIC_step_async(h, dt, n);
+  if (rc) return rc;
+  return femPIC_sync(h);
+}
+
+int femPIC_get(FemPIC* h, int32_t what, void* dst, size_t bytes) {
+  if (!h || !h->stream) return FEMPIC_ERR_ARG;
+  return transfer(h, what, dst, bytes, false, false);
+}
+int femPIC_set(FemPIC* h, int32_t what, const void* src, size_t bytes) {
+  if (!h || !h->stream) return FEMPIC_ERR_ARG;
+  return transfer(h, what, const_cast<void*>(src), bytes, true, false);
+}
+int femPIC_get_device(FemPIC* h, int32_t what, void* dst, size_t bytes) {
+  if (!h || !h->stream) return FEMPIC_ERR_ARG;
+  return transfer(h, what, dst, bytes, false, true);
+}
+int femPIC_set_device(FemPIC* h, int32_t what, const void* src, size_t bytes) {
+  if (!h || !h->stream) return FEMPIC_ERR_ARG;
+  return transfer(h, what, const_cast<void*>(src), bytes, true, true);
+}
+
+int femPIC_apply(FemPIC* h, int32_t op, const double* x_host, size_t nx, double* y_host, size_t ny) {
+  if (!h || !h->stream || !x_host || !y_host) return FEMPIC_ERR_ARG;
+  const DevCSR* A = nullptr;
+  const double* vals = nullptr;
+  switch (op) {
+    case FEMPIC_OP_M1: A = &h->M; break;
+    case FEMPIC_OP_K: A = &h->K; break;
+    case FEMPIC_OP_C: A = &h->C; break;
+    case FEMPIC_OP_D: A = &h->D; break;
+    case FEMPIC_OP_DT: A = &h->DT; break;
+    case FEMPIC_OP_M2: A = &h->M2; break;
+    case FEMPIC_OP_A:
+      A = &h->M;
+      vals = h->Aval;
+      if (h->dt_cur < 0) {
+        h->err = "no system matrix before the first step";
+        return FEMPIC_ERR_STATE;
+      }
+      break;
+    case FEMPIC_OP_L: A = &h->L; break;
+    default:
+      h->err = "unknown operator";
+      return FEMPIC_ERR_ARG;
+  }
+  if (nx != (size_t)A->n_cols || ny != (size_t)A->n_rows) {
+    h->err = "operator size mismatch";
+    return FEMPIC_ERR_SIZE;
+  }
+  CK(cudaSetDevice(h->device));
+  double *dx = nullptr, *dy = nullptr;
+  CK(cudaMalloc(&dx, sizeof(double) * std::max<size_t>(nx, 1)));
+  if (cudaMalloc(&dy, sizeof(double) * std::max<size_t>(ny, 1)) != cudaSuccess) {
+    cudaFree(dx);
+    h->err = "cudaMalloc failed";
+    return FEMPIC_ERR_OOM;
+  }
+  int rc = FEMPIC_OK;
+  if (cudaMemcpy(dx, x_host, sizeof(double) * nx, cudaMemcpyHostToDevice) != cudaSuccess) rc = FEMPIC_ERR_CUDA;
+  if (!rc) rc = spmv(h, A->view(vals), dx, dy);
+  if (!rc && cudaMemcpyAsync(y_host, dy, sizeof(double) * ny, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    rc = FEMPIC_ERR_CUDA;
+  if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = FEMPIC_ERR_CUDA;
+  cudaFree(dx);
+  cudaFree(dy);
+  if (rc == FEMPIC_ERR_CUDA) h->err = "operator application failed";
+  return rc;
+}
+
+int femPIC_eval_fields(FemPIC* h, int64_t n, const double* x_host, const int32_t* tet_host, double* E_host,
+                       double* B_host) {
+  if (!h || !h->stream || n < 0 || (n > 0 && (!x_host || !tet_host || !E_host || !B_host))) return FEMPIC_ERR_ARG;
+  if (n == 0) return FEMPIC_OK;
+  for (int64_t i = 0; i < n; ++i)
+    if (tet_host[i] < 0 || tet_host[i] >= h->n_tets) {
+      h->err = "tet id out of range";
+      return FEMPIC_ERR_ARG;
+    }
+  CK(cudaSetDevice(h->device));
+  double *dx = nullptr, *dE = nullptr, *dB = nullptr;
+  int32_t* dt = nullptr;
+  CK(cudaMalloc(&dx, sizeof(double) * 3 * n));
+  CK(cudaMalloc(&dE, sizeof(double) * 3 * n));
+  CK(cudaMalloc(&dB, sizeof(double) * 3 * n));
+  CK(cudaMalloc(&dt, sizeof(int32_t) * n));
+  CK(cudaMemcpy(dx, x_host, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dt, tet_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+  int grid = grid_for(n, 128, 1 << 30);
+  bool strict = h->opts.precision == FEMPIC_FP64_STRICT;
+  const double* B0 = h->opts.B0;
+  if (h->order == 1) {
+    if (strict)
+      k_eval_fields<1, Strict><<<grid, 128, 0, h->stream>>>(n, dx, dt, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
+                                                            B0[1], B0[2], dE, dB);
+    else
+      k_eval_fields<1, Fast><<<grid, 128, 0, h->stream>>>(n, dx, dt, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
+                                                          B0[1], B0[2], dE, dB);
+  } else {
+    if (strict)
+      k_eval_fields<2, Strict><<<grid, 128, 0, h->stream>>>(n, dx, dt, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
+                                                            B0[1], B0[2], dE, dB);
+    else
+      k_eval_fields<2, Fast><<<grid, 128, 0, h->stream>>>(n, dx, dt, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
+                                                          B0[1], B0[2], dE, dB);
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(E_host, dE, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(B_host, dB, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  cudaFree(dx);
+  cudaFree(dE);
+  cudaFree(dB);
+  cudaFree(dt);
+  return FEMPIC_OK;
+}
+
+int femPIC_get_info(const FemPIC* h, femPIC_info* info) {
+  if (!h || !info) return FEMPIC_ERR_ARG;
+  memset(info, 0, sizeof(*info));
+  info->n_nodes = h->n_nodes;
+  info->n_tets = h->n_tets;
+  info->n_edges = h->n_edges;
+  info->n_faces = h->n_faces;
+  info->order = h->order;
+  info->n0 = h->n0;
+  info->n1 = h->n1;
+  info->n2 = h->n2;
+  info->nl0 = h->nl0;
+  info->nl1 = h->nl1;
+  info->nl2 = h->nl2;
+  info->n_particles = h->np;
+  info->nnz_A = h->M.nnz;
+  info->nnz_C = h->C.nnz;
+  info->nnz_Q = h->Q.nnz;
+  info->n_boundary_faces = h->n_bfaces;
+  info->device_bytes = h->bytes;
+  return FEMPIC_OK;
+}
+
+int femPIC_last_timing(const FemPIC* h, double* times, int32_t n) {
+  if (!h || !times || n < 1) return FEMPIC_ERR_ARG;
+  if (n > 0) times[0] = h->t_particle_ms;
+  if (n > 1) times[1] = h->t_field_ms;
+  if (n > 2) times[2] = h->launches;
+  return FEMPIC_OK;
+}
+
+void femPIC_destroy(FemPIC* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* p : h->allocs) cudaFree(p);
+  for (auto e : h->ev) cudaEventDestroy(e);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+const char* femPIC_last_error(const FemPIC* h) { return h ? h->err.c_str() : "NULL handle"; }
+
+}  // extern "C"

@@ -1,0 +1,69 @@
+// Internal structures shared by the host set-up (setup.cpp) and the device
+// code (fempic.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace fempic {
+
+// Local DOF counts per tet (Appendix): W0 (k+1)(k+2)(k+3)/6, W1 k(k+2)(k+3)/2,
+// W2 k(k+1)(k+3)/2.
+inline int nloc0(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+inline int nloc1(int p) { return p * (p + 2) * (p + 3) / 2; }
+inline int nloc2(int p) { return p * (p + 1) * (p + 3) / 2; }
+
+constexpr int kLocalEdges[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+constexpr int kLocalFaces[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};  // face i opposite vertex i
+
+struct HostCSR {
+  int32_t n_rows = 0, n_cols = 0;
+  std::vector<int32_t> rowptr, col;
+  std::vector<double> val;
+  int64_t nnz() const { return (int64_t)col.size(); }
+};
+
+// Everything the device needs, built on the host at create time.
+struct HostModel {
+  int order = 1, nl0 = 4, nl1 = 6, nl2 = 4;
+  int32_t n_nodes = 0, n_tets = 0, n_edges = 0, n_faces = 0;
+  int32_t n0 = 0, n1 = 0, n2 = 0, n_bfaces = 0;
+  std::vector<int32_t> tets;     // [nt][4] sorted vertex ids
+  std::vector<double> geom;      // [nt][16]: g (4x3 row-major), c[4]
+  std::vector<double> vol;       // [nt]
+  std::vector<int32_t> nbr;      // [nt][4]: (neighbour << 2) | neighbour's local face, -1 = wall
+  std::vector<int32_t> dof0, dof1, dof2;  // [nt][nl*]
+  std::vector<uint8_t> pec1;     // [n1] 1 on boundary W1 DOFs
+  std::vector<uint8_t> bnd0;     // [n0] 1 on boundary W0 DOFs
+  HostCSR M, K;                  // [*eps], curl-curl (free rows/cols), same pattern
+  HostCSR Q;                     // C^T [*mu^-1] (free rows), N1 x N2
+  HostCSR C;                     // N2 x N1 (free cols)
+  HostCSR M2;                    // [*mu^-1]
+  HostCSR D;                     // N1 x N0 (interior cols)
+  HostCSR DT;                    // N0 x N1
+  HostCSR L;                     // nodal Laplacian D^T [*eps] D, interior rows/cols
+  std::vector<double> load0;     // <W0_k, 1>
+};
+
+// Local tables of the order-p bases, computed exactly on the reference tet.
+struct LocalTables {
+  int order = 1, nl0 = 4, nl1 = 6, nl2 = 4;
+  std::vector<double> Dloc;  // [nl1][nl0]: grad W0_k = sum_i Dloc[i][k] W1_i
+  std::vector<double> Cloc;  // [nl2][nl1]: curl W1_j = sum_f Cloc[f][j] W2_f
+  std::vector<double> T1;    // [nl1][nl1][4][4]: int_ref P1_ia P1_jb
+  std::vector<double> T2;    // [nl2][nl2][6][6]: int_ref P2_{f,ab} P2_{h,cd}
+  std::vector<double> I0;    // [nl0]: int_ref W0_k
+};
+
+// Returns "" on success, else an error message.
+std::string build_local_tables(int order, LocalTables* out);
+// code: 0 ok, 2 mesh error, 1 argument error.
+int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets, int32_t n_tets,
+                int order, HostModel* m, std::string* err);
+
+// Physical constants (CODATA 2018).
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kMu0 = 1.25663706212e-6;
+
+}  // namespace fempic

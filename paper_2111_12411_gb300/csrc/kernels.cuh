@@ -1,0 +1,433 @@
+// Device code of the EM-FEMPIC step: the fused particle kernel (gather E and B,
+// Lorentz push, ray-face walk, charge-conserving path-integral deposit, charge
+// measurement), counting sort by tet, CSR kernels and the device-resident
+// preconditioned conjugate-gradient solve.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fempic {
+namespace dev {
+
+constexpr double kGL2X = 0.5773502691896257645;  // 1/sqrt(3)
+constexpr uint64_t kFnvOffset = 14695981039346656037ull;
+constexpr uint64_t kFnvPrime = 1099511628211ull;
+
+// Device status bits (latched; the host maps them to FEMPIC_ERR_*).
+constexpr int kStatusWalk = 1;
+constexpr int kStatusCG = 2;
+constexpr int kStatusBarrier = 4;
+
+// ---- arithmetic policies ----------------------------------------------------
+// Strict: one rounding per operation, in the written order (no contraction).
+struct Strict {
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+  // a*b + c with two roundings
+  static __device__ __forceinline__ double mad(double a, double b, double c) { return __dadd_rn(__dmul_rn(a, b), c); }
+};
+// Fast: the compiler may fuse multiply-adds.
+struct Fast {
+  static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
+  static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+  static __device__ __forceinline__ double sub(double a, double b) { return a - b; }
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
+};
+
+__device__ __constant__ int c_edges[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+__device__ __constant__ int c_faces[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+
+// W1 of order p: function j = m(l) * (l_a grad l_b - l_b grad l_a);
+// w1spec[j] = {a, b, x, kind} with kind 0: m = 1, 1: m = 3 l_x - 1, 2: m = 3 l_x.
+__device__ __constant__ int c_w1spec2[20][4] = {
+    {0, 1, 0, 1}, {0, 1, 1, 1}, {0, 2, 0, 1}, {0, 2, 2, 1}, {0, 3, 0, 1}, {0, 3, 3, 1},
+    {1, 2, 1, 1}, {1, 2, 2, 1}, {1, 3, 1, 1}, {1, 3, 3, 1}, {2, 3, 2, 1}, {2, 3, 3, 1},
+    {1, 2, 3, 2}, {1, 3, 2, 2},  // face 0 = (1,2,3): 3 l_3 w_12, 3 l_2 w_13
+    {0, 2, 3, 2}, {0, 3, 2, 2},  // face 1 = (0,2,3)
+    {0, 1, 3, 2}, {0, 3, 1, 2},  // face 2 = (0,1,3)
+    {0, 1, 2, 2}, {0, 2, 1, 2}}; // face 3 = (0,1,2)
+// W2 of order 2: function j = m(l) * w_face; {face, x, kind} kind 1: 4 l_x - 1, 2: 4 l_x.
+__device__ __constant__ int c_w2spec2[15][3] = {
+    {0, 1, 1}, {0, 2, 1}, {0, 3, 1}, {1, 0, 1}, {1, 2, 1}, {1, 3, 1}, {2, 0, 1}, {2, 1, 1},
+    {2, 3, 1}, {3, 0, 1}, {3, 1, 1}, {3, 2, 1}, {0, 0, 2}, {1, 1, 2}, {2, 2, 2}};
+
+template <class Ar>
+__device__ __forceinline__ void cross3(const double* a, const double* b, double* o) {
+  o[0] = Ar::sub(Ar::mul(a[1], b[2]), Ar::mul(a[2], b[1]));
+  o[1] = Ar::sub(Ar::mul(a[2], b[0]), Ar::mul(a[0], b[2]));
+  o[2] = Ar::sub(Ar::mul(a[0], b[1]), Ar::mul(a[1], b[0]));
+}
+
+template <class Ar>
+__device__ __forceinline__ double dot3(const double* a, const double* b) {
+  return Ar::add(Ar::add(Ar::mul(a[0], b[0]), Ar::mul(a[1], b[1])), Ar::mul(a[2], b[2]));
+}
+
+// geom layout per tet: g[4][3] row-major then c[4]
+struct TetGeom {
+  double g[4][3];
+  double c[4];
+};
+
+__device__ __forceinline__ void load_geom(const double* __restrict__ geom, int t, TetGeom& G) {
+  const double2* p = reinterpret_cast<const double2*>(geom + (size_t)t * 16);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    double2 v = __ldg(p + k);
+    double* dst = &G.g[0][0];
+    dst[2 * k] = v.x;
+    dst[2 * k + 1] = v.y;
+  }
+}
+
+// lambda_i(x) = ((g_i0 x0 + g_i1 x1) + g_i2 x2) + c_i
+template <class Ar>
+__device__ __forceinline__ void bary(const TetGeom& G, const double* x, double* l) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    l[i] = Ar::add(Ar::add(Ar::add(Ar::mul(G.g[i][0], x[0]), Ar::mul(G.g[i][1], x[1])), Ar::mul(G.g[i][2], x[2])),
+                   G.c[i]);
+}
+
+// E = sum_j e_j W1_j(x), accumulated in j order
+template <int P, class Ar>
+__device__ __forceinline__ void gather_E(const TetGeom& G, const double* l, const double* ev, double* E) {
+  E[0] = E[1] = E[2] = 0.0;
+  constexpr int N = P == 1 ? 6 : 20;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    int a, b, x = 0, kind = 0;
+    if (P == 1) {
+      a = c_edges[j][0];
+      b = c_edges[j][1];
+    } else {
+      a = c_w1spec2[j][0];
+      b = c_w1spec2[j][1];
+      x = c_w1spec2[j][2];
+      kind = c_w1spec2[j][3];
+    }
+    double w[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) w[k] = Ar::sub(Ar::mul(l[a], G.g[b][k]), Ar::mul(l[b], G.g[a][k]));
+    if (P == 2) {
+      double m = kind == 1 ? Ar::sub(Ar::mul(3.0, l[x]), 1.0) : Ar::mul(3.0, l[x]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) w[k] = Ar::mul(m, w[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) E[k] = Ar::add(E[k], Ar::mul(ev[j], w[k]));
+  }
+}
+
+// Whitney face function of local face f: 2 ((l_s X_tu + l_t X_us) + l_u X_st)
+template <class Ar>
+__device__ __forceinline__ void whitney_face(const TetGeom& G, const double* l, int f, double* w) {
+  int s = c_faces[f][0], t = c_faces[f][1], u = c_faces[f][2];
+  double xtu[3], xus[3], xst[3];
+  cross3<Ar>(G.g[t], G.g[u], xtu);
+  cross3<Ar>(G.g[u], G.g[s], xus);
+  cross3<Ar>(G.g[s], G.g[t], xst);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    w[k] = Ar::mul(Ar::add(Ar::add(Ar::mul(l[s], xtu[k]), Ar::mul(l[t], xus[k])), Ar::mul(l[u], xst[k])), 2.0);
+}
+
+template <int P, class Ar>
+__device__ __forceinline__ void gather_B(const TetGeom& G, const double* l, const double* bv, const double* B0,
+                                         double* B) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  if (P == 1) {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      double w[3];
+      whitney_face<Ar>(G, l, f, w);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc[k] = Ar::add(acc[k], Ar::mul(bv[f], w[k]));
+    }
+  } else {
+    double wf[4][3];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) whitney_face<Ar>(G, l, f, wf[f]);
+#pragma unroll
+    for (int j = 0; j < 15; ++j) {
+      int f = c_w2spec2[j][0], x = c_w2spec2[j][1], kind = c_w2spec2[j][2];
+      double m = kind == 1 ? Ar::sub(Ar::mul(4.0, l[x]), 1.0) : Ar::mul(4.0, l[x]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc[k] = Ar::add(acc[k], Ar::mul(bv[j], Ar::mul(m, wf[f][k])));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) B[k] = Ar::add(acc[k], B0[k]);
+}
+
+// Boris rotation (h = q dt / 2m precomputed on the host as ((q/m) dt) 0.5)
+template <class Ar>
+__device__ __forceinline__ void boris(double* v, const double* E, const double* B, double h) {
+  double eh[3], vm[3], t[3], s[3], vp[3], cr[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    eh[k] = Ar::mul(E[k], h);
+    vm[k] = Ar::add(v[k], eh[k]);
+    t[k] = Ar::mul(B[k], h);
+  }
+  double t2 = Ar::add(Ar::add(Ar::mul(t[0], t[0]), Ar::mul(t[1], t[1])), Ar::mul(t[2], t[2]));
+  double sf = Ar::div(2.0, Ar::add(1.0, t2));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) s[k] = Ar::mul(t[k], sf);
+  cross3<Ar>(vm, t, cr);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) vp[k] = Ar::add(vm[k], cr[k]);
+  cross3<Ar>(vp, s, cr);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v[k] = Ar::add(Ar::add(vm[k], cr[k]), eh[k]);
+}
+
+// q w int_{s0}^{s1} W1_j(r(s)) . (b - a) ds for all local j, added into dg
+template <int P, class Ar>
+__device__ __forceinline__ void deposit_segment(const double* la, const double* lb, double s0, double s1, double qw,
+                                                const int32_t* __restrict__ dofs, double* __restrict__ dg) {
+  double d[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) d[i] = Ar::sub(lb[i], la[i]);
+  if (P == 1) {
+    double Pv[4], Qv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      Pv[i] = Ar::add(la[i], Ar::mul(s0, d[i]));
+      Qv[i] = Ar::add(la[i], Ar::mul(s1, d[i]));
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      int s = c_edges[j][0], t = c_edges[j][1];
+      double val = Ar::sub(Ar::mul(Pv[s], Qv[t]), Ar::mul(Pv[t], Qv[s]));
+      atomicAdd(dg + __ldg(dofs + j), Ar::mul(qw, val));
+    }
+  } else {
+    double half = Ar::mul(Ar::sub(s1, s0), 0.5);
+    double mid = Ar::mul(Ar::add(s0, s1), 0.5);
+    double r = Ar::mul(half, kGL2X);
+    double sg[2] = {Ar::sub(mid, r), Ar::add(mid, r)};
+    double L[2][4];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) L[q][i] = Ar::add(la[i], Ar::mul(sg[q], d[i]));
+#pragma unroll
+    for (int j = 0; j < 20; ++j) {
+      int a = c_w1spec2[j][0], b = c_w1spec2[j][1], x = c_w1spec2[j][2], kind = c_w1spec2[j][3];
+      double f[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        double m = kind == 1 ? Ar::sub(Ar::mul(3.0, L[q][x]), 1.0) : Ar::mul(3.0, L[q][x]);
+        f[q] = Ar::mul(m, Ar::sub(Ar::mul(L[q][a], d[b]), Ar::mul(L[q][b], d[a])));
+      }
+      atomicAdd(dg + __ldg(dofs + j), Ar::mul(qw, Ar::mul(half, Ar::add(f[0], f[1]))));
+    }
+  }
+}
+
+template <int P, class Ar>
+__device__ __forceinline__ void deposit_rho(const double* l, double qw, const int32_t* __restrict__ dofs,
+                                            double* __restrict__ rho) {
+  if (P == 1) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) atomicAdd(rho + __ldg(dofs + k), Ar::mul(qw, l[k]));
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      atomicAdd(rho + __ldg(dofs + k), Ar::mul(qw, Ar::mul(l[k], Ar::sub(Ar::mul(2.0, l[k]), 1.0))));
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+      atomicAdd(rho + __ldg(dofs + 4 + j), Ar::mul(qw, Ar::mul(Ar::mul(4.0, l[c_edges[j][0]]), l[c_edges[j][1]])));
+  }
+}
+
+struct ParticleArgs {
+  int64_t n;
+  double* x[3];
+  double* v[3];
+  int32_t* tet;
+  int32_t* ncross;
+  unsigned long long* hash;
+  const double* geom;
+  const int32_t* nbr;
+  const int32_t* dof0;
+  const int32_t* dof1;
+  const int32_t* dof2;
+  const double* e;
+  const double* b;
+  double* dg;
+  double* rho;
+  double B0[3];
+  double h;    // q dt / 2m
+  double dt;
+  double qw;
+  int max_cross;
+  int32_t* status;
+  unsigned long long* crossings;
+};
+
+// One thread per particle: gather, push, walk, deposit, charge.
+template <int P, class Ar>
+__global__ void __launch_bounds__(256) k_particle(ParticleArgs a) {
+  constexpr int N1 = P == 1 ? 6 : 20;
+  constexpr int N2 = P == 1 ? 4 : 15;
+  constexpr int N0 = P == 1 ? 4 : 10;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long my_cross = 0;
+  if (i < a.n) {
+    int T = a.tet[i];
+    double x[3] = {a.x[0][i], a.x[1][i], a.x[2][i]};
+    double v[3] = {a.v[0][i], a.v[1][i], a.v[2][i]};
+    TetGeom G;
+    load_geom(a.geom, T, G);
+    double l[4];
+    bary<Ar>(G, x, l);
+    double ev[N1], bv[N2];
+    const int32_t* d1 = a.dof1 + (size_t)T * N1;
+    const int32_t* d2 = a.dof2 + (size_t)T * N2;
+#pragma unroll
+    for (int j = 0; j < N1; ++j) ev[j] = __ldg(a.e + __ldg(d1 + j));
+#pragma unroll
+    for (int j = 0; j < N2; ++j) bv[j] = __ldg(a.b + __ldg(d2 + j));
+    double E[3], B[3];
+    gather_E<P, Ar>(G, l, ev, E);
+    gather_B<P, Ar>(G, l, bv, a.B0, B);
+    boris<Ar>(v, E, B, a.h);
+    double pa[3] = {x[0], x[1], x[2]};
+    double pb[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) pb[k] = Ar::add(x[k], Ar::mul(a.dt, v[k]));
+    int entry = -1;
+    double s0 = 0.0;
+    int nc = 0;
+    unsigned long long hsh = kFnvOffset;
+    for (;;) {
+      double la[4], lb[4];
+      bary<Ar>(G, pa, la);
+      bary<Ar>(G, pb, lb);
+      int best = -1;
+      double sbest = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        if (f != entry && lb[f] < 0.0) {
+          double si = Ar::div(la[f], Ar::sub(la[f], lb[f]));
+          if (si < sbest) {
+            sbest = si;
+            best = f;
+          }
+        }
+      }
+      double s1 = best < 0 ? 1.0 : fmin(fmax(sbest, s0), 1.0);
+      deposit_segment<P, Ar>(la, lb, s0, s1, a.qw, a.dof1 + (size_t)T * N1, a.dg);
+      if (best < 0) {
+        deposit_rho<P, Ar>(lb, a.qw, a.dof0 + (size_t)T * N0, a.rho);
+        break;
+      }
+      ++nc;
+      int nb = __ldg(a.nbr + (size_t)T * 4 + best);
+      unsigned long long code = nb < 0 ? (0x80000000ull | (unsigned)best) : (unsigned long long)(nb >> 2);
+      hsh = (hsh ^ code) * kFnvPrime;
+      if (nb >= 0) {
+        entry = nb & 3;
+        T = nb >> 2;
+        s0 = s1;
+        load_geom(a.geom, T, G);
+      } else {
+        const double* gw = G.g[best];
+        double d[3], hit[3], dr[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d[k] = Ar::sub(pb[k], pa[k]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) hit[k] = Ar::add(pa[k], Ar::mul(s1, d[k]));
+        double gg = dot3<Ar>(gw, gw);
+        double fd = Ar::div(Ar::mul(2.0, dot3<Ar>(d, gw)), gg);
+        double fv = Ar::div(Ar::mul(2.0, dot3<Ar>(v, gw)), gg);
+        double rem = Ar::sub(1.0, s1);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          dr[k] = Ar::sub(d[k], Ar::mul(fd, gw[k]));
+          v[k] = Ar::sub(v[k], Ar::mul(fv, gw[k]));
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          pb[k] = Ar::add(hit[k], Ar::mul(rem, dr[k]));
+          pa[k] = hit[k];
+        }
+        s0 = 0.0;
+        entry = best;
+      }
+      if (nc >= a.max_cross) {
+        double lf[4];
+        bary<Ar>(G, pb, lf);
+        deposit_rho<P, Ar>(lf, a.qw, a.dof0 + (size_t)T * N0, a.rho);
+        atomicOr(a.status, kStatusWalk);
+        break;
+      }
+    }
+    a.x[0][i] = pb[0];
+    a.x[1][i] = pb[1];
+    a.x[2][i] = pb[2];
+    a.v[0][i] = v[0];
+    a.v[1][i] = v[1];
+    a.v[2][i] = v[2];
+    a.tet[i] = T;
+    if (a.ncross) a.ncross[i] = nc;
+    if (a.hash) a.hash[i] = hsh;
+    my_cross = nc;
+  }
+  // block-aggregated crossing count
+  for (int o = 16; o > 0; o >>= 1) my_cross += __shfl_xor_sync(0xffffffffu, my_cross, o);
+  if ((threadIdx.x & 31) == 0 && my_cross) atomicAdd(a.crossings, my_cross);
+}
+
+// rho from positions (used at start and after the state is set)
+template <int P>
+__global__ void k_rho(int64_t n, const double* x0, const double* x1, const double* x2, const int32_t* tet,
+                      const double* geom, const int32_t* dof0, double qw, double* rho) {
+  constexpr int N0 = P == 1 ? 4 : 10;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int T = tet[i];
+  TetGeom G;
+  load_geom(geom, T, G);
+  double x[3] = {x0[i], x1[i], x2[i]};
+  double l[4];
+  bary<Strict>(G, x, l);
+  deposit_rho<P, Strict>(l, qw, dof0 + (size_t)T * N0, rho);
+}
+
+// E and B at given points (owning tets known)
+template <int P, class Ar>
+__global__ void k_eval_fields(int64_t n, const double* xs, const int32_t* tets, const double* geom,
+                              const int32_t* dof1, const int32_t* dof2, const double* e, const double* b,
+                              double B00, double B01, double B02, double* Eo, double* Bo) {
+  constexpr int N1 = P == 1 ? 6 : 20;
+  constexpr int N2 = P == 1 ? 4 : 15;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int T = tets[i];
+  TetGeom G;
+  load_geom(geom, T, G);
+  double x[3] = {xs[3 * i], xs[3 * i + 1], xs[3 * i + 2]};
+  double l[4];
+  bary<Ar>(G, x, l);
+  double ev[N1], bv[N2];
+  for (int j = 0; j < N1; ++j) ev[j] = e[dof1[(size_t)T * N1 + j]];
+  for (int j = 0; j < N2; ++j) bv[j] = b[dof2[(size_t)T * N2 + j]];
+  double B0[3] = {B00, B01, B02};
+  double E[3], B[3];
+  gather_E<P, Ar>(G, l, ev, E);
+  gather_B<P, Ar>(G, l, bv, B0, B);
+  for (int k = 0; k < 3; ++k) {
+    Eo[3 * i + k] = E[k];
+    Bo[3 * i + k] = B[k];
+  }
+}
+
+}  // namespace dev
+}  // namespace fempic

@@ -1,0 +1,484 @@
+// Sparse linear algebra on the device: CSR products, the Newmark right-hand
+// side, the magnetic update and a persistent preconditioned conjugate-gradient
+// solve whose blocks synchronise through a bounded grid barrier (one
+// cooperative launch per solve; the host never sees the iterations).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace fempic {
+namespace dev {
+
+struct CsrView {
+  int32_t n_rows;
+  const int32_t* rp;
+  const int32_t* ci;
+  const double* v;
+};
+
+// y = alpha * A x (+ beta * y)
+template <int LPR>
+__global__ void k_spmv(CsrView A, const double* __restrict__ x, double* __restrict__ y, double alpha, double beta) {
+  int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  int lane = gid % LPR;
+  int groups = gridDim.x * blockDim.x / LPR;
+  for (int r = gid / LPR; ; r += groups) {
+    bool act = r < A.n_rows;
+    if (!__any_sync(0xffffffffu, act)) break;
+    double s = 0.0;
+    if (act) {
+      int beg = __ldg(A.rp + r), end = __ldg(A.rp + r + 1);
+      for (int k = beg + lane; k < end; k += LPR) s = fma(__ldg(A.v + k), __ldg(x + __ldg(A.ci + k)), s);
+    }
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
+    if (act && lane == 0) y[r] = beta == 0.0 ? alpha * s : fma(beta, y[r], alpha * s);
+  }
+}
+
+// Newmark right-hand side, one row per LPR lanes:
+//   rhs = R1 e - R2 e_prev + qfac (Q b) - (dg - dgp_fac dg_prev), PEC rows 0.
+// R1, R2 share M's pattern (R2 may be null).
+template <int LPR>
+__global__ void k_rhs(CsrView R1, const double* __restrict__ r2v, CsrView Q, const double* __restrict__ e,
+                      const double* __restrict__ e_prev, const double* __restrict__ b, double qfac,
+                      const double* __restrict__ dg, const double* __restrict__ dg_prev, double dgp_fac,
+                      const uint8_t* __restrict__ pec, double* __restrict__ rhs) {
+  int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  int lane = gid % LPR;
+  int groups = gridDim.x * blockDim.x / LPR;
+  int n = R1.n_rows;
+  for (int r = gid / LPR; ; r += groups) {
+    bool act = r < n;
+    if (!__any_sync(0xffffffffu, act)) break;
+    double s = 0.0;
+    if (act) {
+      int beg = __ldg(R1.rp + r), end = __ldg(R1.rp + r + 1);
+      for (int k = beg + lane; k < end; k += LPR) {
+        int c = __ldg(R1.ci + k);
+        s = fma(__ldg(R1.v + k), __ldg(e + c), s);
+        if (r2v) s = fma(-__ldg(r2v + k), __ldg(e_prev + c), s);
+      }
+      if (qfac != 0.0) {
+        double t = 0.0;
+        int qb = __ldg(Q.rp + r), qe = __ldg(Q.rp + r + 1);
+        for (int k = qb + lane; k < qe; k += LPR) t = fma(__ldg(Q.v + k), __ldg(b + __ldg(Q.ci + k)), t);
+        s = fma(qfac, t, s);
+      }
+    }
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
+    if (act && lane == 0) {
+      double src = dg[r];
+      if (dgp_fac != 0.0) src -= dgp_fac * dg_prev[r];
+      rhs[r] = pec[r] ? 0.0 : s - src;
+    }
+  }
+}
+
+// b -= hdt * C (e_new + e)
+template <int LPR>
+__global__ void k_bupdate(CsrView C, const double* __restrict__ e_new, const double* __restrict__ e, double hdt,
+                          double* __restrict__ b) {
+  int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  int lane = gid % LPR;
+  int groups = gridDim.x * blockDim.x / LPR;
+  int n = C.n_rows;
+  for (int r = gid / LPR; ; r += groups) {
+    bool act = r < n;
+    if (!__any_sync(0xffffffffu, act)) break;
+    double s = 0.0;
+    if (act) {
+      int beg = __ldg(C.rp + r), end = __ldg(C.rp + r + 1);
+      for (int k = beg + lane; k < end; k += LPR) {
+        int c = __ldg(C.ci + k);
+        s = fma(__ldg(C.v + k), __ldg(e_new + c) + __ldg(e + c), s);
+      }
+    }
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
+    if (act && lane == 0) b[r] = fma(-hdt, s, b[r]);
+  }
+}
+
+// out = a x + b y
+__global__ void k_lincomb(int32_t n, const double* __restrict__ x, const double* __restrict__ y, double a, double b,
+                          double* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = a * x[i] + b * y[i];
+}
+
+// A = M + ca K, R = M + cr K (same pattern), inverse diagonal of A (0 on empty rows)
+__global__ void k_form_system(int32_t n, const int32_t* rp, const int32_t* ci, const double* m, const double* k,
+                              double ca, double cr, double* a, double* r, double* dinv) {
+  int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  double diag = 0.0;
+  for (int j = rp[row]; j < rp[row + 1]; ++j) {
+    double av = m[j] + ca * k[j];
+    a[j] = av;
+    if (r) r[j] = m[j] + cr * k[j];
+    if (ci[j] == row) diag = av;
+  }
+  dinv[row] = diag != 0.0 ? 1.0 / diag : 0.0;
+}
+
+__global__ void k_inv_diag(int32_t n, const int32_t* rp, const int32_t* ci, const double* v, double* dinv) {
+  int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  double diag = 0.0;
+  for (int j = rp[row]; j < rp[row + 1]; ++j)
+    if (ci[j] == row) diag = v[j];
+  dinv[row] = diag != 0.0 ? 1.0 / diag : 0.0;
+}
+
+// ---- persistent PCG ---------------------------------------------------------
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+};
+
+constexpr long long kBarrierSpinLimit = 20000000;  // ~1-2 s with the backoff below
+
+__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) { return *(volatile const unsigned*)p; }
+
+// Returns false (and latches kStatusBarrier) if the barrier timed out.
+__device__ bool grid_sync(GridBarrier* bar, int32_t* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    unsigned gen = ld_volatile(&bar->gen);
+    __threadfence();
+    unsigned arrived = atomicAdd(&bar->count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      long long spins = 0;
+      while (ld_volatile(&bar->gen) == gen) {
+        if (++spins > kBarrierSpinLimit) {
+          atomicOr(status, kStatusBarrier);
+          ok = 0;
+          break;
+        }
+        if (spins > 64) __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+struct PcgArgs {
+  CsrView A;
+  const double* dinv;
+  // optional auxiliary nodal correction of the preconditioner:
+  // z = dinv r + D (dinvL (D^T r)); DT.n_rows == 0 disables it
+  CsrView D;
+  CsrView DT;
+  const double* dinvL;
+  double* t;   // [DT.n_rows] scratch
+  const double* rhs;
+  double* x;   // in: initial guess, out: solution
+  double* r;
+  double* z;
+  double* p;
+  double* q;
+  double* partials;  // [gridDim.x * 4]
+  GridBarrier* bar;
+  int32_t* status;
+  int32_t* iters_out;
+  double* res_out;
+  double rtol;
+  int max_it;
+};
+
+// reduce up to 4 values over the block into partials[blockIdx.x*4 + k]
+template <int NV>
+__device__ __forceinline__ void block_partials(double (&v)[NV], double* partials) {
+  __shared__ double red[32][4];
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[w][k] = v[k];
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = l < nw ? red[l][k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (l == 0) partials[blockIdx.x * 4 + k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// every block sums the partials in the same order -> identical totals everywhere
+template <int NV>
+__device__ __forceinline__ void grid_totals(const double* partials, double (&tot)[NV]) {
+  __shared__ double res[4];
+  if (threadIdx.x < 32) {
+    int l = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int b = l; b < (int)gridDim.x; b += 32) s += *((volatile const double*)(partials + b * 4 + k));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (l == 0) res[k] = s;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) tot[k] = res[k];
+  __syncthreads();
+}
+
+// y_r = sum_k A_rk x_k for the rows this thread group owns, LPR lanes per row;
+// x is read around L1 (written by other blocks in this launch)
+template <int LPR, class F>
+__device__ __forceinline__ void rows_spmv(const CsrView& A, const double* x, int gid, int groups, F emit) {
+  const int lane = gid % LPR;
+  for (int r0 = gid / LPR; ; r0 += groups) {
+    bool act = r0 < A.n_rows;
+    if (!__any_sync(0xffffffffu, act)) break;
+    double s = 0.0;
+    if (act) {
+      int beg = __ldg(A.rp + r0), end = __ldg(A.rp + r0 + 1);
+      for (int k = beg + lane; k < end; k += LPR) s = fma(__ldg(A.v + k), __ldcg(x + __ldg(A.ci + k)), s);
+    }
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
+    if (act && lane == 0) emit(r0, s);
+  }
+}
+
+// z = M^-1 r with the nodal correction (r complete in memory); returns r.z
+// contribution of this thread; sets p = z when first.  false on barrier timeout.
+__device__ __forceinline__ bool nodal_precondition(const PcgArgs& a, int gid, bool first, double& rz) {
+  const int tpg = gridDim.x * blockDim.x;
+  rows_spmv<4>(a.DT, a.r, gid, tpg / 4, [&](int k, double s) { a.t[k] = __ldg(a.dinvL + k) * s; });
+  if (!grid_sync(a.bar, a.status)) return false;
+  rows_spmv<4>(a.D, a.t, gid, tpg / 4, [&](int i, double s) {
+    double rr = __ldcg(a.r + i);
+    double zz = fma(__ldg(a.dinv + i), rr, s);
+    a.z[i] = zz;
+    if (first) a.p[i] = zz;
+    rz += rr * zz;
+  });
+  return true;
+}
+
+template <int LPR>
+__global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
+  const int n = a.A.n_rows;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int tpg = gridDim.x * blockDim.x;
+  const int groups = tpg / LPR;
+  const bool nodal = a.DT.n_rows > 0;
+  // phase 0: r = rhs - A x, z = M^-1 r, p = z
+  double acc[3] = {0.0, 0.0, 0.0};  // r.z, r.r, rhs.rhs
+  rows_spmv<LPR>(a.A, a.x, gid, groups, [&](int r0, double s) {
+    double b = a.rhs[r0];
+    double rr = b - s;
+    a.r[r0] = rr;
+    acc[1] += rr * rr;
+    acc[2] += b * b;
+    if (!nodal) {
+      double zz = a.dinv[r0] * rr;
+      a.z[r0] = zz;
+      a.p[r0] = zz;
+      acc[0] += rr * zz;
+    }
+  });
+  if (nodal) {
+    if (!grid_sync(a.bar, a.status)) return;
+    if (!nodal_precondition(a, gid, true, acc[0])) return;
+  }
+  block_partials<3>(acc, a.partials);
+  if (!grid_sync(a.bar, a.status)) return;
+  double tot[3];
+  grid_totals<3>(a.partials, tot);
+  double rz = tot[0];
+  double bnorm = sqrt(tot[2]);
+  double rnorm = sqrt(tot[1]);
+  double thresh = a.rtol * bnorm;
+  int it = 0;
+  bool conv = rnorm <= thresh || bnorm == 0.0;
+  while (!conv && it < a.max_it) {
+    if (!grid_sync(a.bar, a.status)) return;  // p complete; partials free
+    // phase 1: q = A p, p.q
+    double acc1[1] = {0.0};
+    rows_spmv<LPR>(a.A, a.p, gid, groups, [&](int r0, double s) {
+      a.q[r0] = s;
+      acc1[0] += __ldcg(a.p + r0) * s;
+    });
+    block_partials<1>(acc1, a.partials);
+    if (!grid_sync(a.bar, a.status)) return;
+    double t1[1];
+    grid_totals<1>(a.partials, t1);
+    double alpha = t1[0] != 0.0 ? rz / t1[0] : 0.0;
+    if (!grid_sync(a.bar, a.status)) return;  // everyone has read the partials
+    // phase 2: x += alpha p, r -= alpha q, z = M^-1 r
+    double acc2[2] = {0.0, 0.0};  // r.z, r.r
+    for (int i = gid; i < n; i += tpg) {
+      double pi = __ldcg(a.p + i);
+      a.x[i] = fma(alpha, pi, __ldcg(a.x + i));
+      double rr = fma(-alpha, __ldcg(a.q + i), __ldcg(a.r + i));
+      a.r[i] = rr;
+      acc2[1] += rr * rr;
+      if (!nodal) {
+        double zz = a.dinv[i] * rr;
+        a.z[i] = zz;
+        acc2[0] += rr * zz;
+      }
+    }
+    if (nodal) {
+      if (!grid_sync(a.bar, a.status)) return;
+      if (!nodal_precondition(a, gid, false, acc2[0])) return;
+    }
+    block_partials<2>(acc2, a.partials);
+    if (!grid_sync(a.bar, a.status)) return;
+    double t2[2];
+    grid_totals<2>(a.partials, t2);
+    ++it;
+    rnorm = sqrt(t2[1]);
+    conv = rnorm <= thresh;
+    if (conv) break;
+    double beta = rz != 0.0 ? t2[0] / rz : 0.0;
+    rz = t2[0];
+    // phase 3: p = z + beta p
+    for (int i = gid; i < n; i += tpg) a.p[i] = fma(beta, __ldcg(a.p + i), __ldcg(a.z + i));
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *a.iters_out = it;
+    *a.res_out = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+    if (!conv) atomicOr(a.status, kStatusCG);
+  }
+}
+
+// ---- counting sort by tet -----------------------------------------------------
+__global__ void k_hist(int64_t n, const int32_t* __restrict__ tet, int32_t* __restrict__ cnt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicAdd(cnt + tet[i], 1);
+}
+
+// exclusive scan of one tile of 1024 values per block; tile totals to sums
+__global__ void k_scan_tiles(int32_t n, const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                             int32_t* __restrict__ sums) {
+  __shared__ int32_t warp_tot[32];
+  int i = blockIdx.x * 1024 + threadIdx.x;
+  int v = i < n ? in[i] : 0;
+  int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int s = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, s, o);
+    if (l >= o) s += t;
+  }
+  if (l == 31) warp_tot[w] = s;
+  __syncthreads();
+  if (w == 0) {
+    int t = warp_tot[l];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int u = __shfl_up_sync(0xffffffffu, t, o);
+      if (l >= o) t += u;
+    }
+    warp_tot[l] = t;
+  }
+  __syncthreads();
+  int excl = s - v + (w > 0 ? warp_tot[w - 1] : 0);
+  if (i < n) out[i] = excl;
+  if (threadIdx.x == 1023 && sums) sums[blockIdx.x] = excl + v;
+}
+
+__global__ void k_scan_add(int32_t n, int32_t* __restrict__ out, const int32_t* __restrict__ tile_off) {
+  int i = blockIdx.x * 1024 + threadIdx.x;
+  if (i < n) out[i] += tile_off[blockIdx.x];
+}
+
+struct SortArgs {
+  int64_t n;
+  const int32_t* tet_in;
+  int32_t* cursor;  // exclusive offsets, consumed
+  const double* src[6];
+  double* dst[6];
+  const int32_t* ti[2];
+  int32_t* to[2];   // tet, particle id
+};
+
+__global__ void k_sort_scatter(SortArgs a) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  int t = a.tet_in[i];
+  int pos = atomicAdd(a.cursor + t, 1);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) a.dst[k][pos] = a.src[k][i];
+  a.to[0][pos] = t;
+  a.to[1][pos] = a.ti[1][i];
+}
+
+// particle-id order <-> device order
+__global__ void k_gather_by_id(int64_t n, const int32_t* pid, const double* src_il, double* d0, double* d1,
+                               double* d2) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t p = pid[i];
+  d0[i] = src_il[3 * p];
+  d1[i] = src_il[3 * p + 1];
+  d2[i] = src_il[3 * p + 2];
+}
+__global__ void k_scatter_by_id(int64_t n, const int32_t* pid, const double* s0, const double* s1,
+                                const double* s2, double* dst_il) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t p = pid[i];
+  dst_il[3 * p] = s0[i];
+  dst_il[3 * p + 1] = s1[i];
+  dst_il[3 * p + 2] = s2[i];
+}
+template <class T>
+__global__ void k_scatter1_by_id(int64_t n, const int32_t* pid, const T* s, T* dst) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[pid[i]] = s[i];
+}
+template <class T>
+__global__ void k_gather1_by_id(int64_t n, const int32_t* pid, const T* s, T* dst) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = s[pid[i]];
+}
+
+// ---- diagnostics ----------------------------------------------------------------
+// out[0] += sum over mask of a^2, out[1] += sum of b^2 where a = x1 - x0 - y, b = x1 - x0
+__global__ void k_norms2(int32_t n, const uint8_t* mask, const double* u, const double* w, const double* y,
+                         double c_y, double c_w2, const double* w2, double* out) {
+  double s[2] = {0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (!mask[i]) continue;
+    double base = u[i] - (w ? w[i] : 0.0);
+    double res = base + c_y * y[i] + (w2 ? c_w2 * w2[i] : 0.0);
+    s[0] += res * res;
+    s[1] += base * base;
+  }
+  for (int k = 0; k < 2; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out + k, s[k]);
+  }
+}
+
+}  // namespace dev
+}  // namespace fempic

@@ -1,0 +1,777 @@
+// Host set-up of the EM-FEMPIC model: exact local tables of the order-p
+// interpolatory Whitney bases (Appendix), mesh complex and DOF numbering
+// (Section III-A), barycentric maps, and CSR assembly of the Hodge matrices,
+// the curl-curl matrix and the exact-sequence maps.
+//
+// This file must be compiled without floating-point contraction
+// (-ffp-contract=off): the barycentric maps are evaluated in a fixed order with
+// one rounding per operation so that the device walk is reproducible.
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <thread>
+
+#include "internal.h"
+
+namespace fempic {
+namespace {
+
+// ------------------------------------------------------------------------
+// Exact rational arithmetic and polynomials (local tables only).
+// ------------------------------------------------------------------------
+using i128 = __int128;
+
+i128 gcd128(i128 a, i128 b) {
+  if (a < 0) a = -a;
+  if (b < 0) b = -b;
+  while (b != 0) {
+    i128 t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+struct Rat {
+  i128 n = 0, d = 1;
+};
+
+Rat mk(i128 n, i128 d) {
+  if (d < 0) {
+    n = -n;
+    d = -d;
+  }
+  i128 g = gcd128(n, d);
+  if (g > 1) {
+    n /= g;
+    d /= g;
+  }
+  if (n == 0) d = 1;
+  return Rat{n, d};
+}
+Rat operator+(Rat a, Rat b) { return mk(a.n * b.d + b.n * a.d, a.d * b.d); }
+Rat operator-(Rat a, Rat b) { return mk(a.n * b.d - b.n * a.d, a.d * b.d); }
+Rat operator*(Rat a, Rat b) { return mk(a.n * b.n, a.d * b.d); }
+Rat operator/(Rat a, Rat b) { return mk(a.n * b.d, a.d * b.n); }
+bool is_zero(Rat a) { return a.n == 0; }
+double to_double(Rat a) { return (double)a.n / (double)a.d; }
+Rat R(long long n, long long d = 1) { return mk(n, d); }
+
+// Polynomial: exponent key -> coefficient.  Four 4-bit exponent fields, used
+// either for barycentric (l0,l1,l2,l3) or Cartesian reference (x,y,z) terms.
+struct Poly {
+  std::map<uint32_t, Rat> c;
+};
+
+int ex(uint32_t key, int v) { return (key >> (4 * v)) & 15; }
+
+Poly padd(const Poly& a, const Poly& b, Rat sb = R(1)) {
+  Poly r = a;
+  for (auto& kv : b.c) {
+    Rat v = r.c.count(kv.first) ? r.c[kv.first] + sb * kv.second : sb * kv.second;
+    if (is_zero(v))
+      r.c.erase(kv.first);
+    else
+      r.c[kv.first] = v;
+  }
+  return r;
+}
+Poly pscale(const Poly& a, Rat s) {
+  Poly r;
+  if (is_zero(s)) return r;
+  for (auto& kv : a.c) r.c[kv.first] = kv.second * s;
+  return r;
+}
+Poly pmul(const Poly& a, const Poly& b) {
+  Poly r;
+  for (auto& x : a.c)
+    for (auto& y : b.c) {
+      uint32_t k = x.first + y.first;  // fields never exceed 15 here
+      Rat v = r.c.count(k) ? r.c[k] + x.second * y.second : x.second * y.second;
+      if (is_zero(v))
+        r.c.erase(k);
+      else
+        r.c[k] = v;
+    }
+  return r;
+}
+Poly pconst(Rat v) {
+  Poly r;
+  if (!is_zero(v)) r.c[0] = v;
+  return r;
+}
+Poly lam(int i) {  // barycentric l_i
+  Poly r;
+  r.c[1u << (4 * i)] = R(1);
+  return r;
+}
+// a*l_i + b
+Poly lin(int i, long long a, long long b) { return padd(pscale(lam(i), R(a)), pconst(R(b))); }
+
+long long fact(int n) {
+  long long f = 1;
+  for (int i = 2; i <= n; ++i) f *= i;
+  return f;
+}
+
+// int over the reference tet of l0^a l1^b l2^c l3^d = a! b! c! d! / (a+b+c+d+3)!
+Rat integrate_bary(const Poly& p) {
+  Rat s = R(0);
+  for (auto& kv : p.c) {
+    int a = ex(kv.first, 0), b = ex(kv.first, 1), c = ex(kv.first, 2), d = ex(kv.first, 3);
+    s = s + kv.second * mk((i128)fact(a) * fact(b) * fact(c) * fact(d), (i128)fact(a + b + c + d + 3));
+  }
+  return s;
+}
+
+// Barycentric -> Cartesian on the reference tet: l0 = 1-x-y-z, l1 = x, l2 = y, l3 = z.
+Poly to_xyz(const Poly& p) {
+  Poly X, Y, Z;
+  X.c[1u] = R(1);
+  Y.c[1u << 4] = R(1);
+  Z.c[1u << 8] = R(1);
+  Poly L0 = padd(padd(padd(pconst(R(1)), X, R(-1)), Y, R(-1)), Z, R(-1));
+  Poly out;
+  for (auto& kv : p.c) {
+    Poly t = pconst(kv.second);
+    for (int k = 0; k < ex(kv.first, 0); ++k) t = pmul(t, L0);
+    for (int k = 0; k < ex(kv.first, 1); ++k) t = pmul(t, X);
+    for (int k = 0; k < ex(kv.first, 2); ++k) t = pmul(t, Y);
+    for (int k = 0; k < ex(kv.first, 3); ++k) t = pmul(t, Z);
+    out = padd(out, t);
+  }
+  return out;
+}
+
+Poly deriv(const Poly& p, int v) {  // d/dx_v of a Cartesian polynomial
+  Poly r;
+  for (auto& kv : p.c) {
+    int e = ex(kv.first, v);
+    if (e == 0) continue;
+    r.c[kv.first - (1u << (4 * v))] = kv.second * R(e);
+  }
+  return r;
+}
+
+using Vec = std::array<Poly, 3>;
+const int kG[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};  // grad l on the reference tet
+
+std::array<int, 3> gcross(int a, int b) {
+  return {kG[a][1] * kG[b][2] - kG[a][2] * kG[b][1], kG[a][2] * kG[b][0] - kG[a][0] * kG[b][2],
+          kG[a][0] * kG[b][1] - kG[a][1] * kG[b][0]};
+}
+
+int pair_index(int a, int b) {
+  for (int k = 0; k < 6; ++k)
+    if (kLocalEdges[k][0] == a && kLocalEdges[k][1] == b) return k;
+  return -1;
+}
+
+// Redundant forms: W1 = sum_a P[a] grad l_a; W2 = sum_{a<b} P[pair] grad l_a x grad l_b.
+std::vector<std::array<Poly, 4>> w1_forms(int p) {
+  std::vector<std::array<Poly, 4>> out;
+  auto add = [&](int a, int b, const Poly& m) {
+    std::array<Poly, 4> f;
+    f[b] = pmul(m, lam(a));
+    f[a] = pscale(pmul(m, lam(b)), R(-1));
+    out.push_back(f);
+  };
+  if (p == 1) {
+    for (auto& e : kLocalEdges) add(e[0], e[1], pconst(R(1)));
+    return out;
+  }
+  for (auto& e : kLocalEdges) {
+    add(e[0], e[1], lin(e[0], 3, -1));  // (3 l_s - 1) w_st
+    add(e[0], e[1], lin(e[1], 3, -1));  // (3 l_t - 1) w_st
+  }
+  for (auto& f : kLocalFaces) {
+    add(f[0], f[1], lin(f[2], 3, 0));   // 3 l_u w_st
+    add(f[0], f[2], lin(f[1], 3, 0));   // 3 l_t w_su
+  }
+  return out;
+}
+
+std::vector<std::array<Poly, 6>> w2_forms(int p) {
+  std::vector<std::array<Poly, 6>> out;
+  auto add = [&](int face, const Poly& m) {
+    int s = kLocalFaces[face][0], t = kLocalFaces[face][1], u = kLocalFaces[face][2];
+    std::array<Poly, 6> f;
+    // 2 (l_s X_tu + l_t X_us + l_u X_st), X_us = -X_su
+    f[pair_index(t, u)] = pscale(pmul(m, lam(s)), R(2));
+    f[pair_index(s, u)] = pscale(pmul(m, lam(t)), R(-2));
+    f[pair_index(s, t)] = pscale(pmul(m, lam(u)), R(2));
+    out.push_back(f);
+  };
+  if (p == 1) {
+    for (int f = 0; f < 4; ++f) add(f, pconst(R(1)));
+    return out;
+  }
+  for (int f = 0; f < 4; ++f)
+    for (int v = 0; v < 3; ++v) add(f, lin(kLocalFaces[f][v], 4, -1));  // (4 l_v - 1) w_stu
+  for (int i = 0; i < 3; ++i) add(i, lin(i, 4, 0));                       // 4 l_i w_(face i)
+  return out;
+}
+
+std::vector<Poly> w0_forms(int p) {
+  std::vector<Poly> out;
+  if (p == 1) {
+    for (int i = 0; i < 4; ++i) out.push_back(lam(i));
+    return out;
+  }
+  for (int s = 0; s < 4; ++s) out.push_back(pmul(lam(s), lin(s, 2, -1)));
+  for (auto& e : kLocalEdges) out.push_back(pscale(pmul(lam(e[0]), lam(e[1])), R(4)));
+  return out;
+}
+
+Vec w1_xyz(const std::array<Poly, 4>& f) {
+  Vec v;
+  for (int k = 0; k < 3; ++k) {
+    Poly s;
+    for (int a = 0; a < 4; ++a)
+      if (kG[a][k] != 0) s = padd(s, f[a], R(kG[a][k]));
+    v[k] = to_xyz(s);
+  }
+  return v;
+}
+
+Vec w2_xyz(const std::array<Poly, 6>& f) {
+  Vec v;
+  for (int k = 0; k < 3; ++k) {
+    Poly s;
+    for (int q = 0; q < 6; ++q) {
+      int c = gcross(kLocalEdges[q][0], kLocalEdges[q][1])[k];
+      if (c != 0) s = padd(s, f[q], R(c));
+    }
+    v[k] = to_xyz(s);
+  }
+  return v;
+}
+
+Vec grad_xyz(const Poly& p) {
+  Poly x = to_xyz(p);
+  return {deriv(x, 0), deriv(x, 1), deriv(x, 2)};
+}
+
+Vec curl_xyz(const Vec& v) {
+  return {padd(deriv(v[2], 1), deriv(v[1], 2), R(-1)), padd(deriv(v[0], 2), deriv(v[2], 0), R(-1)),
+          padd(deriv(v[1], 0), deriv(v[0], 1), R(-1))};
+}
+
+// Solve sum_j X[j][k] basis_j = target_k exactly for every k (least squares is
+// unnecessary: the targets lie in the span).  Returns "" or an error.
+std::string solve_in_span(const std::vector<Vec>& basis, const std::vector<Vec>& target,
+                          std::vector<double>* X) {
+  std::map<std::pair<int, uint32_t>, int> rowid;
+  auto collect = [&](const std::vector<Vec>& vs) {
+    for (auto& v : vs)
+      for (int k = 0; k < 3; ++k)
+        for (auto& kv : v[k].c) rowid.emplace(std::make_pair(k, kv.first), 0);
+  };
+  collect(basis);
+  collect(target);
+  int nr = 0;
+  for (auto& kv : rowid) kv.second = nr++;
+  int nb = (int)basis.size(), nt = (int)target.size(), nc = nb + nt;
+  std::vector<Rat> A((size_t)nr * nc);
+  auto put = [&](const Vec& v, int col) {
+    for (int k = 0; k < 3; ++k)
+      for (auto& kv : v[k].c) A[(size_t)rowid[std::make_pair(k, kv.first)] * nc + col] = kv.second;
+  };
+  for (int j = 0; j < nb; ++j) put(basis[j], j);
+  for (int j = 0; j < nt; ++j) put(target[j], nb + j);
+  // Gauss-Jordan on the basis columns
+  std::vector<int> pivcol;
+  int r = 0;
+  for (int c = 0; c < nb && r < nr; ++c) {
+    int piv = -1;
+    for (int i = r; i < nr; ++i)
+      if (!is_zero(A[(size_t)i * nc + c])) {
+        piv = i;
+        break;
+      }
+    if (piv < 0) return "basis is rank deficient";
+    for (int j = 0; j < nc; ++j) std::swap(A[(size_t)r * nc + j], A[(size_t)piv * nc + j]);
+    Rat inv = R(1) / A[(size_t)r * nc + c];
+    for (int j = 0; j < nc; ++j) A[(size_t)r * nc + j] = A[(size_t)r * nc + j] * inv;
+    for (int i = 0; i < nr; ++i) {
+      if (i == r || is_zero(A[(size_t)i * nc + c])) continue;
+      Rat f = A[(size_t)i * nc + c];
+      for (int j = 0; j < nc; ++j) A[(size_t)i * nc + j] = A[(size_t)i * nc + j] - f * A[(size_t)r * nc + j];
+    }
+    pivcol.push_back(c);
+    ++r;
+  }
+  if ((int)pivcol.size() != nb) return "basis is rank deficient";
+  for (int i = nb; i < nr; ++i)
+    for (int j = nb; j < nc; ++j)
+      if (!is_zero(A[(size_t)i * nc + j])) return "target not in the span of the basis";
+  X->assign((size_t)nb * nt, 0.0);
+  for (int i = 0; i < nb; ++i)
+    for (int k = 0; k < nt; ++k) (*X)[(size_t)i * nt + k] = to_double(A[(size_t)i * nc + nb + k]);
+  return "";
+}
+
+// ------------------------------------------------------------------------
+// Helpers
+// ------------------------------------------------------------------------
+template <class F>
+void parallel_for(int64_t n, F fn) {
+  unsigned hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  if (n < 256 || hw == 1) {
+    fn(int64_t(0), n);
+    return;
+  }
+  std::vector<std::thread> th;
+  int64_t chunk = (n + hw - 1) / hw;
+  for (unsigned k = 0; k < hw; ++k) {
+    int64_t a = k * chunk, b = std::min(n, a + chunk);
+    if (a >= b) break;
+    th.emplace_back([=] { fn(a, b); });
+  }
+  for (auto& t : th) t.join();
+}
+
+// CSR pattern of sum_t P_r(t)^T (local) P_c(t): rows R[t][i], cols Cm[t][j],
+// entries where localmask[i*lc+j] and both row and column are kept.
+void build_pattern(int32_t nr, int32_t nc, int32_t nt, int lr, int lc, const int32_t* Rm,
+                   const int32_t* Cm, const std::vector<uint8_t>& rowkeep,
+                   const std::vector<uint8_t>& colkeep, const std::vector<uint8_t>& localmask,
+                   HostCSR* out) {
+  std::vector<int32_t> start((size_t)nr + 1, 0);
+  for (int32_t t = 0; t < nt; ++t)
+    for (int i = 0; i < lr; ++i) {
+      int32_t r = Rm[(size_t)t * lr + i];
+      if (rowkeep[r]) start[r + 1]++;
+    }
+  for (int32_t r = 0; r < nr; ++r) start[r + 1] += start[r];
+  std::vector<int32_t> inc((size_t)start[nr]), ploc((size_t)start[nr]);
+  std::vector<int32_t> fill(start.begin(), start.end() - 1);
+  for (int32_t t = 0; t < nt; ++t)
+    for (int i = 0; i < lr; ++i) {
+      int32_t r = Rm[(size_t)t * lr + i];
+      if (!rowkeep[r]) continue;
+      inc[fill[r]] = t;
+      ploc[fill[r]] = i;
+      fill[r]++;
+    }
+  std::vector<std::vector<int32_t>> rows((size_t)nr);
+  parallel_for(nr, [&](int64_t a, int64_t b) {
+    for (int64_t r = a; r < b; ++r) {
+      auto& v = rows[r];
+      for (int32_t k = start[r]; k < start[r + 1]; ++k) {
+        int32_t t = inc[k], i = ploc[k];
+        for (int j = 0; j < lc; ++j) {
+          if (!localmask[(size_t)i * lc + j]) continue;
+          int32_t c = Cm[(size_t)t * lc + j];
+          if (colkeep[c]) v.push_back(c);
+        }
+      }
+      std::sort(v.begin(), v.end());
+      v.erase(std::unique(v.begin(), v.end()), v.end());
+    }
+  });
+  out->n_rows = nr;
+  out->n_cols = nc;
+  out->rowptr.assign((size_t)nr + 1, 0);
+  for (int32_t r = 0; r < nr; ++r) out->rowptr[r + 1] = out->rowptr[r] + (int32_t)rows[r].size();
+  out->col.resize((size_t)out->rowptr[nr]);
+  for (int32_t r = 0; r < nr; ++r) std::copy(rows[r].begin(), rows[r].end(), out->col.begin() + out->rowptr[r]);
+  out->val.assign(out->col.size(), 0.0);
+}
+
+// add (or set) a local matrix into the pattern
+inline void scatter(HostCSR* A, const int32_t* Rm, const int32_t* Cm, int lr, int lc, const double* Ae,
+                    const std::vector<uint8_t>& rowkeep, const std::vector<uint8_t>& colkeep, bool set) {
+  for (int i = 0; i < lr; ++i) {
+    int32_t r = Rm[i];
+    if (!rowkeep[r]) continue;
+    const int32_t* b = A->col.data() + A->rowptr[r];
+    const int32_t* e = A->col.data() + A->rowptr[r + 1];
+    for (int j = 0; j < lc; ++j) {
+      double v = Ae[(size_t)i * lc + j];
+      if (v == 0.0) continue;
+      int32_t c = Cm[j];
+      if (!colkeep[c]) continue;
+      const int32_t* p = std::lower_bound(b, e, c);
+      if (p == e || *p != c) continue;  // structurally zero
+      double& dst = A->val[(size_t)(p - A->col.data())];
+      if (set)
+        dst = v;
+      else
+        dst += v;
+    }
+  }
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------
+std::string build_local_tables(int p, LocalTables* T) {
+  T->order = p;
+  T->nl0 = nloc0(p);
+  T->nl1 = nloc1(p);
+  T->nl2 = nloc2(p);
+  auto f1 = w1_forms(p);
+  auto f2 = w2_forms(p);
+  auto f0 = w0_forms(p);
+  if ((int)f1.size() != T->nl1 || (int)f2.size() != T->nl2 || (int)f0.size() != T->nl0)
+    return "local DOF count mismatch";
+  std::vector<Vec> w1v, w2v, g0v, c1v;
+  for (auto& f : f1) w1v.push_back(w1_xyz(f));
+  for (auto& f : f2) w2v.push_back(w2_xyz(f));
+  for (auto& f : f0) g0v.push_back(grad_xyz(f));
+  for (auto& v : w1v) c1v.push_back(curl_xyz(v));
+  std::string err = solve_in_span(w1v, g0v, &T->Dloc);
+  if (!err.empty()) return "grad map: " + err;
+  err = solve_in_span(w2v, c1v, &T->Cloc);
+  if (!err.empty()) return "curl map: " + err;
+  int n1 = T->nl1, n2 = T->nl2;
+  T->T1.assign((size_t)n1 * n1 * 16, 0.0);
+  for (int i = 0; i < n1; ++i)
+    for (int j = 0; j < n1; ++j)
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          if (f1[i][a].c.empty() || f1[j][b].c.empty()) continue;
+          T->T1[(((size_t)i * n1 + j) * 4 + a) * 4 + b] = to_double(integrate_bary(pmul(f1[i][a], f1[j][b])));
+        }
+  T->T2.assign((size_t)n2 * n2 * 36, 0.0);
+  for (int i = 0; i < n2; ++i)
+    for (int j = 0; j < n2; ++j)
+      for (int a = 0; a < 6; ++a)
+        for (int b = 0; b < 6; ++b) {
+          if (f2[i][a].c.empty() || f2[j][b].c.empty()) continue;
+          T->T2[(((size_t)i * n2 + j) * 6 + a) * 6 + b] = to_double(integrate_bary(pmul(f2[i][a], f2[j][b])));
+        }
+  T->I0.resize(T->nl0);
+  for (int k = 0; k < T->nl0; ++k) T->I0[k] = to_double(integrate_bary(f0[k]));
+  return "";
+}
+
+int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets_in, int32_t n_tets, int p,
+                HostModel* m, std::string* err) {
+  if (p != 1 && p != 2) {
+    *err = "order must be 1 or 2";
+    return 1;
+  }
+  if (n_nodes < 4 || n_tets < 1 || !xyz || !tets_in) {
+    *err = "empty mesh";
+    return 1;
+  }
+  LocalTables T;
+  std::string e = build_local_tables(p, &T);
+  if (!e.empty()) {
+    *err = "local tables: " + e;
+    return 1;
+  }
+  m->order = p;
+  m->nl0 = T.nl0;
+  m->nl1 = T.nl1;
+  m->nl2 = T.nl2;
+  m->n_nodes = n_nodes;
+  m->n_tets = n_tets;
+  const int32_t nt = n_tets;
+  m->tets.resize((size_t)nt * 4);
+  for (int32_t t = 0; t < nt; ++t) {
+    int32_t v[4];
+    for (int k = 0; k < 4; ++k) {
+      v[k] = tets_in[(size_t)t * 4 + k];
+      if (v[k] < 0 || v[k] >= n_nodes) {
+        *err = "tet " + std::to_string(t) + " references a node out of range";
+        return 2;
+      }
+    }
+    std::sort(v, v + 4);
+    for (int k = 0; k < 3; ++k)
+      if (v[k] == v[k + 1]) {
+        *err = "tet " + std::to_string(t) + " has a repeated vertex";
+        return 2;
+      }
+    std::copy(v, v + 4, m->tets.begin() + (size_t)t * 4);
+  }
+  // ---- edges (sorted pairs, lexicographic) --------------------------------
+  std::vector<uint64_t> ek((size_t)nt * 6);
+  for (int32_t t = 0; t < nt; ++t)
+    for (int k = 0; k < 6; ++k) {
+      uint64_t a = (uint32_t)m->tets[(size_t)t * 4 + kLocalEdges[k][0]];
+      uint64_t b = (uint32_t)m->tets[(size_t)t * 4 + kLocalEdges[k][1]];
+      ek[(size_t)t * 6 + k] = (a << 32) | b;
+    }
+  std::vector<uint64_t> edges(ek);
+  std::sort(edges.begin(), edges.end());
+  edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+  m->n_edges = (int32_t)edges.size();
+  std::vector<int32_t> tet_edge((size_t)nt * 6);
+  for (size_t i = 0; i < ek.size(); ++i)
+    tet_edge[i] = (int32_t)(std::lower_bound(edges.begin(), edges.end(), ek[i]) - edges.begin());
+  // ---- faces (sorted triples, lexicographic) -------------------------------
+  struct F3 {
+    int32_t a, b, c;
+    bool operator<(const F3& o) const {
+      return a != o.a ? a < o.a : (b != o.b ? b < o.b : c < o.c);
+    }
+    bool operator==(const F3& o) const { return a == o.a && b == o.b && c == o.c; }
+  };
+  std::vector<F3> fk((size_t)nt * 4);
+  for (int32_t t = 0; t < nt; ++t)
+    for (int k = 0; k < 4; ++k)
+      fk[(size_t)t * 4 + k] = F3{m->tets[(size_t)t * 4 + kLocalFaces[k][0]],
+                                 m->tets[(size_t)t * 4 + kLocalFaces[k][1]],
+                                 m->tets[(size_t)t * 4 + kLocalFaces[k][2]]};
+  std::vector<F3> faces(fk);
+  std::sort(faces.begin(), faces.end());
+  faces.erase(std::unique(faces.begin(), faces.end()), faces.end());
+  m->n_faces = (int32_t)faces.size();
+  std::vector<int32_t> tet_face((size_t)nt * 4);
+  for (size_t i = 0; i < fk.size(); ++i)
+    tet_face[i] = (int32_t)(std::lower_bound(faces.begin(), faces.end(), fk[i]) - faces.begin());
+  // ---- face owners, neighbours, boundary ----------------------------------
+  std::vector<int32_t> own((size_t)m->n_faces * 2, -1), cnt(m->n_faces, 0);
+  for (int32_t t = 0; t < nt; ++t)
+    for (int k = 0; k < 4; ++k) {
+      int32_t f = tet_face[(size_t)t * 4 + k];
+      if (cnt[f] >= 2) {
+        *err = "face shared by more than two tets (non-manifold mesh)";
+        return 2;
+      }
+      own[(size_t)f * 2 + cnt[f]] = t * 4 + k;
+      cnt[f]++;
+    }
+  m->nbr.assign((size_t)nt * 4, -1);
+  std::vector<uint8_t> bface(m->n_faces, 0), bedge(m->n_edges, 0), bnode(n_nodes, 0);
+  m->n_bfaces = 0;
+  for (int32_t f = 0; f < m->n_faces; ++f) {
+    if (cnt[f] == 2) {
+      int32_t a = own[(size_t)f * 2], b = own[(size_t)f * 2 + 1];
+      m->nbr[a] = ((b >> 2) << 2) | (b & 3);
+      m->nbr[b] = ((a >> 2) << 2) | (a & 3);
+    } else {
+      bface[f] = 1;
+      m->n_bfaces++;
+      bnode[faces[f].a] = bnode[faces[f].b] = bnode[faces[f].c] = 1;
+    }
+  }
+  // boundary edges: edges of boundary faces
+  for (int32_t t = 0; t < nt; ++t)
+    for (int k = 0; k < 4; ++k) {
+      if (!bface[tet_face[(size_t)t * 4 + k]]) continue;
+      for (int j = 0; j < 6; ++j) {
+        int s = kLocalEdges[j][0], u = kLocalEdges[j][1];
+        if (s != k && u != k) bedge[tet_edge[(size_t)t * 6 + j]] = 1;
+      }
+    }
+  // ---- DOF numbering --------------------------------------------------------
+  const int32_t ne = m->n_edges, nf = m->n_faces, nn = n_nodes;
+  const int l0 = m->nl0, l1 = m->nl1, l2 = m->nl2;
+  m->dof0.resize((size_t)nt * l0);
+  m->dof1.resize((size_t)nt * l1);
+  m->dof2.resize((size_t)nt * l2);
+  if (p == 1) {
+    m->n1 = ne;
+    m->n2 = nf;
+    m->n0 = nn;
+    for (int32_t t = 0; t < nt; ++t) {
+      for (int k = 0; k < 6; ++k) m->dof1[(size_t)t * 6 + k] = tet_edge[(size_t)t * 6 + k];
+      for (int k = 0; k < 4; ++k) m->dof2[(size_t)t * 4 + k] = tet_face[(size_t)t * 4 + k];
+      for (int k = 0; k < 4; ++k) m->dof0[(size_t)t * 4 + k] = m->tets[(size_t)t * 4 + k];
+    }
+    m->pec1.assign(bedge.begin(), bedge.end());
+    m->bnd0.assign(bnode.begin(), bnode.end());
+  } else {
+    if ((int64_t)2 * ne + 2 * (int64_t)nf > INT32_MAX || (int64_t)3 * nf + 3 * (int64_t)nt > INT32_MAX) {
+      *err = "mesh too large for 32-bit DOF ids";
+      return 1;
+    }
+    m->n1 = 2 * ne + 2 * nf;
+    m->n2 = 3 * nf + 3 * nt;
+    m->n0 = nn + ne;
+    for (int32_t t = 0; t < nt; ++t) {
+      for (int k = 0; k < 6; ++k) {
+        m->dof1[(size_t)t * 20 + 2 * k] = 2 * tet_edge[(size_t)t * 6 + k];
+        m->dof1[(size_t)t * 20 + 2 * k + 1] = 2 * tet_edge[(size_t)t * 6 + k] + 1;
+      }
+      for (int k = 0; k < 4; ++k) {
+        m->dof1[(size_t)t * 20 + 12 + 2 * k] = 2 * ne + 2 * tet_face[(size_t)t * 4 + k];
+        m->dof1[(size_t)t * 20 + 13 + 2 * k] = 2 * ne + 2 * tet_face[(size_t)t * 4 + k] + 1;
+      }
+      for (int k = 0; k < 4; ++k)
+        for (int v = 0; v < 3; ++v) m->dof2[(size_t)t * 15 + 3 * k + v] = 3 * tet_face[(size_t)t * 4 + k] + v;
+      for (int i = 0; i < 3; ++i) m->dof2[(size_t)t * 15 + 12 + i] = 3 * nf + 3 * t + i;
+      for (int k = 0; k < 4; ++k) m->dof0[(size_t)t * 10 + k] = m->tets[(size_t)t * 4 + k];
+      for (int k = 0; k < 6; ++k) m->dof0[(size_t)t * 10 + 4 + k] = nn + tet_edge[(size_t)t * 6 + k];
+    }
+    m->pec1.assign(m->n1, 0);
+    for (int32_t e2 = 0; e2 < ne; ++e2)
+      if (bedge[e2]) m->pec1[2 * e2] = m->pec1[2 * e2 + 1] = 1;
+    for (int32_t f = 0; f < nf; ++f)
+      if (bface[f]) m->pec1[2 * ne + 2 * f] = m->pec1[2 * ne + 2 * f + 1] = 1;
+    m->bnd0.assign(m->n0, 0);
+    for (int32_t v = 0; v < nn; ++v) m->bnd0[v] = bnode[v];
+    for (int32_t e2 = 0; e2 < ne; ++e2) m->bnd0[nn + e2] = bedge[e2];
+  }
+  // ---- barycentric maps (fixed operation order, no contraction) -----------
+  m->geom.resize((size_t)nt * 16);
+  m->vol.resize(nt);
+  double hmax = 0.0;
+  for (int32_t t = 0; t < nt; ++t) {
+    const double* P0 = xyz + 3 * (size_t)m->tets[(size_t)t * 4 + 0];
+    double e1[3], e2v[3], e3[3];
+    for (int k = 0; k < 3; ++k) {
+      e1[k] = xyz[3 * (size_t)m->tets[(size_t)t * 4 + 1] + k] - P0[k];
+      e2v[k] = xyz[3 * (size_t)m->tets[(size_t)t * 4 + 2] + k] - P0[k];
+      e3[k] = xyz[3 * (size_t)m->tets[(size_t)t * 4 + 3] + k] - P0[k];
+      hmax = std::max(hmax, std::max(std::fabs(e1[k]), std::max(std::fabs(e2v[k]), std::fabs(e3[k]))));
+    }
+    auto cross = [](const double* a, const double* b, double* o) {
+      o[0] = a[1] * b[2] - a[2] * b[1];
+      o[1] = a[2] * b[0] - a[0] * b[2];
+      o[2] = a[0] * b[1] - a[1] * b[0];
+    };
+    double n1v[3], n2v[3], n3v[3];
+    cross(e2v, e3, n1v);
+    cross(e3, e1, n2v);
+    cross(e1, e2v, n3v);
+    double det = (e1[0] * n1v[0] + e1[1] * n1v[1]) + e1[2] * n1v[2];
+    double len = std::max(std::fabs(e1[0]) + std::fabs(e1[1]) + std::fabs(e1[2]),
+                          std::max(std::fabs(e2v[0]) + std::fabs(e2v[1]) + std::fabs(e2v[2]),
+                                   std::fabs(e3[0]) + std::fabs(e3[1]) + std::fabs(e3[2])));
+    if (!(std::fabs(det) > 1e-12 * len * len * len)) {
+      *err = "tet " + std::to_string(t) + " is degenerate (zero volume)";
+      return 2;
+    }
+    double* G = &m->geom[(size_t)t * 16];
+    for (int k = 0; k < 3; ++k) {
+      G[3 + k] = n1v[k] / det;
+      G[6 + k] = n2v[k] / det;
+      G[9 + k] = n3v[k] / det;
+    }
+    for (int k = 0; k < 3; ++k) G[k] = -((G[3 + k] + G[6 + k]) + G[9 + k]);
+    double* c = G + 12;
+    for (int i = 1; i < 4; ++i)
+      c[i] = -((G[3 * i] * P0[0] + G[3 * i + 1] * P0[1]) + G[3 * i + 2] * P0[2]);
+    c[0] = 1.0 - ((c[1] + c[2]) + c[3]);
+    m->vol[t] = std::fabs(det) / 6.0;
+  }
+  (void)hmax;
+  // ---- matrices --------------------------------------------------------------
+  std::vector<uint8_t> free1(m->n1), all1(m->n1, 1), all2(m->n2, 1), int0(m->n0), all0(m->n0, 1);
+  for (int32_t i = 0; i < m->n1; ++i) free1[i] = !m->pec1[i];
+  for (int32_t i = 0; i < m->n0; ++i) int0[i] = !m->bnd0[i];
+  std::vector<uint8_t> full11((size_t)l1 * l1, 1), full12((size_t)l1 * l2, 1), full22((size_t)l2 * l2, 1),
+      full00((size_t)l0 * l0, 1), maskC((size_t)l2 * l1), maskD((size_t)l1 * l0), maskDT((size_t)l0 * l1);
+  for (int f = 0; f < l2; ++f)
+    for (int j = 0; j < l1; ++j) maskC[(size_t)f * l1 + j] = T.Cloc[(size_t)f * l1 + j] != 0.0;
+  for (int i = 0; i < l1; ++i)
+    for (int k = 0; k < l0; ++k) {
+      maskD[(size_t)i * l0 + k] = T.Dloc[(size_t)i * l0 + k] != 0.0;
+      maskDT[(size_t)k * l1 + i] = maskD[(size_t)i * l0 + k];
+    }
+  const int32_t* d1 = m->dof1.data();
+  const int32_t* d2 = m->dof2.data();
+  const int32_t* d0 = m->dof0.data();
+  build_pattern(m->n1, m->n1, nt, l1, l1, d1, d1, free1, free1, full11, &m->M);
+  m->K = m->M;
+  build_pattern(m->n1, m->n2, nt, l1, l2, d1, d2, free1, all2, full12, &m->Q);
+  build_pattern(m->n2, m->n2, nt, l2, l2, d2, d2, all2, all2, full22, &m->M2);
+  build_pattern(m->n2, m->n1, nt, l2, l1, d2, d1, all2, free1, maskC, &m->C);
+  build_pattern(m->n1, m->n0, nt, l1, l0, d1, d0, all1, int0, maskD, &m->D);
+  build_pattern(m->n0, m->n1, nt, l0, l1, d0, d1, all0, all1, maskDT, &m->DT);
+  build_pattern(m->n0, m->n0, nt, l0, l0, d0, d0, int0, int0, full00, &m->L);
+  m->load0.assign(m->n0, 0.0);
+
+  std::vector<double> DT_loc((size_t)l0 * l1);
+  for (int i = 0; i < l1; ++i)
+    for (int k = 0; k < l0; ++k) DT_loc[(size_t)k * l1 + i] = T.Dloc[(size_t)i * l0 + k];
+
+  const int CH = 4096;
+  const size_t sM = (size_t)l1 * l1, sQ = (size_t)l1 * l2, sM2 = (size_t)l2 * l2, sL = (size_t)l0 * l0;
+  std::vector<double> bM(CH * sM), bK(CH * sM), bQ(CH * sQ), bM2(CH * sM2), bL(CH * sL), bW(CH * l0);
+  for (int32_t t0 = 0; t0 < nt; t0 += CH) {
+    int32_t nc = std::min(CH, nt - t0);
+    parallel_for(nc, [&](int64_t a, int64_t b) {
+      std::vector<double> M2e(sM2), tmp((size_t)l1 * l2), tmp2((size_t)l0 * l1);
+      for (int64_t q = a; q < b; ++q) {
+        int32_t t = t0 + (int32_t)q;
+        const double* g = &m->geom[(size_t)t * 16];
+        double G[4][4];
+        for (int i = 0; i < 4; ++i)
+          for (int j = 0; j < 4; ++j) G[i][j] = g[3 * i] * g[3 * j] + g[3 * i + 1] * g[3 * j + 1] + g[3 * i + 2] * g[3 * j + 2];
+        double H[6][6];
+        for (int P = 0; P < 6; ++P)
+          for (int Qi = 0; Qi < 6; ++Qi) {
+            int a1 = kLocalEdges[P][0], b1 = kLocalEdges[P][1], c1 = kLocalEdges[Qi][0], e1 = kLocalEdges[Qi][1];
+            H[P][Qi] = G[a1][c1] * G[b1][e1] - G[a1][e1] * G[b1][c1];
+          }
+        double v6 = 6.0 * m->vol[t];
+        double* Me = &bM[q * sM];
+        for (int i = 0; i < l1; ++i)
+          for (int j = 0; j < l1; ++j) {
+            const double* tt = &T.T1[((size_t)i * l1 + j) * 16];
+            double s = 0.0;
+            for (int x = 0; x < 4; ++x)
+              for (int y = 0; y < 4; ++y) s += G[x][y] * tt[x * 4 + y];
+            Me[(size_t)i * l1 + j] = kEps0 * v6 * s;
+          }
+        for (int i = 0; i < l2; ++i)
+          for (int j = 0; j < l2; ++j) {
+            const double* tt = &T.T2[((size_t)i * l2 + j) * 36];
+            double s = 0.0;
+            for (int x = 0; x < 6; ++x)
+              for (int y = 0; y < 6; ++y) s += H[x][y] * tt[x * 6 + y];
+            M2e[(size_t)i * l2 + j] = v6 * s / kMu0;
+          }
+        std::copy(M2e.begin(), M2e.end(), &bM2[q * sM2]);
+        // Q_e = Cloc^T M2e  (l1 x l2);  K_e = Q_e Cloc (l1 x l1)
+        double* Qe = &bQ[q * sQ];
+        for (int i = 0; i < l1; ++i)
+          for (int h = 0; h < l2; ++h) {
+            double s = 0.0;
+            for (int f = 0; f < l2; ++f) s += T.Cloc[(size_t)f * l1 + i] * M2e[(size_t)f * l2 + h];
+            Qe[(size_t)i * l2 + h] = s;
+          }
+        double* Ke = &bK[q * sM];
+        for (int i = 0; i < l1; ++i)
+          for (int j = 0; j < l1; ++j) {
+            double s = 0.0;
+            for (int h = 0; h < l2; ++h) s += Qe[(size_t)i * l2 + h] * T.Cloc[(size_t)h * l1 + j];
+            Ke[(size_t)i * l1 + j] = s;
+          }
+        // L_e = Dloc^T M_e Dloc
+        for (int k = 0; k < l0; ++k)
+          for (int j = 0; j < l1; ++j) {
+            double s = 0.0;
+            for (int i = 0; i < l1; ++i) s += DT_loc[(size_t)k * l1 + i] * Me[(size_t)i * l1 + j];
+            tmp2[(size_t)k * l1 + j] = s;
+          }
+        double* Le = &bL[q * sL];
+        for (int k = 0; k < l0; ++k)
+          for (int n = 0; n < l0; ++n) {
+            double s = 0.0;
+            for (int j = 0; j < l1; ++j) s += tmp2[(size_t)k * l1 + j] * T.Dloc[(size_t)j * l0 + n];
+            Le[(size_t)k * l0 + n] = s;
+          }
+        for (int k = 0; k < l0; ++k) bW[q * l0 + k] = v6 * T.I0[k];
+      }
+    });
+    for (int32_t q = 0; q < nc; ++q) {
+      int32_t t = t0 + q;
+      const int32_t* r1 = d1 + (size_t)t * l1;
+      const int32_t* r2 = d2 + (size_t)t * l2;
+      const int32_t* r0 = d0 + (size_t)t * l0;
+      scatter(&m->M, r1, r1, l1, l1, &bM[q * sM], free1, free1, false);
+      scatter(&m->K, r1, r1, l1, l1, &bK[q * sM], free1, free1, false);
+      scatter(&m->Q, r1, r2, l1, l2, &bQ[q * sQ], free1, all2, false);
+      scatter(&m->M2, r2, r2, l2, l2, &bM2[q * sM2], all2, all2, false);
+      scatter(&m->L, r0, r0, l0, l0, &bL[q * sL], int0, int0, false);
+      scatter(&m->C, r2, r1, l2, l1, T.Cloc.data(), all2, free1, true);
+      scatter(&m->D, r1, r0, l1, l0, T.Dloc.data(), all1, int0, true);
+      scatter(&m->DT, r0, r1, l0, l1, DT_loc.data(), all0, all1, true);
+      for (int k = 0; k < l0; ++k) m->load0[r0[k]] += bW[q * l0 + k];
+    }
+  }
+  return 0;
+}
+
+}  // namespace fempic

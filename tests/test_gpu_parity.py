@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA library through its C ABI against the oracle.
+
+Tolerances (derived from the arithmetic):
+* walk decisions (owning tet, crossing count, crossing-sequence hash) and, in
+  the strict FP64 mode, positions and velocities: bit-exact (both sides
+  evaluate the same formulas with one rounding per operation);
+* in the FP64 mode with fused multiply-adds: positions/velocities rel 1e-12,
+  owning tet exact where the particle is not within 1e-9 (in lambda) of a
+  face;
+* Delta g and rho: normwise rel 1e-12 (the same terms, summed in a different
+  order by atomics; the bar is charge conservation to 1e-12);
+* assembled operators: rel 1e-12 (exact rational element tables vs a
+  Gauss-Legendre collapsed-cube rule, both exact for the integrands);
+* the field solve: the GPU solution must satisfy the oracle's linear system
+  to ||A e - rhs|| <= 10 cg_rtol ||rhs|| (CG stops at cg_rtol; the oracle
+  solves directly).
+"""
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import particles as opart, topology as otopo
+from gpu_helpers import build_lib, pair, random_state, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    return build_lib()
+
+
+@pytest.fixture(scope="module")
+def c1small():
+    return workloads.make_config(0, n_particles=10_007)  # ragged: not a multiple of the block
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_sizes_and_operators(c1small, order):
+    o, g = pair(c1small, order=order)
+    t = o.topo
+    i = g.info
+    assert (i.n_tets, i.n_nodes, i.n_edges, i.n_faces) == (t.n_tets, t.n_nodes, t.n_edges, t.n_faces)
+    assert (i.n0, i.n1, i.n2) == (t.n0, t.n1, t.n2)
+    rng = np.random.default_rng(0)
+    fr = t.free1.astype(float)
+    x1 = rng.normal(size=t.n1)
+    x2 = rng.normal(size=t.n2)
+    x0 = rng.normal(size=t.n0)
+    in0 = t.interior0.astype(float)
+    assert rel(g.apply("M1", x1), fr * (o.M @ (fr * x1))) < 1e-12
+    assert rel(g.apply("K", x1), fr * (o.K @ (fr * x1))) < 1e-11
+    assert rel(g.apply("M2", x2), o.M2 @ x2) < 1e-12
+    assert rel(g.apply("C", x1), o.C @ (fr * x1)) < 1e-13
+    assert rel(g.apply("D", x0), o.D @ (in0 * x0)) < 1e-13
+    assert rel(g.apply("DT", x1), o.D.T @ x1) < 1e-13
+    L = (o.D.T @ o.M @ o.D).tocsr()
+    assert rel(g.apply("L", x0), in0 * (L @ (in0 * x0))) < 1e-11
+    g.close()
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("precision", ["fp64_strict", "fp64"])
+def test_eval_fields(c1small, order, precision):
+    o, g = pair(c1small, order=order, precision=precision, matrices=False, es_init=False)
+    rng = np.random.default_rng(1)
+    e, b = random_state(o.topo, rng)
+    g.set("E", e)
+    g.set("B", b)
+    x, tet = c1small["x"][:3000], c1small["tet"][:3000]
+    Eg, Bg = g.eval_fields(x, tet)
+    Eo, Bo = opart.gather(o.topo, o.g, o.c, e, b, o.B0, x, tet)
+    if precision == "fp64_strict":
+        assert np.array_equal(Eg, Eo) and np.array_equal(Bg, Bo)
+    else:
+        assert rel(Eg, Eo) < 1e-13 and rel(Bg, Bo) < 1e-13
+    g.close()
+
+
+def _unambiguous(o, x, tet, tol=1e-9):
+    from oracle import geometry
+    lam = geometry.lam(o.g[tet], o.c[tet], x)
+    return lam.min(axis=1) > tol
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("precision", ["fp64_strict", "fp64"])
+def test_one_step_parity(c1small, order, precision):
+    o, g = pair(c1small, order=order, precision=precision, es_init=False)
+    rng = np.random.default_rng(2)
+    e, b = random_state(o.topo, rng)
+    o.e, o.e_prev, o.b = e.copy(), e.copy(), b.copy()
+    g.set("E", e)
+    g.set("E_PREV", e)
+    g.set("B", b)
+    dt = c1small["dt"]
+    w = o.step(dt)
+    g.step(dt)
+    xg, vg, tg = g.get("X"), g.get("V"), g.get("TET")
+    if precision == "fp64_strict":
+        assert np.array_equal(xg, w["x"]) and np.array_equal(vg, w["v"])
+        assert np.array_equal(tg, w["tet"])
+        assert np.array_equal(g.get("NCROSS"), w["ncross"])
+        assert np.array_equal(g.get("HASH"), w["hash"])
+    else:
+        assert rel(xg, w["x"]) < 1e-12 and rel(vg, w["v"]) < 1e-12
+        ok = _unambiguous(o, w["x"], w["tet"])
+        assert ok.mean() > 0.99
+        assert np.array_equal(tg[ok], w["tet"][ok])
+    assert w["ncross"].mean() > 0.5
+    assert rel(g.get("DG"), w["dg"]) < 1e-12
+    assert rel(g.get("RHO"), o.rho) < 1e-12
+    # field solve: the GPU e^{n+1} satisfies the oracle's system
+    from oracle import fields as ofields
+    A = ofields.system_matrix(o.M, o.K, dt, "trapezoid")
+    eg = g.get("E")
+    fr = o.topo.free1
+    res = (A @ eg - w["rhs"])[fr]
+    assert np.linalg.norm(res) <= 10 * 1e-12 * np.linalg.norm(w["rhs"][fr])
+    assert np.all(eg[~fr] == 0.0)
+    assert rel(eg, o.e) < 1e-6
+    bg = g.get("B")
+    assert rel(bg, o.b) < 1e-6
+    g.close()
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_continuity_and_gauss_on_gpu(c1small, order):
+    """Charge conservation (continuity residual <= 1e-12 rel every step) and
+    Gauss's law carried from the electrostatic start, on the device."""
+    from paper_2111_12411_gb300 import Simulation
+    cfg = c1small
+    g = Simulation.from_config(cfg, diagnostics=True)
+    if order != cfg["order"]:
+        g.close()
+        g = Simulation(cfg["xyz"], cfg["tets"], order, cfg["q"], cfg["m"], cfg["weight"], cfg["x"],
+                       cfg["v"], cfg["tet"], B0=cfg["B0"], rho_ion=cfg["rho_ion"], diagnostics=True)
+    for n in range(5):
+        g.step(cfg["dt"])
+        d = g.diag()
+        assert d["continuity_abs"] <= 1e-12 * d["continuity_ref"]
+        assert d["gauss_abs"] <= 1e-10 * (n + 1) * d["gauss_ref"]
+        assert d["cg_residual"] <= 1e-12
+        assert d["crossings"] > 0
+    g.close()
+
+
+def test_walk_cap_reports_error(c1small):
+    from paper_2111_12411_gb300 import Simulation, FemPICError
+    g = Simulation.from_config(c1small, max_cross=1, es_init=False)
+    with pytest.raises(FemPICError) as ei:
+        g.step(c1small["dt"])
+    assert ei.value.code == 6  # FEMPIC_ERR_WALK
+    g.close()
+
+
+def test_cg_cap_reports_error(c1small):
+    from paper_2111_12411_gb300 import Simulation, FemPICError
+    g = Simulation.from_config(c1small, cg_max_it=1, es_init=False)
+    rng = np.random.default_rng(3)
+    g.set("E", workloads.random_dof_vector(g.info.n1, 1e3, rng,
+                                           otopo.Topology(c1small["xyz"], c1small["tets"], 1).pec1))
+    with pytest.raises(FemPICError) as ei:
+        g.step(c1small["dt"])
+    assert ei.value.code == 5  # FEMPIC_ERR_CG
+    g.close()
+
+
+def test_empty_species_and_reuse(c1small):
+    from paper_2111_12411_gb300 import Simulation
+    cfg = dict(c1small)
+    g = Simulation(cfg["xyz"], cfg["tets"], 2, cfg["q"], cfg["m"], cfg["weight"], np.zeros((0, 3)),
+                   np.zeros((0, 3)), np.zeros(0, np.int32))
+    g.step(cfg["dt"], 3)
+    assert np.all(g.get("E") == 0.0) and np.all(g.get("RHO") == 0.0)
+    g.close()
+
+
+def test_sort_keeps_particle_identity(c1small):
+    """Particles are re-sorted by tet on the device every step; results come
+    back in particle-id order and match an unsorted run."""
+    from paper_2111_12411_gb300 import Simulation
+    a = Simulation.from_config(c1small, precision="fp64_strict", sort_period=1, es_init=False)
+    b = Simulation.from_config(c1small, precision="fp64_strict", sort_period=0, es_init=False)
+    for s in (a, b):
+        s.step(c1small["dt"], 2)
+    assert np.array_equal(a.get("TET"), b.get("TET"))
+    assert rel(a.get("X"), b.get("X")) < 1e-13
+    a.close()
+    b.close()
+
+
+def test_full_size_drift_tube_sampled():
+    """The drift-tube workload at full size (132,480 tets, p = 2, 10^6
+    particles) in the launch configuration the benchmark times: the oracle
+    recomputes 400 sampled particles one by one from the same seeded state;
+    charge conservation is checked over all particles."""
+    from paper_2111_12411_gb300 import Simulation
+    cfg = workloads.make_config(1)
+    g = Simulation.from_config(cfg, precision="fp64_strict", diagnostics=True, es_init=False)
+    t = otopo.Topology(cfg["xyz"], cfg["tets"], 2)
+    rng = np.random.default_rng(4)
+    e, b = random_state(t, rng, e_scale=1e4, b_scale=1e-3)
+    g.set("E", e)
+    g.set("E_PREV", e)
+    g.set("B", b)
+    g.step(cfg["dt"])
+    d = g.diag()
+    assert d["continuity_abs"] <= 1e-12 * d["continuity_ref"]
+    from oracle.geometry import barycentric_maps
+    gg, cc, _ = barycentric_maps(t.xyz, t.tets)
+    idx = np.sort(rng.choice(len(cfg["x"]), 400, replace=False))
+    x0, v0, t0 = cfg["x"][idx], cfg["v"][idx], cfg["tet"][idx]
+    E, B = opart.gather(t, gg, cc, e, b, cfg["B0"], x0, t0)
+    vn = opart.boris(v0, E, B, cfg["q"], cfg["m"], cfg["dt"])
+    x1 = x0 + cfg["dt"] * vn
+    xe, ve, te, dg, nc, hs, st = opart.walk_deposit(t, gg, cc, x0, x1, vn, t0, cfg["q"] * cfg["weight"], t.n1)
+    assert np.array_equal(g.get("X")[idx], xe)
+    assert np.array_equal(g.get("V")[idx], ve)
+    assert np.array_equal(g.get("TET")[idx], te)
+    assert np.array_equal(g.get("HASH")[idx], hs)
+    g.close()
