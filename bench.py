@@ -1,0 +1,361 @@
+"""Benchmark of the EM-FEMPIC step on the drift-tube workload.
+
+Workload: cylinder of radius 1 cm and length 10 cm on a 24 x 12 x 80 polar
+Kuhn mesh (132,480 tets), order p = 2, 10^6 electrons (cold beam of radius
+0.5 cm, v_z = 3e7 m/s with a 1 % spread), B0 = 1 T along the axis,
+dt = 33.3 ps, FP64.  One step is one pass of the whole path: sort by tet,
+gather E/B, Boris push, ray-face walk, path-integral current deposit, charge
+measurement, Newmark right-hand side, device PCG solve and b update.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Prints one JSON line.  ``value`` = particle-steps per second of the whole
+step (all ranks), device-timed with CUDA events, L2 flushed between steps.
+With N > 1 (torchrun) each rank advances an independent replica (the
+path does not shard; no collective on the data path).
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/sec (gather+push+deposit) at p=2 and % HBM roofline; p50/p99 chunk latency"
+UNIT = "particle-steps/s"
+WORKLOAD = ("drift tube R=1cm L=10cm, polar Kuhn mesh 24x12x80 (132480 tets), p=2, "
+            "1e6 electrons, v_z=3e7 m/s, B0=1 T, dt=33.3 ps, FP64")
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, torch copy)"
+    return 6800.0, "fallback 6.8 TB/s"
+
+
+# ---- algorithmic bytes ---------------------------------------------------------------
+def pcg_bytes_per_iteration(info):
+    """Bytes one preconditioned CG iteration must move: the A, D and D^T CSR
+    arrays (8 B value + 4 B column per entry, 4 B row pointer per row) once,
+    and the vector passes (SpMV: p gather + q write; update: x, p, q, r read,
+    x, r write; nodal correction: r, t, dinv, dinv_L reads, t, z writes;
+    direction update: p, z read, p write)."""
+    n1, n0 = info.n1, info.n0
+    mats = 12 * (info.nnz_A + info.nnz_D + info.nnz_DT) + 4 * (2 * n1 + n0)
+    vec = 8 * (2 * n1 + 6 * n1 + (2 * n1 + 2 * n0 + n1 + n0) + n1 + 3 * n1)
+    return mats + vec
+
+
+def particle_bytes_per_step(order, n_particles, occupied_tets, crossings_per_particle):
+    """Bytes the particle loop must move per particle-step: the particle state
+    read and written once (x, v FP64 and the tet id: 2 x (48 + 4) B) plus, per
+    tet touched, its geometry (16 doubles), the gathered W1/W2 DOFs and their
+    index maps, the read-modify-write of its W1 current DOFs and W0 charge
+    DOFs, amortised over the particles per tet and multiplied by the tets
+    visited (1 + crossings)."""
+    n1, n2, n0 = (6, 4, 4) if order == 1 else (20, 15, 10)
+    per_tet = 128 + 8 * (n1 + n2) + 4 * (n1 + n2 + n0) + 16 * n1 + 16 * n0
+    ppc = n_particles / max(1, occupied_tets)
+    return 104.0 + per_tet / ppc * (1.0 + crossings_per_particle)
+
+
+# ---- clocks -----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+
+        sm = [num(r[1]) for r in rows]
+        smax = max(num(r[2]) for r in rows)
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        loaded = [s for s in sm if s == s and s > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(num(r[3]) for r in rows)}
+
+
+# ---- oracle (CPU baseline and reference arm) ------------------------------------------
+def oracle_particle_sample(cfg, n_sample, steps=1):
+    """Time the oracle's particle loop (gather, push, walk, deposit, charge)
+    over the first n_sample particles of the workload; returns seconds."""
+    from oracle import sim as osim
+    s = osim.Sim(cfg["xyz"], cfg["tets"], cfg["order"], cfg["q"], cfg["m"], cfg["weight"],
+                 cfg["B0"], cfg["rho_ion"], matrices=False)
+    s.set_particles(cfg["x"][:n_sample], cfg["v"][:n_sample], cfg["tet"][:n_sample])
+    from oracle import particles as opart
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        w = s.push_walk(cfg["dt"])
+        opart.measure_rho(s.topo, s.g, s.c, w["x"], w["tet"], s.qw)
+        times.append(time.perf_counter() - t0)
+        s.x, s.v, s.tet = w["x"], w["v"], w["tet"]
+    return times
+
+
+def run_reference(args, rank, world):
+    import workloads
+    if rank != 0:
+        return
+    cfg = workloads.make_config(1)
+    n_sample = args.ref_sample
+    times = oracle_particle_sample(cfg, n_sample, steps=args.warmup + args.steps)
+    timed = times[args.warmup:]
+    total = sum(timed)
+    value = n_sample * len(timed) / total
+    sample = (f"oracle particle loop (gather, push, walk, deposit, charge) over the first "
+              f"{n_sample} of the 1e6 particles per step; the oracle's direct field solve "
+              "is not run at this size")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(timed),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---- native arm -----------------------------------------------------------------------------
+def run_native(args, rank, world, local_rank):
+    import torch
+    import workloads
+    from paper_2111_12411_gb300 import Simulation
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    cfg = workloads.make_config(1, n_particles=args.particles)
+    sim = Simulation.from_config(cfg, precision=args.precision, device=local_rank,
+                                 stream=stream.cuda_stream, cg_rtol=args.cg_rtol)
+    info = sim.info
+    npart = sim.n_particles
+    dt = cfg["dt"]
+    occupied = len(np.unique(cfg["tet"]))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        sim.step(dt)
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    acc = {k: 0.0 for k in ("particle_ms", "field_ms", "launches", "sort_ms", "push_ms", "rhs_ms",
+                            "pcg_ms", "bupdate_ms", "cg_iterations")}
+    crossings = 0.0
+    with ClockSampler(local_rank) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            sim.step(dt)
+            ends[k].record(stream)
+            t = sim.last_timing()
+            for key in acc:
+                acc[key] += t[key]
+            crossings += sim.diag()["crossings"]
+        barrier()
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    K = args.steps
+    value = world * npart * K / (total_ms * 1e-3)
+    clocks = clk.summary()
+
+    # ---- rooflines (dominant kernel = the CG solve; the particle kernel beside it)
+    peak, peak_src = measured_peaks()
+    iters = acc["cg_iterations"] / K
+    pcg_bytes = pcg_bytes_per_iteration(info) * (iters + 1.0)
+    pcg_ms = acc["pcg_ms"] / K
+    pcg_gbs = pcg_bytes / (pcg_ms * 1e-3) / 1e9
+    cross_pp = crossings / (K * max(1, npart))
+    pbytes = particle_bytes_per_step(info.order, npart, occupied, cross_pp) * npart
+    push_ms = acc["push_ms"] / K
+    push_gbs = pbytes / (push_ms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("k_pcg_bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    dominant_is_pcg = acc["pcg_ms"] >= acc["push_ms"]
+    roof_pcg = {"kernel": "k_pcg (device PCG, one cooperative launch per step)", "bound": "hbm",
+                "achieved": pcg_gbs, "peak": peak, "unit": "GB/s", "frac": pcg_gbs / peak,
+                "traffic": traffic, "peak_source": peak_src + " of measured" if "measured" in peak_src else peak_src,
+                "bytes_per_launch": pcg_bytes, "cg_iterations_per_launch": iters,
+                "ms_per_launch": pcg_ms}
+    roof_part = {"kernel": "k_particle (gather, push, walk, deposit, charge)", "bound": "hbm",
+                 "achieved": push_gbs, "peak": peak, "unit": "GB/s", "frac": push_gbs / peak,
+                 "traffic": None, "bytes_per_launch": pbytes, "ms_per_launch": push_ms,
+                 "crossings_per_particle": cross_pp, "particles_per_occupied_tet": npart / occupied}
+
+    # ---- end to end through the C ABI with host buffers ---------------------------------
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty((npart, 3), dtype=torch.float64, pin_memory=True).numpy()
+        vh = torch.empty((npart, 3), dtype=torch.float64, pin_memory=True).numpy()
+        th = torch.empty(npart, dtype=torch.int32, pin_memory=True).numpy()
+        eh = torch.empty(info.n1, dtype=torch.float64, pin_memory=True).numpy()
+        xh[:] = sim.get("X")
+        vh[:] = sim.get("V")
+        th[:] = sim.get("TET")
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            sim.set("X", xh)
+            sim.set("V", vh)
+            sim.set("TET", th)
+            sim.step(dt)
+            xh[:] = sim.get("X")
+            vh[:] = sim.get("V")
+            th[:] = sim.get("TET")
+            eh[:] = sim.get("E")
+        barrier()
+        t_e2e = time.perf_counter() - t0
+        h2d = xh.nbytes + vh.nbytes + th.nbytes
+        d2h = h2d + eh.nbytes
+        e2e = {"value": world * npart * K / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h,
+               "note": "per step: particle state host->device, one full step, particle state "
+                       "and E DOFs device->host, through femPIC_set/step/get (pinned host memory)"}
+
+    result = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            n_s = args.cpu_sample
+            ts = oracle_particle_sample(cfg, n_s, steps=1)
+            cpu = {"value": n_s / ts[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"one particle-loop step (gather, push, walk, deposit, charge) of the "
+                             f"first {n_s} of the {npart} particles on the same mesh and seed; the "
+                             "oracle's direct field solve is not timed at this size"}
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision != "mixed" else "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.precision, "l2": "flushed between steps "
+                       "(256 MiB write)", "parallelism": "replicas" if world > 1 else "single GPU",
+                       "n_particles": npart, "n_tets": info.n_tets, "n1": info.n1, "n2": info.n2,
+                       "cg_rtol": args.cg_rtol},
+            "roofline": roof_pcg if dominant_is_pcg else roof_part,
+            "roofline_particle_kernel": roof_part,
+            "roofline_cg_kernel": roof_pcg,
+            "particle_loop": {"value": world * npart * K / ((acc["particle_ms"]) * 1e-3), "unit": UNIT,
+                              "ms_per_step": acc["particle_ms"] / K,
+                              "note": "sort + gather/push/walk/deposit/charge only"},
+            "field_update": {"ms_per_step": acc["field_ms"] / K, "cg_iterations_per_step": iters,
+                             "rhs_ms": acc["rhs_ms"] / K, "pcg_ms": pcg_ms,
+                             "bupdate_ms": acc["bupdate_ms"] / K},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(acc["launches"]),
+            "clocks": clocks,
+        }
+        print(json.dumps(result), flush=True)
+    sim.close()
+    return result
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--precision", default="fp64", choices=("fp64", "fp64_strict", "mixed"))
+    ap.add_argument("--particles", type=int, default=None)
+    ap.add_argument("--cg-rtol", type=float, default=1e-12)
+    ap.add_argument("--cpu-sample", type=int, default=250_000)
+    ap.add_argument("--ref-sample", type=int, default=50_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    from paper_2111_12411_gb300 import build
+    build.build()
+    run_native(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -168,7 +168,8 @@ typedef struct {
   int32_t n0, n1, n2;       /* global W0, W1, W2 DOF counts                     */
   int32_t nl0, nl1, nl2;    /* local DOFs per tet                               */
   int64_t n_particles;
-  int64_t nnz_A, nnz_C, nnz_Q;
+  int64_t nnz_A, nnz_C, nnz_Q;  /* stored entries of A, C, C^T [*mu^-1] */
+  int64_t nnz_D, nnz_DT;        /* stored entries of D and D^T          */
   int32_t n_boundary_faces;
   size_t device_bytes;      /* device memory held by the handle                */
 } femPIC_info;
@@ -219,10 +220,12 @@ int femPIC_eval_fields(FemPIC* h, int64_t n, const double* x_host, const int32_t
 
 int femPIC_get_info(const FemPIC* h, femPIC_info* info);
 
-/* Time (ms) of the device work of the last femPIC_step call split into the
- * particle loop (sort, gather, push, walk, deposit, charge) and the field
- * update (right-hand side, CG, b update), measured with CUDA events on the
- * handle's stream; times[2] = kernel launches in that call. */
+/* Device time of the work of the last femPIC_step / femPIC_sync, measured with
+ * CUDA events on the handle's stream, summed over its steps.  Fills up to n
+ * of: [0] particle loop ms (sort + gather/push/walk/deposit/charge),
+ * [1] field update ms (right-hand side + CG + b update), [2] kernel launches
+ * of the call, [3] sort ms, [4] particle kernel ms, [5] right-hand side ms,
+ * [6] CG ms, [7] b update ms, [8] CG iterations (sum over the steps). */
 int femPIC_last_timing(const FemPIC* h, double* times, int32_t n);
 
 void femPIC_destroy(FemPIC* h);

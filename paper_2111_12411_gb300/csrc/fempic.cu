@@ -90,6 +90,9 @@ struct FemPIC {
   // timing of the last femPIC_step call
   std::vector<cudaEvent_t> ev;
   double t_particle_ms = 0, t_field_ms = 0;
+  double t_sort_ms = 0, t_push_ms = 0, t_rhs_ms = 0, t_pcg_ms = 0, t_bupd_ms = 0;
+  int64_t cg_iters_sum = 0;
+  int32_t* d_cg_iters_acc = nullptr;  // sum of CG iterations since the last sync
   int launches = 0;
   int pending_steps = 0;
 };
@@ -381,7 +384,7 @@ int launch_particles(FemPIC* h, double dt) {
   return FEMPIC_OK;
 }
 
-int field_update(FemPIC* h, double dt) {
+int field_update(FemPIC* h, double dt, cudaEvent_t ev_pcg0, cudaEvent_t ev_pcg1) {
   bool trap = h->opts.scheme == FEMPIC_SCHEME_TRAPEZOID;
   // initial guess: linear extrapolation 2 e^n - e^{n-1}
   {
@@ -401,8 +404,12 @@ int field_update(FemPIC* h, double dt) {
                                           h->dg, h->dg_prev, trap ? 0.0 : 1.0, h->pec1, h->rhs);
   h->launches++;
   CK(cudaGetLastError());
+  CK(cudaEventRecord(ev_pcg0, h->stream));
   int rc = run_pcg(h, h->M.view(h->Aval), h->dinvA, h->rhs, h->e_new, h->pcg_blocks_w1, true);
   if (rc) return rc;
+  CK(cudaEventRecord(ev_pcg1, h->stream));
+  k_accumulate_iters<<<1, 1, 0, h->stream>>>(h->d_cg_iters, h->d_cg_iters_acc);
+  h->launches++;
   int gridc = grid_for((int64_t)h->n2 * 4, 256, h->num_sms * 16);
   k_bupdate<4><<<gridc, 256, 0, h->stream>>>(h->C.view(), h->e_new, h->e, 0.5 * dt, h->b);
   h->launches++;
@@ -451,13 +458,18 @@ int do_steps(FemPIC* h, double dt, int32_t n) {
     if (rc) return rc;
   }
   CK(cudaMemsetAsync(h->d_cross, 0, sizeof(unsigned long long), h->stream));
+  CK(cudaMemsetAsync(h->d_cg_iters_acc, 0, sizeof(int32_t), h->stream));
+  constexpr int kEv = 6;
   for (int32_t s = 0; s < n; ++s) {
-    cudaEvent_t e0 = event_at(h, 3 * s), e1 = event_at(h, 3 * s + 1), e2 = event_at(h, 3 * s + 2);
-    if (!e0 || !e1 || !e2) {
-      h->err = "cudaEventCreate failed";
-      return FEMPIC_ERR_CUDA;
+    cudaEvent_t e[kEv];
+    for (int k = 0; k < kEv; ++k) {
+      e[k] = event_at(h, (size_t)kEv * s + k);
+      if (!e[k]) {
+        h->err = "cudaEventCreate failed";
+        return FEMPIC_ERR_CUDA;
+      }
     }
-    CK(cudaEventRecord(e0, h->stream));
+    CK(cudaEventRecord(e[0], h->stream));
     if (h->opts.sort_period > 0 && h->since_sort >= h->opts.sort_period) {
       int rc = sort_particles(h);
       if (rc) return rc;
@@ -467,12 +479,13 @@ int do_steps(FemPIC* h, double dt, int32_t n) {
     std::swap(h->rho, h->rho_prev);
     CK(cudaMemsetAsync(h->dg, 0, sizeof(double) * h->n1, h->stream));
     CK(cudaMemsetAsync(h->rho, 0, sizeof(double) * h->n0, h->stream));
+    CK(cudaEventRecord(e[1], h->stream));
     int rc = launch_particles(h, dt);
     if (rc) return rc;
-    CK(cudaEventRecord(e1, h->stream));
-    rc = field_update(h, dt);
+    CK(cudaEventRecord(e[2], h->stream));
+    rc = field_update(h, dt, e[3], e[4]);
     if (rc) return rc;
-    CK(cudaEventRecord(e2, h->stream));
+    CK(cudaEventRecord(e[5], h->stream));
     // rotate e: e_prev <- e, e <- e_new
     double* old_prev = h->e_prev;
     h->e_prev = h->e;
@@ -491,13 +504,21 @@ int do_steps(FemPIC* h, double dt, int32_t n) {
 
 int collect_timing(FemPIC* h) {
   h->t_particle_ms = h->t_field_ms = 0.0;
+  h->t_sort_ms = h->t_push_ms = h->t_rhs_ms = h->t_pcg_ms = h->t_bupd_ms = 0.0;
   for (int s = 0; s < h->pending_steps; ++s) {
-    float a = 0.f, b = 0.f;
-    CK(cudaEventElapsedTime(&a, h->ev[3 * s], h->ev[3 * s + 1]));
-    CK(cudaEventElapsedTime(&b, h->ev[3 * s + 1], h->ev[3 * s + 2]));
-    h->t_particle_ms += a;
-    h->t_field_ms += b;
+    float t[5];
+    for (int k = 0; k < 5; ++k) CK(cudaEventElapsedTime(&t[k], h->ev[6 * s + k], h->ev[6 * s + k + 1]));
+    h->t_sort_ms += t[0];
+    h->t_push_ms += t[1];
+    h->t_rhs_ms += t[2];
+    h->t_pcg_ms += t[3];
+    h->t_bupd_ms += t[4];
+    h->t_particle_ms += t[0] + t[1];
+    h->t_field_ms += t[2] + t[3] + t[4];
   }
+  int32_t it = 0;
+  CK(cudaMemcpy(&it, h->d_cg_iters_acc, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  h->cg_iters_sum = it;
   h->pending_steps = 0;
   return FEMPIC_OK;
 }
@@ -772,6 +793,7 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
   }
   if ((rc = dalloc(h, &h->partials, 4 * (size_t)h->pcg_blocks_w1)) || (rc = dalloc(h, &h->bar, 1)) ||
       (rc = dalloc(h, &h->d_status, 1)) || (rc = dalloc(h, &h->d_cg_iters, 1)) || (rc = dalloc(h, &h->d_cg_res, 1)) ||
+      (rc = dalloc(h, &h->d_cg_iters_acc, 1)) ||
       (rc = dalloc(h, &h->d_norms, 4)) || (rc = dalloc(h, &h->d_cross, 1)))
     return rc;
   for (void* p : std::vector<void*>{h->e, h->e_prev, h->e_new, h->dg, h->dg_prev})
@@ -1034,6 +1056,8 @@ int femPIC_get_info(const FemPIC* h, femPIC_info* info) {
   info->nnz_A = h->M.nnz;
   info->nnz_C = h->C.nnz;
   info->nnz_Q = h->Q.nnz;
+  info->nnz_D = h->D.nnz;
+  info->nnz_DT = h->DT.nnz;
   info->n_boundary_faces = h->n_bfaces;
   info->device_bytes = h->bytes;
   return FEMPIC_OK;
@@ -1041,9 +1065,9 @@ int femPIC_get_info(const FemPIC* h, femPIC_info* info) {
 
 int femPIC_last_timing(const FemPIC* h, double* times, int32_t n) {
   if (!h || !times || n < 1) return FEMPIC_ERR_ARG;
-  if (n > 0) times[0] = h->t_particle_ms;
-  if (n > 1) times[1] = h->t_field_ms;
-  if (n > 2) times[2] = h->launches;
+  const double v[10] = {h->t_particle_ms, h->t_field_ms, (double)h->launches, h->t_sort_ms, h->t_push_ms,
+                        h->t_rhs_ms,      h->t_pcg_ms,   h->t_bupd_ms,         (double)h->cg_iters_sum, 0.0};
+  for (int32_t k = 0; k < n && k < 10; ++k) times[k] = v[k];
   return FEMPIC_OK;
 }
 

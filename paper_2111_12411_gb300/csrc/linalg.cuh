@@ -369,6 +369,8 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
   }
 }
 
+__global__ void k_accumulate_iters(const int32_t* it, int32_t* acc) { *acc += *it; }
+
 // ---- counting sort by tet -----------------------------------------------------
 __global__ void k_hist(int64_t n, const int32_t* __restrict__ tet, int32_t* __restrict__ cnt) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -61,6 +61,7 @@ class femPIC_info(ctypes.Structure):
                 ("n2", ctypes.c_int32), ("nl0", ctypes.c_int32), ("nl1", ctypes.c_int32),
                 ("nl2", ctypes.c_int32), ("n_particles", ctypes.c_int64),
                 ("nnz_A", ctypes.c_int64), ("nnz_C", ctypes.c_int64), ("nnz_Q", ctypes.c_int64),
+                ("nnz_D", ctypes.c_int64), ("nnz_DT", ctypes.c_int64),
                 ("n_boundary_faces", ctypes.c_int32), ("device_bytes", ctypes.c_size_t)]
 
 
@@ -200,10 +201,14 @@ def femPIC_get_info(h):
     return info
 
 
+TIMING_KEYS = ("particle_ms", "field_ms", "launches", "sort_ms", "push_ms", "rhs_ms", "pcg_ms",
+               "bupdate_ms", "cg_iterations")
+
+
 def femPIC_last_timing(h):
-    t = np.zeros(3)
-    _check(h, load().femPIC_last_timing(h, _ptr(t), 3))
-    return t
+    t = np.zeros(len(TIMING_KEYS))
+    _check(h, load().femPIC_last_timing(h, _ptr(t), len(t)))
+    return dict(zip(TIMING_KEYS, t.tolist()))
 
 
 def femPIC_destroy(h):
