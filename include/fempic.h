@@ -218,6 +218,30 @@ int femPIC_apply(FemPIC* h, int32_t op, const double* x_host, size_t nx,
 int femPIC_eval_fields(FemPIC* h, int64_t n, const double* x_host, const int32_t* tet_host,
                        double* E_host, double* B_host);
 
+/* Field probe that makes no device allocation.  The paper has no counterpart;
+ * this is a library service for callers that must not allocate device memory
+ * while they run: a serving loop that has handed its whole HBM budget to
+ * simulation instances, or a latency-critical host loop that cannot afford the
+ * device-wide synchronisation that cudaMalloc/cudaFree bring with them.
+ *
+ * Same inputs, outputs and result as femPIC_eval_fields (the same kernel runs),
+ * but the points, tet ids and results are staged in one fixed device array
+ * that lives in the library for as long as it is loaded (on every device that
+ * uses it), instead of buffers allocated per call.  Limits and rules:
+ *   - at most FEMPIC_PROBE_MAX_POINTS points per call; larger n returns
+ *     FEMPIC_ERR_SIZE and touches nothing;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture starts;
+ *   - all calls share the array and it keeps the last call's contents; every
+ *     output value is rewritten by each call, so nothing needs clearing.
+ *     Calls that overlap on the GPU (from several host threads or handles at
+ *     once) race on the array: serialise them per device.
+ *   - returns after the results are in E_host and B_host. */
+#define FEMPIC_PROBE_MAX_POINTS 65536
+int femPIC_eval_fields_noalloc(FemPIC* h, int64_t n, const double* x_host, const int32_t* tet_host,
+                               double* E_host, double* B_host);
+
 int femPIC_get_info(const FemPIC* h, femPIC_info* info);
 
 /* Device time of the work of the last femPIC_step / femPIC_sync, measured with

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1035,6 +1036,91 @@ int femPIC_eval_fields(FemPIC* h, int64_t n, const double* x_host, const int32_t
   cudaFree(dE);
   cudaFree(dB);
   cudaFree(dt);
+  return FEMPIC_OK;
+}
+
+}  // extern "C"
+
+// ---- field probe without device allocation ------------------------------------------
+// One fixed staging array per loaded library (and per device that uses it):
+// x [3n] doubles, E [3n], B [3n], then tet [n] int32.  Its device address is
+// looked up once per device, with that device current.
+namespace {
+constexpr size_t kProbeBytes = (size_t)FEMPIC_PROBE_MAX_POINTS * (9 * sizeof(double) + sizeof(int32_t));
+static __device__ __align__(256) unsigned char g_probe_scratch[kProbeBytes];
+
+constexpr int kProbeMaxDevices = 64;
+std::mutex g_probe_mutex;
+void* g_probe_ptr[kProbeMaxDevices] = {};
+
+// device address of g_probe_scratch on the current device (nullptr on error)
+void* probe_scratch(int device, std::string* err) {
+  if (device < 0 || device >= kProbeMaxDevices) {
+    *err = "device ordinal out of range for the probe scratch table";
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(g_probe_mutex);
+  if (!g_probe_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_probe_scratch);
+    if (e != cudaSuccess || !p) {
+      *err = std::string("cudaGetSymbolAddress(probe scratch): ") + cudaGetErrorString(e);
+      return nullptr;
+    }
+    g_probe_ptr[device] = p;
+  }
+  return g_probe_ptr[device];
+}
+}  // namespace
+
+extern "C" {
+
+int femPIC_eval_fields_noalloc(FemPIC* h, int64_t n, const double* x_host, const int32_t* tet_host, double* E_host,
+                               double* B_host) {
+  if (!h || !h->stream || n < 0 || (n > 0 && (!x_host || !tet_host || !E_host || !B_host))) return FEMPIC_ERR_ARG;
+  if (n > FEMPIC_PROBE_MAX_POINTS) {
+    h->err = "femPIC_eval_fields_noalloc: " + std::to_string(n) + " points exceed FEMPIC_PROBE_MAX_POINTS (" +
+             std::to_string(FEMPIC_PROBE_MAX_POINTS) + ")";
+    return FEMPIC_ERR_SIZE;
+  }
+  if (n == 0) return FEMPIC_OK;
+  for (int64_t i = 0; i < n; ++i)
+    if (tet_host[i] < 0 || tet_host[i] >= h->n_tets) {
+      h->err = "tet id out of range";
+      return FEMPIC_ERR_ARG;
+    }
+  CK(cudaSetDevice(h->device));
+  void* base = probe_scratch(h->device, &h->err);
+  if (!base) return FEMPIC_ERR_CUDA;
+  const size_t cap = FEMPIC_PROBE_MAX_POINTS;
+  double* dx = static_cast<double*>(base);
+  double* dE = dx + 3 * cap;
+  double* dB = dE + 3 * cap;
+  int32_t* dt = reinterpret_cast<int32_t*>(dB + 3 * cap);
+  CK(cudaMemcpyAsync(dx, x_host, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(dt, tet_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
+  int grid = grid_for(n, 128, 1 << 30);
+  bool strict = h->opts.precision == FEMPIC_FP64_STRICT;
+  const double* B0 = h->opts.B0;
+  if (h->order == 1) {
+    if (strict)
+      k_eval_fields<1, Strict><<<grid, 128, 0, h->stream>>>(n, dx, dt, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
+                                                            B0[1], B0[2], dE, dB);
+    else
+      k_eval_fields<1, Fast><<<grid, 128, 0, h->stream>>>(n, dx, dt, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
+                                                          B0[1], B0[2], dE, dB);
+  } else {
+    if (strict)
+      k_eval_fields<2, Strict><<<grid, 128, 0, h->stream>>>(n, dx, dt, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
+                                                            B0[1], B0[2], dE, dB);
+    else
+      k_eval_fields<2, Fast><<<grid, 128, 0, h->stream>>>(n, dx, dt, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
+                                                          B0[1], B0[2], dE, dB);
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(E_host, dE, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(B_host, dB, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
   return FEMPIC_OK;
 }
 

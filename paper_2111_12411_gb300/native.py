@@ -81,6 +81,7 @@ EXPORTS = [
     ("femPIC_set_device", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t]),
     ("femPIC_apply", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t, _P, ctypes.c_size_t]),
     ("femPIC_eval_fields", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P]),
+    ("femPIC_eval_fields_noalloc", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P]),
     ("femPIC_get_info", ctypes.c_int, [_P, ctypes.POINTER(femPIC_info)]),
     ("femPIC_last_timing", ctypes.c_int, [_P, _P, ctypes.c_int32]),
     ("femPIC_destroy", None, [_P]),
@@ -192,6 +193,21 @@ def femPIC_eval_fields(h, x, tet):
     E = np.empty_like(x)
     B = np.empty_like(x)
     _check(h, load().femPIC_eval_fields(h, len(x), _ptr(x), _ptr(tet), _ptr(E), _ptr(B)))
+    return E, B
+
+
+FEMPIC_PROBE_MAX_POINTS = 65536
+
+
+def femPIC_eval_fields_noalloc(h, x, tet):
+    """E and B at points, like femPIC_eval_fields, staged in the library's fixed
+    device array instead of per-call allocations (at most
+    FEMPIC_PROBE_MAX_POINTS points; calls that overlap on the GPU race)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    tet = np.ascontiguousarray(tet, dtype=np.int32)
+    E = np.empty_like(x)
+    B = np.empty_like(x)
+    _check(h, load().femPIC_eval_fields_noalloc(h, len(x), _ptr(x), _ptr(tet), _ptr(E), _ptr(B)))
     return E, B
 
 
