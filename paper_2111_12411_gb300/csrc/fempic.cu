@@ -21,6 +21,7 @@
 #include "internal.h"
 #include "kernels.cuh"
 #include "linalg.cuh"
+#include "particle_fast.cuh"
 
 using namespace fempic;
 using namespace fempic::dev;
@@ -369,16 +370,21 @@ int launch_particles(FemPIC* h, double dt) {
   if (h->np == 0) return FEMPIC_OK;
   int grid = grid_for(h->np, 256, 1 << 30);
   bool strict = h->opts.precision == FEMPIC_FP64_STRICT;
+  const bool agg = h->opts.sort_period == 1;  // lanes share tets only right after a sort
   if (h->order == 1) {
     if (strict)
       k_particle<1, Strict><<<grid, 256, 0, h->stream>>>(a);
+    else if (agg)
+      k_particle_fast<1, true><<<grid, 256, 0, h->stream>>>(a);
     else
-      k_particle<1, Fast><<<grid, 256, 0, h->stream>>>(a);
+      k_particle_fast<1, false><<<grid, 256, 0, h->stream>>>(a);
   } else {
     if (strict)
       k_particle<2, Strict><<<grid, 256, 0, h->stream>>>(a);
+    else if (agg)
+      k_particle_fast<2, true><<<grid, 256, 0, h->stream>>>(a);
     else
-      k_particle<2, Fast><<<grid, 256, 0, h->stream>>>(a);
+      k_particle_fast<2, false><<<grid, 256, 0, h->stream>>>(a);
   }
   h->launches++;
   CK(cudaGetLastError());

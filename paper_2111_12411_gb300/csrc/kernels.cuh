@@ -38,22 +38,33 @@ struct Fast {
   static __device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
 };
 
-__device__ __constant__ int c_edges[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
-__device__ __constant__ int c_faces[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
-
-// W1 of order p: function j = m(l) * (l_a grad l_b - l_b grad l_a);
-// w1spec[j] = {a, b, x, kind} with kind 0: m = 1, 1: m = 3 l_x - 1, 2: m = 3 l_x.
-__device__ __constant__ int c_w1spec2[20][4] = {
-    {0, 1, 0, 1}, {0, 1, 1, 1}, {0, 2, 0, 1}, {0, 2, 2, 1}, {0, 3, 0, 1}, {0, 3, 3, 1},
-    {1, 2, 1, 1}, {1, 2, 2, 1}, {1, 3, 1, 1}, {1, 3, 3, 1}, {2, 3, 2, 1}, {2, 3, 3, 1},
-    {1, 2, 3, 2}, {1, 3, 2, 2},  // face 0 = (1,2,3): 3 l_3 w_12, 3 l_2 w_13
-    {0, 2, 3, 2}, {0, 3, 2, 2},  // face 1 = (0,2,3)
-    {0, 1, 3, 2}, {0, 3, 1, 2},  // face 2 = (0,1,3)
-    {0, 1, 2, 2}, {0, 2, 1, 2}}; // face 3 = (0,1,2)
-// W2 of order 2: function j = m(l) * w_face; {face, x, kind} kind 1: 4 l_x - 1, 2: 4 l_x.
-__device__ __constant__ int c_w2spec2[15][3] = {
-    {0, 1, 1}, {0, 2, 1}, {0, 3, 1}, {1, 0, 1}, {1, 2, 1}, {1, 3, 1}, {2, 0, 1}, {2, 1, 1},
-    {2, 3, 1}, {3, 0, 1}, {3, 1, 1}, {3, 2, 1}, {0, 0, 2}, {1, 1, 2}, {2, 2, 2}};
+// ---- compile-time tables (constexpr functions fold to immediates after unrolling)
+// local edge j = (edge_s(j), edge_t(j)); local face f = (face_v(f,0..2)), opposite vertex f
+__host__ __device__ constexpr int edge_s(int j) { constexpr int t[6] = {0, 0, 0, 1, 1, 2}; return t[j]; }
+__host__ __device__ constexpr int edge_t(int j) { constexpr int t[6] = {1, 2, 3, 2, 3, 3}; return t[j]; }
+__host__ __device__ constexpr int face_v(int f, int k) {
+  constexpr int t[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+  return t[f][k];
+}
+// index of the local edge (a,b), a < b
+__host__ __device__ constexpr int pair_of(int a, int b) {
+  return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
+}
+// W1 of order 2: function j = m(l) (l_a grad l_b - l_b grad l_a), {a, b, x, kind}
+// kind 1: m = 3 l_x - 1 (edge functions), kind 2: m = 3 l_x (face functions)
+__host__ __device__ constexpr int w1q(int j, int c) {
+  constexpr int t[20][4] = {{0, 1, 0, 1}, {0, 1, 1, 1}, {0, 2, 0, 1}, {0, 2, 2, 1}, {0, 3, 0, 1},
+                            {0, 3, 3, 1}, {1, 2, 1, 1}, {1, 2, 2, 1}, {1, 3, 1, 1}, {1, 3, 3, 1},
+                            {2, 3, 2, 1}, {2, 3, 3, 1}, {1, 2, 3, 2}, {1, 3, 2, 2}, {0, 2, 3, 2},
+                            {0, 3, 2, 2}, {0, 1, 3, 2}, {0, 3, 1, 2}, {0, 1, 2, 2}, {0, 2, 1, 2}};
+  return t[j][c];
+}
+// W2 of order 2: function j = m(l) w_face, {face, x, kind}; kind 1: 4 l_x - 1, 2: 4 l_x
+__host__ __device__ constexpr int w2q(int j, int c) {
+  constexpr int t[15][3] = {{0, 1, 1}, {0, 2, 1}, {0, 3, 1}, {1, 0, 1}, {1, 2, 1}, {1, 3, 1}, {2, 0, 1}, {2, 1, 1},
+                            {2, 3, 1}, {3, 0, 1}, {3, 1, 1}, {3, 2, 1}, {0, 0, 2}, {1, 1, 2}, {2, 2, 2}};
+  return t[j][c];
+}
 
 template <class Ar>
 __device__ __forceinline__ void cross3(const double* a, const double* b, double* o) {
@@ -102,13 +113,13 @@ __device__ __forceinline__ void gather_E(const TetGeom& G, const double* l, cons
   for (int j = 0; j < N; ++j) {
     int a, b, x = 0, kind = 0;
     if (P == 1) {
-      a = c_edges[j][0];
-      b = c_edges[j][1];
+      a = edge_s(j);
+      b = edge_t(j);
     } else {
-      a = c_w1spec2[j][0];
-      b = c_w1spec2[j][1];
-      x = c_w1spec2[j][2];
-      kind = c_w1spec2[j][3];
+      a = w1q(j, 0);
+      b = w1q(j, 1);
+      x = w1q(j, 2);
+      kind = w1q(j, 3);
     }
     double w[3];
 #pragma unroll
@@ -126,7 +137,7 @@ __device__ __forceinline__ void gather_E(const TetGeom& G, const double* l, cons
 // Whitney face function of local face f: 2 ((l_s X_tu + l_t X_us) + l_u X_st)
 template <class Ar>
 __device__ __forceinline__ void whitney_face(const TetGeom& G, const double* l, int f, double* w) {
-  int s = c_faces[f][0], t = c_faces[f][1], u = c_faces[f][2];
+  const int s = face_v(f, 0), t = face_v(f, 1), u = face_v(f, 2);
   double xtu[3], xus[3], xst[3];
   cross3<Ar>(G.g[t], G.g[u], xtu);
   cross3<Ar>(G.g[u], G.g[s], xus);
@@ -154,7 +165,7 @@ __device__ __forceinline__ void gather_B(const TetGeom& G, const double* l, cons
     for (int f = 0; f < 4; ++f) whitney_face<Ar>(G, l, f, wf[f]);
 #pragma unroll
     for (int j = 0; j < 15; ++j) {
-      int f = c_w2spec2[j][0], x = c_w2spec2[j][1], kind = c_w2spec2[j][2];
+      const int f = w2q(j, 0), x = w2q(j, 1), kind = w2q(j, 2);
       double m = kind == 1 ? Ar::sub(Ar::mul(4.0, l[x]), 1.0) : Ar::mul(4.0, l[x]);
 #pragma unroll
       for (int k = 0; k < 3; ++k) acc[k] = Ar::add(acc[k], Ar::mul(bv[j], Ar::mul(m, wf[f][k])));
@@ -202,7 +213,7 @@ __device__ __forceinline__ void deposit_segment(const double* la, const double* 
     }
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-      int s = c_edges[j][0], t = c_edges[j][1];
+      const int s = edge_s(j), t = edge_t(j);
       double val = Ar::sub(Ar::mul(Pv[s], Qv[t]), Ar::mul(Pv[t], Qv[s]));
       atomicAdd(dg + __ldg(dofs + j), Ar::mul(qw, val));
     }
@@ -218,7 +229,7 @@ __device__ __forceinline__ void deposit_segment(const double* la, const double* 
       for (int i = 0; i < 4; ++i) L[q][i] = Ar::add(la[i], Ar::mul(sg[q], d[i]));
 #pragma unroll
     for (int j = 0; j < 20; ++j) {
-      int a = c_w1spec2[j][0], b = c_w1spec2[j][1], x = c_w1spec2[j][2], kind = c_w1spec2[j][3];
+      const int a = w1q(j, 0), b = w1q(j, 1), x = w1q(j, 2), kind = w1q(j, 3);
       double f[2];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
@@ -242,7 +253,7 @@ __device__ __forceinline__ void deposit_rho(const double* l, double qw, const in
       atomicAdd(rho + __ldg(dofs + k), Ar::mul(qw, Ar::mul(l[k], Ar::sub(Ar::mul(2.0, l[k]), 1.0))));
 #pragma unroll
     for (int j = 0; j < 6; ++j)
-      atomicAdd(rho + __ldg(dofs + 4 + j), Ar::mul(qw, Ar::mul(Ar::mul(4.0, l[c_edges[j][0]]), l[c_edges[j][1]])));
+      atomicAdd(rho + __ldg(dofs + 4 + j), Ar::mul(qw, Ar::mul(Ar::mul(4.0, l[edge_s(j)]), l[edge_t(j)])));
   }
 }
 
@@ -338,7 +349,14 @@ __global__ void __launch_bounds__(256) k_particle(ParticleArgs a) {
         s0 = s1;
         load_geom(a.geom, T, G);
       } else {
-        const double* gw = G.g[best];
+        double gw[3];
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+          if (f == best) {
+            gw[0] = G.g[f][0];
+            gw[1] = G.g[f][1];
+            gw[2] = G.g[f][2];
+          }
         double d[3], hit[3], dr[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) d[k] = Ar::sub(pb[k], pa[k]);

@@ -1,0 +1,330 @@
+// FP64 particle kernel with fused multiply-adds and factored basis sums.
+//
+// Same method as k_particle (gather, Boris push, ray-face walk, path-integral
+// deposit, charge), rearranged to cut work:
+//   * E = sum_j e_j m_j(l) w_ab = sum_k alpha_k grad l_k, where the DOF sums
+//     are first collected per local edge pair (c_ab), then
+//     alpha_b += c_ab l_a, alpha_a -= c_ab l_b;
+//   * B = B0 + sum_f beta_f w_f = B0 + sum_{a<b} gamma_ab grad l_a x grad l_b;
+//   * the deposit evaluates w_ab . (b - a) = l_a d_b - l_b d_a once per pair and
+//     Gauss point and scales it by each DOF's multiplier;
+//   * the first sub-segment of every particle lies in its own (sorted) tet: its
+//     current is summed across the warp's lanes that share the tet before the
+//     atomic add, and so is the charge of particles that end in the same tet.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace fempic {
+namespace dev {
+
+struct WarpRuns {
+  int lo, hi;   // first/last lane of this lane's run of equal keys
+  bool ok;      // every run in the warp is contiguous
+};
+
+__device__ __forceinline__ WarpRuns warp_runs(int key) {
+  unsigned m = __match_any_sync(0xffffffffu, key);
+  int lo = __ffs(m) - 1;
+  int hi = 31 - __clz(m);
+  unsigned want = (hi == 31 ? 0xffffffffu : ((1u << (hi + 1)) - 1u)) & ~((1u << lo) - 1u);
+  bool ok = __all_sync(0xffffffffu, m == want);
+  return WarpRuns{lo, hi, ok};
+}
+
+// inclusive segmented sum; the run total ends in lane hi
+__device__ __forceinline__ double run_sum(double v, const WarpRuns& r, int lane) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    double t = __shfl_up_sync(0xffffffffu, v, off);
+    if (lane - off >= r.lo) v += t;
+  }
+  return v;
+}
+
+// add v into dst: summed over the run first when `agg` (all lanes participate)
+__device__ __forceinline__ void run_add(double* dst, double v, bool agg, const WarpRuns& r, int lane, bool valid) {
+  if (agg) {
+    v = run_sum(v, r, lane);
+    if (valid && lane == r.hi) atomicAdd(dst, v);
+  } else if (valid) {
+    atomicAdd(dst, v);
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void gather_E_fact(const TetGeom& G, const double* l, const double* __restrict__ e,
+                                              const int32_t* __restrict__ d1, double* E) {
+  double c[6];
+  if (P == 1) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) c[j] = __ldg(e + __ldg(d1 + j));
+  } else {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const int s = edge_s(j), t = edge_t(j);
+      double e0 = __ldg(e + __ldg(d1 + 2 * j)), e1 = __ldg(e + __ldg(d1 + 2 * j + 1));
+      c[j] = fma(e0, fma(3.0, l[s], -1.0), e1 * fma(3.0, l[t], -1.0));
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const int s = face_v(f, 0), t = face_v(f, 1), u = face_v(f, 2);
+      double e0 = __ldg(e + __ldg(d1 + 12 + 2 * f)), e1 = __ldg(e + __ldg(d1 + 13 + 2 * f));
+      c[pair_of(s, t)] = fma(e0, 3.0 * l[u], c[pair_of(s, t)]);
+      c[pair_of(s, u)] = fma(e1, 3.0 * l[t], c[pair_of(s, u)]);
+    }
+  }
+  double al[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const int s = edge_s(j), t = edge_t(j);
+    al[t] = fma(c[j], l[s], al[t]);
+    al[s] = fma(-c[j], l[t], al[s]);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    E[k] = fma(al[0], G.g[0][k], fma(al[1], G.g[1][k], fma(al[2], G.g[2][k], al[3] * G.g[3][k])));
+}
+
+template <int P>
+__device__ __forceinline__ void gather_B_fact(const TetGeom& G, const double* l, const double* __restrict__ b,
+                                              const int32_t* __restrict__ d2, const double* B0, double* B) {
+  double beta[4];
+  if (P == 1) {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) beta[f] = __ldg(b + __ldg(d2 + f));
+  } else {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      double s = 0.0;
+#pragma unroll
+      for (int v = 0; v < 3; ++v) s = fma(__ldg(b + __ldg(d2 + 3 * f + v)), fma(4.0, l[face_v(f, v)], -1.0), s);
+      if (f < 3) s = fma(__ldg(b + __ldg(d2 + 12 + f)), 4.0 * l[f], s);
+      beta[f] = s;
+    }
+  }
+  // w_f = 2 (l_s X_tu - l_t X_su + l_u X_st)
+  double gam[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const int s = face_v(f, 0), t = face_v(f, 1), u = face_v(f, 2);
+    double b2 = 2.0 * beta[f];
+    gam[pair_of(t, u)] = fma(b2, l[s], gam[pair_of(t, u)]);
+    gam[pair_of(s, u)] = fma(-b2, l[t], gam[pair_of(s, u)]);
+    gam[pair_of(s, t)] = fma(b2, l[u], gam[pair_of(s, t)]);
+  }
+  B[0] = B0[0];
+  B[1] = B0[1];
+  B[2] = B0[2];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const double* ga = G.g[edge_s(j)];
+    const double* gb = G.g[edge_t(j)];
+    B[0] = fma(gam[j], ga[1] * gb[2] - ga[2] * gb[1], B[0]);
+    B[1] = fma(gam[j], ga[2] * gb[0] - ga[0] * gb[2], B[1]);
+    B[2] = fma(gam[j], ga[0] * gb[1] - ga[1] * gb[0], B[2]);
+  }
+}
+
+// current of the sub-segment [s0, s1] of the chord in one tet
+template <int P>
+__device__ __forceinline__ void deposit_fact(const double* la, const double* lb, double s0, double s1, double qw,
+                                             const int32_t* __restrict__ dofs, double* __restrict__ dg, bool agg,
+                                             const WarpRuns& runs, int lane, bool valid) {
+  double d[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) d[i] = lb[i] - la[i];
+  if (P == 1) {
+    double Pv[4], Qv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      Pv[i] = fma(s0, d[i], la[i]);
+      Qv[i] = fma(s1, d[i], la[i]);
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const int s = edge_s(j), t = edge_t(j);
+      double val = qw * fma(Pv[s], Qv[t], -Pv[t] * Qv[s]);
+      run_add(dg + __ldg(dofs + j), val, agg, runs, lane, valid);
+    }
+  } else {
+    const double half = (s1 - s0) * 0.5;
+    const double mid = (s0 + s1) * 0.5;
+    const double r = half * kGL2X;
+    double LA[4], LB[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      LA[i] = fma(mid - r, d[i], la[i]);
+      LB[i] = fma(mid + r, d[i], la[i]);
+    }
+    double wA[6], wB[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const int s = edge_s(j), t = edge_t(j);
+      wA[j] = fma(LA[s], d[t], -LA[t] * d[s]);
+      wB[j] = fma(LB[s], d[t], -LB[t] * d[s]);
+    }
+    const double sc = qw * half;
+#pragma unroll
+    for (int j = 0; j < 20; ++j) {
+      const int a = w1q(j, 0), b = w1q(j, 1), x = w1q(j, 2), kind = w1q(j, 3);
+      const int pr = pair_of(a, b);
+      double mA = kind == 1 ? fma(3.0, LA[x], -1.0) : 3.0 * LA[x];
+      double mB = kind == 1 ? fma(3.0, LB[x], -1.0) : 3.0 * LB[x];
+      double val = sc * fma(mA, wA[pr], mB * wB[pr]);
+      run_add(dg + __ldg(dofs + j), val, agg, runs, lane, valid);
+    }
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void deposit_rho_fact(const double* l, double qw, const int32_t* __restrict__ dofs,
+                                                 double* __restrict__ rho, bool agg, const WarpRuns& runs, int lane,
+                                                 bool valid) {
+  if (P == 1) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) run_add(rho + __ldg(dofs + k), qw * l[k], agg, runs, lane, valid);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) run_add(rho + __ldg(dofs + k), qw * l[k] * fma(2.0, l[k], -1.0), agg, runs, lane, valid);
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+      run_add(rho + __ldg(dofs + 4 + j), qw * 4.0 * l[edge_s(j)] * l[edge_t(j)], agg, runs, lane, valid);
+  }
+}
+
+// exit face of the chord in the current tet (entry face excluded); -1 if it ends here
+__device__ __forceinline__ int exit_face(const double* la, const double* lb, int entry, double s0, double& s1) {
+  int best = -1;
+  double sbest = __longlong_as_double(0x7ff0000000000000ll);
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    if (f != entry && lb[f] < 0.0) {
+      double si = la[f] / (la[f] - lb[f]);
+      if (si < sbest) {
+        sbest = si;
+        best = f;
+      }
+    }
+  }
+  s1 = best < 0 ? 1.0 : fmin(fmax(sbest, s0), 1.0);
+  return best;
+}
+
+__device__ __forceinline__ void bary_fma(const TetGeom& G, const double* x, double* l) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) l[i] = fma(G.g[i][0], x[0], fma(G.g[i][1], x[1], fma(G.g[i][2], x[2], G.c[i])));
+}
+
+template <int P, bool AGG>
+__global__ void __launch_bounds__(256, 2) k_particle_fast(ParticleArgs a) {
+  constexpr int N1 = P == 1 ? 6 : 20;
+  constexpr int N2 = P == 1 ? 4 : 15;
+  constexpr int N0 = P == 1 ? 4 : 10;
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < a.n;
+  int T = valid ? a.tet[i] : 0;
+  double x[3], v[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    x[k] = valid ? a.x[k][i] : 0.0;
+    v[k] = valid ? a.v[k][i] : 0.0;
+  }
+  TetGeom G;
+  load_geom(a.geom, T, G);
+  double la[4];
+  bary_fma(G, x, la);
+  double E[3], B[3];
+  gather_E_fact<P>(G, la, a.e, a.dof1 + (size_t)T * N1, E);
+  gather_B_fact<P>(G, la, a.b, a.dof2 + (size_t)T * N2, a.B0, B);
+  boris<Fast>(v, E, B, a.h);
+  double pa[3] = {x[0], x[1], x[2]};
+  double pb[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) pb[k] = fma(a.dt, v[k], x[k]);
+  // ---- first visit: every lane, current summed over lanes sharing the tet
+  double lb[4];
+  bary_fma(G, pb, lb);
+  double s1;
+  int best = exit_face(la, lb, -1, 0.0, s1);
+  {
+    WarpRuns runs = warp_runs(valid ? T : -1 - lane);
+    deposit_fact<P>(la, lb, 0.0, s1, a.qw, a.dof1 + (size_t)T * N1, a.dg, AGG && runs.ok, runs, lane, valid);
+  }
+  int nc = 0;
+  unsigned long long hsh = kFnvOffset;
+  int entry = -1;
+  double s0 = 0.0;
+  bool walking = valid && best >= 0;
+  while (walking) {
+    ++nc;
+    int nb = __ldg(a.nbr + (size_t)T * 4 + best);
+    unsigned long long code = nb < 0 ? (0x80000000ull | (unsigned)best) : (unsigned long long)(nb >> 2);
+    hsh = (hsh ^ code) * kFnvPrime;
+    if (nb >= 0) {
+      entry = nb & 3;
+      T = nb >> 2;
+      s0 = s1;
+      load_geom(a.geom, T, G);
+    } else {
+      double gw[3];
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        if (f == best) {
+          gw[0] = G.g[f][0];
+          gw[1] = G.g[f][1];
+          gw[2] = G.g[f][2];
+        }
+      double d[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) d[k] = pb[k] - pa[k];
+      double gg = gw[0] * gw[0] + gw[1] * gw[1] + gw[2] * gw[2];
+      double fd = 2.0 * (d[0] * gw[0] + d[1] * gw[1] + d[2] * gw[2]) / gg;
+      double fv = 2.0 * (v[0] * gw[0] + v[1] * gw[1] + v[2] * gw[2]) / gg;
+      double rem = 1.0 - s1;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        double hit = fma(s1, d[k], pa[k]);
+        pb[k] = fma(rem, d[k] - fd * gw[k], hit);
+        pa[k] = hit;
+        v[k] -= fv * gw[k];
+      }
+      s0 = 0.0;
+      entry = best;
+    }
+    if (nc >= a.max_cross) {
+      bary_fma(G, pb, lb);
+      atomicOr(a.status, kStatusWalk);
+      break;
+    }
+    bary_fma(G, pa, la);
+    bary_fma(G, pb, lb);
+    best = exit_face(la, lb, entry, s0, s1);
+    WarpRuns none{0, 0, false};
+    deposit_fact<P>(la, lb, s0, s1, a.qw, a.dof1 + (size_t)T * N1, a.dg, false, none, lane, true);
+    walking = best >= 0;
+  }
+  // ---- charge at the end point, summed over lanes ending in the same tet
+  {
+    WarpRuns runs = warp_runs(valid ? T : -1 - lane);
+    deposit_rho_fact<P>(lb, a.qw, a.dof0 + (size_t)T * N0, a.rho, AGG && runs.ok, runs, lane, valid);
+  }
+  if (valid) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      a.x[k][i] = pb[k];
+      a.v[k][i] = v[k];
+    }
+    a.tet[i] = T;
+    if (a.ncross) a.ncross[i] = nc;
+    if (a.hash) a.hash[i] = hsh;
+  }
+  unsigned long long my_cross = nc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_cross += __shfl_xor_sync(0xffffffffu, my_cross, o);
+  if (lane == 0 && my_cross) atomicAdd(a.crossings, my_cross);
+}
+
+}  // namespace dev
+}  // namespace fempic
