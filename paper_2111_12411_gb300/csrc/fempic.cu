@@ -67,6 +67,7 @@ struct FemPIC {
   double *rho = nullptr, *rho_prev = nullptr, *phi = nullptr, *rhs = nullptr;
   // CG scratch
   double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *partials = nullptr;
+  double *cg_r2 = nullptr, *cg_p2 = nullptr;
   GridBarrier* bar = nullptr;
   int pcg_blocks_w1 = 0, pcg_blocks_w0 = 0;
   // particles (device order), SoA
@@ -208,11 +209,14 @@ int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, 
   a.t = h->d_tmp0;
   a.rhs = rhs;
   a.x = x;
-  a.r = h->cg_r;
+  a.r[0] = h->cg_r;
+  a.r[1] = h->cg_r2;
   a.z = h->cg_z;
-  a.p = h->cg_p;
+  a.p[0] = h->cg_p;
+  a.p[1] = h->cg_p2;
   a.q = h->cg_q;
-  a.partials = h->partials;
+  a.partials[0] = h->partials;
+  a.partials[1] = h->partials + 4 * (size_t)blocks;
   a.bar = h->bar;
   a.status = h->d_status;
   a.iters_out = h->d_cg_iters;
@@ -371,20 +375,25 @@ int launch_particles(FemPIC* h, double dt) {
   int grid = grid_for(h->np, 256, 1 << 30);
   bool strict = h->opts.precision == FEMPIC_FP64_STRICT;
   const bool agg = h->opts.sort_period == 1;  // lanes share tets only right after a sort
+  const bool mixed = h->opts.precision == FEMPIC_MIXED;
   if (h->order == 1) {
     if (strict)
       k_particle<1, Strict><<<grid, 256, 0, h->stream>>>(a);
-    else if (agg)
-      k_particle_fast<1, true><<<grid, 256, 0, h->stream>>>(a);
+    else if (mixed)
+      agg ? k_particle_fast<1, true, true><<<grid, 256, 0, h->stream>>>(a)
+          : k_particle_fast<1, false, true><<<grid, 256, 0, h->stream>>>(a);
     else
-      k_particle_fast<1, false><<<grid, 256, 0, h->stream>>>(a);
+      agg ? k_particle_fast<1, true, false><<<grid, 256, 0, h->stream>>>(a)
+          : k_particle_fast<1, false, false><<<grid, 256, 0, h->stream>>>(a);
   } else {
     if (strict)
       k_particle<2, Strict><<<grid, 256, 0, h->stream>>>(a);
-    else if (agg)
-      k_particle_fast<2, true><<<grid, 256, 0, h->stream>>>(a);
+    else if (mixed)
+      agg ? k_particle_fast<2, true, true><<<grid, 256, 0, h->stream>>>(a)
+          : k_particle_fast<2, false, true><<<grid, 256, 0, h->stream>>>(a);
     else
-      k_particle_fast<2, false><<<grid, 256, 0, h->stream>>>(a);
+      agg ? k_particle_fast<2, true, false><<<grid, 256, 0, h->stream>>>(a)
+          : k_particle_fast<2, false, false><<<grid, 256, 0, h->stream>>>(a);
   }
   h->launches++;
   CK(cudaGetLastError());
@@ -786,7 +795,7 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
   if ((rc = dalloc(h, &h->b, h->n2))) return rc;
   int32_t nmax = std::max(h->n1, h->n0);
   if ((rc = dalloc(h, &h->rhs, nmax))) return rc;
-  double** cgv[] = {&h->cg_r, &h->cg_z, &h->cg_p, &h->cg_q};
+  double** cgv[] = {&h->cg_r, &h->cg_z, &h->cg_p, &h->cg_q, &h->cg_r2, &h->cg_p2};
   for (auto p : cgv)
     if ((rc = dalloc(h, p, nmax))) return rc;
   if (order == 1) {
@@ -798,7 +807,7 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
     if (bl < 0) return FEMPIC_ERR_CUDA;
     h->pcg_blocks_w1 = h->pcg_blocks_w0 = bl;
   }
-  if ((rc = dalloc(h, &h->partials, 4 * (size_t)h->pcg_blocks_w1)) || (rc = dalloc(h, &h->bar, 1)) ||
+  if ((rc = dalloc(h, &h->partials, 8 * (size_t)h->pcg_blocks_w1)) || (rc = dalloc(h, &h->bar, 1)) ||
       (rc = dalloc(h, &h->d_status, 1)) || (rc = dalloc(h, &h->d_cg_iters, 1)) || (rc = dalloc(h, &h->d_cg_res, 1)) ||
       (rc = dalloc(h, &h->d_cg_iters_acc, 1)) ||
       (rc = dalloc(h, &h->d_norms, 4)) || (rc = dalloc(h, &h->d_cross, 1)))

@@ -186,11 +186,11 @@ struct PcgArgs {
   double* t;   // [DT.n_rows] scratch
   const double* rhs;
   double* x;   // in: initial guess, out: solution
-  double* r;
+  double* r[2];  // residual, double-buffered
   double* z;
-  double* p;
+  double* p[2];  // search direction, double-buffered
   double* q;
-  double* partials;  // [gridDim.x * 4]
+  double* partials[2];  // [gridDim.x * 4] each, used alternately
   GridBarrier* bar;
   int32_t* status;
   int32_t* iters_out;
@@ -234,7 +234,7 @@ __device__ __forceinline__ void grid_totals(const double* partials, double (&tot
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       double s = 0.0;
-      for (int b = l; b < (int)gridDim.x; b += 32) s += *((volatile const double*)(partials + b * 4 + k));
+      for (int b = l; b < (int)gridDim.x; b += 32) s += __ldcg(partials + b * 4 + k);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (l == 0) res[k] = s;
@@ -246,10 +246,9 @@ __device__ __forceinline__ void grid_totals(const double* partials, double (&tot
   __syncthreads();
 }
 
-// y_r = sum_k A_rk x_k for the rows this thread group owns, LPR lanes per row;
-// x is read around L1 (written by other blocks in this launch)
-template <int LPR, class F>
-__device__ __forceinline__ void rows_spmv(const CsrView& A, const double* x, int gid, int groups, F emit) {
+// y_r = sum_k A_rk f(k) for the rows this thread group owns, LPR lanes per row
+template <int LPR, class X, class F>
+__device__ __forceinline__ void rows_spmv(const CsrView& A, int gid, int groups, X x_of, F emit) {
   const int lane = gid % LPR;
   for (int r0 = gid / LPR; ; r0 += groups) {
     bool act = r0 < A.n_rows;
@@ -257,7 +256,8 @@ __device__ __forceinline__ void rows_spmv(const CsrView& A, const double* x, int
     double s = 0.0;
     if (act) {
       int beg = __ldg(A.rp + r0), end = __ldg(A.rp + r0 + 1);
-      for (int k = beg + lane; k < end; k += LPR) s = fma(__ldg(A.v + k), __ldcg(x + __ldg(A.ci + k)), s);
+      int k = beg + lane;
+      for (; k < end; k += LPR) s = fma(__ldg(A.v + k), x_of(__ldg(A.ci + k)), s);
     }
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
@@ -265,22 +265,13 @@ __device__ __forceinline__ void rows_spmv(const CsrView& A, const double* x, int
   }
 }
 
-// z = M^-1 r with the nodal correction (r complete in memory); returns r.z
-// contribution of this thread; sets p = z when first.  false on barrier timeout.
-__device__ __forceinline__ bool nodal_precondition(const PcgArgs& a, int gid, bool first, double& rz) {
-  const int tpg = gridDim.x * blockDim.x;
-  rows_spmv<4>(a.DT, a.r, gid, tpg / 4, [&](int k, double s) { a.t[k] = __ldg(a.dinvL + k) * s; });
-  if (!grid_sync(a.bar, a.status)) return false;
-  rows_spmv<4>(a.D, a.t, gid, tpg / 4, [&](int i, double s) {
-    double rr = __ldcg(a.r + i);
-    double zz = fma(__ldg(a.dinv + i), rr, s);
-    a.z[i] = zz;
-    if (first) a.p[i] = zz;
-    rz += rr * zz;
-  });
-  return true;
-}
-
+// Preconditioned CG, four grid barriers per iteration with the nodal
+// correction (three without):
+//   phase 0: p_k = z + beta p_{k-1}; barrier
+//   phase 1: q = A p_k; barrier; alpha = rz / (p.q)
+//   phase 2: x += alpha p, r' = r - alpha q; t = dinvL (D^T r') with r' formed
+//            on the fly; barrier
+//   phase 3: z = dinv r' + D t; barrier; rz', r'.r' -> convergence, beta
 template <int LPR>
 __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
   const int n = a.A.n_rows;
@@ -288,56 +279,81 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
   const int tpg = gridDim.x * blockDim.x;
   const int groups = tpg / LPR;
   const bool nodal = a.DT.n_rows > 0;
-  // phase 0: r = rhs - A x, z = M^-1 r, p = z
+  double* r_cur = a.r[0];
+  // ---- start: r = rhs - A x; z = M^-1 r
   double acc[3] = {0.0, 0.0, 0.0};  // r.z, r.r, rhs.rhs
-  rows_spmv<LPR>(a.A, a.x, gid, groups, [&](int r0, double s) {
-    double b = a.rhs[r0];
-    double rr = b - s;
-    a.r[r0] = rr;
-    acc[1] += rr * rr;
-    acc[2] += b * b;
-    if (!nodal) {
-      double zz = a.dinv[r0] * rr;
-      a.z[r0] = zz;
-      a.p[r0] = zz;
-      acc[0] += rr * zz;
-    }
-  });
+  rows_spmv<LPR>(
+      a.A, gid, groups, [&](int c) { return __ldcg(a.x + c); },
+      [&](int r0, double s) {
+        double b = a.rhs[r0];
+        double rr = b - s;
+        r_cur[r0] = rr;
+        acc[1] += rr * rr;
+        acc[2] += b * b;
+        if (!nodal) {
+          double zz = a.dinv[r0] * rr;
+          a.z[r0] = zz;
+          acc[0] += rr * zz;
+        }
+      });
   if (nodal) {
     if (!grid_sync(a.bar, a.status)) return;
-    if (!nodal_precondition(a, gid, true, acc[0])) return;
+    rows_spmv<4>(a.DT, gid, tpg / 4, [&](int c) { return __ldcg(r_cur + c); },
+                 [&](int k, double s) { a.t[k] = __ldg(a.dinvL + k) * s; });
+    if (!grid_sync(a.bar, a.status)) return;
+    rows_spmv<4>(a.D, gid, tpg / 4, [&](int c) { return __ldcg(a.t + c); }, [&](int i, double s) {
+      double rr = __ldcg(r_cur + i);
+      double zz = fma(__ldg(a.dinv + i), rr, s);
+      a.z[i] = zz;
+      acc[0] += rr * zz;
+    });
   }
-  block_partials<3>(acc, a.partials);
+  block_partials<3>(acc, a.partials[1]);
   if (!grid_sync(a.bar, a.status)) return;
   double tot[3];
-  grid_totals<3>(a.partials, tot);
+  grid_totals<3>(a.partials[1], tot);
   double rz = tot[0];
-  double bnorm = sqrt(tot[2]);
+  const double bnorm = sqrt(tot[2]);
   double rnorm = sqrt(tot[1]);
-  double thresh = a.rtol * bnorm;
+  const double thresh = a.rtol * bnorm;
   int it = 0;
   bool conv = rnorm <= thresh || bnorm == 0.0;
+  double beta = 0.0;
+  int pb = 0;  // p_{k-1} lives in p[pb], p_k is written to p[pb ^ 1]
   while (!conv && it < a.max_it) {
-    if (!grid_sync(a.bar, a.status)) return;  // p complete; partials free
-    // phase 1: q = A p, p.q
+    const double* p_old = a.p[pb];
+    double* p_new = a.p[pb ^ 1];
+    const bool first = it == 0;
+    // phase 0: p_k = z + beta p_{k-1} (elementwise), then q = A p_k
+    if (!first) {
+      for (int i = gid; i < n; i += tpg) p_new[i] = fma(beta, __ldcg(p_old + i), __ldcg(a.z + i));
+      if (!grid_sync(a.bar, a.status)) return;
+    } else {
+      // p_0 = z_0: kept for the next iteration (z is overwritten below); this
+      // iteration's product reads z itself, so no barrier is needed here
+      for (int i = gid; i < n; i += tpg) p_new[i] = __ldcg(a.z + i);
+    }
+    const double* pk_vec = first ? a.z : p_new;
     double acc1[1] = {0.0};
-    rows_spmv<LPR>(a.A, a.p, gid, groups, [&](int r0, double s) {
-      a.q[r0] = s;
-      acc1[0] += __ldcg(a.p + r0) * s;
-    });
-    block_partials<1>(acc1, a.partials);
+    rows_spmv<LPR>(
+        a.A, gid, groups, [&](int c) { return __ldcg(pk_vec + c); },
+        [&](int r0, double s) {
+          a.q[r0] = s;
+          acc1[0] += __ldcg(pk_vec + r0) * s;
+        });
+    block_partials<1>(acc1, a.partials[0]);
     if (!grid_sync(a.bar, a.status)) return;
     double t1[1];
-    grid_totals<1>(a.partials, t1);
-    double alpha = t1[0] != 0.0 ? rz / t1[0] : 0.0;
-    if (!grid_sync(a.bar, a.status)) return;  // everyone has read the partials
-    // phase 2: x += alpha p, r -= alpha q, z = M^-1 r
-    double acc2[2] = {0.0, 0.0};  // r.z, r.r
+    grid_totals<1>(a.partials[0], t1);
+    const double alpha = t1[0] != 0.0 ? rz / t1[0] : 0.0;
+    // phase 2: x += alpha p, r' = r - alpha q
+    double* r_new = a.r[(it + 1) & 1];
+    const double* r_old = r_cur;
+    double acc2[2] = {0.0, 0.0};  // r'.z', r'.r'
     for (int i = gid; i < n; i += tpg) {
-      double pi = __ldcg(a.p + i);
-      a.x[i] = fma(alpha, pi, __ldcg(a.x + i));
-      double rr = fma(-alpha, __ldcg(a.q + i), __ldcg(a.r + i));
-      a.r[i] = rr;
+      a.x[i] = fma(alpha, __ldcg(pk_vec + i), __ldcg(a.x + i));
+      double rr = fma(-alpha, __ldcg(a.q + i), __ldcg(r_old + i));
+      r_new[i] = rr;
       acc2[1] += rr * rr;
       if (!nodal) {
         double zz = a.dinv[i] * rr;
@@ -346,21 +362,29 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
       }
     }
     if (nodal) {
+      rows_spmv<4>(a.DT, gid, tpg / 4,
+                   [&](int c) { return fma(-alpha, __ldcg(a.q + c), __ldcg(r_old + c)); },
+                   [&](int k, double s) { a.t[k] = __ldg(a.dinvL + k) * s; });
       if (!grid_sync(a.bar, a.status)) return;
-      if (!nodal_precondition(a, gid, false, acc2[0])) return;
+      // phase 3: z = dinv r' + D t
+      rows_spmv<4>(a.D, gid, tpg / 4, [&](int c) { return __ldcg(a.t + c); }, [&](int i, double s) {
+        double rr = __ldcg(r_new + i);
+        double zz = fma(__ldg(a.dinv + i), rr, s);
+        a.z[i] = zz;
+        acc2[0] += rr * zz;
+      });
     }
-    block_partials<2>(acc2, a.partials);
+    block_partials<2>(acc2, a.partials[1]);
     if (!grid_sync(a.bar, a.status)) return;
     double t2[2];
-    grid_totals<2>(a.partials, t2);
+    grid_totals<2>(a.partials[1], t2);
     ++it;
+    r_cur = r_new;
+    pb ^= 1;
     rnorm = sqrt(t2[1]);
     conv = rnorm <= thresh;
-    if (conv) break;
-    double beta = rz != 0.0 ? t2[0] / rz : 0.0;
+    beta = rz != 0.0 ? t2[0] / rz : 0.0;
     rz = t2[0];
-    // phase 3: p = z + beta p
-    for (int i = gid; i < n; i += tpg) a.p[i] = fma(beta, __ldcg(a.p + i), __ldcg(a.z + i));
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *a.iters_out = it;

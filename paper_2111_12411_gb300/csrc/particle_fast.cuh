@@ -193,6 +193,103 @@ __device__ __forceinline__ void deposit_rho_fact(const double* l, double qw, con
   }
 }
 
+
+// ---- FP32 gather and push (mixed precision): lambda and geometry rounded to
+// float, DOF values read as FP64 and rounded, E, B and the Boris rotation in
+// FP32.  Positions, the walk, the deposit and the charge stay FP64.
+template <int P>
+__device__ __forceinline__ void gather_EB_f32(const TetGeom& Gd, const double* lad, const double* __restrict__ e,
+                                              const int32_t* __restrict__ d1, const double* __restrict__ b,
+                                              const int32_t* __restrict__ d2, const double* B0d, float* E, float* B) {
+  float l[4], g[4][3];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    l[i] = (float)lad[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[i][k] = (float)Gd.g[i][k];
+  }
+  float c[6];
+  if (P == 1) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) c[j] = (float)__ldg(e + __ldg(d1 + j));
+  } else {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const int s = edge_s(j), t = edge_t(j);
+      float e0 = (float)__ldg(e + __ldg(d1 + 2 * j)), e1 = (float)__ldg(e + __ldg(d1 + 2 * j + 1));
+      c[j] = fmaf(e0, fmaf(3.f, l[s], -1.f), e1 * fmaf(3.f, l[t], -1.f));
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const int s = face_v(f, 0), t = face_v(f, 1), u = face_v(f, 2);
+      float e0 = (float)__ldg(e + __ldg(d1 + 12 + 2 * f)), e1 = (float)__ldg(e + __ldg(d1 + 13 + 2 * f));
+      c[pair_of(s, t)] = fmaf(e0, 3.f * l[u], c[pair_of(s, t)]);
+      c[pair_of(s, u)] = fmaf(e1, 3.f * l[t], c[pair_of(s, u)]);
+    }
+  }
+  float al[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const int s = edge_s(j), t = edge_t(j);
+    al[t] = fmaf(c[j], l[s], al[t]);
+    al[s] = fmaf(-c[j], l[t], al[s]);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) E[k] = fmaf(al[0], g[0][k], fmaf(al[1], g[1][k], fmaf(al[2], g[2][k], al[3] * g[3][k])));
+  float beta[4];
+  if (P == 1) {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) beta[f] = (float)__ldg(b + __ldg(d2 + f));
+  } else {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      float sacc = 0.f;
+#pragma unroll
+      for (int v = 0; v < 3; ++v)
+        sacc = fmaf((float)__ldg(b + __ldg(d2 + 3 * f + v)), fmaf(4.f, l[face_v(f, v)], -1.f), sacc);
+      if (f < 3) sacc = fmaf((float)__ldg(b + __ldg(d2 + 12 + f)), 4.f * l[f], sacc);
+      beta[f] = sacc;
+    }
+  }
+  float gam[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const int s = face_v(f, 0), t = face_v(f, 1), u = face_v(f, 2);
+    float b2 = 2.f * beta[f];
+    gam[pair_of(t, u)] = fmaf(b2, l[s], gam[pair_of(t, u)]);
+    gam[pair_of(s, u)] = fmaf(-b2, l[t], gam[pair_of(s, u)]);
+    gam[pair_of(s, t)] = fmaf(b2, l[u], gam[pair_of(s, t)]);
+  }
+  B[0] = (float)B0d[0];
+  B[1] = (float)B0d[1];
+  B[2] = (float)B0d[2];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const float* ga = g[edge_s(j)];
+    const float* gb = g[edge_t(j)];
+    B[0] = fmaf(gam[j], ga[1] * gb[2] - ga[2] * gb[1], B[0]);
+    B[1] = fmaf(gam[j], ga[2] * gb[0] - ga[0] * gb[2], B[1]);
+    B[2] = fmaf(gam[j], ga[0] * gb[1] - ga[1] * gb[0], B[2]);
+  }
+}
+
+__device__ __forceinline__ void boris_f32(float* v, const float* E, const float* B, float h) {
+  float eh[3], vm[3], t[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    eh[k] = E[k] * h;
+    vm[k] = v[k] + eh[k];
+    t[k] = B[k] * h;
+  }
+  float sf = 2.f / (1.f + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+  float vp[3] = {vm[0] + (vm[1] * t[2] - vm[2] * t[1]), vm[1] + (vm[2] * t[0] - vm[0] * t[2]),
+                 vm[2] + (vm[0] * t[1] - vm[1] * t[0])};
+  float sv[3] = {t[0] * sf, t[1] * sf, t[2] * sf};
+  v[0] = vm[0] + (vp[1] * sv[2] - vp[2] * sv[1]) + eh[0];
+  v[1] = vm[1] + (vp[2] * sv[0] - vp[0] * sv[2]) + eh[1];
+  v[2] = vm[2] + (vp[0] * sv[1] - vp[1] * sv[0]) + eh[2];
+}
+
 // exit face of the chord in the current tet (entry face excluded); -1 if it ends here
 __device__ __forceinline__ int exit_face(const double* la, const double* lb, int entry, double s0, double& s1) {
   int best = -1;
@@ -216,7 +313,7 @@ __device__ __forceinline__ void bary_fma(const TetGeom& G, const double* x, doub
   for (int i = 0; i < 4; ++i) l[i] = fma(G.g[i][0], x[0], fma(G.g[i][1], x[1], fma(G.g[i][2], x[2], G.c[i])));
 }
 
-template <int P, bool AGG>
+template <int P, bool AGG, bool MIXED = false>
 __global__ void __launch_bounds__(256, 2) k_particle_fast(ParticleArgs a) {
   constexpr int N1 = P == 1 ? 6 : 20;
   constexpr int N2 = P == 1 ? 4 : 15;
@@ -235,10 +332,19 @@ __global__ void __launch_bounds__(256, 2) k_particle_fast(ParticleArgs a) {
   load_geom(a.geom, T, G);
   double la[4];
   bary_fma(G, x, la);
-  double E[3], B[3];
-  gather_E_fact<P>(G, la, a.e, a.dof1 + (size_t)T * N1, E);
-  gather_B_fact<P>(G, la, a.b, a.dof2 + (size_t)T * N2, a.B0, B);
-  boris<Fast>(v, E, B, a.h);
+  if (MIXED) {
+    float Ef[3], Bf[3], vf[3] = {(float)v[0], (float)v[1], (float)v[2]};
+    gather_EB_f32<P>(G, la, a.e, a.dof1 + (size_t)T * N1, a.b, a.dof2 + (size_t)T * N2, a.B0, Ef, Bf);
+    boris_f32(vf, Ef, Bf, (float)a.h);
+    v[0] = vf[0];
+    v[1] = vf[1];
+    v[2] = vf[2];
+  } else {
+    double E[3], B[3];
+    gather_E_fact<P>(G, la, a.e, a.dof1 + (size_t)T * N1, E);
+    gather_B_fact<P>(G, la, a.b, a.dof2 + (size_t)T * N2, a.B0, B);
+    boris<Fast>(v, E, B, a.h);
+  }
   double pa[3] = {x[0], x[1], x[2]};
   double pb[3];
 #pragma unroll

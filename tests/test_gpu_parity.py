@@ -221,3 +221,29 @@ def test_full_size_drift_tube_sampled():
     assert np.array_equal(g.get("TET")[idx], te)
     assert np.array_equal(g.get("HASH")[idx], hs)
     g.close()
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_mixed_precision_step(c1small, order):
+    """FP32 gather and push, FP64 walk/deposit/charge: positions and velocities
+    within 2e-6 of the FP64 oracle after one step, owning tets equal where the
+    particle is not within 1e-5 (in lambda) of a face, and charge still
+    conserved to 1e-12 on the device (the deposit and charge are FP64)."""
+    o, g = pair(c1small, order=order, precision="mixed", es_init=False, diagnostics=True)
+    rng = np.random.default_rng(5)
+    e, b = random_state(o.topo, rng)
+    o.e, o.e_prev, o.b = e.copy(), e.copy(), b.copy()
+    g.set("E", e)
+    g.set("E_PREV", e)
+    g.set("B", b)
+    w = o.step(c1small["dt"])
+    g.step(c1small["dt"])
+    assert rel(g.get("X"), w["x"]) < 2e-6
+    assert rel(g.get("V"), w["v"]) < 2e-6
+    ok = _unambiguous(o, w["x"], w["tet"], tol=1e-5)
+    assert ok.mean() > 0.98
+    assert np.array_equal(g.get("TET")[ok], w["tet"][ok])
+    d = g.diag()
+    assert d["continuity_abs"] <= 1e-12 * d["continuity_ref"]
+    assert rel(g.get("DG"), w["dg"]) < 1e-4
+    g.close()
