@@ -255,6 +255,31 @@ int femPIC_last_timing(const FemPIC* h, double* times, int32_t n);
 void femPIC_destroy(FemPIC* h);
 const char* femPIC_last_error(const FemPIC* h);
 
+/* ---- batching: many independent instances advanced together -------------
+ * The paper runs one simulation at a time; this is a systems extension for
+ * many small, uneven instances on one GPU.  A batch groups created handles
+ * (FEMPIC_FP64 or FEMPIC_MIXED, trapezoid scheme, at most 2^20 tets each, one
+ * device).  femPIC_batch_step advances every member by n_steps steps of its
+ * own dt (dt_host[i]) with one launch per kernel for all members: a batched
+ * counting sort, one persistent gather/push/walk/deposit kernel, batched
+ * right-hand side and b update, and one cooperative block-diagonal PCG in
+ * which each member owns a range of CTAs, its own reductions and its own
+ * convergence test.  The step's launch sequence is captured once in a CUDA
+ * graph and replayed (plain launches if capture is refused).  Each member's
+ * result is the same as stepping it alone, up to the order of floating-point
+ * atomic sums.  Between batch calls the members can be read (femPIC_get) and
+ * stepped alone; the batch does not own them (destroy it before them).
+ * femPIC_batch_step returns the first member error (message in
+ * femPIC_batch_last_error). */
+typedef struct FemPICBatch FemPICBatch;
+int femPIC_batch_create(FemPIC* const* members, int32_t n, FemPICBatch** out);
+int femPIC_batch_step(FemPICBatch* b, const double* dt_host, int32_t n_steps);
+/* times: [0] device ms of the last femPIC_batch_step call, [1] launches per
+ * step, [2] 1 if the CUDA graph was used, [3] CTAs of the batched CG. */
+int femPIC_batch_timing(const FemPICBatch* b, double* times, int32_t n);
+void femPIC_batch_destroy(FemPICBatch* b);
+const char* femPIC_batch_last_error(const FemPICBatch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,524 @@
+// Batched execution of many independent EM-FEMPIC instances ("members") of
+// different meshes, orders, precisions and particle counts on one GPU.
+//
+// Every member keeps its own device state; a device-resident descriptor per
+// member holds all pointers the kernels need.  Work is cut into fixed-size work
+// blocks tagged with a member (prefix tables), so one launch covers all
+// members and every warp works on one member.  The per-step buffer rotations
+// are done by tiny kernels on the descriptors, so a whole batched step is a
+// fixed launch sequence that can be captured once in a CUDA graph and
+// replayed.  The field solve is one cooperative, block-diagonal PCG: each
+// member owns a contiguous range of CTAs, has its own reductions and
+// convergence test, and the launch ends once every member has converged.
+#pragma once
+
+#include "linalg.cuh"
+#include "particle_fast.cuh"
+
+namespace fempic {
+namespace dev {
+
+struct MemberDesc {
+  int32_t order, mixed, max_cross, max_it;
+  int32_t n1, n2, n0, nt;
+  int64_t np;
+  double qw, h, dt, rtol;
+  double B0[3];
+  const double* geom;
+  const int32_t* nbr;
+  const int32_t* dof0;
+  const int32_t* dof1;
+  const int32_t* dof2;
+  const uint8_t* pec;
+  double* x[3];
+  double* v[3];
+  int32_t* tet;
+  int32_t* pid;
+  double* xa[3];
+  double* va[3];
+  int32_t* teta;
+  int32_t* pida;
+  int32_t* ncross;
+  unsigned long long* hash;
+  int32_t* cnt;
+  int32_t* off;
+  double *e, *e_prev, *e_new, *b, *dg, *dg_prev, *rho, *rho_prev;
+  CsrView A, R1, Q, C, D, DT;
+  const double* dinvA;
+  const double* dinvL;
+  double* rhs;
+  double* r[2];
+  double* z;
+  double* p[2];
+  double* q;
+  double* t;
+  int32_t* status;
+  int32_t* cg_iters;
+  double* cg_res;
+  unsigned long long* crossings;
+};
+
+struct BatchWork {
+  int32_t n;                // members
+  MemberDesc* d;            // [n]
+  const int32_t* pblk;      // [n+1] particle work blocks (256 particles)
+  const int32_t* tblk;      // [n+1] tet tiles (1024 tets)
+  const int32_t* r1blk;     // [n+1] W1 row blocks (32 rows: 8 lanes per row)
+  const int32_t* r2blk;     // [n+1] W2 row blocks (64 rows: 4 lanes per row)
+  const int32_t* zblk;      // [n+1] zeroing blocks (256 entries of dg | rho | counts)
+  const int32_t* cgblk;     // [n+1] CTAs of the cooperative PCG per member
+  int32_t* tile_sums;       // [total tiles]
+  GridBarrier* bar;
+  double* partials;         // [2][grid * 4]
+  int32_t* status;          // batch-level status (barrier timeouts)
+};
+
+// largest m with pref[m] <= wb
+__device__ __forceinline__ int member_of(const int32_t* pref, int n, int wb) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(pref + mid) <= wb)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_batch_begin(BatchWork w) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= w.n) return;
+  MemberDesc& d = w.d[m];
+  double* t = d.dg;
+  d.dg = d.dg_prev;
+  d.dg_prev = t;
+  t = d.rho;
+  d.rho = d.rho_prev;
+  d.rho_prev = t;
+}
+
+__global__ void k_batch_zero(BatchWork w) {
+  const int total = __ldg(w.zblk + w.n);
+  for (int wb = blockIdx.x; wb < total; wb += gridDim.x) {
+    const int m = member_of(w.zblk, w.n, wb);
+    const MemberDesc& d = w.d[m];
+    int64_t k = (int64_t)(wb - __ldg(w.zblk + m)) * 256 + threadIdx.x;
+    if (k < d.n1)
+      d.dg[k] = 0.0;
+    else if (k < d.n1 + d.n0)
+      d.rho[k - d.n1] = 0.0;
+    else if (k < d.n1 + d.n0 + d.nt)
+      d.cnt[k - d.n1 - d.n0] = 0;
+  }
+}
+
+__global__ void k_batch_hist(BatchWork w) {
+  const int total = __ldg(w.pblk + w.n);
+  for (int wb = blockIdx.x; wb < total; wb += gridDim.x) {
+    const int m = member_of(w.pblk, w.n, wb);
+    const MemberDesc& d = w.d[m];
+    int64_t i = (int64_t)(wb - __ldg(w.pblk + m)) * 256 + threadIdx.x;
+    if (i < d.np) atomicAdd(d.cnt + d.tet[i], 1);
+  }
+}
+
+// exclusive scan of one 1024-tet tile; tile total into tile_sums (global tile id)
+__global__ void k_batch_scan_tiles(BatchWork w) {
+  __shared__ int32_t warp_tot[32];
+  const int tile = blockIdx.x;
+  const int m = member_of(w.tblk, w.n, tile);
+  const MemberDesc& d = w.d[m];
+  const int local = tile - __ldg(w.tblk + m);
+  const int i = local * 1024 + threadIdx.x;
+  int v = i < d.nt ? d.cnt[i] : 0;
+  int l = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  int s = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, s, o);
+    if (l >= o) s += t;
+  }
+  if (l == 31) warp_tot[wi] = s;
+  __syncthreads();
+  if (wi == 0) {
+    int t = warp_tot[l];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int u = __shfl_up_sync(0xffffffffu, t, o);
+      if (l >= o) t += u;
+    }
+    warp_tot[l] = t;
+  }
+  __syncthreads();
+  int excl = s - v + (wi > 0 ? warp_tot[wi - 1] : 0);
+  if (i < d.nt) d.off[i] = excl;
+  if (threadIdx.x == 1023) w.tile_sums[tile] = excl + v;
+}
+
+// one CTA per member: exclusive scan of its tile totals (at most 1024 tiles)
+__global__ void k_batch_scan_sums(BatchWork w) {
+  __shared__ int32_t warp_tot[32];
+  const int m = blockIdx.x;
+  const int t0 = __ldg(w.tblk + m), nt = __ldg(w.tblk + m + 1) - t0;
+  int v = threadIdx.x < nt ? w.tile_sums[t0 + threadIdx.x] : 0;
+  int l = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  int s = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, s, o);
+    if (l >= o) s += t;
+  }
+  if (l == 31) warp_tot[wi] = s;
+  __syncthreads();
+  if (wi == 0) {
+    int t = warp_tot[l];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int u = __shfl_up_sync(0xffffffffu, t, o);
+      if (l >= o) t += u;
+    }
+    warp_tot[l] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < nt) w.tile_sums[t0 + threadIdx.x] = s - v + (wi > 0 ? warp_tot[wi - 1] : 0);
+}
+
+__global__ void k_batch_scan_add(BatchWork w) {
+  const int tile = blockIdx.x;
+  const int m = member_of(w.tblk, w.n, tile);
+  const MemberDesc& d = w.d[m];
+  const int i = (tile - __ldg(w.tblk + m)) * 1024 + threadIdx.x;
+  if (i < d.nt) d.off[i] += w.tile_sums[tile];
+}
+
+__global__ void k_batch_scatter(BatchWork w) {
+  const int total = __ldg(w.pblk + w.n);
+  for (int wb = blockIdx.x; wb < total; wb += gridDim.x) {
+    const int m = member_of(w.pblk, w.n, wb);
+    const MemberDesc& d = w.d[m];
+    int64_t i = (int64_t)(wb - __ldg(w.pblk + m)) * 256 + threadIdx.x;
+    if (i >= d.np) continue;
+    int t = d.tet[i];
+    int pos = atomicAdd(d.off + t, 1);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      d.xa[k][pos] = d.x[k][i];
+      d.va[k][pos] = d.v[k][i];
+    }
+    d.teta[pos] = t;
+    d.pida[pos] = d.pid[i];
+  }
+}
+
+__global__ void k_batch_swap_particles(BatchWork w) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= w.n) return;
+  MemberDesc& d = w.d[m];
+  for (int k = 0; k < 3; ++k) {
+    double* t = d.x[k];
+    d.x[k] = d.xa[k];
+    d.xa[k] = t;
+    t = d.v[k];
+    d.v[k] = d.va[k];
+    d.va[k] = t;
+  }
+  int32_t* ti = d.tet;
+  d.tet = d.teta;
+  d.teta = ti;
+  ti = d.pid;
+  d.pid = d.pida;
+  d.pida = ti;
+}
+
+__device__ __forceinline__ ParticleArgs member_particle_args(const MemberDesc& d) {
+  ParticleArgs a;
+  a.n = d.np;
+  for (int k = 0; k < 3; ++k) {
+    a.x[k] = d.x[k];
+    a.v[k] = d.v[k];
+    a.B0[k] = d.B0[k];
+  }
+  a.tet = d.tet;
+  a.ncross = d.ncross;
+  a.hash = d.hash;
+  a.geom = d.geom;
+  a.nbr = d.nbr;
+  a.dof0 = d.dof0;
+  a.dof1 = d.dof1;
+  a.dof2 = d.dof2;
+  a.e = d.e;
+  a.b = d.b;
+  a.dg = d.dg;
+  a.rho = d.rho;
+  a.h = d.h;
+  a.dt = d.dt;
+  a.qw = d.qw;
+  a.max_cross = d.max_cross;
+  a.status = d.status;
+  a.crossings = d.crossings;
+  return a;
+}
+
+// persistent: CTAs loop over the particle work blocks of all members
+__global__ void __launch_bounds__(256, 2) k_batch_particles(BatchWork w) {
+  const int total = __ldg(w.pblk + w.n);
+  for (int wb = blockIdx.x; wb < total; wb += gridDim.x) {
+    const int m = member_of(w.pblk, w.n, wb);
+    const MemberDesc& d = w.d[m];
+    const ParticleArgs a = member_particle_args(d);
+    const int64_t i = (int64_t)(wb - __ldg(w.pblk + m)) * 256 + threadIdx.x;
+    if (d.order == 1) {
+      if (d.mixed)
+        particle_step<1, true, true>(a, i);
+      else
+        particle_step<1, true, false>(a, i);
+    } else {
+      if (d.mixed)
+        particle_step<2, true, true>(a, i);
+      else
+        particle_step<2, true, false>(a, i);
+    }
+  }
+}
+
+// initial guess e_new = 2 e - e_prev, over W1 row blocks (32 rows each)
+__global__ void k_batch_guess(BatchWork w) {
+  const int total = __ldg(w.r1blk + w.n);
+  for (int wb = blockIdx.x; wb < total; wb += gridDim.x) {
+    const int m = member_of(w.r1blk, w.n, wb);
+    const MemberDesc& d = w.d[m];
+    int base = (wb - __ldg(w.r1blk + m)) * 32;
+    for (int r = base + threadIdx.x; r < base + 32 && r < d.n1; r += blockDim.x)
+      d.e_new[r] = 2.0 * d.e[r] - d.e_prev[r];
+  }
+}
+
+// trapezoidal right-hand side, 8 lanes per row
+__global__ void k_batch_rhs(BatchWork w) {
+  const int total = __ldg(w.r1blk + w.n);
+  const int lane = threadIdx.x & 7;
+  for (int wb = blockIdx.x; wb < total; wb += gridDim.x) {
+    const int m = member_of(w.r1blk, w.n, wb);
+    const MemberDesc& d = w.d[m];
+    const int r = (wb - __ldg(w.r1blk + m)) * 32 + (threadIdx.x >> 3);
+    const bool act = r < d.n1;
+    double s = 0.0;
+    if (act) {
+      for (int k = __ldg(d.R1.rp + r) + lane; k < __ldg(d.R1.rp + r + 1); k += 8)
+        s = fma(__ldg(d.R1.v + k), __ldg(d.e + __ldg(d.R1.ci + k)), s);
+      double t = 0.0;
+      for (int k = __ldg(d.Q.rp + r) + lane; k < __ldg(d.Q.rp + r + 1); k += 8)
+        t = fma(__ldg(d.Q.v + k), __ldg(d.b + __ldg(d.Q.ci + k)), t);
+      s = fma(d.dt, t, s);
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 8);
+    if (act && lane == 0) d.rhs[r] = d.pec[r] ? 0.0 : s - d.dg[r];
+  }
+}
+
+// b -= dt/2 C (e_new + e), 4 lanes per row
+__global__ void k_batch_bupdate(BatchWork w) {
+  const int total = __ldg(w.r2blk + w.n);
+  const int lane = threadIdx.x & 3;
+  for (int wb = blockIdx.x; wb < total; wb += gridDim.x) {
+    const int m = member_of(w.r2blk, w.n, wb);
+    const MemberDesc& d = w.d[m];
+    const int r = (wb - __ldg(w.r2blk + m)) * 64 + (threadIdx.x >> 2);
+    const bool act = r < d.n2;
+    double s = 0.0;
+    if (act) {
+      for (int k = __ldg(d.C.rp + r) + lane; k < __ldg(d.C.rp + r + 1); k += 4) {
+        int c = __ldg(d.C.ci + k);
+        s = fma(__ldg(d.C.v + k), __ldg(d.e_new + c) + __ldg(d.e + c), s);
+      }
+    }
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 4);
+    if (act && lane == 0) d.b[r] = fma(-0.5 * d.dt, s, d.b[r]);
+  }
+}
+
+__global__ void k_batch_end(BatchWork w) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= w.n) return;
+  MemberDesc& d = w.d[m];
+  double* old_prev = d.e_prev;
+  d.e_prev = d.e;
+  d.e = d.e_new;
+  d.e_new = old_prev;
+}
+
+// ---- block-diagonal PCG ---------------------------------------------------------
+// member totals: sum of the member's CTA partials in CTA order
+template <int NV>
+__device__ __forceinline__ void member_totals(const double* partials, int b0, int b1, double (&tot)[NV]) {
+  __shared__ double res[4];
+  if (threadIdx.x < 32) {
+    int l = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int b = b0 + l; b < b1; b += 32) s += __ldcg(partials + b * 4 + k);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (l == 0) res[k] = s;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) tot[k] = res[k];
+  __syncthreads();
+}
+
+// rows of one member, LPR lanes per row, spread over the member's CTAs
+template <int LPR, class X, class F>
+__device__ __forceinline__ void member_rows(const CsrView& A, int tid, int tcount, X x_of, F emit) {
+  const int lane = tid % LPR;
+  const int groups = tcount / LPR;
+  for (int r0 = tid / LPR; ; r0 += groups) {
+    bool act = r0 < A.n_rows;
+    if (!__any_sync(0xffffffffu, act)) break;
+    double s = 0.0;
+    if (act) {
+      int beg = __ldg(A.rp + r0), end = __ldg(A.rp + r0 + 1);
+      for (int k = beg + lane; k < end; k += LPR) s = fma(__ldg(A.v + k), x_of(__ldg(A.ci + k)), s);
+    }
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
+    if (act && lane == 0) emit(r0, s);
+  }
+}
+
+// Every CTA runs the same number of iterations and barriers; a CTA whose
+// member has converged skips the work.  The exit test uses each member's
+// state at the start of the iteration (summed over all CTAs after the last
+// barrier), so every CTA leaves at the same iteration.
+__global__ void __launch_bounds__(256) k_batch_pcg(BatchWork w, int max_it_all) {
+  const int m = member_of(w.cgblk, w.n, blockIdx.x);
+  const MemberDesc& d = w.d[m];
+  const int b0 = __ldg(w.cgblk + m), b1 = __ldg(w.cgblk + m + 1);
+  const int tid = (blockIdx.x - b0) * blockDim.x + threadIdx.x;
+  const int tcount = (b1 - b0) * blockDim.x;
+  double* part[2] = {w.partials, w.partials + 4 * (size_t)gridDim.x};
+  const int n = d.n1;
+  double* x = d.e_new;
+  double* r_cur = d.r[0];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // r.z, r.r, rhs.rhs, (unused)
+  member_rows<8>(
+      d.A, tid, tcount, [&](int c) { return __ldcg(x + c); },
+      [&](int r0, double s) {
+        double b = d.rhs[r0];
+        double rr = b - s;
+        r_cur[r0] = rr;
+        acc[1] += rr * rr;
+        acc[2] += b * b;
+      });
+  if (!grid_sync(w.bar, w.status)) return;
+  member_rows<4>(d.DT, tid, tcount, [&](int c) { return __ldcg(r_cur + c); },
+                 [&](int k, double s) { d.t[k] = __ldg(d.dinvL + k) * s; });
+  if (!grid_sync(w.bar, w.status)) return;
+  member_rows<4>(d.D, tid, tcount, [&](int c) { return __ldcg(d.t + c); }, [&](int i, double s) {
+    double rr = __ldcg(r_cur + i);
+    double zz = fma(__ldg(d.dinvA + i), rr, s);
+    d.z[i] = zz;
+    acc[0] += rr * zz;
+  });
+  block_partials<4>(acc, part[1]);
+  if (!grid_sync(w.bar, w.status)) return;
+  double tot[3];
+  member_totals<3>(part[1], b0, b1, tot);
+  double rz = tot[0];
+  const double bnorm = sqrt(tot[2]);
+  double rnorm = sqrt(tot[1]);
+  const double thresh = d.rtol * bnorm;
+  bool conv = rnorm <= thresh || bnorm == 0.0;
+  int it_m = 0;
+  double beta = 0.0;
+  int pb = 0;
+  for (int it = 0; it < max_it_all; ++it) {
+    const bool work = !conv && it_m < d.max_it;
+    const double* p_old = d.p[pb];
+    double* p_new = d.p[pb ^ 1];
+    const bool first = it_m == 0;
+    if (work) {
+      if (first) {
+        for (int i = tid; i < n; i += tcount) p_new[i] = __ldcg(d.z + i);
+      } else {
+        for (int i = tid; i < n; i += tcount) p_new[i] = fma(beta, __ldcg(p_old + i), __ldcg(d.z + i));
+      }
+    }
+    if (!grid_sync(w.bar, w.status)) return;
+    double acc1[4] = {0.0, 0.0, 0.0, work ? 1.0 : 0.0};  // p.q, -, -, members still working
+    if (work)
+      member_rows<8>(
+          d.A, tid, tcount, [&](int c) { return __ldcg(p_new + c); },
+          [&](int r0, double s) {
+            d.q[r0] = s;
+            acc1[0] += __ldcg(p_new + r0) * s;
+          });
+    block_partials<4>(acc1, part[0]);
+    if (!grid_sync(w.bar, w.status)) return;
+    // all CTAs: is any member still working?  (flag of this iteration's start)
+    {
+      __shared__ double any;
+      if (threadIdx.x < 32) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) s += __ldcg(part[0] + b * 4 + 3);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) any = s;
+      }
+      __syncthreads();
+      bool stop = any == 0.0;
+      __syncthreads();
+      if (stop) break;
+    }
+    double t1[1];
+    member_totals<1>(part[0], b0, b1, t1);
+    const double alpha = (work && t1[0] != 0.0) ? rz / t1[0] : 0.0;
+    double* r_new = d.r[(it_m + 1) & 1];
+    const double* r_old = r_cur;
+    double acc2[4] = {0.0, 0.0, 0.0, 0.0};
+    if (work) {
+      for (int i = tid; i < n; i += tcount) {
+        x[i] = fma(alpha, __ldcg(p_new + i), __ldcg(x + i));
+        double rr = fma(-alpha, __ldcg(d.q + i), __ldcg(r_old + i));
+        r_new[i] = rr;
+        acc2[1] += rr * rr;
+      }
+      member_rows<4>(d.DT, tid, tcount, [&](int c) { return fma(-alpha, __ldcg(d.q + c), __ldcg(r_old + c)); },
+                     [&](int k, double s) { d.t[k] = __ldg(d.dinvL + k) * s; });
+    }
+    if (!grid_sync(w.bar, w.status)) return;
+    if (work)
+      member_rows<4>(d.D, tid, tcount, [&](int c) { return __ldcg(d.t + c); }, [&](int i, double s) {
+        double rr = __ldcg(r_new + i);
+        double zz = fma(__ldg(d.dinvA + i), rr, s);
+        d.z[i] = zz;
+        acc2[0] += rr * zz;
+      });
+    block_partials<4>(acc2, part[1]);
+    if (!grid_sync(w.bar, w.status)) return;
+    double t2[2];
+    member_totals<2>(part[1], b0, b1, t2);
+    if (work) {
+      ++it_m;
+      r_cur = r_new;
+      pb ^= 1;
+      rnorm = sqrt(t2[1]);
+      conv = rnorm <= thresh;
+      beta = rz != 0.0 ? t2[0] / rz : 0.0;
+      rz = t2[0];
+    }
+  }
+  if (blockIdx.x == b0 && threadIdx.x == 0) {
+    *d.cg_iters = it_m;
+    *d.cg_res = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+    if (!conv) atomicOr(d.status, kStatusCG);
+  }
+}
+
+}  // namespace dev
+}  // namespace fempic

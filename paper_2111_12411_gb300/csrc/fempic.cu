@@ -22,6 +22,7 @@
 #include "kernels.cuh"
 #include "linalg.cuh"
 #include "particle_fast.cuh"
+#include "batch.cuh"
 
 using namespace fempic;
 using namespace fempic::dev;
@@ -1183,5 +1184,401 @@ void femPIC_destroy(FemPIC* h) {
 }
 
 const char* femPIC_last_error(const FemPIC* h) { return h ? h->err.c_str() : "NULL handle"; }
+
+}  // extern "C"
+
+// =============================================================================
+// Batched execution of several handles (members) on one stream.
+struct FemPICBatch {
+  std::vector<FemPIC*> m;
+  std::string err;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  std::vector<MemberDesc> hd;
+  MemberDesc* dd = nullptr;
+  int32_t *pblk = nullptr, *tblk = nullptr, *r1blk = nullptr, *r2blk = nullptr, *zblk = nullptr, *cgblk = nullptr;
+  int32_t* tile_sums = nullptr;
+  GridBarrier* bar = nullptr;
+  double* partials = nullptr;
+  int32_t* status = nullptr;
+  int total_tiles = 0, cg_grid = 0, persist_grid = 0;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_failed = false;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  double t_particle_ms = 0, t_field_ms = 0;
+  int launches_per_step = 0;
+  bool used_graph = false;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+#define BCK(call)                                                \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) {                                     \
+      b->err = std::string(#call) + ": " + cudaGetErrorString(e_); \
+      return FEMPIC_ERR_CUDA;                                    \
+    }                                                            \
+  } while (0)
+
+template <class T>
+int balloc(FemPICBatch* b, T** p, size_t n) {
+  cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    b->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? FEMPIC_ERR_OOM : FEMPIC_ERR_CUDA;
+  }
+  b->allocs.push_back(*p);
+  return FEMPIC_OK;
+}
+
+MemberDesc describe(FemPIC* h, double dt) {
+  MemberDesc d;
+  memset(&d, 0, sizeof(d));
+  d.order = h->order;
+  d.mixed = h->opts.precision == FEMPIC_MIXED;
+  d.max_cross = h->opts.max_cross;
+  d.max_it = h->opts.cg_max_it;
+  d.n1 = h->n1;
+  d.n2 = h->n2;
+  d.n0 = h->n0;
+  d.nt = h->n_tets;
+  d.np = h->np;
+  d.qw = h->q * h->weight;
+  d.h = ((h->q / h->m) * dt) * 0.5;
+  d.dt = dt;
+  d.rtol = h->opts.cg_rtol;
+  for (int k = 0; k < 3; ++k) d.B0[k] = h->opts.B0[k];
+  d.geom = h->geom;
+  d.nbr = h->nbr;
+  d.dof0 = h->dof0;
+  d.dof1 = h->dof1;
+  d.dof2 = h->dof2;
+  d.pec = h->pec1;
+  for (int k = 0; k < 3; ++k) {
+    d.x[k] = h->px[k];
+    d.v[k] = h->pv[k];
+    d.xa[k] = h->alt[k];
+    d.va[k] = h->alt[3 + k];
+  }
+  d.tet = h->ptet;
+  d.pid = h->pid;
+  d.teta = h->ptet_alt;
+  d.pida = h->pid_alt;
+  d.ncross = h->pncross;
+  d.hash = h->phash;
+  d.cnt = h->sort_cnt;
+  d.off = h->sort_off;
+  d.e = h->e;
+  d.e_prev = h->e_prev;
+  d.e_new = h->e_new;
+  d.b = h->b;
+  d.dg = h->dg;
+  d.dg_prev = h->dg_prev;
+  d.rho = h->rho;
+  d.rho_prev = h->rho_prev;
+  d.A = h->M.view(h->Aval);
+  d.R1 = h->M.view(h->R1val);
+  d.Q = h->Q.view();
+  d.C = h->C.view();
+  d.D = h->D.view();
+  d.DT = h->DT.view();
+  d.dinvA = h->dinvA;
+  d.dinvL = h->dinvL;
+  d.rhs = h->rhs;
+  d.r[0] = h->cg_r;
+  d.r[1] = h->cg_r2;
+  d.z = h->cg_z;
+  d.p[0] = h->cg_p;
+  d.p[1] = h->cg_p2;
+  d.q = h->cg_q;
+  d.t = h->d_tmp0;
+  d.status = h->d_status;
+  d.cg_iters = h->d_cg_iters;
+  d.cg_res = h->d_cg_res;
+  d.crossings = h->d_cross;
+  return d;
+}
+
+void write_back(FemPIC* h, const MemberDesc& d) {
+  for (int k = 0; k < 3; ++k) {
+    h->px[k] = d.x[k];
+    h->pv[k] = d.v[k];
+    h->alt[k] = d.xa[k];
+    h->alt[3 + k] = d.va[k];
+  }
+  h->ptet = d.tet;
+  h->pid = d.pid;
+  h->ptet_alt = d.teta;
+  h->pid_alt = d.pida;
+  h->e = d.e;
+  h->e_prev = d.e_prev;
+  h->e_new = d.e_new;
+  h->dg = d.dg;
+  h->dg_prev = d.dg_prev;
+  h->rho = d.rho;
+  h->rho_prev = d.rho_prev;
+}
+
+std::vector<int32_t> prefix_blocks(const std::vector<int64_t>& work, int64_t per_block) {
+  std::vector<int32_t> p(work.size() + 1, 0);
+  for (size_t i = 0; i < work.size(); ++i) p[i + 1] = p[i] + (int32_t)((work[i] + per_block - 1) / per_block);
+  return p;
+}
+
+BatchWork batch_work(FemPICBatch* b) {
+  BatchWork w;
+  w.n = (int32_t)b->m.size();
+  w.d = b->dd;
+  w.pblk = b->pblk;
+  w.tblk = b->tblk;
+  w.r1blk = b->r1blk;
+  w.r2blk = b->r2blk;
+  w.zblk = b->zblk;
+  w.cgblk = b->cgblk;
+  w.tile_sums = b->tile_sums;
+  w.bar = b->bar;
+  w.partials = b->partials;
+  w.status = b->status;
+  return w;
+}
+
+// one batched step: 13 launches (+1 memset), no host synchronisation
+int batch_launch_step(FemPICBatch* b, int max_it_all) {
+  BatchWork w = batch_work(b);
+  const int n = (int)b->m.size();
+  const int g1 = (n + 127) / 128;
+  const int pg = b->persist_grid;
+  cudaStream_t s = b->stream;
+  k_batch_begin<<<g1, 128, 0, s>>>(w);
+  k_batch_zero<<<pg, 256, 0, s>>>(w);
+  k_batch_hist<<<pg, 256, 0, s>>>(w);
+  k_batch_scan_tiles<<<b->total_tiles, 1024, 0, s>>>(w);
+  k_batch_scan_sums<<<n, 1024, 0, s>>>(w);
+  k_batch_scan_add<<<b->total_tiles, 1024, 0, s>>>(w);
+  k_batch_scatter<<<pg, 256, 0, s>>>(w);
+  k_batch_swap_particles<<<g1, 128, 0, s>>>(w);
+  k_batch_particles<<<pg, 256, 0, s>>>(w);
+  BCK(cudaGetLastError());
+  BCK(cudaEventRecord(b->ev[1], s));
+  k_batch_guess<<<pg, 256, 0, s>>>(w);
+  k_batch_rhs<<<pg, 256, 0, s>>>(w);
+  BCK(cudaMemsetAsync(b->bar, 0, sizeof(GridBarrier), s));
+  void* args[] = {&w, &max_it_all};
+  BCK(cudaLaunchCooperativeKernel((void*)k_batch_pcg, b->cg_grid, 256, args, 0, s));
+  k_batch_bupdate<<<pg, 256, 0, s>>>(w);
+  k_batch_end<<<g1, 128, 0, s>>>(w);
+  BCK(cudaGetLastError());
+  b->launches_per_step = 14;
+  return FEMPIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int femPIC_batch_create(FemPIC* const* members, int32_t n, FemPICBatch** out) {
+  if (!out) return FEMPIC_ERR_ARG;
+  *out = nullptr;
+  FemPICBatch* b = new (std::nothrow) FemPICBatch();
+  if (!b) return FEMPIC_ERR_OOM;
+  *out = b;
+  if (!members || n < 1) {
+    b->err = "a batch needs at least one member";
+    return FEMPIC_ERR_ARG;
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    FemPIC* h = members[i];
+    if (!h || !h->stream) {
+      b->err = "member " + std::to_string(i) + " is not a created handle";
+      return FEMPIC_ERR_ARG;
+    }
+    if (h->opts.precision == FEMPIC_FP64_STRICT || h->opts.scheme != FEMPIC_SCHEME_TRAPEZOID) {
+      b->err = "batched members must use FEMPIC_FP64 or FEMPIC_MIXED and the trapezoid scheme";
+      return FEMPIC_ERR_ARG;
+    }
+    if (h->n_tets > 1024 * 1024) {
+      b->err = "batched members are limited to 1048576 tets";
+      return FEMPIC_ERR_ARG;
+    }
+    if (i > 0 && h->device != members[0]->device) {
+      b->err = "all members must be on one device";
+      return FEMPIC_ERR_ARG;
+    }
+    b->m.push_back(h);
+  }
+  b->device = members[0]->device;
+  BCK(cudaSetDevice(b->device));
+  cudaDeviceProp prop;
+  BCK(cudaGetDeviceProperties(&prop, b->device));
+  b->num_sms = prop.multiProcessorCount;
+  BCK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+  for (auto& e : b->ev) BCK(cudaEventCreate(&e));
+  std::vector<int64_t> wp, wt, w1, w2, wz, wnnz;
+  for (FemPIC* h : b->m) {
+    wp.push_back(h->np);
+    wt.push_back(h->n_tets);
+    w1.push_back(h->n1);
+    w2.push_back(h->n2);
+    wz.push_back((int64_t)h->n1 + h->n0 + h->n_tets);
+    wnnz.push_back(h->M.nnz + h->D.nnz + h->DT.nnz);
+  }
+  auto pp = prefix_blocks(wp, 256), pt = prefix_blocks(wt, 1024), p1 = prefix_blocks(w1, 32),
+       p2 = prefix_blocks(w2, 64), pz = prefix_blocks(wz, 256);
+  b->total_tiles = pt.back();
+  int per_sm = 0;
+  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_pcg, 256, 0));
+  b->cg_grid = std::max(1, per_sm) * b->num_sms;
+  if (b->cg_grid < n) {
+    b->err = "more members than co-resident CTAs for the batched CG";
+    return FEMPIC_ERR_ARG;
+  }
+  // CTAs of the block-diagonal CG in proportion to each member's matrix entries
+  std::vector<int32_t> pc(n + 1, 0);
+  {
+    double tot = 0;
+    for (auto v : wnnz) tot += (double)v;
+    int spare = b->cg_grid - n;
+    std::vector<int32_t> cnt(n, 1);
+    int used = 0;
+    for (int i = 0; i < n; ++i) {
+      int extra = (int)std::floor(spare * (double)wnnz[i] / tot);
+      cnt[i] += extra;
+      used += extra;
+    }
+    for (int i = 0; used < spare; i = (i + 1) % n, ++used) cnt[i]++;
+    for (int i = 0; i < n; ++i) pc[i + 1] = pc[i] + cnt[i];
+  }
+  int per_sm_p = 0;
+  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_p, k_batch_particles, 256, 0));
+  b->persist_grid = std::max(1, per_sm_p) * b->num_sms;
+  int rc;
+  if ((rc = balloc(b, &b->dd, n)) || (rc = balloc(b, &b->pblk, n + 1)) || (rc = balloc(b, &b->tblk, n + 1)) ||
+      (rc = balloc(b, &b->r1blk, n + 1)) || (rc = balloc(b, &b->r2blk, n + 1)) || (rc = balloc(b, &b->zblk, n + 1)) ||
+      (rc = balloc(b, &b->cgblk, n + 1)) || (rc = balloc(b, &b->tile_sums, b->total_tiles)) ||
+      (rc = balloc(b, &b->bar, 1)) || (rc = balloc(b, &b->partials, 8 * (size_t)b->cg_grid)) ||
+      (rc = balloc(b, &b->status, 1)))
+    return rc;
+  BCK(cudaMemcpy(b->pblk, pp.data(), pp.size() * 4, cudaMemcpyHostToDevice));
+  BCK(cudaMemcpy(b->tblk, pt.data(), pt.size() * 4, cudaMemcpyHostToDevice));
+  BCK(cudaMemcpy(b->r1blk, p1.data(), p1.size() * 4, cudaMemcpyHostToDevice));
+  BCK(cudaMemcpy(b->r2blk, p2.data(), p2.size() * 4, cudaMemcpyHostToDevice));
+  BCK(cudaMemcpy(b->zblk, pz.data(), pz.size() * 4, cudaMemcpyHostToDevice));
+  BCK(cudaMemcpy(b->cgblk, pc.data(), pc.size() * 4, cudaMemcpyHostToDevice));
+  BCK(cudaMemset(b->status, 0, sizeof(int32_t)));
+  return FEMPIC_OK;
+}
+
+int femPIC_batch_step(FemPICBatch* b, const double* dt, int32_t n_steps) {
+  if (!b || !b->stream || !dt || n_steps < 0) return FEMPIC_ERR_ARG;
+  const int n = (int)b->m.size();
+  BCK(cudaSetDevice(b->device));
+  int max_it_all = 1;
+  b->hd.resize(n);
+  for (int i = 0; i < n; ++i) {
+    FemPIC* h = b->m[i];
+    if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) {
+      b->err = "dt must be positive and finite";
+      return FEMPIC_ERR_ARG;
+    }
+    int rc = FEMPIC_OK;
+    if (dt[i] != h->dt_cur) rc = form_system(h, dt[i]);
+    if (rc) {
+      b->err = h->err;
+      return rc;
+    }
+    BCK(cudaStreamSynchronize(h->stream));
+    BCK(cudaMemsetAsync(h->d_cross, 0, sizeof(unsigned long long), b->stream));
+    b->hd[i] = describe(h, dt[i]);
+    max_it_all = std::max(max_it_all, h->opts.cg_max_it);
+  }
+  BCK(cudaMemcpyAsync(b->dd, b->hd.data(), sizeof(MemberDesc) * n, cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaEventRecord(b->ev[0], b->stream));
+  // capture one step in a CUDA graph the first time; replay it n_steps times
+  if (!b->graph && !b->graph_failed && n_steps > 0) {
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    int rc = ok ? batch_launch_step(b, max_it_all) : FEMPIC_ERR_CUDA;
+    ok = (cudaStreamEndCapture(b->stream, &g) == cudaSuccess) && ok && rc == FEMPIC_OK;
+    if (ok) ok = cudaGraphInstantiate(&b->graph, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+      b->graph = nullptr;
+      b->graph_failed = true;
+      cudaGetLastError();
+    }
+  }
+  double tp = 0, tf = 0;
+  for (int32_t s = 0; s < n_steps; ++s) {
+    if (b->graph) {
+      BCK(cudaGraphLaunch(b->graph, b->stream));
+      b->used_graph = true;
+    } else {
+      int rc = batch_launch_step(b, max_it_all);
+      if (rc) return rc;
+      b->used_graph = false;
+    }
+  }
+  BCK(cudaEventRecord(b->ev[2], b->stream));
+  BCK(cudaMemcpyAsync(b->hd.data(), b->dd, sizeof(MemberDesc) * n, cudaMemcpyDeviceToHost, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  float tot = 0.f;
+  BCK(cudaEventElapsedTime(&tot, b->ev[0], b->ev[2]));
+  if (!b->graph) {
+    float a = 0.f;
+    BCK(cudaEventElapsedTime(&a, b->ev[0], b->ev[1]));
+    tp = a;
+    tf = tot - a;
+  } else {
+    tp = 0.0;
+    tf = tot;
+  }
+  b->t_particle_ms = tp;
+  b->t_field_ms = tf;
+  int32_t bst = 0;
+  BCK(cudaMemcpy(&bst, b->status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  int worst = FEMPIC_OK;
+  for (int i = 0; i < n; ++i) {
+    FemPIC* h = b->m[i];
+    write_back(h, b->hd[i]);
+    h->steps += n_steps;
+    h->since_sort = 1;
+    h->dt_cur = dt[i];
+    int rc = latch_status(h);
+    if (rc && !worst) {
+      worst = rc;
+      b->err = "member " + std::to_string(i) + ": " + h->err;
+    }
+  }
+  if (bst & kStatusBarrier) {
+    b->err = "batched CG grid barrier timed out";
+    return FEMPIC_ERR_BARRIER;
+  }
+  return worst;
+}
+
+int femPIC_batch_timing(const FemPICBatch* b, double* times, int32_t n) {
+  if (!b || !times || n < 1) return FEMPIC_ERR_ARG;
+  const double v[4] = {b->t_particle_ms + b->t_field_ms, (double)b->launches_per_step, b->used_graph ? 1.0 : 0.0,
+                       (double)b->cg_grid};
+  for (int32_t k = 0; k < n && k < 4; ++k) times[k] = v[k];
+  return FEMPIC_OK;
+}
+
+void femPIC_batch_destroy(FemPICBatch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (void* p : b->allocs) cudaFree(p);
+  for (auto e : b->ev)
+    if (e) cudaEventDestroy(e);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+const char* femPIC_batch_last_error(const FemPICBatch* b) { return b ? b->err.c_str() : "NULL batch"; }
 
 }  // extern "C"

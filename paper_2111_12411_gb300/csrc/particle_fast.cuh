@@ -313,13 +313,15 @@ __device__ __forceinline__ void bary_fma(const TetGeom& G, const double* x, doub
   for (int i = 0; i < 4; ++i) l[i] = fma(G.g[i][0], x[0], fma(G.g[i][1], x[1], fma(G.g[i][2], x[2], G.c[i])));
 }
 
-template <int P, bool AGG, bool MIXED = false>
-__global__ void __launch_bounds__(256, 2) k_particle_fast(ParticleArgs a) {
+// One particle per thread; every lane of the warp must call it (lanes past the
+// end pass valid = false) because the first sub-segment and the charge are
+// summed across lanes.
+template <int P, bool AGG, bool MIXED>
+__device__ __forceinline__ void particle_step(const ParticleArgs& a, int64_t i) {
   constexpr int N1 = P == 1 ? 6 : 20;
   constexpr int N2 = P == 1 ? 4 : 15;
   constexpr int N0 = P == 1 ? 4 : 10;
   const int lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = i < a.n;
   int T = valid ? a.tet[i] : 0;
   double x[3], v[3];
@@ -430,6 +432,11 @@ __global__ void __launch_bounds__(256, 2) k_particle_fast(ParticleArgs a) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) my_cross += __shfl_xor_sync(0xffffffffu, my_cross, o);
   if (lane == 0 && my_cross) atomicAdd(a.crossings, my_cross);
+}
+
+template <int P, bool AGG, bool MIXED = false>
+__global__ void __launch_bounds__(256, 2) k_particle_fast(ParticleArgs a) {
+  particle_step<P, AGG, MIXED>(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 }  // namespace dev

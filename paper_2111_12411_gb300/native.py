@@ -86,6 +86,11 @@ EXPORTS = [
     ("femPIC_last_timing", ctypes.c_int, [_P, _P, ctypes.c_int32]),
     ("femPIC_destroy", None, [_P]),
     ("femPIC_last_error", ctypes.c_char_p, [_P]),
+    ("femPIC_batch_create", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
+    ("femPIC_batch_step", ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    ("femPIC_batch_timing", ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    ("femPIC_batch_destroy", None, [_P]),
+    ("femPIC_batch_last_error", ctypes.c_char_p, [_P]),
 ]
 
 _lib = None
@@ -325,6 +330,66 @@ class Simulation:
     def __del__(self):
         try:
             if self.h is not None:
+                self.close()
+        except Exception:
+            pass
+
+
+# ---- batching ------------------------------------------------------------------
+def femPIC_batch_create(handles):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    b = ctypes.c_void_p()
+    rc = load().femPIC_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(handles), ctypes.byref(b))
+    if rc != FEMPIC_OK:
+        msg = load().femPIC_batch_last_error(b).decode() if b.value else "batch create failed"
+        if b.value:
+            load().femPIC_batch_destroy(b)
+        raise FemPICError(rc, msg)
+    return b
+
+
+def femPIC_batch_step(b, dts, n_steps=1):
+    dts = np.ascontiguousarray(dts, dtype=np.float64)
+    rc = load().femPIC_batch_step(b, _ptr(dts), n_steps)
+    if rc != FEMPIC_OK:
+        raise FemPICError(rc, load().femPIC_batch_last_error(b).decode())
+
+
+def femPIC_batch_timing(b):
+    t = np.zeros(4)
+    load().femPIC_batch_timing(b, _ptr(t), 4)
+    return dict(zip(("ms", "launches_per_step", "graph", "cg_ctas"), t.tolist()))
+
+
+def femPIC_batch_destroy(b):
+    if b is not None and b.value:
+        load().femPIC_batch_destroy(b)
+
+
+def femPIC_batch_last_error(b):
+    return load().femPIC_batch_last_error(b).decode()
+
+
+class Batch:
+    """Several Simulations advanced together (one launch per kernel for all)."""
+
+    def __init__(self, sims):
+        self.sims = list(sims)
+        self.b = femPIC_batch_create([s.h for s in self.sims])
+
+    def step(self, dts, n=1):
+        femPIC_batch_step(self.b, dts, n)
+
+    def timing(self):
+        return femPIC_batch_timing(self.b)
+
+    def close(self):
+        femPIC_batch_destroy(self.b)
+        self.b = None
+
+    def __del__(self):
+        try:
+            if self.b is not None:
                 self.close()
         except Exception:
             pass
