@@ -1,10 +1,12 @@
 """GPU tests of batched execution: uneven instances (orders 1 and 2, FP64 and
 mixed precision, different meshes and particle counts) advanced together in
 one launch per kernel give, member by member, the same state as each instance
-advanced alone.  Tolerances: positions/velocities rel 1e-9 after 3 steps
-(same arithmetic; only the order of the FP64 atomic current sums differs, and
-it feeds the field solve), fields rel 1e-6 (CG stopped at rel 1e-12 residual
-on systems with condition numbers up to ~1e6), charge conservation 1e-12."""
+advanced alone.  Tolerances: positions/velocities rel 1e-9 after 3 steps in
+FP64 (same arithmetic; only the order of the FP64 atomic current sums
+differs, and it feeds the field solve), 2e-6 with the FP32 push (a last-bit
+field difference can flip an FP32 rounding); fields rel 1e-6 (CG stopped at
+rel 1e-12 residual on systems with condition numbers up to ~1e6); charge
+conservation 1e-12."""
 
 import numpy as np
 import pytest
@@ -43,9 +45,10 @@ def test_batch_matches_members_alone():
     t = batch.timing()
     assert t["launches_per_step"] > 0
     for k, (a, m, c) in enumerate(zip(alone, mixed, cfgs)):
+        tol = 2e-6 if c["precision"] == "mixed" else 1e-9
         xa, xm = a.get("X"), m.get("X")
-        assert rel(xm, xa) < 1e-9, k
-        assert rel(m.get("V"), a.get("V")) < 1e-9, k
+        assert rel(xm, xa) < tol, k
+        assert rel(m.get("V"), a.get("V")) < tol, k
         assert (m.get("TET") == a.get("TET")).mean() > 0.999
         assert rel(m.get("E"), a.get("E")) < 1e-6, k
         assert rel(m.get("B"), a.get("B")) < 1e-6, k
