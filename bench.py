@@ -322,6 +322,93 @@ def run_native(args, rank, world, local_rank):
     return result
 
 
+def run_batched(args, local_rank):
+    """Batched workload: uneven box instances advanced together (mixed
+    precision, one launch per kernel for all) against the plain per-instance
+    FP64 path (each instance stepped alone, one after the other)."""
+    import torch
+    import workloads
+    from paper_2111_12411_gb300 import Batch, Simulation
+
+    torch.cuda.set_device(local_rank)
+    cfgs = workloads.make_batch(n_instances=args.instances, steps=args.steps)
+    total_np = sum(len(c["x"]) for c in cfgs)
+    K, W = args.steps, args.warmup
+    out = {"metric": "aggregate particle-steps/s, batched mixed precision vs per-instance FP64",
+           "unit": UNIT, "steps": K, "warmup": W, "data": "synthetic",
+           "config": {"workload": f"{len(cfgs)} Kuhn-box instances, tets log-uniform 2e3-5e4, p in {{1,2}}, "
+                                  "particles log-uniform 1e4-1e6, B0 uniform 0-1 T",
+                      "instances": len(cfgs), "particles": total_np,
+                      "tets": sum(len(c["tets"]) for c in cfgs),
+                      "orders": [c["order"] for c in cfgs]}}
+    sims = [Simulation.from_config(c, precision="fp64", device=local_rank) for c in cfgs]
+    for _ in range(W):
+        for sm, c in zip(sims, cfgs):
+            sm.step(c["dt"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iters = 0
+    for _ in range(K):
+        for sm, c in zip(sims, cfgs):
+            sm.step(c["dt"])
+            iters += sm.last_timing()["cg_iterations"]
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    for sm in sims:
+        sm.close()
+    out["per_instance_fp64"] = {"value": total_np * K / t_plain, "ms_per_step": 1e3 * t_plain / K,
+                                "cg_iterations_per_instance_step": iters / (K * len(cfgs))}
+    sims = [Simulation.from_config(c, precision="mixed", device=local_rank) for c in cfgs]
+    batch = Batch(sims)
+    dts = np.array([c["dt"] for c in cfgs])
+    batch.step(dts, W)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch.step(dts, K)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    tm = batch.timing()
+    out["value"] = total_np * K / t_batch
+    out["ms_per_step"] = 1e3 * t_batch / K
+    out["batched_mixed"] = {"value": total_np * K / t_batch, "ms_per_step": 1e3 * t_batch / K,
+                            "device_ms_per_step": tm["ms"] / K, "cuda_graph": bool(tm["graph"]),
+                            "launches_per_step": tm["launches_per_step"], "cg_ctas": tm["cg_ctas"]}
+    out["speedup_batched_vs_per_instance"] = out["value"] / out["per_instance_fp64"]["value"]
+    batch.close()
+    for sm in sims:
+        sm.close()
+    print(json.dumps(out), flush=True)
+
+
+def run_serving(args, local_rank):
+    """Serving workload: a Poisson stream of box simulations admitted by HBM
+    budget and advanced in chunks with continuous batching."""
+    import torch
+    import workloads
+    from paper_2111_12411_gb300.serve import Request, Server
+
+    torch.cuda.set_device(local_rank)
+    reqs = workloads.make_requests(n_requests=args.requests, rate_hz=args.rate,
+                                   chunk_steps=args.chunk_steps, chunks=(1, 2))
+    server = Server(args.hbm_budget_gb * (1 << 30), max_slots=args.instances, device=local_rank,
+                    precision="mixed", result_keys=("E",))
+    t_build = time.perf_counter()
+    for r in reqs:
+        cfg = workloads.build_request(r)
+        server.submit(Request(r["id"], cfg, r["arrival"], r["n_chunks"], r["chunk_steps"]))
+    t_build = time.perf_counter() - t_build
+    server.run()
+    rep = server.report()
+    out = {"metric": "serving: p50/p99 chunk latency and aggregate particle-steps/s", "unit": UNIT,
+           "value": rep["particle_steps_per_s_busy"], "data": "synthetic",
+           "config": {"workload": f"{len(reqs)} Poisson requests at {args.rate} Hz, Kuhn boxes 2e3-5e4 "
+                                  "tets, p in {1,2}, particles 1e4-4e6, mixed precision",
+                      "chunk_steps": args.chunk_steps, "hbm_budget_gb": args.hbm_budget_gb,
+                      "max_slots": args.instances, "host_input_generation_s": t_build},
+           "serving": rep}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,6 +422,12 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=50_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=("tube", "batched", "serving"), default="tube")
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=2.0)
+    ap.add_argument("--chunk-steps", type=int, default=50)
+    ap.add_argument("--hbm-budget-gb", type=float, default=200.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -351,7 +444,12 @@ def main():
         dist.init_process_group("nccl")
     from paper_2111_12411_gb300 import build
     build.build()
-    run_native(args, rank, world, local_rank)
+    if args.workload == "batched":
+        run_batched(args, local_rank)
+    elif args.workload == "serving":
+        run_serving(args, local_rank)
+    else:
+        run_native(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
