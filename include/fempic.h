@@ -109,7 +109,12 @@ enum {
   FEMPIC_OP_DT = 4,  /* D^T, N0 x N1                                            */
   FEMPIC_OP_M2 = 5,  /* [*mu^-1], N2 x N2                                       */
   FEMPIC_OP_A = 6,   /* system matrix of the last dt, N1 x N1                   */
-  FEMPIC_OP_L = 7    /* nodal Laplacian D^T [*eps] D on interior W0 DOFs        */
+  FEMPIC_OP_L = 7,   /* nodal Laplacian D^T [*eps] D on interior W0 DOFs        */
+  FEMPIC_OP_PI = 8,  /* vector nodal interpolation Pi, N1 x 3*n_nodes: W1
+                        coefficients of hat_v e_c (exact at order 2; edge
+                        moments at order 1), PEC rows removed; an auxiliary
+                        space of the CG preconditioner                        */
+  FEMPIC_OP_PIT = 9  /* Pi^T, 3*n_nodes x N1                                   */
 };
 
 typedef struct FemPIC FemPIC; /* opaque handle */
@@ -170,6 +175,7 @@ typedef struct {
   int64_t n_particles;
   int64_t nnz_A, nnz_C, nnz_Q;  /* stored entries of A, C, C^T [*mu^-1] */
   int64_t nnz_D, nnz_DT;        /* stored entries of D and D^T          */
+  int64_t nnz_Pi;               /* stored entries of the vector nodal interpolation */
   int32_t n_boundary_faces;
   size_t device_bytes;      /* device memory held by the handle                */
 } femPIC_info;

@@ -46,6 +46,9 @@ struct MemberDesc {
   CsrView A, R1, Q, C, D, DT;
   const double* dinvA;
   const double* dinvL;
+  CsrView Pi, PiT;
+  const double* dinvV;
+  double* u;
   double* rhs;
   double* r[2];
   double* z;
@@ -391,6 +394,33 @@ __device__ __forceinline__ void member_rows(const CsrView& A, int tid, int tcoun
   }
 }
 
+// z_i = dinvA_i r_i + (D t)_i + (Pi u)_i over the member's rows; returns r.z part
+__device__ __forceinline__ double member_z(const MemberDesc& d, const double* rvec, int tid, int tcount) {
+  const int lane = tid % 4;
+  const int groups = tcount / 4;
+  double rz = 0.0;
+  for (int i = tid / 4; ; i += groups) {
+    bool act = i < d.n1;
+    if (!__any_sync(0xffffffffu, act)) break;
+    double s = 0.0;
+    if (act) {
+      for (int k = __ldg(d.D.rp + i) + lane; k < __ldg(d.D.rp + i + 1); k += 4)
+        s = fma(__ldg(d.D.v + k), __ldcg(d.t + __ldg(d.D.ci + k)), s);
+      for (int k = __ldg(d.Pi.rp + i) + lane; k < __ldg(d.Pi.rp + i + 1); k += 4)
+        s = fma(__ldg(d.Pi.v + k), __ldcg(d.u + __ldg(d.Pi.ci + k)), s);
+    }
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 4);
+    if (act && (tid & 3) == 0) {
+      double rr = __ldcg(rvec + i);
+      double zz = fma(__ldg(d.dinvA + i), rr, s);
+      d.z[i] = zz;
+      rz += rr * zz;
+    }
+  }
+  return rz;
+}
+
 // Every CTA runs the same number of iterations and barriers; a CTA whose
 // member has converged skips the work.  The exit test uses each member's
 // state at the start of the iteration (summed over all CTAs after the last
@@ -418,13 +448,10 @@ __global__ void __launch_bounds__(256) k_batch_pcg(BatchWork w, int max_it_all) 
   if (!grid_sync(w.bar, w.status)) return;
   member_rows<4>(d.DT, tid, tcount, [&](int c) { return __ldcg(r_cur + c); },
                  [&](int k, double s) { d.t[k] = __ldg(d.dinvL + k) * s; });
+  member_rows<4>(d.PiT, tid, tcount, [&](int c) { return __ldcg(r_cur + c); },
+                 [&](int k, double s) { d.u[k] = __ldg(d.dinvV + k) * s; });
   if (!grid_sync(w.bar, w.status)) return;
-  member_rows<4>(d.D, tid, tcount, [&](int c) { return __ldcg(d.t + c); }, [&](int i, double s) {
-    double rr = __ldcg(r_cur + i);
-    double zz = fma(__ldg(d.dinvA + i), rr, s);
-    d.z[i] = zz;
-    acc[0] += rr * zz;
-  });
+  acc[0] += member_z(d, r_cur, tid, tcount);
   block_partials<4>(acc, part[1]);
   if (!grid_sync(w.bar, w.status)) return;
   double tot[3];
@@ -490,15 +517,11 @@ __global__ void __launch_bounds__(256) k_batch_pcg(BatchWork w, int max_it_all) 
       }
       member_rows<4>(d.DT, tid, tcount, [&](int c) { return fma(-alpha, __ldcg(d.q + c), __ldcg(r_old + c)); },
                      [&](int k, double s) { d.t[k] = __ldg(d.dinvL + k) * s; });
+      member_rows<4>(d.PiT, tid, tcount, [&](int c) { return fma(-alpha, __ldcg(d.q + c), __ldcg(r_old + c)); },
+                     [&](int k, double s) { d.u[k] = __ldg(d.dinvV + k) * s; });
     }
     if (!grid_sync(w.bar, w.status)) return;
-    if (work)
-      member_rows<4>(d.D, tid, tcount, [&](int c) { return __ldcg(d.t + c); }, [&](int i, double s) {
-        double rr = __ldcg(r_new + i);
-        double zz = fma(__ldg(d.dinvA + i), rr, s);
-        d.z[i] = zz;
-        acc2[0] += rr * zz;
-      });
+    if (work) acc2[0] += member_z(d, r_new, tid, tcount);
     block_partials<4>(acc2, part[1]);
     if (!grid_sync(w.bar, w.status)) return;
     double t2[2];

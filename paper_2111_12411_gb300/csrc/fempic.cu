@@ -61,7 +61,8 @@ struct FemPIC {
   uint8_t *pec1 = nullptr, *int0 = nullptr;
   double* load0 = nullptr;
   // matrices
-  DevCSR M, K, Q, C, M2, D, DT, L;
+  DevCSR M, K, Q, C, M2, D, DT, L, Pi, PiT;
+  double *dvM = nullptr, *dvK = nullptr, *dinvV = nullptr, *aux_u = nullptr;
   double *Aval = nullptr, *R1val = nullptr, *R2val = nullptr, *dinvA = nullptr, *dinvL = nullptr;
   // fields
   double *e = nullptr, *e_prev = nullptr, *e_new = nullptr, *b = nullptr, *dg = nullptr, *dg_prev = nullptr;
@@ -208,6 +209,10 @@ int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, 
   a.DT = nodal ? h->DT.view() : CsrView{0, nullptr, nullptr, nullptr};
   a.dinvL = h->dinvL;
   a.t = h->d_tmp0;
+  a.Pi = nodal ? h->Pi.view() : CsrView{0, nullptr, nullptr, nullptr};
+  a.PiT = nodal ? h->PiT.view() : CsrView{0, nullptr, nullptr, nullptr};
+  a.dinvV = h->dinvV;
+  a.u = h->aux_u;
   a.rhs = rhs;
   a.x = x;
   a.r[0] = h->cg_r;
@@ -265,6 +270,10 @@ int form_system(FemPIC* h, double dt) {
     h->launches++;
     CK(cudaGetLastError());
   }
+  k_form_dv<<<grid_for(h->PiT.n_rows, 256, 1 << 30), 256, 0, h->stream>>>(h->PiT.n_rows, h->dvM, h->dvK, c1,
+                                                                            h->dinvV);
+  h->launches++;
+  CK(cudaGetLastError());
   h->dt_cur = dt;
   return FEMPIC_OK;
 }
@@ -780,7 +789,10 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
 #undef UP
   if ((rc = upload_csr(h, &h->M, hm.M)) || (rc = upload_csr(h, &h->K, hm.K)) || (rc = upload_csr(h, &h->Q, hm.Q)) ||
       (rc = upload_csr(h, &h->C, hm.C)) || (rc = upload_csr(h, &h->M2, hm.M2)) || (rc = upload_csr(h, &h->D, hm.D)) ||
-      (rc = upload_csr(h, &h->DT, hm.DT)) || (rc = upload_csr(h, &h->L, hm.L)))
+      (rc = upload_csr(h, &h->DT, hm.DT)) || (rc = upload_csr(h, &h->L, hm.L)) ||
+      (rc = upload_csr(h, &h->Pi, hm.Pi)) || (rc = upload_csr(h, &h->PiT, hm.PiT)) ||
+      (rc = upload(h, &h->dvM, hm.dvM)) || (rc = upload(h, &h->dvK, hm.dvK)) ||
+      (rc = dalloc(h, &h->dinvV, hm.PiT.n_rows)) || (rc = dalloc(h, &h->aux_u, hm.PiT.n_rows)))
     return rc;
   const size_t nnz = hm.M.col.size();
   if ((rc = dalloc(h, &h->Aval, nnz)) || (rc = dalloc(h, &h->R1val, nnz)) ||
@@ -980,6 +992,8 @@ int femPIC_apply(FemPIC* h, int32_t op, const double* x_host, size_t nx, double*
       }
       break;
     case FEMPIC_OP_L: A = &h->L; break;
+    case FEMPIC_OP_PI: A = &h->Pi; break;
+    case FEMPIC_OP_PIT: A = &h->PiT; break;
     default:
       h->err = "unknown operator";
       return FEMPIC_ERR_ARG;
@@ -1160,6 +1174,7 @@ int femPIC_get_info(const FemPIC* h, femPIC_info* info) {
   info->nnz_Q = h->Q.nnz;
   info->nnz_D = h->D.nnz;
   info->nnz_DT = h->DT.nnz;
+  info->nnz_Pi = h->Pi.nnz;
   info->n_boundary_faces = h->n_bfaces;
   info->device_bytes = h->bytes;
   return FEMPIC_OK;
@@ -1287,6 +1302,10 @@ MemberDesc describe(FemPIC* h, double dt) {
   d.DT = h->DT.view();
   d.dinvA = h->dinvA;
   d.dinvL = h->dinvL;
+  d.Pi = h->Pi.view();
+  d.PiT = h->PiT.view();
+  d.dinvV = h->dinvV;
+  d.u = h->aux_u;
   d.rhs = h->rhs;
   d.r[0] = h->cg_r;
   d.r[1] = h->cg_r2;
@@ -1423,7 +1442,7 @@ int femPIC_batch_create(FemPIC* const* members, int32_t n, FemPICBatch** out) {
     w1.push_back(h->n1);
     w2.push_back(h->n2);
     wz.push_back((int64_t)h->n1 + h->n0 + h->n_tets);
-    wnnz.push_back(h->M.nnz + h->D.nnz + h->DT.nnz);
+    wnnz.push_back(h->M.nnz + h->D.nnz + h->DT.nnz + 2 * h->Pi.nnz);
   }
   auto pp = prefix_blocks(wp, 256), pt = prefix_blocks(wt, 1024), p1 = prefix_blocks(w1, 32),
        p2 = prefix_blocks(w2, 64), pz = prefix_blocks(wz, 256);

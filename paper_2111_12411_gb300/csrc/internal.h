@@ -44,6 +44,8 @@ struct HostModel {
   HostCSR DT;                    // N0 x N1
   HostCSR L;                     // nodal Laplacian D^T [*eps] D, interior rows/cols
   std::vector<double> load0;     // <W0_k, 1>
+  HostCSR Pi, PiT;               // vector nodal interpolation: W1 coefficients of hat_v e_c
+  std::vector<double> dvM, dvK;  // diag(Pi^T M Pi), diag(Pi^T K Pi)
 };
 
 // Local tables of the order-p bases, computed exactly on the reference tet.
@@ -54,6 +56,7 @@ struct LocalTables {
   std::vector<double> T1;    // [nl1][nl1][4][4]: int_ref P1_ia P1_jb
   std::vector<double> T2;    // [nl2][nl2][6][6]: int_ref P2_{f,ab} P2_{h,cd}
   std::vector<double> I0;    // [nl0]: int_ref W0_k
+  std::vector<double> Rv;    // order 2: [4][4][nl1]: W1 coefficients of l_v grad l_a
 };
 
 // Returns "" on success, else an error message.

@@ -111,6 +111,14 @@ __global__ void k_lincomb(int32_t n, const double* __restrict__ x, const double*
     out[i] = a * x[i] + b * y[i];
 }
 
+// dinvV = 1 / (dvM + c dvK), 0 where the sum vanishes
+__global__ void k_form_dv(int32_t n, const double* dvm, const double* dvk, double c, double* dinv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double d = dvm[i] + c * dvk[i];
+  dinv[i] = d > 0.0 ? 1.0 / d : 0.0;
+}
+
 // A = M + ca K, R = M + cr K (same pattern), inverse diagonal of A (0 on empty rows)
 __global__ void k_form_system(int32_t n, const int32_t* rp, const int32_t* ci, const double* m, const double* k,
                               double ca, double cr, double* a, double* r, double* dinv) {
@@ -184,6 +192,12 @@ struct PcgArgs {
   CsrView DT;
   const double* dinvL;
   double* t;   // [DT.n_rows] scratch
+  // vector nodal auxiliary space (used with the nodal correction):
+  // z += Pi (dinvV (Pi^T r))
+  CsrView Pi;
+  CsrView PiT;
+  const double* dinvV;
+  double* u;   // [PiT.n_rows] scratch
   const double* rhs;
   double* x;   // in: initial guess, out: solution
   double* r[2];  // residual, double-buffered
@@ -265,6 +279,36 @@ __device__ __forceinline__ void rows_spmv(const CsrView& A, int gid, int groups,
   }
 }
 
+// z_i = dinv_i r_i + (D t)_i + (Pi u)_i for the rows this group owns; returns r.z part
+template <int LPR>
+__device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, int gid, int tpg) {
+  const int lane = gid % LPR;
+  const int groups = tpg / LPR;
+  const bool vec = a.Pi.n_rows > 0;
+  double rz = 0.0;
+  for (int i = gid / LPR; ; i += groups) {
+    bool act = i < a.D.n_rows;
+    if (!__any_sync(0xffffffffu, act)) break;
+    double s = 0.0;
+    if (act) {
+      for (int k = __ldg(a.D.rp + i) + lane; k < __ldg(a.D.rp + i + 1); k += LPR)
+        s = fma(__ldg(a.D.v + k), __ldcg(a.t + __ldg(a.D.ci + k)), s);
+      if (vec)
+        for (int k = __ldg(a.Pi.rp + i) + lane; k < __ldg(a.Pi.rp + i + 1); k += LPR)
+          s = fma(__ldg(a.Pi.v + k), __ldcg(a.u + __ldg(a.Pi.ci + k)), s);
+    }
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
+    if (act && lane == 0) {
+      double rr = __ldcg(rvec + i);
+      double zz = fma(__ldg(a.dinv + i), rr, s);
+      a.z[i] = zz;
+      rz += rr * zz;
+    }
+  }
+  return rz;
+}
+
 // Preconditioned CG, four grid barriers per iteration with the nodal
 // correction (three without):
 //   phase 0: p_k = z + beta p_{k-1}; barrier
@@ -300,13 +344,11 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
     if (!grid_sync(a.bar, a.status)) return;
     rows_spmv<4>(a.DT, gid, tpg / 4, [&](int c) { return __ldcg(r_cur + c); },
                  [&](int k, double s) { a.t[k] = __ldg(a.dinvL + k) * s; });
+    if (a.PiT.n_rows > 0)
+      rows_spmv<4>(a.PiT, gid, tpg / 4, [&](int c) { return __ldcg(r_cur + c); },
+                   [&](int k, double s) { a.u[k] = __ldg(a.dinvV + k) * s; });
     if (!grid_sync(a.bar, a.status)) return;
-    rows_spmv<4>(a.D, gid, tpg / 4, [&](int c) { return __ldcg(a.t + c); }, [&](int i, double s) {
-      double rr = __ldcg(r_cur + i);
-      double zz = fma(__ldg(a.dinv + i), rr, s);
-      a.z[i] = zz;
-      acc[0] += rr * zz;
-    });
+    acc[0] += aux_z<4>(a, r_cur, gid, tpg);
   }
   block_partials<3>(acc, a.partials[1]);
   if (!grid_sync(a.bar, a.status)) return;
@@ -365,14 +407,13 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
       rows_spmv<4>(a.DT, gid, tpg / 4,
                    [&](int c) { return fma(-alpha, __ldcg(a.q + c), __ldcg(r_old + c)); },
                    [&](int k, double s) { a.t[k] = __ldg(a.dinvL + k) * s; });
+      if (a.PiT.n_rows > 0)
+        rows_spmv<4>(a.PiT, gid, tpg / 4,
+                     [&](int c) { return fma(-alpha, __ldcg(a.q + c), __ldcg(r_old + c)); },
+                     [&](int k, double s) { a.u[k] = __ldg(a.dinvV + k) * s; });
       if (!grid_sync(a.bar, a.status)) return;
-      // phase 3: z = dinv r' + D t
-      rows_spmv<4>(a.D, gid, tpg / 4, [&](int c) { return __ldcg(a.t + c); }, [&](int i, double s) {
-        double rr = __ldcg(r_new + i);
-        double zz = fma(__ldg(a.dinv + i), rr, s);
-        a.z[i] = zz;
-        acc2[0] += rr * zz;
-      });
+      // phase 3: z = dinv r' + D t + Pi u
+      acc2[0] += aux_z<4>(a, r_new, gid, tpg);
     }
     block_partials<2>(acc2, a.partials[1]);
     if (!grid_sync(a.bar, a.status)) return;

@@ -447,6 +447,22 @@ std::string build_local_tables(int p, LocalTables* T) {
         }
   T->I0.resize(T->nl0);
   for (int k = 0; k < T->nl0; ++k) T->I0[k] = to_double(integrate_bary(f0[k]));
+  if (p == 2) {
+    // l_v grad l_a lies in the order-2 space: its exact W1 coefficients
+    std::vector<Vec> tg;
+    for (int v = 0; v < 4; ++v)
+      for (int a = 0; a < 4; ++a) {
+        std::array<Poly, 4> f;
+        f[a] = lam(v);
+        tg.push_back(w1_xyz(f));
+      }
+    std::vector<double> X;
+    err = solve_in_span(w1v, tg, &X);  // [nl1][16]
+    if (!err.empty()) return "vector interpolation: " + err;
+    T->Rv.assign(16 * (size_t)n1, 0.0);
+    for (int j = 0; j < n1; ++j)
+      for (int q = 0; q < 16; ++q) T->Rv[(size_t)q * n1 + j] = X[(size_t)j * 16 + q];
+  }
   return "";
 }
 
@@ -770,6 +786,87 @@ int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets_in, int3
       scatter(&m->DT, r0, r1, l0, l1, DT_loc.data(), all0, all1, true);
       for (int k = 0; k < l0; ++k) m->load0[r0[k]] += bW[q * l0 + k];
     }
+  }
+  // ---- vector nodal interpolation Pi (auxiliary space of the preconditioner)
+  {
+    const int lc = 12;  // (local vertex, component)
+    std::vector<int32_t> colmap((size_t)nt * lc);
+    for (int32_t t = 0; t < nt; ++t)
+      for (int v = 0; v < 4; ++v)
+        for (int c = 0; c < 3; ++c) colmap[(size_t)t * lc + 3 * v + c] = 3 * m->tets[(size_t)t * 4 + v] + c;
+    std::vector<uint8_t> maskP((size_t)l1 * lc, 0), allv(3 * (size_t)nn, 1);
+    for (int j = 0; j < l1; ++j)
+      for (int v = 0; v < 4; ++v)
+        for (int c = 0; c < 3; ++c) {
+          bool nz = false;
+          if (p == 1) {
+            nz = kLocalEdges[j][0] == v || kLocalEdges[j][1] == v;
+          } else {
+            for (int a = 0; a < 4; ++a) nz = nz || T.Rv[(size_t)(4 * v + a) * l1 + j] != 0.0;
+          }
+          maskP[(size_t)j * lc + 3 * v + c] = nz;
+        }
+    build_pattern(m->n1, 3 * nn, nt, l1, lc, d1, colmap.data(), free1, allv, maskP, &m->Pi);
+    std::vector<double> loc((size_t)l1 * lc);
+    for (int32_t t = 0; t < nt; ++t) {
+      const int32_t* tv = &m->tets[(size_t)t * 4];
+      std::fill(loc.begin(), loc.end(), 0.0);
+      for (int j = 0; j < l1; ++j)
+        for (int v = 0; v < 4; ++v)
+          for (int c = 0; c < 3; ++c) {
+            double val = 0.0;
+            if (p == 1) {
+              int s0 = kLocalEdges[j][0], s1 = kLocalEdges[j][1];
+              if (s0 == v || s1 == v) val = 0.5 * (xyz[3 * (size_t)tv[s1] + c] - xyz[3 * (size_t)tv[s0] + c]);
+            } else {
+              for (int a = 0; a < 4; ++a) val += xyz[3 * (size_t)tv[a] + c] * T.Rv[(size_t)(4 * v + a) * l1 + j];
+            }
+            loc[(size_t)j * lc + 3 * v + c] = val;
+          }
+      scatter(&m->Pi, d1 + (size_t)t * l1, colmap.data() + (size_t)t * lc, l1, lc, loc.data(), free1, allv, true);
+    }
+    // transpose
+    HostCSR& P = m->Pi;
+    HostCSR& PT = m->PiT;
+    PT.n_rows = P.n_cols;
+    PT.n_cols = P.n_rows;
+    PT.rowptr.assign((size_t)PT.n_rows + 1, 0);
+    for (int32_t c : P.col) PT.rowptr[c + 1]++;
+    for (int32_t r = 0; r < PT.n_rows; ++r) PT.rowptr[r + 1] += PT.rowptr[r];
+    PT.col.resize(P.col.size());
+    PT.val.resize(P.col.size());
+    std::vector<int32_t> fillp(PT.rowptr.begin(), PT.rowptr.end() - 1);
+    for (int32_t r = 0; r < P.n_rows; ++r)
+      for (int32_t k = P.rowptr[r]; k < P.rowptr[r + 1]; ++k) {
+        int32_t c = P.col[k];
+        PT.col[fillp[c]] = r;
+        PT.val[fillp[c]] = P.val[k];
+        fillp[c]++;
+      }
+    // diag(Pi^T M Pi) and diag(Pi^T K Pi), one column of Pi at a time
+    m->dvM.assign(PT.n_rows, 0.0);
+    m->dvK.assign(PT.n_rows, 0.0);
+    parallel_for(PT.n_rows, [&](int64_t a, int64_t b) {
+      std::vector<double> dense((size_t)m->n1, 0.0);
+      for (int64_t c = a; c < b; ++c) {
+        for (int32_t k = PT.rowptr[c]; k < PT.rowptr[c + 1]; ++k) dense[PT.col[k]] = PT.val[k];
+        double sm = 0.0, sk = 0.0;
+        for (int32_t k = PT.rowptr[c]; k < PT.rowptr[c + 1]; ++k) {
+          int32_t i = PT.col[k];
+          double pi = PT.val[k];
+          for (int32_t q = m->M.rowptr[i]; q < m->M.rowptr[i + 1]; ++q) {
+            double pj = dense[m->M.col[q]];
+            if (pj != 0.0) {
+              sm += pi * m->M.val[q] * pj;
+              sk += pi * m->K.val[q] * pj;
+            }
+          }
+        }
+        m->dvM[c] = sm;
+        m->dvK[c] = sk;
+        for (int32_t k = PT.rowptr[c]; k < PT.rowptr[c + 1]; ++k) dense[PT.col[k]] = 0.0;
+      }
+    });
   }
   return 0;
 }

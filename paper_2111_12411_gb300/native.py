@@ -22,7 +22,7 @@ PRECISION = {"fp64_strict": 0, "fp64": 1, "mixed": 2}
 SCHEME = {"trapezoid": 0, "wave": 1}
 QUANTITY = {"E": 0, "B": 1, "DG": 2, "RHO": 3, "X": 4, "V": 5, "TET": 6, "NCROSS": 7, "HASH": 8,
             "E_PREV": 9, "DG_PREV": 10, "DIAG": 11, "PHI": 12}
-OPERATOR = {"M1": 0, "K": 1, "C": 2, "D": 3, "DT": 4, "M2": 5, "A": 6, "L": 7}
+OPERATOR = {"M1": 0, "K": 1, "C": 2, "D": 3, "DT": 4, "M2": 5, "A": 6, "L": 7, "PI": 8, "PIT": 9}
 
 
 class femPIC_mesh(ctypes.Structure):
@@ -61,7 +61,7 @@ class femPIC_info(ctypes.Structure):
                 ("n2", ctypes.c_int32), ("nl0", ctypes.c_int32), ("nl1", ctypes.c_int32),
                 ("nl2", ctypes.c_int32), ("n_particles", ctypes.c_int64),
                 ("nnz_A", ctypes.c_int64), ("nnz_C", ctypes.c_int64), ("nnz_Q", ctypes.c_int64),
-                ("nnz_D", ctypes.c_int64), ("nnz_DT", ctypes.c_int64),
+                ("nnz_D", ctypes.c_int64), ("nnz_DT", ctypes.c_int64), ("nnz_Pi", ctypes.c_int64),
                 ("n_boundary_faces", ctypes.c_int32), ("device_bytes", ctypes.c_size_t)]
 
 
@@ -308,7 +308,7 @@ class Simulation:
     def apply(self, op, x):
         i = self.info
         rows = {"M1": i.n1, "K": i.n1, "C": i.n2, "D": i.n1, "DT": i.n0, "M2": i.n2, "A": i.n1,
-                "L": i.n0}[op]
+                "L": i.n0, "PI": i.n1, "PIT": 3 * i.n_nodes}[op]
         return femPIC_apply(self.h, op, x, rows)
 
     def eval_fields(self, x, tet):

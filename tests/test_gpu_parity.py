@@ -247,3 +247,36 @@ def test_mixed_precision_step(c1small, order):
     assert d["continuity_abs"] <= 1e-12 * d["continuity_ref"]
     assert rel(g.get("DG"), w["dg"]) < 1e-4
     g.close()
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_vector_interpolation_operator(c1small, order):
+    """Pi maps nodal values of a linear vector field F = G x + a to W1 DOFs:
+    at order 2 the exact coefficients of F (in the space; oracle L2
+    projection), at order 1 the edge moments (F(x_s) + F(x_t))/2 . (x_t - x_s);
+    PEC rows are removed."""
+    import scipy.sparse.linalg as spla
+    from oracle import assemble, basis as obasis, quadrature
+    o, g = pair(c1small, order=order, es_init=False)
+    t = o.topo
+    rng = np.random.default_rng(6)
+    G, a0 = rng.normal(size=(3, 3)), rng.normal(size=3)
+    F = t.xyz @ G.T + a0
+    y = g.apply("PI", F.reshape(-1))
+    fr = t.free1
+    if order == 1:
+        xs, xt = t.xyz[t.edges[:, 0]], t.xyz[t.edges[:, 1]]
+        want = np.einsum("ij,ij->i", 0.5 * (F[t.edges[:, 0]] + F[t.edges[:, 1]]), xt - xs)
+    else:
+        lam_q, w_q = quadrature.tet_rule(4)
+        f = np.zeros(t.n1)
+        xq = np.einsum("qk,tkd->tqd", lam_q, t.xyz[t.tets])
+        for tt in range(t.n_tets):
+            w = obasis.w1(2, lam_q, np.broadcast_to(o.g[tt], (len(lam_q), 4, 3)))
+            np.add.at(f, t.dof1[tt], 6 * o.vol[tt] * np.einsum("q,qik,qk->i", w_q, w, xq[tt] @ G.T + a0))
+        want = spla.spsolve((o.M / assemble.EPS0).tocsc(), f)
+    assert rel(y[fr], want[fr]) < 1e-12
+    assert np.all(y[~fr] == 0.0)
+    x1 = rng.normal(size=t.n1)
+    assert abs(g.apply("PIT", x1) @ F.reshape(-1) - x1 @ y) < 1e-10 * np.abs(x1 @ y)
+    g.close()
