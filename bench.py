@@ -46,14 +46,14 @@ def measured_peaks():
 
 # ---- algorithmic bytes ---------------------------------------------------------------
 def pcg_bytes_per_iteration(info):
-    """Bytes one preconditioned CG iteration must move: the A, D, D^T, Pi and
-    Pi^T CSR arrays (8 B value + 4 B column per entry, 4 B row pointer per
-    row) once, and the vector passes (SpMV: p gather + q write; update: x, p,
+    """Bytes one preconditioned CG iteration must move: the A CSR arrays (8 B
+    value + 4 B column per entry), the FP32 D, D^T, Pi and Pi^T arrays of the
+    preconditioner (4 B value + 4 B column), 4 B row pointers, and the vector passes (SpMV: p gather + q write; update: x, p,
     q, r read, x, r write; auxiliary corrections: r, t, u, dinv, dinv_L,
     dinv_V reads, t, u, z writes; direction update: p, z read, p write)."""
     n1, n0 = info.n1, info.n0
     nv = 3 * info.n_nodes
-    mats = 12 * (info.nnz_A + info.nnz_D + info.nnz_DT + 2 * info.nnz_Pi) + 4 * (3 * n1 + n0 + nv)
+    mats = 12 * info.nnz_A + 8 * (info.nnz_D + info.nnz_DT + 2 * info.nnz_Pi) + 4 * (3 * n1 + n0 + nv)
     vec = 8 * (2 * n1 + 6 * n1 + (2 * n1 + 2 * n0 + n1 + n0) + (2 * nv + nv) + n1 + 3 * n1)
     return mats + vec
 

@@ -60,6 +60,7 @@ def build(force=False, verbose=False, ptxas_info=False):
          os.path.join(CSRC, "setup.cpp"), "-o", host_o],
         [nvcc, "-O3", "-std=c++17", "-lineinfo", ARCH, "-Xcompiler", "-fPIC,-ffp-contract=off",
          "-I" + INCLUDE, "-c", os.path.join(CSRC, "fempic.cu"), "-o", dev_o]
+        + os.environ.get("FEMPIC_NVCC_FLAGS", "").split()
         + (["-Xptxas", "-v"] if ptxas_info else []),
     ]
     with ThreadPoolExecutor(2) as ex:

@@ -43,18 +43,18 @@ struct MemberDesc {
   int32_t* cnt;
   int32_t* off;
   double *e, *e_prev, *e_new, *b, *dg, *dg_prev, *rho, *rho_prev;
-  CsrView A, R1, Q, C, D, DT;
+  CsrView A, R1, Q, C;
   const double* dinvA;
-  const double* dinvL;
-  CsrView Pi, PiT;
-  const double* dinvV;
-  double* u;
+  CsrView32 D, DT, Pi, PiT;  // FP32 preconditioner operators
+  const float* dinvL;
+  const float* dinvV;
+  float* t;
+  float* u;
   double* rhs;
   double* r[2];
   double* z;
   double* p[2];
   double* q;
-  double* t;
   int32_t* status;
   int32_t* cg_iters;
   double* cg_res;
@@ -402,23 +402,42 @@ __device__ __forceinline__ double member_z(const MemberDesc& d, const double* rv
   for (int i = tid / 4; ; i += groups) {
     bool act = i < d.n1;
     if (!__any_sync(0xffffffffu, act)) break;
-    double s = 0.0;
+    float s = 0.f;
     if (act) {
       for (int k = __ldg(d.D.rp + i) + lane; k < __ldg(d.D.rp + i + 1); k += 4)
-        s = fma(__ldg(d.D.v + k), __ldcg(d.t + __ldg(d.D.ci + k)), s);
+        s = fmaf(__ldg(d.D.v + k), __ldcg(d.t + __ldg(d.D.ci + k)), s);
       for (int k = __ldg(d.Pi.rp + i) + lane; k < __ldg(d.Pi.rp + i + 1); k += 4)
-        s = fma(__ldg(d.Pi.v + k), __ldcg(d.u + __ldg(d.Pi.ci + k)), s);
+        s = fmaf(__ldg(d.Pi.v + k), __ldcg(d.u + __ldg(d.Pi.ci + k)), s);
     }
 #pragma unroll
     for (int o = 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 4);
     if (act && (tid & 3) == 0) {
       double rr = __ldcg(rvec + i);
-      double zz = fma(__ldg(d.dinvA + i), rr, s);
+      double zz = fma(__ldg(d.dinvA + i), rr, (double)s);
       d.z[i] = zz;
       rz += rr * zz;
     }
   }
   return rz;
+}
+
+// FP32 rows of one member
+template <int LPR, class X, class F>
+__device__ __forceinline__ void member_rows32(const CsrView32& A, int tid, int tcount, X x_of, F emit) {
+  const int lane = tid % LPR;
+  const int groups = tcount / LPR;
+  for (int r0 = tid / LPR; ; r0 += groups) {
+    bool act = r0 < A.n_rows;
+    if (!__any_sync(0xffffffffu, act)) break;
+    float s = 0.f;
+    if (act) {
+      int beg = __ldg(A.rp + r0), end = __ldg(A.rp + r0 + 1);
+      for (int k = beg + lane; k < end; k += LPR) s = fmaf(__ldg(A.v + k), x_of(__ldg(A.ci + k)), s);
+    }
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
+    if (act && lane == 0) emit(r0, s);
+  }
 }
 
 // Every CTA runs the same number of iterations and barriers; a CTA whose
@@ -446,10 +465,10 @@ __global__ void __launch_bounds__(256) k_batch_pcg(BatchWork w, int max_it_all) 
         acc[2] += b * b;
       });
   if (!grid_sync(w.bar, w.status)) return;
-  member_rows<4>(d.DT, tid, tcount, [&](int c) { return __ldcg(r_cur + c); },
-                 [&](int k, double s) { d.t[k] = __ldg(d.dinvL + k) * s; });
-  member_rows<4>(d.PiT, tid, tcount, [&](int c) { return __ldcg(r_cur + c); },
-                 [&](int k, double s) { d.u[k] = __ldg(d.dinvV + k) * s; });
+  member_rows32<4>(d.DT, tid, tcount, [&](int c) { return (float)__ldcg(r_cur + c); },
+                   [&](int k, float s) { d.t[k] = __ldg(d.dinvL + k) * s; });
+  member_rows32<4>(d.PiT, tid, tcount, [&](int c) { return (float)__ldcg(r_cur + c); },
+                   [&](int k, float s) { d.u[k] = __ldg(d.dinvV + k) * s; });
   if (!grid_sync(w.bar, w.status)) return;
   acc[0] += member_z(d, r_cur, tid, tcount);
   block_partials<4>(acc, part[1]);
@@ -515,10 +534,13 @@ __global__ void __launch_bounds__(256) k_batch_pcg(BatchWork w, int max_it_all) 
         r_new[i] = rr;
         acc2[1] += rr * rr;
       }
-      member_rows<4>(d.DT, tid, tcount, [&](int c) { return fma(-alpha, __ldcg(d.q + c), __ldcg(r_old + c)); },
-                     [&](int k, double s) { d.t[k] = __ldg(d.dinvL + k) * s; });
-      member_rows<4>(d.PiT, tid, tcount, [&](int c) { return fma(-alpha, __ldcg(d.q + c), __ldcg(r_old + c)); },
-                     [&](int k, double s) { d.u[k] = __ldg(d.dinvV + k) * s; });
+      const float a32 = (float)alpha;
+      member_rows32<4>(d.DT, tid, tcount,
+                       [&](int c) { return fmaf(-a32, (float)__ldcg(d.q + c), (float)__ldcg(r_old + c)); },
+                       [&](int k, float s) { d.t[k] = __ldg(d.dinvL + k) * s; });
+      member_rows32<4>(d.PiT, tid, tcount,
+                       [&](int c) { return fmaf(-a32, (float)__ldcg(d.q + c), (float)__ldcg(r_old + c)); },
+                       [&](int k, float s) { d.u[k] = __ldg(d.dinvV + k) * s; });
     }
     if (!grid_sync(w.bar, w.status)) return;
     if (work) acc2[0] += member_z(d, r_new, tid, tcount);

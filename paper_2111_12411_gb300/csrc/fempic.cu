@@ -62,7 +62,10 @@ struct FemPIC {
   double* load0 = nullptr;
   // matrices
   DevCSR M, K, Q, C, M2, D, DT, L, Pi, PiT;
-  double *dvM = nullptr, *dvK = nullptr, *dinvV = nullptr, *aux_u = nullptr;
+  double *dvM = nullptr, *dvK = nullptr;
+  // FP32 copies for the preconditioner's auxiliary-space corrections
+  float *D32 = nullptr, *DT32 = nullptr, *Pi32 = nullptr, *PiT32 = nullptr;
+  float *dinvL32 = nullptr, *dinvV = nullptr, *aux_t = nullptr, *aux_u = nullptr;
   double *Aval = nullptr, *R1val = nullptr, *R2val = nullptr, *dinvA = nullptr, *dinvL = nullptr;
   // fields
   double *e = nullptr, *e_prev = nullptr, *e_new = nullptr, *b = nullptr, *dg = nullptr, *dg_prev = nullptr;
@@ -146,13 +149,20 @@ int upload_csr(FemPIC* h, DevCSR* d, const HostCSR& s) {
   return rc;
 }
 
+CsrView32 view32(const DevCSR& m, const float* v) { return CsrView32{m.n_rows, m.rp, m.ci, v}; }
+
 inline int grid_for(int64_t work, int block, int cap) {
   int64_t g = (work + block - 1) / block;
   if (g < 1) g = 1;
   return (int)std::min<int64_t>(g, cap);
 }
 
-int lpr_w1(const FemPIC* h) { return h->order == 1 ? 4 : 8; }
+// lanes per CSR row of the order-2 system matrix (rows of ~30-75 entries);
+// 4 measured faster than 8 and 16 in the persistent CG
+#ifndef FEMPIC_LPR_P2
+#define FEMPIC_LPR_P2 4
+#endif
+int lpr_w1(const FemPIC* h) { return h->order == 1 ? 4 : FEMPIC_LPR_P2; }
 
 int latch_status(FemPIC* h) {
   int32_t st = 0;
@@ -205,12 +215,12 @@ int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, 
   PcgArgs a;
   a.A = A;
   a.dinv = dinv;
-  a.D = nodal ? h->D.view() : CsrView{0, nullptr, nullptr, nullptr};
-  a.DT = nodal ? h->DT.view() : CsrView{0, nullptr, nullptr, nullptr};
-  a.dinvL = h->dinvL;
-  a.t = h->d_tmp0;
-  a.Pi = nodal ? h->Pi.view() : CsrView{0, nullptr, nullptr, nullptr};
-  a.PiT = nodal ? h->PiT.view() : CsrView{0, nullptr, nullptr, nullptr};
+  a.D = nodal ? view32(h->D, h->D32) : CsrView32{0, nullptr, nullptr, nullptr};
+  a.DT = nodal ? view32(h->DT, h->DT32) : CsrView32{0, nullptr, nullptr, nullptr};
+  a.dinvL = h->dinvL32;
+  a.t = h->aux_t;
+  a.Pi = nodal ? view32(h->Pi, h->Pi32) : CsrView32{0, nullptr, nullptr, nullptr};
+  a.PiT = nodal ? view32(h->PiT, h->PiT32) : CsrView32{0, nullptr, nullptr, nullptr};
   a.dinvV = h->dinvV;
   a.u = h->aux_u;
   a.rhs = rhs;
@@ -234,7 +244,7 @@ int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, 
   if (h->order == 1)
     CK(cudaLaunchCooperativeKernel((void*)k_pcg<4>, blocks, 256, args, 0, h->stream));
   else
-    CK(cudaLaunchCooperativeKernel((void*)k_pcg<8>, blocks, 256, args, 0, h->stream));
+    CK(cudaLaunchCooperativeKernel((void*)k_pcg<FEMPIC_LPR_P2>, blocks, 256, args, 0, h->stream));
   h->launches++;
   return FEMPIC_OK;
 }
@@ -792,8 +802,19 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
       (rc = upload_csr(h, &h->DT, hm.DT)) || (rc = upload_csr(h, &h->L, hm.L)) ||
       (rc = upload_csr(h, &h->Pi, hm.Pi)) || (rc = upload_csr(h, &h->PiT, hm.PiT)) ||
       (rc = upload(h, &h->dvM, hm.dvM)) || (rc = upload(h, &h->dvK, hm.dvK)) ||
-      (rc = dalloc(h, &h->dinvV, hm.PiT.n_rows)) || (rc = dalloc(h, &h->aux_u, hm.PiT.n_rows)))
+      (rc = dalloc(h, &h->dinvV, hm.PiT.n_rows)) || (rc = dalloc(h, &h->aux_u, hm.PiT.n_rows)) ||
+      (rc = dalloc(h, &h->aux_t, hm.n0)) || (rc = dalloc(h, &h->dinvL32, hm.n0)) ||
+      (rc = dalloc(h, &h->D32, hm.D.col.size())) || (rc = dalloc(h, &h->DT32, hm.DT.col.size())) ||
+      (rc = dalloc(h, &h->Pi32, hm.Pi.col.size())) || (rc = dalloc(h, &h->PiT32, hm.PiT.col.size())))
     return rc;
+  {
+    const std::pair<const double*, float*> cv[] = {{h->D.v, h->D32}, {h->DT.v, h->DT32}, {h->Pi.v, h->Pi32},
+                                                   {h->PiT.v, h->PiT32}};
+    const int64_t nn[] = {h->D.nnz, h->DT.nnz, h->Pi.nnz, h->PiT.nnz};
+    for (int k = 0; k < 4; ++k)
+      if (nn[k] > 0) k_to_f32<<<grid_for(nn[k], 256, 4096), 256, 0, h->stream>>>(nn[k], cv[k].first, cv[k].second);
+    CK(cudaGetLastError());
+  }
   const size_t nnz = hm.M.col.size();
   if ((rc = dalloc(h, &h->Aval, nnz)) || (rc = dalloc(h, &h->R1val, nnz)) ||
       (rc = dalloc(h, &h->R2val, o.scheme == FEMPIC_SCHEME_WAVE ? nnz : 1)) || (rc = dalloc(h, &h->dinvA, h->n1)) ||
@@ -816,7 +837,7 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
     if (bl < 0) return FEMPIC_ERR_CUDA;
     h->pcg_blocks_w1 = h->pcg_blocks_w0 = bl;
   } else {
-    int bl = pcg_blocks<8>(h);
+    int bl = pcg_blocks<FEMPIC_LPR_P2>(h);
     if (bl < 0) return FEMPIC_ERR_CUDA;
     h->pcg_blocks_w1 = h->pcg_blocks_w0 = bl;
   }
@@ -871,6 +892,7 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
   {
     int grid = grid_for(h->n0, 256, 1 << 30);
     k_inv_diag<<<grid, 256, 0, h->stream>>>(h->n0, h->L.rp, h->L.ci, h->L.v, h->dinvL);
+    k_to_f32<<<grid, 256, 0, h->stream>>>(h->n0, h->dinvL, h->dinvL32);
     CK(cudaGetLastError());
   }
   // electrostatic start: L phi = rho + rho_ion <W0, 1> on interior DOFs, e = -D phi
@@ -1298,12 +1320,13 @@ MemberDesc describe(FemPIC* h, double dt) {
   d.R1 = h->M.view(h->R1val);
   d.Q = h->Q.view();
   d.C = h->C.view();
-  d.D = h->D.view();
-  d.DT = h->DT.view();
   d.dinvA = h->dinvA;
-  d.dinvL = h->dinvL;
-  d.Pi = h->Pi.view();
-  d.PiT = h->PiT.view();
+  d.D = view32(h->D, h->D32);
+  d.DT = view32(h->DT, h->DT32);
+  d.dinvL = h->dinvL32;
+  d.t = h->aux_t;
+  d.Pi = view32(h->Pi, h->Pi32);
+  d.PiT = view32(h->PiT, h->PiT32);
   d.dinvV = h->dinvV;
   d.u = h->aux_u;
   d.rhs = h->rhs;
@@ -1313,7 +1336,6 @@ MemberDesc describe(FemPIC* h, double dt) {
   d.p[0] = h->cg_p;
   d.p[1] = h->cg_p2;
   d.q = h->cg_q;
-  d.t = h->d_tmp0;
   d.status = h->d_status;
   d.cg_iters = h->d_cg_iters;
   d.cg_res = h->d_cg_res;

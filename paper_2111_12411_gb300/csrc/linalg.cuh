@@ -19,6 +19,19 @@ struct CsrView {
   const double* v;
 };
 
+// FP32 values: used for the preconditioner's auxiliary-space operators
+struct CsrView32 {
+  int32_t n_rows;
+  const int32_t* rp;
+  const int32_t* ci;
+  const float* v;
+};
+
+__global__ void k_to_f32(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
 // y = alpha * A x (+ beta * y)
 template <int LPR>
 __global__ void k_spmv(CsrView A, const double* __restrict__ x, double* __restrict__ y, double alpha, double beta) {
@@ -111,12 +124,12 @@ __global__ void k_lincomb(int32_t n, const double* __restrict__ x, const double*
     out[i] = a * x[i] + b * y[i];
 }
 
-// dinvV = 1 / (dvM + c dvK), 0 where the sum vanishes
-__global__ void k_form_dv(int32_t n, const double* dvm, const double* dvk, double c, double* dinv) {
+// dinvV = 1 / (dvM + c dvK), 0 where the sum vanishes (FP32 for the preconditioner)
+__global__ void k_form_dv(int32_t n, const double* dvm, const double* dvk, double c, float* dinv) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double d = dvm[i] + c * dvk[i];
-  dinv[i] = d > 0.0 ? 1.0 / d : 0.0;
+  dinv[i] = d > 0.0 ? (float)(1.0 / d) : 0.f;
 }
 
 // A = M + ca K, R = M + cr K (same pattern), inverse diagonal of A (0 on empty rows)
@@ -186,18 +199,17 @@ __device__ bool grid_sync(GridBarrier* bar, int32_t* status) {
 struct PcgArgs {
   CsrView A;
   const double* dinv;
-  // optional auxiliary nodal correction of the preconditioner:
-  // z = dinv r + D (dinvL (D^T r)); DT.n_rows == 0 disables it
-  CsrView D;
-  CsrView DT;
-  const double* dinvL;
-  double* t;   // [DT.n_rows] scratch
-  // vector nodal auxiliary space (used with the nodal correction):
-  // z += Pi (dinvV (Pi^T r))
-  CsrView Pi;
-  CsrView PiT;
-  const double* dinvV;
-  double* u;   // [PiT.n_rows] scratch
+  // optional auxiliary-space corrections of the preconditioner, applied in
+  // FP32: z = dinv r + D (dinvL (D^T r)) + Pi (dinvV (Pi^T r));
+  // DT.n_rows == 0 disables both
+  CsrView32 D;
+  CsrView32 DT;
+  const float* dinvL;
+  float* t;    // [DT.n_rows] scratch
+  CsrView32 Pi;
+  CsrView32 PiT;
+  const float* dinvV;
+  float* u;    // [PiT.n_rows] scratch
   const double* rhs;
   double* x;   // in: initial guess, out: solution
   double* r[2];  // residual, double-buffered
@@ -279,6 +291,24 @@ __device__ __forceinline__ void rows_spmv(const CsrView& A, int gid, int groups,
   }
 }
 
+// FP32 row products: y_r = sum_k A_rk f(k), LPR lanes per row
+template <int LPR, class X, class F>
+__device__ __forceinline__ void rows_spmv32(const CsrView32& A, int gid, int groups, X x_of, F emit) {
+  const int lane = gid % LPR;
+  for (int r0 = gid / LPR; ; r0 += groups) {
+    bool act = r0 < A.n_rows;
+    if (!__any_sync(0xffffffffu, act)) break;
+    float s = 0.f;
+    if (act) {
+      int beg = __ldg(A.rp + r0), end = __ldg(A.rp + r0 + 1);
+      for (int k = beg + lane; k < end; k += LPR) s = fmaf(__ldg(A.v + k), x_of(__ldg(A.ci + k)), s);
+    }
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
+    if (act && lane == 0) emit(r0, s);
+  }
+}
+
 // z_i = dinv_i r_i + (D t)_i + (Pi u)_i for the rows this group owns; returns r.z part
 template <int LPR>
 __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, int gid, int tpg) {
@@ -289,19 +319,19 @@ __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, in
   for (int i = gid / LPR; ; i += groups) {
     bool act = i < a.D.n_rows;
     if (!__any_sync(0xffffffffu, act)) break;
-    double s = 0.0;
+    float s = 0.f;
     if (act) {
       for (int k = __ldg(a.D.rp + i) + lane; k < __ldg(a.D.rp + i + 1); k += LPR)
-        s = fma(__ldg(a.D.v + k), __ldcg(a.t + __ldg(a.D.ci + k)), s);
+        s = fmaf(__ldg(a.D.v + k), __ldcg(a.t + __ldg(a.D.ci + k)), s);
       if (vec)
         for (int k = __ldg(a.Pi.rp + i) + lane; k < __ldg(a.Pi.rp + i + 1); k += LPR)
-          s = fma(__ldg(a.Pi.v + k), __ldcg(a.u + __ldg(a.Pi.ci + k)), s);
+          s = fmaf(__ldg(a.Pi.v + k), __ldcg(a.u + __ldg(a.Pi.ci + k)), s);
     }
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
     if (act && lane == 0) {
       double rr = __ldcg(rvec + i);
-      double zz = fma(__ldg(a.dinv + i), rr, s);
+      double zz = fma(__ldg(a.dinv + i), rr, (double)s);
       a.z[i] = zz;
       rz += rr * zz;
     }
@@ -316,8 +346,14 @@ __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, in
 //   phase 2: x += alpha p, r' = r - alpha q; t = dinvL (D^T r') with r' formed
 //            on the fly; barrier
 //   phase 3: z = dinv r' + D t; barrier; rz', r'.r' -> convergence, beta
+// Register cap of the persistent CG kernel: 8 co-resident 256-thread CTAs per
+// SM (<= 32 registers) measured fastest on the drift-tube system (memory
+// latency bound: more warps in flight beat fewer spills).
+#ifndef FEMPIC_PCG_MIN_BLOCKS
+#define FEMPIC_PCG_MIN_BLOCKS 8
+#endif
 template <int LPR>
-__global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
+__global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
   const int n = a.A.n_rows;
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int tpg = gridDim.x * blockDim.x;
@@ -342,11 +378,11 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
       });
   if (nodal) {
     if (!grid_sync(a.bar, a.status)) return;
-    rows_spmv<4>(a.DT, gid, tpg / 4, [&](int c) { return __ldcg(r_cur + c); },
-                 [&](int k, double s) { a.t[k] = __ldg(a.dinvL + k) * s; });
+    rows_spmv32<4>(a.DT, gid, tpg / 4, [&](int c) { return (float)__ldcg(r_cur + c); },
+                   [&](int k, float s) { a.t[k] = __ldg(a.dinvL + k) * s; });
     if (a.PiT.n_rows > 0)
-      rows_spmv<4>(a.PiT, gid, tpg / 4, [&](int c) { return __ldcg(r_cur + c); },
-                   [&](int k, double s) { a.u[k] = __ldg(a.dinvV + k) * s; });
+      rows_spmv32<4>(a.PiT, gid, tpg / 4, [&](int c) { return (float)__ldcg(r_cur + c); },
+                     [&](int k, float s) { a.u[k] = __ldg(a.dinvV + k) * s; });
     if (!grid_sync(a.bar, a.status)) return;
     acc[0] += aux_z<4>(a, r_cur, gid, tpg);
   }
@@ -404,13 +440,14 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
       }
     }
     if (nodal) {
-      rows_spmv<4>(a.DT, gid, tpg / 4,
-                   [&](int c) { return fma(-alpha, __ldcg(a.q + c), __ldcg(r_old + c)); },
-                   [&](int k, double s) { a.t[k] = __ldg(a.dinvL + k) * s; });
+      const float alpha32 = (float)alpha;
+      rows_spmv32<4>(a.DT, gid, tpg / 4,
+                     [&](int c) { return fmaf(-alpha32, (float)__ldcg(a.q + c), (float)__ldcg(r_old + c)); },
+                     [&](int k, float s) { a.t[k] = __ldg(a.dinvL + k) * s; });
       if (a.PiT.n_rows > 0)
-        rows_spmv<4>(a.PiT, gid, tpg / 4,
-                     [&](int c) { return fma(-alpha, __ldcg(a.q + c), __ldcg(r_old + c)); },
-                     [&](int k, double s) { a.u[k] = __ldg(a.dinvV + k) * s; });
+        rows_spmv32<4>(a.PiT, gid, tpg / 4,
+                       [&](int c) { return fmaf(-alpha32, (float)__ldcg(a.q + c), (float)__ldcg(r_old + c)); },
+                       [&](int k, float s) { a.u[k] = __ldg(a.dinvV + k) * s; });
       if (!grid_sync(a.bar, a.status)) return;
       // phase 3: z = dinv r' + D t + Pi u
       acc2[0] += aux_z<4>(a, r_new, gid, tpg);
