@@ -62,6 +62,11 @@ struct FemPIC {
   double* load0 = nullptr;
   // matrices
   DevCSR M, K, Q, C, M2, D, DT, L, Pi, PiT;
+  // order 2: the W1 system in 2x2 blocks (DOF pairs of one edge or face)
+  int32_t nb = 0;
+  int64_t nnzb = 0;
+  int32_t *brp = nullptr, *bci = nullptr;
+  double *bM = nullptr, *bK = nullptr, *bA = nullptr, *binv = nullptr;
   double *dvM = nullptr, *dvK = nullptr;
   // FP32 copies for the preconditioner's auxiliary-space corrections
   float *D32 = nullptr, *DT32 = nullptr, *Pi32 = nullptr, *PiT32 = nullptr;
@@ -72,7 +77,8 @@ struct FemPIC {
   double *rho = nullptr, *rho_prev = nullptr, *phi = nullptr, *rhs = nullptr;
   // CG scratch
   double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *partials = nullptr;
-  double *cg_r2 = nullptr, *cg_p2 = nullptr;
+  double *cg_r2 = nullptr, *cg_p2 = nullptr, *cg_red = nullptr;
+  float *cg_q32 = nullptr, *cg_r32 = nullptr;
   GridBarrier* bar = nullptr;
   int pcg_blocks_w1 = 0, pcg_blocks_w0 = 0;
   // particles (device order), SoA
@@ -223,6 +229,11 @@ int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, 
   a.PiT = nodal ? view32(h->PiT, h->PiT32) : CsrView32{0, nullptr, nullptr, nullptr};
   a.dinvV = h->dinvV;
   a.u = h->aux_u;
+  a.Ab = (nodal && h->nb > 0) ? BsrView{h->nb, h->brp, h->bci, h->bA} : BsrView{0, nullptr, nullptr, nullptr};
+  a.q32 = h->cg_q32;
+  a.r32 = h->cg_r32;
+  a.red = h->cg_red;
+  a.binv = h->binv;
   a.rhs = rhs;
   a.x = x;
   a.r[0] = h->cg_r;
@@ -240,6 +251,7 @@ int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, 
   a.rtol = h->opts.cg_rtol;
   a.max_it = h->opts.cg_max_it;
   CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), h->stream));
+  CK(cudaMemsetAsync(h->cg_red, 0, 12 * sizeof(double), h->stream));
   void* args[] = {&a};
   if (h->order == 1)
     CK(cudaLaunchCooperativeKernel((void*)k_pcg<4>, blocks, 256, args, 0, h->stream));
@@ -282,6 +294,11 @@ int form_system(FemPIC* h, double dt) {
   }
   k_form_dv<<<grid_for(h->PiT.n_rows, 256, 1 << 30), 256, 0, h->stream>>>(h->PiT.n_rows, h->dvM, h->dvK, c1,
                                                                             h->dinvV);
+  if (h->nb > 0) {
+    k_form_blocks<<<grid_for(h->nb, 256, 1 << 30), 256, 0, h->stream>>>(h->nb, h->brp, h->bci, h->bM, h->bK, c1,
+                                                                        h->bA, h->binv);
+    h->launches++;
+  }
   h->launches++;
   CK(cudaGetLastError());
   h->dt_cur = dt;
@@ -815,6 +832,41 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
       if (nn[k] > 0) k_to_f32<<<grid_for(nn[k], 256, 4096), 256, 0, h->stream>>>(nn[k], cv[k].first, cv[k].second);
     CK(cudaGetLastError());
   }
+  if (order == 2) {
+    // DOFs 2k, 2k+1 belong to one edge or face and share their couplings
+    const int32_t nb = hm.n1 / 2;
+    std::vector<int32_t> brp(nb + 1, 0), bci;
+    std::vector<double> bM, bK;
+    bool ok = (hm.n1 % 2) == 0;
+    for (int32_t k = 0; k < nb && ok; ++k) {
+      int32_t r0 = 2 * k, r1 = 2 * k + 1;
+      int32_t b0 = hm.M.rowptr[r0], e0 = hm.M.rowptr[r0 + 1], b1 = hm.M.rowptr[r1];
+      if (e0 - b0 != hm.M.rowptr[r1 + 1] - b1 || (e0 - b0) % 2) {
+        ok = false;
+        break;
+      }
+      for (int32_t j = b0; j < e0; j += 2) {
+        int32_t c = hm.M.col[j];
+        if ((c & 1) || hm.M.col[j + 1] != c + 1 || hm.M.col[b1 + (j - b0)] != c ||
+            hm.M.col[b1 + (j - b0) + 1] != c + 1) {
+          ok = false;
+          break;
+        }
+        bci.push_back(c / 2);
+        const int32_t q0 = j, q1 = b1 + (j - b0);
+        bM.insert(bM.end(), {hm.M.val[q0], hm.M.val[q0 + 1], hm.M.val[q1], hm.M.val[q1 + 1]});
+        bK.insert(bK.end(), {hm.K.val[q0], hm.K.val[q0 + 1], hm.K.val[q1], hm.K.val[q1 + 1]});
+      }
+      brp[k + 1] = (int32_t)bci.size();
+    }
+    if (ok) {
+      h->nb = nb;
+      h->nnzb = (int64_t)bci.size();
+      if ((rc = upload(h, &h->brp, brp)) || (rc = upload(h, &h->bci, bci)) || (rc = upload(h, &h->bM, bM)) ||
+          (rc = upload(h, &h->bK, bK)) || (rc = dalloc(h, &h->bA, bM.size())) || (rc = dalloc(h, &h->binv, 4 * (size_t)nb)))
+        return rc;
+    }
+  }
   const size_t nnz = hm.M.col.size();
   if ((rc = dalloc(h, &h->Aval, nnz)) || (rc = dalloc(h, &h->R1val, nnz)) ||
       (rc = dalloc(h, &h->R2val, o.scheme == FEMPIC_SCHEME_WAVE ? nnz : 1)) || (rc = dalloc(h, &h->dinvA, h->n1)) ||
@@ -841,6 +893,9 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
     if (bl < 0) return FEMPIC_ERR_CUDA;
     h->pcg_blocks_w1 = h->pcg_blocks_w0 = bl;
   }
+  if ((rc = dalloc(h, &h->cg_q32, nmax)) || (rc = dalloc(h, &h->cg_r32, 2 * (size_t)nmax)) ||
+      (rc = dalloc(h, &h->cg_red, 12)))
+    return rc;
   if ((rc = dalloc(h, &h->partials, 8 * (size_t)h->pcg_blocks_w1)) || (rc = dalloc(h, &h->bar, 1)) ||
       (rc = dalloc(h, &h->d_status, 1)) || (rc = dalloc(h, &h->d_cg_iters, 1)) || (rc = dalloc(h, &h->d_cg_res, 1)) ||
       (rc = dalloc(h, &h->d_cg_iters_acc, 1)) ||

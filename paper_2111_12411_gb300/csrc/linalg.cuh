@@ -19,6 +19,15 @@ struct CsrView {
   const double* v;
 };
 
+// 2x2-block CSR: block row k holds DOF rows 2k, 2k+1; each block is stored
+// row-major (a00 a01 a10 a11) and multiplies DOFs 2c, 2c+1 of block column c
+struct BsrView {
+  int32_t nb;
+  const int32_t* rp;
+  const int32_t* ci;
+  const double* v;
+};
+
 // FP32 values: used for the preconditioner's auxiliary-space operators
 struct CsrView32 {
   int32_t n_rows;
@@ -147,6 +156,28 @@ __global__ void k_form_system(int32_t n, const int32_t* rp, const int32_t* ci, c
   dinv[row] = diag != 0.0 ? 1.0 / diag : 0.0;
 }
 
+// 2x2 blocks: Ab = bM + c bK and the inverse of each diagonal block (0 if absent)
+__global__ void k_form_blocks(int32_t nb, const int32_t* rp, const int32_t* ci, const double* bm, const double* bk,
+                              double c, double* ab, double* binv) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nb) return;
+  double d[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int j = rp[k]; j < rp[k + 1]; ++j) {
+    for (int q = 0; q < 4; ++q) ab[4 * j + q] = bm[4 * j + q] + c * bk[4 * j + q];
+    if (ci[j] == k)
+      for (int q = 0; q < 4; ++q) d[q] = ab[4 * j + q];
+  }
+  double det = d[0] * d[3] - d[1] * d[2];
+  if (det != 0.0) {
+    binv[4 * k + 0] = d[3] / det;
+    binv[4 * k + 1] = -d[1] / det;
+    binv[4 * k + 2] = -d[2] / det;
+    binv[4 * k + 3] = d[0] / det;
+  } else {
+    binv[4 * k + 0] = binv[4 * k + 1] = binv[4 * k + 2] = binv[4 * k + 3] = 0.0;
+  }
+}
+
 __global__ void k_inv_diag(int32_t n, const int32_t* rp, const int32_t* ci, const double* v, double* dinv) {
   int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
@@ -210,6 +241,13 @@ struct PcgArgs {
   CsrView32 PiT;
   const float* dinvV;
   float* u;    // [PiT.n_rows] scratch
+  float* q32;  // FP32 shadows of q and r (inputs of the auxiliary products)
+  float* r32;
+  double* red; // [3][4] reduction slots, zeroed before the launch
+  // order 2: the system matrix in 2x2 blocks and the inverses of its
+  // diagonal blocks (block Jacobi); Ab.nb == 0 uses A and dinv
+  BsrView Ab;
+  const double* binv;
   const double* rhs;
   double* x;   // in: initial guess, out: solution
   double* r[2];  // residual, double-buffered
@@ -251,6 +289,49 @@ __device__ __forceinline__ void block_partials(double (&v)[NV], double* partials
   __syncthreads();
 }
 
+// Grid-wide sums through a ring of three accumulator slots: every CTA adds its
+// block total with one atomic; after the next grid barrier every CTA reads the
+// same value.  Slot k+1 is cleared by CTA 0 while slot k is being filled: its
+// last readers finished before the previous barrier.
+template <int NV>
+__device__ __forceinline__ void grid_sum_add(double (&v)[NV], double* red, int k) {
+  __shared__ double tot_sh[4];
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  __shared__ double wsum[32][4];
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) wsum[w][q] = v[q];
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = l < nw ? wsum[l][q] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (l == 0) tot_sh[q] = s;
+    }
+    if (l == 0) {
+      if (blockIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) red[((k + 1) % 3) * 4 + q] = 0.0;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) atomicAdd(red + (k % 3) * 4 + q, tot_sh[q]);
+    }
+  }
+  __syncthreads();
+}
+
+template <int NV>
+__device__ __forceinline__ void grid_sum_read(const double* red, int k, double (&tot)[NV]) {
+#pragma unroll
+  for (int q = 0; q < NV; ++q) tot[q] = __ldcg(red + (k % 3) * 4 + q);
+}
+
 // every block sums the partials in the same order -> identical totals everywhere
 template <int NV>
 __device__ __forceinline__ void grid_totals(const double* partials, double (&tot)[NV]) {
@@ -288,6 +369,35 @@ __device__ __forceinline__ void rows_spmv(const CsrView& A, int gid, int groups,
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
     if (act && lane == 0) emit(r0, s);
+  }
+}
+
+// block rows of a 2x2-block matrix times a vector, LPR lanes per block row
+template <int LPR, class F>
+__device__ __forceinline__ void rows_bspmv(const BsrView& A, const double* x, int gid, int groups, F emit) {
+  const int lane = gid % LPR;
+  const double2* x2 = reinterpret_cast<const double2*>(x);
+  const double2* v2 = reinterpret_cast<const double2*>(A.v);
+  for (int k0 = gid / LPR; ; k0 += groups) {
+    bool act = k0 < A.nb;
+    if (!__any_sync(0xffffffffu, act)) break;
+    double s0 = 0.0, s1 = 0.0;
+    if (act) {
+      int beg = __ldg(A.rp + k0), end = __ldg(A.rp + k0 + 1);
+      for (int j = beg + lane; j < end; j += LPR) {
+        int c = __ldg(A.ci + j);
+        double2 xv = __ldcg(x2 + c);
+        double2 a01 = __ldg(v2 + 2 * j), a23 = __ldg(v2 + 2 * j + 1);
+        s0 = fma(a01.x, xv.x, fma(a01.y, xv.y, s0));
+        s1 = fma(a23.x, xv.x, fma(a23.y, xv.y, s1));
+      }
+    }
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o, LPR);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o, LPR);
+    }
+    if (act && lane == 0) emit(k0, s0, s1);
   }
 }
 
@@ -331,13 +441,40 @@ __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, in
     for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
     if (act && lane == 0) {
       double rr = __ldcg(rvec + i);
-      double zz = fma(__ldg(a.dinv + i), rr, (double)s);
+      double zz;
+      if (a.Ab.nb > 0) {
+        const int k = i >> 1, par = i & 1;
+        double r0 = __ldcg(rvec + 2 * k), r1 = __ldcg(rvec + 2 * k + 1);
+        zz = fma(__ldg(a.binv + 4 * k + 2 * par), r0, fma(__ldg(a.binv + 4 * k + 2 * par + 1), r1, (double)s));
+      } else {
+        zz = fma(__ldg(a.dinv + i), rr, (double)s);
+      }
       a.z[i] = zz;
       rz += rr * zz;
     }
   }
   return rz;
 }
+
+#ifdef FEMPIC_PCG_PROFILE
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+#define PCG_MARK(k)                                                   \
+  do {                                                                \
+    if (blockIdx.x == 0 && threadIdx.x == 0) {                        \
+      unsigned long long now_ = gtime();                              \
+      prof_acc[k] += now_ - prof_last;                                \
+      prof_last = now_;                                               \
+    }                                                                 \
+  } while (0)
+#else
+#define PCG_MARK(k) \
+  do {              \
+  } while (0)
+#endif
 
 // Preconditioned CG, four grid barriers per iteration with the nodal
 // correction (three without):
@@ -346,11 +483,11 @@ __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, in
 //   phase 2: x += alpha p, r' = r - alpha q; t = dinvL (D^T r') with r' formed
 //            on the fly; barrier
 //   phase 3: z = dinv r' + D t; barrier; rz', r'.r' -> convergence, beta
-// Register cap of the persistent CG kernel: 8 co-resident 256-thread CTAs per
-// SM (<= 32 registers) measured fastest on the drift-tube system (memory
-// latency bound: more warps in flight beat fewer spills).
+// Register cap of the persistent CG kernel: 6 co-resident 256-thread CTAs per
+// SM (<= 40 registers) measured fastest on the drift-tube system (5 and 8 CTAs
+// were slower: fewer warps in flight vs more spills and reduction traffic).
 #ifndef FEMPIC_PCG_MIN_BLOCKS
-#define FEMPIC_PCG_MIN_BLOCKS 8
+#define FEMPIC_PCG_MIN_BLOCKS 6
 #endif
 template <int LPR>
 __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
@@ -360,36 +497,49 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
   const int groups = tpg / LPR;
   const bool nodal = a.DT.n_rows > 0;
   double* r_cur = a.r[0];
+  float* r32_cur = a.r32;        // FP32 shadow of r, double-buffered like r
+  float* r32_alt = a.r32 + n;
+  int kred = 0;  // reductions so far (slot of the ring)
+#ifdef FEMPIC_PCG_PROFILE
+  unsigned long long prof_acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long prof_last = (blockIdx.x == 0 && threadIdx.x == 0) ? gtime() : 0;
+#endif
   // ---- start: r = rhs - A x; z = M^-1 r
   double acc[3] = {0.0, 0.0, 0.0};  // r.z, r.r, rhs.rhs
-  rows_spmv<LPR>(
-      a.A, gid, groups, [&](int c) { return __ldcg(a.x + c); },
-      [&](int r0, double s) {
-        double b = a.rhs[r0];
-        double rr = b - s;
-        r_cur[r0] = rr;
-        acc[1] += rr * rr;
-        acc[2] += b * b;
-        if (!nodal) {
-          double zz = a.dinv[r0] * rr;
-          a.z[r0] = zz;
-          acc[0] += rr * zz;
-        }
-      });
+  auto start_row = [&](int r0, double s) {
+    double b = a.rhs[r0];
+    double rr = b - s;
+    r_cur[r0] = rr;
+    if (nodal) r32_cur[r0] = (float)rr;
+    acc[1] += rr * rr;
+    acc[2] += b * b;
+    if (!nodal) {
+      double zz = a.dinv[r0] * rr;
+      a.z[r0] = zz;
+      acc[0] += rr * zz;
+    }
+  };
+  if (a.Ab.nb > 0)
+    rows_bspmv<LPR>(a.Ab, a.x, gid, groups, [&](int k, double s0, double s1) {
+      start_row(2 * k, s0);
+      start_row(2 * k + 1, s1);
+    });
+  else
+    rows_spmv<LPR>(a.A, gid, groups, [&](int c) { return __ldcg(a.x + c); }, start_row);
   if (nodal) {
     if (!grid_sync(a.bar, a.status)) return;
-    rows_spmv32<4>(a.DT, gid, tpg / 4, [&](int c) { return (float)__ldcg(r_cur + c); },
+    rows_spmv32<4>(a.DT, gid, tpg / 4, [&](int c) { return __ldcg(r32_cur + c); },
                    [&](int k, float s) { a.t[k] = __ldg(a.dinvL + k) * s; });
     if (a.PiT.n_rows > 0)
-      rows_spmv32<4>(a.PiT, gid, tpg / 4, [&](int c) { return (float)__ldcg(r_cur + c); },
-                     [&](int k, float s) { a.u[k] = __ldg(a.dinvV + k) * s; });
+      rows_spmv32<16>(a.PiT, gid, tpg / 16, [&](int c) { return __ldcg(r32_cur + c); },
+                      [&](int k, float s) { a.u[k] = __ldg(a.dinvV + k) * s; });
     if (!grid_sync(a.bar, a.status)) return;
     acc[0] += aux_z<4>(a, r_cur, gid, tpg);
   }
-  block_partials<3>(acc, a.partials[1]);
+  grid_sum_add<3>(acc, a.red, kred);
   if (!grid_sync(a.bar, a.status)) return;
   double tot[3];
-  grid_totals<3>(a.partials[1], tot);
+  grid_sum_read<3>(a.red, kred++, tot);
   double rz = tot[0];
   const double bnorm = sqrt(tot[2]);
   double rnorm = sqrt(tot[1]);
@@ -403,9 +553,12 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
     double* p_new = a.p[pb ^ 1];
     const bool first = it == 0;
     // phase 0: p_k = z + beta p_{k-1} (elementwise), then q = A p_k
+    PCG_MARK(0);
     if (!first) {
       for (int i = gid; i < n; i += tpg) p_new[i] = fma(beta, __ldcg(p_old + i), __ldcg(a.z + i));
+      PCG_MARK(1);
       if (!grid_sync(a.bar, a.status)) return;
+      PCG_MARK(2);
     } else {
       // p_0 = z_0: kept for the next iteration (z is overwritten below); this
       // iteration's product reads z itself, so no barrier is needed here
@@ -413,18 +566,33 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
     }
     const double* pk_vec = first ? a.z : p_new;
     double acc1[1] = {0.0};
-    rows_spmv<LPR>(
-        a.A, gid, groups, [&](int c) { return __ldcg(pk_vec + c); },
-        [&](int r0, double s) {
-          a.q[r0] = s;
-          acc1[0] += __ldcg(pk_vec + r0) * s;
-        });
-    block_partials<1>(acc1, a.partials[0]);
+    if (a.Ab.nb > 0)
+      rows_bspmv<LPR>(a.Ab, pk_vec, gid, groups, [&](int k, double s0, double s1) {
+        a.q[2 * k] = s0;
+        a.q[2 * k + 1] = s1;
+        if (nodal) {
+          a.q32[2 * k] = (float)s0;
+          a.q32[2 * k + 1] = (float)s1;
+        }
+        acc1[0] += __ldcg(pk_vec + 2 * k) * s0 + __ldcg(pk_vec + 2 * k + 1) * s1;
+      });
+    else
+      rows_spmv<LPR>(
+          a.A, gid, groups, [&](int c) { return __ldcg(pk_vec + c); },
+          [&](int r0, double s) {
+            a.q[r0] = s;
+            if (nodal) a.q32[r0] = (float)s;
+            acc1[0] += __ldcg(pk_vec + r0) * s;
+          });
+    PCG_MARK(3);
+    grid_sum_add<1>(acc1, a.red, kred);
     if (!grid_sync(a.bar, a.status)) return;
+    PCG_MARK(4);
     double t1[1];
-    grid_totals<1>(a.partials[0], t1);
+    grid_sum_read<1>(a.red, kred++, t1);
     const double alpha = t1[0] != 0.0 ? rz / t1[0] : 0.0;
-    // phase 2: x += alpha p, r' = r - alpha q
+    // phase 2: x += alpha p, r' = r - alpha q; the auxiliary products form
+    // r' on the fly from the FP32 shadows (r' itself is being written)
     double* r_new = a.r[(it + 1) & 1];
     const double* r_old = r_cur;
     double acc2[2] = {0.0, 0.0};  // r'.z', r'.r'
@@ -432,6 +600,7 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
       a.x[i] = fma(alpha, __ldcg(pk_vec + i), __ldcg(a.x + i));
       double rr = fma(-alpha, __ldcg(a.q + i), __ldcg(r_old + i));
       r_new[i] = rr;
+      if (nodal) r32_alt[i] = (float)rr;
       acc2[1] += rr * rr;
       if (!nodal) {
         double zz = a.dinv[i] * rr;
@@ -441,23 +610,30 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
     }
     if (nodal) {
       const float alpha32 = (float)alpha;
+      const float* r32o = r32_cur;
       rows_spmv32<4>(a.DT, gid, tpg / 4,
-                     [&](int c) { return fmaf(-alpha32, (float)__ldcg(a.q + c), (float)__ldcg(r_old + c)); },
+                     [&](int c) { return fmaf(-alpha32, __ldcg(a.q32 + c), __ldcg(r32o + c)); },
                      [&](int k, float s) { a.t[k] = __ldg(a.dinvL + k) * s; });
       if (a.PiT.n_rows > 0)
-        rows_spmv32<4>(a.PiT, gid, tpg / 4,
-                       [&](int c) { return fmaf(-alpha32, (float)__ldcg(a.q + c), (float)__ldcg(r_old + c)); },
-                       [&](int k, float s) { a.u[k] = __ldg(a.dinvV + k) * s; });
+        rows_spmv32<16>(a.PiT, gid, tpg / 16,
+                        [&](int c) { return fmaf(-alpha32, __ldcg(a.q32 + c), __ldcg(r32o + c)); },
+                        [&](int k, float s) { a.u[k] = __ldg(a.dinvV + k) * s; });
+      PCG_MARK(5);
       if (!grid_sync(a.bar, a.status)) return;
+      PCG_MARK(6);
       // phase 3: z = dinv r' + D t + Pi u
       acc2[0] += aux_z<4>(a, r_new, gid, tpg);
     }
-    block_partials<2>(acc2, a.partials[1]);
+    grid_sum_add<2>(acc2, a.red, kred);
+    PCG_MARK(7);
     if (!grid_sync(a.bar, a.status)) return;
     double t2[2];
-    grid_totals<2>(a.partials[1], t2);
+    grid_sum_read<2>(a.red, kred++, t2);
     ++it;
     r_cur = r_new;
+    float* tmp32 = r32_cur;
+    r32_cur = r32_alt;
+    r32_alt = tmp32;
     pb ^= 1;
     rnorm = sqrt(t2[1]);
     conv = rnorm <= thresh;
@@ -468,6 +644,11 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
     *a.iters_out = it;
     *a.res_out = bnorm > 0.0 ? rnorm / bnorm : 0.0;
     if (!conv) atomicOr(a.status, kStatusCG);
+#ifdef FEMPIC_PCG_PROFILE
+    printf("PCGPROF it=%d loop_top+totals=%.1f p_update=%.1f bar0=%.1f spmv=%.1f bar1=%.1f xr_aux_t=%.1f bar2=%.1f aux_z=%.1f (us)\n",
+           it, prof_acc[0] * 1e-3, prof_acc[1] * 1e-3, prof_acc[2] * 1e-3, prof_acc[3] * 1e-3, prof_acc[4] * 1e-3,
+           prof_acc[5] * 1e-3, prof_acc[6] * 1e-3, prof_acc[7] * 1e-3);
+#endif
   }
 }
 
