@@ -241,7 +241,8 @@ def run_native(args, rank, world, local_rank):
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         try:
-            traffic = json.load(open(prof)).get("k_pcg_bytes_per_launch")
+            per_it = json.load(open(prof)).get("k_pcg_bytes_per_iteration")
+            traffic = per_it * (iters + 1.0) if per_it else None
         except (OSError, ValueError):
             traffic = None
     dominant_is_pcg = acc["pcg_ms"] >= acc["push_ms"]
