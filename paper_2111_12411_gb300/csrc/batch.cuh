@@ -55,6 +55,10 @@ struct MemberDesc {
   double* z;
   double* p[2];
   double* q;
+  float* q32;    // FP32 shadows of q and r (auxiliary products)
+  float* r32;    // [2][n1]
+  BsrView Ab;    // order 2: 2x2-block system matrix (nb = 0 otherwise)
+  const double* binv;
   int32_t* status;
   int32_t* cg_iters;
   double* cg_res;
@@ -73,6 +77,7 @@ struct BatchWork {
   int32_t* tile_sums;       // [total tiles]
   GridBarrier* bar;
   double* partials;         // [2][grid * 4]
+  double* red;              // [3][n + 1][4] reduction ring (per member, then the working count)
   int32_t* status;          // batch-level status (barrier timeouts)
 };
 
@@ -394,7 +399,7 @@ __device__ __forceinline__ void member_rows(const CsrView& A, int tid, int tcoun
   }
 }
 
-// z_i = dinvA_i r_i + (D t)_i + (Pi u)_i over the member's rows; returns r.z part
+// z_i = (block-)Jacobi + (D t)_i + (Pi u)_i over the member's rows; returns r.z part
 __device__ __forceinline__ double member_z(const MemberDesc& d, const double* rvec, int tid, int tcount) {
   const int lane = tid % 4;
   const int groups = tcount / 4;
@@ -413,7 +418,14 @@ __device__ __forceinline__ double member_z(const MemberDesc& d, const double* rv
     for (int o = 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 4);
     if (act && (tid & 3) == 0) {
       double rr = __ldcg(rvec + i);
-      double zz = fma(__ldg(d.dinvA + i), rr, (double)s);
+      double zz;
+      if (d.Ab.nb > 0) {
+        const int k = i >> 1, par = i & 1;
+        double r0 = __ldcg(rvec + 2 * k), r1 = __ldcg(rvec + 2 * k + 1);
+        zz = fma(__ldg(d.binv + 4 * k + 2 * par), r0, fma(__ldg(d.binv + 4 * k + 2 * par + 1), r1, (double)s));
+      } else {
+        zz = fma(__ldg(d.dinvA + i), rr, (double)s);
+      }
       d.z[i] = zz;
       rz += rr * zz;
     }
@@ -440,44 +452,92 @@ __device__ __forceinline__ void member_rows32(const CsrView32& A, int tid, int t
   }
 }
 
+// q = A x over one member's rows (2x2 blocks at order 2); emit(row, value)
+template <class F>
+__device__ __forceinline__ void member_matvec(const MemberDesc& d, const double* x, int tid, int tcount, F emit) {
+  if (d.Ab.nb > 0)
+    rows_bspmv<4>(d.Ab, x, tid, tcount / 4, [&](int k, double s0, double s1) {
+      emit(2 * k, s0);
+      emit(2 * k + 1, s1);
+    });
+  else
+    member_rows<8>(d.A, tid, tcount, [&](int c) { return __ldcg(x + c); }, emit);
+}
+
+// per-member sums through the reduction ring: CTA totals are added atomically
+// into slot k of the member; the last entry of each slot counts CTAs whose
+// member is still working.  CTA 0 clears slot k+1 (its readers are done).
+template <int NV>
+__device__ __forceinline__ void member_sum_add(double (&v)[NV], double working, const BatchWork& w, int m, int k) {
+  __shared__ double wsum[32][4];
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) wsum[wi][q] = v[q];
+  __syncthreads();
+  const int stride = (w.n + 1) * 4;
+  if (blockIdx.x == 0)
+    for (int j = threadIdx.x; j < stride; j += blockDim.x) w.red[((k + 1) % 3) * stride + j] = 0.0;
+  if (wi == 0) {
+    int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = l < nw ? wsum[l][q] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (l == 0) atomicAdd(w.red + (k % 3) * stride + m * 4 + q, s);
+    }
+    if (l == 0 && working != 0.0) atomicAdd(w.red + (k % 3) * stride + w.n * 4, working);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double member_sum_read(const BatchWork& w, int m, int k, int q) {
+  return __ldcg(w.red + (k % 3) * (w.n + 1) * 4 + m * 4 + q);
+}
+
 // Every CTA runs the same number of iterations and barriers; a CTA whose
-// member has converged skips the work.  The exit test uses each member's
-// state at the start of the iteration (summed over all CTAs after the last
-// barrier), so every CTA leaves at the same iteration.
-__global__ void __launch_bounds__(256) k_batch_pcg(BatchWork w, int max_it_all) {
+// member has converged skips the work.  The exit test counts members still
+// working at the start of the iteration (summed after the barrier), so every
+// CTA leaves at the same iteration.
+__global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_batch_pcg(BatchWork w, int max_it_all) {
   const int m = member_of(w.cgblk, w.n, blockIdx.x);
   const MemberDesc& d = w.d[m];
   const int b0 = __ldg(w.cgblk + m), b1 = __ldg(w.cgblk + m + 1);
   const int tid = (blockIdx.x - b0) * blockDim.x + threadIdx.x;
   const int tcount = (b1 - b0) * blockDim.x;
-  double* part[2] = {w.partials, w.partials + 4 * (size_t)gridDim.x};
   const int n = d.n1;
   double* x = d.e_new;
   double* r_cur = d.r[0];
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // r.z, r.r, rhs.rhs, (unused)
-  member_rows<8>(
-      d.A, tid, tcount, [&](int c) { return __ldcg(x + c); },
-      [&](int r0, double s) {
-        double b = d.rhs[r0];
-        double rr = b - s;
-        r_cur[r0] = rr;
-        acc[1] += rr * rr;
-        acc[2] += b * b;
-      });
+  float* r32_cur = d.r32;
+  float* r32_alt = d.r32 + n;
+  int kred = 0;
+  double acc[3] = {0.0, 0.0, 0.0};  // r.z, r.r, rhs.rhs
+  member_matvec(d, x, tid, tcount, [&](int r0, double s) {
+    double b = d.rhs[r0];
+    double rr = b - s;
+    r_cur[r0] = rr;
+    r32_cur[r0] = (float)rr;
+    acc[1] += rr * rr;
+    acc[2] += b * b;
+  });
   if (!grid_sync(w.bar, w.status)) return;
-  member_rows32<4>(d.DT, tid, tcount, [&](int c) { return (float)__ldcg(r_cur + c); },
+  member_rows32<4>(d.DT, tid, tcount, [&](int c) { return __ldcg(r32_cur + c); },
                    [&](int k, float s) { d.t[k] = __ldg(d.dinvL + k) * s; });
-  member_rows32<4>(d.PiT, tid, tcount, [&](int c) { return (float)__ldcg(r_cur + c); },
-                   [&](int k, float s) { d.u[k] = __ldg(d.dinvV + k) * s; });
+  member_rows32<16>(d.PiT, tid, tcount, [&](int c) { return __ldcg(r32_cur + c); },
+                    [&](int k, float s) { d.u[k] = __ldg(d.dinvV + k) * s; });
   if (!grid_sync(w.bar, w.status)) return;
   acc[0] += member_z(d, r_cur, tid, tcount);
-  block_partials<4>(acc, part[1]);
+  member_sum_add<3>(acc, 0.0, w, m, kred);
   if (!grid_sync(w.bar, w.status)) return;
-  double tot[3];
-  member_totals<3>(part[1], b0, b1, tot);
-  double rz = tot[0];
-  const double bnorm = sqrt(tot[2]);
-  double rnorm = sqrt(tot[1]);
+  double rz = member_sum_read(w, m, kred, 0);
+  const double bnorm = sqrt(member_sum_read(w, m, kred, 2));
+  double rnorm = sqrt(member_sum_read(w, m, kred, 1));
+  ++kred;
   const double thresh = d.rtol * bnorm;
   bool conv = rnorm <= thresh || bnorm == 0.0;
   int it_m = 0;
@@ -496,66 +556,55 @@ __global__ void __launch_bounds__(256) k_batch_pcg(BatchWork w, int max_it_all) 
       }
     }
     if (!grid_sync(w.bar, w.status)) return;
-    double acc1[4] = {0.0, 0.0, 0.0, work ? 1.0 : 0.0};  // p.q, -, -, members still working
+    double acc1[1] = {0.0};
     if (work)
-      member_rows<8>(
-          d.A, tid, tcount, [&](int c) { return __ldcg(p_new + c); },
-          [&](int r0, double s) {
-            d.q[r0] = s;
-            acc1[0] += __ldcg(p_new + r0) * s;
-          });
-    block_partials<4>(acc1, part[0]);
+      member_matvec(d, p_new, tid, tcount, [&](int r0, double s) {
+        d.q[r0] = s;
+        d.q32[r0] = (float)s;
+        acc1[0] += __ldcg(p_new + r0) * s;
+      });
+    member_sum_add<1>(acc1, work ? 1.0 : 0.0, w, m, kred);
     if (!grid_sync(w.bar, w.status)) return;
-    // all CTAs: is any member still working?  (flag of this iteration's start)
-    {
-      __shared__ double any;
-      if (threadIdx.x < 32) {
-        double s = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) s += __ldcg(part[0] + b * 4 + 3);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (threadIdx.x == 0) any = s;
-      }
-      __syncthreads();
-      bool stop = any == 0.0;
-      __syncthreads();
-      if (stop) break;
-    }
-    double t1[1];
-    member_totals<1>(part[0], b0, b1, t1);
-    const double alpha = (work && t1[0] != 0.0) ? rz / t1[0] : 0.0;
+    // every CTA: is any member still working?  (state at this iteration's start)
+    if (__ldcg(w.red + (kred % 3) * (w.n + 1) * 4 + w.n * 4) == 0.0) break;
+    const double pq = member_sum_read(w, m, kred, 0);
+    ++kred;
+    const double alpha = (work && pq != 0.0) ? rz / pq : 0.0;
     double* r_new = d.r[(it_m + 1) & 1];
     const double* r_old = r_cur;
-    double acc2[4] = {0.0, 0.0, 0.0, 0.0};
+    double acc2[2] = {0.0, 0.0};
     if (work) {
       for (int i = tid; i < n; i += tcount) {
         x[i] = fma(alpha, __ldcg(p_new + i), __ldcg(x + i));
         double rr = fma(-alpha, __ldcg(d.q + i), __ldcg(r_old + i));
         r_new[i] = rr;
+        r32_alt[i] = (float)rr;
         acc2[1] += rr * rr;
       }
       const float a32 = (float)alpha;
-      member_rows32<4>(d.DT, tid, tcount,
-                       [&](int c) { return fmaf(-a32, (float)__ldcg(d.q + c), (float)__ldcg(r_old + c)); },
+      const float* r32o = r32_cur;
+      member_rows32<4>(d.DT, tid, tcount, [&](int c) { return fmaf(-a32, __ldcg(d.q32 + c), __ldcg(r32o + c)); },
                        [&](int k, float s) { d.t[k] = __ldg(d.dinvL + k) * s; });
-      member_rows32<4>(d.PiT, tid, tcount,
-                       [&](int c) { return fmaf(-a32, (float)__ldcg(d.q + c), (float)__ldcg(r_old + c)); },
-                       [&](int k, float s) { d.u[k] = __ldg(d.dinvV + k) * s; });
+      member_rows32<16>(d.PiT, tid, tcount, [&](int c) { return fmaf(-a32, __ldcg(d.q32 + c), __ldcg(r32o + c)); },
+                        [&](int k, float s) { d.u[k] = __ldg(d.dinvV + k) * s; });
     }
     if (!grid_sync(w.bar, w.status)) return;
     if (work) acc2[0] += member_z(d, r_new, tid, tcount);
-    block_partials<4>(acc2, part[1]);
+    member_sum_add<2>(acc2, 0.0, w, m, kred);
     if (!grid_sync(w.bar, w.status)) return;
-    double t2[2];
-    member_totals<2>(part[1], b0, b1, t2);
+    const double rzn = member_sum_read(w, m, kred, 0), rrn = member_sum_read(w, m, kred, 1);
+    ++kred;
     if (work) {
       ++it_m;
       r_cur = r_new;
+      float* t32 = r32_cur;
+      r32_cur = r32_alt;
+      r32_alt = t32;
       pb ^= 1;
-      rnorm = sqrt(t2[1]);
+      rnorm = sqrt(rrn);
       conv = rnorm <= thresh;
-      beta = rz != 0.0 ? t2[0] / rz : 0.0;
-      rz = t2[0];
+      beta = rz != 0.0 ? rzn / rz : 0.0;
+      rz = rzn;
     }
   }
   if (blockIdx.x == b0 && threadIdx.x == 0) {

@@ -1293,6 +1293,7 @@ struct FemPICBatch {
   int32_t* tile_sums = nullptr;
   GridBarrier* bar = nullptr;
   double* partials = nullptr;
+  double* red = nullptr;
   int32_t* status = nullptr;
   int total_tiles = 0, cg_grid = 0, persist_grid = 0;
   cudaGraphExec_t graph = nullptr;
@@ -1391,6 +1392,10 @@ MemberDesc describe(FemPIC* h, double dt) {
   d.p[0] = h->cg_p;
   d.p[1] = h->cg_p2;
   d.q = h->cg_q;
+  d.q32 = h->cg_q32;
+  d.r32 = h->cg_r32;
+  d.Ab = h->nb > 0 ? BsrView{h->nb, h->brp, h->bci, h->bA} : BsrView{0, nullptr, nullptr, nullptr};
+  d.binv = h->binv;
   d.status = h->d_status;
   d.cg_iters = h->d_cg_iters;
   d.cg_res = h->d_cg_res;
@@ -1437,6 +1442,7 @@ BatchWork batch_work(FemPICBatch* b) {
   w.tile_sums = b->tile_sums;
   w.bar = b->bar;
   w.partials = b->partials;
+  w.red = b->red;
   w.status = b->status;
   return w;
 }
@@ -1462,6 +1468,7 @@ int batch_launch_step(FemPICBatch* b, int max_it_all) {
   k_batch_guess<<<pg, 256, 0, s>>>(w);
   k_batch_rhs<<<pg, 256, 0, s>>>(w);
   BCK(cudaMemsetAsync(b->bar, 0, sizeof(GridBarrier), s));
+  BCK(cudaMemsetAsync(b->red, 0, 12 * (size_t)(n + 1) * sizeof(double), s));
   void* args[] = {&w, &max_it_all};
   BCK(cudaLaunchCooperativeKernel((void*)k_batch_pcg, b->cg_grid, 256, args, 0, s));
   k_batch_bupdate<<<pg, 256, 0, s>>>(w);
@@ -1555,6 +1562,7 @@ int femPIC_batch_create(FemPIC* const* members, int32_t n, FemPICBatch** out) {
       (rc = balloc(b, &b->r1blk, n + 1)) || (rc = balloc(b, &b->r2blk, n + 1)) || (rc = balloc(b, &b->zblk, n + 1)) ||
       (rc = balloc(b, &b->cgblk, n + 1)) || (rc = balloc(b, &b->tile_sums, b->total_tiles)) ||
       (rc = balloc(b, &b->bar, 1)) || (rc = balloc(b, &b->partials, 8 * (size_t)b->cg_grid)) ||
+      (rc = balloc(b, &b->red, 12 * (size_t)(n + 1))) ||
       (rc = balloc(b, &b->status, 1)))
     return rc;
   BCK(cudaMemcpy(b->pblk, pp.data(), pp.size() * 4, cudaMemcpyHostToDevice));
