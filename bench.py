@@ -304,6 +304,7 @@ def run_native(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD, "precision": args.precision, "l2": "flushed between steps "
                        "(256 MiB write)", "parallelism": "replicas" if world > 1 else "single GPU",
                        "n_particles": npart, "n_tets": info.n_tets, "n1": info.n1, "n2": info.n2,
+                       "device_bytes": int(info.device_bytes),
                        "cg_rtol": args.cg_rtol},
             "roofline": roof_pcg if dominant_is_pcg else roof_part,
             "roofline_particle_kernel": roof_part,
