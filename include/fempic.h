@@ -178,6 +178,10 @@ typedef struct {
   int64_t nnz_Pi;               /* stored entries of the vector nodal interpolation */
   int32_t n_boundary_faces;
   size_t device_bytes;      /* device memory held by the handle                */
+  int64_t nnz_L;            /* stored entries of the nodal Laplacian D^T [*eps] D */
+  int64_t nnz_V;            /* stored entries of Pi^T A Pi (0 without smoothing) */
+  int32_t aux_cheb_degree;  /* Chebyshev degree of the auxiliary-space solves
+                               in the CG preconditioner (1 = diagonal only)  */
 } femPIC_info;
 
 /* Fill *opts with defaults: FP64, trapezoid, cg_rtol 1e-12, cg_max_it 2000,

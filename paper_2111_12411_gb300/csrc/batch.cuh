@@ -50,6 +50,12 @@ struct MemberDesc {
   const float* dinvV;
   float* t;
   float* u;
+  // Chebyshev smoothing of the auxiliary problems (as in k_pcg)
+  CsrView32 L, V;
+  float *tf, *td, *t2, *uf, *ud, *u2;
+  int32_t cheb_k;
+  float chebL[3][kMaxCheb];
+  float chebV[3][kMaxCheb];
   double* rhs;
   double* r[2];
   double* z;
@@ -400,7 +406,8 @@ __device__ __forceinline__ void member_rows(const CsrView& A, int tid, int tcoun
 }
 
 // z_i = (block-)Jacobi + (D t)_i + (Pi u)_i over the member's rows; returns r.z part
-__device__ __forceinline__ double member_z(const MemberDesc& d, const double* rvec, int tid, int tcount) {
+__device__ __forceinline__ double member_z(const MemberDesc& d, const double* rvec, const float* tv, const float* uv,
+                                           int tid, int tcount) {
   const int lane = tid % 4;
   const int groups = tcount / 4;
   double rz = 0.0;
@@ -410,9 +417,9 @@ __device__ __forceinline__ double member_z(const MemberDesc& d, const double* rv
     float s = 0.f;
     if (act) {
       for (int k = __ldg(d.D.rp + i) + lane; k < __ldg(d.D.rp + i + 1); k += 4)
-        s = fmaf(__ldg(d.D.v + k), __ldcg(d.t + __ldg(d.D.ci + k)), s);
+        s = fmaf(__ldg(d.D.v + k), __ldcg(tv + __ldg(d.D.ci + k)), s);
       for (int k = __ldg(d.Pi.rp + i) + lane; k < __ldg(d.Pi.rp + i + 1); k += 4)
-        s = fmaf(__ldg(d.Pi.v + k), __ldcg(d.u + __ldg(d.Pi.ci + k)), s);
+        s = fmaf(__ldg(d.Pi.v + k), __ldcg(uv + __ldg(d.Pi.ci + k)), s);
     }
 #pragma unroll
     for (int o = 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 4);
@@ -450,6 +457,60 @@ __device__ __forceinline__ void member_rows32(const CsrView32& A, int tid, int t
     for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
     if (act && lane == 0) emit(r0, s);
   }
+}
+
+// first Chebyshev iterate of the member's auxiliary problems from their right-hand sides
+__device__ __forceinline__ void member_first_t(const MemberDesc& d, int k, float f) {
+  const float y = d.chebL[0][0] * __ldg(d.dinvL + k) * f;
+  d.t[k] = y;
+  if (d.cheb_k > 1) {
+    d.tf[k] = f;
+    d.td[k] = y;
+  }
+}
+__device__ __forceinline__ void member_first_u(const MemberDesc& d, int k, float f) {
+  const float y = d.chebV[0][0] * __ldg(d.dinvV + k) * f;
+  d.u[k] = y;
+  if (d.cheb_k > 1) {
+    d.uf[k] = f;
+    d.ud[k] = y;
+  }
+}
+
+// The remaining Chebyshev steps of the member's auxiliary problems.  Every CTA
+// passes kc - 1 grid barriers (kc: largest degree in the batch); a member works
+// in the first cheb_k - 1 of them while it is still iterating.
+__device__ bool member_cheb(const BatchWork& w, const MemberDesc& d, bool work, int kc, int tid, int tcount,
+                            const float*& tfin, const float*& ufin) {
+  float* ty[2] = {d.t, d.t2};
+  float* uy[2] = {d.u, d.u2};
+  int cur = 0;
+  for (int i = 1; i < kc; ++i) {
+    if (!grid_sync(w.bar, w.status)) return false;
+    if (!work || i >= d.cheb_k) continue;
+    const float* yc = ty[cur];
+    float* yn = ty[cur ^ 1];
+    const float c1 = d.chebL[1][i], c2 = d.chebL[2][i];
+    member_rows32<8>(d.L, tid, tcount, [&](int c) { return __ldcg(yc + c); }, [&](int k, float s) {
+      const float dd = fmaf(c1, __ldcg(d.td + k), c2 * __ldg(d.dinvL + k) * (__ldcg(d.tf + k) - s));
+      d.td[k] = dd;
+      yn[k] = __ldcg(yc + k) + dd;
+    });
+    if (d.V.n_rows > 0) {
+      const float* vc = uy[cur];
+      float* vn = uy[cur ^ 1];
+      const float e1 = d.chebV[1][i], e2 = d.chebV[2][i];
+      member_rows32<16>(d.V, tid, tcount, [&](int c) { return __ldcg(vc + c); }, [&](int k, float s) {
+        const float dd = fmaf(e1, __ldcg(d.ud + k), e2 * __ldg(d.dinvV + k) * (__ldcg(d.uf + k) - s));
+        d.ud[k] = dd;
+        vn[k] = __ldcg(vc + k) + dd;
+      });
+    }
+    cur ^= 1;
+  }
+  tfin = ty[cur];
+  ufin = uy[cur];
+  return true;
 }
 
 // q = A x over one member's rows (2x2 blocks at order 2); emit(row, value)
@@ -504,7 +565,7 @@ __device__ __forceinline__ double member_sum_read(const BatchWork& w, int m, int
 // member has converged skips the work.  The exit test counts members still
 // working at the start of the iteration (summed after the barrier), so every
 // CTA leaves at the same iteration.
-__global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_batch_pcg(BatchWork w, int max_it_all) {
+__global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_batch_pcg(BatchWork w, int max_it_all, int kc) {
   const int m = member_of(w.cgblk, w.n, blockIdx.x);
   const MemberDesc& d = w.d[m];
   const int b0 = __ldg(w.cgblk + m), b1 = __ldg(w.cgblk + m + 1);
@@ -527,11 +588,15 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_batch_pcg(BatchW
   });
   if (!grid_sync(w.bar, w.status)) return;
   member_rows32<4>(d.DT, tid, tcount, [&](int c) { return __ldcg(r32_cur + c); },
-                   [&](int k, float s) { d.t[k] = __ldg(d.dinvL + k) * s; });
+                   [&](int k, float s) { member_first_t(d, k, s); });
   member_rows32<16>(d.PiT, tid, tcount, [&](int c) { return __ldcg(r32_cur + c); },
-                    [&](int k, float s) { d.u[k] = __ldg(d.dinvV + k) * s; });
-  if (!grid_sync(w.bar, w.status)) return;
-  acc[0] += member_z(d, r_cur, tid, tcount);
+                    [&](int k, float s) { member_first_u(d, k, s); });
+  {
+    const float *tv, *uv;
+    if (!member_cheb(w, d, true, kc, tid, tcount, tv, uv)) return;
+    if (!grid_sync(w.bar, w.status)) return;
+    acc[0] += member_z(d, r_cur, tv, uv, tid, tcount);
+  }
   member_sum_add<3>(acc, 0.0, w, m, kred);
   if (!grid_sync(w.bar, w.status)) return;
   double rz = member_sum_read(w, m, kred, 0);
@@ -584,12 +649,14 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_batch_pcg(BatchW
       const float a32 = (float)alpha;
       const float* r32o = r32_cur;
       member_rows32<4>(d.DT, tid, tcount, [&](int c) { return fmaf(-a32, __ldcg(d.q32 + c), __ldcg(r32o + c)); },
-                       [&](int k, float s) { d.t[k] = __ldg(d.dinvL + k) * s; });
+                       [&](int k, float s) { member_first_t(d, k, s); });
       member_rows32<16>(d.PiT, tid, tcount, [&](int c) { return fmaf(-a32, __ldcg(d.q32 + c), __ldcg(r32o + c)); },
-                        [&](int k, float s) { d.u[k] = __ldg(d.dinvV + k) * s; });
+                        [&](int k, float s) { member_first_u(d, k, s); });
     }
+    const float *tv, *uv;
+    if (!member_cheb(w, d, work, kc, tid, tcount, tv, uv)) return;
     if (!grid_sync(w.bar, w.status)) return;
-    if (work) acc2[0] += member_z(d, r_new, tid, tcount);
+    if (work) acc2[0] += member_z(d, r_new, tv, uv, tid, tcount);
     member_sum_add<2>(acc2, 0.0, w, m, kred);
     if (!grid_sync(w.bar, w.status)) return;
     const double rzn = member_sum_read(w, m, kred, 0), rrn = member_sum_read(w, m, kred, 1);

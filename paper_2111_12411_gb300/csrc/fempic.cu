@@ -71,6 +71,19 @@ struct FemPIC {
   // FP32 copies for the preconditioner's auxiliary-space corrections
   float *D32 = nullptr, *DT32 = nullptr, *Pi32 = nullptr, *PiT32 = nullptr;
   float *dinvL32 = nullptr, *dinvV = nullptr, *aux_t = nullptr, *aux_u = nullptr;
+  // Chebyshev smoothing of the auxiliary problems: V = Pi^T (M + c K) Pi on
+  // the pattern of V_M = Pi^T M Pi (values of V_K beside it), FP32 copies of
+  // V and L, the Chebyshev buffers, and host copies of V for its eigenvalue
+  // bound (recomputed when dt changes)
+  DevCSR V;
+  double* VKv = nullptr;
+  float *V32 = nullptr, *L32 = nullptr;
+  float *aux_tf = nullptr, *aux_td = nullptr, *aux_t2 = nullptr, *aux_uf = nullptr, *aux_ud = nullptr,
+        *aux_u2 = nullptr;
+  std::vector<int32_t> hV_rp, hV_ci;
+  std::vector<double> hV_m, hV_k;
+  int cheb_k = 1;
+  float chebL[3][kMaxCheb] = {}, chebV[3][kMaxCheb] = {};
   double *Aval = nullptr, *R1val = nullptr, *R2val = nullptr, *dinvA = nullptr, *dinvL = nullptr;
   // fields
   double *e = nullptr, *e_prev = nullptr, *e_new = nullptr, *b = nullptr, *dg = nullptr, *dg_prev = nullptr;
@@ -163,6 +176,58 @@ inline int grid_for(int64_t work, int block, int cap) {
   return (int)std::min<int64_t>(g, cap);
 }
 
+// Degree of the Chebyshev smoothing of the auxiliary problems and the ratio
+// lambda_max / lambda_min of the interval it damps.  Degree 4 cuts the CG
+// iterations of the drift-tube (p = 2) and box (p = 1, 2) systems by 2.0-2.4x
+// against diagonal scaling (degree 1); higher degrees gain little because the
+// block-Jacobi part then limits.
+#ifndef FEMPIC_AUX_CHEB
+#define FEMPIC_AUX_CHEB 4
+#endif
+constexpr double kChebRatio = 100.0;
+
+// Chebyshev iteration for a Jacobi-scaled SPD matrix whose scaled spectrum is
+// taken as [lmax / kChebRatio, lmax]: step 0 sets y = dinv f / theta; step i
+// sets d <- c1_i d + c2_i dinv (f - A y), y <- y + d.  Degree 1 (or no bound)
+// leaves the diagonal scaling y = dinv f.
+void cheb_coeffs(double lmax, int k, float (&c)[3][kMaxCheb]) {
+  for (auto& row : c)
+    for (float& v : row) v = 0.f;
+  if (k <= 1 || !(lmax > 0.0)) {
+    c[0][0] = 1.f;
+    return;
+  }
+  const double lmin = lmax / kChebRatio, th = 0.5 * (lmax + lmin), de = 0.5 * (lmax - lmin);
+  const double sig = th / de;
+  double rho = 1.0 / sig;
+  c[0][0] = (float)(1.0 / th);
+  for (int i = 1; i < k; ++i) {
+    const double rn = 1.0 / (2.0 * sig - rho);
+    c[1][i] = (float)(rn * rho);
+    c[2][i] = (float)(2.0 * rn / de);
+    rho = rn;
+  }
+}
+
+// Gershgorin bound of the spectrum of diag(A)^-1 A, A = a + c b on one CSR
+// pattern (b may be null): max over rows with a positive diagonal of
+// sum_j |A_ij| / A_ii.
+double gershgorin_scaled(const std::vector<int32_t>& rp, const std::vector<int32_t>& ci, const double* a,
+                         const double* b, double c) {
+  double best = 0.0;
+  const int32_t n = (int32_t)rp.size() - 1;
+  for (int32_t i = 0; i < n; ++i) {
+    double sum = 0.0, diag = 0.0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+      const double v = b ? a[k] + c * b[k] : a[k];
+      sum += std::fabs(v);
+      if (ci[k] == i) diag = v;
+    }
+    if (diag > 0.0) best = std::max(best, sum / diag);
+  }
+  return best;
+}
+
 // lanes per CSR row of the order-2 system matrix (rows of ~30-75 entries);
 // 4 measured faster than 8 and 16 in the persistent CG
 #ifndef FEMPIC_LPR_P2
@@ -229,6 +294,17 @@ int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, 
   a.PiT = nodal ? view32(h->PiT, h->PiT32) : CsrView32{0, nullptr, nullptr, nullptr};
   a.dinvV = h->dinvV;
   a.u = h->aux_u;
+  a.L = nodal ? view32(h->L, h->L32) : CsrView32{0, nullptr, nullptr, nullptr};
+  a.V = (nodal && h->V.nnz > 0) ? view32(h->V, h->V32) : CsrView32{0, nullptr, nullptr, nullptr};
+  a.tf = h->aux_tf;
+  a.td = h->aux_td;
+  a.t2 = h->aux_t2;
+  a.uf = h->aux_uf;
+  a.ud = h->aux_ud;
+  a.u2 = h->aux_u2;
+  a.cheb_k = nodal ? h->cheb_k : 1;
+  memcpy(a.chebL, h->chebL, sizeof(a.chebL));
+  memcpy(a.chebV, h->chebV, sizeof(a.chebV));
   a.Ab = (nodal && h->nb > 0) ? BsrView{h->nb, h->brp, h->bci, h->bA} : BsrView{0, nullptr, nullptr, nullptr};
   a.q32 = h->cg_q32;
   a.r32 = h->cg_r32;
@@ -294,6 +370,11 @@ int form_system(FemPIC* h, double dt) {
   }
   k_form_dv<<<grid_for(h->PiT.n_rows, 256, 1 << 30), 256, 0, h->stream>>>(h->PiT.n_rows, h->dvM, h->dvK, c1,
                                                                             h->dinvV);
+  if (h->V.nnz > 0) {
+    k_axpy_to_f32<<<grid_for(h->V.nnz, 256, 4096), 256, 0, h->stream>>>(h->V.nnz, h->V.v, h->VKv, c1, h->V32);
+    h->launches++;
+    cheb_coeffs(gershgorin_scaled(h->hV_rp, h->hV_ci, h->hV_m.data(), h->hV_k.data(), c1), h->cheb_k, h->chebV);
+  }
   if (h->nb > 0) {
     k_form_blocks<<<grid_for(h->nb, 256, 1 << 30), 256, 0, h->stream>>>(h->nb, h->brp, h->bci, h->bM, h->bK, c1,
                                                                         h->bA, h->binv);
@@ -824,6 +905,26 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
       (rc = dalloc(h, &h->D32, hm.D.col.size())) || (rc = dalloc(h, &h->DT32, hm.DT.col.size())) ||
       (rc = dalloc(h, &h->Pi32, hm.Pi.col.size())) || (rc = dalloc(h, &h->PiT32, hm.PiT.col.size())))
     return rc;
+  h->cheb_k = std::max(1, std::min(FEMPIC_AUX_CHEB, kMaxCheb));
+  if (h->cheb_k > 1) {
+    const size_t nv = hm.PiT.n_rows;
+    if ((rc = upload_csr(h, &h->V, hm.VM)) || (rc = upload(h, &h->VKv, hm.VK)) ||
+        (rc = dalloc(h, &h->V32, hm.VM.col.size())) || (rc = dalloc(h, &h->L32, hm.L.col.size())) ||
+        (rc = dalloc(h, &h->aux_tf, hm.n0)) || (rc = dalloc(h, &h->aux_td, hm.n0)) ||
+        (rc = dalloc(h, &h->aux_t2, hm.n0)) || (rc = dalloc(h, &h->aux_uf, nv)) || (rc = dalloc(h, &h->aux_ud, nv)) ||
+        (rc = dalloc(h, &h->aux_u2, nv)))
+      return rc;
+    if (h->L.nnz > 0) k_to_f32<<<grid_for(h->L.nnz, 256, 4096), 256, 0, h->stream>>>(h->L.nnz, h->L.v, h->L32);
+    CK(cudaGetLastError());
+    h->hV_rp = hm.VM.rowptr;
+    h->hV_ci = hm.VM.col;
+    h->hV_m = hm.VM.val;
+    h->hV_k = hm.VK;
+    cheb_coeffs(gershgorin_scaled(hm.L.rowptr, hm.L.col, hm.L.val.data(), nullptr, 0.0), h->cheb_k, h->chebL);
+  } else {
+    cheb_coeffs(0.0, 1, h->chebL);
+  }
+  cheb_coeffs(0.0, 1, h->chebV);
   {
     const std::pair<const double*, float*> cv[] = {{h->D.v, h->D32}, {h->DT.v, h->DT32}, {h->Pi.v, h->Pi32},
                                                    {h->PiT.v, h->PiT32}};
@@ -1254,6 +1355,9 @@ int femPIC_get_info(const FemPIC* h, femPIC_info* info) {
   info->nnz_Pi = h->Pi.nnz;
   info->n_boundary_faces = h->n_bfaces;
   info->device_bytes = h->bytes;
+  info->nnz_L = h->L.nnz;
+  info->nnz_V = h->V.nnz;
+  info->aux_cheb_degree = h->cheb_k;
   return FEMPIC_OK;
 }
 
@@ -1385,6 +1489,17 @@ MemberDesc describe(FemPIC* h, double dt) {
   d.PiT = view32(h->PiT, h->PiT32);
   d.dinvV = h->dinvV;
   d.u = h->aux_u;
+  d.L = h->cheb_k > 1 ? view32(h->L, h->L32) : CsrView32{0, nullptr, nullptr, nullptr};
+  d.V = h->cheb_k > 1 ? view32(h->V, h->V32) : CsrView32{0, nullptr, nullptr, nullptr};
+  d.tf = h->aux_tf;
+  d.td = h->aux_td;
+  d.t2 = h->aux_t2;
+  d.uf = h->aux_uf;
+  d.ud = h->aux_ud;
+  d.u2 = h->aux_u2;
+  d.cheb_k = h->cheb_k;
+  memcpy(d.chebL, h->chebL, sizeof(d.chebL));
+  memcpy(d.chebV, h->chebV, sizeof(d.chebV));
   d.rhs = h->rhs;
   d.r[0] = h->cg_r;
   d.r[1] = h->cg_r2;
@@ -1469,7 +1584,9 @@ int batch_launch_step(FemPICBatch* b, int max_it_all) {
   k_batch_rhs<<<pg, 256, 0, s>>>(w);
   BCK(cudaMemsetAsync(b->bar, 0, sizeof(GridBarrier), s));
   BCK(cudaMemsetAsync(b->red, 0, 12 * (size_t)(n + 1) * sizeof(double), s));
-  void* args[] = {&w, &max_it_all};
+  int kc = 1;
+  for (FemPIC* h : b->m) kc = std::max(kc, h->cheb_k);
+  void* args[] = {&w, &max_it_all, &kc};
   BCK(cudaLaunchCooperativeKernel((void*)k_batch_pcg, b->cg_grid, 256, args, 0, s));
   k_batch_bupdate<<<pg, 256, 0, s>>>(w);
   k_batch_end<<<g1, 128, 0, s>>>(w);
@@ -1526,7 +1643,7 @@ int femPIC_batch_create(FemPIC* const* members, int32_t n, FemPICBatch** out) {
     w1.push_back(h->n1);
     w2.push_back(h->n2);
     wz.push_back((int64_t)h->n1 + h->n0 + h->n_tets);
-    wnnz.push_back(h->M.nnz + h->D.nnz + h->DT.nnz + 2 * h->Pi.nnz);
+    wnnz.push_back(h->M.nnz + h->D.nnz + h->DT.nnz + 2 * h->Pi.nnz + (h->cheb_k - 1) * (h->L.nnz + h->V.nnz));
   }
   auto pp = prefix_blocks(wp, 256), pt = prefix_blocks(wt, 1024), p1 = prefix_blocks(w1, 32),
        p2 = prefix_blocks(w2, 64), pz = prefix_blocks(wz, 256);

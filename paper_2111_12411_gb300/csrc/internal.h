@@ -46,6 +46,8 @@ struct HostModel {
   std::vector<double> load0;     // <W0_k, 1>
   HostCSR Pi, PiT;               // vector nodal interpolation: W1 coefficients of hat_v e_c
   std::vector<double> dvM, dvK;  // diag(Pi^T M Pi), diag(Pi^T K Pi)
+  HostCSR VM;                    // Pi^T M Pi (values) and its pattern
+  std::vector<double> VK;        // Pi^T K Pi on VM's pattern
 };
 
 // Local tables of the order-p bases, computed exactly on the reference tet.

@@ -141,6 +141,13 @@ __global__ void k_form_dv(int32_t n, const double* dvm, const double* dvk, doubl
   dinv[i] = d > 0.0 ? (float)(1.0 / d) : 0.f;
 }
 
+// out = (float)(a + c b), elementwise
+__global__ void k_axpy_to_f32(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double c,
+                              float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)(a[i] + c * b[i]);
+}
+
 // A = M + ca K, R = M + cr K (same pattern), inverse diagonal of A (0 on empty rows)
 __global__ void k_form_system(int32_t n, const int32_t* rp, const int32_t* ci, const double* m, const double* k,
                               double ca, double cr, double* a, double* r, double* dinv) {
@@ -227,6 +234,8 @@ __device__ bool grid_sync(GridBarrier* bar, int32_t* status) {
   return ok != 0;
 }
 
+constexpr int kMaxCheb = 8;
+
 struct PcgArgs {
   CsrView A;
   const double* dinv;
@@ -241,6 +250,18 @@ struct PcgArgs {
   CsrView32 PiT;
   const float* dinvV;
   float* u;    // [PiT.n_rows] scratch
+  // Chebyshev smoothing of the two auxiliary problems L y = D^T r and
+  // V y = Pi^T r (L = D^T M D, V = Pi^T A Pi, FP32, Jacobi-scaled): cheb_k
+  // steps of the Chebyshev iteration from y = 0; cheb_k = 1 is the diagonal
+  // scaling alone.  t/u hold the iterate, t2/u2 its second buffer, tf/uf the
+  // right-hand sides, td/ud the last Chebyshev step.
+  CsrView32 L;
+  CsrView32 V;
+  float *tf, *td, *t2;
+  float *uf, *ud, *u2;
+  int cheb_k;
+  float chebL[3][kMaxCheb];  // [0][0] = 1/theta; [1][i], [2][i]: step i coefficients
+  float chebV[3][kMaxCheb];
   float* q32;  // FP32 shadows of q and r (inputs of the auxiliary products)
   float* r32;
   double* red; // [3][4] reduction slots, zeroed before the launch
@@ -373,6 +394,10 @@ __device__ __forceinline__ void rows_spmv(const CsrView& A, int gid, int groups,
 }
 
 // block rows of a 2x2-block matrix times a vector, LPR lanes per block row
+// (FEMPIC_BSPMV_UNROLL2: two blocks per lane and pass)
+#ifndef FEMPIC_BSPMV_UNROLL2
+#define FEMPIC_BSPMV_UNROLL2 0
+#endif
 template <int LPR, class F>
 __device__ __forceinline__ void rows_bspmv(const BsrView& A, const double* x, int gid, int groups, F emit) {
   const int lane = gid % LPR;
@@ -384,6 +409,26 @@ __device__ __forceinline__ void rows_bspmv(const BsrView& A, const double* x, in
     double s0 = 0.0, s1 = 0.0;
     if (act) {
       int beg = __ldg(A.rp + k0), end = __ldg(A.rp + k0 + 1);
+#if FEMPIC_BSPMV_UNROLL2
+      int j = beg + lane;
+      for (; j + LPR < end; j += 2 * LPR) {
+        const int c0 = __ldg(A.ci + j), c1 = __ldg(A.ci + j + LPR);
+        const double2 x0 = __ldcg(x2 + c0), x1 = __ldcg(x2 + c1);
+        const double2 a01 = __ldg(v2 + 2 * j), a23 = __ldg(v2 + 2 * j + 1);
+        const double2 b01 = __ldg(v2 + 2 * (j + LPR)), b23 = __ldg(v2 + 2 * (j + LPR) + 1);
+        s0 = fma(a01.x, x0.x, fma(a01.y, x0.y, s0));
+        s1 = fma(a23.x, x0.x, fma(a23.y, x0.y, s1));
+        s0 = fma(b01.x, x1.x, fma(b01.y, x1.y, s0));
+        s1 = fma(b23.x, x1.x, fma(b23.y, x1.y, s1));
+      }
+      if (j < end) {
+        const int c = __ldg(A.ci + j);
+        const double2 xv = __ldcg(x2 + c);
+        const double2 a01 = __ldg(v2 + 2 * j), a23 = __ldg(v2 + 2 * j + 1);
+        s0 = fma(a01.x, xv.x, fma(a01.y, xv.y, s0));
+        s1 = fma(a23.x, xv.x, fma(a23.y, xv.y, s1));
+      }
+#else
       for (int j = beg + lane; j < end; j += LPR) {
         int c = __ldg(A.ci + j);
         double2 xv = __ldcg(x2 + c);
@@ -391,6 +436,7 @@ __device__ __forceinline__ void rows_bspmv(const BsrView& A, const double* x, in
         s0 = fma(a01.x, xv.x, fma(a01.y, xv.y, s0));
         s1 = fma(a23.x, xv.x, fma(a23.y, xv.y, s1));
       }
+#endif
     }
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) {
@@ -401,17 +447,39 @@ __device__ __forceinline__ void rows_bspmv(const BsrView& A, const double* x, in
   }
 }
 
-// FP32 row products: y_r = sum_k A_rk f(k), LPR lanes per row
+// FP32 row products: y_r = sum_k A_rk f(k), LPR lanes per row; each lane
+// loads FEMPIC_SPMV32_UNROLL entries (column, value) before it gathers them,
+// so that the dependent index -> vector loads of several entries overlap
+#ifndef FEMPIC_SPMV32_UNROLL
+#define FEMPIC_SPMV32_UNROLL 4
+#endif
 template <int LPR, class X, class F>
 __device__ __forceinline__ void rows_spmv32(const CsrView32& A, int gid, int groups, X x_of, F emit) {
   const int lane = gid % LPR;
+  constexpr int U = FEMPIC_SPMV32_UNROLL;
   for (int r0 = gid / LPR; ; r0 += groups) {
     bool act = r0 < A.n_rows;
     if (!__any_sync(0xffffffffu, act)) break;
     float s = 0.f;
     if (act) {
       int beg = __ldg(A.rp + r0), end = __ldg(A.rp + r0 + 1);
-      for (int k = beg + lane; k < end; k += LPR) s = fmaf(__ldg(A.v + k), x_of(__ldg(A.ci + k)), s);
+      if (U == 1) {
+        for (int k = beg + lane; k < end; k += LPR) s = fmaf(__ldg(A.v + k), x_of(__ldg(A.ci + k)), s);
+      } else {
+        for (int k0 = beg + lane; k0 < end; k0 += U * LPR) {
+          int c[U];
+          float v[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * LPR;
+            c[u] = k < end ? __ldg(A.ci + k) : -1;
+            v[u] = k < end ? __ldg(A.v + k) : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (c[u] >= 0) s = fmaf(v[u], x_of(c[u]), s);
+        }
+      }
     }
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
@@ -419,9 +487,16 @@ __device__ __forceinline__ void rows_spmv32(const CsrView32& A, int gid, int gro
   }
 }
 
-// z_i = dinv_i r_i + (D t)_i + (Pi u)_i for the rows this group owns; returns r.z part
+// z_i = dinv_i r_i + (D t)_i + (Pi u)_i for the rows this group owns; returns r.z part.
+// The row bounds of D and Pi, the residual and the Jacobi block are loaded
+// together, and each lane takes two entries of each product per pass, so the
+// index -> vector loads of both products overlap.
+#ifndef FEMPIC_AUXZ_FUSED
+#define FEMPIC_AUXZ_FUSED 1
+#endif
 template <int LPR>
-__device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, int gid, int tpg) {
+__device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, const float* tv, const float* uv,
+                                        int gid, int tpg) {
   const int lane = gid % LPR;
   const int groups = tpg / LPR;
   const bool vec = a.Pi.n_rows > 0;
@@ -431,11 +506,27 @@ __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, in
     if (!__any_sync(0xffffffffu, act)) break;
     float s = 0.f;
     if (act) {
-      for (int k = __ldg(a.D.rp + i) + lane; k < __ldg(a.D.rp + i + 1); k += LPR)
-        s = fmaf(__ldg(a.D.v + k), __ldcg(a.t + __ldg(a.D.ci + k)), s);
-      if (vec)
-        for (int k = __ldg(a.Pi.rp + i) + lane; k < __ldg(a.Pi.rp + i + 1); k += LPR)
-          s = fmaf(__ldg(a.Pi.v + k), __ldcg(a.u + __ldg(a.Pi.ci + k)), s);
+      if (FEMPIC_AUXZ_FUSED) {
+        const int db = __ldg(a.D.rp + i), de = __ldg(a.D.rp + i + 1);
+        const int pb = vec ? __ldg(a.Pi.rp + i) : 0, pe = vec ? __ldg(a.Pi.rp + i + 1) : 0;
+        for (int k0 = lane; db + k0 < de || pb + k0 < pe; k0 += 2 * LPR) {
+          const int kd0 = db + k0, kd1 = kd0 + LPR, kp0 = pb + k0, kp1 = kp0 + LPR;
+          const int cd0 = kd0 < de ? __ldg(a.D.ci + kd0) : -1, cd1 = kd1 < de ? __ldg(a.D.ci + kd1) : -1;
+          const int cp0 = kp0 < pe ? __ldg(a.Pi.ci + kp0) : -1, cp1 = kp1 < pe ? __ldg(a.Pi.ci + kp1) : -1;
+          const float vd0 = cd0 >= 0 ? __ldg(a.D.v + kd0) : 0.f, vd1 = cd1 >= 0 ? __ldg(a.D.v + kd1) : 0.f;
+          const float vp0 = cp0 >= 0 ? __ldg(a.Pi.v + kp0) : 0.f, vp1 = cp1 >= 0 ? __ldg(a.Pi.v + kp1) : 0.f;
+          if (cd0 >= 0) s = fmaf(vd0, __ldcg(tv + cd0), s);
+          if (cd1 >= 0) s = fmaf(vd1, __ldcg(tv + cd1), s);
+          if (cp0 >= 0) s = fmaf(vp0, __ldcg(uv + cp0), s);
+          if (cp1 >= 0) s = fmaf(vp1, __ldcg(uv + cp1), s);
+        }
+      } else {
+        for (int k = __ldg(a.D.rp + i) + lane; k < __ldg(a.D.rp + i + 1); k += LPR)
+          s = fmaf(__ldg(a.D.v + k), __ldcg(tv + __ldg(a.D.ci + k)), s);
+        if (vec)
+          for (int k = __ldg(a.Pi.rp + i) + lane; k < __ldg(a.Pi.rp + i + 1); k += LPR)
+            s = fmaf(__ldg(a.Pi.v + k), __ldcg(uv + __ldg(a.Pi.ci + k)), s);
+      }
     }
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
@@ -454,6 +545,69 @@ __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, in
     }
   }
   return rz;
+}
+
+// Store the first Chebyshev iterate of the auxiliary problems from their
+// right-hand sides f = (D^T r)_k or (Pi^T r)_k.
+__device__ __forceinline__ void aux_first_t(const PcgArgs& a, int k, float f) {
+  const float y = a.chebL[0][0] * __ldg(a.dinvL + k) * f;
+  a.t[k] = y;
+  if (a.cheb_k > 1) {
+    a.tf[k] = f;
+    a.td[k] = y;
+  }
+}
+__device__ __forceinline__ void aux_first_u(const PcgArgs& a, int k, float f) {
+  const float y = a.chebV[0][0] * __ldg(a.dinvV + k) * f;
+  a.u[k] = y;
+  if (a.cheb_k > 1) {
+    a.uf[k] = f;
+    a.ud[k] = y;
+  }
+}
+
+// lanes per row of L (rows of ~20-70 entries at order 2) and of V
+#ifndef FEMPIC_LPR_L
+#define FEMPIC_LPR_L 8
+#endif
+#ifndef FEMPIC_LPR_V
+#define FEMPIC_LPR_V 16
+#endif
+
+// Remaining cheb_k - 1 Chebyshev steps of both auxiliary problems, one grid
+// barrier before each (the step gathers the whole previous iterate):
+//   d <- c1 d + c2 dinv (f - A y),  y <- y + d  (y double-buffered).
+// Returns the buffers holding the final iterates; false if a barrier timed out.
+__device__ bool aux_cheb(const PcgArgs& a, int gid, int tpg, const float*& tfin, const float*& ufin) {
+  float* ty[2] = {a.t, a.t2};
+  float* uy[2] = {a.u, a.u2};
+  int cur = 0;
+  const bool vec = a.V.n_rows > 0;
+  for (int i = 1; i < a.cheb_k; ++i) {
+    if (!grid_sync(a.bar, a.status)) return false;
+    const float* yc = ty[cur];
+    float* yn = ty[cur ^ 1];
+    const float c1 = a.chebL[1][i], c2 = a.chebL[2][i];
+    rows_spmv32<FEMPIC_LPR_L>(a.L, gid, tpg / FEMPIC_LPR_L, [&](int c) { return __ldcg(yc + c); }, [&](int k, float s) {
+      const float d = fmaf(c1, __ldcg(a.td + k), c2 * __ldg(a.dinvL + k) * (__ldcg(a.tf + k) - s));
+      a.td[k] = d;
+      yn[k] = __ldcg(yc + k) + d;
+    });
+    if (vec) {
+      const float* vc = uy[cur];
+      float* vn = uy[cur ^ 1];
+      const float e1 = a.chebV[1][i], e2 = a.chebV[2][i];
+      rows_spmv32<FEMPIC_LPR_V>(a.V, gid, tpg / FEMPIC_LPR_V, [&](int c) { return __ldcg(vc + c); }, [&](int k, float s) {
+        const float d = fmaf(e1, __ldcg(a.ud + k), e2 * __ldg(a.dinvV + k) * (__ldcg(a.uf + k) - s));
+        a.ud[k] = d;
+        vn[k] = __ldcg(vc + k) + d;
+      });
+    }
+    cur ^= 1;
+  }
+  tfin = ty[cur];
+  ufin = uy[cur];
+  return true;
 }
 
 #ifdef FEMPIC_PCG_PROFILE
@@ -476,13 +630,16 @@ __device__ __forceinline__ unsigned long long gtime() {
   } while (0)
 #endif
 
-// Preconditioned CG, four grid barriers per iteration with the nodal
-// correction (three without):
+// Preconditioned CG; with the auxiliary-space preconditioner, 3 + cheb_k grid
+// barriers per iteration (three without it):
 //   phase 0: p_k = z + beta p_{k-1}; barrier
 //   phase 1: q = A p_k; barrier; alpha = rz / (p.q)
-//   phase 2: x += alpha p, r' = r - alpha q; t = dinvL (D^T r') with r' formed
-//            on the fly; barrier
-//   phase 3: z = dinv r' + D t; barrier; rz', r'.r' -> convergence, beta
+//   phase 2: x += alpha p, r' = r - alpha q; right-hand sides D^T r' and
+//            Pi^T r' of the auxiliary problems with r' formed on the fly, and
+//            their first Chebyshev iterate; cheb_k - 1 further steps, each
+//            after a barrier; barrier
+//   phase 3: z = B r' + D t + Pi u (B: block or point Jacobi); barrier;
+//            rz', r'.r' -> convergence, beta
 // Register cap of the persistent CG kernel: 6 co-resident 256-thread CTAs per
 // SM (<= 40 registers) measured fastest on the drift-tube system (5 and 8 CTAs
 // were slower: fewer warps in flight vs more spills and reduction traffic).
@@ -501,7 +658,7 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
   float* r32_alt = a.r32 + n;
   int kred = 0;  // reductions so far (slot of the ring)
 #ifdef FEMPIC_PCG_PROFILE
-  unsigned long long prof_acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long prof_acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   unsigned long long prof_last = (blockIdx.x == 0 && threadIdx.x == 0) ? gtime() : 0;
 #endif
   // ---- start: r = rhs - A x; z = M^-1 r
@@ -529,12 +686,14 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
   if (nodal) {
     if (!grid_sync(a.bar, a.status)) return;
     rows_spmv32<4>(a.DT, gid, tpg / 4, [&](int c) { return __ldcg(r32_cur + c); },
-                   [&](int k, float s) { a.t[k] = __ldg(a.dinvL + k) * s; });
+                   [&](int k, float s) { aux_first_t(a, k, s); });
     if (a.PiT.n_rows > 0)
       rows_spmv32<16>(a.PiT, gid, tpg / 16, [&](int c) { return __ldcg(r32_cur + c); },
-                      [&](int k, float s) { a.u[k] = __ldg(a.dinvV + k) * s; });
+                      [&](int k, float s) { aux_first_u(a, k, s); });
+    const float *tv, *uv;
+    if (!aux_cheb(a, gid, tpg, tv, uv)) return;
     if (!grid_sync(a.bar, a.status)) return;
-    acc[0] += aux_z<4>(a, r_cur, gid, tpg);
+    acc[0] += aux_z<4>(a, r_cur, tv, uv, gid, tpg);
   }
   grid_sum_add<3>(acc, a.red, kred);
   if (!grid_sync(a.bar, a.status)) return;
@@ -613,16 +772,19 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
       const float* r32o = r32_cur;
       rows_spmv32<4>(a.DT, gid, tpg / 4,
                      [&](int c) { return fmaf(-alpha32, __ldcg(a.q32 + c), __ldcg(r32o + c)); },
-                     [&](int k, float s) { a.t[k] = __ldg(a.dinvL + k) * s; });
+                     [&](int k, float s) { aux_first_t(a, k, s); });
       if (a.PiT.n_rows > 0)
         rows_spmv32<16>(a.PiT, gid, tpg / 16,
                         [&](int c) { return fmaf(-alpha32, __ldcg(a.q32 + c), __ldcg(r32o + c)); },
-                        [&](int k, float s) { a.u[k] = __ldg(a.dinvV + k) * s; });
+                        [&](int k, float s) { aux_first_u(a, k, s); });
       PCG_MARK(5);
+      const float *tv, *uv;
+      if (!aux_cheb(a, gid, tpg, tv, uv)) return;
+      PCG_MARK(8);
       if (!grid_sync(a.bar, a.status)) return;
       PCG_MARK(6);
       // phase 3: z = dinv r' + D t + Pi u
-      acc2[0] += aux_z<4>(a, r_new, gid, tpg);
+      acc2[0] += aux_z<4>(a, r_new, tv, uv, gid, tpg);
     }
     grid_sum_add<2>(acc2, a.red, kred);
     PCG_MARK(7);
@@ -645,9 +807,10 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
     *a.res_out = bnorm > 0.0 ? rnorm / bnorm : 0.0;
     if (!conv) atomicOr(a.status, kStatusCG);
 #ifdef FEMPIC_PCG_PROFILE
-    printf("PCGPROF it=%d loop_top+totals=%.1f p_update=%.1f bar0=%.1f spmv=%.1f bar1=%.1f xr_aux_t=%.1f bar2=%.1f aux_z=%.1f (us)\n",
+    printf("PCGPROF it=%d loop_top+totals=%.1f p_update=%.1f bar0=%.1f spmv=%.1f bar1=%.1f xr_aux_t=%.1f cheb=%.1f "
+           "bar2=%.1f aux_z=%.1f (us)\n",
            it, prof_acc[0] * 1e-3, prof_acc[1] * 1e-3, prof_acc[2] * 1e-3, prof_acc[3] * 1e-3, prof_acc[4] * 1e-3,
-           prof_acc[5] * 1e-3, prof_acc[6] * 1e-3, prof_acc[7] * 1e-3);
+           prof_acc[5] * 1e-3, prof_acc[8] * 1e-3, prof_acc[6] * 1e-3, prof_acc[7] * 1e-3);
 #endif
   }
 }

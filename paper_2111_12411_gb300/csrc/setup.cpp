@@ -843,30 +843,66 @@ int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets_in, int3
         PT.val[fillp[c]] = P.val[k];
         fillp[c]++;
       }
-    // diag(Pi^T M Pi) and diag(Pi^T K Pi), one column of Pi at a time
-    m->dvM.assign(PT.n_rows, 0.0);
-    m->dvK.assign(PT.n_rows, 0.0);
-    parallel_for(PT.n_rows, [&](int64_t a, int64_t b) {
-      std::vector<double> dense((size_t)m->n1, 0.0);
+    // Galerkin products V_M = Pi^T M Pi and V_K = Pi^T K Pi (one pattern), one
+    // row of Pi^T at a time with a dense accumulator; their diagonals too
+    const int32_t nv = PT.n_rows;
+    std::vector<std::vector<int32_t>> vcol((size_t)nv);
+    std::vector<std::vector<double>> vm((size_t)nv), vk((size_t)nv);
+    parallel_for(nv, [&](int64_t a, int64_t b) {
+      std::vector<double> am((size_t)nv, 0.0), ak((size_t)nv, 0.0);
+      std::vector<uint8_t> seen((size_t)nv, 0);
+      std::vector<int32_t> cols;
       for (int64_t c = a; c < b; ++c) {
-        for (int32_t k = PT.rowptr[c]; k < PT.rowptr[c + 1]; ++k) dense[PT.col[k]] = PT.val[k];
-        double sm = 0.0, sk = 0.0;
+        cols.clear();
         for (int32_t k = PT.rowptr[c]; k < PT.rowptr[c + 1]; ++k) {
-          int32_t i = PT.col[k];
-          double pi = PT.val[k];
+          const int32_t i = PT.col[k];
+          const double pi = PT.val[k];
           for (int32_t q = m->M.rowptr[i]; q < m->M.rowptr[i + 1]; ++q) {
-            double pj = dense[m->M.col[q]];
-            if (pj != 0.0) {
-              sm += pi * m->M.val[q] * pj;
-              sk += pi * m->K.val[q] * pj;
+            const int32_t j = m->M.col[q];
+            const double wm = pi * m->M.val[q], wk = pi * m->K.val[q];
+            for (int32_t r = P.rowptr[j]; r < P.rowptr[j + 1]; ++r) {
+              const int32_t d = P.col[r];
+              if (!seen[d]) {
+                seen[d] = 1;
+                cols.push_back(d);
+              }
+              am[d] += wm * P.val[r];
+              ak[d] += wk * P.val[r];
             }
           }
         }
-        m->dvM[c] = sm;
-        m->dvK[c] = sk;
-        for (int32_t k = PT.rowptr[c]; k < PT.rowptr[c + 1]; ++k) dense[PT.col[k]] = 0.0;
+        std::sort(cols.begin(), cols.end());
+        vcol[c] = cols;
+        vm[c].resize(cols.size());
+        vk[c].resize(cols.size());
+        for (size_t e = 0; e < cols.size(); ++e) {
+          const int32_t d = cols[e];
+          vm[c][e] = am[d];
+          vk[c][e] = ak[d];
+          am[d] = ak[d] = 0.0;
+          seen[d] = 0;
+        }
       }
     });
+    m->VM.n_rows = m->VM.n_cols = nv;
+    m->VM.rowptr.assign((size_t)nv + 1, 0);
+    for (int32_t c = 0; c < nv; ++c) m->VM.rowptr[c + 1] = m->VM.rowptr[c] + (int32_t)vcol[c].size();
+    m->VM.col.reserve((size_t)m->VM.rowptr[nv]);
+    m->VM.val.reserve((size_t)m->VM.rowptr[nv]);
+    m->VK.reserve((size_t)m->VM.rowptr[nv]);
+    m->dvM.assign(nv, 0.0);
+    m->dvK.assign(nv, 0.0);
+    for (int32_t c = 0; c < nv; ++c) {
+      for (size_t e = 0; e < vcol[c].size(); ++e) {
+        if (vcol[c][e] == c) {
+          m->dvM[c] = vm[c][e];
+          m->dvK[c] = vk[c][e];
+        }
+        m->VM.col.push_back(vcol[c][e]);
+        m->VM.val.push_back(vm[c][e]);
+        m->VK.push_back(vk[c][e]);
+      }
+    }
   }
   return 0;
 }

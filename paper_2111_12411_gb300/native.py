@@ -62,7 +62,8 @@ class femPIC_info(ctypes.Structure):
                 ("nl2", ctypes.c_int32), ("n_particles", ctypes.c_int64),
                 ("nnz_A", ctypes.c_int64), ("nnz_C", ctypes.c_int64), ("nnz_Q", ctypes.c_int64),
                 ("nnz_D", ctypes.c_int64), ("nnz_DT", ctypes.c_int64), ("nnz_Pi", ctypes.c_int64),
-                ("n_boundary_faces", ctypes.c_int32), ("device_bytes", ctypes.c_size_t)]
+                ("n_boundary_faces", ctypes.c_int32), ("device_bytes", ctypes.c_size_t),
+                ("nnz_L", ctypes.c_int64), ("nnz_V", ctypes.c_int64), ("aux_cheb_degree", ctypes.c_int32)]
 
 
 # (name, restype, argtypes) of every exported symbol declared in include/fempic.h
