@@ -265,6 +265,29 @@ def run_native(args, rank, world, local_rank):
                  "achieved": push_gbs, "peak": peak, "unit": "GB/s", "frac": push_gbs / peak,
                  "traffic": None, "bytes_per_launch": pbytes, "ms_per_launch": push_ms,
                  "crossings_per_particle": cross_pp, "particles_per_occupied_tet": npart / occupied}
+    # arithmetic roofline of the particle kernel: its FP64 thread instructions
+    # (DFMA + DMUL + DADD, counted by ncu on this workload) per launch over the
+    # kernel's live duration, against the FP64 FMA rate measured on this GPU
+    from paper_2111_12411_gb300.native import measure_alu
+    alu = {k: measure_alu(k, local_rank) for k in ("fp64_fma", "fp32_fma", "fp64_div")}
+    alu_roof = None
+    if os.path.exists(prof):
+        try:
+            tj = json.load(open(prof))
+            ops_pp = tj.get("k_particle_fp64_ops_per_particle_step", {}).get(args.precision)
+            pipe_pp = tj.get("k_particle_fp64_pipe_thread_inst_per_particle_step", {}).get(args.precision)
+        except (OSError, ValueError, AttributeError):
+            ops_pp = pipe_pp = None
+        if ops_pp and info.order == 2 and npart == 1_000_000:
+            ach = ops_pp * npart / (push_ms * 1e-3)
+            alu_roof = {"bound": "alu", "achieved": ach / 1e12, "peak": alu["fp64_fma"] / 1e12,
+                        "unit": "T FP64 thread ops/s", "frac": ach / alu["fp64_fma"],
+                        "ops_per_particle_step": ops_pp,
+                        "fp64_pipe_frac": (pipe_pp * npart / (push_ms * 1e-3) / alu["fp64_fma"]
+                                           if pipe_pp else None),
+                        "peak_source": "femPIC_measure_alu fp64_fma on this GPU (one DFMA = one op)",
+                        "counts": "ncu instruction counts of this kernel on this workload (profiles/traffic.json)"}
+    roof_part["alu"] = alu_roof
 
     # ---- end to end through the C ABI with host buffers ---------------------------------
     e2e = None
@@ -328,6 +351,7 @@ def run_native(args, rank, world, local_rank):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(acc["launches"]),
+            "alu_peaks_ops_per_s": alu,
             "clocks": clocks,
         }
         print(json.dumps(result), flush=True)

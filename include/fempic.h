@@ -290,6 +290,20 @@ int femPIC_batch_timing(const FemPICBatch* b, double* times, int32_t n);
 void femPIC_batch_destroy(FemPICBatch* b);
 const char* femPIC_batch_last_error(const FemPICBatch* b);
 
+/* ---- measurement: arithmetic throughput of the device --------------------
+ * Not part of the method: the denominator of the arithmetic roofline of the
+ * particle kernel, whose walk and deposit are FP64 by design (charge
+ * conservation to 1e-12) on a part with a narrow FP64 pipe.  Runs one kernel
+ * of independent chains on every SM of `device` (about 0.1 s after a warm-up
+ * launch) and returns the operations per second of the whole device in
+ * *ops_per_second: FEMPIC_ALU_FP64_FMA and FEMPIC_ALU_FP32_FMA count one fused
+ * multiply-add as one operation (two flops), FEMPIC_ALU_FP64_DIV counts one
+ * correctly rounded FP64 division.  Allocates 64 bytes of device memory for the
+ * call.  Returns FEMPIC_ERR_ARG for an unknown kind or a NULL pointer,
+ * FEMPIC_ERR_CUDA if the device or the launch fails. */
+enum { FEMPIC_ALU_FP64_FMA = 0, FEMPIC_ALU_FP32_FMA = 1, FEMPIC_ALU_FP64_DIV = 2 };
+int femPIC_measure_alu(int32_t device, int32_t kind, double* ops_per_second);
+
 #ifdef __cplusplus
 }
 #endif

@@ -284,14 +284,14 @@ __global__ void __launch_bounds__(256, 2) k_batch_particles(BatchWork w) {
     const int64_t i = (int64_t)(wb - __ldg(w.pblk + m)) * 256 + threadIdx.x;
     if (d.order == 1) {
       if (d.mixed)
-        particle_step<1, true, true>(a, i);
+        particle_step<1, (bool)FEMPIC_PARTICLE_AGG, true>(a, i);
       else
-        particle_step<1, true, false>(a, i);
+        particle_step<1, (bool)FEMPIC_PARTICLE_AGG, false>(a, i);
     } else {
       if (d.mixed)
-        particle_step<2, true, true>(a, i);
+        particle_step<2, (bool)FEMPIC_PARTICLE_AGG, true>(a, i);
       else
-        particle_step<2, true, false>(a, i);
+        particle_step<2, (bool)FEMPIC_PARTICLE_AGG, false>(a, i);
     }
   }
 }

@@ -228,6 +228,7 @@ double gershgorin_scaled(const std::vector<int32_t>& rp, const std::vector<int32
   return best;
 }
 
+
 // lanes per CSR row of the order-2 system matrix (rows of ~30-75 entries);
 // 4 measured faster than 8 and 16 in the persistent CG
 #ifndef FEMPIC_LPR_P2
@@ -492,7 +493,8 @@ int launch_particles(FemPIC* h, double dt) {
   if (h->np == 0) return FEMPIC_OK;
   int grid = grid_for(h->np, 256, 1 << 30);
   bool strict = h->opts.precision == FEMPIC_FP64_STRICT;
-  const bool agg = h->opts.sort_period == 1;  // lanes share tets only right after a sort
+  // lanes share tets only right after a sort
+  const bool agg = FEMPIC_PARTICLE_AGG && h->opts.sort_period == 1;
   const bool mixed = h->opts.precision == FEMPIC_MIXED;
   if (h->order == 1) {
     if (strict)
@@ -1803,3 +1805,91 @@ void femPIC_batch_destroy(FemPICBatch* b) {
 const char* femPIC_batch_last_error(const FemPICBatch* b) { return b ? b->err.c_str() : "NULL batch"; }
 
 }  // extern "C"
+
+// ---- measurement: arithmetic throughput -----------------------------------
+namespace {
+
+constexpr int kAluChains = 8;
+constexpr int kAluUnroll = 16;
+
+// kAluChains independent chains x = x * m + c per thread; the final sum is
+// written only if it equals an impossible value, so the chains stay live
+template <class T>
+__global__ void __launch_bounds__(256) k_alu_fma(int iters, T m, T c, T* out) {
+  T a[kAluChains];
+#pragma unroll
+  for (int j = 0; j < kAluChains; ++j) a[j] = (T)(threadIdx.x + j) * (T)1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < kAluUnroll; ++u)
+#pragma unroll
+      for (int j = 0; j < kAluChains; ++j) a[j] = fma(a[j], m, c);
+  }
+  T s = 0;
+#pragma unroll
+  for (int j = 0; j < kAluChains; ++j) s += a[j];
+  if (s == (T)-12345.0) out[0] = s;
+}
+
+// kAluChains independent chains x = c / (x + d) per thread (division as the
+// compiler implements it)
+__global__ void __launch_bounds__(256) k_alu_div(int iters, double c, double d, double* out) {
+  double a[kAluChains];
+#pragma unroll
+  for (int j = 0; j < kAluChains; ++j) a[j] = 1.0 + (threadIdx.x + j) * 1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < kAluChains; ++j) a[j] = c / (a[j] + d);
+  }
+  double s = 0;
+#pragma unroll
+  for (int j = 0; j < kAluChains; ++j) s += a[j];
+  if (s == -12345.0) out[0] = s;
+}
+
+}  // namespace
+
+extern "C" int femPIC_measure_alu(int32_t device, int32_t kind, double* ops_per_second) {
+  if (!ops_per_second || kind < FEMPIC_ALU_FP64_FMA || kind > FEMPIC_ALU_FP64_DIV) return FEMPIC_ERR_ARG;
+  *ops_per_second = 0.0;
+  if (cudaSetDevice(device) != cudaSuccess) return FEMPIC_ERR_CUDA;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return FEMPIC_ERR_CUDA;
+  const int blocks = prop.multiProcessorCount * 4, threads = 256;
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, 64) != cudaSuccess) return FEMPIC_ERR_CUDA;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = FEMPIC_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = FEMPIC_ERR_CUDA;
+  auto launch = [&](int iters) {
+    if (kind == FEMPIC_ALU_FP64_FMA)
+      k_alu_fma<double><<<blocks, threads>>>(iters, 0.999999, 1e-7, (double*)buf);
+    else if (kind == FEMPIC_ALU_FP32_FMA)
+      k_alu_fma<float><<<blocks, threads>>>(iters, 0.999999f, 1e-7f, (float*)buf);
+    else
+      k_alu_div<<<blocks, threads>>>(iters, 1.5, 0.75, (double*)buf);
+  };
+  // per-thread operations of one loop pass
+  const double per_pass = kind == FEMPIC_ALU_FP64_DIV ? kAluChains : (double)kAluChains * kAluUnroll;
+  int iters = 64;
+  float ms = 0.f;
+  for (int round = 0; round < 12 && rc == FEMPIC_OK; ++round) {
+    launch(iters);  // warm-up (and first estimate)
+    cudaEventRecord(e0);
+    launch(iters);
+    cudaEventRecord(e1);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      rc = FEMPIC_ERR_CUDA;
+      break;
+    }
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms >= 50.f) break;
+    iters = (int)std::min<double>(1 << 26, iters * std::max(2.0, 80.0 / std::max(ms, 0.01f)));
+  }
+  if (rc == FEMPIC_OK && ms > 0.f)
+    *ops_per_second = per_pass * iters * (double)blocks * threads / (ms * 1e-3);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  return rc;
+}

@@ -5,15 +5,26 @@
 //   * E = sum_j e_j m_j(l) w_ab = sum_k alpha_k grad l_k, where the DOF sums
 //     are first collected per local edge pair (c_ab), then
 //     alpha_b += c_ab l_a, alpha_a -= c_ab l_b;
-//   * B = B0 + sum_f beta_f w_f = B0 + sum_{a<b} gamma_ab grad l_a x grad l_b;
-//   * the deposit evaluates w_ab . (b - a) = l_a d_b - l_b d_a once per pair and
-//     Gauss point and scales it by each DOF's multiplier;
-//   * the first sub-segment of every particle lies in its own (sorted) tet: its
-//     current is summed across the warp's lanes that share the tet before the
-//     atomic add, and so is the charge of particles that end in the same tet.
+//   * B = B0 + sum_f beta_f w_f = B0 + sum_{a<b} gamma_ab grad l_a x grad l_b,
+//     with the six cross products reduced to three (the gradients sum to 0);
+//   * the deposit evaluates w_ab . (b - a) = l_a d_b - l_b d_a once per pair
+//     (constant along the chord) and scales it by each DOF's multiplier at the
+//     sub-segment's midpoint (exact: the integrand is affine in s);
+//   * optionally (AGG), the first sub-segment's current and the end-point
+//     charge are summed across the warp's lanes that share a tet (particles
+//     are sorted by tet) before the atomic adds.
 #pragma once
 
 #include "kernels.cuh"
+
+// Sum the first sub-segment's current and the end-point charge over the lanes
+// of a warp that share a tet before the FP64 atomics (segmented warp scans).
+// Off by default: on GB300 the scans' FP64 adds occupy the narrow FP64 pipe
+// that bounds the particle kernel, while the atomics execute in L2; direct
+// atomics measured 12-14 % faster (drift tube and 37^3 box, FP64 and mixed).
+#ifndef FEMPIC_PARTICLE_AGG
+#define FEMPIC_PARTICLE_AGG 0
+#endif
 
 namespace fempic {
 namespace dev {
@@ -113,20 +124,30 @@ __device__ __forceinline__ void gather_B_fact(const TetGeom& G, const double* l,
     gam[pair_of(s, u)] = fma(-b2, l[t], gam[pair_of(s, u)]);
     gam[pair_of(s, t)] = fma(b2, l[u], gam[pair_of(s, t)]);
   }
-  B[0] = B0[0];
-  B[1] = B0[1];
-  B[2] = B0[2];
+  // grad l_3 = -(grad l_0 + grad l_1 + grad l_2): the six products
+  // grad l_a x grad l_b reduce to X01, X02, X12 with combined coefficients
+  const double k01 = gam[pair_of(0, 1)] - gam[pair_of(0, 3)] + gam[pair_of(1, 3)];
+  const double k02 = gam[pair_of(0, 2)] - gam[pair_of(0, 3)] + gam[pair_of(2, 3)];
+  const double k12 = gam[pair_of(1, 2)] - gam[pair_of(1, 3)] + gam[pair_of(2, 3)];
+  const double* g0 = G.g[0];
+  const double* g1 = G.g[1];
+  const double* g2 = G.g[2];
 #pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    const double* ga = G.g[edge_s(j)];
-    const double* gb = G.g[edge_t(j)];
-    B[0] = fma(gam[j], ga[1] * gb[2] - ga[2] * gb[1], B[0]);
-    B[1] = fma(gam[j], ga[2] * gb[0] - ga[0] * gb[2], B[1]);
-    B[2] = fma(gam[j], ga[0] * gb[1] - ga[1] * gb[0], B[2]);
+  for (int c = 0; c < 3; ++c) {
+    const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+    const double x01 = fma(g0[c1], g1[c2], -g0[c2] * g1[c1]);
+    const double x02 = fma(g0[c1], g2[c2], -g0[c2] * g2[c1]);
+    const double x12 = fma(g1[c1], g2[c2], -g1[c2] * g2[c1]);
+    B[c] = fma(k01, x01, fma(k02, x02, fma(k12, x12, B0[c])));
   }
 }
 
-// current of the sub-segment [s0, s1] of the chord in one tet
+// current of the sub-segment [s0, s1] of the chord in one tet.  Along the
+// straight chord l(s) = la + s d, w_ab . (b - a) = l_a d_b - l_b d_a does not
+// depend on s, and the order-2 multipliers (3 l_x - 1, 3 l_x) are affine in s,
+// so the path integral of every basis function is the sub-segment length times
+// its value at the midpoint: the midpoint rule is exact here (the oracle's
+// two-point Gauss-Legendre rule gives the same value up to rounding).
 template <int P>
 __device__ __forceinline__ void deposit_fact(const double* la, const double* lb, double s0, double s1, double qw,
                                              const int32_t* __restrict__ dofs, double* __restrict__ dg, bool agg,
@@ -134,44 +155,26 @@ __device__ __forceinline__ void deposit_fact(const double* la, const double* lb,
   double d[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) d[i] = lb[i] - la[i];
+  const double sc = qw * (s1 - s0);
+  double w[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const int s = edge_s(j), t = edge_t(j);
+    w[j] = sc * fma(la[s], d[t], -la[t] * d[s]);
+  }
   if (P == 1) {
-    double Pv[4], Qv[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      Pv[i] = fma(s0, d[i], la[i]);
-      Qv[i] = fma(s1, d[i], la[i]);
-    }
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      const int s = edge_s(j), t = edge_t(j);
-      double val = qw * fma(Pv[s], Qv[t], -Pv[t] * Qv[s]);
-      run_add(dg + __ldg(dofs + j), val, agg, runs, lane, valid);
-    }
+    for (int j = 0; j < 6; ++j) run_add(dg + __ldg(dofs + j), w[j], agg, runs, lane, valid);
   } else {
-    const double half = (s1 - s0) * 0.5;
     const double mid = (s0 + s1) * 0.5;
-    const double r = half * kGL2X;
-    double LA[4], LB[4];
+    double t3[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      LA[i] = fma(mid - r, d[i], la[i]);
-      LB[i] = fma(mid + r, d[i], la[i]);
-    }
-    double wA[6], wB[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      const int s = edge_s(j), t = edge_t(j);
-      wA[j] = fma(LA[s], d[t], -LA[t] * d[s]);
-      wB[j] = fma(LB[s], d[t], -LB[t] * d[s]);
-    }
-    const double sc = qw * half;
+    for (int i = 0; i < 4; ++i) t3[i] = 3.0 * fma(mid, d[i], la[i]);
 #pragma unroll
     for (int j = 0; j < 20; ++j) {
       const int a = w1q(j, 0), b = w1q(j, 1), x = w1q(j, 2), kind = w1q(j, 3);
-      const int pr = pair_of(a, b);
-      double mA = kind == 1 ? fma(3.0, LA[x], -1.0) : 3.0 * LA[x];
-      double mB = kind == 1 ? fma(3.0, LB[x], -1.0) : 3.0 * LB[x];
-      double val = sc * fma(mA, wA[pr], mB * wB[pr]);
+      const double wp = w[pair_of(a, b)];
+      const double val = kind == 1 ? fma(t3[x], wp, -wp) : t3[x] * wp;
       run_add(dg + __ldg(dofs + j), val, agg, runs, lane, valid);
     }
   }
@@ -357,7 +360,7 @@ __device__ __forceinline__ void particle_step(const ParticleArgs& a, int64_t i) 
   double s1;
   int best = exit_face(la, lb, -1, 0.0, s1);
   {
-    WarpRuns runs = warp_runs(valid ? T : -1 - lane);
+    const WarpRuns runs = AGG ? warp_runs(valid ? T : -1 - lane) : WarpRuns{0, 0, false};
     deposit_fact<P>(la, lb, 0.0, s1, a.qw, a.dof1 + (size_t)T * N1, a.dg, AGG && runs.ok, runs, lane, valid);
   }
   int nc = 0;
@@ -415,7 +418,7 @@ __device__ __forceinline__ void particle_step(const ParticleArgs& a, int64_t i) 
   }
   // ---- charge at the end point, summed over lanes ending in the same tet
   {
-    WarpRuns runs = warp_runs(valid ? T : -1 - lane);
+    const WarpRuns runs = AGG ? warp_runs(valid ? T : -1 - lane) : WarpRuns{0, 0, false};
     deposit_rho_fact<P>(lb, a.qw, a.dof0 + (size_t)T * N0, a.rho, AGG && runs.ok, runs, lane, valid);
   }
   if (valid) {

@@ -87,6 +87,7 @@ EXPORTS = [
     ("femPIC_last_timing", ctypes.c_int, [_P, _P, ctypes.c_int32]),
     ("femPIC_destroy", None, [_P]),
     ("femPIC_last_error", ctypes.c_char_p, [_P]),
+    ("femPIC_measure_alu", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     ("femPIC_batch_create", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
     ("femPIC_batch_step", ctypes.c_int, [_P, _P, ctypes.c_int32]),
     ("femPIC_batch_timing", ctypes.c_int, [_P, _P, ctypes.c_int32]),
@@ -394,3 +395,16 @@ class Batch:
                 self.close()
         except Exception:
             pass
+
+
+ALU_KIND = {"fp64_fma": 0, "fp32_fma": 1, "fp64_div": 2}
+
+
+def measure_alu(kind, device=0):
+    """Arithmetic throughput of the device (operations per second of the whole
+    GPU; one fused multiply-add or one division counts as one operation)."""
+    out = ctypes.c_double(0.0)
+    rc = load().femPIC_measure_alu(int(device), ALU_KIND[kind], ctypes.byref(out))
+    if rc != 0:
+        raise FemPICError(rc, f"femPIC_measure_alu({kind}) failed")
+    return out.value

@@ -223,6 +223,43 @@ def test_full_size_drift_tube_sampled():
     g.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_size_drift_tube_sampled_fast(precision):
+    """The drift-tube workload at full size in the precision the benchmark
+    times (fast FP64 kernel: fused multiply-adds, factored sums, midpoint
+    deposit; mixed: FP32 gather and push): 400 sampled particles against the
+    oracle, recomputed one by one from the same seeded state; owning tets equal
+    wherever the end point is not within 1e-9 of a face; charge conserved over
+    all particles."""
+    from paper_2111_12411_gb300 import Simulation
+    from oracle import geometry
+    cfg = workloads.make_config(1)
+    g = Simulation.from_config(cfg, precision=precision, diagnostics=True, es_init=False)
+    t = otopo.Topology(cfg["xyz"], cfg["tets"], 2)
+    rng = np.random.default_rng(5)
+    e, b = random_state(t, rng, e_scale=1e4, b_scale=1e-3)
+    g.set("E", e)
+    g.set("E_PREV", e)
+    g.set("B", b)
+    g.step(cfg["dt"])
+    d = g.diag()
+    assert d["continuity_abs"] <= 1e-12 * d["continuity_ref"]
+    gg, cc, _ = geometry.barycentric_maps(t.xyz, t.tets)
+    idx = np.sort(rng.choice(len(cfg["x"]), 400, replace=False))
+    x0, v0, t0 = cfg["x"][idx], cfg["v"][idx], cfg["tet"][idx]
+    E, B = opart.gather(t, gg, cc, e, b, cfg["B0"], x0, t0)
+    vn = opart.boris(v0, E, B, cfg["q"], cfg["m"], cfg["dt"])
+    x1 = x0 + cfg["dt"] * vn
+    xe, ve, te, dg, nc, hs, st = opart.walk_deposit(t, gg, cc, x0, x1, vn, t0, cfg["q"] * cfg["weight"], t.n1)
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    assert rel(g.get("X")[idx], xe) < tol
+    assert rel(g.get("V")[idx], ve) < tol
+    ok = geometry.lam(gg[te], cc[te], xe).min(axis=1) > 1e-9
+    assert ok.mean() > 0.99
+    assert np.array_equal(g.get("TET")[idx][ok], te[ok])
+    g.close()
+
+
 @pytest.mark.parametrize("order", [1, 2])
 def test_mixed_precision_step(c1small, order):
     """FP32 gather and push, FP64 walk/deposit/charge: positions and velocities
