@@ -561,11 +561,16 @@ __device__ __forceinline__ double member_sum_read(const BatchWork& w, int m, int
   return __ldcg(w.red + (k % 3) * (w.n + 1) * 4 + m * 4 + q);
 }
 
+// 6 co-resident 256-thread CTAs per SM (<= 40 registers)
+#ifndef FEMPIC_BATCH_PCG_MIN_BLOCKS
+#define FEMPIC_BATCH_PCG_MIN_BLOCKS 6
+#endif
+
 // Every CTA runs the same number of iterations and barriers; a CTA whose
 // member has converged skips the work.  The exit test counts members still
 // working at the start of the iteration (summed after the barrier), so every
 // CTA leaves at the same iteration.
-__global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_batch_pcg(BatchWork w, int max_it_all, int kc) {
+__global__ void __launch_bounds__(256, FEMPIC_BATCH_PCG_MIN_BLOCKS) k_batch_pcg(BatchWork w, int max_it_all, int kc) {
   const int m = member_of(w.cgblk, w.n, blockIdx.x);
   const MemberDesc& d = w.d[m];
   const int b0 = __ldg(w.cgblk + m), b1 = __ldg(w.cgblk + m + 1);

@@ -94,6 +94,7 @@ struct FemPIC {
   float *cg_q32 = nullptr, *cg_r32 = nullptr;
   GridBarrier* bar = nullptr;
   int pcg_blocks_w1 = 0, pcg_blocks_w0 = 0;
+  int32_t* apart = nullptr;  // [pcg_blocks_w1 + 1] per-CTA row ranges of A in the CG
   // particles (device order), SoA
   double* px[3] = {nullptr, nullptr, nullptr};
   double* pv[3] = {nullptr, nullptr, nullptr};
@@ -209,6 +210,23 @@ void cheb_coeffs(double lmax, int k, float (&c)[3][kMaxCheb]) {
   }
 }
 
+// Cut rows 0..n-1 (prefix of stored entries `pre`, pre[n] = total) into
+// `parts` contiguous ranges of about equal cost, a row costing its entries
+// plus two (its pointer loads and result store); returns parts + 1 bounds.
+std::vector<int32_t> balanced_ranges(const std::vector<int64_t>& pre, int parts) {
+  const int64_t n = (int64_t)pre.size() - 1;
+  const int64_t total = pre[n] + 2 * n;
+  std::vector<int32_t> out((size_t)parts + 1, 0);
+  int64_t r = 0;
+  for (int b = 1; b < parts; ++b) {
+    const int64_t target = total * b / parts;
+    while (r < n && pre[r] + 2 * r < target) ++r;
+    out[b] = (int32_t)r;
+  }
+  out[parts] = (int32_t)n;
+  return out;
+}
+
 // Gershgorin bound of the spectrum of diag(A)^-1 A, A = a + c b on one CSR
 // pattern (b may be null): max over rows with a positive diagonal of
 // sum_j |A_ij| / A_ii.
@@ -272,7 +290,7 @@ int spmv(FemPIC* h, const CsrView& A, const double* x, double* y, double alpha =
 template <int LPR>
 int pcg_blocks(FemPIC* h) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<LPR>, 256, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<LPR>, FEMPIC_PCG_THREADS, 0);
   if (e != cudaSuccess) {
     h->err = std::string("occupancy query: ") + cudaGetErrorString(e);
     return -1;
@@ -311,6 +329,7 @@ int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, 
   a.r32 = h->cg_r32;
   a.red = h->cg_red;
   a.binv = h->binv;
+  a.Apart = (nodal && blocks == h->pcg_blocks_w1) ? h->apart : nullptr;
   a.rhs = rhs;
   a.x = x;
   a.r[0] = h->cg_r;
@@ -331,9 +350,9 @@ int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, 
   CK(cudaMemsetAsync(h->cg_red, 0, 12 * sizeof(double), h->stream));
   void* args[] = {&a};
   if (h->order == 1)
-    CK(cudaLaunchCooperativeKernel((void*)k_pcg<4>, blocks, 256, args, 0, h->stream));
+    CK(cudaLaunchCooperativeKernel((void*)k_pcg<4>, blocks, FEMPIC_PCG_THREADS, args, 0, h->stream));
   else
-    CK(cudaLaunchCooperativeKernel((void*)k_pcg<FEMPIC_LPR_P2>, blocks, 256, args, 0, h->stream));
+    CK(cudaLaunchCooperativeKernel((void*)k_pcg<FEMPIC_LPR_P2>, blocks, FEMPIC_PCG_THREADS, args, 0, h->stream));
   h->launches++;
   return FEMPIC_OK;
 }
@@ -995,6 +1014,18 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
     int bl = pcg_blocks<FEMPIC_LPR_P2>(h);
     if (bl < 0) return FEMPIC_ERR_CUDA;
     h->pcg_blocks_w1 = h->pcg_blocks_w0 = bl;
+  }
+  {
+    // CG row ranges of A per CTA, balanced by stored entries (block rows at order 2)
+    std::vector<int64_t> pre;
+    if (h->nb > 0) {
+      pre.assign((size_t)h->nb + 1, 0);
+      for (int32_t k = 0; k < h->nb; ++k) pre[k + 1] = pre[k] + (hm.M.rowptr[2 * k + 1] - hm.M.rowptr[2 * k]) / 2;
+    } else {
+      pre.assign(hm.M.rowptr.begin(), hm.M.rowptr.end());
+    }
+    std::vector<int32_t> part = balanced_ranges(pre, h->pcg_blocks_w1);
+    if ((rc = upload(h, &h->apart, part))) return rc;
   }
   if ((rc = dalloc(h, &h->cg_q32, nmax)) || (rc = dalloc(h, &h->cg_r32, 2 * (size_t)nmax)) ||
       (rc = dalloc(h, &h->cg_red, 12)))

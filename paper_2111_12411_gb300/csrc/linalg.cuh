@@ -269,6 +269,7 @@ struct PcgArgs {
   // diagonal blocks (block Jacobi); Ab.nb == 0 uses A and dinv
   BsrView Ab;
   const double* binv;
+  const int32_t* Apart;  // [gridDim.x + 1] per-CTA row ranges of A (block rows at order 2), or null
   const double* rhs;
   double* x;   // in: initial guess, out: solution
   double* r[2];  // residual, double-buffered
@@ -321,7 +322,7 @@ __device__ __forceinline__ void grid_sum_add(double (&v)[NV], double* red, int k
   for (int q = 0; q < NV; ++q)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-  __shared__ double wsum[32][4];
+  __shared__ double wsum[64][4];
   int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0)
 #pragma unroll
@@ -331,7 +332,7 @@ __device__ __forceinline__ void grid_sum_add(double (&v)[NV], double* red, int k
     int nw = blockDim.x >> 5;
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      double s = l < nw ? wsum[l][q] : 0.0;
+      double s = (l < nw ? wsum[l][q] : 0.0) + (l + 32 < nw ? wsum[l + 32][q] : 0.0);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (l == 0) tot_sh[q] = s;
@@ -374,120 +375,189 @@ __device__ __forceinline__ void grid_totals(const double* partials, double (&tot
   __syncthreads();
 }
 
-// y_r = sum_k A_rk f(k) for the rows this thread group owns, LPR lanes per row
+// ---- row products ------------------------------------------------------------
+// Each "row body" computes one row with a group of LPR lanes (lane = index in
+// the group; all 32 lanes of the warp call it together, act = this group has a
+// row) and emits the result from lane 0 of the group.  Two drivers hand out
+// the rows: a static grid stride (rows_*), and a dynamic one (for_rows) in
+// which each CTA owns a contiguous range and its warps take the next pass of
+// 32 / LPR rows from a shared-memory counter.
+
+// y_r = sum_k A_rk f(k), FP64 CSR
 template <int LPR, class X, class F>
-__device__ __forceinline__ void rows_spmv(const CsrView& A, int gid, int groups, X x_of, F emit) {
-  const int lane = gid % LPR;
-  for (int r0 = gid / LPR; ; r0 += groups) {
-    bool act = r0 < A.n_rows;
-    if (!__any_sync(0xffffffffu, act)) break;
-    double s = 0.0;
-    if (act) {
-      int beg = __ldg(A.rp + r0), end = __ldg(A.rp + r0 + 1);
-      int k = beg + lane;
-      for (; k < end; k += LPR) s = fma(__ldg(A.v + k), x_of(__ldg(A.ci + k)), s);
-    }
-#pragma unroll
-    for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
-    if (act && lane == 0) emit(r0, s);
+__device__ __forceinline__ void spmv_row(const CsrView& A, int r0, bool act, int lane, X x_of, F emit) {
+  double s = 0.0;
+  if (act) {
+    int beg = __ldg(A.rp + r0), end = __ldg(A.rp + r0 + 1);
+    for (int k = beg + lane; k < end; k += LPR) s = fma(__ldg(A.v + k), x_of(__ldg(A.ci + k)), s);
   }
+#pragma unroll
+  for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
+  if (act && lane == 0) emit(r0, s);
 }
 
-// block rows of a 2x2-block matrix times a vector, LPR lanes per block row
-// (FEMPIC_BSPMV_UNROLL2: two blocks per lane and pass)
+// block row k0 of a 2x2-block matrix times a vector (two blocks per lane and
+// pass with FEMPIC_BSPMV_UNROLL2)
 #ifndef FEMPIC_BSPMV_UNROLL2
-#define FEMPIC_BSPMV_UNROLL2 0
+#define FEMPIC_BSPMV_UNROLL2 1
 #endif
 template <int LPR, class F>
-__device__ __forceinline__ void rows_bspmv(const BsrView& A, const double* x, int gid, int groups, F emit) {
-  const int lane = gid % LPR;
+__device__ __forceinline__ void bspmv_row(const BsrView& A, const double* x, int k0, bool act, int lane, F emit) {
   const double2* x2 = reinterpret_cast<const double2*>(x);
   const double2* v2 = reinterpret_cast<const double2*>(A.v);
-  for (int k0 = gid / LPR; ; k0 += groups) {
-    bool act = k0 < A.nb;
-    if (!__any_sync(0xffffffffu, act)) break;
-    double s0 = 0.0, s1 = 0.0;
-    if (act) {
-      int beg = __ldg(A.rp + k0), end = __ldg(A.rp + k0 + 1);
+  double s0 = 0.0, s1 = 0.0;
+  if (act) {
+    int beg = __ldg(A.rp + k0), end = __ldg(A.rp + k0 + 1);
 #if FEMPIC_BSPMV_UNROLL2
-      int j = beg + lane;
-      for (; j + LPR < end; j += 2 * LPR) {
-        const int c0 = __ldg(A.ci + j), c1 = __ldg(A.ci + j + LPR);
-        const double2 x0 = __ldcg(x2 + c0), x1 = __ldcg(x2 + c1);
-        const double2 a01 = __ldg(v2 + 2 * j), a23 = __ldg(v2 + 2 * j + 1);
-        const double2 b01 = __ldg(v2 + 2 * (j + LPR)), b23 = __ldg(v2 + 2 * (j + LPR) + 1);
-        s0 = fma(a01.x, x0.x, fma(a01.y, x0.y, s0));
-        s1 = fma(a23.x, x0.x, fma(a23.y, x0.y, s1));
-        s0 = fma(b01.x, x1.x, fma(b01.y, x1.y, s0));
-        s1 = fma(b23.x, x1.x, fma(b23.y, x1.y, s1));
-      }
-      if (j < end) {
-        const int c = __ldg(A.ci + j);
-        const double2 xv = __ldcg(x2 + c);
-        const double2 a01 = __ldg(v2 + 2 * j), a23 = __ldg(v2 + 2 * j + 1);
-        s0 = fma(a01.x, xv.x, fma(a01.y, xv.y, s0));
-        s1 = fma(a23.x, xv.x, fma(a23.y, xv.y, s1));
-      }
+    int j = beg + lane;
+    for (; j + LPR < end; j += 2 * LPR) {
+      const int c0 = __ldg(A.ci + j), c1 = __ldg(A.ci + j + LPR);
+      const double2 x0 = __ldcg(x2 + c0), x1 = __ldcg(x2 + c1);
+      const double2 a01 = __ldg(v2 + 2 * j), a23 = __ldg(v2 + 2 * j + 1);
+      const double2 b01 = __ldg(v2 + 2 * (j + LPR)), b23 = __ldg(v2 + 2 * (j + LPR) + 1);
+      s0 = fma(a01.x, x0.x, fma(a01.y, x0.y, s0));
+      s1 = fma(a23.x, x0.x, fma(a23.y, x0.y, s1));
+      s0 = fma(b01.x, x1.x, fma(b01.y, x1.y, s0));
+      s1 = fma(b23.x, x1.x, fma(b23.y, x1.y, s1));
+    }
+    if (j < end) {
+      const int c = __ldg(A.ci + j);
+      const double2 xv = __ldcg(x2 + c);
+      const double2 a01 = __ldg(v2 + 2 * j), a23 = __ldg(v2 + 2 * j + 1);
+      s0 = fma(a01.x, xv.x, fma(a01.y, xv.y, s0));
+      s1 = fma(a23.x, xv.x, fma(a23.y, xv.y, s1));
+    }
 #else
-      for (int j = beg + lane; j < end; j += LPR) {
-        int c = __ldg(A.ci + j);
-        double2 xv = __ldcg(x2 + c);
-        double2 a01 = __ldg(v2 + 2 * j), a23 = __ldg(v2 + 2 * j + 1);
-        s0 = fma(a01.x, xv.x, fma(a01.y, xv.y, s0));
-        s1 = fma(a23.x, xv.x, fma(a23.y, xv.y, s1));
-      }
+    for (int j = beg + lane; j < end; j += LPR) {
+      int c = __ldg(A.ci + j);
+      double2 xv = __ldcg(x2 + c);
+      double2 a01 = __ldg(v2 + 2 * j), a23 = __ldg(v2 + 2 * j + 1);
+      s0 = fma(a01.x, xv.x, fma(a01.y, xv.y, s0));
+      s1 = fma(a23.x, xv.x, fma(a23.y, xv.y, s1));
+    }
 #endif
-    }
-#pragma unroll
-    for (int o = LPR / 2; o > 0; o >>= 1) {
-      s0 += __shfl_xor_sync(0xffffffffu, s0, o, LPR);
-      s1 += __shfl_xor_sync(0xffffffffu, s1, o, LPR);
-    }
-    if (act && lane == 0) emit(k0, s0, s1);
   }
+#pragma unroll
+  for (int o = LPR / 2; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o, LPR);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o, LPR);
+  }
+  if (act && lane == 0) emit(k0, s0, s1);
 }
 
-// FP32 row products: y_r = sum_k A_rk f(k), LPR lanes per row; each lane
-// loads FEMPIC_SPMV32_UNROLL entries (column, value) before it gathers them,
-// so that the dependent index -> vector loads of several entries overlap
+// FP32 row: each lane loads FEMPIC_SPMV32_UNROLL entries (column, value)
+// before it gathers them, so that the dependent index -> vector loads of
+// several entries overlap
 #ifndef FEMPIC_SPMV32_UNROLL
 #define FEMPIC_SPMV32_UNROLL 4
 #endif
 template <int LPR, class X, class F>
-__device__ __forceinline__ void rows_spmv32(const CsrView32& A, int gid, int groups, X x_of, F emit) {
-  const int lane = gid % LPR;
+__device__ __forceinline__ void spmv32_row(const CsrView32& A, int r0, bool act, int lane, X x_of, F emit) {
   constexpr int U = FEMPIC_SPMV32_UNROLL;
-  for (int r0 = gid / LPR; ; r0 += groups) {
-    bool act = r0 < A.n_rows;
-    if (!__any_sync(0xffffffffu, act)) break;
-    float s = 0.f;
-    if (act) {
-      int beg = __ldg(A.rp + r0), end = __ldg(A.rp + r0 + 1);
-      if (U == 1) {
-        for (int k = beg + lane; k < end; k += LPR) s = fmaf(__ldg(A.v + k), x_of(__ldg(A.ci + k)), s);
-      } else {
-        for (int k0 = beg + lane; k0 < end; k0 += U * LPR) {
-          int c[U];
-          float v[U];
+  float s = 0.f;
+  if (act) {
+    int beg = __ldg(A.rp + r0), end = __ldg(A.rp + r0 + 1);
+    if (U == 1) {
+      for (int k = beg + lane; k < end; k += LPR) s = fmaf(__ldg(A.v + k), x_of(__ldg(A.ci + k)), s);
+    } else {
+      for (int k0 = beg + lane; k0 < end; k0 += U * LPR) {
+        int c[U];
+        float v[U];
 #pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int k = k0 + u * LPR;
-            c[u] = k < end ? __ldg(A.ci + k) : -1;
-            v[u] = k < end ? __ldg(A.v + k) : 0.f;
-          }
-#pragma unroll
-          for (int u = 0; u < U; ++u)
-            if (c[u] >= 0) s = fmaf(v[u], x_of(c[u]), s);
+        for (int u = 0; u < U; ++u) {
+          const int k = k0 + u * LPR;
+          c[u] = k < end ? __ldg(A.ci + k) : -1;
+          v[u] = k < end ? __ldg(A.v + k) : 0.f;
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (c[u] >= 0) s = fmaf(v[u], x_of(c[u]), s);
       }
     }
+  }
 #pragma unroll
-    for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
-    if (act && lane == 0) emit(r0, s);
+  for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
+  if (act && lane == 0) emit(r0, s);
+}
+
+// static driver: the groups of the grid stride through rows [0, n)
+template <int LPR, class Body>
+__device__ __forceinline__ void rows_static(int n, int gid, int groups, Body body) {
+  const int lane = gid % LPR;
+  for (int r0 = gid / LPR; ; r0 += groups) {
+    bool act = r0 < n;
+    if (!__any_sync(0xffffffffu, act)) break;
+    body(r0, act, lane);
   }
 }
 
-// z_i = dinv_i r_i + (D t)_i + (Pi u)_i for the rows this group owns; returns r.z part.
+template <int LPR, class X, class F>
+__device__ __forceinline__ void rows_spmv(const CsrView& A, int gid, int groups, X x_of, F emit) {
+  rows_static<LPR>(A.n_rows, gid, groups,
+                   [&](int r, bool act, int lane) { spmv_row<LPR>(A, r, act, lane, x_of, emit); });
+}
+
+template <int LPR, class F>
+__device__ __forceinline__ void rows_bspmv(const BsrView& A, const double* x, int gid, int groups, F emit) {
+  rows_static<LPR>(A.nb, gid, groups, [&](int k, bool act, int lane) { bspmv_row<LPR>(A, x, k, act, lane, emit); });
+}
+
+template <int LPR, class X, class F>
+__device__ __forceinline__ void rows_spmv32(const CsrView32& A, int gid, int groups, X x_of, F emit) {
+  rows_static<LPR>(A.n_rows, gid, groups,
+                   [&](int r, bool act, int lane) { spmv32_row<LPR>(A, r, act, lane, x_of, emit); });
+}
+
+// dynamic driver: this CTA's range of rows [0, n) (part[b]..part[b+1], or an
+// equal share), handed to its warps in passes of 32 / LPR rows through the
+// shared counter ring[id & 7].  The loop resets ring[(id + 4) & 7] for a later
+// loop; a counter is reused only four loops later, and at most two loops run
+// between grid barriers, so no warp still reads a counter being reset.
+template <int LPR, class Body>
+__device__ __forceinline__ void for_rows(int n, const int32_t* part, int* ring, int& id, Body body) {
+  const int slot = id & 7;
+  if (threadIdx.x == 0) ring[(id + 4) & 7] = 0;
+  ++id;
+  const int rb = part ? __ldg(part + blockIdx.x) : (int)((int64_t)n * blockIdx.x / gridDim.x);
+  const int re = part ? __ldg(part + blockIdx.x + 1) : (int)((int64_t)n * (blockIdx.x + 1) / gridDim.x);
+  constexpr int RPW = 32 / LPR;
+  const int l32 = threadIdx.x & 31;
+  for (;;) {
+    int c = 0;
+    if (l32 == 0) c = atomicAdd(ring + slot, 1);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    const int r0 = rb + c * RPW;
+    if (r0 >= re) break;
+    const int r = r0 + l32 / LPR;
+    body(r, r < re, l32 % LPR);
+  }
+}
+
+// Row scheduling of the persistent CG: the static grid stride (default) or,
+// with FEMPIC_PCG_DYN, one CTA per SM over an entry-balanced contiguous range
+// whose warps take passes from a shared counter.  With the static stride the
+// CTAs of each phase finish unevenly (drift tube, A product per CTA 63 / 88 /
+// 131 us min / mean / max, later CTAs of an SM slowest); the dynamic form
+// evens out the warps of an SM but not the SMs (96 / 105 / 150 us) and runs
+// fewer warps per SM, and measured slower (451 vs 385 us per iteration).
+#ifndef FEMPIC_PCG_DYN
+#define FEMPIC_PCG_DYN 0
+#endif
+struct PcgSched {
+  int gid, tpg;
+  int* ring;
+  int id;
+  template <int LPR, class Body>
+  __device__ __forceinline__ void run(int n, const int32_t* part, Body body) {
+#if FEMPIC_PCG_DYN
+    for_rows<LPR>(n, part, ring, id, body);
+#else
+    rows_static<LPR>(n, gid, tpg / LPR, body);
+#endif
+  }
+};
+
+// z_i = dinv_i r_i + (D t)_i + (Pi u)_i over the rows (returns this thread's r.z part).
 // The row bounds of D and Pi, the residual and the Jacobi block are loaded
 // together, and each lane takes two entries of each product per pass, so the
 // index -> vector loads of both products overlap.
@@ -496,14 +566,10 @@ __device__ __forceinline__ void rows_spmv32(const CsrView32& A, int gid, int gro
 #endif
 template <int LPR>
 __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, const float* tv, const float* uv,
-                                        int gid, int tpg) {
-  const int lane = gid % LPR;
-  const int groups = tpg / LPR;
+                                        PcgSched& sc) {
   const bool vec = a.Pi.n_rows > 0;
   double rz = 0.0;
-  for (int i = gid / LPR; ; i += groups) {
-    bool act = i < a.D.n_rows;
-    if (!__any_sync(0xffffffffu, act)) break;
+  sc.run<LPR>(a.D.n_rows, nullptr, [&](int i, bool act, int lane) {
     float s = 0.f;
     if (act) {
       if (FEMPIC_AUXZ_FUSED) {
@@ -543,7 +609,7 @@ __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, co
       a.z[i] = zz;
       rz += rr * zz;
     }
-  }
+  });
   return rz;
 }
 
@@ -578,7 +644,7 @@ __device__ __forceinline__ void aux_first_u(const PcgArgs& a, int k, float f) {
 // barrier before each (the step gathers the whole previous iterate):
 //   d <- c1 d + c2 dinv (f - A y),  y <- y + d  (y double-buffered).
 // Returns the buffers holding the final iterates; false if a barrier timed out.
-__device__ bool aux_cheb(const PcgArgs& a, int gid, int tpg, const float*& tfin, const float*& ufin) {
+__device__ bool aux_cheb(const PcgArgs& a, PcgSched& sc, const float*& tfin, const float*& ufin) {
   float* ty[2] = {a.t, a.t2};
   float* uy[2] = {a.u, a.u2};
   int cur = 0;
@@ -588,20 +654,26 @@ __device__ bool aux_cheb(const PcgArgs& a, int gid, int tpg, const float*& tfin,
     const float* yc = ty[cur];
     float* yn = ty[cur ^ 1];
     const float c1 = a.chebL[1][i], c2 = a.chebL[2][i];
-    rows_spmv32<FEMPIC_LPR_L>(a.L, gid, tpg / FEMPIC_LPR_L, [&](int c) { return __ldcg(yc + c); }, [&](int k, float s) {
+    auto xl = [&](int c) { return __ldcg(yc + c); };
+    auto el = [&](int k, float s) {
       const float d = fmaf(c1, __ldcg(a.td + k), c2 * __ldg(a.dinvL + k) * (__ldcg(a.tf + k) - s));
       a.td[k] = d;
       yn[k] = __ldcg(yc + k) + d;
-    });
+    };
+    sc.run<FEMPIC_LPR_L>(a.L.n_rows, nullptr,
+                         [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_L>(a.L, r, act, lane, xl, el); });
     if (vec) {
       const float* vc = uy[cur];
       float* vn = uy[cur ^ 1];
       const float e1 = a.chebV[1][i], e2 = a.chebV[2][i];
-      rows_spmv32<FEMPIC_LPR_V>(a.V, gid, tpg / FEMPIC_LPR_V, [&](int c) { return __ldcg(vc + c); }, [&](int k, float s) {
+      auto xv = [&](int c) { return __ldcg(vc + c); };
+      auto ev = [&](int k, float s) {
         const float d = fmaf(e1, __ldcg(a.ud + k), e2 * __ldg(a.dinvV + k) * (__ldcg(a.uf + k) - s));
         a.ud[k] = d;
         vn[k] = __ldcg(vc + k) + d;
-      });
+      };
+      sc.run<FEMPIC_LPR_V>(a.V.n_rows, nullptr,
+                           [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_V>(a.V, r, act, lane, xv, ev); });
     }
     cur ^= 1;
   }
@@ -616,6 +688,15 @@ __device__ __forceinline__ unsigned long long gtime() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+// per-CTA time stamps of one iteration (FEMPIC_PCG_PROFILE builds only):
+// [0] start of the A product, [1] its end, [2] after the reduction add,
+// [3] after the barrier
+__device__ unsigned long long g_pcg_stamp[4096][4];
+#define PCG_STAMP(k, it)                                        \
+  do {                                                          \
+    if ((it) == 10 && threadIdx.x == 0 && blockIdx.x < 4096)    \
+      g_pcg_stamp[blockIdx.x][k] = gtime();                     \
+  } while (0)
 #define PCG_MARK(k)                                                   \
   do {                                                                \
     if (blockIdx.x == 0 && threadIdx.x == 0) {                        \
@@ -627,6 +708,9 @@ __device__ __forceinline__ unsigned long long gtime() {
 #else
 #define PCG_MARK(k) \
   do {              \
+  } while (0)
+#define PCG_STAMP(k, it) \
+  do {                   \
   } while (0)
 #endif
 
@@ -640,19 +724,27 @@ __device__ __forceinline__ unsigned long long gtime() {
 //            after a barrier; barrier
 //   phase 3: z = B r' + D t + Pi u (B: block or point Jacobi); barrier;
 //            rz', r'.r' -> convergence, beta
-// Register cap of the persistent CG kernel: 6 co-resident 256-thread CTAs per
-// SM (<= 40 registers) measured fastest on the drift-tube system (5 and 8 CTAs
-// were slower: fewer warps in flight vs more spills and reduction traffic).
+// Launch shape of the persistent CG kernel: with dynamic row scheduling one
+// CTA of 1024 threads (the most a CTA can have) per SM; with the static
+// stride, 6 co-resident 256-thread CTAs per SM measured fastest (5 and 8 were
+// slower).
+#ifndef FEMPIC_PCG_THREADS
+#define FEMPIC_PCG_THREADS (FEMPIC_PCG_DYN ? 1024 : 256)
+#endif
 #ifndef FEMPIC_PCG_MIN_BLOCKS
-#define FEMPIC_PCG_MIN_BLOCKS 6
+#define FEMPIC_PCG_MIN_BLOCKS (FEMPIC_PCG_DYN ? 1 : 6)
 #endif
 template <int LPR>
-__global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
+__global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
   const int n = a.A.n_rows;
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int tpg = gridDim.x * blockDim.x;
-  const int groups = tpg / LPR;
   const bool nodal = a.DT.n_rows > 0;
+  __shared__ int ring[8];
+  if (threadIdx.x < 8) ring[threadIdx.x] = 0;
+  __syncthreads();
+  PcgSched sc{gid, tpg, ring, 0};
+  const int32_t* apart = a.Apart;
   double* r_cur = a.r[0];
   float* r32_cur = a.r32;        // FP32 shadow of r, double-buffered like r
   float* r32_alt = a.r32 + n;
@@ -676,24 +768,29 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
       acc[0] += rr * zz;
     }
   };
-  if (a.Ab.nb > 0)
-    rows_bspmv<LPR>(a.Ab, a.x, gid, groups, [&](int k, double s0, double s1) {
+  if (a.Ab.nb > 0) {
+    auto em = [&](int k, double s0, double s1) {
       start_row(2 * k, s0);
       start_row(2 * k + 1, s1);
-    });
-  else
-    rows_spmv<LPR>(a.A, gid, groups, [&](int c) { return __ldcg(a.x + c); }, start_row);
+    };
+    sc.run<LPR>(a.Ab.nb, apart, [&](int k, bool act, int lane) { bspmv_row<LPR>(a.Ab, a.x, k, act, lane, em); });
+  } else {
+    auto xo = [&](int c) { return __ldcg(a.x + c); };
+    sc.run<LPR>(n, apart, [&](int r, bool act, int lane) { spmv_row<LPR>(a.A, r, act, lane, xo, start_row); });
+  }
   if (nodal) {
     if (!grid_sync(a.bar, a.status)) return;
-    rows_spmv32<4>(a.DT, gid, tpg / 4, [&](int c) { return __ldcg(r32_cur + c); },
-                   [&](int k, float s) { aux_first_t(a, k, s); });
+    auto x0 = [&](int c) { return __ldcg(r32_cur + c); };
+    auto et = [&](int k, float s) { aux_first_t(a, k, s); };
+    auto eu = [&](int k, float s) { aux_first_u(a, k, s); };
+    sc.run<4>(a.DT.n_rows, nullptr, [&](int r, bool act, int lane) { spmv32_row<4>(a.DT, r, act, lane, x0, et); });
     if (a.PiT.n_rows > 0)
-      rows_spmv32<16>(a.PiT, gid, tpg / 16, [&](int c) { return __ldcg(r32_cur + c); },
-                      [&](int k, float s) { aux_first_u(a, k, s); });
+      sc.run<16>(a.PiT.n_rows, nullptr,
+                 [&](int r, bool act, int lane) { spmv32_row<16>(a.PiT, r, act, lane, x0, eu); });
     const float *tv, *uv;
-    if (!aux_cheb(a, gid, tpg, tv, uv)) return;
+    if (!aux_cheb(a, sc, tv, uv)) return;
     if (!grid_sync(a.bar, a.status)) return;
-    acc[0] += aux_z<4>(a, r_cur, tv, uv, gid, tpg);
+    acc[0] += aux_z<4>(a, r_cur, tv, uv, sc);
   }
   grid_sum_add<3>(acc, a.red, kred);
   if (!grid_sync(a.bar, a.status)) return;
@@ -725,8 +822,9 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
     }
     const double* pk_vec = first ? a.z : p_new;
     double acc1[1] = {0.0};
-    if (a.Ab.nb > 0)
-      rows_bspmv<LPR>(a.Ab, pk_vec, gid, groups, [&](int k, double s0, double s1) {
+    PCG_STAMP(0, it);
+    if (a.Ab.nb > 0) {
+      auto em = [&](int k, double s0, double s1) {
         a.q[2 * k] = s0;
         a.q[2 * k + 1] = s1;
         if (nodal) {
@@ -734,18 +832,24 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
           a.q32[2 * k + 1] = (float)s1;
         }
         acc1[0] += __ldcg(pk_vec + 2 * k) * s0 + __ldcg(pk_vec + 2 * k + 1) * s1;
-      });
-    else
-      rows_spmv<LPR>(
-          a.A, gid, groups, [&](int c) { return __ldcg(pk_vec + c); },
-          [&](int r0, double s) {
-            a.q[r0] = s;
-            if (nodal) a.q32[r0] = (float)s;
-            acc1[0] += __ldcg(pk_vec + r0) * s;
-          });
+      };
+      sc.run<LPR>(a.Ab.nb, apart,
+                  [&](int k, bool act, int lane) { bspmv_row<LPR>(a.Ab, pk_vec, k, act, lane, em); });
+    } else {
+      auto xo = [&](int c) { return __ldcg(pk_vec + c); };
+      auto em = [&](int r0, double s) {
+        a.q[r0] = s;
+        if (nodal) a.q32[r0] = (float)s;
+        acc1[0] += __ldcg(pk_vec + r0) * s;
+      };
+      sc.run<LPR>(n, apart, [&](int r, bool act, int lane) { spmv_row<LPR>(a.A, r, act, lane, xo, em); });
+    }
     PCG_MARK(3);
+    PCG_STAMP(1, it);
     grid_sum_add<1>(acc1, a.red, kred);
+    PCG_STAMP(2, it);
     if (!grid_sync(a.bar, a.status)) return;
+    PCG_STAMP(3, it);
     PCG_MARK(4);
     double t1[1];
     grid_sum_read<1>(a.red, kred++, t1);
@@ -770,21 +874,21 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
     if (nodal) {
       const float alpha32 = (float)alpha;
       const float* r32o = r32_cur;
-      rows_spmv32<4>(a.DT, gid, tpg / 4,
-                     [&](int c) { return fmaf(-alpha32, __ldcg(a.q32 + c), __ldcg(r32o + c)); },
-                     [&](int k, float s) { aux_first_t(a, k, s); });
+      auto xr = [&](int c) { return fmaf(-alpha32, __ldcg(a.q32 + c), __ldcg(r32o + c)); };
+      auto et = [&](int k, float s) { aux_first_t(a, k, s); };
+      auto eu = [&](int k, float s) { aux_first_u(a, k, s); };
+      sc.run<4>(a.DT.n_rows, nullptr, [&](int r, bool act, int lane) { spmv32_row<4>(a.DT, r, act, lane, xr, et); });
       if (a.PiT.n_rows > 0)
-        rows_spmv32<16>(a.PiT, gid, tpg / 16,
-                        [&](int c) { return fmaf(-alpha32, __ldcg(a.q32 + c), __ldcg(r32o + c)); },
-                        [&](int k, float s) { aux_first_u(a, k, s); });
+        sc.run<16>(a.PiT.n_rows, nullptr,
+                   [&](int r, bool act, int lane) { spmv32_row<16>(a.PiT, r, act, lane, xr, eu); });
       PCG_MARK(5);
       const float *tv, *uv;
-      if (!aux_cheb(a, gid, tpg, tv, uv)) return;
+      if (!aux_cheb(a, sc, tv, uv)) return;
       PCG_MARK(8);
       if (!grid_sync(a.bar, a.status)) return;
       PCG_MARK(6);
       // phase 3: z = dinv r' + D t + Pi u
-      acc2[0] += aux_z<4>(a, r_new, tv, uv, gid, tpg);
+      acc2[0] += aux_z<4>(a, r_new, tv, uv, sc);
     }
     grid_sum_add<2>(acc2, a.red, kred);
     PCG_MARK(7);
@@ -807,6 +911,22 @@ __global__ void __launch_bounds__(256, FEMPIC_PCG_MIN_BLOCKS) k_pcg(PcgArgs a) {
     *a.res_out = bnorm > 0.0 ? rnorm / bnorm : 0.0;
     if (!conv) atomicOr(a.status, kStatusCG);
 #ifdef FEMPIC_PCG_PROFILE
+    if (it > 10) {
+      const int nb = min((int)gridDim.x, 4096);
+      double mn = 1e30, mx = 0, sum = 0, amx = 0, asum = 0;
+      for (int b = 0; b < nb; ++b) {
+        const double d = 1e-3 * (double)(g_pcg_stamp[b][1] - g_pcg_stamp[b][0]);
+        const double ad = 1e-3 * (double)(g_pcg_stamp[b][2] - g_pcg_stamp[b][1]);
+        mn = fmin(mn, d);
+        mx = fmax(mx, d);
+        sum += d;
+        amx = fmax(amx, ad);
+        asum += ad;
+      }
+      printf("PCGSTAMP it=10 A product per CTA min/mean/max %.1f/%.1f/%.1f us; reduction add mean/max %.1f/%.1f us; "
+             "barrier exit CTA0 %.1f us\n",
+             mn, sum / nb, mx, asum / nb, amx, 1e-3 * (double)(g_pcg_stamp[0][3] - g_pcg_stamp[0][0]));
+    }
     printf("PCGPROF it=%d loop_top+totals=%.1f p_update=%.1f bar0=%.1f spmv=%.1f bar1=%.1f xr_aux_t=%.1f cheb=%.1f "
            "bar2=%.1f aux_z=%.1f (us)\n",
            it, prof_acc[0] * 1e-3, prof_acc[1] * 1e-3, prof_acc[2] * 1e-3, prof_acc[3] * 1e-3, prof_acc[4] * 1e-3,
