@@ -10,7 +10,14 @@
   reference tet by least squares (the bases are written in barycentric
   coordinates and their gradients, so the coefficients are the same on every
   tet) and assembled, with a check that shared entities get equal values;
-* the nodal Laplacian L = D^T [*eps] D and the nodal load <W0_k, 1>.
+* the nodal Laplacian L = D^T [*eps] D and the nodal load <W0_k, 1>;
+* the surface impedance matrix of Section III-A,
+  [*_I]_ij = <n x W1_i, Y n x W1_j> over the impedance faces (eq.
+  impedanceBC).  Reading: the printed weight is mu^-1, but only the
+  admittance Y makes the term commensurate with [*eps] d/dt e (the weak form
+  of Ampere's law picks up  Y int (n x W_i).(n x E) dS  from n x H =
+  Y n x n x E); Y = Y0 = sqrt(eps0 / mu0), free space, for the first-order
+  absorbing condition.
 
 Integrals use the collapsed-cube rule with 4 points per direction (exact for
 degree 5 >= 2p).
@@ -20,10 +27,11 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import basis
-from .quadrature import tet_rule
+from .quadrature import tet_rule, tri_rule
 
 EPS0 = 8.8541878128e-12
 MU0 = 1.25663706212e-6
+Y0 = (EPS0 / MU0) ** 0.5
 
 G_REF = np.array([[-1.0, -1.0, -1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
 
@@ -146,3 +154,36 @@ def nodal_load(topo, g, vol):
     out = np.zeros(topo.n0)
     np.add.at(out, topo.dof0.ravel(), loc.ravel())
     return out
+
+
+def impedance(topo, g, Y=None):
+    """[*_I]_ij = Y <n x W1_i, n x W1_j> over the faces tagged impedance: on
+    each such face (the face opposite local vertex i of its tet, where
+    lambda_i = 0) the tangential part W - (W.n) n of every local W1 function
+    is integrated against every other with the collapsed triangle rule of
+    order + 2 points per direction (exact for degree 2p + 2)."""
+    Y = Y0 if Y is None else Y
+    n1 = topo.n1
+    rows, cols, vals = [], [], []
+    lam2, w2 = tri_rule(topo.order + 2)
+    for f in np.nonzero(topo.imp_face)[0]:
+        tt, i = None, None
+        hit = np.nonzero(topo.tet_faces == f)
+        tt, i = int(hit[0][0]), int(hit[1][0])
+        verts = [k for k in range(4) if k != i]
+        lam = np.zeros((len(w2), 4))
+        for j, k in enumerate(verts):
+            lam[:, k] = lam2[:, j]
+        P = topo.xyz[topo.tets[tt]]
+        area = 0.5 * np.linalg.norm(np.cross(P[verts[1]] - P[verts[0]], P[verts[2]] - P[verts[0]]))
+        nrm = g[tt, i] / np.linalg.norm(g[tt, i])
+        W = basis.w1(topo.order, lam, np.broadcast_to(g[tt], (len(w2), 4, 3)))
+        Wt = W - np.einsum("qjk,k->qj", W, nrm)[:, :, None] * nrm[None, None, :]
+        ke = Y * 2.0 * area * np.einsum("q,qak,qbk->ab", w2, Wt, Wt)
+        d = topo.dof1[tt]
+        rows.append(np.repeat(d, len(d)))
+        cols.append(np.tile(d, len(d)))
+        vals.append(ke.ravel())
+    if not rows:
+        return sp.csr_matrix((n1, n1))
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n1, n1))

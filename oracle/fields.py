@@ -28,8 +28,19 @@ weights
    = -(g^{n+1} - 2 g^n + g^{n-1}),
 followed by the same trapezoidal b update.
 
-The boundary is PEC (Dirichlet n x E = 0): W1 DOFs on boundary edges/faces
-are fixed at 0.  Linear systems are solved directly (sparse LU).
+Boundaries: PEC faces (Dirichlet n x E = 0) hold their W1 DOFs at 0.
+Impedance faces (first-order absorbing, eq. impedanceBC) add the surface
+impedance matrix I = [*_I] to the e row of the first-order system (Section
+III-A, the S matrix): [*eps] e' = C^T [*mu^-1] b - I e - g'.  The trapezoid
+rule then gives
+
+  ([*eps] + dt^2/4 K + dt/2 I) e^{n+1} = ([*eps] - dt^2/4 K - dt/2 I) e^n
+                                         + dt C^T [*mu^-1] b^n - Delta g,
+
+and the discrete energy W = e.[*eps]e/2 + b.[*mu^-1]b/2 drops by exactly
+dt ebar.I ebar per step (ebar = (e^{n+1} + e^n)/2) without sources.  The
+wave form has no impedance term here.  Linear systems are solved directly
+(sparse LU).
 """
 
 import numpy as np
@@ -40,13 +51,21 @@ def newmark_coeffs(gamma, beta):
     return beta, 0.5 + gamma - 2.0 * beta, 0.5 - gamma + beta
 
 
-def system_matrix(M, K, dt, scheme, gamma=0.5, beta=0.25):
+def system_matrix(M, K, dt, scheme, gamma=0.5, beta=0.25, I=None):
     c1 = 0.25 if scheme == "trapezoid" else newmark_coeffs(gamma, beta)[0]
-    return (M + (c1 * dt * dt) * K).tocsr()
+    A = M + (c1 * dt * dt) * K
+    if I is not None and I.nnz:
+        if scheme != "trapezoid":
+            raise ValueError("impedance boundaries need the trapezoid scheme")
+        A = A + (0.5 * dt) * I
+    return A.tocsr()
 
 
-def rhs_trapezoid(M, K, CtM2, e_n, b_n, dg_np1, dt):
-    return (M @ e_n - (0.25 * dt * dt) * (K @ e_n) + dt * (CtM2 @ b_n)) - dg_np1
+def rhs_trapezoid(M, K, CtM2, e_n, b_n, dg_np1, dt, I=None):
+    r = (M @ e_n - (0.25 * dt * dt) * (K @ e_n) + dt * (CtM2 @ b_n)) - dg_np1
+    if I is not None and I.nnz:
+        r = r - (0.5 * dt) * (I @ e_n)
+    return r
 
 
 def rhs_wave(M, K, e_n, e_nm1, dg_np1, dg_n, dt, gamma, beta):

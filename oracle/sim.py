@@ -10,6 +10,12 @@ the Gauss residual D^T [*eps] e + rho + rho_ion <W0, 1> on interior W0 DOFs
 (the paper's "[div] D vs -[grad] G").  The electrostatic start solves the
 nodal Laplacian D^T [*eps] D phi = rho + rho_ion <W0,1> with phi = 0 on the
 boundary and sets e^0 = e^{-1} = -D phi (the paper is silent on the start).
+
+Several species (the paper's plasma-ball example: ions and electrons) are
+advanced one after the other with their own q, m and weight; their currents
+and charges add.  Particles are kept concatenated in species order.
+Impedance faces (``bface_tag``, see Topology) add [*_I] to the trapezoid
+rule (see fields).
 """
 
 import numpy as np
@@ -23,8 +29,8 @@ from .topology import Topology
 class Sim:
     def __init__(self, xyz, tets, order, q, m, weight, B0=(0.0, 0.0, 0.0),
                  rho_ion=0.0, scheme="trapezoid", gamma=0.5, beta=0.25, matrices=True,
-                 max_cross=4096):
-        self.topo = t = Topology(xyz, tets, order)
+                 max_cross=4096, bface_tag=None):
+        self.topo = t = Topology(xyz, tets, order, bface_tag)
         self.g, self.c, self.vol = barycentric_maps(t.xyz, t.tets)
         self.order = order
         self.q, self.m, self.weight = float(q), float(m), float(weight)
@@ -46,13 +52,37 @@ class Sim:
             self.CtM2 = (self.C.T @ self.M2).tocsr()
             self.D = assemble.grad_matrix(t)
             self.load = assemble.nodal_load(t, self.g, self.vol)
+            self.I = assemble.impedance(t, self.g)
+        self.species = [(self.q, self.m, self.weight)]
+        self.offsets = [0]
 
     # ----------------------------------------------------------------- state
     def set_particles(self, x, v, tet):
         self.x = np.array(x, dtype=np.float64)
         self.v = np.array(v, dtype=np.float64)
         self.tet = np.array(tet, dtype=np.int64)
-        self.rho = particles.measure_rho(self.topo, self.g, self.c, self.x, self.tet, self.qw)
+        self.offsets = [0, len(self.x)]
+        self.species = [(self.q, self.m, self.weight)]
+        self.rho = self._measure_rho(self.x, self.tet)
+
+    def set_species(self, species):
+        """species: list of dicts with q, m, weight, x, v, tet."""
+        self.species = [(float(s["q"]), float(s["m"]), float(s["weight"])) for s in species]
+        self.x = np.concatenate([np.asarray(s["x"], dtype=np.float64).reshape(-1, 3) for s in species])
+        self.v = np.concatenate([np.asarray(s["v"], dtype=np.float64).reshape(-1, 3) for s in species])
+        self.tet = np.concatenate([np.asarray(s["tet"], dtype=np.int64) for s in species])
+        self.offsets = list(np.cumsum([0] + [len(np.asarray(s["tet"])) for s in species]))
+        self.rho = self._measure_rho(self.x, self.tet)
+
+    def _slices(self):
+        for k, (q, m, w) in enumerate(self.species):
+            yield slice(self.offsets[k], self.offsets[k + 1]), q, m, w
+
+    def _measure_rho(self, x, tet):
+        rho = np.zeros(self.topo.n0)
+        for sl, q, m, w in self._slices():
+            rho += particles.measure_rho(self.topo, self.g, self.c, x[sl], tet[sl], q * w)
+        return rho
 
     def electrostatic_init(self):
         t = self.topo
@@ -68,29 +98,37 @@ class Sim:
 
     # ------------------------------------------------------------------ step
     def push_walk(self, dt):
-        """Particle half-step; returns the walk record."""
+        """Particle half-step of every species; returns the walk record
+        (per-particle arrays concatenated in species order, summed current)."""
         t = self.topo
-        E, B = particles.gather(t, self.g, self.c, self.e, self.b, self.B0, self.x, self.tet)
-        vn = particles.boris(self.v, E, B, self.q, self.m, dt)
-        x1 = self.x + dt * vn
-        xe, ve, te, dg, ncross, hsh, status = particles.walk_deposit(
-            t, self.g, self.c, self.x, x1, vn, self.tet, self.qw, t.n1, self.max_cross)
-        return dict(E=E, B=B, v_half=vn, x_target=x1, x=xe, v=ve, tet=te, dg=dg,
-                    ncross=ncross, hash=hsh, status=status)
+        parts = []
+        dg = np.zeros(t.n1)
+        for sl, q, m, w in self._slices():
+            E, B = particles.gather(t, self.g, self.c, self.e, self.b, self.B0, self.x[sl], self.tet[sl])
+            vn = particles.boris(self.v[sl], E, B, q, m, dt)
+            x1 = self.x[sl] + dt * vn
+            xe, ve, te, d, ncross, hsh, st = particles.walk_deposit(
+                t, self.g, self.c, self.x[sl], x1, vn, self.tet[sl], q * w, t.n1, self.max_cross)
+            dg += d
+            parts.append(dict(E=E, B=B, v_half=vn, x_target=x1, x=xe, v=ve, tet=te, ncross=ncross, hash=hsh,
+                              status=st))
+        out = {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
+        out["dg"] = dg
+        return out
 
     def step(self, dt):
         t = self.topo
         w = self.push_walk(dt)
-        A = fields.system_matrix(self.M, self.K, dt, self.scheme, self.gamma, self.beta)
+        A = fields.system_matrix(self.M, self.K, dt, self.scheme, self.gamma, self.beta, self.I)
         if self.scheme == "trapezoid":
-            r = fields.rhs_trapezoid(self.M, self.K, self.CtM2, self.e, self.b, w["dg"], dt)
+            r = fields.rhs_trapezoid(self.M, self.K, self.CtM2, self.e, self.b, w["dg"], dt, self.I)
         else:
             r = fields.rhs_wave(self.M, self.K, self.e, self.e_prev, w["dg"], self.dg_prev,
                                 dt, self.gamma, self.beta)
         w["rhs"] = r
         e_new = fields.solve(A, r, t.free1)
         b_new = fields.update_b(self.C, self.b, e_new, self.e, dt)
-        rho_new = particles.measure_rho(t, self.g, self.c, w["x"], w["tet"], self.qw)
+        rho_new = self._measure_rho(w["x"], w["tet"])
         w["continuity"] = (rho_new - self.rho) - self.D.T @ w["dg"]
         w["drho"] = rho_new - self.rho
         self.e_prev, self.e, self.b = self.e, e_new, b_new
@@ -98,6 +136,10 @@ class Sim:
         self.x, self.v, self.tet, self.rho = w["x"], w["v"], w["tet"], rho_new
         w["gauss"] = self.gauss_residual()
         return w
+
+    def energy(self):
+        """W = e.[*eps]e / 2 + b.[*mu^-1]b / 2 (self fields)."""
+        return 0.5 * self.e @ (self.M @ self.e) + 0.5 * self.b @ (self.M2 @ self.b)
 
     def gauss_residual(self):
         return self.D.T @ (self.M @ self.e) + self.rho + self.rho_ion * self.load

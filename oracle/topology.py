@@ -19,6 +19,16 @@ Canonical numbering (a reading: the paper states none):
   vertex, v=1: to the upper) then ``2*N_e + 2*face + v``; W2 DOFs are
   ``3*face + v`` then ``3*N_f + 3*tet + i``; W0 DOFs are nodes then
   ``N_n + edge`` (mid-edge Lagrange nodes).
+
+Boundary conditions (Section II, eq. bceq): every boundary face is either
+perfect electric conductor (Dirichlet n x E = 0, tag 0, the default) or
+impedance (eq. impedanceBC with Psi_I = 0, the first-order absorbing
+condition, tag 1).  ``bface_tag[t, i]`` tags the face opposite the i-th vertex
+of tet t as given (before sorting); it is read for boundary faces only.  A W1
+DOF is held at 0 when its edge or face lies on a PEC face (an edge shared by
+a PEC and an impedance face is PEC); DOFs on impedance faces only are free.
+W0 boundary DOFs (Dirichlet for the nodal Laplacian and the Gauss residual)
+remain all boundary nodes.
 """
 
 import numpy as np
@@ -34,11 +44,12 @@ class MeshError(ValueError):
 class Topology:
     """Entities, adjacency and DOF maps of a tet mesh for a given order."""
 
-    def __init__(self, xyz, tets, order):
+    def __init__(self, xyz, tets, order, bface_tag=None):
         if order not in (1, 2):
             raise ValueError("order must be 1 or 2")
         xyz = np.asarray(xyz, dtype=np.float64)
-        t = np.sort(np.asarray(tets, dtype=np.int64), axis=1)
+        t_in = np.asarray(tets, dtype=np.int64)
+        t = np.sort(t_in, axis=1)
         if t.size and (t.min() < 0 or t.max() >= len(xyz)):
             raise MeshError("tet references a node out of range")
         if np.any(t[:, 1:] == t[:, :-1]):
@@ -77,6 +88,29 @@ class Topology:
             self.tet2tet[a, ia], self.tet2face[a, ia] = b, ib
             self.tet2tet[b, ib], self.tet2face[b, ib] = a, ia
         self.boundary_face = count == 1
+        # boundary face tags: -1 interior, 0 PEC, 1 impedance
+        self.face_tag = np.where(self.boundary_face, 0, -1).astype(np.int64)
+        if bface_tag is not None:
+            tag_in = np.asarray(bface_tag, dtype=np.int64).reshape(nt, 4)
+            for tt in range(nt):
+                for i in range(4):
+                    tri = np.sort(np.delete(t_in[tt], i))
+                    # the face of the sorted tet that has the same three vertices
+                    j = int(np.nonzero(t[tt] == t_in[tt, i])[0][0])
+                    f = self.tet_faces[tt, j]
+                    assert np.array_equal(self.faces[f], tri)
+                    if self.boundary_face[f]:
+                        self.face_tag[f] = 1 if tag_in[tt, i] == 1 else 0
+        self.imp_face = self.face_tag == 1
+        pf = self.faces[self.face_tag == 0]
+        pedge = set()
+        for (a, b, c) in pf:
+            pedge.update([(a, b), (a, c), (b, c)])
+        self.pec_edge = np.zeros(len(self.edges), dtype=bool)
+        if pedge:
+            pe = np.array(sorted(pedge), dtype=np.int64)
+            key = self.edges[:, 0] * self.n_nodes + self.edges[:, 1]
+            self.pec_edge = np.isin(key, pe[:, 0] * self.n_nodes + pe[:, 1])
         bf = self.faces[self.boundary_face]
         self.boundary_node = np.zeros(self.n_nodes, dtype=bool)
         self.boundary_node[bf.ravel()] = True
@@ -99,7 +133,7 @@ class Topology:
             self.dof1 = te.copy()
             self.dof2 = tf.copy()
             self.dof0 = self.tets.copy()
-            self.pec1 = self.boundary_edge.copy()
+            self.pec1 = self.pec_edge.copy()
             self.bnd0 = self.boundary_node.copy()
         else:
             self.n1 = 2 * ne + 2 * nf
@@ -119,10 +153,10 @@ class Topology:
             self.dof2 = d2
             self.dof0 = np.concatenate([self.tets, nn + te], axis=1)
             pec = np.zeros(self.n1, dtype=bool)
-            be = np.nonzero(self.boundary_edge)[0]
+            be = np.nonzero(self.pec_edge)[0]
             pec[2 * be] = True
             pec[2 * be + 1] = True
-            bfid = np.nonzero(self.boundary_face)[0]
+            bfid = np.nonzero(self.face_tag == 0)[0]
             pec[2 * ne + 2 * bfid] = True
             pec[2 * ne + 2 * bfid + 1] = True
             self.pec1 = pec
