@@ -36,8 +36,9 @@
  *     W2 DOFs 3*face + v ((4 l_v - 1) w_stu for the v-th face vertex) then
  *     3*N_f + 3*tet + i (4 l_i w_(face opposite local vertex i), i = 0..2);
  *     W0 DOFs nodes then N_n + edge (mid-edge Lagrange nodes).
- *   - Units are SI.  The boundary is a perfect electric conductor: W1 DOFs on
- *     boundary edges/faces are held at 0 and particles reflect specularly.
+ *   - Units are SI.  Boundary faces are perfect electric conductors (W1 DOFs
+ *     on them held at 0) unless femPIC_create_ext tags them impedance
+ *     (first-order absorbing); particles reflect specularly at every wall.
  */
 #ifndef FEMPIC_H
 #define FEMPIC_H
@@ -97,7 +98,8 @@ enum {
   FEMPIC_E_PREV = 9,   /* double[N1]  e^{n-1} (wave scheme, CG initial guess)    */
   FEMPIC_DG_PREV = 10, /* double[N1]  Delta g of the step before (wave scheme)   */
   FEMPIC_DIAG = 11,    /* femPIC_diag (get only)                                */
-  FEMPIC_PHI = 12      /* double[N0]  potential of the electrostatic start (get) */
+  FEMPIC_PHI = 12,     /* double[N0]  potential of the electrostatic start (get) */
+  FEMPIC_SPECIES = 13  /* int32[Np]   species index of each particle (get)      */
 };
 
 /* ---- operators for femPIC_apply ----------------------------------------- */
@@ -182,6 +184,8 @@ typedef struct {
   int64_t nnz_V;            /* stored entries of Pi^T A Pi (0 without smoothing) */
   int32_t aux_cheb_degree;  /* Chebyshev degree of the auxiliary-space solves
                                in the CG preconditioner (1 = diagonal only)  */
+  int32_t n_species;        /* species of the handle                          */
+  int32_t n_impedance_faces; /* boundary faces with the absorbing condition   */
 } femPIC_info;
 
 /* Fill *opts with defaults: FP64, trapezoid, cg_rtol 1e-12, cg_max_it 2000,
@@ -196,6 +200,29 @@ void femPIC_default_opts(femPIC_opts* opts);
  * (femPIC_last_error); release it with femPIC_destroy. */
 int femPIC_create(const femPIC_mesh* mesh, int32_t order, const femPIC_species* species,
                   const femPIC_opts* opts, FemPIC** out);
+
+/* As femPIC_create, with two additions of the paper's problem statement:
+ *   - several species (up to FEMPIC_MAX_SPECIES, e.g. the ions and electrons
+ *     of the plasma-ball example, Section IV): species[k] has its own q, m and
+ *     weight; particle ids run through the species in order (species 0's
+ *     particles first), the order of FEMPIC_X/V/TET; their currents and charges
+ *     add;
+ *   - impedance faces (Section II, eq. impedanceBC with Psi_I = 0, the
+ *     first-order absorbing condition): bface_tag_host (NULL = all PEC) is
+ *     int32[4*n_tets], the tag of the face opposite the i-th vertex of each tet
+ *     as given in the mesh, read for boundary faces only: 0 PEC, 1 impedance.
+ *     The surface matrix [*_I]_ij = Y0 <n x W1_i, n x W1_j> (Section III-A;
+ *     Y0 = sqrt(eps0/mu0), free-space admittance) enters the trapezoid rule as
+ *     ([*eps] + dt^2/4 K + dt/2 [*_I]) e^{n+1} = ([*eps] - dt^2/4 K -
+ *     dt/2 [*_I]) e^n + dt C^T [*mu^-1] b^n - Delta g.  W1 DOFs on impedance
+ *     faces are free; an edge shared with a PEC face stays PEC.  Needs the
+ *     trapezoid scheme (FEMPIC_ERR_ARG otherwise).
+ * Errors as femPIC_create; n_species outside 1..FEMPIC_MAX_SPECIES, a NULL
+ * species array or a species with m <= 0, weight < 0 or a non-finite q gives
+ * FEMPIC_ERR_ARG.  Handles with several species cannot join a batch. */
+#define FEMPIC_MAX_SPECIES 8
+int femPIC_create_ext(const femPIC_mesh* mesh, int32_t order, const femPIC_species* species, int32_t n_species,
+                      const int32_t* bface_tag_host, const femPIC_opts* opts, FemPIC** out);
 
 /* Advance n_steps PIC steps of size dt (s): gather, Lorentz push, walk,
  * charge-conserving deposit, Newmark field solve, b update, rho measurement

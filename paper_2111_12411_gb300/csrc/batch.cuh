@@ -268,6 +268,8 @@ __device__ __forceinline__ ParticleArgs member_particle_args(const MemberDesc& d
   a.h = d.h;
   a.dt = d.dt;
   a.qw = d.qw;
+  a.pid = d.pid;
+  a.sp.n = 1;
   a.max_cross = d.max_cross;
   a.status = d.status;
   a.crossings = d.crossings;

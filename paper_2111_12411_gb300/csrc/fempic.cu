@@ -95,6 +95,14 @@ struct FemPIC {
   GridBarrier* bar = nullptr;
   int pcg_blocks_w1 = 0, pcg_blocks_w0 = 0;
   int32_t* apart = nullptr;  // [pcg_blocks_w1 + 1] per-CTA row ranges of A in the CG
+  // impedance (first-order absorbing) faces: Y0 <n x W1, n x W1> on M's pattern
+  // and, at order 2, in 2x2 blocks; null without such faces
+  int32_t n_imp_faces = 0;
+  double *Iv = nullptr, *bI = nullptr;
+  // species: ids [sp_off[k], sp_off[k+1]) belong to species k
+  int n_species = 1;
+  int64_t sp_off[kMaxSpecies + 1] = {};
+  double sp_q[kMaxSpecies] = {}, sp_m[kMaxSpecies] = {}, sp_w[kMaxSpecies] = {};
   // particles (device order), SoA
   double* px[3] = {nullptr, nullptr, nullptr};
   double* pv[3] = {nullptr, nullptr, nullptr};
@@ -124,6 +132,8 @@ struct FemPIC {
   int launches = 0;
   int pending_steps = 0;
 };
+
+static_assert(kMaxSpecies == FEMPIC_MAX_SPECIES, "species table size");
 
 namespace {
 
@@ -208,6 +218,20 @@ void cheb_coeffs(double lmax, int k, float (&c)[3][kMaxCheb]) {
     c[2][i] = (float)(2.0 * rn / de);
     rho = rn;
   }
+}
+
+// species table of a launch: q w and q dt / 2m per species (the same
+// expressions as the single-species scalars)
+SpeciesTable species_table(const FemPIC* h, double dt) {
+  SpeciesTable t;
+  memset(&t, 0, sizeof(t));
+  t.n = h->n_species;
+  for (int k = 0; k <= h->n_species && k <= kMaxSpecies; ++k) t.off[k] = (int32_t)h->sp_off[k];
+  for (int k = 0; k < h->n_species; ++k) {
+    t.qw[k] = h->sp_q[k] * h->sp_w[k];
+    t.h[k] = ((h->sp_q[k] / h->sp_m[k]) * dt) * 0.5;
+  }
+  return t;
 }
 
 // Cut rows 0..n-1 (prefix of stored entries `pre`, pre[n] = total) into
@@ -371,8 +395,10 @@ int form_system(FemPIC* h, double dt) {
     cr2 = c3 * dt * dt;   // R2 = M + c3 dt^2 K
   }
   int grid = grid_for(h->n1, 256, 1 << 30);
+  // impedance faces (trapezoid only): A += dt/2 I, R1 -= dt/2 I
+  const double ci_imp = h->Iv ? 0.5 * dt : 0.0;
   k_form_system<<<grid, 256, 0, h->stream>>>(h->n1, h->M.rp, h->M.ci, h->M.v, h->K.v, c1, cr1, h->Aval, h->R1val,
-                                             h->dinvA);
+                                             h->dinvA, h->Iv, ci_imp, -ci_imp);
   h->launches++;
   CK(cudaGetLastError());
   if (h->opts.scheme == FEMPIC_SCHEME_WAVE) {
@@ -397,7 +423,7 @@ int form_system(FemPIC* h, double dt) {
   }
   if (h->nb > 0) {
     k_form_blocks<<<grid_for(h->nb, 256, 1 << 30), 256, 0, h->stream>>>(h->nb, h->brp, h->bci, h->bM, h->bK, c1,
-                                                                        h->bA, h->binv);
+                                                                        h->bA, h->binv, h->bI, ci_imp);
     h->launches++;
   }
   h->launches++;
@@ -411,12 +437,13 @@ int measure_rho(FemPIC* h, double* rho_out) {
   if (h->np == 0) return FEMPIC_OK;
   int grid = grid_for(h->np, 256, 1 << 30);
   double qw = h->q * h->weight;
+  const SpeciesTable st = species_table(h, 0.0);
   if (h->order == 1)
     k_rho<1><<<grid, 256, 0, h->stream>>>(h->np, h->px[0], h->px[1], h->px[2], h->ptet, h->geom, h->dof0, qw,
-                                          rho_out);
+                                          rho_out, h->pid, st);
   else
     k_rho<2><<<grid, 256, 0, h->stream>>>(h->np, h->px[0], h->px[1], h->px[2], h->ptet, h->geom, h->dof0, qw,
-                                          rho_out);
+                                          rho_out, h->pid, st);
   h->launches++;
   CK(cudaGetLastError());
   return FEMPIC_OK;
@@ -509,6 +536,8 @@ int launch_particles(FemPIC* h, double dt) {
   a.max_cross = h->opts.max_cross;
   a.status = h->d_status;
   a.crossings = h->d_cross;
+  a.pid = h->pid;
+  a.sp = species_table(h, dt);
   if (h->np == 0) return FEMPIC_OK;
   int grid = grid_for(h->np, 256, 1 << 30);
   bool strict = h->opts.precision == FEMPIC_FP64_STRICT;
@@ -695,6 +724,7 @@ size_t what_bytes(const FemPIC* h, int32_t what) {
       return sizeof(double) * 3 * (size_t)h->np;
     case FEMPIC_TET:
     case FEMPIC_NCROSS:
+    case FEMPIC_SPECIES:
       return sizeof(int32_t) * (size_t)h->np;
     case FEMPIC_HASH:
       return sizeof(uint64_t) * (size_t)h->np;
@@ -731,6 +761,7 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
   if (!h) return FEMPIC_ERR_ARG;
   size_t need = what_bytes(h, what);
   if (need == 0 || (to_handle && (what == FEMPIC_DIAG || what == FEMPIC_PHI || what == FEMPIC_NCROSS ||
+                                  what == FEMPIC_SPECIES ||
                                   what == FEMPIC_HASH))) {
     h->err = "unknown or read-only quantity";
     return FEMPIC_ERR_ARG;
@@ -752,6 +783,16 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
       }
   }
   CK(cudaSetDevice(h->device));
+  if (what == FEMPIC_SPECIES) {  // fixed by the particle-id ranges
+    std::vector<int32_t> sp((size_t)h->np);
+    for (int k = 0; k < h->n_species; ++k)
+      for (int64_t i = h->sp_off[k]; i < h->sp_off[k + 1]; ++i) sp[(size_t)i] = k;
+    if (buf_on_device)
+      CK(cudaMemcpy(buf, sp.data(), need, cudaMemcpyHostToDevice));
+    else if (need)
+      memcpy(buf, sp.data(), need);
+    return FEMPIC_OK;
+  }
   cudaMemcpyKind up = buf_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   cudaMemcpyKind down = buf_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (what == FEMPIC_DIAG) {
@@ -823,7 +864,7 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
 }
 
 int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp, const femPIC_opts* opts,
-                FemPIC* h) {
+                FemPIC* h, const int32_t* bface_tag) {
   if (opts)
     h->opts = *opts;
   else
@@ -849,11 +890,16 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
   }
   HostModel hm;
   std::string err;
-  int code = build_model(mesh->xyz_host, mesh->n_nodes, mesh->tets_host, mesh->n_tets, order, &hm, &err);
+  int code = build_model(mesh->xyz_host, mesh->n_nodes, mesh->tets_host, mesh->n_tets, order, &hm, &err, bface_tag);
   if (code) {
     h->err = err;
     return code == 2 ? FEMPIC_ERR_MESH : FEMPIC_ERR_ARG;
   }
+  if (hm.n_imp_faces > 0 && o.scheme != FEMPIC_SCHEME_TRAPEZOID) {
+    h->err = "impedance (absorbing) faces need the trapezoid scheme";
+    return FEMPIC_ERR_ARG;
+  }
+  h->n_imp_faces = hm.n_imp_faces;
   // particle ownership check on the host: lambda >= -1e-9 in the given tet
   for (int64_t i = 0; i < sp->n; ++i) {
     int32_t t = sp->tet_host[i];
@@ -958,7 +1004,8 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
     // DOFs 2k, 2k+1 belong to one edge or face and share their couplings
     const int32_t nb = hm.n1 / 2;
     std::vector<int32_t> brp(nb + 1, 0), bci;
-    std::vector<double> bM, bK;
+    std::vector<double> bM, bK, bI;
+    const bool imp = !hm.Ival.empty();
     bool ok = (hm.n1 % 2) == 0;
     for (int32_t k = 0; k < nb && ok; ++k) {
       int32_t r0 = 2 * k, r1 = 2 * k + 1;
@@ -978,6 +1025,7 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
         const int32_t q0 = j, q1 = b1 + (j - b0);
         bM.insert(bM.end(), {hm.M.val[q0], hm.M.val[q0 + 1], hm.M.val[q1], hm.M.val[q1 + 1]});
         bK.insert(bK.end(), {hm.K.val[q0], hm.K.val[q0 + 1], hm.K.val[q1], hm.K.val[q1 + 1]});
+        if (imp) bI.insert(bI.end(), {hm.Ival[q0], hm.Ival[q0 + 1], hm.Ival[q1], hm.Ival[q1 + 1]});
       }
       brp[k + 1] = (int32_t)bci.size();
     }
@@ -987,9 +1035,11 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
       if ((rc = upload(h, &h->brp, brp)) || (rc = upload(h, &h->bci, bci)) || (rc = upload(h, &h->bM, bM)) ||
           (rc = upload(h, &h->bK, bK)) || (rc = dalloc(h, &h->bA, bM.size())) || (rc = dalloc(h, &h->binv, 4 * (size_t)nb)))
         return rc;
+      if (imp && (rc = upload(h, &h->bI, bI))) return rc;
     }
   }
   const size_t nnz = hm.M.col.size();
+  if (!hm.Ival.empty() && (rc = upload(h, &h->Iv, hm.Ival))) return rc;
   if ((rc = dalloc(h, &h->Aval, nnz)) || (rc = dalloc(h, &h->R1val, nnz)) ||
       (rc = dalloc(h, &h->R2val, o.scheme == FEMPIC_SCHEME_WAVE ? nnz : 1)) || (rc = dalloc(h, &h->dinvA, h->n1)) ||
       (rc = dalloc(h, &h->dinvL, h->n0)))
@@ -1136,9 +1186,68 @@ int femPIC_create(const femPIC_mesh* mesh, int32_t order, const femPIC_species* 
   *out = nullptr;
   FemPIC* h = new (std::nothrow) FemPIC();
   if (!h) return FEMPIC_ERR_OOM;
-  int rc = create_impl(mesh, order, species, opts, h);
+  h->n_species = 1;
+  if (species) {
+    h->sp_q[0] = species->q;
+    h->sp_m[0] = species->m;
+    h->sp_w[0] = species->weight;
+    h->sp_off[1] = species->n;
+  }
+  int rc = create_impl(mesh, order, species, opts, h, nullptr);
   *out = h;  // the handle carries the error message even on failure
   return rc;
+}
+
+int femPIC_create_ext(const femPIC_mesh* mesh, int32_t order, const femPIC_species* species, int32_t n_species,
+                      const int32_t* bface_tag_host, const femPIC_opts* opts, FemPIC** out) {
+  if (!out) return FEMPIC_ERR_ARG;
+  *out = nullptr;
+  FemPIC* h = new (std::nothrow) FemPIC();
+  if (!h) return FEMPIC_ERR_OOM;
+  *out = h;  // the handle carries the error message even on failure
+  if (!species || n_species < 1 || n_species > FEMPIC_MAX_SPECIES) {
+    h->err = "n_species must be 1.." + std::to_string(FEMPIC_MAX_SPECIES) + " with a species array";
+    return FEMPIC_ERR_ARG;
+  }
+  int64_t total = 0;
+  for (int32_t k = 0; k < n_species; ++k) {
+    const femPIC_species& sk = species[k];
+    if (sk.n < 0 || (sk.n > 0 && (!sk.x_host || !sk.v_host || !sk.tet_host)) || !(sk.m > 0) ||
+        !std::isfinite(sk.q) || !(sk.weight >= 0)) {
+      h->err = "invalid species " + std::to_string(k);
+      return FEMPIC_ERR_ARG;
+    }
+    h->sp_q[k] = sk.q;
+    h->sp_m[k] = sk.m;
+    h->sp_w[k] = sk.weight;
+    h->sp_off[k] = total;
+    total += sk.n;
+  }
+  h->sp_off[n_species] = total;
+  h->n_species = n_species;
+  if (total > INT32_MAX) {
+    h->err = "too many particles";
+    return FEMPIC_ERR_ARG;
+  }
+  if (n_species == 1) return create_impl(mesh, order, species, opts, h, bface_tag_host);
+  // one particle array in species order; species 0's constants stand as the scalars
+  std::vector<double> xs((size_t)3 * total), vs((size_t)3 * total);
+  std::vector<int32_t> ts((size_t)total);
+  for (int32_t k = 0; k < n_species; ++k) {
+    const femPIC_species& sk = species[k];
+    const int64_t o = h->sp_off[k];
+    if (sk.n > 0) {
+      std::copy(sk.x_host, sk.x_host + 3 * sk.n, xs.begin() + 3 * o);
+      std::copy(sk.v_host, sk.v_host + 3 * sk.n, vs.begin() + 3 * o);
+      std::copy(sk.tet_host, sk.tet_host + sk.n, ts.begin() + o);
+    }
+  }
+  femPIC_species all = species[0];
+  all.n = total;
+  all.x_host = xs.data();
+  all.v_host = vs.data();
+  all.tet_host = ts.data();
+  return create_impl(mesh, order, &all, opts, h, bface_tag_host);
 }
 
 int femPIC_step_async(FemPIC* h, double dt, int32_t n) {
@@ -1391,6 +1500,8 @@ int femPIC_get_info(const FemPIC* h, femPIC_info* info) {
   info->nnz_L = h->L.nnz;
   info->nnz_V = h->V.nnz;
   info->aux_cheb_degree = h->cheb_k;
+  info->n_species = h->n_species;
+  info->n_impedance_faces = h->n_imp_faces;
   return FEMPIC_OK;
 }
 
@@ -1650,6 +1761,10 @@ int femPIC_batch_create(FemPIC* const* members, int32_t n, FemPICBatch** out) {
     }
     if (h->opts.precision == FEMPIC_FP64_STRICT || h->opts.scheme != FEMPIC_SCHEME_TRAPEZOID) {
       b->err = "batched members must use FEMPIC_FP64 or FEMPIC_MIXED and the trapezoid scheme";
+      return FEMPIC_ERR_ARG;
+    }
+    if (h->n_species != 1) {
+      b->err = "batched members must have a single species";
       return FEMPIC_ERR_ARG;
     }
     if (h->n_tets > 1024 * 1024) {

@@ -46,6 +46,8 @@ struct HostModel {
   std::vector<double> load0;     // <W0_k, 1>
   HostCSR Pi, PiT;               // vector nodal interpolation: W1 coefficients of hat_v e_c
   std::vector<double> dvM, dvK;  // diag(Pi^T M Pi), diag(Pi^T K Pi)
+  int32_t n_imp_faces = 0;       // boundary faces with the impedance (absorbing) condition
+  std::vector<double> Ival;      // Y0 <n x W1_i, n x W1_j> over impedance faces, on M's pattern
   HostCSR VM;                    // Pi^T M Pi (values) and its pattern
   std::vector<double> VK;        // Pi^T K Pi on VM's pattern
 };
@@ -59,16 +61,21 @@ struct LocalTables {
   std::vector<double> T2;    // [nl2][nl2][6][6]: int_ref P2_{f,ab} P2_{h,cd}
   std::vector<double> I0;    // [nl0]: int_ref W0_k
   std::vector<double> Rv;    // order 2: [4][4][nl1]: W1 coefficients of l_v grad l_a
+  std::vector<double> TF;    // [4][nl1][nl1][4][4]: int over the face opposite vertex i of the
+                             // reference tet of P1_ia P1_jb, per unit of twice the face area
 };
 
 // Returns "" on success, else an error message.
 std::string build_local_tables(int order, LocalTables* out);
 // code: 0 ok, 2 mesh error, 1 argument error.
+// bface_tag (nullable): [4*n_tets], tag of the face opposite the i-th vertex
+// of each tet as given: 0 PEC, 1 impedance (read for boundary faces only).
 int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets, int32_t n_tets,
-                int order, HostModel* m, std::string* err);
+                int order, HostModel* m, std::string* err, const int32_t* bface_tag = nullptr);
 
 // Physical constants (CODATA 2018).
 constexpr double kEps0 = 8.8541878128e-12;
 constexpr double kMu0 = 1.25663706212e-6;
+// free-space admittance sqrt(eps0 / mu0) of the first-order absorbing condition
 
 }  // namespace fempic

@@ -257,6 +257,23 @@ __device__ __forceinline__ void deposit_rho(const double* l, double qw, const in
   }
 }
 
+// Several species: particle ids are given out in species order, so species k
+// owns the ids [off[k], off[k+1]); its charge weight q w and push factor
+// q dt / 2m come from the table (n == 1: the scalar qw, h of the launch).
+constexpr int kMaxSpecies = 8;
+struct SpeciesTable {
+  int n;
+  int32_t off[kMaxSpecies + 1];
+  double qw[kMaxSpecies];
+  double h[kMaxSpecies];
+};
+
+__device__ __forceinline__ int species_of(const SpeciesTable& s, int32_t id) {
+  int k = 0;
+  while (k + 1 < s.n && id >= s.off[k + 1]) ++k;
+  return k;
+}
+
 struct ParticleArgs {
   int64_t n;
   double* x[3];
@@ -280,7 +297,20 @@ struct ParticleArgs {
   int max_cross;
   int32_t* status;
   unsigned long long* crossings;
+  const int32_t* pid;  // particle ids in device order (read only with several species)
+  SpeciesTable sp;
 };
+
+// q w and q dt / 2m of the particle in device slot i
+__device__ __forceinline__ void particle_consts(const ParticleArgs& a, int64_t i, double& qw, double& h) {
+  qw = a.qw;
+  h = a.h;
+  if (a.sp.n > 1) {
+    const int k = species_of(a.sp, __ldg(a.pid + i));
+    qw = a.sp.qw[k];
+    h = a.sp.h[k];
+  }
+}
 
 // One thread per particle: gather, push, walk, deposit, charge.
 template <int P, class Ar>
@@ -294,6 +324,8 @@ __global__ void __launch_bounds__(256) k_particle(ParticleArgs a) {
     int T = a.tet[i];
     double x[3] = {a.x[0][i], a.x[1][i], a.x[2][i]};
     double v[3] = {a.v[0][i], a.v[1][i], a.v[2][i]};
+    double qw, hq;
+    particle_consts(a, i, qw, hq);
     TetGeom G;
     load_geom(a.geom, T, G);
     double l[4];
@@ -308,7 +340,7 @@ __global__ void __launch_bounds__(256) k_particle(ParticleArgs a) {
     double E[3], B[3];
     gather_E<P, Ar>(G, l, ev, E);
     gather_B<P, Ar>(G, l, bv, a.B0, B);
-    boris<Ar>(v, E, B, a.h);
+    boris<Ar>(v, E, B, hq);
     double pa[3] = {x[0], x[1], x[2]};
     double pb[3];
 #pragma unroll
@@ -334,9 +366,9 @@ __global__ void __launch_bounds__(256) k_particle(ParticleArgs a) {
         }
       }
       double s1 = best < 0 ? 1.0 : fmin(fmax(sbest, s0), 1.0);
-      deposit_segment<P, Ar>(la, lb, s0, s1, a.qw, a.dof1 + (size_t)T * N1, a.dg);
+      deposit_segment<P, Ar>(la, lb, s0, s1, qw, a.dof1 + (size_t)T * N1, a.dg);
       if (best < 0) {
-        deposit_rho<P, Ar>(lb, a.qw, a.dof0 + (size_t)T * N0, a.rho);
+        deposit_rho<P, Ar>(lb, qw, a.dof0 + (size_t)T * N0, a.rho);
         break;
       }
       ++nc;
@@ -382,7 +414,7 @@ __global__ void __launch_bounds__(256) k_particle(ParticleArgs a) {
       if (nc >= a.max_cross) {
         double lf[4];
         bary<Ar>(G, pb, lf);
-        deposit_rho<P, Ar>(lf, a.qw, a.dof0 + (size_t)T * N0, a.rho);
+        deposit_rho<P, Ar>(lf, qw, a.dof0 + (size_t)T * N0, a.rho);
         atomicOr(a.status, kStatusWalk);
         break;
       }
@@ -406,10 +438,12 @@ __global__ void __launch_bounds__(256) k_particle(ParticleArgs a) {
 // rho from positions (used at start and after the state is set)
 template <int P>
 __global__ void k_rho(int64_t n, const double* x0, const double* x1, const double* x2, const int32_t* tet,
-                      const double* geom, const int32_t* dof0, double qw, double* rho) {
+                      const double* geom, const int32_t* dof0, double qw, double* rho, const int32_t* pid,
+                      SpeciesTable sp) {
   constexpr int N0 = P == 1 ? 4 : 10;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (sp.n > 1) qw = sp.qw[species_of(sp, __ldg(pid + i))];
   int T = tet[i];
   TetGeom G;
   load_geom(geom, T, G);

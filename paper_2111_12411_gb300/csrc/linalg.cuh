@@ -148,16 +148,23 @@ __global__ void k_axpy_to_f32(int64_t n, const double* __restrict__ a, const dou
     out[i] = (float)(a[i] + c * b[i]);
 }
 
-// A = M + ca K, R = M + cr K (same pattern), inverse diagonal of A (0 on empty rows)
+// A = M + ca K + ia I, R = M + cr K + ir I (one pattern; I, the surface
+// impedance matrix, may be null), inverse diagonal of A (0 on empty rows)
 __global__ void k_form_system(int32_t n, const int32_t* rp, const int32_t* ci, const double* m, const double* k,
-                              double ca, double cr, double* a, double* r, double* dinv) {
+                              double ca, double cr, double* a, double* r, double* dinv, const double* iv = nullptr,
+                              double ia = 0.0, double ir = 0.0) {
   int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
   double diag = 0.0;
   for (int j = rp[row]; j < rp[row + 1]; ++j) {
     double av = m[j] + ca * k[j];
+    double rv = m[j] + cr * k[j];
+    if (iv) {
+      av += ia * iv[j];
+      rv += ir * iv[j];
+    }
     a[j] = av;
-    if (r) r[j] = m[j] + cr * k[j];
+    if (r) r[j] = rv;
     if (ci[j] == row) diag = av;
   }
   dinv[row] = diag != 0.0 ? 1.0 / diag : 0.0;
@@ -165,12 +172,13 @@ __global__ void k_form_system(int32_t n, const int32_t* rp, const int32_t* ci, c
 
 // 2x2 blocks: Ab = bM + c bK and the inverse of each diagonal block (0 if absent)
 __global__ void k_form_blocks(int32_t nb, const int32_t* rp, const int32_t* ci, const double* bm, const double* bk,
-                              double c, double* ab, double* binv) {
+                              double c, double* ab, double* binv, const double* bi = nullptr, double ci_ = 0.0) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nb) return;
   double d[4] = {0.0, 0.0, 0.0, 0.0};
   for (int j = rp[k]; j < rp[k + 1]; ++j) {
-    for (int q = 0; q < 4; ++q) ab[4 * j + q] = bm[4 * j + q] + c * bk[4 * j + q];
+    for (int q = 0; q < 4; ++q)
+      ab[4 * j + q] = bi ? bm[4 * j + q] + c * bk[4 * j + q] + ci_ * bi[4 * j + q] : bm[4 * j + q] + c * bk[4 * j + q];
     if (ci[j] == k)
       for (int q = 0; q < 4; ++q) d[q] = ab[4 * j + q];
   }

@@ -327,6 +327,8 @@ __device__ __forceinline__ void particle_step(const ParticleArgs& a, int64_t i) 
   const int lane = threadIdx.x & 31;
   const bool valid = i < a.n;
   int T = valid ? a.tet[i] : 0;
+  double qw = a.qw, hq = a.h;
+  if (valid) particle_consts(a, i, qw, hq);
   double x[3], v[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -340,7 +342,7 @@ __device__ __forceinline__ void particle_step(const ParticleArgs& a, int64_t i) 
   if (MIXED) {
     float Ef[3], Bf[3], vf[3] = {(float)v[0], (float)v[1], (float)v[2]};
     gather_EB_f32<P>(G, la, a.e, a.dof1 + (size_t)T * N1, a.b, a.dof2 + (size_t)T * N2, a.B0, Ef, Bf);
-    boris_f32(vf, Ef, Bf, (float)a.h);
+    boris_f32(vf, Ef, Bf, (float)hq);
     v[0] = vf[0];
     v[1] = vf[1];
     v[2] = vf[2];
@@ -348,7 +350,7 @@ __device__ __forceinline__ void particle_step(const ParticleArgs& a, int64_t i) 
     double E[3], B[3];
     gather_E_fact<P>(G, la, a.e, a.dof1 + (size_t)T * N1, E);
     gather_B_fact<P>(G, la, a.b, a.dof2 + (size_t)T * N2, a.B0, B);
-    boris<Fast>(v, E, B, a.h);
+    boris<Fast>(v, E, B, hq);
   }
   double pa[3] = {x[0], x[1], x[2]};
   double pb[3];
@@ -361,7 +363,7 @@ __device__ __forceinline__ void particle_step(const ParticleArgs& a, int64_t i) 
   int best = exit_face(la, lb, -1, 0.0, s1);
   {
     const WarpRuns runs = AGG ? warp_runs(valid ? T : -1 - lane) : WarpRuns{0, 0, false};
-    deposit_fact<P>(la, lb, 0.0, s1, a.qw, a.dof1 + (size_t)T * N1, a.dg, AGG && runs.ok, runs, lane, valid);
+    deposit_fact<P>(la, lb, 0.0, s1, qw, a.dof1 + (size_t)T * N1, a.dg, AGG && runs.ok, runs, lane, valid);
   }
   int nc = 0;
   unsigned long long hsh = kFnvOffset;
@@ -413,13 +415,13 @@ __device__ __forceinline__ void particle_step(const ParticleArgs& a, int64_t i) 
     bary_fma(G, pb, lb);
     best = exit_face(la, lb, entry, s0, s1);
     WarpRuns none{0, 0, false};
-    deposit_fact<P>(la, lb, s0, s1, a.qw, a.dof1 + (size_t)T * N1, a.dg, false, none, lane, true);
+    deposit_fact<P>(la, lb, s0, s1, qw, a.dof1 + (size_t)T * N1, a.dg, false, none, lane, true);
     walking = best >= 0;
   }
   // ---- charge at the end point, summed over lanes ending in the same tet
   {
     const WarpRuns runs = AGG ? warp_runs(valid ? T : -1 - lane) : WarpRuns{0, 0, false};
-    deposit_rho_fact<P>(lb, a.qw, a.dof0 + (size_t)T * N0, a.rho, AGG && runs.ok, runs, lane, valid);
+    deposit_rho_fact<P>(lb, qw, a.dof0 + (size_t)T * N0, a.rho, AGG && runs.ok, runs, lane, valid);
   }
   if (valid) {
 #pragma unroll

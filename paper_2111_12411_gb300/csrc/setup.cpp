@@ -127,6 +127,24 @@ Rat integrate_bary(const Poly& p) {
   return s;
 }
 
+// int over the face l_i = 0 of l_a^. l_b^. l_c^. (the other three), per unit
+// of twice the face area: a! b! c! / (a+b+c+2)!; monomials with l_i vanish
+Rat integrate_face(const Poly& p, int face) {
+  Rat s = R(0);
+  for (auto& kv : p.c) {
+    if (ex(kv.first, face) != 0) continue;
+    long long num = 1;
+    int tot = 0;
+    for (int v = 0; v < 4; ++v)
+      if (v != face) {
+        num *= fact(ex(kv.first, v));
+        tot += ex(kv.first, v);
+      }
+    s = s + kv.second * mk((i128)num, (i128)fact(tot + 2));
+  }
+  return s;
+}
+
 // Barycentric -> Cartesian on the reference tet: l0 = 1-x-y-z, l1 = x, l2 = y, l3 = z.
 Poly to_xyz(const Poly& p) {
   Poly X, Y, Z;
@@ -445,6 +463,16 @@ std::string build_local_tables(int p, LocalTables* T) {
           if (f2[i][a].c.empty() || f2[j][b].c.empty()) continue;
           T->T2[(((size_t)i * n2 + j) * 6 + a) * 6 + b] = to_double(integrate_bary(pmul(f2[i][a], f2[j][b])));
         }
+  T->TF.assign((size_t)4 * n1 * n1 * 16, 0.0);
+  for (int fc = 0; fc < 4; ++fc)
+    for (int i = 0; i < n1; ++i)
+      for (int j = 0; j < n1; ++j)
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) {
+            if (f1[i][a].c.empty() || f1[j][b].c.empty()) continue;
+            T->TF[((((size_t)fc * n1 + i) * n1 + j) * 4 + a) * 4 + b] =
+                to_double(integrate_face(pmul(f1[i][a], f1[j][b]), fc));
+          }
   T->I0.resize(T->nl0);
   for (int k = 0; k < T->nl0; ++k) T->I0[k] = to_double(integrate_bary(f0[k]));
   if (p == 2) {
@@ -467,7 +495,7 @@ std::string build_local_tables(int p, LocalTables* T) {
 }
 
 int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets_in, int32_t n_tets, int p,
-                HostModel* m, std::string* err) {
+                HostModel* m, std::string* err, const int32_t* bface_tag) {
   if (p != 1 && p != 2) {
     *err = "order must be 1 or 2";
     return 1;
@@ -569,13 +597,33 @@ int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets_in, int3
       bnode[faces[f].a] = bnode[faces[f].b] = bnode[faces[f].c] = 1;
     }
   }
-  // boundary edges: edges of boundary faces
+  // boundary face tags (face opposite the i-th given vertex -> sorted local face)
+  std::vector<uint8_t> fimp(m->n_faces, 0);
+  if (bface_tag) {
+    for (int32_t t = 0; t < nt; ++t)
+      for (int i = 0; i < 4; ++i) {
+        if (bface_tag[(size_t)t * 4 + i] != 1) continue;
+        const int32_t vid = tets_in[(size_t)t * 4 + i];
+        int k = 0;
+        while (k < 4 && m->tets[(size_t)t * 4 + k] != vid) ++k;
+        const int32_t f = tet_face[(size_t)t * 4 + k];
+        if (bface[f]) fimp[f] = 1;
+      }
+  }
+  m->n_imp_faces = 0;
+  for (int32_t f = 0; f < m->n_faces; ++f) m->n_imp_faces += fimp[f];
+  // boundary edges: edges of boundary faces; PEC edges: edges of PEC faces
+  std::vector<uint8_t> pedge(m->n_edges, 0);
   for (int32_t t = 0; t < nt; ++t)
     for (int k = 0; k < 4; ++k) {
-      if (!bface[tet_face[(size_t)t * 4 + k]]) continue;
+      const int32_t f = tet_face[(size_t)t * 4 + k];
+      if (!bface[f]) continue;
       for (int j = 0; j < 6; ++j) {
         int s = kLocalEdges[j][0], u = kLocalEdges[j][1];
-        if (s != k && u != k) bedge[tet_edge[(size_t)t * 6 + j]] = 1;
+        if (s != k && u != k) {
+          bedge[tet_edge[(size_t)t * 6 + j]] = 1;
+          if (!fimp[f]) pedge[tet_edge[(size_t)t * 6 + j]] = 1;
+        }
       }
     }
   // ---- DOF numbering --------------------------------------------------------
@@ -593,7 +641,7 @@ int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets_in, int3
       for (int k = 0; k < 4; ++k) m->dof2[(size_t)t * 4 + k] = tet_face[(size_t)t * 4 + k];
       for (int k = 0; k < 4; ++k) m->dof0[(size_t)t * 4 + k] = m->tets[(size_t)t * 4 + k];
     }
-    m->pec1.assign(bedge.begin(), bedge.end());
+    m->pec1.assign(pedge.begin(), pedge.end());
     m->bnd0.assign(bnode.begin(), bnode.end());
   } else {
     if ((int64_t)2 * ne + 2 * (int64_t)nf > INT32_MAX || (int64_t)3 * nf + 3 * (int64_t)nt > INT32_MAX) {
@@ -620,9 +668,9 @@ int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets_in, int3
     }
     m->pec1.assign(m->n1, 0);
     for (int32_t e2 = 0; e2 < ne; ++e2)
-      if (bedge[e2]) m->pec1[2 * e2] = m->pec1[2 * e2 + 1] = 1;
+      if (pedge[e2]) m->pec1[2 * e2] = m->pec1[2 * e2 + 1] = 1;
     for (int32_t f = 0; f < nf; ++f)
-      if (bface[f]) m->pec1[2 * ne + 2 * f] = m->pec1[2 * ne + 2 * f + 1] = 1;
+      if (bface[f] && !fimp[f]) m->pec1[2 * ne + 2 * f] = m->pec1[2 * ne + 2 * f + 1] = 1;
     m->bnd0.assign(m->n0, 0);
     for (int32_t v = 0; v < nn; ++v) m->bnd0[v] = bnode[v];
     for (int32_t e2 = 0; e2 < ne; ++e2) m->bnd0[nn + e2] = bedge[e2];
@@ -786,6 +834,53 @@ int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets_in, int3
       scatter(&m->DT, r0, r1, l0, l1, DT_loc.data(), all0, all1, true);
       for (int k = 0; k < l0; ++k) m->load0[r0[k]] += bW[q * l0 + k];
     }
+  }
+  // ---- surface impedance matrix Y0 <n x W1_i, n x W1_j> over the impedance
+  // faces, on M's pattern: the tangential part of grad l_x on the face opposite
+  // local vertex i is grad l_x - (grad l_x . n) n with n = grad l_i / |grad l_i|
+  m->Ival.clear();
+  if (m->n_imp_faces > 0) {
+    HostCSR Ih = m->M;
+    std::fill(Ih.val.begin(), Ih.val.end(), 0.0);
+    const double Y0 = std::sqrt(kEps0 / kMu0);
+    std::vector<double> Ie((size_t)l1 * l1);
+    for (int32_t t = 0; t < nt; ++t)
+      for (int i = 0; i < 4; ++i) {
+        if (!fimp[tet_face[(size_t)t * 4 + i]]) continue;
+        const double* g = &m->geom[(size_t)t * 16];
+        const double gn = std::sqrt(g[3 * i] * g[3 * i] + g[3 * i + 1] * g[3 * i + 1] + g[3 * i + 2] * g[3 * i + 2]);
+        const double nv[3] = {g[3 * i] / gn, g[3 * i + 1] / gn, g[3 * i + 2] / gn};
+        double Gt[4][4];
+        for (int x = 0; x < 4; ++x)
+          for (int y = 0; y < 4; ++y) {
+            const double* gx = g + 3 * x;
+            const double* gy = g + 3 * y;
+            const double dxy = gx[0] * gy[0] + gx[1] * gy[1] + gx[2] * gy[2];
+            const double dxn = gx[0] * nv[0] + gx[1] * nv[1] + gx[2] * nv[2];
+            const double dyn = gy[0] * nv[0] + gy[1] * nv[1] + gy[2] * nv[2];
+            Gt[x][y] = dxy - dxn * dyn;
+          }
+        int fv[3], q = 0;
+        for (int k = 0; k < 4; ++k)
+          if (k != i) fv[q++] = m->tets[(size_t)t * 4 + k];
+        double u[3], w[3];
+        for (int k = 0; k < 3; ++k) {
+          u[k] = xyz[3 * (size_t)fv[1] + k] - xyz[3 * (size_t)fv[0] + k];
+          w[k] = xyz[3 * (size_t)fv[2] + k] - xyz[3 * (size_t)fv[0] + k];
+        }
+        const double cx = u[1] * w[2] - u[2] * w[1], cy = u[2] * w[0] - u[0] * w[2], cz = u[0] * w[1] - u[1] * w[0];
+        const double area2 = std::sqrt(cx * cx + cy * cy + cz * cz);
+        for (int a = 0; a < l1; ++a)
+          for (int b = 0; b < l1; ++b) {
+            const double* tf = &T.TF[((((size_t)i * l1 + a) * l1 + b) * 4) * 4];
+            double sum = 0.0;
+            for (int x = 0; x < 4; ++x)
+              for (int y = 0; y < 4; ++y) sum += Gt[x][y] * tf[x * 4 + y];
+            Ie[(size_t)a * l1 + b] = Y0 * area2 * sum;
+          }
+        scatter(&Ih, d1 + (size_t)t * l1, d1 + (size_t)t * l1, l1, l1, Ie.data(), free1, free1, false);
+      }
+    m->Ival = Ih.val;
   }
   // ---- vector nodal interpolation Pi (auxiliary space of the preconditioner)
   {

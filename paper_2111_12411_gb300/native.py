@@ -21,7 +21,8 @@ ERROR_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_MESH", 3: "ERR_OOM", 4: "ERR_CUDA"
 PRECISION = {"fp64_strict": 0, "fp64": 1, "mixed": 2}
 SCHEME = {"trapezoid": 0, "wave": 1}
 QUANTITY = {"E": 0, "B": 1, "DG": 2, "RHO": 3, "X": 4, "V": 5, "TET": 6, "NCROSS": 7, "HASH": 8,
-            "E_PREV": 9, "DG_PREV": 10, "DIAG": 11, "PHI": 12}
+            "E_PREV": 9, "DG_PREV": 10, "DIAG": 11, "PHI": 12, "SPECIES": 13}
+MAX_SPECIES = 8
 OPERATOR = {"M1": 0, "K": 1, "C": 2, "D": 3, "DT": 4, "M2": 5, "A": 6, "L": 7, "PI": 8, "PIT": 9}
 
 
@@ -63,7 +64,8 @@ class femPIC_info(ctypes.Structure):
                 ("nnz_A", ctypes.c_int64), ("nnz_C", ctypes.c_int64), ("nnz_Q", ctypes.c_int64),
                 ("nnz_D", ctypes.c_int64), ("nnz_DT", ctypes.c_int64), ("nnz_Pi", ctypes.c_int64),
                 ("n_boundary_faces", ctypes.c_int32), ("device_bytes", ctypes.c_size_t),
-                ("nnz_L", ctypes.c_int64), ("nnz_V", ctypes.c_int64), ("aux_cheb_degree", ctypes.c_int32)]
+                ("nnz_L", ctypes.c_int64), ("nnz_V", ctypes.c_int64), ("aux_cheb_degree", ctypes.c_int32),
+                ("n_species", ctypes.c_int32), ("n_impedance_faces", ctypes.c_int32)]
 
 
 # (name, restype, argtypes) of every exported symbol declared in include/fempic.h
@@ -73,6 +75,9 @@ EXPORTS = [
     ("femPIC_create", ctypes.c_int, [ctypes.POINTER(femPIC_mesh), ctypes.c_int32,
                                      ctypes.POINTER(femPIC_species), ctypes.POINTER(femPIC_opts),
                                      ctypes.POINTER(_P)]),
+    ("femPIC_create_ext", ctypes.c_int, [ctypes.POINTER(femPIC_mesh), ctypes.c_int32,
+                                         ctypes.POINTER(femPIC_species), ctypes.c_int32, _P,
+                                         ctypes.POINTER(femPIC_opts), ctypes.POINTER(_P)]),
     ("femPIC_step", ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int32]),
     ("femPIC_step_async", ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int32]),
     ("femPIC_sync", ctypes.c_int, [_P]),
@@ -144,6 +149,36 @@ def femPIC_create(xyz, tets, order, q, m, weight, x, v, tet, opts=None):
     h = ctypes.c_void_p()
     rc = lib.femPIC_create(ctypes.byref(mesh), order, ctypes.byref(sp),
                            ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
+    if rc != FEMPIC_OK:
+        msg = lib.femPIC_last_error(h).decode() if h.value else "create failed"
+        if h.value:
+            lib.femPIC_destroy(h)
+        raise FemPICError(rc, msg)
+    return h
+
+
+def femPIC_create_ext(xyz, tets, order, species, bface_tag=None, opts=None):
+    """species: list of dicts with q, m, weight, x, v, tet; bface_tag:
+    int32[n_tets, 4] (0 PEC, 1 impedance) or None."""
+    lib = load()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    mesh = femPIC_mesh(len(xyz), len(tets), _ptr(xyz), _ptr(tets))
+    keep = []
+    arr = (femPIC_species * max(1, len(species)))()
+    for k, spc in enumerate(species):
+        x = np.ascontiguousarray(spc["x"], dtype=np.float64).reshape(-1, 3)
+        v = np.ascontiguousarray(spc["v"], dtype=np.float64).reshape(-1, 3)
+        tet = np.ascontiguousarray(spc["tet"], dtype=np.int32)
+        keep += [x, v, tet]
+        arr[k] = femPIC_species(spc["q"], spc["m"], spc["weight"], len(x), _ptr(x), _ptr(v), _ptr(tet))
+    tag = None
+    if bface_tag is not None:
+        tag = np.ascontiguousarray(bface_tag, dtype=np.int32).reshape(len(tets), 4)
+        keep.append(tag)
+    h = ctypes.c_void_p()
+    rc = lib.femPIC_create_ext(ctypes.byref(mesh), order, arr, len(species), _ptr(tag) if tag is not None else None,
+                               ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
     if rc != FEMPIC_OK:
         msg = lib.femPIC_last_error(h).decode() if h.value else "create failed"
         if h.value:
@@ -250,7 +285,7 @@ class Simulation:
     def __init__(self, xyz, tets, order, q, m, weight, x, v, tet, precision="fp64",
                  scheme="trapezoid", gamma=0.5, beta=0.25, cg_rtol=1e-12, cg_max_it=2000,
                  max_cross=4096, sort_period=1, B0=(0.0, 0.0, 0.0), rho_ion=0.0, es_init=True,
-                 diagnostics=False, device=0, stream=None):
+                 diagnostics=False, device=0, stream=None, species=None, bface_tag=None):
         o = default_opts()
         o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
         o.scheme = SCHEME[scheme] if isinstance(scheme, str) else int(scheme)
@@ -261,7 +296,12 @@ class Simulation:
         o.rho_ion = rho_ion
         o.es_init, o.diagnostics, o.device = int(es_init), int(diagnostics), device
         o.stream = stream
-        self.h = femPIC_create(xyz, tets, order, q, m, weight, x, v, tet, o)
+        if species is None and bface_tag is None:
+            self.h = femPIC_create(xyz, tets, order, q, m, weight, x, v, tet, o)
+        else:
+            if species is None:
+                species = [dict(q=q, m=m, weight=weight, x=x, v=v, tet=tet)]
+            self.h = femPIC_create_ext(xyz, tets, order, species, bface_tag, o)
         self.info = femPIC_get_info(self.h)
         self.n_particles = int(self.info.n_particles)
 
@@ -278,7 +318,7 @@ class Simulation:
         return {"E": (n1, np.float64), "E_PREV": (n1, np.float64), "DG": (n1, np.float64),
                 "DG_PREV": (n1, np.float64), "B": (n2, np.float64), "RHO": (n0, np.float64),
                 "PHI": (n0, np.float64), "X": ((npart, 3), np.float64),
-                "V": ((npart, 3), np.float64), "TET": (npart, np.int32),
+                "V": ((npart, 3), np.float64), "TET": (npart, np.int32), "SPECIES": (npart, np.int32),
                 "NCROSS": (npart, np.int32), "HASH": (npart, np.uint64)}[what]
 
     def step(self, dt, n=1):
