@@ -21,7 +21,7 @@ rule (see fields).
 import numpy as np
 import scipy.sparse.linalg as spla
 
-from . import assemble, fields, particles
+from . import ab4, assemble, fields, particles
 from .geometry import barycentric_maps
 from .topology import Topology
 
@@ -29,7 +29,7 @@ from .topology import Topology
 class Sim:
     def __init__(self, xyz, tets, order, q, m, weight, B0=(0.0, 0.0, 0.0),
                  rho_ion=0.0, scheme="trapezoid", gamma=0.5, beta=0.25, matrices=True,
-                 max_cross=4096, bface_tag=None):
+                 max_cross=4096, bface_tag=None, push="boris"):
         self.topo = t = Topology(xyz, tets, order, bface_tag)
         self.g, self.c, self.vol = barycentric_maps(t.xyz, t.tets)
         self.order = order
@@ -40,6 +40,10 @@ class Sim:
         self.scheme = scheme
         self.gamma, self.beta = float(gamma), float(beta)
         self.max_cross = max_cross
+        if push not in ("boris", "ab4"):
+            raise ValueError("push must be 'boris' or 'ab4'")
+        self.push = push
+        self.hcount = 0
         self.e = np.zeros(t.n1)
         self.e_prev = np.zeros(t.n1)
         self.b = np.zeros(t.n2)
@@ -64,6 +68,13 @@ class Sim:
         self.offsets = [0, len(self.x)]
         self.species = [(self.q, self.m, self.weight)]
         self.rho = self._measure_rho(self.x, self.tet)
+        self._reset_history()
+
+    def _reset_history(self):
+        """Adams-Bashforth history (v^{n-j}, a^{n-j}, j = 1..3), empty."""
+        self.vh = np.zeros((3, len(self.x), 3))
+        self.ah = np.zeros((3, len(self.x), 3))
+        self.hcount = 0
 
     def set_species(self, species):
         """species: list of dicts with q, m, weight, x, v, tet."""
@@ -73,6 +84,7 @@ class Sim:
         self.tet = np.concatenate([np.asarray(s["tet"], dtype=np.int64) for s in species])
         self.offsets = list(np.cumsum([0] + [len(np.asarray(s["tet"])) for s in species]))
         self.rho = self._measure_rho(self.x, self.tet)
+        self._reset_history()
 
     def _slices(self):
         for k, (q, m, w) in enumerate(self.species):
@@ -103,6 +115,8 @@ class Sim:
         t = self.topo
         parts = []
         dg = np.zeros(t.n1)
+        if self.push == "ab4":
+            return self._push_walk_ab4(dt)
         for sl, q, m, w in self._slices():
             E, B = particles.gather(t, self.g, self.c, self.e, self.b, self.B0, self.x[sl], self.tet[sl])
             vn = particles.boris(self.v[sl], E, B, q, m, dt)
@@ -114,6 +128,24 @@ class Sim:
                               status=st))
         out = {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
         out["dg"] = dg
+        return out
+
+    def _push_walk_ab4(self, dt):
+        """Adams-Bashforth step of every species on the quartic path."""
+        t = self.topo
+        parts = []
+        dg = np.zeros(t.n1)
+        for sl, q, m, w in self._slices():
+            E, B = particles.gather(t, self.g, self.c, self.e, self.b, self.B0, self.x[sl], self.tet[sl])
+            r = ab4.step(t, self.g, self.c, self.x[sl], self.v[sl], self.tet[sl], self.vh[:, sl],
+                         self.ah[:, sl], self.hcount, E, B, q, m, q * w, dt, t.n1, self.max_cross)
+            dg += r["dg"]
+            parts.append(r)
+        out = {k: np.concatenate([p[k] for p in parts]) for k in ("x", "v", "tet", "ncross", "hash", "status")}
+        out["vh"] = np.concatenate([p["vh"] for p in parts], axis=1)
+        out["ah"] = np.concatenate([p["ah"] for p in parts], axis=1)
+        out["dg"] = dg
+        out["order"] = parts[0]["order"] if parts else min(4, self.hcount + 1)
         return out
 
     def step(self, dt):
@@ -134,6 +166,9 @@ class Sim:
         self.e_prev, self.e, self.b = self.e, e_new, b_new
         self.dg_prev = w["dg"]
         self.x, self.v, self.tet, self.rho = w["x"], w["v"], w["tet"], rho_new
+        if self.push == "ab4":
+            self.vh, self.ah = w["vh"], w["ah"]
+            self.hcount = min(3, self.hcount + 1)
         w["gauss"] = self.gauss_residual()
         return w
 
