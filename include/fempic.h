@@ -80,6 +80,23 @@ enum {
   FEMPIC_SCHEME_WAVE = 1       /* second-order e form with free gamma, beta    */
 };
 
+/* ---- particle push (set at create) --------------------------------------- */
+enum {
+  FEMPIC_PUSH_BORIS = 0, /* Boris rotation, straight chord x^{n+1} = x^n + dt v^{n+1/2};
+                            FEMPIC_V holds v^{n-1/2}                           */
+  FEMPIC_PUSH_AB4 = 1    /* the paper's Adams-Bashforth push (Section III-B): v^{n+1}
+                            = v^n + dt sum_j beta_j a^{n-j}, path x(s) = x^n + dt
+                            int_0^s V, V the Lagrange polynomial through the last
+                            velocities (quartic in s); orders 1..3 while the history
+                            fills; the walk samples the path at 8 steps per tet and
+                            bisects the crossings; walls mirror the path and the
+                            history; current by the (2p+2)-point Gauss-Legendre
+                            rule.  FEMPIC_V holds v^n.  One kernel with every
+                            operation rounded separately, whatever the precision
+                            mode; particles are not re-sorted; setting X, V or TET
+                            restarts the history.                                */
+};
+
 /* ---- quantities for femPIC_get / femPIC_set ----------------------------- */
 enum {
   FEMPIC_E = 0,        /* double[N1]  electric field DOFs e^n                   */
@@ -154,6 +171,7 @@ typedef struct {
   int32_t diagnostics;  /* 1: compute continuity/Gauss residuals every step    */
   int32_t device;       /* CUDA device ordinal                                  */
   void* stream;         /* cudaStream_t to run on; NULL = library-owned stream */
+  int32_t push;         /* FEMPIC_PUSH_* (default FEMPIC_PUSH_BORIS)           */
 } femPIC_opts;
 
 /* Per-step diagnostics (Section IV-D): continuity and Gauss residuals. */

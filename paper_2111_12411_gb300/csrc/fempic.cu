@@ -23,6 +23,7 @@
 #include "linalg.cuh"
 #include "particle_fast.cuh"
 #include "batch.cuh"
+#include "particle_ab4.cuh"
 
 using namespace fempic;
 using namespace fempic::dev;
@@ -100,6 +101,11 @@ struct FemPIC {
   int32_t n_imp_faces = 0;
   double *Iv = nullptr, *bI = nullptr;
   // species: ids [sp_off[k], sp_off[k+1]) belong to species k
+  // Adams-Bashforth push: history v^{n-1-j}, a^{n-1-j} per particle (device
+  // order; the particles are not re-sorted), entries filled so far
+  double* ab_vh[3][3] = {};
+  double* ab_ah[3][3] = {};
+  int ab_count = 0;
   int n_species = 1;
   int64_t sp_off[kMaxSpecies + 1] = {};
   double sp_q[kMaxSpecies] = {}, sp_m[kMaxSpecies] = {}, sp_w[kMaxSpecies] = {};
@@ -539,6 +545,39 @@ int launch_particles(FemPIC* h, double dt) {
   a.pid = h->pid;
   a.sp = species_table(h, dt);
   if (h->np == 0) return FEMPIC_OK;
+  if (h->opts.push == FEMPIC_PUSH_AB4) {
+    Ab4Args A;
+    A.p = a;
+    for (int j = 0; j < 3; ++j)
+      for (int c = 0; c < 3; ++c) {
+        A.vh[j][c] = h->ab_vh[j][c];
+        A.ah[j][c] = h->ab_ah[j][c];
+      }
+    A.k = std::min(4, h->ab_count + 1);
+    A.qm = h->q / h->m;
+    for (int k = 0; k < kMaxSpecies; ++k) A.qm_s[k] = k < h->n_species ? h->sp_q[k] / h->sp_m[k] : 0.0;
+    const int g128 = grid_for(h->np, 128, 1 << 30);
+    auto launch = [&](auto kern) { kern<<<g128, 128, 0, h->stream>>>(A); };
+    if (h->order == 1) {
+      switch (A.k) {
+        case 1: launch(k_particle_ab4<1, 1>); break;
+        case 2: launch(k_particle_ab4<1, 2>); break;
+        case 3: launch(k_particle_ab4<1, 3>); break;
+        default: launch(k_particle_ab4<1, 4>); break;
+      }
+    } else {
+      switch (A.k) {
+        case 1: launch(k_particle_ab4<2, 1>); break;
+        case 2: launch(k_particle_ab4<2, 2>); break;
+        case 3: launch(k_particle_ab4<2, 3>); break;
+        default: launch(k_particle_ab4<2, 4>); break;
+      }
+    }
+    h->launches++;
+    CK(cudaGetLastError());
+    h->ab_count = std::min(3, h->ab_count + 1);
+    return FEMPIC_OK;
+  }
   int grid = grid_for(h->np, 256, 1 << 30);
   bool strict = h->opts.precision == FEMPIC_FP64_STRICT;
   // lanes share tets only right after a sort
@@ -654,7 +693,7 @@ int do_steps(FemPIC* h, double dt, int32_t n) {
       }
     }
     CK(cudaEventRecord(e[0], h->stream));
-    if (h->opts.sort_period > 0 && h->since_sort >= h->opts.sort_period) {
+    if (h->opts.sort_period > 0 && h->since_sort >= h->opts.sort_period && h->opts.push != FEMPIC_PUSH_AB4) {
       int rc = sort_particles(h);
       if (rc) return rc;
       h->since_sort = 0;
@@ -829,6 +868,7 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
   if (h->np == 0) return FEMPIC_OK;
   int grid = grid_for(h->np, 256, 1 << 30);
   double* stage = h->stage;
+  if (to_handle && (what == FEMPIC_X || what == FEMPIC_V || what == FEMPIC_TET)) h->ab_count = 0;
   if (what == FEMPIC_X || what == FEMPIC_V) {
     double** dst = what == FEMPIC_X ? h->px : h->pv;
     if (to_handle) {
@@ -879,7 +919,7 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
     return FEMPIC_ERR_ARG;
   }
   if (o.precision < 0 || o.precision > 2 || o.scheme < 0 || o.scheme > 1 || !(o.cg_rtol > 0) ||
-      o.cg_max_it < 1 || o.max_cross < 1 || o.sort_period < 0) {
+      o.cg_max_it < 1 || o.max_cross < 1 || o.sort_period < 0 || o.push < 0 || o.push > 1) {
     h->err = "invalid option";
     return FEMPIC_ERR_ARG;
   }
@@ -1110,6 +1150,17 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
       (rc = dalloc(h, &h->sort_sums, (h->n_tets + 1023) / 1024 + 1)) ||
       (rc = dalloc(h, &h->sort_sums2, (h->n_tets + 1023) / 1024 / 1024 + 2)))
     return rc;
+  if (o.push == FEMPIC_PUSH_AB4) {
+    for (int j = 0; j < 3; ++j)
+      for (int c = 0; c < 3; ++c) {
+        if ((rc = dalloc(h, &h->ab_vh[j][c], n)) || (rc = dalloc(h, &h->ab_ah[j][c], n))) return rc;
+        if (n > 0) {
+          CK(cudaMemset(h->ab_vh[j][c], 0, n * sizeof(double)));
+          CK(cudaMemset(h->ab_ah[j][c], 0, n * sizeof(double)));
+        }
+      }
+    h->ab_count = 0;
+  }
   if (n > 0) {
     std::vector<double> tmp((size_t)n);
     for (int k = 0; k < 3; ++k) {
@@ -1763,8 +1814,8 @@ int femPIC_batch_create(FemPIC* const* members, int32_t n, FemPICBatch** out) {
       b->err = "batched members must use FEMPIC_FP64 or FEMPIC_MIXED and the trapezoid scheme";
       return FEMPIC_ERR_ARG;
     }
-    if (h->n_species != 1) {
-      b->err = "batched members must have a single species";
+    if (h->n_species != 1 || h->opts.push != FEMPIC_PUSH_BORIS) {
+      b->err = "batched members must have a single species and the Boris push";
       return FEMPIC_ERR_ARG;
     }
     if (h->n_tets > 1024 * 1024) {

@@ -1,0 +1,350 @@
+// Adams-Bashforth push on the polynomial path (Section III-B, last paragraph:
+// a fourth-order Adams-Bashforth push makes the particle path a fourth-order
+// Lagrange polynomial, and the current integrates the edge basis along it).
+//
+// Per particle: x^n, v^n (integer times), the history v^{n-j}, a^{n-j}
+// (j = 1..3), a = (q/m)(E + v x B) gathered at x^n.  With k the Adams-Bashforth
+// order of the step (1..4 while the history fills):
+//   v^{n+1} = v^n + dt sum_j beta_j a^{n-j},
+//   x(s) = sum_m C_m s^m, C_0 = x^n, C_m = dt sum_j gam_jm v^{n-j}, s in [0, 1]
+// (the integral of the Lagrange polynomial through the last k velocities,
+// so x(1) is the Adams-Bashforth position update).  In each tet lambda(x(s))
+// is a polynomial in s: [s0, 1] is sampled at 8 equal steps, the faces that
+// turn negative in the first such step are bisected 60 times, the smallest
+// crossing wins (ties to the lowest face).  Walls mirror the rest of the path
+// and the velocity history.  The current of each sub-path is
+// q w int W1_i(x(s)) . x'(s) ds by the (2p + 2)-point Gauss-Legendre rule,
+// exact for the degree pk + k - 1 integrand.  Every operation is rounded
+// separately in a fixed order (Strict), so positions and walk decisions are
+// reproducible.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace fempic {
+namespace dev {
+
+constexpr int kAbSamples = 8;
+constexpr int kAbBisect = 60;
+
+// beta_j of order k (exact fractions, rounded once)
+__host__ __device__ constexpr double ab_beta(int k, int j) {
+  return k == 1   ? 1.0
+         : k == 2 ? (j == 0 ? 3.0 / 2.0 : -1.0 / 2.0)
+         : k == 3 ? (j == 0 ? 23.0 / 12.0 : (j == 1 ? -4.0 / 3.0 : 5.0 / 12.0))
+                  : (j == 0 ? 55.0 / 24.0 : (j == 1 ? -59.0 / 24.0 : (j == 2 ? 37.0 / 24.0 : -3.0 / 8.0)));
+}
+
+// gam_jm of order k: int_0^s l_j = sum_m gam_jm s^m, l_j the Lagrange basis
+// on the nodes 0, -1, ..., -(k-1)
+__host__ __device__ constexpr double ab_gam(int k, int j, int m) {
+  if (m == 0 || m > k || j >= k) return 0.0;
+  if (k == 1) return m == 1 ? 1.0 : 0.0;
+  if (k == 2) {
+    constexpr double t[2][3] = {{0.0, 1.0, 1.0 / 2.0}, {0.0, 0.0, -1.0 / 2.0}};
+    return t[j][m];
+  }
+  if (k == 3) {
+    constexpr double t[3][4] = {{0.0, 1.0, 3.0 / 4.0, 1.0 / 6.0},
+                                {0.0, 0.0, -1.0, -1.0 / 3.0},
+                                {0.0, 0.0, 1.0 / 4.0, 1.0 / 6.0}};
+    return t[j][m];
+  }
+  constexpr double t[4][5] = {{0.0, 1.0, 11.0 / 12.0, 1.0 / 3.0, 1.0 / 24.0},
+                              {0.0, 0.0, -3.0 / 2.0, -5.0 / 6.0, -1.0 / 8.0},
+                              {0.0, 0.0, 3.0 / 4.0, 2.0 / 3.0, 1.0 / 8.0},
+                              {0.0, 0.0, -1.0 / 6.0, -1.0 / 6.0, -1.0 / 24.0}};
+  return t[j][m];
+}
+
+// Gauss-Legendre on [0, 1]: 4 points (order 1) and 6 points (order 2), from
+// the standard abscissae and weights on [-1, 1]
+template <int P>
+__device__ __forceinline__ void gl_rule(int q, double& x, double& w) {
+  if (P == 1) {
+    constexpr double xs[4] = {-0.86113631159405257522, -0.33998104358485626480, 0.33998104358485626480,
+                              0.86113631159405257522};
+    constexpr double ws[4] = {0.34785484513745385737, 0.65214515486254614263, 0.65214515486254614263,
+                              0.34785484513745385737};
+    x = 0.5 * (xs[q] + 1.0);
+    w = 0.5 * ws[q];
+  } else {
+    constexpr double xs[6] = {-0.93246951420315202781, -0.66120938646626451366, -0.23861918608319690863,
+                              0.23861918608319690863, 0.66120938646626451366, 0.93246951420315202781};
+    constexpr double ws[6] = {0.17132449237917034504, 0.36076157304813860757, 0.46791393457269104739,
+                              0.46791393457269104739, 0.36076157304813860757, 0.17132449237917034504};
+    x = 0.5 * (xs[q] + 1.0);
+    w = 0.5 * ws[q];
+  }
+}
+
+struct Ab4Args {
+  ParticleArgs p;
+  double* vh[3][3];  // [j][component]: v^{n-1-j}
+  double* ah[3][3];  // a^{n-1-j}
+  int k;             // Adams-Bashforth order of this step (1..4)
+  double qm;         // q / m (one species)
+  double qm_s[kMaxSpecies];
+};
+
+// Horner over the K+1 ascending coefficients c[m][i], and its derivative
+template <int K>
+__device__ __forceinline__ double ab_horner(const double (&c)[5][4], int i, double s) {
+  double p = c[K][i];
+#pragma unroll
+  for (int m = K - 1; m >= 0; --m) p = __dadd_rn(__dmul_rn(p, s), c[m][i]);
+  return p;
+}
+template <int K>
+__device__ __forceinline__ double ab_horner_d(const double (&c)[5][4], int i, double s) {
+  double p = __dmul_rn((double)K, c[K][i]);
+#pragma unroll
+  for (int m = K - 1; m >= 1; --m) p = __dadd_rn(__dmul_rn(p, s), __dmul_rn((double)m, c[m][i]));
+  return p;
+}
+
+__device__ __forceinline__ void ab_mirror(double* vec, const double* gw, double gg) {
+  const double f = __ddiv_rn(__dmul_rn(2.0, dot3<Strict>(vec, gw)), gg);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) vec[c] = __dsub_rn(vec[c], __dmul_rn(f, gw[c]));
+}
+
+// K: the Adams-Bashforth order of the step (a template parameter, so the path
+// and lambda coefficients stay in registers)
+template <int P, int K>
+__global__ void __launch_bounds__(128) k_particle_ab4(Ab4Args A) {
+  constexpr int N1 = P == 1 ? 6 : 20;
+  constexpr int N2 = P == 1 ? 4 : 15;
+  constexpr int N0 = P == 1 ? 4 : 10;
+  constexpr int NQ = 2 * P + 2;
+  const ParticleArgs& a = A.p;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long my_cross = 0;
+  if (i < a.n) {
+    double qw = a.qw, qm = A.qm;
+    if (a.sp.n > 1) {
+      const int s = species_of(a.sp, __ldg(a.pid + i));
+      qw = a.sp.qw[s];
+      qm = A.qm_s[s];
+    }
+    int T = a.tet[i];
+    double x[3], v[3], vh[3][3], ah[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      x[c] = a.x[c][i];
+      v[c] = a.v[c][i];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        vh[j][c] = A.vh[j][c][i];
+        ah[j][c] = A.ah[j][c][i];
+      }
+    }
+    TetGeom G;
+    load_geom(a.geom, T, G);
+    double l[4];
+    bary<Strict>(G, x, l);
+    double ev[N1], bv[N2];
+    const int32_t* d1 = a.dof1 + (size_t)T * N1;
+    const int32_t* d2 = a.dof2 + (size_t)T * N2;
+#pragma unroll
+    for (int j = 0; j < N1; ++j) ev[j] = __ldg(a.e + __ldg(d1 + j));
+#pragma unroll
+    for (int j = 0; j < N2; ++j) bv[j] = __ldg(a.b + __ldg(d2 + j));
+    double E[3], B[3], vxb[3], an[3];
+    gather_E<P, Strict>(G, l, ev, E);
+    gather_B<P, Strict>(G, l, bv, a.B0, B);
+    cross3<Strict>(v, B, vxb);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) an[c] = __dmul_rn(qm, __dadd_rn(E[c], vxb[c]));
+    // velocity update and path coefficients
+    double vnew[3], C[5][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double acc = __dmul_rn(ab_beta(K, 0), an[c]);
+#pragma unroll
+      for (int j = 1; j < K; ++j) acc = __dadd_rn(acc, __dmul_rn(ab_beta(K, j), ah[j - 1][c]));
+      vnew[c] = __dadd_rn(v[c], __dmul_rn(a.dt, acc));
+      C[0][c] = x[c];
+#pragma unroll
+      for (int m = 1; m <= K; ++m) {
+        double s = __dmul_rn(ab_gam(K, 0, m), v[c]);
+#pragma unroll
+        for (int j = 1; j < K; ++j) s = __dadd_rn(s, __dmul_rn(ab_gam(K, j, m), vh[j - 1][c]));
+        C[m][c] = __dmul_rn(a.dt, s);
+      }
+    }
+    int entry = -1;
+    double s0 = 0.0;
+    int nc = 0;
+    unsigned long long hsh = kFnvOffset;
+    for (;;) {
+      // lambda coefficients in this tet
+      double L[5][4];
+#pragma unroll
+      for (int m = 0; m <= K; ++m)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const double t = __dadd_rn(__dadd_rn(__dmul_rn(G.g[f][0], C[m][0]), __dmul_rn(G.g[f][1], C[m][1])),
+                                     __dmul_rn(G.g[f][2], C[m][2]));
+          L[m][f] = m == 0 ? __dadd_rn(t, G.c[f]) : t;
+        }
+      const double span = __dsub_rn(1.0, s0);
+      int best = -1;
+      double s1 = 1.0;
+      for (int j = 1; j <= kAbSamples && best < 0; ++j) {
+        const double lo_s = __dadd_rn(s0, __dmul_rn(span, (double)(j - 1) / kAbSamples));
+        const double hi_s = __dadd_rn(s0, __dmul_rn(span, (double)j / kAbSamples));
+        double sbest = __longlong_as_double(0x7ff0000000000000ll);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          if (!(ab_horner<K>(L, f, hi_s) < 0.0)) continue;
+          double lo = lo_s, hi = hi_s;
+          for (int it = 0; it < kAbBisect; ++it) {
+            const double mid = __dmul_rn(__dadd_rn(lo, hi), 0.5);
+            if (ab_horner<K>(L, f, mid) < 0.0)
+              hi = mid;
+            else
+              lo = mid;
+          }
+          if (hi < sbest) {
+            sbest = hi;
+            best = f;
+          }
+        }
+        if (best >= 0) s1 = sbest;
+      }
+      // current of the sub-path [s0, s1]
+      {
+        const double ln = __dsub_rn(s1, s0);
+        double acc[N1];
+#pragma unroll
+        for (int j = 0; j < N1; ++j) acc[j] = 0.0;
+#pragma unroll 1
+        for (int q = 0; q < NQ; ++q) {
+          double xq, wq;
+          gl_rule<P>(q, xq, wq);
+          const double sq = __dadd_rn(s0, __dmul_rn(ln, xq));
+          double lv[4], dl[4];
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            lv[f] = ab_horner<K>(L, f, sq);
+            dl[f] = ab_horner_d<K>(L, f, sq);
+          }
+#pragma unroll
+          for (int j = 0; j < N1; ++j) {
+            int aa, bb, xx, kind;
+            if (P == 1) {
+              aa = edge_s(j);
+              bb = edge_t(j);
+              xx = 0;
+              kind = 0;
+            } else {
+              aa = w1q(j, 0);
+              bb = w1q(j, 1);
+              xx = w1q(j, 2);
+              kind = w1q(j, 3);
+            }
+            double wv = __dsub_rn(__dmul_rn(lv[aa], dl[bb]), __dmul_rn(lv[bb], dl[aa]));
+            if (kind == 1)
+              wv = __dmul_rn(__dsub_rn(__dmul_rn(3.0, lv[xx]), 1.0), wv);
+            else if (kind == 2)
+              wv = __dmul_rn(__dmul_rn(3.0, lv[xx]), wv);
+            acc[j] = __dadd_rn(acc[j], __dmul_rn(wq, wv));
+          }
+        }
+        const int32_t* dofs = a.dof1 + (size_t)T * N1;
+#pragma unroll
+        for (int j = 0; j < N1; ++j) atomicAdd(a.dg + __ldg(dofs + j), __dmul_rn(qw, __dmul_rn(ln, acc[j])));
+      }
+      if (best < 0) break;
+      ++nc;
+      const int nb = __ldg(a.nbr + (size_t)T * 4 + best);
+      const unsigned long long code = nb < 0 ? (0x80000000ull | (unsigned)best) : (unsigned long long)(nb >> 2);
+      hsh = (hsh ^ code) * kFnvPrime;
+      if (nb >= 0) {
+        entry = nb & 3;
+        T = nb >> 2;
+        s0 = s1;
+        load_geom(a.geom, T, G);
+      } else {
+        double gw[3];
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+          if (f == best) {
+            gw[0] = G.g[f][0];
+            gw[1] = G.g[f][1];
+            gw[2] = G.g[f][2];
+          }
+        const double gg = dot3<Strict>(gw, gw);
+        double hit[3], d0[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          double p = C[K][c];
+#pragma unroll
+          for (int m = K - 1; m >= 0; --m) p = __dadd_rn(__dmul_rn(p, s1), C[m][c]);
+          hit[c] = p;
+          d0[c] = __dsub_rn(C[0][c], p);
+        }
+        ab_mirror(d0, gw, gg);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) C[0][c] = __dadd_rn(hit[c], d0[c]);
+#pragma unroll
+        for (int m = 1; m <= K; ++m) {
+          double cm[3] = {C[m][0], C[m][1], C[m][2]};
+          ab_mirror(cm, gw, gg);
+          C[m][0] = cm[0];
+          C[m][1] = cm[1];
+          C[m][2] = cm[2];
+        }
+        ab_mirror(vnew, gw, gg);
+        ab_mirror(v, gw, gg);
+        ab_mirror(an, gw, gg);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          ab_mirror(vh[j], gw, gg);
+          ab_mirror(ah[j], gw, gg);
+        }
+        s0 = s1;
+        entry = best;
+      }
+      (void)entry;
+      if (nc >= a.max_cross) {
+        atomicOr(a.status, kStatusWalk);
+        break;
+      }
+    }
+    // end point x(1), charge there, state and history
+    double xe[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double p = C[K][c];
+#pragma unroll
+      for (int m = K - 1; m >= 0; --m) p = __dadd_rn(__dmul_rn(p, 1.0), C[m][c]);
+      xe[c] = p;
+    }
+    double le[4];
+    bary<Strict>(G, xe, le);
+    deposit_rho<P, Strict>(le, qw, a.dof0 + (size_t)T * N0, a.rho);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      a.x[c][i] = xe[c];
+      a.v[c][i] = vnew[c];
+      A.vh[2][c][i] = vh[1][c];
+      A.vh[1][c][i] = vh[0][c];
+      A.vh[0][c][i] = v[c];
+      A.ah[2][c][i] = ah[1][c];
+      A.ah[1][c][i] = ah[0][c];
+      A.ah[0][c][i] = an[c];
+    }
+    a.tet[i] = T;
+    if (a.ncross) a.ncross[i] = nc;
+    if (a.hash) a.hash[i] = hsh;
+    my_cross = nc;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_cross += __shfl_xor_sync(0xffffffffu, my_cross, o);
+  if ((threadIdx.x & 31) == 0 && my_cross) atomicAdd(a.crossings, my_cross);
+}
+
+}  // namespace dev
+}  // namespace fempic

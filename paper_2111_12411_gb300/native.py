@@ -20,6 +20,7 @@ ERROR_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_MESH", 3: "ERR_OOM", 4: "ERR_CUDA"
                6: "ERR_WALK", 7: "ERR_SIZE", 8: "ERR_STATE", 9: "ERR_BARRIER"}
 PRECISION = {"fp64_strict": 0, "fp64": 1, "mixed": 2}
 SCHEME = {"trapezoid": 0, "wave": 1}
+PUSH = {"boris": 0, "ab4": 1}
 QUANTITY = {"E": 0, "B": 1, "DG": 2, "RHO": 3, "X": 4, "V": 5, "TET": 6, "NCROSS": 7, "HASH": 8,
             "E_PREV": 9, "DG_PREV": 10, "DIAG": 11, "PHI": 12, "SPECIES": 13}
 MAX_SPECIES = 8
@@ -44,7 +45,7 @@ class femPIC_opts(ctypes.Structure):
                 ("sort_period", ctypes.c_int32), ("B0", ctypes.c_double * 3),
                 ("rho_ion", ctypes.c_double), ("es_init", ctypes.c_int32),
                 ("diagnostics", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("push", ctypes.c_int32)]
 
 
 class femPIC_diag(ctypes.Structure):
@@ -285,7 +286,7 @@ class Simulation:
     def __init__(self, xyz, tets, order, q, m, weight, x, v, tet, precision="fp64",
                  scheme="trapezoid", gamma=0.5, beta=0.25, cg_rtol=1e-12, cg_max_it=2000,
                  max_cross=4096, sort_period=1, B0=(0.0, 0.0, 0.0), rho_ion=0.0, es_init=True,
-                 diagnostics=False, device=0, stream=None, species=None, bface_tag=None):
+                 diagnostics=False, device=0, stream=None, species=None, bface_tag=None, push="boris"):
         o = default_opts()
         o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
         o.scheme = SCHEME[scheme] if isinstance(scheme, str) else int(scheme)
@@ -296,6 +297,7 @@ class Simulation:
         o.rho_ion = rho_ion
         o.es_init, o.diagnostics, o.device = int(es_init), int(diagnostics), device
         o.stream = stream
+        o.push = PUSH[push] if isinstance(push, str) else int(push)
         if species is None and bface_tag is None:
             self.h = femPIC_create(xyz, tets, order, q, m, weight, x, v, tet, o)
         else:

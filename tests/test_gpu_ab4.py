@@ -1,0 +1,101 @@
+"""GPU parity of the Adams-Bashforth push on the quartic path (FEMPIC_PUSH_AB4)
+against the oracle, through the C ABI.
+
+Every step starts both sides from the same fields (the oracle's e, b are set
+on the device), so the particle half of each step is compared on its own
+across the AB1 -> AB4 start-up: positions, velocities, owning tets and
+crossing-sequence hashes bit-exact (one rounding per operation on both
+sides), the current rel 1e-12 (atomics reorder the sums; the Gauss-Legendre
+abscissae are written independently on each side), charge conserved on the
+device to 1e-12.
+"""
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import sim as osim
+from gpu_helpers import build_lib, rel
+from test_oracle_boundary_species import M_E, M_SR, Q_E
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    return build_lib()
+
+
+def _setup(order, seed, species=False, n=1500):
+    from paper_2111_12411_gb300 import Simulation
+    xyz, tets = workloads.kuhn_box(4, 4, 4, jitter=0.1, seed=seed)
+    rng = np.random.default_rng(seed)
+    x, tet = workloads.sample_uniform_in_tets(xyz, tets, n, rng)
+    # 0.05 m per step, gyroradius ~0.3 m (curved paths); omega_c dt = 0.18, inside the
+    # Adams-Bashforth 4 stability interval on the imaginary axis (|omega dt| < ~0.43)
+    v = workloads.maxwellian(n, 5e7, rng)
+    sp = [dict(q=-Q_E, m=M_E, weight=1e4, x=x, v=v, tet=tet)]
+    if species:
+        xi, ti = workloads.sample_uniform_in_tets(xyz, tets, n // 3, rng)
+        sp.append(dict(q=Q_E, m=M_SR, weight=1e4, x=xi, v=workloads.maxwellian(n // 3, 1e6, rng), tet=ti))
+    o = osim.Sim(xyz, tets, order, -Q_E, M_E, 1e4, B0=(0.0, 0.0, 1e-3), push="ab4")
+    o.set_species(sp)
+    g = Simulation(xyz, tets, order, -Q_E, M_E, 1e4, x, v, tet, B0=(0.0, 0.0, 1e-3), es_init=False,
+                   diagnostics=True, push="ab4", species=sp if species else None)
+    t = o.topo
+    o.e = workloads.random_dof_vector(t.n1, 3e3, rng, t.pec1)
+    o.e_prev = o.e.copy()
+    return o, g
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("species", [False, True])
+def test_ab4_steps_match_oracle(order, species):
+    o, g = _setup(order, 30 + order, species)
+    dt = 1e-9
+    for k in range(5):
+        g.set("E", o.e)
+        g.set("E_PREV", o.e_prev)
+        g.set("B", o.b)
+        w = o.step(dt)
+        g.step(dt)
+        assert w["order"] == min(4, k + 1)
+        assert np.array_equal(g.get("X"), w["x"])
+        assert np.array_equal(g.get("V"), w["v"])
+        assert np.array_equal(g.get("TET"), w["tet"])
+        assert np.array_equal(g.get("NCROSS"), w["ncross"])
+        assert np.array_equal(g.get("HASH"), w["hash"])
+        assert rel(g.get("DG"), w["dg"]) < 1e-12
+        assert rel(g.get("RHO"), o.rho) < 1e-12
+        d = g.diag()
+        assert d["continuity_abs"] <= 1e-12 * d["continuity_ref"]
+    assert w["ncross"].sum() > 1000 and w["ncross"].max() < 50
+    g.close()
+
+
+def test_ab4_restarts_history_on_set():
+    """Setting the particle state restarts the Adams-Bashforth order at 1, as
+    a fresh oracle from the same state does."""
+    o, g = _setup(1, 40, n=600)
+    dt = 1e-9
+    for _ in range(3):
+        g.set("E", o.e)
+        g.set("E_PREV", o.e_prev)
+        g.set("B", o.b)
+        o.step(dt)
+        g.step(dt)
+    x, v, tet = g.get("X"), g.get("V"), g.get("TET")
+    g.set("X", x)
+    g.set("V", v)
+    g.set("TET", tet)
+    fresh = osim.Sim(o.topo.xyz, o.topo.tets, 1, -Q_E, M_E, 1e4, B0=(0.0, 0.0, 1e-3), push="ab4")
+    fresh.set_particles(x, v, tet)
+    fresh.e, fresh.e_prev, fresh.b = o.e.copy(), o.e_prev.copy(), o.b.copy()
+    g.set("E", fresh.e)
+    g.set("E_PREV", fresh.e_prev)
+    g.set("B", fresh.b)
+    w = fresh.step(dt)
+    g.step(dt)
+    assert w["order"] == 1
+    assert np.array_equal(g.get("X"), w["x"]) and np.array_equal(g.get("TET"), w["tet"])
+    g.close()
