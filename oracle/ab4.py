@@ -18,9 +18,12 @@ Readings (the paper gives no further detail):
 * Walk: in each tet, lambda_i(x(s)) is a polynomial in s (lambda affine).
   From the entry parameter s0 the interval [s0, 1] is sampled at 8 equal
   steps; in the first step where some lambda_i turns negative, each such face
-  is bisected (60 halvings, keeping the negative end); the exit face is the
-  one with the smallest crossing (ties to the lowest index) and the particle
-  continues in the neighbour from that parameter.  The entry face counts as 0
+  gets 8 safeguarded Newton steps inside that bracket (start at its middle;
+  the sign of lambda shrinks the bracket; a Newton step that leaves the
+  closed bracket is replaced by its middle); the last iterate is the
+  crossing.  The
+  exit face is the one with the smallest crossing (ties to the lowest index)
+  and the particle continues in the neighbour from that parameter.  The entry face counts as 0
   at the entry parameter.  (A grazing excursion shorter than one sample step
   is not split off; charge stays conserved, since the sub-path's ends are in
   the tet and W0 is continuous there.)
@@ -44,7 +47,7 @@ from . import basis, geometry
 from .particles import FNV_OFFSET, FNV_PRIME
 
 N_SAMPLES = 8
-N_BISECT = 60
+N_REFINE = 8
 
 
 def _lagrange_integrals(k):
@@ -211,13 +214,19 @@ def step(topo, g_all, c_all, x, v, tet, vh, ah, hcount, E, B, q, m, qw, dt, n1, 
                 lo = lo_s.copy()
                 hi = hi_s.copy()
                 Ai = A[:, :, i:i + 1]
-                for _ in range(N_BISECT):
-                    mid = (lo + hi) * 0.5
-                    neg = _horner(Ai, mid)[:, 0] < 0.0
-                    hi = np.where(neg, mid, hi)
-                    lo = np.where(neg, lo, mid)
-                upd = cand & (hi < sbest)
-                sbest[upd] = hi[upd]
+                sx = (lo + hi) * 0.5
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    for _ in range(N_REFINE):
+                        f = _horner(Ai, sx)[:, 0]
+                        neg = f < 0.0
+                        hi = np.where(neg, sx, hi)
+                        lo = np.where(neg, lo, sx)
+                        d = _horner_deriv(Ai, sx)[:, 0]
+                        sn = sx - f / d
+                        ok = (sn >= lo) & (sn <= hi)
+                        sx = np.where(ok, sn, (lo + hi) * 0.5)
+                upd = cand & (sx < sbest)
+                sbest[upd] = sx[upd]
                 best[upd] = i
             hit = look & (best >= 0)
             s1[hit] = sbest[hit]

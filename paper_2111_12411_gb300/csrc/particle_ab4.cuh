@@ -10,8 +10,8 @@
 // (the integral of the Lagrange polynomial through the last k velocities,
 // so x(1) is the Adams-Bashforth position update).  In each tet lambda(x(s))
 // is a polynomial in s: [s0, 1] is sampled at 8 equal steps, the faces that
-// turn negative in the first such step are bisected 60 times, the smallest
-// crossing wins (ties to the lowest face).  Walls mirror the rest of the path
+// turn negative in the first such step get 8 safeguarded Newton steps in that
+// bracket, the smallest crossing wins (ties to the lowest face).  Walls mirror the rest of the path
 // and the velocity history.  The current of each sub-path is
 // q w int W1_i(x(s)) . x'(s) ds by the (2p + 2)-point Gauss-Legendre rule,
 // exact for the degree pk + k - 1 integrand.  Every operation is rounded
@@ -25,7 +25,7 @@ namespace fempic {
 namespace dev {
 
 constexpr int kAbSamples = 8;
-constexpr int kAbBisect = 60;
+constexpr int kAbRefine = 8;
 
 // beta_j of order k (exact fractions, rounded once)
 __host__ __device__ constexpr double ab_beta(int k, int j) {
@@ -199,15 +199,19 @@ __global__ void __launch_bounds__(128) k_particle_ab4(Ab4Args A) {
         for (int f = 0; f < 4; ++f) {
           if (!(ab_horner<K>(L, f, hi_s) < 0.0)) continue;
           double lo = lo_s, hi = hi_s;
-          for (int it = 0; it < kAbBisect; ++it) {
-            const double mid = __dmul_rn(__dadd_rn(lo, hi), 0.5);
-            if (ab_horner<K>(L, f, mid) < 0.0)
-              hi = mid;
+          double sx = __dmul_rn(__dadd_rn(lo, hi), 0.5);
+          for (int it = 0; it < kAbRefine; ++it) {
+            const double fv = ab_horner<K>(L, f, sx);
+            if (fv < 0.0)
+              hi = sx;
             else
-              lo = mid;
+              lo = sx;
+            const double dv = ab_horner_d<K>(L, f, sx);
+            const double sn = __dsub_rn(sx, __ddiv_rn(fv, dv));
+            sx = (sn >= lo && sn <= hi) ? sn : __dmul_rn(__dadd_rn(lo, hi), 0.5);
           }
-          if (hi < sbest) {
-            sbest = hi;
+          if (sx < sbest) {
+            sbest = sx;
             best = f;
           }
         }
