@@ -19,8 +19,8 @@
   Y n x n x E); Y = Y0 = sqrt(eps0 / mu0), free space, for the first-order
   absorbing condition.
 
-Integrals use the collapsed-cube rule with 4 points per direction (exact for
-degree 5 >= 2p).
+Integrals use the collapsed-cube rule with p + 2 points per direction (exact
+for degree 2p + 1 >= 2p).
 """
 
 import numpy as np
@@ -107,7 +107,7 @@ def curl_matrix(topo):
 def _element_integrals(topo, g, vol, kind, chunk=2048):
     """Per-tet integrals of products of basis values; kind in
     {'m1','k','m2','w0'}."""
-    lam_q, w_q = tet_rule(4)
+    lam_q, w_q = tet_rule(topo.order + 2)   # exact for degree 2p + 1
     out = []
     for s in range(0, topo.n_tets, chunk):
         gg = g[s:s + chunk][:, None, :, :]

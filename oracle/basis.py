@@ -1,4 +1,5 @@
-"""Interpolatory Whitney bases of order 1 and 2 on a tetrahedron (Appendix).
+"""Interpolatory Whitney bases of order 1 and 2 on a tetrahedron (Appendix);
+order 3 is delegated to ``basis3``.
 
 The Appendix builds each basis as an interpolatory Silvester polynomial
 (P_i, shifted P^_i) times a lowest-order Whitney form.  Readings taken here
@@ -25,6 +26,7 @@ All arithmetic is written in a fixed order, one rounding per operation.
 
 import numpy as np
 
+from . import basis3
 from .geometry import cross
 from .topology import LOCAL_EDGES, LOCAL_FACES
 
@@ -94,6 +96,8 @@ def whitney_face(lam, g, f):
 
 
 def w1(order, lam, g):
+    if order == 3:
+        return basis3.w1(lam, g)
     out = []
     for (a, b, x, kind) in w1_spec(order):
         w = whitney_edge(lam, g, a, b)
@@ -104,6 +108,8 @@ def w1(order, lam, g):
 
 def curl_w1(order, lam, g):
     """curl(m w_ab) = grad m x w_ab + 2 m grad l_a x grad l_b."""
+    if order == 3:
+        return basis3.curl_w1(lam, g)
     out = []
     for (a, b, x, kind) in w1_spec(order):
         c = cross(g[..., a, :], g[..., b, :]) * 2.0
@@ -117,6 +123,8 @@ def curl_w1(order, lam, g):
 
 
 def w2(order, lam, g):
+    if order == 3:
+        return basis3.w2(lam, g)
     out = []
     for (f, x, kind) in w2_spec(order):
         w = whitney_face(lam, g, f)
@@ -131,6 +139,8 @@ def w2(order, lam, g):
 
 def div_w2(order, lam, g):
     """div(m w_f) = grad m . w_f + m div w_f, div w_stu = 6 grad l_s . (grad l_t x grad l_u)."""
+    if order == 3:
+        return basis3.div_w2(lam, g)
     out = []
     for (f, x, kind) in w2_spec(order):
         s, t, u = LOCAL_FACES[f]
@@ -146,6 +156,8 @@ def div_w2(order, lam, g):
 
 
 def w0(order, lam):
+    if order == 3:
+        return basis3.w0(lam)
     if order == 1:
         return lam.copy()
     vals = [lam[..., s] * (2.0 * lam[..., s] - 1.0) for s in range(4)]
@@ -154,6 +166,8 @@ def w0(order, lam):
 
 
 def grad_w0(order, lam, g):
+    if order == 3:
+        return basis3.grad_w0(lam, g)
     if order == 1:
         return g.copy() * np.ones(lam.shape + (1,))
     vals = [(4.0 * lam[..., s] - 1.0)[..., None] * g[..., s, :] for s in range(4)]

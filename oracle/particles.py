@@ -16,7 +16,7 @@
   q w int W1_i(r(s)) . (b - a) ds (Section III-B: g_i = <W1_i, G>, with an
   integration rule exact for the product of the basis and the path): the
   integrand has degree p in s, so 1 Gauss-Legendre point suffices at p=1 and
-  2 at p=2.  Note grad l . (b - a) = l(b) - l(a), so no geometry is needed
+  2 at p=2 and p=3.  Note grad l . (b - a) = l(b) - l(a), so no geometry is needed
   beyond lambda at the two ends.  Walls (faces without neighbour) reflect the
   particle specularly at the hit point; the path stays a connected polyline.
 * ``measure_rho``: rho_k = q w sum_p W0_k(x_p) (Section III-A: charge
@@ -27,7 +27,7 @@ Every float operation is written out in a fixed order (one rounding each).
 
 import numpy as np
 
-from . import basis, geometry
+from . import basis, basis3, geometry
 from .topology import LOCAL_EDGES
 
 GL2_X = 0.5773502691896257645  # 1/sqrt(3): 2-point Gauss-Legendre abscissa on [-1, 1]
@@ -70,13 +70,17 @@ def _segment_currents(order, la, lb, s0, s1, qw):
     tot = None
     for sg in (mid - r, mid + r):
         L = la + sg[:, None] * d
-        f = []
-        for (a, bb, x, kind) in basis.w1_spec(order):
-            m = 3.0 * L[:, x] - 1.0 if kind == "e" else 3.0 * L[:, x]
-            f.append(m * (L[:, a] * d[:, bb] - L[:, bb] * d[:, a]))
-        f = np.stack(f, axis=1)
+        if order == 3:
+            f = basis3.w1_along(L, d)
+        else:
+            f = []
+            for (a, bb, x, kind) in basis.w1_spec(order):
+                m = 3.0 * L[:, x] - 1.0 if kind == "e" else 3.0 * L[:, x]
+                f.append(m * (L[:, a] * d[:, bb] - L[:, bb] * d[:, a]))
+            f = np.stack(f, axis=1)
         tot = f if tot is None else tot + f
     return qw * (half[:, None] * tot)
+
 
 
 def walk_deposit(topo, g_all, c_all, x0, x1, v, tet, qw, n1, max_cross=4096):

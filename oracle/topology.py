@@ -45,8 +45,8 @@ class Topology:
     """Entities, adjacency and DOF maps of a tet mesh for a given order."""
 
     def __init__(self, xyz, tets, order, bface_tag=None):
-        if order not in (1, 2):
-            raise ValueError("order must be 1 or 2")
+        if order not in (1, 2, 3):
+            raise ValueError("order must be 1, 2 or 3")
         xyz = np.asarray(xyz, dtype=np.float64)
         t_in = np.asarray(tets, dtype=np.int64)
         t = np.sort(t_in, axis=1)
@@ -135,6 +135,48 @@ class Topology:
             self.dof0 = self.tets.copy()
             self.pec1 = self.pec_edge.copy()
             self.bnd0 = self.boundary_node.copy()
+        elif self.order == 3:
+            # basis3: W1 3 per edge, 6 per face, 3 per tet; W2 6 per face,
+            # 12 per tet; W0 nodes, 2 per edge, 1 per face
+            self.n1 = 3 * ne + 6 * nf + 3 * nt
+            self.n2 = 6 * nf + 12 * nt
+            self.n0 = nn + 2 * ne + nf
+            d1 = np.zeros((nt, 45), dtype=np.int64)
+            for j in range(6):
+                for v in range(3):
+                    d1[:, 3 * j + v] = 3 * te[:, j] + v
+            for i in range(4):
+                for v in range(6):
+                    d1[:, 18 + 6 * i + v] = 3 * ne + 6 * tf[:, i] + v
+            for v in range(3):
+                d1[:, 42 + v] = 3 * ne + 6 * nf + 3 * np.arange(nt) + v
+            self.dof1 = d1
+            d2 = np.zeros((nt, 36), dtype=np.int64)
+            for i in range(4):
+                for v in range(6):
+                    d2[:, 6 * i + v] = 6 * tf[:, i] + v
+            for v in range(12):
+                d2[:, 24 + v] = 6 * nf + 12 * np.arange(nt) + v
+            self.dof2 = d2
+            d0 = np.zeros((nt, 20), dtype=np.int64)
+            d0[:, :4] = self.tets
+            for j in range(6):
+                for v in range(2):
+                    d0[:, 4 + 2 * j + v] = nn + 2 * te[:, j] + v
+            for i in range(4):
+                d0[:, 16 + i] = nn + 2 * ne + tf[:, i]
+            self.dof0 = d0
+            pec = np.zeros(self.n1, dtype=bool)
+            for v in range(3):
+                pec[3 * np.nonzero(self.pec_edge)[0] + v] = True
+            pf = np.nonzero(self.face_tag == 0)[0]
+            for v in range(6):
+                pec[3 * ne + 6 * pf + v] = True
+            self.pec1 = pec
+            bf = np.nonzero(self.boundary_face)[0]
+            bnd_face = np.zeros(nf, dtype=bool)
+            bnd_face[bf] = True
+            self.bnd0 = np.concatenate([self.boundary_node, np.repeat(self.boundary_edge, 2), bnd_face])
         else:
             self.n1 = 2 * ne + 2 * nf
             self.n2 = 3 * nf + 3 * nt

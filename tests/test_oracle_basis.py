@@ -82,10 +82,15 @@ def test_tube_mesh_counts():
 
 def test_dof_counts_match_appendix():
     gold = json.load(open(GOLDEN))["dof_counts_per_tet"]
-    for k in (1, 2):
+    for k in (1, 2, 3):
         n0, n1, n2 = basis.n_local(k)
         assert (n0, n1, n2) == (gold[f"k{k}"]["w0"], gold[f"k{k}"]["w1"], gold[f"k{k}"]["w2"])
-        assert len(basis.w1_spec(k)) == n1 and len(basis.w2_spec(k)) == n2
+        if k < 3:
+            assert len(basis.w1_spec(k)) == n1 and len(basis.w2_spec(k)) == n2
+        else:
+            from oracle import basis3
+            assert len(basis3.w1_spec3()) == n1 and len(basis3.w2_spec3()) == n2
+            assert len(basis3.w0_spec3()) == n0
 
 
 def test_barycentric_maps():
@@ -108,7 +113,7 @@ def _values(fn, order, p, pts):
     return fn(order, lam, gg) if fn is not basis.w0 else fn(order, lam)
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_ranks(order):
     rng = np.random.default_rng(1)
     p = _rand_tet(rng)
@@ -129,7 +134,7 @@ def _in_span(vals, target):
     return np.max(np.abs(A @ x - y)) / max(1.0, np.max(np.abs(y)))
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_polynomial_reproduction(order):
     """W1 of order 1 spans the Whitney space {a + b x r}; order 2 spans all
     linear vector fields and gradients of quadratics (Nedelec first kind of
@@ -144,7 +149,13 @@ def test_polynomial_reproduction(order):
         c0 = rng.normal()
         assert _in_span(w1, a + np.cross(bb, pts)) < 1e-12
         assert _in_span(w2, a + c0 * pts) < 1e-12
-        if order == 2:
+        if order == 3:
+            # all quadratic vector fields (Nedelec / Raviart-Thomas of degree 3 contain P2^3)
+            Q = rng.normal(size=(3, 3, 3))
+            quad = np.einsum("kij,qi,qj->qk", Q, pts, pts) + pts @ rng.normal(size=(3, 3)) + a
+            assert _in_span(w1, quad) < 1e-11
+            assert _in_span(w2, quad) < 1e-11
+        if order >= 2:
             G = rng.normal(size=(3, 3))
             lin = pts @ G.T + a
             assert _in_span(w1, lin) < 1e-12
@@ -159,7 +170,7 @@ def test_polynomial_reproduction(order):
     assert np.allclose(w0.sum(axis=1), 1.0, atol=1e-13)  # partition of unity
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_curl_against_finite_differences(order):
     rng = np.random.default_rng(3)
     p = _rand_tet(rng)
@@ -190,12 +201,13 @@ def test_curl_against_finite_differences(order):
         assert np.max(np.abs(dfd - dw)) < 1e-6 * max(1.0, np.max(np.abs(dw)))
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_exact_sequence_maps(order):
     d_loc, res_d = assemble.local_grad_map(order)
     c_loc, res_c = assemble.local_curl_map(order)
-    assert res_d < 1e-13 and res_c < 1e-13
-    assert np.max(np.abs(c_loc @ d_loc)) < 1e-13  # curl grad = 0
+    tol = 1e-13 if order < 3 else 1e-12   # order-3 values reach (4 l)^3
+    assert res_d < tol and res_c < tol
+    assert np.max(np.abs(c_loc @ d_loc)) < tol  # curl grad = 0
     # affine invariance: the reference-tet coefficients hold on any tet
     rng = np.random.default_rng(4)
     for _ in range(5):
@@ -224,7 +236,7 @@ def test_exact_sequence_maps(order):
             assert np.allclose(c_loc[f], row)
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_interelement_continuity(order):
     """Tangential trace of sum e_i W1_i and normal trace of sum b_j W2_j agree
     from both sides of every interior face of a small jittered mesh."""
@@ -255,7 +267,7 @@ def test_interelement_continuity(order):
     assert worst_t < 1e-10 and worst_n < 1e-10
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_global_maps_consistent_and_exact(order):
     xyz, tets = workloads.kuhn_box(3, 3, 3, jitter=0.1, seed=7)
     t = topology.Topology(xyz, tets, order)
@@ -340,7 +352,7 @@ def test_whitney_element_matrices_closed_form():
                 assert abs(K[I, J] - k) < 1e-13 * np.abs(K).max()
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_global_mass_and_curlcurl_energies(order):
     """For E = grad(phi) with phi linear, e = D phi_h gives e^T M e =
     eps0 |grad phi|^2 Vol and K e = 0; the L2 projection of E = (-y, x, 0)/2
@@ -354,9 +366,15 @@ def test_global_mass_and_curlcurl_energies(order):
     k = np.array([0.3, -1.2, 0.7])
     if order == 1:
         phi = xyz @ k
-    else:
+    elif order == 2:
         mid = 0.5 * (xyz[t.edges[:, 0]] + xyz[t.edges[:, 1]])
         phi = np.concatenate([xyz @ k, mid @ k])
+    else:
+        # W0 lattice points: nodes, (2a+b)/3 and (a+2b)/3 per edge, face centroids
+        a, b = xyz[t.edges[:, 0]], xyz[t.edges[:, 1]]
+        ep = np.stack([(2 * a + b) / 3, (a + 2 * b) / 3], axis=1).reshape(-1, 3)
+        fc = xyz[t.faces].mean(axis=1)
+        phi = np.concatenate([xyz @ k, ep @ k, fc @ k])
     e = D @ phi
     assert abs(e @ (M @ e) - assemble.EPS0 * (k @ k) * 1.0) < 1e-12 * assemble.EPS0 * (k @ k)
     assert np.abs(K @ e).max() < 1e-10 * np.abs(K).max() * np.abs(e).max()

@@ -47,7 +47,7 @@ def test_gathered_B_equals_uniform_B0(c1):
     assert np.all(E == 0.0) and np.all(B == np.array([0.1, -0.2, 0.3]))
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_segment_current_vs_brute_force(order):
     """q w int W1_j . dr by the few-point rule vs a 64-point Gauss-Legendre
     integral of the basis evaluated at physical points along the chord."""
@@ -80,7 +80,7 @@ def _locate(topo, g, c, x, tol=1e-9):
     return inside, lam.min(axis=1)
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_walk_subsegments_cover_chord(order):
     """The sub-segments the walk integrates over cover [0, 1] in order without
     gaps; the chord ends in the returned tet (brute-force location)."""
@@ -169,7 +169,7 @@ def test_wall_reflection_mirror_image():
         assert lam.min() > -1e-12
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_continuity_identity_one_step(order):
     """rho^{n+1} - rho^n = D^T Delta g on interior W0 DOFs (Section IV-D)."""
     cfg = workloads.make_config(0, n_particles=2000)
