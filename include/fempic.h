@@ -35,7 +35,18 @@
  *     2*N_e + 2*face + v (v=0: 3 l_u w_st, v=1: 3 l_t w_su for face s<t<u);
  *     W2 DOFs 3*face + v ((4 l_v - 1) w_stu for the v-th face vertex) then
  *     3*N_f + 3*tet + i (4 l_i w_(face opposite local vertex i), i = 0..2);
- *     W0 DOFs nodes then N_n + edge (mid-edge Lagrange nodes).
+ *     W0 DOFs nodes then N_n + edge (mid-edge Lagrange nodes).  Order 3
+ *     (Appendix; P_i / P^_i the Silvester polynomials at scale = index sum):
+ *     W1 DOFs 3*edge + v (P^_a(l_lo) P^_b(l_hi) w, (a,b) = (3,1), (2,2),
+ *     (1,3)), then 3*N_e + 6*face + v (pairs (s,t) then (s,u) of face s<t<u,
+ *     each with (a,b,c) = (2,1,1), (1,2,1), (1,1,2) on the pair's first and
+ *     second vertex and the face's third, the third as P_c), then 3*N_e +
+ *     6*N_f + 3*tet + v (pairs (0,1), (0,2), (0,3) of the sorted tet, all
+ *     indices 1); W2 DOFs 6*face + v ((a,b,c) = (3,1,1), (1,3,1), (1,1,3),
+ *     (2,2,1), (2,1,2), (1,2,2)) then 6*N_f + 12*tet + 4*i + v (faces
+ *     opposite local vertices i = 0..2, index 2 on the v-th of face vertex
+ *     0, 1, 2 or the opposite vertex); W0 DOFs nodes, then N_n + 2*edge + v
+ *     (lattice point nearer the lower vertex first), then N_n + 2*N_e + face.
  *   - Units are SI.  Boundary faces are perfect electric conductors (W1 DOFs
  *     on them held at 0) unless femPIC_create_ext tags them impedance
  *     (first-order absorbing); particles reflect specularly at every wall.
@@ -71,7 +82,8 @@ enum {
                              walk's decisions are bit-reproducible             */
   FEMPIC_FP64 = 1,        /* all FP64, fused multiply-add and factored forms   */
   FEMPIC_MIXED = 2        /* FP32 gather and push; FP64 positions, walk,
-                             deposit, charge and CG                            */
+                             deposit, charge and CG (order 3 has no FP32
+                             kernel: it runs as FEMPIC_FP64)                  */
 };
 
 /* ---- field time schemes ------------------------------------------------- */
@@ -213,7 +225,8 @@ void femPIC_default_opts(femPIC_opts* opts);
 
 /* Build the mesh complex, DOF numbering, Hodge/curl/gradient matrices (Section
  * III-A) and upload mesh, matrices and particles to the device.  order is p
- * (1 or 2).  opts may be NULL for defaults.  On success *out holds a handle.
+ * (1, 2 or 3; FEMPIC_PUSH_AB4 and batching take 1 or 2 only).  opts may be
+ * NULL for defaults.  On success *out holds a handle.
  * On failure *out may still hold a handle that only carries the error message
  * (femPIC_last_error); release it with femPIC_destroy. */
 int femPIC_create(const femPIC_mesh* mesh, int32_t order, const femPIC_species* species,
@@ -313,8 +326,8 @@ const char* femPIC_last_error(const FemPIC* h);
 /* ---- batching: many independent instances advanced together -------------
  * The paper runs one simulation at a time; this is a systems extension for
  * many small, uneven instances on one GPU.  A batch groups created handles
- * (FEMPIC_FP64 or FEMPIC_MIXED, trapezoid scheme, at most 2^20 tets each, one
- * device).  femPIC_batch_step advances every member by n_steps steps of its
+ * (FEMPIC_FP64 or FEMPIC_MIXED, trapezoid scheme, order 1 or 2, Boris push,
+ * one species, at most 2^20 tets each, one device).  femPIC_batch_step advances every member by n_steps steps of its
  * own dt (dt_host[i]) with one launch per kernel for all members: a batched
  * counting sort, one persistent gather/push/walk/deposit kernel, batched
  * right-hand side and b update, and one cooperative block-diagonal PCG in

@@ -447,8 +447,11 @@ int measure_rho(FemPIC* h, double* rho_out) {
   if (h->order == 1)
     k_rho<1><<<grid, 256, 0, h->stream>>>(h->np, h->px[0], h->px[1], h->px[2], h->ptet, h->geom, h->dof0, qw,
                                           rho_out, h->pid, st);
-  else
+  else if (h->order == 2)
     k_rho<2><<<grid, 256, 0, h->stream>>>(h->np, h->px[0], h->px[1], h->px[2], h->ptet, h->geom, h->dof0, qw,
+                                          rho_out, h->pid, st);
+  else
+    k_rho<3><<<grid, 256, 0, h->stream>>>(h->np, h->px[0], h->px[1], h->px[2], h->ptet, h->geom, h->dof0, qw,
                                           rho_out, h->pid, st);
   h->launches++;
   CK(cudaGetLastError());
@@ -592,6 +595,13 @@ int launch_particles(FemPIC* h, double dt) {
     else
       agg ? k_particle_fast<1, true, false><<<grid, 256, 0, h->stream>>>(a)
           : k_particle_fast<1, false, false><<<grid, 256, 0, h->stream>>>(a);
+  } else if (h->order == 3) {
+    // order 3 has no hand-factored fast forms: the generic kernel, one rounding
+    // per operation when strict, contracted otherwise
+    if (strict)
+      k_particle<3, Strict><<<grid, 256, 0, h->stream>>>(a);
+    else
+      k_particle<3, Fast><<<grid, 256, 0, h->stream>>>(a);
   } else {
     if (strict)
       k_particle<2, Strict><<<grid, 256, 0, h->stream>>>(a);
@@ -605,6 +615,29 @@ int launch_particles(FemPIC* h, double dt) {
   h->launches++;
   CK(cudaGetLastError());
   return FEMPIC_OK;
+}
+
+// field evaluation at given points: order and arithmetic picked at run time
+template <int P>
+void launch_eval_fields_p(FemPIC* h, int grid, bool strict, int64_t n, const double* x, const int32_t* tet, double* E,
+                          double* B) {
+  const double* B0 = h->opts.B0;
+  if (strict)
+    k_eval_fields<P, Strict><<<grid, 128, 0, h->stream>>>(n, x, tet, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
+                                                          B0[1], B0[2], E, B);
+  else
+    k_eval_fields<P, Fast><<<grid, 128, 0, h->stream>>>(n, x, tet, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0], B0[1],
+                                                        B0[2], E, B);
+}
+
+void launch_eval_fields(FemPIC* h, int grid, bool strict, int64_t n, const double* x, const int32_t* tet, double* E,
+                        double* B) {
+  if (h->order == 1)
+    launch_eval_fields_p<1>(h, grid, strict, n, x, tet, E, B);
+  else if (h->order == 2)
+    launch_eval_fields_p<2>(h, grid, strict, n, x, tet, E, B);
+  else
+    launch_eval_fields_p<3>(h, grid, strict, n, x, tet, E, B);
 }
 
 int field_update(FemPIC* h, double dt, cudaEvent_t ev_pcg0, cudaEvent_t ev_pcg1) {
@@ -914,8 +947,12 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
     h->err = "NULL mesh or species";
     return FEMPIC_ERR_ARG;
   }
-  if (order != 1 && order != 2) {
-    h->err = "order must be 1 or 2";
+  if (order < 1 || order > 3) {
+    h->err = "order must be 1, 2 or 3";
+    return FEMPIC_ERR_ARG;
+  }
+  if (order == 3 && opts && opts->push == FEMPIC_PUSH_AB4) {
+    h->err = "the Adams-Bashforth push is built for orders 1 and 2";
     return FEMPIC_ERR_ARG;
   }
   if (o.precision < 0 || o.precision > 2 || o.scheme < 0 || o.scheme > 1 || !(o.cg_rtol > 0) ||
@@ -1413,22 +1450,7 @@ int femPIC_eval_fields(FemPIC* h, int64_t n, const double* x_host, const int32_t
   CK(cudaMemcpy(dt, tet_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice));
   int grid = grid_for(n, 128, 1 << 30);
   bool strict = h->opts.precision == FEMPIC_FP64_STRICT;
-  const double* B0 = h->opts.B0;
-  if (h->order == 1) {
-    if (strict)
-      k_eval_fields<1, Strict><<<grid, 128, 0, h->stream>>>(n, dx, dt, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
-                                                            B0[1], B0[2], dE, dB);
-    else
-      k_eval_fields<1, Fast><<<grid, 128, 0, h->stream>>>(n, dx, dt, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
-                                                          B0[1], B0[2], dE, dB);
-  } else {
-    if (strict)
-      k_eval_fields<2, Strict><<<grid, 128, 0, h->stream>>>(n, dx, dt, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
-                                                            B0[1], B0[2], dE, dB);
-    else
-      k_eval_fields<2, Fast><<<grid, 128, 0, h->stream>>>(n, dx, dt, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
-                                                          B0[1], B0[2], dE, dB);
-  }
+  launch_eval_fields(h, grid, strict, n, dx, dt, dE, dB);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(E_host, dE, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(B_host, dB, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
@@ -1502,22 +1524,7 @@ int femPIC_eval_fields_noalloc(FemPIC* h, int64_t n, const double* x_host, const
   CK(cudaMemcpyAsync(dt, tet_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
   int grid = grid_for(n, 128, 1 << 30);
   bool strict = h->opts.precision == FEMPIC_FP64_STRICT;
-  const double* B0 = h->opts.B0;
-  if (h->order == 1) {
-    if (strict)
-      k_eval_fields<1, Strict><<<grid, 128, 0, h->stream>>>(n, dx, dt, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
-                                                            B0[1], B0[2], dE, dB);
-    else
-      k_eval_fields<1, Fast><<<grid, 128, 0, h->stream>>>(n, dx, dt, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
-                                                          B0[1], B0[2], dE, dB);
-  } else {
-    if (strict)
-      k_eval_fields<2, Strict><<<grid, 128, 0, h->stream>>>(n, dx, dt, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
-                                                            B0[1], B0[2], dE, dB);
-    else
-      k_eval_fields<2, Fast><<<grid, 128, 0, h->stream>>>(n, dx, dt, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
-                                                          B0[1], B0[2], dE, dB);
-  }
+  launch_eval_fields(h, grid, strict, n, dx, dt, dE, dB);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(E_host, dE, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(B_host, dB, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
@@ -1816,6 +1823,10 @@ int femPIC_batch_create(FemPIC* const* members, int32_t n, FemPICBatch** out) {
     }
     if (h->n_species != 1 || h->opts.push != FEMPIC_PUSH_BORIS) {
       b->err = "batched members must have a single species and the Boris push";
+      return FEMPIC_ERR_ARG;
+    }
+    if (h->order > 2) {
+      b->err = "batched members must be of order 1 or 2";
       return FEMPIC_ERR_ARG;
     }
     if (h->n_tets > 1024 * 1024) {

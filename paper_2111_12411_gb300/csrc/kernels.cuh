@@ -104,10 +104,135 @@ __device__ __forceinline__ void bary(const TetGeom& G, const double* x, double* 
                    G.c[i]);
 }
 
+// ---- order 3 (Appendix): multipliers as products of Silvester polynomials,
+// P_i(l) = prod_{m<i} (n l - m) / i!, P^_i(l) = prod_{1<=m<i} (n l - m) / (i-1)!,
+// evaluated factor by factor from 1.0, one rounding per operation.
+template <class Ar>
+__device__ __forceinline__ double silv(int i, double n, double l, bool hat) {
+  double val = 1.0;
+  for (int m = hat ? 1 : 0; m < i; ++m) val = Ar::mul(val, Ar::sub(Ar::mul(n, l), (double)m));
+  const int k = hat ? i - 1 : i;
+  const double fac = k <= 1 ? 1.0 : (k == 2 ? 2.0 : 6.0);
+  return Ar::div(val, fac);
+}
+
+// W1 of order 3, function j: m(l) (l_a grad l_b - l_b grad l_a), scale 4.
+// j < 18: edge j/3 with (P^_a(l_s), P^_b(l_t)), (a, b) = (3,1), (2,2), (1,3);
+// j < 42: face (j-18)/6, pairs (s,t) then (s,u) of the face s<t<u, each with
+// (P^_a, P^_b, P_c) on (pair first, pair second, third vertex), (a,b,c) =
+// (2,1,1), (1,2,1), (1,1,2); j < 45: pairs (0,1), (0,2), (0,3) with
+// P^_1 P^_1 P_1 P_1 (the other two vertices ascending).
+template <class Ar>
+__device__ __forceinline__ double w1_p3(int j, const double* l, int& a, int& b) {
+  if (j < 18) {
+    const int e = j / 3, q = j % 3;
+    a = edge_s(e);
+    b = edge_t(e);
+    double m = 1.0;
+    m = Ar::mul(m, silv<Ar>(3 - q, 4.0, l[a], true));
+    m = Ar::mul(m, silv<Ar>(1 + q, 4.0, l[b], true));
+    return m;
+  }
+  if (j < 42) {
+    const int f = (j - 18) / 6, r = (j - 18) % 6, pr = r / 3, q = r % 3;
+    const int s = face_v(f, 0), t = face_v(f, 1), u = face_v(f, 2);
+    a = s;
+    b = pr == 0 ? t : u;
+    const int c = pr == 0 ? u : t;
+    const int ia = q == 0 ? 2 : 1, ib = q == 1 ? 2 : 1, ic = q == 2 ? 2 : 1;
+    double m = 1.0;
+    m = Ar::mul(m, silv<Ar>(ia, 4.0, l[a], true));
+    m = Ar::mul(m, silv<Ar>(ib, 4.0, l[b], true));
+    m = Ar::mul(m, silv<Ar>(ic, 4.0, l[c], false));
+    return m;
+  }
+  a = 0;
+  b = j - 41;
+  int o0 = -1, o1 = -1;
+#pragma unroll
+  for (int v = 1; v < 4; ++v)
+    if (v != b) {
+      if (o0 < 0)
+        o0 = v;
+      else
+        o1 = v;
+    }
+  double m = 1.0;
+  m = Ar::mul(m, silv<Ar>(1, 4.0, l[a], true));
+  m = Ar::mul(m, silv<Ar>(1, 4.0, l[b], true));
+  m = Ar::mul(m, silv<Ar>(1, 4.0, l[o0], false));
+  m = Ar::mul(m, silv<Ar>(1, 4.0, l[o1], false));
+  return m;
+}
+
+// W2 of order 3, function j: m(l) w_face, scale 5.  j < 24: face j/6 with
+// (P^_a, P^_b, P^_c) on its vertices, (a,b,c) = (3,1,1), (1,3,1), (1,1,3),
+// (2,2,1), (2,1,2), (1,2,2); j < 36: the faces opposite vertices 0, 1, 2,
+// (j-24)/4, with (a,b,c,d) = (2,1,1,1), (1,2,1,1), (1,1,2,1), (1,1,1,2), d on
+// the opposite vertex (P_d).
+template <class Ar>
+__device__ __forceinline__ double w2_p3(int j, const double* l, int& f) {
+  if (j < 24) {
+    f = j / 6;
+    const int q = j % 6;
+    constexpr int T[6][3] = {{3, 1, 1}, {1, 3, 1}, {1, 1, 3}, {2, 2, 1}, {2, 1, 2}, {1, 2, 2}};
+    double m = 1.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) m = Ar::mul(m, silv<Ar>(T[q][k], 5.0, l[face_v(f, k)], true));
+    return m;
+  }
+  f = (j - 24) / 4;
+  const int q = (j - 24) % 4;
+  double m = 1.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) m = Ar::mul(m, silv<Ar>(q == k ? 2 : 1, 5.0, l[face_v(f, k)], true));
+  m = Ar::mul(m, silv<Ar>(q == 3 ? 2 : 1, 5.0, l[f], false));
+  return m;
+}
+
+// W0 of order 3 (Lagrange on the scale-3 lattice), function k: nodes, then two
+// per edge ((2,1) then (1,2) on (s,t)), then one per face; factors in vertex order
+template <class Ar>
+__device__ __forceinline__ double w0_p3(int k, const double* l) {
+  if (k < 4) return Ar::mul(1.0, silv<Ar>(3, 3.0, l[k], false));
+  if (k < 16) {
+    const int e = (k - 4) / 2, q = (k - 4) % 2;
+    double m = 1.0;
+    m = Ar::mul(m, silv<Ar>(q == 0 ? 2 : 1, 3.0, l[edge_s(e)], false));
+    m = Ar::mul(m, silv<Ar>(q == 0 ? 1 : 2, 3.0, l[edge_t(e)], false));
+    return m;
+  }
+  const int f = k - 16;
+  double m = 1.0;
+#pragma unroll
+  for (int v = 0; v < 3; ++v) m = Ar::mul(m, silv<Ar>(1, 3.0, l[face_v(f, v)], false));
+  return m;
+}
+
+template <int P>
+struct Nloc {
+  static constexpr int n1 = P == 1 ? 6 : (P == 2 ? 20 : 45);
+  static constexpr int n2 = P == 1 ? 4 : (P == 2 ? 15 : 36);
+  static constexpr int n0 = P == 1 ? 4 : (P == 2 ? 10 : 20);
+};
+
 // E = sum_j e_j W1_j(x), accumulated in j order
 template <int P, class Ar>
 __device__ __forceinline__ void gather_E(const TetGeom& G, const double* l, const double* ev, double* E) {
   E[0] = E[1] = E[2] = 0.0;
+  if (P == 3) {
+    #pragma unroll
+    for (int j = 0; j < 45; ++j) {
+      int a, b;
+      const double m = w1_p3<Ar>(j, l, a, b);
+      double w[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) w[k] = Ar::mul(m, Ar::sub(Ar::mul(l[a], G.g[b][k]), Ar::mul(l[b], G.g[a][k])));
+#pragma unroll
+      for (int k = 0; k < 3; ++k) E[k] = Ar::add(E[k], Ar::mul(ev[j], w[k]));
+    }
+    return;
+  }
   constexpr int N = P == 1 ? 6 : 20;
 #pragma unroll
   for (int j = 0; j < N; ++j) {
@@ -158,6 +283,17 @@ __device__ __forceinline__ void gather_B(const TetGeom& G, const double* l, cons
       whitney_face<Ar>(G, l, f, w);
 #pragma unroll
       for (int k = 0; k < 3; ++k) acc[k] = Ar::add(acc[k], Ar::mul(bv[f], w[k]));
+    }
+  } else if (P == 3) {
+    double wf[4][3];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) whitney_face<Ar>(G, l, f, wf[f]);
+    #pragma unroll
+    for (int j = 0; j < 36; ++j) {
+      int f;
+      const double m = w2_p3<Ar>(j, l, f);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc[k] = Ar::add(acc[k], Ar::mul(bv[j], Ar::mul(m, wf[f][k])));
     }
   } else {
     double wf[4][3];
@@ -217,6 +353,27 @@ __device__ __forceinline__ void deposit_segment(const double* la, const double* 
       double val = Ar::sub(Ar::mul(Pv[s], Qv[t]), Ar::mul(Pv[t], Qv[s]));
       atomicAdd(dg + __ldg(dofs + j), Ar::mul(qw, val));
     }
+  } else if (P == 3) {
+    double half = Ar::mul(Ar::sub(s1, s0), 0.5);
+    double mid = Ar::mul(Ar::add(s0, s1), 0.5);
+    double r = Ar::mul(half, kGL2X);
+    double sg[2] = {Ar::sub(mid, r), Ar::add(mid, r)};
+    double L[2][4];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) L[q][i] = Ar::add(la[i], Ar::mul(sg[q], d[i]));
+    #pragma unroll
+    for (int j = 0; j < 45; ++j) {
+      double f[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        int a, b;
+        const double m = w1_p3<Ar>(j, L[q], a, b);
+        f[q] = Ar::mul(m, Ar::sub(Ar::mul(L[q][a], d[b]), Ar::mul(L[q][b], d[a])));
+      }
+      atomicAdd(dg + __ldg(dofs + j), Ar::mul(qw, Ar::mul(half, Ar::add(f[0], f[1]))));
+    }
   } else {
     double half = Ar::mul(Ar::sub(s1, s0), 0.5);
     double mid = Ar::mul(Ar::add(s0, s1), 0.5);
@@ -247,6 +404,9 @@ __device__ __forceinline__ void deposit_rho(const double* l, double qw, const in
   if (P == 1) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) atomicAdd(rho + __ldg(dofs + k), Ar::mul(qw, l[k]));
+  } else if (P == 3) {
+    #pragma unroll
+    for (int k = 0; k < 20; ++k) atomicAdd(rho + __ldg(dofs + k), Ar::mul(qw, w0_p3<Ar>(k, l)));
   } else {
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -315,9 +475,9 @@ __device__ __forceinline__ void particle_consts(const ParticleArgs& a, int64_t i
 // One thread per particle: gather, push, walk, deposit, charge.
 template <int P, class Ar>
 __global__ void __launch_bounds__(256) k_particle(ParticleArgs a) {
-  constexpr int N1 = P == 1 ? 6 : 20;
-  constexpr int N2 = P == 1 ? 4 : 15;
-  constexpr int N0 = P == 1 ? 4 : 10;
+  constexpr int N1 = Nloc<P>::n1;
+  constexpr int N2 = Nloc<P>::n2;
+  constexpr int N0 = Nloc<P>::n0;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long my_cross = 0;
   if (i < a.n) {
@@ -440,7 +600,7 @@ template <int P>
 __global__ void k_rho(int64_t n, const double* x0, const double* x1, const double* x2, const int32_t* tet,
                       const double* geom, const int32_t* dof0, double qw, double* rho, const int32_t* pid,
                       SpeciesTable sp) {
-  constexpr int N0 = P == 1 ? 4 : 10;
+  constexpr int N0 = Nloc<P>::n0;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (sp.n > 1) qw = sp.qw[species_of(sp, __ldg(pid + i))];
@@ -458,8 +618,8 @@ template <int P, class Ar>
 __global__ void k_eval_fields(int64_t n, const double* xs, const int32_t* tets, const double* geom,
                               const int32_t* dof1, const int32_t* dof2, const double* e, const double* b,
                               double B00, double B01, double B02, double* Eo, double* Bo) {
-  constexpr int N1 = P == 1 ? 6 : 20;
-  constexpr int N2 = P == 1 ? 4 : 15;
+  constexpr int N1 = Nloc<P>::n1;
+  constexpr int N2 = Nloc<P>::n2;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int T = tets[i];

@@ -188,6 +188,27 @@ int pair_index(int a, int b) {
   return -1;
 }
 
+// Silvester polynomials at scale n in l_v (Appendix): P_i = prod_{m<i} (n l - m) / i!,
+// P^_i = prod_{1<=m<i} (n l - m) / (i-1)!
+Poly silvester(int i, int n, int v, bool hat) {
+  Poly r = pconst(R(1));
+  for (int m = hat ? 1 : 0; m < i; ++m) r = pmul(r, lin(v, n, -m));
+  return pscale(r, R(1, fact(hat ? i - 1 : i)));
+}
+
+// Order-3 multipliers (the same families as the reference evaluation): W1
+// m w_st with m = P^_a(l_s) P^_b(l_t) P_c(l_u) P_d(l_v) at scale 4; W2
+// m w_stu with P^_a P^_b P^_c P_d at scale 5; W0 the scale-3 lattice.
+struct Factor {
+  int v, i;
+  bool hat;
+};
+Poly multiplier(const std::vector<Factor>& fs, int n) {
+  Poly r = pconst(R(1));
+  for (const Factor& f : fs) r = pmul(r, silvester(f.i, n, f.v, f.hat));
+  return r;
+}
+
 // Redundant forms: W1 = sum_a P[a] grad l_a; W2 = sum_{a<b} P[pair] grad l_a x grad l_b.
 std::vector<std::array<Poly, 4>> w1_forms(int p) {
   std::vector<std::array<Poly, 4>> out;
@@ -199,6 +220,27 @@ std::vector<std::array<Poly, 4>> w1_forms(int p) {
   };
   if (p == 1) {
     for (auto& e : kLocalEdges) add(e[0], e[1], pconst(R(1)));
+    return out;
+  }
+  if (p == 3) {
+    for (auto& e : kLocalEdges) {
+      const int ab[3][2] = {{3, 1}, {2, 2}, {1, 3}};
+      for (auto& q : ab) add(e[0], e[1], multiplier({{e[0], q[0], true}, {e[1], q[1], true}}, 4));
+    }
+    for (auto& f : kLocalFaces) {
+      const int pr[2][3] = {{f[0], f[1], f[2]}, {f[0], f[2], f[1]}};
+      const int abc[3][3] = {{2, 1, 1}, {1, 2, 1}, {1, 1, 2}};
+      for (auto& P : pr)
+        for (auto& q : abc)
+          add(P[0], P[1], multiplier({{P[0], q[0], true}, {P[1], q[1], true}, {P[2], q[2], false}}, 4));
+    }
+    const int inner[3][2] = {{0, 1}, {0, 2}, {0, 3}};
+    for (auto& P : inner) {
+      int o[2], k = 0;
+      for (int v = 0; v < 4; ++v)
+        if (v != P[0] && v != P[1]) o[k++] = v;
+      add(P[0], P[1], multiplier({{P[0], 1, true}, {P[1], 1, true}, {o[0], 1, false}, {o[1], 1, false}}, 4));
+    }
     return out;
   }
   for (auto& e : kLocalEdges) {
@@ -227,6 +269,20 @@ std::vector<std::array<Poly, 6>> w2_forms(int p) {
     for (int f = 0; f < 4; ++f) add(f, pconst(R(1)));
     return out;
   }
+  if (p == 3) {
+    const int abc[6][3] = {{3, 1, 1}, {1, 3, 1}, {1, 1, 3}, {2, 2, 1}, {2, 1, 2}, {1, 2, 2}};
+    for (int f = 0; f < 4; ++f) {
+      const int* F = kLocalFaces[f];
+      for (auto& q : abc) add(f, multiplier({{F[0], q[0], true}, {F[1], q[1], true}, {F[2], q[2], true}}, 5));
+    }
+    const int abcd[4][4] = {{2, 1, 1, 1}, {1, 2, 1, 1}, {1, 1, 2, 1}, {1, 1, 1, 2}};
+    for (int f = 0; f < 3; ++f) {
+      const int* F = kLocalFaces[f];
+      for (auto& q : abcd)
+        add(f, multiplier({{F[0], q[0], true}, {F[1], q[1], true}, {F[2], q[2], true}, {f, q[3], false}}, 5));
+    }
+    return out;
+  }
   for (int f = 0; f < 4; ++f)
     for (int v = 0; v < 3; ++v) add(f, lin(kLocalFaces[f][v], 4, -1));  // (4 l_v - 1) w_stu
   for (int i = 0; i < 3; ++i) add(i, lin(i, 4, 0));                       // 4 l_i w_(face i)
@@ -237,6 +293,15 @@ std::vector<Poly> w0_forms(int p) {
   std::vector<Poly> out;
   if (p == 1) {
     for (int i = 0; i < 4; ++i) out.push_back(lam(i));
+    return out;
+  }
+  if (p == 3) {
+    for (int v = 0; v < 4; ++v) out.push_back(multiplier({{v, 3, false}}, 3));
+    for (auto& e : kLocalEdges) {
+      out.push_back(multiplier({{e[0], 2, false}, {e[1], 1, false}}, 3));
+      out.push_back(multiplier({{e[0], 1, false}, {e[1], 2, false}}, 3));
+    }
+    for (auto& f : kLocalFaces) out.push_back(multiplier({{f[0], 1, false}, {f[1], 1, false}, {f[2], 1, false}}, 3));
     return out;
   }
   for (int s = 0; s < 4; ++s) out.push_back(pmul(lam(s), lin(s, 2, -1)));
@@ -475,8 +540,8 @@ std::string build_local_tables(int p, LocalTables* T) {
           }
   T->I0.resize(T->nl0);
   for (int k = 0; k < T->nl0; ++k) T->I0[k] = to_double(integrate_bary(f0[k]));
-  if (p == 2) {
-    // l_v grad l_a lies in the order-2 space: its exact W1 coefficients
+  if (p >= 2) {
+    // l_v grad l_a lies in the order-p space (p >= 2): its exact W1 coefficients
     std::vector<Vec> tg;
     for (int v = 0; v < 4; ++v)
       for (int a = 0; a < 4; ++a) {
@@ -496,8 +561,8 @@ std::string build_local_tables(int p, LocalTables* T) {
 
 int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets_in, int32_t n_tets, int p,
                 HostModel* m, std::string* err, const int32_t* bface_tag) {
-  if (p != 1 && p != 2) {
-    *err = "order must be 1 or 2";
+  if (p < 1 || p > 3) {
+    *err = "order must be 1, 2 or 3";
     return 1;
   }
   if (n_nodes < 4 || n_tets < 1 || !xyz || !tets_in) {
@@ -643,6 +708,45 @@ int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets_in, int3
     }
     m->pec1.assign(pedge.begin(), pedge.end());
     m->bnd0.assign(bnode.begin(), bnode.end());
+  } else if (p == 3) {
+    // W1: 3 per edge, 6 per face, 3 per tet; W2: 6 per face, 12 per tet;
+    // W0: nodes, 2 per edge, 1 per face (the local order of the forms above)
+    if ((int64_t)3 * ne + 6 * (int64_t)nf + 3 * (int64_t)nt > INT32_MAX ||
+        (int64_t)6 * nf + 12 * (int64_t)nt > INT32_MAX) {
+      *err = "mesh too large for 32-bit DOF ids";
+      return 1;
+    }
+    m->n1 = 3 * ne + 6 * nf + 3 * nt;
+    m->n2 = 6 * nf + 12 * nt;
+    m->n0 = nn + 2 * ne + nf;
+    for (int32_t t = 0; t < nt; ++t) {
+      int32_t* d1t = &m->dof1[(size_t)t * 45];
+      for (int k = 0; k < 6; ++k)
+        for (int v = 0; v < 3; ++v) d1t[3 * k + v] = 3 * tet_edge[(size_t)t * 6 + k] + v;
+      for (int k = 0; k < 4; ++k)
+        for (int v = 0; v < 6; ++v) d1t[18 + 6 * k + v] = 3 * ne + 6 * tet_face[(size_t)t * 4 + k] + v;
+      for (int v = 0; v < 3; ++v) d1t[42 + v] = 3 * ne + 6 * nf + 3 * t + v;
+      int32_t* d2t = &m->dof2[(size_t)t * 36];
+      for (int k = 0; k < 4; ++k)
+        for (int v = 0; v < 6; ++v) d2t[6 * k + v] = 6 * tet_face[(size_t)t * 4 + k] + v;
+      for (int v = 0; v < 12; ++v) d2t[24 + v] = 6 * nf + 12 * t + v;
+      int32_t* d0t = &m->dof0[(size_t)t * 20];
+      for (int k = 0; k < 4; ++k) d0t[k] = m->tets[(size_t)t * 4 + k];
+      for (int k = 0; k < 6; ++k)
+        for (int v = 0; v < 2; ++v) d0t[4 + 2 * k + v] = nn + 2 * tet_edge[(size_t)t * 6 + k] + v;
+      for (int k = 0; k < 4; ++k) d0t[16 + k] = nn + 2 * ne + tet_face[(size_t)t * 4 + k];
+    }
+    m->pec1.assign(m->n1, 0);
+    for (int32_t e2 = 0; e2 < ne; ++e2)
+      if (pedge[e2])
+        for (int v = 0; v < 3; ++v) m->pec1[3 * e2 + v] = 1;
+    for (int32_t f = 0; f < nf; ++f)
+      if (bface[f] && !fimp[f])
+        for (int v = 0; v < 6; ++v) m->pec1[3 * ne + 6 * f + v] = 1;
+    m->bnd0.assign(m->n0, 0);
+    for (int32_t v = 0; v < nn; ++v) m->bnd0[v] = bnode[v];
+    for (int32_t e2 = 0; e2 < ne; ++e2) m->bnd0[nn + 2 * e2] = m->bnd0[nn + 2 * e2 + 1] = bedge[e2];
+    for (int32_t f = 0; f < nf; ++f) m->bnd0[nn + 2 * ne + f] = bface[f];
   } else {
     if ((int64_t)2 * ne + 2 * (int64_t)nf > INT32_MAX || (int64_t)3 * nf + 3 * (int64_t)nt > INT32_MAX) {
       *err = "mesh too large for 32-bit DOF ids";

@@ -1,0 +1,142 @@
+"""GPU parity at order 3 (the Appendix's p = 3 bases): the library through its
+C ABI against the oracle, with the tolerances of the order-1/2 parity tests.
+
+* assembled operators M, K, M2, C, D, L: rel 1e-12 (1e-11 for the products
+  with the larger cancellation);
+* field evaluation and one strict step: bit-exact positions, velocities,
+  owning tets, crossing counts and hashes (one rounding per operation on both
+  sides, the multipliers evaluated factor by factor in the same order);
+* the contracted FP64 kernel: rel 1e-12;
+* Delta g and rho: rel 1e-12 (atomics reorder the sums);
+* the field solve: ||A e - rhs|| <= 10 cg_rtol ||rhs|| on the oracle's system;
+* continuity to 1e-12 relative every step on the device.
+"""
+
+import copy
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import particles as opart, sim as osim
+from gpu_helpers import build_lib, random_state, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    return build_lib()
+
+
+@pytest.fixture(scope="module")
+def cfg():
+    return workloads.make_config(0, n_particles=4_099)  # ragged: not a multiple of the block
+
+
+@pytest.fixture(scope="module")
+def o3(cfg):
+    o = osim.Sim(cfg["xyz"], cfg["tets"], 3, cfg["q"], cfg["m"], cfg["weight"], cfg["B0"], cfg["rho_ion"])
+    o.set_particles(cfg["x"], cfg["v"], cfg["tet"])
+    return o
+
+
+def _gpu(cfg, **kw):
+    from paper_2111_12411_gb300 import Simulation
+    return Simulation(cfg["xyz"], cfg["tets"], 3, cfg["q"], cfg["m"], cfg["weight"], cfg["x"], cfg["v"],
+                      cfg["tet"], B0=cfg["B0"], rho_ion=cfg["rho_ion"], **kw)
+
+
+def test_sizes_and_operators_order3(cfg, o3):
+    g = _gpu(cfg)
+    t = o3.topo
+    i = g.info
+    assert (i.n0, i.n1, i.n2) == (t.n0, t.n1, t.n2)
+    assert (i.nl0, i.nl1, i.nl2) == (20, 45, 36)
+    rng = np.random.default_rng(0)
+    fr = t.free1.astype(float)
+    in0 = t.interior0.astype(float)
+    x1, x2, x0 = rng.normal(size=t.n1), rng.normal(size=t.n2), rng.normal(size=t.n0)
+    assert rel(g.apply("M1", x1), fr * (o3.M @ (fr * x1))) < 1e-12
+    assert rel(g.apply("K", x1), fr * (o3.K @ (fr * x1))) < 1e-11
+    assert rel(g.apply("M2", x2), o3.M2 @ x2) < 1e-12
+    assert rel(g.apply("C", x1), o3.C @ (fr * x1)) < 1e-13
+    assert rel(g.apply("D", x0), o3.D @ (in0 * x0)) < 1e-13
+    assert rel(g.apply("DT", x1), o3.D.T @ x1) < 1e-13
+    L = (o3.D.T @ o3.M @ o3.D).tocsr()
+    assert rel(g.apply("L", x0), in0 * (L @ (in0 * x0))) < 1e-11
+    g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64_strict", "fp64"])
+def test_eval_fields_order3(cfg, o3, precision):
+    g = _gpu(cfg, precision=precision, es_init=False)
+    e, b = random_state(o3.topo, np.random.default_rng(1))
+    g.set("E", e)
+    g.set("B", b)
+    x, tet = cfg["x"][:2000], cfg["tet"][:2000]
+    Eg, Bg = g.eval_fields(x, tet)
+    Eo, Bo = opart.gather(o3.topo, o3.g, o3.c, e, b, o3.B0, x, tet)
+    if precision == "fp64_strict":
+        assert np.array_equal(Eg, Eo) and np.array_equal(Bg, Bo)
+    else:
+        assert rel(Eg, Eo) < 1e-13 and rel(Bg, Bo) < 1e-13
+    g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64_strict", "fp64"])
+def test_one_step_parity_order3(cfg, o3, precision):
+    o = copy.deepcopy(o3)
+    g = _gpu(cfg, precision=precision, es_init=False)
+    e, b = random_state(o.topo, np.random.default_rng(2))
+    o.e, o.e_prev, o.b = e.copy(), e.copy(), b.copy()
+    g.set("E", e)
+    g.set("E_PREV", e)
+    g.set("B", b)
+    dt = cfg["dt"]
+    w = o.step(dt)
+    g.step(dt)
+    xg, vg, tg = g.get("X"), g.get("V"), g.get("TET")
+    if precision == "fp64_strict":
+        assert np.array_equal(xg, w["x"]) and np.array_equal(vg, w["v"])
+        assert np.array_equal(tg, w["tet"])
+        assert np.array_equal(g.get("NCROSS"), w["ncross"])
+        assert np.array_equal(g.get("HASH"), w["hash"])
+    else:
+        assert rel(xg, w["x"]) < 1e-12 and rel(vg, w["v"]) < 1e-12
+    assert w["ncross"].mean() > 0.5
+    assert rel(g.get("DG"), w["dg"]) < 1e-12
+    assert rel(g.get("RHO"), o.rho) < 1e-12
+    from oracle import fields as ofields
+    A = ofields.system_matrix(o.M, o.K, dt, "trapezoid")
+    eg = g.get("E")
+    fr = o.topo.free1
+    res = (A @ eg - w["rhs"])[fr]
+    assert np.linalg.norm(res) <= 10 * 1e-12 * np.linalg.norm(w["rhs"][fr])
+    assert np.all(eg[~fr] == 0.0)
+    assert rel(g.get("B"), o.b) < 1e-6
+    g.close()
+
+
+def test_continuity_and_gauss_order3(cfg):
+    """Continuity to 1e-12 every step.  Gauss's law drifts only by D^T applied
+    to the field solve's residual (cg_rtol 1e-12 relative to the right-hand
+    side); the cubic W0 gradients are about three times those of the linear
+    ones per unit length and the right-hand side is far larger than rho, so
+    the bound per step is 1e-9 relative to ||rho|| here (1e-10 at orders 1
+    and 2)."""
+    g = _gpu(cfg, diagnostics=True)
+    for n in range(4):
+        g.step(cfg["dt"])
+        d = g.diag()
+        assert d["continuity_abs"] <= 1e-12 * d["continuity_ref"]
+        assert d["gauss_abs"] <= 1e-9 * (n + 1) * d["gauss_ref"]
+        assert d["cg_residual"] <= 1e-12
+        assert d["crossings"] > 0
+    g.close()
+
+
+def test_order3_rejects_ab4(cfg):
+    from paper_2111_12411_gb300 import FemPICError
+    with pytest.raises(FemPICError):
+        _gpu(cfg, push="ab4")

@@ -82,7 +82,12 @@ def test_host_validation_errors(native):
         native.femPIC_create(flat, tets, 1, -1.6e-19, 9.1e-31, 1.0, x, v, tet)
     assert ei.value.code == native.FEMPIC_ERR_MESH
     with pytest.raises(native.FemPICError) as ei:
-        native.femPIC_create(xyz, tets, 3, -1.6e-19, 9.1e-31, 1.0, x, v, tet)
+        native.femPIC_create(xyz, tets, 4, -1.6e-19, 9.1e-31, 1.0, x, v, tet)
+    assert ei.value.code == native.FEMPIC_ERR_ARG
+    o = native.default_opts()
+    o.push = native.PUSH["ab4"]
+    with pytest.raises(native.FemPICError) as ei:  # the Adams-Bashforth push stops at order 2
+        native.femPIC_create(xyz, tets, 3, -1.6e-19, 9.1e-31, 1.0, x, v, tet, o)
     assert ei.value.code == native.FEMPIC_ERR_ARG
     wrong = (tet + 1) % len(tets)
     with pytest.raises(native.FemPICError) as ei:
