@@ -36,6 +36,11 @@ WORKLOAD = ("drift tube R=1cm L=10cm, polar Kuhn mesh 24x12x80 (132480 tets), p=
             "1e6 electrons, v_z=3e7 m/s, B0=1 T, dt=33.3 ps, FP64")
 
 
+def workload_name(order, n_particles):
+    return WORKLOAD.replace("p=2", f"p={order}").replace("1e6 electrons", f"{n_particles:.0e} electrons"
+                                                         .replace("e+0", "e"))
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -72,7 +77,7 @@ def particle_bytes_per_step(order, n_particles, occupied_tets, crossings_per_par
     index maps, the read-modify-write of its W1 current DOFs and W0 charge
     DOFs, amortised over the particles per tet and multiplied by the tets
     visited (1 + crossings)."""
-    n1, n2, n0 = (6, 4, 4) if order == 1 else (20, 15, 10)
+    n1, n2, n0 = {1: (6, 4, 4), 2: (20, 15, 10), 3: (45, 36, 20)}[order]
     per_tet = 128 + 8 * (n1 + n2) + 4 * (n1 + n2 + n0) + 16 * n1 + 16 * n0
     ppc = n_particles / max(1, occupied_tets)
     return 104.0 + per_tet / ppc * (1.0 + crossings_per_particle)
@@ -191,8 +196,10 @@ def run_native(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
     cfg = workloads.make_config(1, n_particles=args.particles)
+    cfg["order"] = args.order
     sim = Simulation.from_config(cfg, precision=args.precision, device=local_rank,
-                                 stream=stream.cuda_stream, cg_rtol=args.cg_rtol, push=args.push)
+                                 stream=stream.cuda_stream, cg_rtol=args.cg_rtol, push=args.push,
+                                 cg_max_it=args.cg_max_it)
     info = sim.info
     npart = sim.n_particles
     dt = cfg["dt"]
@@ -334,7 +341,8 @@ def run_native(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision != "mixed" else "f64+f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": args.precision, "push": args.push,
+            "config": {"workload": workload_name(info.order, npart), "precision": args.precision,
+                       "push": args.push,
                        "l2": "flushed between steps "
                        "(256 MiB write)", "parallelism": "replicas" if world > 1 else "single GPU",
                        "n_particles": npart, "n_tets": info.n_tets, "n1": info.n1, "n2": info.n2,
@@ -575,6 +583,68 @@ def run_push(args, local_rank):
     print(json.dumps(out), flush=True)
 
 
+def run_project(args, local_rank):
+    """The divergence-free projection of an impressed flux density (Section
+    III-C, eq. conB) on the drift-tube mesh: a quadrupole lens field
+    B = grad phi, phi = (G / k^2) sin(k x) sinh(k y) (harmonic, so B is
+    divergence- and curl-free; G x y near the axis), G = 1 T/m,
+    k = pi / 2 cm (far from polynomial across the 1 cm radius), projected with
+    and without Gauss's magnetic law.  Per call: host time of the W3
+    operators, device time of the load and the nested CG solve, and the inner
+    CG iteration's algorithmic bytes against its device-timed duration (HBM
+    roofline)."""
+    import torch
+    import workloads
+    from paper_2111_12411_gb300 import Simulation
+
+    torch.cuda.set_device(local_rank)
+    cfg = workloads.make_config(1, n_particles=1000)
+    cfg["order"] = args.order
+    G, k = 1.0, math.pi / 0.02
+
+    def lens(x):
+        return np.stack([G / k * np.cos(k * x[:, 0]) * np.sinh(k * x[:, 1]),
+                         G / k * np.sin(k * x[:, 0]) * np.cosh(k * x[:, 1]), 0.0 * x[:, 2]], axis=1)
+
+    sim = Simulation.from_config(cfg, device=local_rank, es_init=False, cg_rtol=args.cg_rtol)
+    info = sim.info
+    pts = sim.impressed_points()
+    Bv = lens(pts)
+    peak, peak_src = measured_peaks()
+    out = {"metric": "impressed-field projection (eq. conB): device ms per call and inner-CG HBM roofline",
+           "unit": "ms", "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+           "data": "synthetic",
+           "config": {"workload": "drift tube R=1cm L=10cm, polar Kuhn mesh 24x12x80 (132480 tets), "
+                                  f"p={args.order}, quadrupole lens B = grad((G/k^2) sin(kx) sinh(ky)), "
+                                  "G = 1 T/m, k = pi/2cm", "n2": info.n2, "n_points": len(pts),
+                      "cg_rtol": args.cg_rtol}}
+    for name, con in (("galerkin", False), ("constrained", True)):
+        for _ in range(max(1, args.warmup // 3)):
+            sim.set_impressed_B(Bv, constrained=con)
+        runs = []
+        for _ in range(args.steps):
+            runs.append(sim.set_impressed_B(Bv, constrained=con))
+        inner_it = sum(r["inner_iterations"] for r in runs)
+        inner_ms = sum(r["inner_ms"] for r in runs)
+        gbs = runs[0]["bytes_per_inner_iteration"] * inner_it / (inner_ms * 1e-3) / 1e9 if inner_ms > 0 else None
+        out[name] = {"device_ms": statistics.median(r["device_ms"] for r in runs),
+                     "host_ms": statistics.median(r["host_ms"] for r in runs),
+                     "outer_iterations": runs[-1]["outer_iterations"],
+                     "inner_iterations": runs[-1]["inner_iterations"],
+                     "div_residual": runs[-1]["div_residual"],
+                     "inner_iteration_us": 1e3 * inner_ms / max(1, inner_it),
+                     "roofline_inner_iteration": {
+                         "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak if gbs else None, "traffic": None,
+                         "peak_source": peak_src,
+                         "bytes_per_iteration": runs[0]["bytes_per_inner_iteration"]}}
+    bi = sim.get("B_IMPRESSED")
+    out["value"] = out["constrained"]["device_ms"]
+    out["b_impressed_norm"] = float(np.linalg.norm(bi))
+    print(json.dumps(out), flush=True)
+    sim.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -591,8 +661,11 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=50_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("tube", "batched", "serving", "precision", "push"),
+    ap.add_argument("--workload", choices=("tube", "batched", "serving", "precision", "push", "project"),
                     default="tube")
+    ap.add_argument("--order", type=int, default=2, choices=(1, 2, 3),
+                    help="basis order p of the tube and project workloads")
+    ap.add_argument("--cg-max-it", type=int, default=2000)
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--rate", type=float, default=2.0)
@@ -622,6 +695,8 @@ def main():
         run_precision(args, local_rank)
     elif args.workload == "push":
         run_push(args, local_rank)
+    elif args.workload == "project":
+        run_project(args, local_rank)
     else:
         run_native(args, rank, world, local_rank)
     if world > 1:

@@ -113,7 +113,8 @@ enum {
 enum {
   FEMPIC_E = 0,        /* double[N1]  electric field DOFs e^n                   */
   FEMPIC_B = 1,        /* double[N2]  magnetic flux DOFs b^n (self field only;
-                          the uniform impressed B0 is added at the gather)      */
+                          the uniform B0 and FEMPIC_B_IMPRESSED are added at
+                          the gather)                                           */
   FEMPIC_DG = 2,       /* double[N1]  g^n - g^{n-1} deposited by the last step  */
   FEMPIC_RHO = 3,      /* double[N0]  rho_k = q w sum_p W0_k(x_p)               */
   FEMPIC_X = 4,        /* double[3*Np] positions, particle-id order, xyz interleaved */
@@ -128,7 +129,10 @@ enum {
   FEMPIC_DG_PREV = 10, /* double[N1]  Delta g of the step before (wave scheme)   */
   FEMPIC_DIAG = 11,    /* femPIC_diag (get only)                                */
   FEMPIC_PHI = 12,     /* double[N0]  potential of the electrostatic start (get) */
-  FEMPIC_SPECIES = 13  /* int32[Np]   species index of each particle (get)      */
+  FEMPIC_SPECIES = 13, /* int32[Np]   species index of each particle (get)      */
+  FEMPIC_B_IMPRESSED = 14 /* double[N2] W2 coefficients of an impressed flux
+                          density (zeros when none is set): added to b wherever
+                          the particles sample B, absent from the field update */
 };
 
 /* ---- operators for femPIC_apply ----------------------------------------- */
@@ -311,6 +315,61 @@ int femPIC_eval_fields_noalloc(FemPIC* h, int64_t n, const double* x_host, const
                                double* E_host, double* B_host);
 
 int femPIC_get_info(const FemPIC* h, femPIC_info* info);
+
+/* ---- impressed magnetic flux density (Section III-C, eq. conB) ------------
+ * A static, externally produced B^i (e.g. magnets) enters the particle push
+ * through its W2 coefficients b^i: the particles sample B0 + (b + b^i) . W2
+ * while the field update sees b alone.  The coefficients come from a
+ * projection of B^i given at quadrature points:
+ *
+ *   femPIC_impressed_points: the points at which the caller evaluates B^i.
+ *     Per tet (input order) the conical-product rule of p + 3 Gauss-Legendre
+ *     points per direction on the tet with its vertices sorted by node id,
+ *     (p + 3)^3 points per tet, exact for polynomials of degree 2p + 3.  With
+ *     xyz_host NULL only *n_points is written; otherwise *n_points must equal
+ *     that count (FEMPIC_ERR_SIZE if not) and xyz_host [3 * n_points]
+ *     receives the points, xyz interleaved, tet-major.
+ *
+ *   femPIC_set_impressed_B: B_host [3 * n_points] holds B^i at those points
+ *     (T).  The load f_i = <W2_i, B^i> is integrated with the same rule.
+ *     constrained = 0: the Galerkin projection [*mu^-1] b^i = f / mu0.
+ *     constrained = 1: eq. conB, the same energy minimised under Gauss's
+ *     magnetic law imposed against the order-p volume functions W3 (products
+ *     P^_a(l0) P^_b(l1) P^_c(l2) P^_d(l3), a..d >= 1, a+b+c+d = p+3), which
+ *     span the degree p-1 polynomials where div W2 lives, so div b^i = 0
+ *     exactly up to the solver tolerance: the saddle-point system
+ *     [[*mu^-1], [~div]^T; [~div], 0] is solved on the device by CG on its
+ *     Schur complement (preconditioned by per-tet inverses) around inner CG
+ *     solves of [*mu^-1] (block-Jacobi by face and interior DOF groups);
+ *     tolerances: ||[~div] b|| reduced by opts.cg_rtol from the Galerkin
+ *     projection's, but not below 100 eps || |[~div]| |b_Galerkin| || (the
+ *     rounding floor of its terms; no outer iteration if the Galerkin
+ *     projection is already there: a field the space reproduces), inner
+ *     0.01 cg_rtol.
+ *     B_host NULL (n_points 0) clears b^i.  The result replaces any earlier
+ *     b^i (readable and settable as FEMPIC_B_IMPRESSED).  stats_out
+ *     (nullable) receives the iteration counts, timings and the relative
+ *     constraint residual.  Synchronous; allocates its work
+ *     space for the call (a few times N2 doubles, the point values and the
+ *     W3 operators) and frees it before returning.  Errors: FEMPIC_ERR_SIZE
+ *     (point count), FEMPIC_ERR_CG (a solve hit its cap), FEMPIC_ERR_CUDA. */
+typedef struct {
+  int32_t outer_iterations; /* CG iterations on the Schur complement (0 if unconstrained) */
+  int32_t inner_iterations; /* CG iterations of all [*mu^-1] solves                     */
+  double div_residual;      /* ||[~div] b^i|| / || |[~div]| |b^i| || (entrywise absolute
+                               values: the size of the terms whose sum is [~div] b^i)  */
+  double host_ms;           /* host time of the W3 operators and preconditioners        */
+  double device_ms;         /* device time from the load to the last kernel (CUDA events,
+                               idle gaps at the host's convergence reads included)      */
+  double inner_ms;          /* device time of the inner iterations alone (events around
+                               each chunk of iterations)                                */
+  double bytes_per_inner_iteration; /* algorithmic: 12 (nnz(M2) + nnz(Bm)) + 8 (N2 + 1)
+                               + 104 N2 (CSR values and columns, row pointers, and the
+                               products' and updates' vector passes)                    */
+} femPIC_projection;
+int femPIC_impressed_points(FemPIC* h, double* xyz_host, int64_t* n_points);
+int femPIC_set_impressed_B(FemPIC* h, const double* B_host, int64_t n_points, int32_t constrained,
+                           femPIC_projection* stats_out);
 
 /* Device time of the work of the last femPIC_step / femPIC_sync, measured with
  * CUDA events on the handle's stream, summed over its steps.  Fills up to n

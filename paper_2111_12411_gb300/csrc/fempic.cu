@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,6 +25,7 @@
 #include "particle_fast.cuh"
 #include "batch.cuh"
 #include "particle_ab4.cuh"
+#include "project.cuh"
 
 using namespace fempic;
 using namespace fempic::dev;
@@ -137,7 +139,16 @@ struct FemPIC {
   int32_t* d_cg_iters_acc = nullptr;  // sum of CG iterations since the last sync
   int launches = 0;
   int pending_steps = 0;
+  // impressed magnetic flux density (Section III-C): W2 coefficients bimp and
+  // the sum btot = b + bimp the particles sample; null until one is set.  The
+  // mesh as given (sorted tets) is kept for the projection's quadrature points.
+  double *bimp = nullptr, *btot = nullptr;
+  std::vector<double> hxyz;
+  std::vector<int32_t> htets;
 };
+
+// the flux the particles see (self field, plus the impressed one if set)
+inline const double* b_gather(const FemPIC* h) { return h->bimp ? h->btot : h->b; }
 
 static_assert(kMaxSpecies == FEMPIC_MAX_SPECIES, "species table size");
 
@@ -535,7 +546,7 @@ int launch_particles(FemPIC* h, double dt) {
   a.dof1 = h->dof1;
   a.dof2 = h->dof2;
   a.e = h->e;
-  a.b = h->b;
+  a.b = b_gather(h);
   a.dg = h->dg;
   a.rho = h->rho;
   for (int k = 0; k < 3; ++k) a.B0[k] = h->opts.B0[k];
@@ -623,10 +634,10 @@ void launch_eval_fields_p(FemPIC* h, int grid, bool strict, int64_t n, const dou
                           double* B) {
   const double* B0 = h->opts.B0;
   if (strict)
-    k_eval_fields<P, Strict><<<grid, 128, 0, h->stream>>>(n, x, tet, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0],
+    k_eval_fields<P, Strict><<<grid, 128, 0, h->stream>>>(n, x, tet, h->geom, h->dof1, h->dof2, h->e, b_gather(h), B0[0],
                                                           B0[1], B0[2], E, B);
   else
-    k_eval_fields<P, Fast><<<grid, 128, 0, h->stream>>>(n, x, tet, h->geom, h->dof1, h->dof2, h->e, h->b, B0[0], B0[1],
+    k_eval_fields<P, Fast><<<grid, 128, 0, h->stream>>>(n, x, tet, h->geom, h->dof1, h->dof2, h->e, b_gather(h), B0[0], B0[1],
                                                         B0[2], E, B);
 }
 
@@ -670,6 +681,11 @@ int field_update(FemPIC* h, double dt, cudaEvent_t ev_pcg0, cudaEvent_t ev_pcg1)
   k_bupdate<4><<<gridc, 256, 0, h->stream>>>(h->C.view(), h->e_new, h->e, 0.5 * dt, h->b);
   h->launches++;
   CK(cudaGetLastError());
+  if (h->bimp) {
+    k_lincomb<<<grid_for(h->n2, 256, h->num_sms * 8), 256, 0, h->stream>>>(h->n2, h->b, h->bimp, 1.0, 1.0, h->btot);
+    h->launches++;
+    CK(cudaGetLastError());
+  }
   return FEMPIC_OK;
 }
 
@@ -787,6 +803,7 @@ size_t what_bytes(const FemPIC* h, int32_t what) {
     case FEMPIC_DG_PREV:
       return sizeof(double) * (size_t)h->n1;
     case FEMPIC_B:
+    case FEMPIC_B_IMPRESSED:
       return sizeof(double) * (size_t)h->n2;
     case FEMPIC_RHO:
     case FEMPIC_PHI:
@@ -826,6 +843,25 @@ double* field_ptr(FemPIC* h, int32_t what) {
     default:
       return nullptr;
   }
+}
+
+// allocate the impressed-field coefficients (zero) and the sampled sum
+int ensure_impressed(FemPIC* h) {
+  if (h->bimp) return FEMPIC_OK;
+  int rc = dalloc(h, &h->bimp, h->n2);
+  if (!rc) rc = dalloc(h, &h->btot, h->n2);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(h->bimp, 0, sizeof(double) * h->n2, h->stream));
+  return FEMPIC_OK;
+}
+
+// btot = b + bimp (stream-ordered)
+int refresh_btot(FemPIC* h) {
+  if (!h->bimp) return FEMPIC_OK;
+  k_lincomb<<<grid_for(h->n2, 256, h->num_sms * 8), 256, 0, h->stream>>>(h->n2, h->b, h->bimp, 1.0, 1.0, h->btot);
+  h->launches++;
+  CK(cudaGetLastError());
+  return FEMPIC_OK;
 }
 
 // move a quantity between the handle and a buffer (host or device)
@@ -890,11 +926,34 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
       memcpy(buf, &d, sizeof(d));
     return FEMPIC_OK;
   }
+  if (what == FEMPIC_B_IMPRESSED) {
+    if (!to_handle && !h->bimp) {  // none set: zeros
+      if (buf_on_device)
+        CK(cudaMemset(buf, 0, need));
+      else
+        memset(buf, 0, need);
+      return FEMPIC_OK;
+    }
+    if (to_handle) {
+      int rc = ensure_impressed(h);
+      if (rc) return rc;
+      CK(cudaMemcpyAsync(h->bimp, buf, need, up, h->stream));
+      if ((rc = refresh_btot(h))) return rc;
+    } else {
+      CK(cudaMemcpyAsync(buf, h->bimp, need, down, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return FEMPIC_OK;
+  }
   if (double* f = field_ptr(h, what)) {
     if (to_handle)
       CK(cudaMemcpyAsync(f, buf, need, up, h->stream));
     else
       CK(cudaMemcpyAsync(buf, f, need, down, h->stream));
+    if (to_handle && what == FEMPIC_B) {
+      int rc = refresh_btot(h);
+      if (rc) return rc;
+    }
     CK(cudaStreamSynchronize(h->stream));
     return FEMPIC_OK;
   }
@@ -995,6 +1054,8 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
     }
   }
   h->order = order;
+  h->hxyz.assign(mesh->xyz_host, mesh->xyz_host + 3 * (size_t)mesh->n_nodes);
+  h->htets = hm.tets;
   h->nl0 = hm.nl0;
   h->nl1 = hm.nl1;
   h->nl2 = hm.nl2;
@@ -1829,6 +1890,10 @@ int femPIC_batch_create(FemPIC* const* members, int32_t n, FemPICBatch** out) {
       b->err = "batched members must be of order 1 or 2";
       return FEMPIC_ERR_ARG;
     }
+    if (h->bimp) {
+      b->err = "batched members cannot carry an impressed flux density";
+      return FEMPIC_ERR_ARG;
+    }
     if (h->n_tets > 1024 * 1024) {
       b->err = "batched members are limited to 1048576 tets";
       return FEMPIC_ERR_ARG;
@@ -2101,3 +2166,305 @@ extern "C" int femPIC_measure_alu(int32_t device, int32_t kind, double* ops_per_
   cudaFree(buf);
   return rc;
 }
+
+// ---- impressed magnetic flux density (Section III-C, eq. conB) -----------
+namespace {
+
+// frees the allocations made after it (temporaries of one call), after the
+// stream has drained
+struct ScratchScope {
+  FemPIC* h;
+  size_t mark, bytes;
+  explicit ScratchScope(FemPIC* hh) : h(hh), mark(hh->allocs.size()), bytes(hh->bytes) {}
+  ~ScratchScope() {
+    cudaStreamSynchronize(h->stream);
+    for (size_t i = mark; i < h->allocs.size(); ++i) cudaFree(h->allocs[i]);
+    h->allocs.resize(mark);
+    h->bytes = bytes;
+  }
+};
+
+constexpr int kProjChunk = 16;
+
+// four timing events, destroyed with the scope
+struct ScopedEvents {
+  cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+  int create(FemPIC* h) {
+    for (auto& x : e) CK(cudaEventCreate(&x));
+    return FEMPIC_OK;
+  }
+  ~ScopedEvents() {
+    for (auto& x : e)
+      if (x) cudaEventDestroy(x);
+  }
+};  // CG iterations launched between convergence reads
+
+struct ProjBuffers {
+  double *r, *z, *p, *q, *sc, *part;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around each chunk of inner iterations
+  double inner_ms = 0.0;
+};
+
+// x = A^-1 rhs by CG from x = 0, preconditioned by the product with P; every
+// scalar on the device, the host reading the flag every kProjChunk iterations
+int proj_pcg(FemPIC* h, const CsrView& A, const CsrView& P, const double* rhs, double* x, int32_t n, double rtol,
+             int32_t max_it, ProjBuffers& w, int32_t* iters) {
+  cudaStream_t st = h->stream;
+  const int gv = grid_for(n, 256, h->num_sms * 8);
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+  CK(cudaMemcpyAsync(w.r, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  k_spmv_dot<4, true><<<kRedGrid, kRedThreads, 0, st>>>(P, w.r, w.z, w.r, w.part, nullptr);
+  k_cg_start<<<1, kRedThreads, 0, st>>>(w.sc, w.part, rtol * rtol);
+  CK(cudaMemcpyAsync(w.p, w.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  h->launches += 2;
+  CK(cudaGetLastError());
+  double hs[kCgN];
+  bool timed = false;
+  for (;;) {
+    CK(cudaMemcpyAsync(hs, w.sc, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (timed) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, w.ev0, w.ev1));
+      w.inner_ms += ms;
+    }
+    if (hs[kCgDone] != 0.0) break;
+    CK(cudaEventRecord(w.ev0, st));
+    for (int k = 0; k < kProjChunk; ++k) {
+      k_spmv_dot<8, false><<<kRedGrid, kRedThreads, 0, st>>>(A, w.p, w.q, w.p, w.part, w.sc);
+      k_cg_alpha<<<1, kRedThreads, 0, st>>>(w.sc, w.part);
+      k_cg_xr<<<gv, 256, 0, st>>>(n, w.sc, w.p, w.q, x, w.r);
+      k_spmv_dot<4, true><<<kRedGrid, kRedThreads, 0, st>>>(P, w.r, w.z, w.r, w.part, w.sc);
+      k_cg_beta<<<1, kRedThreads, 0, st>>>(w.sc, w.part, max_it);
+      k_cg_p<<<gv, 256, 0, st>>>(n, w.sc, w.z, w.p);
+    }
+    CK(cudaEventRecord(w.ev1, st));
+    timed = true;
+    h->launches += 6 * kProjChunk;
+    CK(cudaGetLastError());
+  }
+  *iters = (int32_t)hs[kCgIt];
+  if (hs[kCgDone] == 2.0) {
+    h->err = "projection CG: the operator is not positive definite on the search direction";
+    return FEMPIC_ERR_CG;
+  }
+  if (hs[kCgDone] == 3.0) {
+    h->err = "projection CG reached its iteration cap before the tolerance";
+    return FEMPIC_ERR_CG;
+  }
+  return FEMPIC_OK;
+}
+
+double host_norm(const std::vector<double>& v) {
+  double s = 0.0;
+  for (double x : v) s += x * x;
+  return std::sqrt(s);
+}
+
+// || |A| |x| ||: the size of the terms of A x, the scale rounding errors of A x live on
+double abs_product_norm(const HostCSR& A, const std::vector<double>& x) {
+  double s = 0.0;
+  for (int32_t r = 0; r < A.n_rows; ++r) {
+    double t = 0.0;
+    for (int32_t k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k) t += std::fabs(A.val[k]) * std::fabs(x[A.col[k]]);
+    s += t * t;
+  }
+  return std::sqrt(s);
+}
+
+int project_impressed(FemPIC* h, const double* B_host, int64_t n_points, int32_t constrained,
+                      femPIC_projection* stats) {
+  CK(cudaSetDevice(h->device));
+  CK(cudaStreamSynchronize(h->stream));
+  // host structures: M2 and the W2 numbering come back from the device
+  HostCSR M2;
+  M2.n_rows = h->M2.n_rows;
+  M2.n_cols = h->M2.n_cols;
+  M2.rowptr.resize((size_t)M2.n_rows + 1);
+  M2.col.resize((size_t)h->M2.nnz);
+  M2.val.resize((size_t)h->M2.nnz);
+  std::vector<int32_t> dof2((size_t)h->n_tets * h->nl2);
+  CK(cudaMemcpy(M2.rowptr.data(), h->M2.rp, sizeof(int32_t) * M2.rowptr.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(M2.col.data(), h->M2.ci, sizeof(int32_t) * M2.col.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(M2.val.data(), h->M2.v, sizeof(double) * M2.val.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(dof2.data(), h->dof2, sizeof(int32_t) * dof2.size(), cudaMemcpyDeviceToHost));
+  ProjModel P;
+  const auto th0 = std::chrono::steady_clock::now();
+  std::string err = build_projection(h->order, h->n_tets, h->n_faces, h->n2, h->hxyz.data(), h->htets.data(),
+                                     dof2.data(), M2, &P);
+  const double host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count();
+  if (!err.empty()) {
+    h->err = err;
+    return FEMPIC_ERR_MESH;
+  }
+  const int64_t need = (int64_t)h->n_tets * P.nq;
+  if (n_points != need) {
+    h->err = "impressed B: " + std::to_string(n_points) + " points given, the rule has " + std::to_string(need);
+    return FEMPIC_ERR_SIZE;
+  }
+  int rc = ensure_impressed(h);
+  if (rc) return rc;
+  double* b = h->bimp;
+  ScratchScope scope(h);
+  const int32_t n2 = h->n2, N3 = P.Dv.n_rows, nl2 = h->nl2;
+  DevCSR Dv, DvT, Bm, Bs, Asm;
+  double *qlam, *qw, *vol6, *Bq, *fl, *f, *t2, *wv, *r3, *z3, *p3, *q3, *sc3;
+  ProjBuffers w;
+  if ((rc = upload_csr(h, &Dv, P.Dv)) || (rc = upload_csr(h, &DvT, P.DvT)) || (rc = upload_csr(h, &Bm, P.Bm)) ||
+      (rc = upload_csr(h, &Bs, P.Bs)) || (rc = upload_csr(h, &Asm, P.Asm)) || (rc = upload(h, &qlam, P.qlam)) ||
+      (rc = upload(h, &qw, P.qw)) || (rc = upload(h, &vol6, P.vol6)) || (rc = dalloc(h, &Bq, 3 * (size_t)need)) ||
+      (rc = dalloc(h, &fl, (size_t)h->n_tets * nl2)) || (rc = dalloc(h, &f, n2)) || (rc = dalloc(h, &t2, n2)) ||
+      (rc = dalloc(h, &wv, n2)) || (rc = dalloc(h, &w.r, n2)) || (rc = dalloc(h, &w.z, n2)) ||
+      (rc = dalloc(h, &w.p, n2)) || (rc = dalloc(h, &w.q, n2)) || (rc = dalloc(h, &w.sc, kCgN)) ||
+      (rc = dalloc(h, &w.part, 2 * kRedGrid)) || (rc = dalloc(h, &r3, std::max(N3, 1))) ||
+      (rc = dalloc(h, &z3, std::max(N3, 1))) || (rc = dalloc(h, &p3, std::max(N3, 1))) ||
+      (rc = dalloc(h, &q3, std::max(N3, 1))) || (rc = dalloc(h, &sc3, kCgN)))
+    return rc;
+  cudaStream_t st = h->stream;
+  ScopedEvents evs;
+  if ((rc = evs.create(h))) return rc;
+  w.ev0 = evs.e[2];
+  w.ev1 = evs.e[3];
+  CK(cudaMemcpyAsync(Bq, B_host, sizeof(double) * 3 * (size_t)need, cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(evs.e[0], st));
+  // load f = <W2, B> / mu0, per tet then assembled
+  const int gt = grid_for(h->n_tets, 128, 1 << 30);
+  const double inv_mu0 = 1.0 / kMu0;
+  if (h->order == 1)
+    k_w2_load<1><<<gt, 128, 0, st>>>(h->n_tets, P.nq, qlam, qw, vol6, inv_mu0, h->geom, Bq, fl);
+  else if (h->order == 2)
+    k_w2_load<2><<<gt, 128, 0, st>>>(h->n_tets, P.nq, qlam, qw, vol6, inv_mu0, h->geom, Bq, fl);
+  else
+    k_w2_load<3><<<gt, 128, 0, st>>>(h->n_tets, P.nq, qlam, qw, vol6, inv_mu0, h->geom, Bq, fl);
+  k_spmv<4><<<grid_for((int64_t)n2 * 4, 256, h->num_sms * 16), 256, 0, st>>>(Asm.view(), fl, f, 1.0, 0.0);
+  h->launches += 2;
+  CK(cudaGetLastError());
+  // Galerkin projection b_G = M2^-1 f
+  const double rtol_in = 1e-2 * h->opts.cg_rtol, rtol_out = h->opts.cg_rtol;
+  const int32_t max_in = std::max(1000, 4 * h->opts.cg_max_it), max_out = std::max(1000, 10 * h->opts.cg_max_it);
+  femPIC_projection S;
+  memset(&S, 0, sizeof(S));
+  S.host_ms = host_ms;
+  S.bytes_per_inner_iteration = 12.0 * ((double)h->M2.nnz + (double)Bm.nnz) + 8.0 * (n2 + 1.0) + 104.0 * n2;
+  int32_t it = 0;
+  if ((rc = proj_pcg(h, h->M2.view(), Bm.view(), f, b, n2, rtol_in, max_in, w, &it))) return rc;
+  S.inner_iterations += it;
+  // the constraint residual Dv b_G against the size of its terms || |Dv| |b_G| ||:
+  // a Galerkin projection that is divergence free up to rounding needs no correction
+  std::vector<double> hr((size_t)N3), hb((size_t)n2);
+  k_spmv<8><<<grid_for((int64_t)N3 * 8, 256, h->num_sms * 16), 256, 0, st>>>(Dv.view(), b, r3, 1.0, 0.0);
+  h->launches++;
+  CK(cudaMemcpyAsync(hr.data(), r3, sizeof(double) * N3, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hb.data(), b, sizeof(double) * n2, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const double div0 = host_norm(hr), scale0 = abs_product_norm(P.Dv, hb);
+  // reduce ||Dv b|| by rtol_out, but not below the rounding floor of its terms
+  const double target = std::max(rtol_out * div0, 1e2 * 2.220446049250313e-16 * scale0);
+  if (constrained && div0 > target) {
+    // CG on S lambda = Dv b_G carried as b = b_G - M2^-1 Dv^T lambda; its residual is Dv b
+    const double tol = target / div0;
+    k_spmv_dot<4, true><<<kRedGrid, kRedThreads, 0, st>>>(Bs.view(), r3, z3, r3, w.part, nullptr);
+    k_cg_start<<<1, kRedThreads, 0, st>>>(sc3, w.part, tol * tol);
+    CK(cudaMemcpyAsync(p3, z3, sizeof(double) * N3, cudaMemcpyDeviceToDevice, st));
+    h->launches += 2;
+    const int g3 = grid_for(N3, 256, h->num_sms * 8), g2 = grid_for(n2, 256, h->num_sms * 8);
+    double hs[kCgN];
+    for (;;) {
+      CK(cudaMemcpyAsync(hs, sc3, sizeof(hs), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (hs[kCgDone] != 0.0) break;
+      k_spmv<8><<<grid_for((int64_t)n2 * 8, 256, h->num_sms * 16), 256, 0, st>>>(DvT.view(), p3, t2, 1.0, 0.0);
+      h->launches++;
+      if ((rc = proj_pcg(h, h->M2.view(), Bm.view(), t2, wv, n2, rtol_in, max_in, w, &it))) return rc;
+      S.inner_iterations += it;
+      k_spmv_dot<8, false><<<kRedGrid, kRedThreads, 0, st>>>(Dv.view(), wv, q3, p3, w.part, sc3);
+      k_cg_alpha<<<1, kRedThreads, 0, st>>>(sc3, w.part);
+      k_cg_sub<<<g2, 256, 0, st>>>(n2, sc3, wv, b);
+      k_cg_sub<<<g3, 256, 0, st>>>(N3, sc3, q3, r3);
+      k_spmv_dot<4, true><<<kRedGrid, kRedThreads, 0, st>>>(Bs.view(), r3, z3, r3, w.part, sc3);
+      k_cg_beta<<<1, kRedThreads, 0, st>>>(sc3, w.part, max_out);
+      k_cg_p<<<g3, 256, 0, st>>>(N3, sc3, z3, p3);
+      h->launches += 7;
+      CK(cudaGetLastError());
+    }
+    S.outer_iterations = (int32_t)hs[kCgIt];
+    if (hs[kCgDone] == 2.0 || hs[kCgDone] == 3.0) {
+      h->err = hs[kCgDone] == 2.0 ? "projection: the divergence Schur complement lost positivity"
+                                  : "projection: outer CG reached its iteration cap before the tolerance";
+      return FEMPIC_ERR_CG;
+    }
+  }
+  // true constraint residual of the result, against the size of its terms
+  k_spmv<8><<<grid_for((int64_t)N3 * 8, 256, h->num_sms * 16), 256, 0, st>>>(Dv.view(), b, r3, 1.0, 0.0);
+  h->launches++;
+  CK(cudaMemcpyAsync(hr.data(), r3, sizeof(double) * N3, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hb.data(), b, sizeof(double) * n2, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  {
+    const double sc_end = abs_product_norm(P.Dv, hb);
+    S.div_residual = sc_end > 0.0 ? host_norm(hr) / sc_end : 0.0;
+  }
+  if ((rc = refresh_btot(h))) return rc;
+  CK(cudaEventRecord(evs.e[1], st));
+  CK(cudaStreamSynchronize(st));
+  float dms = 0.f;
+  CK(cudaEventElapsedTime(&dms, evs.e[0], evs.e[1]));
+  S.device_ms = dms;
+  S.inner_ms = w.inner_ms;
+  if (stats) *stats = S;
+  return FEMPIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int femPIC_impressed_points(FemPIC* h, double* xyz_host, int64_t* n_points) {
+  if (!h || !h->stream || !n_points) return FEMPIC_ERR_ARG;
+  const int n1d = h->order + 3;
+  const int64_t nq = (int64_t)n1d * n1d * n1d, need = (int64_t)h->n_tets * nq;
+  if (!xyz_host) {
+    *n_points = need;
+    return FEMPIC_OK;
+  }
+  if (*n_points != need) {
+    h->err = "impressed points: buffer holds " + std::to_string(*n_points) + " points, the rule has " +
+             std::to_string(need);
+    return FEMPIC_ERR_SIZE;
+  }
+  // the rule of the projection's load, mapped into every tet (sorted vertices)
+  ProjModel P;
+  projection_rule(h->order, &P);
+  for (int32_t t = 0; t < h->n_tets; ++t) {
+    const int32_t* v = &h->htets[(size_t)t * 4];
+    for (int64_t q = 0; q < nq; ++q) {
+      const double* l = &P.qlam[(size_t)q * 4];
+      for (int d = 0; d < 3; ++d)
+        xyz_host[((size_t)t * nq + q) * 3 + d] =
+            ((l[0] * h->hxyz[3 * (size_t)v[0] + d] + l[1] * h->hxyz[3 * (size_t)v[1] + d]) +
+             l[2] * h->hxyz[3 * (size_t)v[2] + d]) +
+            l[3] * h->hxyz[3 * (size_t)v[3] + d];
+    }
+  }
+  return FEMPIC_OK;
+}
+
+int femPIC_set_impressed_B(FemPIC* h, const double* B_host, int64_t n_points, int32_t constrained,
+                           femPIC_projection* stats) {
+  if (!h || !h->stream) return FEMPIC_ERR_ARG;
+  if (!B_host) {
+    if (n_points != 0) return FEMPIC_ERR_ARG;
+    if (h->bimp) {
+      CK(cudaSetDevice(h->device));
+      CK(cudaMemsetAsync(h->bimp, 0, sizeof(double) * h->n2, h->stream));
+      int rc = refresh_btot(h);
+      if (rc) return rc;
+      CK(cudaStreamSynchronize(h->stream));
+    }
+    if (stats) memset(stats, 0, sizeof(*stats));
+    return FEMPIC_OK;
+  }
+  return project_impressed(h, B_host, n_points, constrained, stats);
+}
+
+}  // extern "C"

@@ -73,6 +73,26 @@ std::string build_local_tables(int order, LocalTables* out);
 int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets, int32_t n_tets,
                 int order, HostModel* m, std::string* err, const int32_t* bface_tag = nullptr);
 
+// Host structures of the impressed-field projection (Section III-C, eq. conB).
+struct ProjModel {
+  int n3 = 0, nq = 0;            // W3 per tet; quadrature points per tet
+  std::vector<double> qlam, qw;  // [nq][4] barycentric points, [nq] weights (sum 1/6)
+  std::vector<double> vol6;      // [nt] 6 |V_t|
+  HostCSR Dv, DvT;               // [~div]_ij = <W3_i, div W2_j>, N3 x N2, and its transpose
+  HostCSR Bm;                    // block-Jacobi inverse of [*mu^-1] (face and interior DOF groups)
+  HostCSR Bs;                    // per-tet block inverse of Dv Bm Dv^T
+  HostCSR Asm;                   // N2 x (nt nl2): sums per-tet load vectors into global DOFs
+};
+
+// The load's quadrature on the reference tet: conical product of (p + 3)-point
+// Gauss-Legendre rules, x = u, y = (1-u) v, z = (1-u)(1-v) w, Jacobian
+// (1-u)^2 (1-v); exact for total degree 2p + 3.  Fills nq, qlam, qw.
+void projection_rule(int order, ProjModel* out);
+// tets: [nt][4] sorted vertex ids (as in HostModel); M2 the assembled [*mu^-1].
+// Returns "" on success, else an error message.
+std::string build_projection(int order, int32_t n_tets, int32_t n_faces, int32_t n2, const double* xyz,
+                             const int32_t* tets, const int32_t* dof2, const HostCSR& M2, ProjModel* out);
+
 // Physical constants (CODATA 2018).
 constexpr double kEps0 = 8.8541878128e-12;
 constexpr double kMu0 = 1.25663706212e-6;

@@ -1106,4 +1106,251 @@ int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets_in, int3
   return 0;
 }
 
+
+// --------------------------------------------------------------------------
+// Impressed-field projection (Section III-C, eq. conB)
+// --------------------------------------------------------------------------
+namespace {
+
+// n-point Gauss-Legendre rule mapped to [0, 1]: Newton's iteration on P_n
+// (three-term recurrence k P_k = (2k-1) x P_{k-1} - (k-1) P_{k-2}) from the
+// guesses cos(pi (i + 3/4) / (n + 1/2)); weights 2 / ((1 - x^2) P_n'(x)^2)
+void gauss_legendre01(int n, std::vector<double>* x, std::vector<double>* w) {
+  x->assign(n, 0.0);
+  w->assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) <= 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    (*x)[n - 1 - i] = 0.5 * (z + 1.0);
+    (*w)[n - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Cholesky inverse of a dense SPD matrix (row-major, in place); false if not SPD
+bool spd_inverse(int n, std::vector<double>& A) {
+  std::vector<double> L((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double d = A[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+    if (!(d > 0.0)) return false;
+    L[(size_t)j * n + j] = std::sqrt(d);
+    for (int i = j + 1; i < n; ++i) {
+      double s = A[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) s -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      L[(size_t)i * n + j] = s / L[(size_t)j * n + j];
+    }
+  }
+  // columns of L^-T L^-1
+  std::vector<double> col(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) {  // forward: L y = e_c
+      double s = i == c ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * col[k];
+      col[i] = s / L[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {  // backward: L^T x = y
+      double s = col[i];
+      for (int k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * col[k];
+      col[i] = s / L[(size_t)i * n + i];
+    }
+    for (int i = 0; i < n; ++i) A[(size_t)i * n + c] = col[i];
+  }
+  return true;
+}
+
+// W3 of order p: P^_a(l0) P^_b(l1) P^_c(l2) P^_d(l3), a, b, c, d >= 1,
+// a + b + c + d = p + 3, scale p + 3 (the volume form's constant factor left out)
+std::vector<Poly> w3_forms(int p) {
+  const int n = p + 3;
+  std::vector<Poly> out;
+  for (int a = 1; a < n; ++a)
+    for (int b = 1; b < n - a; ++b)
+      for (int c = 1; c < n - a - b; ++c) {
+        const int d = n - a - b - c;
+        if (d < 1) continue;
+        out.push_back(multiplier({{0, a, true}, {1, b, true}, {2, c, true}, {3, d, true}}, n));
+      }
+  return out;
+}
+
+// dense rows -> CSR (entries exactly zero dropped)
+void rows_to_csr(int32_t n_rows, int32_t n_cols, std::vector<std::vector<std::pair<int32_t, double>>>& rows,
+                 HostCSR* A) {
+  A->n_rows = n_rows;
+  A->n_cols = n_cols;
+  A->rowptr.assign((size_t)n_rows + 1, 0);
+  A->col.clear();
+  A->val.clear();
+  for (int32_t r = 0; r < n_rows; ++r) {
+    auto& v = rows[r];
+    std::sort(v.begin(), v.end());
+    for (auto& e : v)
+      if (e.second != 0.0) {
+        A->col.push_back(e.first);
+        A->val.push_back(e.second);
+      }
+    A->rowptr[r + 1] = (int32_t)A->col.size();
+  }
+}
+
+}  // namespace
+
+void projection_rule(int p, ProjModel* out) {
+  std::vector<double> x, w;
+  const int nq1 = p + 3;
+  gauss_legendre01(nq1, &x, &w);
+  out->nq = nq1 * nq1 * nq1;
+  out->qlam.clear();
+  out->qw.clear();
+  for (int a = 0; a < nq1; ++a)
+    for (int b = 0; b < nq1; ++b)
+      for (int c = 0; c < nq1; ++c) {
+        const double u = x[a], v = x[b], s = x[c];
+        const double px = u, py = (1.0 - u) * v, pz = (1.0 - u) * (1.0 - v) * s;
+        out->qlam.insert(out->qlam.end(), {1.0 - px - py - pz, px, py, pz});
+        out->qw.push_back(w[a] * w[b] * w[c] * ((1.0 - u) * (1.0 - u) * (1.0 - v)));
+      }
+}
+
+std::string build_projection(int p, int32_t nt, int32_t nf, int32_t n2, const double* xyz,
+                             const int32_t* tets, const int32_t* dof2, const HostCSR& M2, ProjModel* out) {
+  const int nl2 = nloc2(p);
+  // exact local table: Dref[i][j] = int_ref W3_i div W2_j
+  auto f3 = w3_forms(p);
+  auto f2 = w2_forms(p);
+  const int n3 = (int)f3.size();
+  std::vector<double> Dref((size_t)n3 * nl2, 0.0);
+  {
+    std::vector<Poly> div2;
+    for (auto& f : f2) {
+      Vec v = w2_xyz(f);
+      div2.push_back(padd(padd(deriv(v[0], 0), deriv(v[1], 1)), deriv(v[2], 2)));
+    }
+    for (int i = 0; i < n3; ++i) {
+      // int over the reference tet of x^a y^b z^c = a! b! c! / (a+b+c+3)!: the
+      // barycentric formula with the fourth exponent 0
+      Poly w = to_xyz(f3[i]);
+      for (int j = 0; j < nl2; ++j) Dref[(size_t)i * nl2 + j] = to_double(integrate_bary(pmul(w, div2[j])));
+    }
+  }
+  out->n3 = n3;
+  projection_rule(p, out);
+  // per-tet orientation and volume: sign(det J) and 6|V|, J = [x1-x0, x2-x0, x3-x0]
+  std::vector<double> sgn(nt);
+  out->vol6.assign(nt, 0.0);
+  for (int32_t t = 0; t < nt; ++t) {
+    const double* x0 = xyz + 3 * (size_t)tets[4 * (size_t)t];
+    double e[3][3];
+    for (int k = 0; k < 3; ++k)
+      for (int d = 0; d < 3; ++d) e[k][d] = xyz[3 * (size_t)tets[4 * (size_t)t + k + 1] + d] - x0[d];
+    const double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                       e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                       e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+    if (det == 0.0) return "degenerate tet " + std::to_string(t);
+    sgn[t] = det > 0.0 ? 1.0 : -1.0;
+    out->vol6[t] = std::fabs(det);
+  }
+  // [~div]: the physical divergence of W2 (contravariant Piola map) is the
+  // reference one over det J, so int_T W3 div W2 = sign(det J) Dref
+  const int32_t N3 = n3 * nt;
+  {
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(N3), rowsT(n2);
+    for (int32_t t = 0; t < nt; ++t)
+      for (int i = 0; i < n3; ++i)
+        for (int j = 0; j < nl2; ++j) {
+          const double v = sgn[t] * Dref[(size_t)i * nl2 + j];
+          if (v == 0.0) continue;
+          const int32_t r = t * n3 + i, c = dof2[(size_t)t * nl2 + j];
+          rows[r].push_back({c, v});
+          rowsT[c].push_back({r, v});
+        }
+    rows_to_csr(N3, n2, rows, &out->Dv);
+    rows_to_csr(n2, N3, rowsT, &out->DvT);
+  }
+  // block-Jacobi inverse of M2: the W2 DOFs of one face, and the interior DOFs of one tet
+  const int nfg = p * (p + 1) / 2, nint = nl2 - 4 * nfg;
+  const int32_t ngroups = nf + (nint > 0 ? nt : 0);
+  std::vector<std::vector<double>> ginv(ngroups);
+  auto group_base = [&](int32_t g) { return g < nf ? nfg * g : nfg * nf + nint * (g - nf); };
+  auto group_size = [&](int32_t g) { return g < nf ? nfg : nint; };
+  {
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(n2);
+    for (int32_t g = 0; g < ngroups; ++g) {
+      const int32_t b0 = group_base(g);
+      const int gs = group_size(g);
+      std::vector<double> B((size_t)gs * gs, 0.0);
+      for (int a = 0; a < gs; ++a) {
+        const int32_t r = b0 + a;
+        for (int32_t k = M2.rowptr[r]; k < M2.rowptr[r + 1]; ++k) {
+          const int32_t c = M2.col[k];
+          if (c >= b0 && c < b0 + gs) B[(size_t)a * gs + (c - b0)] = M2.val[k];
+        }
+      }
+      if (!spd_inverse(gs, B)) return "a diagonal block of the W2 mass matrix is not positive definite";
+      for (int a = 0; a < gs; ++a)
+        for (int c = 0; c < gs; ++c) rows[b0 + a].push_back({b0 + c, B[(size_t)a * gs + c]});
+      ginv[g] = std::move(B);
+    }
+    rows_to_csr(n2, n2, rows, &out->Bm);
+  }
+  // per-tet block inverse of Dv Bm Dv^T (the tet's W2 DOFs cover whole groups)
+  {
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(N3);
+    std::vector<double> S((size_t)n3 * n3), DB((size_t)n3 * nl2);
+    for (int32_t t = 0; t < nt; ++t) {
+      std::fill(DB.begin(), DB.end(), 0.0);
+      // DB = Dv_t Bm_t, block by block (local blocks: faces k, then the interior)
+      for (int blk = 0; blk < 4 + (nint > 0); ++blk) {
+        const int l0 = blk < 4 ? nfg * blk : 4 * nfg;
+        const int gs = blk < 4 ? nfg : nint;
+        const int32_t g = blk < 4 ? dof2[(size_t)t * nl2 + l0] / nfg : nf + t;
+        const std::vector<double>& Bi = ginv[g];
+        for (int i = 0; i < n3; ++i)
+          for (int c = 0; c < gs; ++c) {
+            double s = 0.0;
+            for (int a = 0; a < gs; ++a) s += sgn[t] * Dref[(size_t)i * nl2 + l0 + a] * Bi[(size_t)a * gs + c];
+            DB[(size_t)i * nl2 + l0 + c] = s;
+          }
+      }
+      for (int i = 0; i < n3; ++i)
+        for (int k = 0; k < n3; ++k) {
+          double s = 0.0;
+          for (int j = 0; j < nl2; ++j) s += DB[(size_t)i * nl2 + j] * sgn[t] * Dref[(size_t)k * nl2 + j];
+          S[(size_t)i * n3 + k] = s;
+        }
+      if (!spd_inverse(n3, S)) return "the divergence Schur block of tet " + std::to_string(t) + " is singular";
+      for (int i = 0; i < n3; ++i)
+        for (int k = 0; k < n3; ++k) rows[t * n3 + i].push_back({t * n3 + k, S[(size_t)i * n3 + k]});
+    }
+    rows_to_csr(N3, N3, rows, &out->Bs);
+  }
+  // assembly of the per-tet local load vectors: f_r = sum over (t, j) with dof2[t][j] = r
+  {
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(n2);
+    for (int64_t k = 0; k < (int64_t)nt * nl2; ++k) rows[dof2[k]].push_back({(int32_t)k, 1.0});
+    rows_to_csr(n2, (int32_t)std::min<int64_t>((int64_t)nt * nl2, INT32_MAX), rows, &out->Asm);
+  }
+  return "";
+}
+
 }  // namespace fempic

@@ -22,7 +22,7 @@ PRECISION = {"fp64_strict": 0, "fp64": 1, "mixed": 2}
 SCHEME = {"trapezoid": 0, "wave": 1}
 PUSH = {"boris": 0, "ab4": 1}
 QUANTITY = {"E": 0, "B": 1, "DG": 2, "RHO": 3, "X": 4, "V": 5, "TET": 6, "NCROSS": 7, "HASH": 8,
-            "E_PREV": 9, "DG_PREV": 10, "DIAG": 11, "PHI": 12, "SPECIES": 13}
+            "E_PREV": 9, "DG_PREV": 10, "DIAG": 11, "PHI": 12, "SPECIES": 13, "B_IMPRESSED": 14}
 MAX_SPECIES = 8
 OPERATOR = {"M1": 0, "K": 1, "C": 2, "D": 3, "DT": 4, "M2": 5, "A": 6, "L": 7, "PI": 8, "PIT": 9}
 
@@ -71,6 +71,12 @@ class femPIC_info(ctypes.Structure):
 
 # (name, restype, argtypes) of every exported symbol declared in include/fempic.h
 _P = ctypes.c_void_p
+class femPIC_projection(ctypes.Structure):
+    _fields_ = [("outer_iterations", ctypes.c_int32), ("inner_iterations", ctypes.c_int32),
+                ("div_residual", ctypes.c_double), ("host_ms", ctypes.c_double), ("device_ms", ctypes.c_double),
+                ("inner_ms", ctypes.c_double), ("bytes_per_inner_iteration", ctypes.c_double)]
+
+
 EXPORTS = [
     ("femPIC_default_opts", None, [ctypes.POINTER(femPIC_opts)]),
     ("femPIC_create", ctypes.c_int, [ctypes.POINTER(femPIC_mesh), ctypes.c_int32,
@@ -90,6 +96,9 @@ EXPORTS = [
     ("femPIC_eval_fields", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P]),
     ("femPIC_eval_fields_noalloc", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P]),
     ("femPIC_get_info", ctypes.c_int, [_P, ctypes.POINTER(femPIC_info)]),
+    ("femPIC_impressed_points", ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
+    ("femPIC_set_impressed_B", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32,
+                                              ctypes.POINTER(femPIC_projection)]),
     ("femPIC_last_timing", ctypes.c_int, [_P, _P, ctypes.c_int32]),
     ("femPIC_destroy", None, [_P]),
     ("femPIC_last_error", ctypes.c_char_p, [_P]),
@@ -254,6 +263,27 @@ def femPIC_eval_fields_noalloc(h, x, tet):
     return E, B
 
 
+def femPIC_impressed_points(h):
+    """[n_points, 3] quadrature points at which to evaluate an impressed B."""
+    n = ctypes.c_int64(0)
+    _check(h, load().femPIC_impressed_points(h, None, ctypes.byref(n)))
+    xyz = np.empty((n.value, 3), dtype=np.float64)
+    _check(h, load().femPIC_impressed_points(h, _ptr(xyz), ctypes.byref(n)))
+    return xyz
+
+
+def femPIC_set_impressed_B(h, B, constrained=True):
+    """Project B [n_points, 3] (values at femPIC_impressed_points) onto W2;
+    None clears it.  Returns the solver statistics as a dict."""
+    st = femPIC_projection()
+    if B is None:
+        _check(h, load().femPIC_set_impressed_B(h, None, 0, int(constrained), ctypes.byref(st)))
+    else:
+        B = np.ascontiguousarray(B, dtype=np.float64).reshape(-1, 3)
+        _check(h, load().femPIC_set_impressed_B(h, _ptr(B), len(B), int(constrained), ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in femPIC_projection._fields_}
+
+
 def femPIC_get_info(h):
     info = femPIC_info()
     _check(h, load().femPIC_get_info(h, ctypes.byref(info)))
@@ -318,7 +348,8 @@ class Simulation:
         i = self.info
         n1, n2, n0, npart = i.n1, i.n2, i.n0, self.n_particles
         return {"E": (n1, np.float64), "E_PREV": (n1, np.float64), "DG": (n1, np.float64),
-                "DG_PREV": (n1, np.float64), "B": (n2, np.float64), "RHO": (n0, np.float64),
+                "DG_PREV": (n1, np.float64), "B": (n2, np.float64), "B_IMPRESSED": (n2, np.float64),
+                "RHO": (n0, np.float64),
                 "PHI": (n0, np.float64), "X": ((npart, 3), np.float64),
                 "V": ((npart, 3), np.float64), "TET": (npart, np.int32), "SPECIES": (npart, np.int32),
                 "NCROSS": (npart, np.int32), "HASH": (npart, np.uint64)}[what]
@@ -357,6 +388,16 @@ class Simulation:
 
     def eval_fields(self, x, tet):
         return femPIC_eval_fields(self.h, x, tet)
+
+    def impressed_points(self):
+        return femPIC_impressed_points(self.h)
+
+    def set_impressed_B(self, B, constrained=True):
+        """B: [n_points, 3] values at impressed_points(), or a callable of the
+        points; None clears the impressed field."""
+        if callable(B):
+            B = B(self.impressed_points())
+        return femPIC_set_impressed_B(self.h, B, constrained)
 
     def last_timing(self):
         return femPIC_last_timing(self.h)
