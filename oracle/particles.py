@@ -83,13 +83,17 @@ def _segment_currents(order, la, lb, s0, s1, qw):
 
 
 
-def walk_deposit(topo, g_all, c_all, x0, x1, v, tet, qw, n1, max_cross=4096):
+def walk_deposit(topo, g_all, c_all, x0, x1, v, tet, qw, n1, max_cross=4096, absorb=None):
     """Walk every chord [x0, x1] through the mesh and deposit its current.
 
-    Returns (x_end, v_end, tet_end, dg, n_cross, hash, status) where ``hash``
-    is an FNV-1a style 64-bit hash over the 32-bit codes of the crossing
-    events (new tet id, or 0x80000000|face for a wall reflection) and
-    ``status`` is 1 where the crossing cap was hit.
+    Returns (x_end, v_end, tet_end, dg, n_cross, hash, status, absorbed)
+    where ``hash`` is an FNV-1a style 64-bit hash over the 32-bit codes of
+    the crossing events (new tet id, 0x80000000|face for a wall reflection,
+    0xC0000000|face for an absorbing wall), ``status`` is 1 where the
+    crossing cap was hit and ``absorbed`` marks paths that ended on an
+    absorbing wall (``absorb`` [n_tets, 4] bool per local face of the sorted
+    tet; None: every wall reflects).  An absorbed path ends at the hit point,
+    its current deposited up to there.
     """
     n = len(x0)
     a = x0.copy()
@@ -101,6 +105,7 @@ def walk_deposit(topo, g_all, c_all, x0, x1, v, tet, qw, n1, max_cross=4096):
     ncross = np.zeros(n, dtype=np.int64)
     hsh = np.full(n, FNV_OFFSET, dtype=np.uint64)
     status = np.zeros(n, dtype=np.int32)
+    absorbed = np.zeros(n, dtype=bool)
     dg = np.zeros(n1)
     act = np.arange(n)
     with np.errstate(divide="ignore", invalid="ignore"):
@@ -129,18 +134,26 @@ def walk_deposit(topo, g_all, c_all, x0, x1, v, tet, qw, n1, max_cross=4096):
                 f = best[go]
                 nb = topo.tet2tet[T[p], f]
                 wall = nb < 0
-                code = np.where(wall, np.int64(0x80000000) | f, nb).astype(np.uint64)
+                ab = wall & (absorb[T[p], f] if absorb is not None else False)
+                code = np.where(ab, np.int64(0xC0000000) | f,
+                                np.where(wall, np.int64(0x80000000) | f, nb)).astype(np.uint64)
                 hsh[p] = (hsh[p] ^ code) * FNV_PRIME
                 ncross[p] += 1
+                pa_ = p[ab]
+                if pa_.size:  # the path ends on the absorbing wall
+                    d = b[pa_] - a[pa_]
+                    b[pa_] = a[pa_] + s1[go][ab][:, None] * d
+                    absorbed[pa_] = True
                 inner = p[~wall]
                 entry[inner] = topo.tet2face[T[inner], f[~wall]]
                 T[inner] = nb[~wall]
                 s_in[inner] = s1[go][~wall]
-                pw = p[wall]
+                refl = wall & ~ab
+                pw = p[refl]
                 if pw.size:
-                    fw = f[wall]
+                    fw = f[refl]
                     gw = g_all[T[pw], fw]
-                    sw = s1[go][wall]
+                    sw = s1[go][refl]
                     d = b[pw] - a[pw]
                     hit = a[pw] + sw[:, None] * d
                     gg = geometry.dot3(gw, gw)
@@ -151,13 +164,13 @@ def walk_deposit(topo, g_all, c_all, x0, x1, v, tet, qw, n1, max_cross=4096):
                     v[pw] = v[pw] - ((2.0 * geometry.dot3(v[pw], gw)) / gg)[:, None] * gw
                     s_in[pw] = 0.0
                     entry[pw] = fw
-                capped = p[ncross[p] >= max_cross]
+                capped = p[(ncross[p] >= max_cross) & ~absorbed[p]]
                 status[capped] = 1
-                keep = go[ncross[p] < max_cross]
+                keep = go[(ncross[p] < max_cross) & ~absorbed[p]]
                 act = act[keep]
             else:
                 act = act[:0]
-    return b, v, T, dg, ncross, hsh, status
+    return b, v, T, dg, ncross, hsh, status, absorbed
 
 
 def measure_rho(topo, g_all, c_all, x, tet, qw):

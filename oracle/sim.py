@@ -15,13 +15,15 @@ Several species (the paper's plasma-ball example: ions and electrons) are
 advanced one after the other with their own q, m and weight; their currents
 and charges add.  Particles are kept concatenated in species order.
 Impedance faces (``bface_tag``, see Topology) add [*_I] to the trapezoid
-rule (see fields).
+rule (see fields).  Absorbing faces end a particle's path on the wall; the
+particle is then re-injected by its species' injector (see inject) before
+the charge is measured, so the particle count is constant.
 """
 
 import numpy as np
 import scipy.sparse.linalg as spla
 
-from . import ab4, assemble, fields, particles
+from . import ab4, assemble, fields, inject, particles
 from .geometry import barycentric_maps
 from .topology import Topology
 
@@ -59,6 +61,18 @@ class Sim:
             self.I = assemble.impedance(t, self.g)
         self.species = [(self.q, self.m, self.weight)]
         self.offsets = [0]
+        self.nstep = 0
+        self.injectors = {}
+        self.seed = 0
+        if push == "ab4" and t.tet_absorb.any():
+            raise ValueError("the Adams-Bashforth push has no absorbing walls")
+
+    def set_injection(self, injectors, seed):
+        """injectors: list of dicts with species, v_drift[3], v_sigma[3]."""
+        self.injectors = {int(d["species"]): (np.asarray(d["v_drift"], dtype=np.float64),
+                                              np.asarray(d["v_sigma"], dtype=np.float64)) for d in injectors}
+        self.seed = int(seed) & inject.MASK
+        self.inj_table = inject.face_table(self.topo)
 
     # ----------------------------------------------------------------- state
     def set_particles(self, x, v, tet):
@@ -121,11 +135,20 @@ class Sim:
             E, B = particles.gather(t, self.g, self.c, self.e, self.b, self.B0, self.x[sl], self.tet[sl])
             vn = particles.boris(self.v[sl], E, B, q, m, dt)
             x1 = self.x[sl] + dt * vn
-            xe, ve, te, d, ncross, hsh, st = particles.walk_deposit(
-                t, self.g, self.c, self.x[sl], x1, vn, self.tet[sl], q * w, t.n1, self.max_cross)
+            xe, ve, te, d, ncross, hsh, st, ab = particles.walk_deposit(
+                t, self.g, self.c, self.x[sl], x1, vn, self.tet[sl], q * w, t.n1, self.max_cross,
+                absorb=t.tet_absorb if t.tet_absorb.any() else None)
             dg += d
+            k = len(parts)
+            if ab.any():
+                if k not in self.injectors:
+                    raise ValueError("absorbing walls need an injector for every species")
+                drift, sigma = self.injectors[k]
+                for i in np.nonzero(ab)[0]:
+                    xe[i], ve[i], te[i] = inject.sample(self.inj_table, self.seed, self.nstep, sl.start + i,
+                                                        drift, sigma)
             parts.append(dict(E=E, B=B, v_half=vn, x_target=x1, x=xe, v=ve, tet=te, ncross=ncross, hash=hsh,
-                              status=st))
+                              status=st, absorbed=ab))
         out = {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
         out["dg"] = dg
         return out
@@ -169,6 +192,7 @@ class Sim:
         if self.push == "ab4":
             self.vh, self.ah = w["vh"], w["ah"]
             self.hcount = min(3, self.hcount + 1)
+        self.nstep += 1
         w["gauss"] = self.gauss_residual()
         return w
 

@@ -29,6 +29,13 @@ DOF is held at 0 when its edge or face lies on a PEC face (an edge shared by
 a PEC and an impedance face is PEC); DOFs on impedance faces only are free.
 W0 boundary DOFs (Dirichlet for the nodal Laplacian and the Gauss residual)
 remain all boundary nodes.
+
+Particle walls (the paper is silent on what happens to particles at walls):
+a boundary face reflects particles specularly unless its tag has bit 2 set
+(absorbing: the path ends on the face and the particle is re-injected).  Bit 4
+marks an injection face (particles are re-injected on such faces; an
+injection face reflects unless it is also absorbing).  Bit 1 is the field
+condition above, so a tag is (impedance) | 2 (absorb) | 4 (inject).
 """
 
 import numpy as np
@@ -88,10 +95,14 @@ class Topology:
             self.tet2tet[a, ia], self.tet2face[a, ia] = b, ib
             self.tet2tet[b, ib], self.tet2face[b, ib] = a, ia
         self.boundary_face = count == 1
-        # boundary face tags: -1 interior, 0 PEC, 1 impedance
+        # boundary face tags: -1 interior, 0 PEC, 1 impedance; particle walls
         self.face_tag = np.where(self.boundary_face, 0, -1).astype(np.int64)
+        self.absorb_face = np.zeros(self.n_faces, dtype=bool)
+        self.inject_face = np.zeros(self.n_faces, dtype=bool)
         if bface_tag is not None:
             tag_in = np.asarray(bface_tag, dtype=np.int64).reshape(nt, 4)
+            if np.any((tag_in < 0) | (tag_in > 7)):
+                raise ValueError("face tags are 0..7: 1 impedance | 2 absorb | 4 inject")
             for tt in range(nt):
                 for i in range(4):
                     tri = np.sort(np.delete(t_in[tt], i))
@@ -100,8 +111,12 @@ class Topology:
                     f = self.tet_faces[tt, j]
                     assert np.array_equal(self.faces[f], tri)
                     if self.boundary_face[f]:
-                        self.face_tag[f] = 1 if tag_in[tt, i] == 1 else 0
+                        self.face_tag[f] = tag_in[tt, i] & 1
+                        self.absorb_face[f] = bool(tag_in[tt, i] & 2)
+                        self.inject_face[f] = bool(tag_in[tt, i] & 4)
         self.imp_face = self.face_tag == 1
+        # absorbing wall per (tet, local face) for the walk
+        self.tet_absorb = self.absorb_face[self.tet_faces] & self.boundary_face[self.tet_faces]
         pf = self.faces[self.face_tag == 0]
         pedge = set()
         for (a, b, c) in pf:

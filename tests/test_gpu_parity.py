@@ -215,7 +215,7 @@ def test_full_size_drift_tube_sampled():
     E, B = opart.gather(t, gg, cc, e, b, cfg["B0"], x0, t0)
     vn = opart.boris(v0, E, B, cfg["q"], cfg["m"], cfg["dt"])
     x1 = x0 + cfg["dt"] * vn
-    xe, ve, te, dg, nc, hs, st = opart.walk_deposit(t, gg, cc, x0, x1, vn, t0, cfg["q"] * cfg["weight"], t.n1)
+    xe, ve, te, dg, nc, hs, st, _ = opart.walk_deposit(t, gg, cc, x0, x1, vn, t0, cfg["q"] * cfg["weight"], t.n1)
     assert np.array_equal(g.get("X")[idx], xe)
     assert np.array_equal(g.get("V")[idx], ve)
     assert np.array_equal(g.get("TET")[idx], te)
@@ -250,7 +250,7 @@ def test_full_size_drift_tube_sampled_fast(precision):
     E, B = opart.gather(t, gg, cc, e, b, cfg["B0"], x0, t0)
     vn = opart.boris(v0, E, B, cfg["q"], cfg["m"], cfg["dt"])
     x1 = x0 + cfg["dt"] * vn
-    xe, ve, te, dg, nc, hs, st = opart.walk_deposit(t, gg, cc, x0, x1, vn, t0, cfg["q"] * cfg["weight"], t.n1)
+    xe, ve, te, dg, nc, hs, st, _ = opart.walk_deposit(t, gg, cc, x0, x1, vn, t0, cfg["q"] * cfg["weight"], t.n1)
     tol = 1e-12 if precision == "fp64" else 2e-6
     assert rel(g.get("X")[idx], xe) < tol
     assert rel(g.get("V")[idx], ve) < tol

@@ -54,7 +54,7 @@ def test_constant_velocity_is_the_straight_chord(order):
     zero = np.zeros((n, 3))
     r = ab4.step(t, g, c, x, v, tet, vh, ah, 3, zero, zero, -1.0, 1.0, 2.0, dt, t.n1)
     x1 = x + dt * v
-    xe, ve, te, dg, nc, hs, st = particles.walk_deposit(t, g, c, x, x1, v, tet, 2.0, t.n1)
+    xe, ve, te, dg, nc, hs, st, _ = particles.walk_deposit(t, g, c, x, x1, v, tet, 2.0, t.n1)
     moved = nc > 0
     assert moved.mean() > 0.3
     assert np.abs(r["x"] - xe).max() < 1e-12

@@ -101,7 +101,7 @@ def test_walk_subsegments_cover_chord(order):
         trace.clear()
         particles._segment_currents = spy
         try:
-            xe, ve, te, dg, nc, hs, st = particles.walk_deposit(
+            xe, ve, te, dg, nc, hs, st, _ = particles.walk_deposit(
                 t, g, c, x0[k:k + 1], x1[k:k + 1], np.zeros((1, 3)), own[k:k + 1], 1.0, t.n1)
         finally:
             particles._segment_currents = orig
@@ -133,7 +133,7 @@ def test_walk_sequence_brute_force_tets():
             inside = np.nonzero(mn > 1e-7)[0]
             if len(inside) == 1 and (not seq or seq[-1] != inside[0]):
                 seq.append(int(inside[0]))
-        xe, ve, te, dg, nc, hs, st = particles.walk_deposit(
+        xe, ve, te, dg, nc, hs, st, _ = particles.walk_deposit(
             t, g, c, a[None], b[None], np.zeros((1, 3)), np.array([T]), 1.0, t.n1)
         # reproduce the hash from the brute-force sequence (interior crossings only)
         h = particles.FNV_OFFSET
@@ -159,7 +159,7 @@ def test_wall_reflection_mirror_image():
     x0, own = x0[keep], own[keep]
     d = np.array([-0.5, 0.05, -0.03])
     v = np.tile(d, (len(x0), 1))
-    xe, ve, te, dg, nc, hs, st = particles.walk_deposit(t, g, c, x0, x0 + d, v, own, 1.0, t.n1)
+    xe, ve, te, dg, nc, hs, st, _ = particles.walk_deposit(t, g, c, x0, x0 + d, v, own, 1.0, t.n1)
     target = x0 + d
     mirror = target * np.array([-1.0, 1.0, 1.0])
     assert np.allclose(xe, mirror, atol=1e-13)

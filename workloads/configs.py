@@ -13,7 +13,7 @@ import math
 
 import numpy as np
 
-from .meshes import kuhn_box, polar_tube, tet_volumes
+from .meshes import kuhn_box, polar_tube, tet_volumes, tube_wall_tags
 from .particles import sample_uniform_in_tets, maxwellian
 
 Q_E = 1.602176634e-19        # elementary charge [C]
@@ -50,8 +50,13 @@ def _box_instance(n, order, n_particles, vth, b0z, seed, jitter=0.1,
         steps=steps, precision=precision)
 
 
-def make_config(name_or_index, n_particles=None, steps=None):
-    """Build one config; ``n_particles``/``steps`` override the sizes."""
+def make_config(name_or_index, n_particles=None, steps=None, walls="reflect", tube=(24, 12, 80)):
+    """Build one config; ``n_particles``/``steps`` override the sizes.
+
+    Drift tube only: ``walls="beam"`` makes the beam flow through (particles
+    absorbed on z = L and re-injected on the z = 0 faces inside the beam
+    radius with the beam's velocity distribution, seed ``seed``); the default
+    reflects at every wall.  ``tube`` = (azimuthal, radial, axial) cells."""
     idx = (CONFIG_NAMES.index(name_or_index) if isinstance(name_or_index, str)
            else int(name_or_index))
     seed = SEED0 + idx
@@ -59,7 +64,7 @@ def make_config(name_or_index, n_particles=None, steps=None):
         cfg = _box_instance(6, 1, n_particles or 10_000, 1.0e6, 0.1, seed, steps=100)
     elif idx == 1:
         rng = np.random.default_rng(seed)
-        xyz, tets = polar_tube(24, 12, 80, radius=0.01, length=0.10)
+        xyz, tets = polar_tube(*tube, radius=0.01, length=0.10)
         n = n_particles or 1_000_000
         r_beam, v0, current = 0.005, 3.0e7, 5.0e-3
         cent = xyz[tets].mean(axis=1)
@@ -72,6 +77,12 @@ def make_config(name_or_index, n_particles=None, steps=None):
                    q=-Q_E, m=M_E, weight=n_e * beam_volume / n,
                    dt=33.3e-12, B0=(0.0, 0.0, 1.0), rho_ion=0.0,
                    steps=1000, precision="fp64")
+        if walls == "beam":
+            cfg["bface_tag"] = tube_wall_tags(xyz, tets, 0.10, r_beam)
+            cfg["injectors"] = [dict(species=0, v_drift=(0.0, 0.0, v0), v_sigma=(0.01 * v0,) * 3)]
+            cfg["inject_seed"] = seed
+        elif walls != "reflect":
+            raise ValueError(walls)
     elif idx == 2:
         cfg = _box_instance(37, 2, n_particles or 10_000_000, 1.0e6, 0.0, seed,
                             beams=2.0e7, precision="mixed", steps=500)

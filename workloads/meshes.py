@@ -139,3 +139,24 @@ def polar_tube(n_az=24, n_rad=12, n_ax=80, radius=0.01, length=0.10):
 
     tets += _kuhn_cells(n_rad - 1, n_az, n_ax, nid, wrap_y=True)
     return xyz, np.asarray(tets, dtype=np.int32)
+
+
+def tube_wall_tags(xyz, tets, length, r_inject):
+    """Face tags [n_tets, 4] (face opposite the i-th vertex as given) for a
+    beam through a tube along +z: faces lying on z = length absorb particles
+    (2), faces on z = 0 whose centroid is within r_inject of the axis are
+    injection faces (4), every other face 0.  Geometry only."""
+    tets = np.asarray(tets)
+    tags = np.zeros(tets.shape, dtype=np.int32)
+    z = xyz[:, 2]
+    for i in range(4):
+        others = np.delete(tets, i, axis=1)
+        zf = z[others]
+        cen = xyz[others].mean(axis=1)
+        at_end = np.all(np.abs(zf - length) <= 1e-12 * max(1.0, abs(length)), axis=1)
+        at_start = np.all(np.abs(zf) <= 1e-12 * max(1.0, abs(length)), axis=1)
+        in_beam = np.hypot(cen[:, 0], cen[:, 1]) < r_inject
+        tags[at_end, i] = 2
+        tags[at_start & in_beam, i] = 4
+    return tags
+
