@@ -201,6 +201,8 @@ typedef struct {
   double gauss_abs;         /* ||D^T [*eps] e + rho + rho_ion <W0,1>||_2, interior */
   double gauss_ref;         /* ||rho||_2, interior                             */
   double crossings;         /* face crossings in the last step (all particles) */
+  double absorbed;          /* particles absorbed on walls (and re-injected) by the
+                               last femPIC_step call, all its steps           */
 } femPIC_diag;
 
 typedef struct {
@@ -220,6 +222,8 @@ typedef struct {
                                in the CG preconditioner (1 = diagonal only)  */
   int32_t n_species;        /* species of the handle                          */
   int32_t n_impedance_faces; /* boundary faces with the absorbing condition   */
+  int32_t n_absorb_faces;   /* boundary faces that absorb particles            */
+  int32_t n_inject_faces;   /* boundary faces particles are re-injected on     */
 } femPIC_info;
 
 /* Fill *opts with defaults: FP64, trapezoid, cg_rtol 1e-12, cg_max_it 2000,
@@ -245,7 +249,11 @@ int femPIC_create(const femPIC_mesh* mesh, int32_t order, const femPIC_species* 
  *   - impedance faces (Section II, eq. impedanceBC with Psi_I = 0, the
  *     first-order absorbing condition): bface_tag_host (NULL = all PEC) is
  *     int32[4*n_tets], the tag of the face opposite the i-th vertex of each tet
- *     as given in the mesh, read for boundary faces only: 0 PEC, 1 impedance.
+ *     as given in the mesh, read for boundary faces only, a sum of bits:
+ *     FEMPIC_FACE_IMPEDANCE (else PEC), FEMPIC_FACE_ABSORB (particles whose
+ *     path reaches the face stop on it, their current deposited up to the
+ *     wall, and are re-injected, see femPIC_set_injection; else they reflect
+ *     specularly), FEMPIC_FACE_INJECT (re-injection happens on such faces).
  *     The surface matrix [*_I]_ij = Y0 <n x W1_i, n x W1_j> (Section III-A;
  *     Y0 = sqrt(eps0/mu0), free-space admittance) enters the trapezoid rule as
  *     ([*eps] + dt^2/4 K + dt/2 [*_I]) e^{n+1} = ([*eps] - dt^2/4 K -
@@ -253,11 +261,39 @@ int femPIC_create(const femPIC_mesh* mesh, int32_t order, const femPIC_species* 
  *     faces are free; an edge shared with a PEC face stays PEC.  Needs the
  *     trapezoid scheme (FEMPIC_ERR_ARG otherwise).
  * Errors as femPIC_create; n_species outside 1..FEMPIC_MAX_SPECIES, a NULL
- * species array or a species with m <= 0, weight < 0 or a non-finite q gives
- * FEMPIC_ERR_ARG.  Handles with several species cannot join a batch. */
+ * species array or a species with m <= 0, weight < 0 or a non-finite q, a
+ * tag outside 0..7, or absorbing faces with FEMPIC_PUSH_AB4 give
+ * FEMPIC_ERR_ARG.  Handles with several species or absorbing faces cannot
+ * join a batch. */
 #define FEMPIC_MAX_SPECIES 8
+enum { FEMPIC_FACE_IMPEDANCE = 1, FEMPIC_FACE_ABSORB = 2, FEMPIC_FACE_INJECT = 4 };
 int femPIC_create_ext(const femPIC_mesh* mesh, int32_t order, const femPIC_species* species, int32_t n_species,
                       const int32_t* bface_tag_host, const femPIC_opts* opts, FemPIC** out);
+
+/* Re-injection of absorbed particles (the paper's drift-tube beam enters at
+ * one end; it does not say how): a particle absorbed by a FEMPIC_FACE_ABSORB
+ * face during a step is replaced in its slot (same id, same species) at the
+ * end of that step by a sample of its species' injector on the
+ * FEMPIC_FACE_INJECT faces, and its charge q w W0(x) is added to rho (the
+ * absorbed particle's is not); the particle count stays fixed.  Sampling,
+ * with every operation rounded once whatever the precision mode: u_d = top 53
+ * bits of SplitMix64 (Steele, Lea and Flood) at state seed + (c + 1)
+ * 0x9E3779B97F4A7C15, c = (step << 40) + (particle id << 6) + d, step the
+ * 0-based index of the step since create; the face is the first (in global
+ * face order) whose running area sum exceeds u_0 times the total; the point
+ * (a + u1 (b - a)) + u2 (c - a) on its sorted vertices, (u1, u2) = (u_1, u_2)
+ * or (1 - u_1, 1 - u_2) when u_1 + u_2 > 1; the tet is the face's; velocity
+ * component j = v_drift[j] + v_sigma[j] ((u_(3+12j) + ... + u_(14+12j)) - 6).
+ * inj[k] configures species inj[k].species; n = 0 clears.  A step of a
+ * handle with absorbing faces and a species without an injector returns
+ * FEMPIC_ERR_STATE.  Errors: FEMPIC_ERR_ARG (species out of range, given
+ * twice, non-finite values, or injectors without FEMPIC_FACE_INJECT faces). */
+typedef struct {
+  int32_t species;   /* species index (0 for femPIC_create handles)          */
+  double v_drift[3]; /* m/s                                                   */
+  double v_sigma[3]; /* m/s, spread of each component (Irwin-Hall, 12 uniforms) */
+} femPIC_injector;
+int femPIC_set_injection(FemPIC* h, const femPIC_injector* inj, int32_t n, uint64_t seed);
 
 /* Advance n_steps PIC steps of size dt (s): gather, Lorentz push, walk,
  * charge-conserving deposit, Newmark field solve, b update, rho measurement

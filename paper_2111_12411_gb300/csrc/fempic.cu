@@ -26,6 +26,7 @@
 #include "batch.cuh"
 #include "particle_ab4.cuh"
 #include "project.cuh"
+#include "inject.cuh"
 
 using namespace fempic;
 using namespace fempic::dev;
@@ -145,6 +146,17 @@ struct FemPIC {
   double *bimp = nullptr, *btot = nullptr;
   std::vector<double> hxyz;
   std::vector<int32_t> htets;
+  // particle walls: absorbing faces (nbr = -2), injection faces (sorted
+  // vertices, owning tet, running area), per-particle absorbed flags of the
+  // last step, the injectors and the absorbed count of the last call
+  int32_t n_absorb_faces = 0, n_inj_faces = 0;
+  double *inj_xyz = nullptr, *inj_cum = nullptr;
+  int32_t* inj_tet = nullptr;
+  uint8_t* pabs = nullptr;
+  bool inj_has[kMaxSpecies] = {};
+  double inj_drift[kMaxSpecies][3] = {}, inj_sigma[kMaxSpecies][3] = {};
+  uint64_t inj_seed = 0;
+  unsigned long long* d_absorbed = nullptr;
 };
 
 // the flux the particles see (self field, plus the impressed one if set)
@@ -558,6 +570,7 @@ int launch_particles(FemPIC* h, double dt) {
   a.crossings = h->d_cross;
   a.pid = h->pid;
   a.sp = species_table(h, dt);
+  a.absorbed = h->pabs;
   if (h->np == 0) return FEMPIC_OK;
   if (h->opts.push == FEMPIC_PUSH_AB4) {
     Ab4Args A;
@@ -625,6 +638,41 @@ int launch_particles(FemPIC* h, double dt) {
   }
   h->launches++;
   CK(cudaGetLastError());
+  if (h->n_absorb_faces > 0) {
+    InjectArgs in;
+    in.n = h->np;
+    for (int k = 0; k < 3; ++k) {
+      in.x[k] = h->px[k];
+      in.v[k] = h->pv[k];
+    }
+    in.tet = h->ptet;
+    in.absorbed = h->pabs;
+    in.pid = h->pid;
+    in.geom = h->geom;
+    in.dof0 = h->dof0;
+    in.rho = h->rho;
+    in.face_xyz = h->inj_xyz;
+    in.face_tet = h->inj_tet;
+    in.face_cum = h->inj_cum;
+    in.n_faces = h->n_inj_faces;
+    in.seed = h->inj_seed;
+    in.step = (uint64_t)h->steps;
+    in.sp = species_table(h, dt);
+    for (int k = 0; k < kMaxSpecies; ++k)
+      for (int c = 0; c < 3; ++c) {
+        in.drift[k][c] = h->inj_drift[k][c];
+        in.sigma[k][c] = h->inj_sigma[k][c];
+      }
+    in.count = h->d_absorbed;
+    if (h->order == 1)
+      k_inject<1><<<grid, 256, 0, h->stream>>>(in);
+    else if (h->order == 2)
+      k_inject<2><<<grid, 256, 0, h->stream>>>(in);
+    else
+      k_inject<3><<<grid, 256, 0, h->stream>>>(in);
+    h->launches++;
+    CK(cudaGetLastError());
+  }
   return FEMPIC_OK;
 }
 
@@ -729,7 +777,15 @@ int do_steps(FemPIC* h, double dt, int32_t n) {
     int rc = form_system(h, dt);
     if (rc) return rc;
   }
+  if (h->n_absorb_faces > 0) {
+    for (int k = 0; k < h->n_species; ++k)
+      if (!h->inj_has[k]) {
+        h->err = "absorbing faces need an injector for every species (femPIC_set_injection)";
+        return FEMPIC_ERR_STATE;
+      }
+  }
   CK(cudaMemsetAsync(h->d_cross, 0, sizeof(unsigned long long), h->stream));
+  CK(cudaMemsetAsync(h->d_absorbed, 0, sizeof(unsigned long long), h->stream));
   CK(cudaMemsetAsync(h->d_cg_iters_acc, 0, sizeof(int32_t), h->stream));
   constexpr int kEv = 6;
   for (int32_t s = 0; s < n; ++s) {
@@ -910,8 +966,9 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
     CK(cudaMemcpyAsync(norms, h->d_norms, sizeof(norms), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(&d.cg_iterations, h->d_cg_iters, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(&d.cg_residual, h->d_cg_res, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    unsigned long long cr = 0;
+    unsigned long long cr = 0, nab = 0;
     CK(cudaMemcpyAsync(&cr, h->d_cross, sizeof(cr), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&nab, h->d_absorbed, sizeof(nab), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(&d.status, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     d.steps = h->steps;
@@ -920,6 +977,7 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
     d.gauss_abs = std::sqrt(norms[2]);
     d.gauss_ref = std::sqrt(norms[3]);
     d.crossings = (double)cr;
+    d.absorbed = (double)nab;
     if (buf_on_device)
       CK(cudaMemcpy(buf, &d, sizeof(d), cudaMemcpyHostToDevice));
     else
@@ -1036,6 +1094,12 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
     return FEMPIC_ERR_ARG;
   }
   h->n_imp_faces = hm.n_imp_faces;
+  if (hm.n_absorb_faces > 0 && o.push == FEMPIC_PUSH_AB4) {
+    h->err = "absorbing faces are built for the Boris push only";
+    return FEMPIC_ERR_ARG;
+  }
+  h->n_absorb_faces = hm.n_absorb_faces;
+  h->n_inj_faces = (int32_t)hm.inj_tet.size();
   // particle ownership check on the host: lambda >= -1e-9 in the given tet
   for (int64_t i = 0; i < sp->n; ++i) {
     int32_t t = sp->tet_host[i];
@@ -1247,6 +1311,12 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
       (rc = dalloc(h, &h->sort_cnt, h->n_tets)) || (rc = dalloc(h, &h->sort_off, h->n_tets)) ||
       (rc = dalloc(h, &h->sort_sums, (h->n_tets + 1023) / 1024 + 1)) ||
       (rc = dalloc(h, &h->sort_sums2, (h->n_tets + 1023) / 1024 / 1024 + 2)))
+    return rc;
+  if ((rc = dalloc(h, &h->d_absorbed, 1))) return rc;
+  CK(cudaMemset(h->d_absorbed, 0, sizeof(unsigned long long)));
+  if (h->n_absorb_faces > 0 && (rc = dalloc(h, &h->pabs, n))) return rc;
+  if (h->n_inj_faces > 0 && ((rc = upload(h, &h->inj_xyz, hm.inj_xyz)) || (rc = upload(h, &h->inj_tet, hm.inj_tet)) ||
+                             (rc = upload(h, &h->inj_cum, hm.inj_cum))))
     return rc;
   if (o.push == FEMPIC_PUSH_AB4) {
     for (int j = 0; j < 3; ++j)
@@ -1621,6 +1691,8 @@ int femPIC_get_info(const FemPIC* h, femPIC_info* info) {
   info->aux_cheb_degree = h->cheb_k;
   info->n_species = h->n_species;
   info->n_impedance_faces = h->n_imp_faces;
+  info->n_absorb_faces = h->n_absorb_faces;
+  info->n_inject_faces = h->n_inj_faces;
   return FEMPIC_OK;
 }
 
@@ -1892,6 +1964,10 @@ int femPIC_batch_create(FemPIC* const* members, int32_t n, FemPICBatch** out) {
     }
     if (h->bimp) {
       b->err = "batched members cannot carry an impressed flux density";
+      return FEMPIC_ERR_ARG;
+    }
+    if (h->n_absorb_faces > 0) {
+      b->err = "batched members cannot have absorbing faces";
       return FEMPIC_ERR_ARG;
     }
     if (h->n_tets > 1024 * 1024) {
@@ -2468,3 +2544,39 @@ int femPIC_set_impressed_B(FemPIC* h, const double* B_host, int64_t n_points, in
 }
 
 }  // extern "C"
+
+extern "C" int femPIC_set_injection(FemPIC* h, const femPIC_injector* inj, int32_t n, uint64_t seed) {
+  if (!h || !h->stream || n < 0 || (n > 0 && !inj)) return FEMPIC_ERR_ARG;
+  bool has[kMaxSpecies] = {};
+  double drift[kMaxSpecies][3] = {}, sigma[kMaxSpecies][3] = {};
+  for (int32_t k = 0; k < n; ++k) {
+    const int32_t s = inj[k].species;
+    if (s < 0 || s >= h->n_species || has[s]) {
+      h->err = "injector " + std::to_string(k) + ": species out of range or given twice";
+      return FEMPIC_ERR_ARG;
+    }
+    for (int c = 0; c < 3; ++c)
+      if (!std::isfinite(inj[k].v_drift[c]) || !std::isfinite(inj[k].v_sigma[c])) {
+        h->err = "injector " + std::to_string(k) + ": non-finite velocity";
+        return FEMPIC_ERR_ARG;
+      }
+    has[s] = true;
+    for (int c = 0; c < 3; ++c) {
+      drift[s][c] = inj[k].v_drift[c];
+      sigma[s][c] = inj[k].v_sigma[c];
+    }
+  }
+  if (n > 0 && h->n_inj_faces == 0) {
+    h->err = "injectors need FEMPIC_FACE_INJECT faces";
+    return FEMPIC_ERR_ARG;
+  }
+  for (int k = 0; k < kMaxSpecies; ++k) {
+    h->inj_has[k] = has[k];
+    for (int c = 0; c < 3; ++c) {
+      h->inj_drift[k][c] = drift[k][c];
+      h->inj_sigma[k][c] = sigma[k][c];
+    }
+  }
+  h->inj_seed = seed;
+  return FEMPIC_OK;
+}

@@ -32,7 +32,8 @@ struct HostModel {
   std::vector<int32_t> tets;     // [nt][4] sorted vertex ids
   std::vector<double> geom;      // [nt][16]: g (4x3 row-major), c[4]
   std::vector<double> vol;       // [nt]
-  std::vector<int32_t> nbr;      // [nt][4]: (neighbour << 2) | neighbour's local face, -1 = wall
+  std::vector<int32_t> nbr;      // [nt][4]: (neighbour << 2) | neighbour's local face, -1 = wall,
+                                 // -2 = wall that absorbs particles
   std::vector<int32_t> dof0, dof1, dof2;  // [nt][nl*]
   std::vector<uint8_t> pec1;     // [n1] 1 on boundary W1 DOFs
   std::vector<uint8_t> bnd0;     // [n0] 1 on boundary W0 DOFs
@@ -47,6 +48,10 @@ struct HostModel {
   HostCSR Pi, PiT;               // vector nodal interpolation: W1 coefficients of hat_v e_c
   std::vector<double> dvM, dvK;  // diag(Pi^T M Pi), diag(Pi^T K Pi)
   int32_t n_imp_faces = 0;       // boundary faces with the impedance (absorbing) condition
+  int32_t n_absorb_faces = 0;    // boundary faces that absorb particles (nbr = -2 there)
+  std::vector<double> inj_xyz;   // [F][3][3] injection faces (global order), sorted vertices
+  std::vector<int32_t> inj_tet;  // [F] owning tet
+  std::vector<double> inj_cum;   // [F] running sum of the faces' areas
   std::vector<double> Ival;      // Y0 <n x W1_i, n x W1_j> over impedance faces, on M's pattern
   HostCSR VM;                    // Pi^T M Pi (values) and its pattern
   std::vector<double> VK;        // Pi^T K Pi on VM's pattern

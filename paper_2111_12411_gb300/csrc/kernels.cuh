@@ -459,6 +459,7 @@ struct ParticleArgs {
   unsigned long long* crossings;
   const int32_t* pid;  // particle ids in device order (read only with several species)
   SpeciesTable sp;
+  uint8_t* absorbed = nullptr;  // [n] 1 where the path ended on an absorbing wall (null: none)
 };
 
 // q w and q dt / 2m of the particle in device slot i
@@ -508,6 +509,7 @@ __global__ void __launch_bounds__(256) k_particle(ParticleArgs a) {
     int entry = -1;
     double s0 = 0.0;
     int nc = 0;
+    uint8_t absorbed = 0;
     unsigned long long hsh = kFnvOffset;
     for (;;) {
       double la[4], lb[4];
@@ -533,13 +535,20 @@ __global__ void __launch_bounds__(256) k_particle(ParticleArgs a) {
       }
       ++nc;
       int nb = __ldg(a.nbr + (size_t)T * 4 + best);
-      unsigned long long code = nb < 0 ? (0x80000000ull | (unsigned)best) : (unsigned long long)(nb >> 2);
+      unsigned long long code = nb == -2  ? (0xC0000000ull | (unsigned)best)
+                                : nb < 0 ? (0x80000000ull | (unsigned)best)
+                                         : (unsigned long long)(nb >> 2);
       hsh = (hsh ^ code) * kFnvPrime;
       if (nb >= 0) {
         entry = nb & 3;
         T = nb >> 2;
         s0 = s1;
         load_geom(a.geom, T, G);
+      } else if (nb == -2) {  // absorbing wall: the path ends at the hit point, no charge left
+#pragma unroll
+        for (int k = 0; k < 3; ++k) pb[k] = Ar::add(pa[k], Ar::mul(s1, Ar::sub(pb[k], pa[k])));
+        absorbed = 1;
+        break;
       } else {
         double gw[3];
 #pragma unroll
@@ -588,6 +597,7 @@ __global__ void __launch_bounds__(256) k_particle(ParticleArgs a) {
     a.tet[i] = T;
     if (a.ncross) a.ncross[i] = nc;
     if (a.hash) a.hash[i] = hsh;
+    if (a.absorbed) a.absorbed[i] = absorbed;
     my_cross = nc;
   }
   // block-aggregated crossing count

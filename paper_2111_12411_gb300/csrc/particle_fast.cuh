@@ -369,17 +369,25 @@ __device__ __forceinline__ void particle_step(const ParticleArgs& a, int64_t i) 
   unsigned long long hsh = kFnvOffset;
   int entry = -1;
   double s0 = 0.0;
+  bool absorbed = false;
   bool walking = valid && best >= 0;
   while (walking) {
     ++nc;
     int nb = __ldg(a.nbr + (size_t)T * 4 + best);
-    unsigned long long code = nb < 0 ? (0x80000000ull | (unsigned)best) : (unsigned long long)(nb >> 2);
+    unsigned long long code = nb == -2  ? (0xC0000000ull | (unsigned)best)
+                              : nb < 0 ? (0x80000000ull | (unsigned)best)
+                                       : (unsigned long long)(nb >> 2);
     hsh = (hsh ^ code) * kFnvPrime;
     if (nb >= 0) {
       entry = nb & 3;
       T = nb >> 2;
       s0 = s1;
       load_geom(a.geom, T, G);
+    } else if (nb == -2) {  // absorbing wall: the path ends at the hit point, no charge left
+#pragma unroll
+      for (int k = 0; k < 3; ++k) pb[k] = fma(s1, pb[k] - pa[k], pa[k]);
+      absorbed = true;
+      break;
     } else {
       double gw[3];
 #pragma unroll
@@ -420,8 +428,9 @@ __device__ __forceinline__ void particle_step(const ParticleArgs& a, int64_t i) 
   }
   // ---- charge at the end point, summed over lanes ending in the same tet
   {
-    const WarpRuns runs = AGG ? warp_runs(valid ? T : -1 - lane) : WarpRuns{0, 0, false};
-    deposit_rho_fact<P>(lb, qw, a.dof0 + (size_t)T * N0, a.rho, AGG && runs.ok, runs, lane, valid);
+    const bool keep = valid && !absorbed;
+    const WarpRuns runs = AGG ? warp_runs(keep ? T : -1 - lane) : WarpRuns{0, 0, false};
+    deposit_rho_fact<P>(lb, qw, a.dof0 + (size_t)T * N0, a.rho, AGG && runs.ok, runs, lane, keep);
   }
   if (valid) {
 #pragma unroll
@@ -432,6 +441,7 @@ __device__ __forceinline__ void particle_step(const ParticleArgs& a, int64_t i) 
     a.tet[i] = T;
     if (a.ncross) a.ncross[i] = nc;
     if (a.hash) a.hash[i] = hsh;
+    if (a.absorbed) a.absorbed[i] = absorbed ? 1 : 0;
   }
   unsigned long long my_cross = nc;
 #pragma unroll

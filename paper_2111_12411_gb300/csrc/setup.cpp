@@ -662,21 +662,60 @@ int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets_in, int3
       bnode[faces[f].a] = bnode[faces[f].b] = bnode[faces[f].c] = 1;
     }
   }
-  // boundary face tags (face opposite the i-th given vertex -> sorted local face)
-  std::vector<uint8_t> fimp(m->n_faces, 0);
+  // boundary face tags (face opposite the i-th given vertex -> sorted local
+  // face): bit 1 impedance, bit 2 absorbs particles, bit 4 injects them
+  std::vector<uint8_t> fimp(m->n_faces, 0), fabs_(m->n_faces, 0), finj(m->n_faces, 0);
   if (bface_tag) {
     for (int32_t t = 0; t < nt; ++t)
       for (int i = 0; i < 4; ++i) {
-        if (bface_tag[(size_t)t * 4 + i] != 1) continue;
+        const int32_t tag = bface_tag[(size_t)t * 4 + i];
+        if (tag < 0 || tag > 7) {
+          *err = "face tags are 0..7 (1 impedance | 2 absorb | 4 inject)";
+          return 1;
+        }
+        if (tag == 0) continue;
         const int32_t vid = tets_in[(size_t)t * 4 + i];
         int k = 0;
         while (k < 4 && m->tets[(size_t)t * 4 + k] != vid) ++k;
         const int32_t f = tet_face[(size_t)t * 4 + k];
-        if (bface[f]) fimp[f] = 1;
+        if (!bface[f]) continue;
+        if (tag & 1) fimp[f] = 1;
+        if (tag & 2) {
+          fabs_[f] = 1;
+          m->nbr[(size_t)t * 4 + k] = -2;  // the walk ends on this wall
+        }
+        if (tag & 4) finj[f] = 1;
       }
   }
   m->n_imp_faces = 0;
-  for (int32_t f = 0; f < m->n_faces; ++f) m->n_imp_faces += fimp[f];
+  m->n_absorb_faces = 0;
+  for (int32_t f = 0; f < m->n_faces; ++f) {
+    m->n_imp_faces += fimp[f];
+    m->n_absorb_faces += fabs_[f];
+  }
+  // injection faces in global order: sorted vertices, owning tet, running area
+  // (0.5 |(b - a) x (c - a)|, summed one face after the other)
+  m->inj_xyz.clear();
+  m->inj_tet.clear();
+  m->inj_cum.clear();
+  {
+    double run = 0.0;
+    for (int32_t f = 0; f < m->n_faces; ++f) {
+      if (!finj[f]) continue;
+      const double* A = xyz + 3 * (size_t)faces[f].a;
+      const double* B = xyz + 3 * (size_t)faces[f].b;
+      const double* C = xyz + 3 * (size_t)faces[f].c;
+      const double e1[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+      const double e2[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+      const double cx = e1[1] * e2[2] - e1[2] * e2[1];
+      const double cy = e1[2] * e2[0] - e1[0] * e2[2];
+      const double cz = e1[0] * e2[1] - e1[1] * e2[0];
+      run = run + 0.5 * std::sqrt((cx * cx + cy * cy) + cz * cz);
+      for (const double* P : {A, B, C}) m->inj_xyz.insert(m->inj_xyz.end(), P, P + 3);
+      m->inj_tet.push_back(own[(size_t)f * 2] >> 2);
+      m->inj_cum.push_back(run);
+    }
+  }
   // boundary edges: edges of boundary faces; PEC edges: edges of PEC faces
   std::vector<uint8_t> pedge(m->n_edges, 0);
   for (int32_t t = 0; t < nt; ++t)

@@ -53,7 +53,7 @@ class femPIC_diag(ctypes.Structure):
                 ("cg_iterations", ctypes.c_int32), ("cg_residual", ctypes.c_double),
                 ("continuity_abs", ctypes.c_double), ("continuity_ref", ctypes.c_double),
                 ("gauss_abs", ctypes.c_double), ("gauss_ref", ctypes.c_double),
-                ("crossings", ctypes.c_double)]
+                ("crossings", ctypes.c_double), ("absorbed", ctypes.c_double)]
 
 
 class femPIC_info(ctypes.Structure):
@@ -66,11 +66,16 @@ class femPIC_info(ctypes.Structure):
                 ("nnz_D", ctypes.c_int64), ("nnz_DT", ctypes.c_int64), ("nnz_Pi", ctypes.c_int64),
                 ("n_boundary_faces", ctypes.c_int32), ("device_bytes", ctypes.c_size_t),
                 ("nnz_L", ctypes.c_int64), ("nnz_V", ctypes.c_int64), ("aux_cheb_degree", ctypes.c_int32),
-                ("n_species", ctypes.c_int32), ("n_impedance_faces", ctypes.c_int32)]
+                ("n_species", ctypes.c_int32), ("n_impedance_faces", ctypes.c_int32),
+                ("n_absorb_faces", ctypes.c_int32), ("n_inject_faces", ctypes.c_int32)]
 
 
 # (name, restype, argtypes) of every exported symbol declared in include/fempic.h
 _P = ctypes.c_void_p
+class femPIC_injector(ctypes.Structure):
+    _fields_ = [("species", ctypes.c_int32), ("v_drift", ctypes.c_double * 3), ("v_sigma", ctypes.c_double * 3)]
+
+
 class femPIC_projection(ctypes.Structure):
     _fields_ = [("outer_iterations", ctypes.c_int32), ("inner_iterations", ctypes.c_int32),
                 ("div_residual", ctypes.c_double), ("host_ms", ctypes.c_double), ("device_ms", ctypes.c_double),
@@ -97,6 +102,7 @@ EXPORTS = [
     ("femPIC_eval_fields_noalloc", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P]),
     ("femPIC_get_info", ctypes.c_int, [_P, ctypes.POINTER(femPIC_info)]),
     ("femPIC_impressed_points", ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
+    ("femPIC_set_injection", ctypes.c_int, [_P, ctypes.POINTER(femPIC_injector), ctypes.c_int32, ctypes.c_uint64]),
     ("femPIC_set_impressed_B", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32,
                                               ctypes.POINTER(femPIC_projection)]),
     ("femPIC_last_timing", ctypes.c_int, [_P, _P, ctypes.c_int32]),
@@ -263,6 +269,17 @@ def femPIC_eval_fields_noalloc(h, x, tet):
     return E, B
 
 
+def femPIC_set_injection(h, injectors, seed):
+    """injectors: list of dicts with species, v_drift[3], v_sigma[3]."""
+    arr = (femPIC_injector * max(1, len(injectors)))()
+    for k, d in enumerate(injectors):
+        arr[k].species = int(d["species"])
+        for c in range(3):
+            arr[k].v_drift[c] = float(d["v_drift"][c])
+            arr[k].v_sigma[c] = float(d["v_sigma"][c])
+    _check(h, load().femPIC_set_injection(h, arr, len(injectors), int(seed) & ((1 << 64) - 1)))
+
+
 def femPIC_impressed_points(h):
     """[n_points, 3] quadrature points at which to evaluate an impressed B."""
     n = ctypes.c_int64(0)
@@ -339,10 +356,16 @@ class Simulation:
 
     @classmethod
     def from_config(cls, cfg, **kw):
+        """A config's instance, with its face tags and injectors when it has them."""
         args = dict(precision=cfg.get("precision", "fp64"), B0=cfg["B0"], rho_ion=cfg["rho_ion"])
+        if cfg.get("bface_tag") is not None:
+            args["bface_tag"] = cfg["bface_tag"]
         args.update(kw)
-        return cls(cfg["xyz"], cfg["tets"], cfg["order"], cfg["q"], cfg["m"], cfg["weight"],
-                   cfg["x"], cfg["v"], cfg["tet"], **args)
+        sim = cls(cfg["xyz"], cfg["tets"], cfg["order"], cfg["q"], cfg["m"], cfg["weight"],
+                  cfg["x"], cfg["v"], cfg["tet"], **args)
+        if cfg.get("injectors") and args.get("bface_tag") is not None:
+            sim.set_injection(cfg["injectors"], cfg["inject_seed"])
+        return sim
 
     def _shape(self, what):
         i = self.info
@@ -388,6 +411,9 @@ class Simulation:
 
     def eval_fields(self, x, tet):
         return femPIC_eval_fields(self.h, x, tet)
+
+    def set_injection(self, injectors, seed):
+        femPIC_set_injection(self.h, injectors, seed)
 
     def impressed_points(self):
         return femPIC_impressed_points(self.h)
