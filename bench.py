@@ -36,9 +36,10 @@ WORKLOAD = ("drift tube R=1cm L=10cm, polar Kuhn mesh 24x12x80 (132480 tets), p=
             "1e6 electrons, v_z=3e7 m/s, B0=1 T, dt=33.3 ps, FP64")
 
 
-def workload_name(order, n_particles):
-    return WORKLOAD.replace("p=2", f"p={order}").replace("1e6 electrons", f"{n_particles:.0e} electrons"
-                                                         .replace("e+0", "e"))
+def workload_name(order, n_particles, walls="beam"):
+    w = WORKLOAD.replace("p=2", f"p={order}").replace("1e6 electrons", f"{n_particles:.0e} electrons"
+                                                      .replace("e+0", "e"))
+    return w + (", beam absorbed at z=L and re-injected at z=0" if walls == "beam" else ", reflecting walls")
 
 
 def measured_peaks():
@@ -150,8 +151,10 @@ def oracle_particle_sample(cfg, n_sample, steps=1):
     over the first n_sample particles of the workload; returns seconds."""
     from oracle import sim as osim
     s = osim.Sim(cfg["xyz"], cfg["tets"], cfg["order"], cfg["q"], cfg["m"], cfg["weight"],
-                 cfg["B0"], cfg["rho_ion"], matrices=False)
+                 cfg["B0"], cfg["rho_ion"], matrices=False, bface_tag=cfg.get("bface_tag"))
     s.set_particles(cfg["x"][:n_sample], cfg["v"][:n_sample], cfg["tet"][:n_sample])
+    if cfg.get("injectors"):
+        s.set_injection(cfg["injectors"], cfg["inject_seed"])
     from oracle import particles as opart
     times = []
     for _ in range(steps):
@@ -167,7 +170,7 @@ def run_reference(args, rank, world):
     import workloads
     if rank != 0:
         return
-    cfg = workloads.make_config(1)
+    cfg = workloads.make_config(1, walls=args.walls)
     n_sample = args.ref_sample
     times = oracle_particle_sample(cfg, n_sample, steps=args.warmup + args.steps)
     timed = times[args.warmup:]
@@ -179,7 +182,7 @@ def run_reference(args, rank, world):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(timed),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+           "data": "synthetic", "config": {"workload": workload_name(2, 1_000_000, args.walls), "sample": sample},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -195,7 +198,7 @@ def run_native(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
-    cfg = workloads.make_config(1, n_particles=args.particles)
+    cfg = workloads.make_config(1, n_particles=args.particles, walls=args.walls)
     cfg["order"] = args.order
     sim = Simulation.from_config(cfg, precision=args.precision, device=local_rank,
                                  stream=stream.cuda_stream, cg_rtol=args.cg_rtol, push=args.push,
@@ -341,7 +344,7 @@ def run_native(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision != "mixed" else "f64+f32",
             "data": "synthetic",
-            "config": {"workload": workload_name(info.order, npart), "precision": args.precision,
+            "config": {"workload": workload_name(info.order, npart, args.walls), "precision": args.precision,
                        "push": args.push,
                        "l2": "flushed between steps "
                        "(256 MiB write)", "parallelism": "replicas" if world > 1 else "single GPU",
@@ -666,6 +669,8 @@ def main():
     ap.add_argument("--order", type=int, default=2, choices=(1, 2, 3),
                     help="basis order p of the tube and project workloads")
     ap.add_argument("--cg-max-it", type=int, default=2000)
+    ap.add_argument("--walls", default="beam", choices=("beam", "reflect"),
+                    help="drift tube walls: the beam absorbed at z=L and re-injected at z=0, or reflection")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--rate", type=float, default=2.0)
