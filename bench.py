@@ -648,6 +648,102 @@ def run_project(args, local_rank):
     sim.close()
 
 
+def _timed_steps(sm, dt, K, W):
+    """W untimed then K timed steps; per-step library timings and diagnostics."""
+    import torch
+    sm.step(dt, W)
+    torch.cuda.synchronize()
+    acc = {"particle_ms": 0.0, "field_ms": 0.0, "pcg_ms": 0.0, "cg_iterations": 0.0}
+    cont = gauss = 0.0
+    for _ in range(K):
+        sm.step(dt)
+        t = sm.last_timing()
+        for k in acc:
+            acc[k] += t[k]
+        d = sm.diag()
+        if d["continuity_ref"] > 0:
+            cont = max(cont, d["continuity_abs"] / d["continuity_ref"])
+        if d["gauss_ref"] > 0:
+            gauss = d["gauss_abs"] / d["gauss_ref"]
+    out = {k: v / K for k, v in acc.items()}
+    out["step_ms"] = out["particle_ms"] + out["field_ms"]
+    out["continuity_rel_max"] = cont
+    out["gauss_rel_last"] = gauss
+    return out
+
+
+def run_schemes(args, local_rank):
+    """The time schemes of Section III-B / IV-D on the drift-tube workload:
+    the trapezoidal rule on [b; e] against the second-order e form with the
+    backward-difference (gamma 1.5, beta 1) and Galerkin (gamma 1.5, beta 0.8)
+    parameters.  Whole step, CG iterations, Gauss residual after the run."""
+    import torch
+    import workloads
+    from paper_2111_12411_gb300 import Simulation
+
+    torch.cuda.set_device(local_rank)
+    cfg = workloads.make_config(1, n_particles=args.particles, walls=args.walls)
+    K, W = args.steps, args.warmup
+    npart = len(cfg["x"])
+    out = {"metric": "particle-steps/s of the whole step per time scheme", "unit": UNIT, "steps": K, "warmup": W,
+           "data": "synthetic", "config": {"workload": workload_name(2, npart, args.walls), "cg_rtol": args.cg_rtol}}
+    for name, scheme, g, b in (("trapezoid", "trapezoid", 0.5, 0.25), ("backward_difference", "wave", 1.5, 1.0),
+                               ("galerkin", "wave", 1.5, 0.8)):
+        sm = Simulation.from_config(cfg, device=local_rank, scheme=scheme, gamma=g, beta=b, diagnostics=True,
+                                    cg_rtol=args.cg_rtol)
+        r = _timed_steps(sm, cfg["dt"], K, W)
+        r["particle_steps_per_s"] = npart / (r["step_ms"] * 1e-3)
+        out[name] = r
+        sm.close()
+    out["value"] = out["trapezoid"]["particle_steps_per_s"]
+    print(json.dumps(out), flush=True)
+
+
+def run_species(args, local_rank):
+    """Impedance (first-order absorbing) walls and two species, the
+    ingredients of the paper's plasma-ball example (Section IV), on a 24^3
+    Kuhn box of 1 m, p = 2: electrons (v_th 1e6 m/s) and Sr+ ions (v_th
+    1e3 m/s), 5e5 of each, every wall impedance, against the same run with
+    PEC walls and one species.  Whole step, CG iterations, continuity."""
+    import torch
+    import workloads
+    from paper_2111_12411_gb300 import Simulation
+
+    torch.cuda.set_device(local_rank)
+    n = args.particles or 500_000
+    xyz, tets = workloads.kuhn_box(24, 24, 24, jitter=0.1, seed=workloads.configs.SEED0 + 7)
+    rng = np.random.default_rng(workloads.configs.SEED0 + 7)
+    q_e, m_e = workloads.configs.Q_E, workloads.configs.M_E
+    m_sr = 87.62 * 1.66053906660e-27
+    h = 1.0 / 24
+    omega = 1e6 / h
+    n_e = omega * omega * workloads.configs.EPS0 * m_e / (q_e * q_e)
+    w = n_e / n
+    dt = 0.5 / omega
+    xe, te = workloads.sample_uniform_in_tets(xyz, tets, n, rng)
+    xi, ti = workloads.sample_uniform_in_tets(xyz, tets, n, rng)
+    sp = [dict(q=-q_e, m=m_e, weight=w, x=xe, v=workloads.maxwellian(n, 1e6, rng), tet=te),
+          dict(q=q_e, m=m_sr, weight=w, x=xi, v=workloads.maxwellian(n, 1e3, rng), tet=ti)]
+    tag = np.ones((len(tets), 4), dtype=np.int32)
+    K, W = args.steps, args.warmup
+    out = {"metric": "particle-steps/s of the whole step, impedance walls and two species vs PEC and one",
+           "unit": UNIT, "steps": K, "warmup": W, "data": "synthetic",
+           "config": {"workload": f"Kuhn box 24^3 (82944 tets), p=2, {n} electrons + {n} Sr+ ions, "
+                                  f"dt={dt:.3g} s, impedance on every wall", "cg_rtol": args.cg_rtol}}
+    runs = (("impedance_two_species", dict(species=sp, bface_tag=tag), 2 * n),
+            ("pec_electrons", dict(), n))
+    for name, kw, npart in runs:
+        sm = Simulation(xyz, tets, 2, -q_e, m_e, w, xe, sp[0]["v"], te, device=local_rank, diagnostics=True,
+                        cg_rtol=args.cg_rtol, **kw)
+        r = _timed_steps(sm, dt, K, W)
+        r["particle_steps_per_s"] = npart / (r["step_ms"] * 1e-3)
+        r["n_particles"] = npart
+        out[name] = r
+        sm.close()
+    out["value"] = out["impedance_two_species"]["particle_steps_per_s"]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -664,7 +760,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=50_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("tube", "batched", "serving", "precision", "push", "project"),
+    ap.add_argument("--workload", choices=("tube", "batched", "serving", "precision", "push", "project",
+                                           "schemes", "species"),
                     default="tube")
     ap.add_argument("--order", type=int, default=2, choices=(1, 2, 3),
                     help="basis order p of the tube and project workloads")
@@ -702,6 +799,10 @@ def main():
         run_push(args, local_rank)
     elif args.workload == "project":
         run_project(args, local_rank)
+    elif args.workload == "schemes":
+        run_schemes(args, local_rank)
+    elif args.workload == "species":
+        run_species(args, local_rank)
     else:
         run_native(args, rank, world, local_rank)
     if world > 1:

@@ -103,6 +103,16 @@ struct FemPIC {
   // and, at order 2, in 2x2 blocks; null without such faces
   int32_t n_imp_faces = 0;
   double *Iv = nullptr, *bI = nullptr;
+  // with impedance faces: the preconditioner's gradient space (W0 DOFs off
+  // PEC faces), its Laplacian L_a = D_a^T ([*eps] + c_I [*_I]) D_a formed when
+  // dt changes (values LA.v + c_I LAI in LAdt), FP32 copies, Chebyshev
+  // coefficients, host copies for the eigenvalue bound
+  DevCSR DA, DAT, LA;
+  double *LAI = nullptr, *LAdt = nullptr, *dinvLA = nullptr;
+  float *DA32 = nullptr, *DAT32 = nullptr, *LA32 = nullptr, *dinvLA32 = nullptr;
+  std::vector<int32_t> hLA_rp, hLA_ci;
+  std::vector<double> hLA_m, hLA_i;
+  float chebLA[3][kMaxCheb] = {};
   // species: ids [sp_off[k], sp_off[k+1]) belong to species k
   // Adams-Bashforth push: history v^{n-1-j}, a^{n-1-j} per particle (device
   // order; the particles are not re-sorted), entries filled so far
@@ -358,15 +368,16 @@ int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, 
   PcgArgs a;
   a.A = A;
   a.dinv = dinv;
-  a.D = nodal ? view32(h->D, h->D32) : CsrView32{0, nullptr, nullptr, nullptr};
-  a.DT = nodal ? view32(h->DT, h->DT32) : CsrView32{0, nullptr, nullptr, nullptr};
-  a.dinvL = h->dinvL32;
+  const bool imp = nodal && h->LA.nnz > 0;  // gradient space with the impedance faces' W0 DOFs
+  a.D = imp ? view32(h->DA, h->DA32) : nodal ? view32(h->D, h->D32) : CsrView32{0, nullptr, nullptr, nullptr};
+  a.DT = imp ? view32(h->DAT, h->DAT32) : nodal ? view32(h->DT, h->DT32) : CsrView32{0, nullptr, nullptr, nullptr};
+  a.dinvL = imp ? h->dinvLA32 : h->dinvL32;
   a.t = h->aux_t;
   a.Pi = nodal ? view32(h->Pi, h->Pi32) : CsrView32{0, nullptr, nullptr, nullptr};
   a.PiT = nodal ? view32(h->PiT, h->PiT32) : CsrView32{0, nullptr, nullptr, nullptr};
   a.dinvV = h->dinvV;
   a.u = h->aux_u;
-  a.L = nodal ? view32(h->L, h->L32) : CsrView32{0, nullptr, nullptr, nullptr};
+  a.L = imp ? view32(h->LA, h->LA32) : nodal ? view32(h->L, h->L32) : CsrView32{0, nullptr, nullptr, nullptr};
   a.V = (nodal && h->V.nnz > 0) ? view32(h->V, h->V32) : CsrView32{0, nullptr, nullptr, nullptr};
   a.tf = h->aux_tf;
   a.td = h->aux_td;
@@ -375,7 +386,7 @@ int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, 
   a.ud = h->aux_ud;
   a.u2 = h->aux_u2;
   a.cheb_k = nodal ? h->cheb_k : 1;
-  memcpy(a.chebL, h->chebL, sizeof(a.chebL));
+  memcpy(a.chebL, imp ? h->chebLA : h->chebL, sizeof(a.chebL));
   memcpy(a.chebV, h->chebV, sizeof(a.chebV));
   a.Ab = (nodal && h->nb > 0) ? BsrView{h->nb, h->brp, h->bci, h->bA} : BsrView{0, nullptr, nullptr, nullptr};
   a.q32 = h->cg_q32;
@@ -454,6 +465,21 @@ int form_system(FemPIC* h, double dt) {
     k_form_blocks<<<grid_for(h->nb, 256, 1 << 30), 256, 0, h->stream>>>(h->nb, h->brp, h->bci, h->bM, h->bK, c1,
                                                                         h->bA, h->binv, h->bI, ci_imp);
     h->launches++;
+  }
+  if (h->LA.nnz > 0) {
+    // L_a = D_a^T ([*eps] + dt/2 [*_I]) D_a: the gradients of W0 on impedance faces see the boundary term
+    const int32_t nnz = (int32_t)h->LA.nnz;
+    k_lincomb<<<grid_for(nnz, 256, 4096), 256, 0, h->stream>>>(nnz, h->LA.v, h->LAI, 1.0, ci_imp, h->LAdt);
+    k_to_f32<<<grid_for(nnz, 256, 4096), 256, 0, h->stream>>>(nnz, h->LAdt, h->LA32);
+    k_inv_diag<<<grid_for(h->n0, 256, 1 << 30), 256, 0, h->stream>>>(h->n0, h->LA.rp, h->LA.ci, h->LAdt, h->dinvLA);
+    k_to_f32<<<grid_for(h->n0, 256, 4096), 256, 0, h->stream>>>(h->n0, h->dinvLA, h->dinvLA32);
+    h->launches += 4;
+    CK(cudaGetLastError());
+    if (h->cheb_k > 1)
+      cheb_coeffs(gershgorin_scaled(h->hLA_rp, h->hLA_ci, h->hLA_m.data(), h->hLA_i.data(), ci_imp), h->cheb_k,
+                  h->chebLA);
+    else
+      cheb_coeffs(0.0, 1, h->chebLA);
   }
   h->launches++;
   CK(cudaGetLastError());
@@ -1242,6 +1268,23 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
   }
   const size_t nnz = hm.M.col.size();
   if (!hm.Ival.empty() && (rc = upload(h, &h->Iv, hm.Ival))) return rc;
+  if (!hm.LA.col.empty()) {
+    const size_t nl = hm.LA.col.size();
+    if ((rc = upload_csr(h, &h->DA, hm.DA)) || (rc = upload_csr(h, &h->DAT, hm.DAT)) ||
+        (rc = upload_csr(h, &h->LA, hm.LA)) || (rc = upload(h, &h->LAI, hm.LAI)) || (rc = dalloc(h, &h->LAdt, nl)) ||
+        (rc = dalloc(h, &h->dinvLA, h->n0)) || (rc = dalloc(h, &h->DA32, hm.DA.col.size())) ||
+        (rc = dalloc(h, &h->DAT32, hm.DAT.col.size())) || (rc = dalloc(h, &h->LA32, nl)) ||
+        (rc = dalloc(h, &h->dinvLA32, h->n0)))
+      return rc;
+    if (h->DA.nnz > 0) k_to_f32<<<grid_for(h->DA.nnz, 256, 4096), 256, 0, h->stream>>>(h->DA.nnz, h->DA.v, h->DA32);
+    if (h->DAT.nnz > 0)
+      k_to_f32<<<grid_for(h->DAT.nnz, 256, 4096), 256, 0, h->stream>>>(h->DAT.nnz, h->DAT.v, h->DAT32);
+    CK(cudaGetLastError());
+    h->hLA_rp = hm.LA.rowptr;
+    h->hLA_ci = hm.LA.col;
+    h->hLA_m = hm.LA.val;
+    h->hLA_i = hm.LAI;
+  }
   if ((rc = dalloc(h, &h->Aval, nnz)) || (rc = dalloc(h, &h->R1val, nnz)) ||
       (rc = dalloc(h, &h->R2val, o.scheme == FEMPIC_SCHEME_WAVE ? nnz : 1)) || (rc = dalloc(h, &h->dinvA, h->n1)) ||
       (rc = dalloc(h, &h->dinvL, h->n0)))

@@ -53,6 +53,10 @@ struct HostModel {
   std::vector<int32_t> inj_tet;  // [F] owning tet
   std::vector<double> inj_cum;   // [F] running sum of the faces' areas
   std::vector<double> Ival;      // Y0 <n x W1_i, n x W1_j> over impedance faces, on M's pattern
+  HostCSR DA, DAT, LA;           // with impedance faces only: the gradient map on the W0 DOFs
+                                 // off PEC faces (free W1 rows), its transpose, and
+                                 // D_a^T [*eps] D_a on those DOFs (preconditioner space)
+  std::vector<double> LAI;       // D_a^T [*_I] D_a on LA's pattern
   HostCSR VM;                    // Pi^T M Pi (values) and its pattern
   std::vector<double> VK;        // Pi^T K Pi on VM's pattern
 };

@@ -489,6 +489,18 @@ inline void scatter(HostCSR* A, const int32_t* Rm, const int32_t* Cm, int lr, in
   }
 }
 
+// local W0 DOF j (numbering of the order-p forms) lies on local face k (the
+// face opposite vertex k): its lattice multi-index has a zero at vertex k
+bool w0_on_face(int p, int j, int k) {
+  if (j < 4) return j != k;
+  if (p == 2) return kLocalEdges[j - 4][0] != k && kLocalEdges[j - 4][1] != k;
+  if (p == 3) {
+    if (j < 16) return kLocalEdges[(j - 4) / 2][0] != k && kLocalEdges[(j - 4) / 2][1] != k;
+    return j - 16 == k;
+  }
+  return false;
+}
+
 }  // namespace
 
 // --------------------------------------------------------------------------
@@ -886,6 +898,24 @@ int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets_in, int3
   build_pattern(m->n1, m->n0, nt, l1, l0, d1, d0, all1, int0, maskD, &m->D);
   build_pattern(m->n0, m->n1, nt, l0, l1, d0, d1, all0, all1, maskDT, &m->DT);
   build_pattern(m->n0, m->n0, nt, l0, l0, d0, d0, int0, int0, full00, &m->L);
+  // With impedance faces the W1 DOFs on them are free, so the gradients of the
+  // W0 functions that live there are in the near-kernel of K too: the
+  // preconditioner's gradient space is every W0 DOF off the PEC faces
+  // (aux0), its Laplacian D_a^T (M + c_I I) D_a (the I part depends on dt).
+  std::vector<uint8_t> aux0;
+  if (m->n_imp_faces > 0) {
+    aux0.assign(m->n0, 1);
+    for (int32_t t = 0; t < nt; ++t)
+      for (int k = 0; k < 4; ++k) {
+        const int32_t f = tet_face[(size_t)t * 4 + k];
+        if (!bface[f] || fimp[f]) continue;
+        for (int j = 0; j < l0; ++j)
+          if (w0_on_face(p, j, k)) aux0[d0[(size_t)t * l0 + j]] = 0;
+      }
+    build_pattern(m->n1, m->n0, nt, l1, l0, d1, d0, free1, aux0, maskD, &m->DA);
+    build_pattern(m->n0, m->n1, nt, l0, l1, d0, d1, aux0, free1, maskDT, &m->DAT);
+    build_pattern(m->n0, m->n0, nt, l0, l0, d0, d0, aux0, aux0, full00, &m->LA);
+  }
   m->load0.assign(m->n0, 0.0);
 
   std::vector<double> DT_loc((size_t)l0 * l1);
@@ -975,6 +1005,11 @@ int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets_in, int3
       scatter(&m->C, r2, r1, l2, l1, T.Cloc.data(), all2, free1, true);
       scatter(&m->D, r1, r0, l1, l0, T.Dloc.data(), all1, int0, true);
       scatter(&m->DT, r0, r1, l0, l1, DT_loc.data(), all0, all1, true);
+      if (!aux0.empty()) {
+        scatter(&m->LA, r0, r0, l0, l0, &bL[q * sL], aux0, aux0, false);
+        scatter(&m->DA, r1, r0, l1, l0, T.Dloc.data(), free1, aux0, true);
+        scatter(&m->DAT, r0, r1, l0, l1, DT_loc.data(), aux0, free1, true);
+      }
       for (int k = 0; k < l0; ++k) m->load0[r0[k]] += bW[q * l0 + k];
     }
   }
@@ -982,9 +1017,13 @@ int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets_in, int3
   // faces, on M's pattern: the tangential part of grad l_x on the face opposite
   // local vertex i is grad l_x - (grad l_x . n) n with n = grad l_i / |grad l_i|
   m->Ival.clear();
+  m->LAI.clear();
   if (m->n_imp_faces > 0) {
     HostCSR Ih = m->M;
     std::fill(Ih.val.begin(), Ih.val.end(), 0.0);
+    HostCSR LIh = m->LA;  // D_a^T I D_a on the pattern of L_a
+    std::fill(LIh.val.begin(), LIh.val.end(), 0.0);
+    std::vector<double> tmpI((size_t)l0 * l1), LIe((size_t)l0 * l0);
     const double Y0 = std::sqrt(kEps0 / kMu0);
     std::vector<double> Ie((size_t)l1 * l1);
     for (int32_t t = 0; t < nt; ++t)
@@ -1022,8 +1061,22 @@ int build_model(const double* xyz, int32_t n_nodes, const int32_t* tets_in, int3
             Ie[(size_t)a * l1 + b] = Y0 * area2 * sum;
           }
         scatter(&Ih, d1 + (size_t)t * l1, d1 + (size_t)t * l1, l1, l1, Ie.data(), free1, free1, false);
+        for (int k = 0; k < l0; ++k)
+          for (int b = 0; b < l1; ++b) {
+            double sacc = 0.0;
+            for (int a = 0; a < l1; ++a) sacc += DT_loc[(size_t)k * l1 + a] * Ie[(size_t)a * l1 + b];
+            tmpI[(size_t)k * l1 + b] = sacc;
+          }
+        for (int k = 0; k < l0; ++k)
+          for (int n = 0; n < l0; ++n) {
+            double sacc = 0.0;
+            for (int b = 0; b < l1; ++b) sacc += tmpI[(size_t)k * l1 + b] * T.Dloc[(size_t)b * l0 + n];
+            LIe[(size_t)k * l0 + n] = sacc;
+          }
+        scatter(&LIh, d0 + (size_t)t * l0, d0 + (size_t)t * l0, l0, l0, LIe.data(), aux0, aux0, false);
       }
     m->Ival = Ih.val;
+    m->LAI = LIh.val;
   }
   // ---- vector nodal interpolation Pi (auxiliary space of the preconditioner)
   {
