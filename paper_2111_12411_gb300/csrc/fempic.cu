@@ -2303,6 +2303,14 @@ struct ScratchScope {
   }
 };
 
+// lanes per row in the projection's products: [*mu^-1] and [~div] rows, and
+// the block-diagonal preconditioners' rows
+#ifndef FEMPIC_PROJ_LPR_A
+#define FEMPIC_PROJ_LPR_A 2
+#endif
+#ifndef FEMPIC_PROJ_LPR_P
+#define FEMPIC_PROJ_LPR_P 1
+#endif
 constexpr int kProjChunk = 16;
 
 // four timing events, destroyed with the scope
@@ -2332,7 +2340,7 @@ int proj_pcg(FemPIC* h, const CsrView& A, const CsrView& P, const double* rhs, d
   const int gv = grid_for(n, 256, h->num_sms * 8);
   CK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
   CK(cudaMemcpyAsync(w.r, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-  k_spmv_dot<4, true><<<kRedGrid, kRedThreads, 0, st>>>(P, w.r, w.z, w.r, w.part, nullptr);
+  k_spmv_dot<FEMPIC_PROJ_LPR_P, true><<<kRedGrid, kRedThreads, 0, st>>>(P, w.r, w.z, w.r, w.part, nullptr);
   k_cg_start<<<1, kRedThreads, 0, st>>>(w.sc, w.part, rtol * rtol);
   CK(cudaMemcpyAsync(w.p, w.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   h->launches += 2;
@@ -2350,10 +2358,10 @@ int proj_pcg(FemPIC* h, const CsrView& A, const CsrView& P, const double* rhs, d
     if (hs[kCgDone] != 0.0) break;
     CK(cudaEventRecord(w.ev0, st));
     for (int k = 0; k < kProjChunk; ++k) {
-      k_spmv_dot<8, false><<<kRedGrid, kRedThreads, 0, st>>>(A, w.p, w.q, w.p, w.part, w.sc);
+      k_spmv_dot<FEMPIC_PROJ_LPR_A, false><<<kRedGrid, kRedThreads, 0, st>>>(A, w.p, w.q, w.p, w.part, w.sc);
       k_cg_alpha<<<1, kRedThreads, 0, st>>>(w.sc, w.part);
       k_cg_xr<<<gv, 256, 0, st>>>(n, w.sc, w.p, w.q, x, w.r);
-      k_spmv_dot<4, true><<<kRedGrid, kRedThreads, 0, st>>>(P, w.r, w.z, w.r, w.part, w.sc);
+      k_spmv_dot<FEMPIC_PROJ_LPR_P, true><<<kRedGrid, kRedThreads, 0, st>>>(P, w.r, w.z, w.r, w.part, w.sc);
       k_cg_beta<<<1, kRedThreads, 0, st>>>(w.sc, w.part, max_it);
       k_cg_p<<<gv, 256, 0, st>>>(n, w.sc, w.z, w.p);
     }
@@ -2482,7 +2490,7 @@ int project_impressed(FemPIC* h, const double* B_host, int64_t n_points, int32_t
   if (constrained && div0 > target) {
     // CG on S lambda = Dv b_G carried as b = b_G - M2^-1 Dv^T lambda; its residual is Dv b
     const double tol = target / div0;
-    k_spmv_dot<4, true><<<kRedGrid, kRedThreads, 0, st>>>(Bs.view(), r3, z3, r3, w.part, nullptr);
+    k_spmv_dot<FEMPIC_PROJ_LPR_P, true><<<kRedGrid, kRedThreads, 0, st>>>(Bs.view(), r3, z3, r3, w.part, nullptr);
     k_cg_start<<<1, kRedThreads, 0, st>>>(sc3, w.part, tol * tol);
     CK(cudaMemcpyAsync(p3, z3, sizeof(double) * N3, cudaMemcpyDeviceToDevice, st));
     h->launches += 2;
@@ -2496,11 +2504,11 @@ int project_impressed(FemPIC* h, const double* B_host, int64_t n_points, int32_t
       h->launches++;
       if ((rc = proj_pcg(h, h->M2.view(), Bm.view(), t2, wv, n2, rtol_in, max_in, w, &it))) return rc;
       S.inner_iterations += it;
-      k_spmv_dot<8, false><<<kRedGrid, kRedThreads, 0, st>>>(Dv.view(), wv, q3, p3, w.part, sc3);
+      k_spmv_dot<FEMPIC_PROJ_LPR_A, false><<<kRedGrid, kRedThreads, 0, st>>>(Dv.view(), wv, q3, p3, w.part, sc3);
       k_cg_alpha<<<1, kRedThreads, 0, st>>>(sc3, w.part);
       k_cg_sub<<<g2, 256, 0, st>>>(n2, sc3, wv, b);
       k_cg_sub<<<g3, 256, 0, st>>>(N3, sc3, q3, r3);
-      k_spmv_dot<4, true><<<kRedGrid, kRedThreads, 0, st>>>(Bs.view(), r3, z3, r3, w.part, sc3);
+      k_spmv_dot<FEMPIC_PROJ_LPR_P, true><<<kRedGrid, kRedThreads, 0, st>>>(Bs.view(), r3, z3, r3, w.part, sc3);
       k_cg_beta<<<1, kRedThreads, 0, st>>>(sc3, w.part, max_out);
       k_cg_p<<<g3, 256, 0, st>>>(N3, sc3, z3, p3);
       h->launches += 7;
