@@ -440,6 +440,27 @@ int femPIC_batch_step(FemPICBatch* b, const double* dt_host, int32_t n_steps);
 /* times: [0] device ms of the last femPIC_batch_step call, [1] launches per
  * step, [2] 1 if the CUDA graph was used, [3] CTAs of the batched CG. */
 int femPIC_batch_timing(const FemPICBatch* b, double* times, int32_t n);
+/* Autotuner of the batch's launch shapes: advances every member by
+ * steps_per_candidate real steps per tuning round (results differ from
+ * untuned steps only in the order of floating-point atomic sums), timing the
+ * batched particle kernel and the batched CG with CUDA events under each
+ * candidate: particle kernel CTAs of 128 or 256 threads (= particles per work
+ * block), 1 .. max co-resident CTAs per SM or one CTA per work block; CG
+ * CTAs per SM from 1 (as long as every member gets one) to the co-resident
+ * maximum.  Rounds = the larger candidate count (the shorter list cycles);
+ * the fastest mean of each kernel is kept, and the next femPIC_batch_step
+ * captures its CUDA graph with it.  dt_host as femPIC_batch_step.  out
+ * (nullable) receives the choice, the candidate counts, the steps taken and
+ * the kernels' mean device ms per step chosen and at the creation-time
+ * default (256 threads, max co-resident CTAs; CG at its co-resident maximum). */
+typedef struct {
+  int32_t particle_block, particle_grid, cg_ctas_per_sm;
+  int32_t particle_candidates, cg_candidates, steps;
+  double particle_ms, cg_ms;                 /* chosen, mean per step          */
+  double particle_ms_default, cg_ms_default; /* creation-time shapes           */
+} femPIC_batch_tuning;
+int femPIC_batch_autotune(FemPICBatch* b, const double* dt_host, int32_t steps_per_candidate,
+                          femPIC_batch_tuning* out);
 void femPIC_batch_destroy(FemPICBatch* b);
 const char* femPIC_batch_last_error(const FemPICBatch* b);
 

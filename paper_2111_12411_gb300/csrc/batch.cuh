@@ -74,7 +74,9 @@ struct MemberDesc {
 struct BatchWork {
   int32_t n;                // members
   MemberDesc* d;            // [n]
-  const int32_t* pblk;      // [n+1] particle work blocks (256 particles)
+  const int32_t* pblk;      // [n+1] particle work blocks (256 particles) of the sort kernels
+  const int32_t* ppblk;     // [n+1] particle work blocks of the particle kernel (pbs particles)
+  int32_t pbs;              // particles per work block of the particle kernel = its CTA size
   const int32_t* tblk;      // [n+1] tet tiles (1024 tets)
   const int32_t* r1blk;     // [n+1] W1 row blocks (32 rows: 8 lanes per row)
   const int32_t* r2blk;     // [n+1] W2 row blocks (64 rows: 4 lanes per row)
@@ -277,13 +279,14 @@ __device__ __forceinline__ ParticleArgs member_particle_args(const MemberDesc& d
 }
 
 // persistent: CTAs loop over the particle work blocks of all members
+// (CTA size w.pbs and grid picked by the batch's autotuner)
 __global__ void __launch_bounds__(256, 2) k_batch_particles(BatchWork w) {
-  const int total = __ldg(w.pblk + w.n);
+  const int total = __ldg(w.ppblk + w.n);
   for (int wb = blockIdx.x; wb < total; wb += gridDim.x) {
-    const int m = member_of(w.pblk, w.n, wb);
+    const int m = member_of(w.ppblk, w.n, wb);
     const MemberDesc& d = w.d[m];
     const ParticleArgs a = member_particle_args(d);
-    const int64_t i = (int64_t)(wb - __ldg(w.pblk + m)) * 256 + threadIdx.x;
+    const int64_t i = (int64_t)(wb - __ldg(w.ppblk + m)) * w.pbs + threadIdx.x;
     if (d.order == 1) {
       if (d.mixed)
         particle_step<1, (bool)FEMPIC_PARTICLE_AGG, true>(a, i);

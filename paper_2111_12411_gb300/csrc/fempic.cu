@@ -1785,6 +1785,14 @@ struct FemPICBatch {
   int launches_per_step = 0;
   bool used_graph = false;
   std::vector<void*> allocs;
+  // launch shapes picked by femPIC_batch_autotune: CTA size and grid of the
+  // particle kernel (work-block tables for 128 and 256 particles), CTAs per SM
+  // of the cooperative CG; events around those two kernels while tuning
+  int32_t *ppblk128 = nullptr, *ppblk256 = nullptr;
+  int part_block = 256, part_grid = 0, cg_per_sm = 0, cg_max_per_sm = 0;
+  std::vector<int64_t> wnnz;
+  bool time_kernels = false, tuning = false;
+  cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -1922,11 +1930,36 @@ std::vector<int32_t> prefix_blocks(const std::vector<int64_t>& work, int64_t per
   return p;
 }
 
+// CTAs of the block-diagonal CG: per_sm per SM, each member at least one and
+// the rest in proportion to its matrix entries
+int set_cg_grid(FemPICBatch* b, int per_sm) {
+  const int n = (int)b->m.size();
+  b->cg_per_sm = per_sm;
+  b->cg_grid = per_sm * b->num_sms;
+  std::vector<int32_t> pc(n + 1, 0);
+  double tot = 0;
+  for (auto v : b->wnnz) tot += (double)v;
+  const int spare = b->cg_grid - n;
+  std::vector<int32_t> cnt(n, 1);
+  int used = 0;
+  for (int i = 0; i < n; ++i) {
+    const int extra = tot > 0 ? (int)std::floor(spare * (double)b->wnnz[i] / tot) : 0;
+    cnt[i] += extra;
+    used += extra;
+  }
+  for (int i = 0; used < spare; i = (i + 1) % n, ++used) cnt[i]++;
+  for (int i = 0; i < n; ++i) pc[i + 1] = pc[i] + cnt[i];
+  BCK(cudaMemcpy(b->cgblk, pc.data(), pc.size() * 4, cudaMemcpyHostToDevice));
+  return FEMPIC_OK;
+}
+
 BatchWork batch_work(FemPICBatch* b) {
   BatchWork w;
   w.n = (int32_t)b->m.size();
   w.d = b->dd;
   w.pblk = b->pblk;
+  w.ppblk = b->part_block == 128 ? b->ppblk128 : b->ppblk256;
+  w.pbs = b->part_block;
   w.tblk = b->tblk;
   w.r1blk = b->r1blk;
   w.r2blk = b->r2blk;
@@ -1955,7 +1988,9 @@ int batch_launch_step(FemPICBatch* b, int max_it_all) {
   k_batch_scan_add<<<b->total_tiles, 1024, 0, s>>>(w);
   k_batch_scatter<<<pg, 256, 0, s>>>(w);
   k_batch_swap_particles<<<g1, 128, 0, s>>>(w);
-  k_batch_particles<<<pg, 256, 0, s>>>(w);
+  if (b->time_kernels) BCK(cudaEventRecord(b->kev[0], s));
+  k_batch_particles<<<b->part_grid, b->part_block, 0, s>>>(w);
+  if (b->time_kernels) BCK(cudaEventRecord(b->kev[1], s));
   BCK(cudaGetLastError());
   BCK(cudaEventRecord(b->ev[1], s));
   k_batch_guess<<<pg, 256, 0, s>>>(w);
@@ -1965,7 +2000,9 @@ int batch_launch_step(FemPICBatch* b, int max_it_all) {
   int kc = 1;
   for (FemPIC* h : b->m) kc = std::max(kc, h->cheb_k);
   void* args[] = {&w, &max_it_all, &kc};
+  if (b->time_kernels) BCK(cudaEventRecord(b->kev[2], s));
   BCK(cudaLaunchCooperativeKernel((void*)k_batch_pcg, b->cg_grid, 256, args, 0, s));
+  if (b->time_kernels) BCK(cudaEventRecord(b->kev[3], s));
   k_batch_bupdate<<<pg, 256, 0, s>>>(w);
   k_batch_end<<<g1, 128, 0, s>>>(w);
   BCK(cudaGetLastError());
@@ -2044,44 +2081,35 @@ int femPIC_batch_create(FemPIC* const* members, int32_t n, FemPICBatch** out) {
   b->total_tiles = pt.back();
   int per_sm = 0;
   BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_pcg, 256, 0));
-  b->cg_grid = std::max(1, per_sm) * b->num_sms;
-  if (b->cg_grid < n) {
+  b->cg_max_per_sm = std::max(1, per_sm);
+  if (b->cg_max_per_sm * b->num_sms < n) {
     b->err = "more members than co-resident CTAs for the batched CG";
     return FEMPIC_ERR_ARG;
   }
-  // CTAs of the block-diagonal CG in proportion to each member's matrix entries
-  std::vector<int32_t> pc(n + 1, 0);
-  {
-    double tot = 0;
-    for (auto v : wnnz) tot += (double)v;
-    int spare = b->cg_grid - n;
-    std::vector<int32_t> cnt(n, 1);
-    int used = 0;
-    for (int i = 0; i < n; ++i) {
-      int extra = (int)std::floor(spare * (double)wnnz[i] / tot);
-      cnt[i] += extra;
-      used += extra;
-    }
-    for (int i = 0; used < spare; i = (i + 1) % n, ++used) cnt[i]++;
-    for (int i = 0; i < n; ++i) pc[i + 1] = pc[i] + cnt[i];
-  }
+  b->wnnz = wnnz;
   int per_sm_p = 0;
   BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_p, k_batch_particles, 256, 0));
   b->persist_grid = std::max(1, per_sm_p) * b->num_sms;
+  b->part_block = 256;
+  b->part_grid = b->persist_grid;
+  auto pp128 = prefix_blocks(wp, 128);
   int rc;
   if ((rc = balloc(b, &b->dd, n)) || (rc = balloc(b, &b->pblk, n + 1)) || (rc = balloc(b, &b->tblk, n + 1)) ||
       (rc = balloc(b, &b->r1blk, n + 1)) || (rc = balloc(b, &b->r2blk, n + 1)) || (rc = balloc(b, &b->zblk, n + 1)) ||
       (rc = balloc(b, &b->cgblk, n + 1)) || (rc = balloc(b, &b->tile_sums, b->total_tiles)) ||
-      (rc = balloc(b, &b->bar, 1)) || (rc = balloc(b, &b->partials, 8 * (size_t)b->cg_grid)) ||
-      (rc = balloc(b, &b->red, 12 * (size_t)(n + 1))) ||
-      (rc = balloc(b, &b->status, 1)))
+      (rc = balloc(b, &b->bar, 1)) ||
+      (rc = balloc(b, &b->partials, 8 * (size_t)b->cg_max_per_sm * b->num_sms)) ||
+      (rc = balloc(b, &b->red, 12 * (size_t)(n + 1))) || (rc = balloc(b, &b->ppblk128, n + 1)) ||
+      (rc = balloc(b, &b->ppblk256, n + 1)) || (rc = balloc(b, &b->status, 1)))
     return rc;
+  BCK(cudaMemcpy(b->ppblk128, pp128.data(), pp128.size() * 4, cudaMemcpyHostToDevice));
+  BCK(cudaMemcpy(b->ppblk256, pp.data(), pp.size() * 4, cudaMemcpyHostToDevice));
+  if ((rc = set_cg_grid(b, b->cg_max_per_sm))) return rc;
   BCK(cudaMemcpy(b->pblk, pp.data(), pp.size() * 4, cudaMemcpyHostToDevice));
   BCK(cudaMemcpy(b->tblk, pt.data(), pt.size() * 4, cudaMemcpyHostToDevice));
   BCK(cudaMemcpy(b->r1blk, p1.data(), p1.size() * 4, cudaMemcpyHostToDevice));
   BCK(cudaMemcpy(b->r2blk, p2.data(), p2.size() * 4, cudaMemcpyHostToDevice));
   BCK(cudaMemcpy(b->zblk, pz.data(), pz.size() * 4, cudaMemcpyHostToDevice));
-  BCK(cudaMemcpy(b->cgblk, pc.data(), pc.size() * 4, cudaMemcpyHostToDevice));
   BCK(cudaMemset(b->status, 0, sizeof(int32_t)));
   return FEMPIC_OK;
 }
@@ -2112,7 +2140,7 @@ int femPIC_batch_step(FemPICBatch* b, const double* dt, int32_t n_steps) {
   BCK(cudaMemcpyAsync(b->dd, b->hd.data(), sizeof(MemberDesc) * n, cudaMemcpyHostToDevice, b->stream));
   BCK(cudaEventRecord(b->ev[0], b->stream));
   // capture one step in a CUDA graph the first time; replay it n_steps times
-  if (!b->graph && !b->graph_failed && n_steps > 0) {
+  if (!b->graph && !b->graph_failed && !b->tuning && n_steps > 0) {
     cudaGraph_t g = nullptr;
     bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     int rc = ok ? batch_launch_step(b, max_it_all) : FEMPIC_ERR_CUDA;
@@ -2190,11 +2218,103 @@ void femPIC_batch_destroy(FemPICBatch* b) {
   for (void* p : b->allocs) cudaFree(p);
   for (auto e : b->ev)
     if (e) cudaEventDestroy(e);
+  for (auto e : b->kev)
+    if (e) cudaEventDestroy(e);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
 
 const char* femPIC_batch_last_error(const FemPICBatch* b) { return b ? b->err.c_str() : "NULL batch"; }
+
+int femPIC_batch_autotune(FemPICBatch* b, const double* dt, int32_t steps_per_candidate, femPIC_batch_tuning* out) {
+  if (!b || !b->stream || !dt || steps_per_candidate < 1) return FEMPIC_ERR_ARG;
+  BCK(cudaSetDevice(b->device));
+  const int n = (int)b->m.size();
+  // candidates: particle kernel CTA size x CTAs per SM (persistent) or one CTA
+  // per work block; CG CTAs per SM that still give every member one CTA
+  struct PartCfg {
+    int block, grid;
+  };
+  std::vector<PartCfg> pcs;
+  int64_t np_total = 0;
+  for (FemPIC* h : b->m) np_total += h->np;
+  for (int block : {128, 256}) {
+    int per_sm = 0;
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_particles, block, 0));
+    for (int k = 1; k <= std::max(1, per_sm); ++k) pcs.push_back({block, k * b->num_sms});
+    int64_t blocks = 0;
+    for (FemPIC* h : b->m) blocks += (h->np + block - 1) / block;
+    if (blocks > (int64_t)std::max(1, per_sm) * b->num_sms) pcs.push_back({block, (int)std::min<int64_t>(blocks, 1 << 30)});
+  }
+  std::vector<int> ccs;
+  for (int k = 1; k <= b->cg_max_per_sm; ++k)
+    if (k * b->num_sms >= n) ccs.push_back(k);
+  const int def_block = b->part_block, def_grid = b->part_grid, def_cg = b->cg_per_sm;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->graph_failed = false;
+  for (auto& e : b->kev)
+    if (!e) BCK(cudaEventCreate(&e));
+  b->tuning = b->time_kernels = true;
+  std::vector<double> pt(pcs.size(), 0.0), ct(ccs.size(), 0.0);
+  std::vector<int> pn(pcs.size(), 0), cn(ccs.size(), 0);
+  const size_t rounds = std::max(pcs.size(), ccs.size());
+  int rc = FEMPIC_OK;
+  for (size_t r = 0; r < rounds && !rc; ++r) {
+    const size_t ip = r % pcs.size(), ic = r % ccs.size();
+    b->part_block = pcs[ip].block;
+    b->part_grid = pcs[ip].grid;
+    if ((rc = set_cg_grid(b, ccs[ic]))) break;
+    for (int32_t k = 0; k < steps_per_candidate && !rc; ++k) {
+      rc = femPIC_batch_step(b, dt, 1);
+      if (rc) break;
+      float a = 0.f, c = 0.f;
+      if (cudaEventElapsedTime(&a, b->kev[0], b->kev[1]) != cudaSuccess ||
+          cudaEventElapsedTime(&c, b->kev[2], b->kev[3]) != cudaSuccess) {
+        b->err = "autotune: kernel timing failed";
+        rc = FEMPIC_ERR_CUDA;
+        break;
+      }
+      pt[ip] += a;
+      ct[ic] += c;
+      pn[ip]++;
+      cn[ic]++;
+    }
+  }
+  b->tuning = b->time_kernels = false;
+  if (rc) {
+    b->part_block = def_block;
+    b->part_grid = def_grid;
+    set_cg_grid(b, def_cg);
+    return rc;
+  }
+  size_t bp = 0, bc = 0;
+  for (size_t i = 0; i < pcs.size(); ++i)
+    if (pt[i] / pn[i] < pt[bp] / pn[bp]) bp = i;
+  for (size_t i = 0; i < ccs.size(); ++i)
+    if (ct[i] / cn[i] < ct[bc] / cn[bc]) bc = i;
+  b->part_block = pcs[bp].block;
+  b->part_grid = pcs[bp].grid;
+  if ((rc = set_cg_grid(b, ccs[bc]))) return rc;
+  if (out) {
+    memset(out, 0, sizeof(*out));
+    out->particle_block = pcs[bp].block;
+    out->particle_grid = pcs[bp].grid;
+    out->cg_ctas_per_sm = ccs[bc];
+    out->particle_candidates = (int32_t)pcs.size();
+    out->cg_candidates = (int32_t)ccs.size();
+    out->steps = (int32_t)(rounds * steps_per_candidate);
+    out->particle_ms = pt[bp] / pn[bp];
+    out->cg_ms = ct[bc] / cn[bc];
+    for (size_t i = 0; i < pcs.size(); ++i)
+      if (pcs[i].block == def_block && pcs[i].grid == def_grid) out->particle_ms_default = pt[i] / pn[i];
+    for (size_t i = 0; i < ccs.size(); ++i)
+      if (ccs[i] == def_cg) out->cg_ms_default = ct[i] / cn[i];
+  }
+  return FEMPIC_OK;
+}
 
 }  // extern "C"
 

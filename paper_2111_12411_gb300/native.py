@@ -72,6 +72,14 @@ class femPIC_info(ctypes.Structure):
 
 # (name, restype, argtypes) of every exported symbol declared in include/fempic.h
 _P = ctypes.c_void_p
+class femPIC_batch_tuning(ctypes.Structure):
+    _fields_ = [("particle_block", ctypes.c_int32), ("particle_grid", ctypes.c_int32),
+                ("cg_ctas_per_sm", ctypes.c_int32), ("particle_candidates", ctypes.c_int32),
+                ("cg_candidates", ctypes.c_int32), ("steps", ctypes.c_int32),
+                ("particle_ms", ctypes.c_double), ("cg_ms", ctypes.c_double),
+                ("particle_ms_default", ctypes.c_double), ("cg_ms_default", ctypes.c_double)]
+
+
 class femPIC_injector(ctypes.Structure):
     _fields_ = [("species", ctypes.c_int32), ("v_drift", ctypes.c_double * 3), ("v_sigma", ctypes.c_double * 3)]
 
@@ -112,6 +120,7 @@ EXPORTS = [
     ("femPIC_batch_create", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
     ("femPIC_batch_step", ctypes.c_int, [_P, _P, ctypes.c_int32]),
     ("femPIC_batch_timing", ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    ("femPIC_batch_autotune", ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(femPIC_batch_tuning)]),
     ("femPIC_batch_destroy", None, [_P]),
     ("femPIC_batch_last_error", ctypes.c_char_p, [_P]),
 ]
@@ -472,6 +481,15 @@ def femPIC_batch_timing(b):
     return dict(zip(("ms", "launches_per_step", "graph", "cg_ctas"), t.tolist()))
 
 
+def femPIC_batch_autotune(b, dts, steps_per_candidate=2):
+    dts = np.ascontiguousarray(dts, dtype=np.float64)
+    t = femPIC_batch_tuning()
+    rc = load().femPIC_batch_autotune(b, _ptr(dts), int(steps_per_candidate), ctypes.byref(t))
+    if rc != FEMPIC_OK:
+        raise FemPICError(rc, femPIC_batch_last_error(b))
+    return {k: getattr(t, k) for k, _ in femPIC_batch_tuning._fields_}
+
+
 def femPIC_batch_destroy(b):
     if b is not None and b.value:
         load().femPIC_batch_destroy(b)
@@ -493,6 +511,10 @@ class Batch:
 
     def timing(self):
         return femPIC_batch_timing(self.b)
+
+    def autotune(self, dts, steps_per_candidate=2):
+        """Pick the launch shapes of the batched kernels by timing real steps."""
+        return femPIC_batch_autotune(self.b, dts, steps_per_candidate)
 
     def close(self):
         femPIC_batch_destroy(self.b)

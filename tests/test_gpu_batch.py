@@ -75,3 +75,32 @@ def test_batch_conserves_charge_per_member():
     batch.close()
     for s in sims:
         s.close()
+
+
+def test_autotune_picks_a_candidate_and_keeps_results():
+    """The autotuner advances the members by real steps under each launch
+    shape; afterwards the batch (now replaying a graph of the chosen shapes)
+    still gives each member's state alone, to the tolerances above."""
+    from paper_2111_12411_gb300 import Batch, Simulation
+    cfgs = _instances()[:4]
+    alone = [Simulation.from_config(c) for c in cfgs]
+    mixed = [Simulation.from_config(c) for c in cfgs]
+    batch = Batch(mixed)
+    dts = np.array([c["dt"] for c in cfgs])
+    t = batch.autotune(dts, steps_per_candidate=1)
+    assert t["particle_block"] in (128, 256) and t["particle_grid"] > 0
+    assert 1 <= t["cg_ctas_per_sm"] and t["particle_candidates"] >= 3 and t["cg_candidates"] >= 1
+    assert t["steps"] == max(t["particle_candidates"], t["cg_candidates"])
+    assert 0 < t["particle_ms"] <= t["particle_ms_default"] and 0 < t["cg_ms"] <= t["cg_ms_default"]
+    batch.step(dts, 2)
+    assert batch.timing()["graph"] == 1.0
+    for s, c in zip(alone, cfgs):
+        s.step(c["dt"], t["steps"] + 2)
+    for k, (a, m, c) in enumerate(zip(alone, mixed, cfgs)):
+        tol = 2e-6 if c["precision"] == "mixed" else 1e-9
+        assert rel(m.get("X"), a.get("X")) < tol, k
+        assert rel(m.get("V"), a.get("V")) < tol, k
+        assert rel(m.get("E"), a.get("E")) < 1e-6, k
+    batch.close()
+    for s in alone + mixed:
+        s.close()
