@@ -203,6 +203,10 @@ typedef struct {
   double crossings;         /* face crossings in the last step (all particles) */
   double absorbed;          /* particles absorbed on walls (and re-injected) by the
                                last femPIC_step call, all its steps           */
+  double divb_abs;          /* Gauss's magnetic law of b (+ the impressed part):
+                               ||m||_2, m_ti = sign(det J_t) int_ref W3_i div W2 . b
+                               per tet (zero iff div b = 0)                    */
+  double divb_ref;          /* the size of the terms of m: || sum_j |.| ||_2    */
 } femPIC_diag;
 
 typedef struct {

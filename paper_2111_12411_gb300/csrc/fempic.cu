@@ -135,7 +135,9 @@ struct FemPIC {
   int32_t* d_status = nullptr;
   int32_t* d_cg_iters = nullptr;
   double* d_cg_res = nullptr;
-  double* d_norms = nullptr;  // [4]: continuity abs^2, ref^2, gauss abs^2, ref^2
+  double* d_norms = nullptr;  // [6]: continuity abs^2, ref^2, gauss abs^2, ref^2, div b abs^2, ref^2
+  double* divref = nullptr;   // [n3][nl2] int_ref W3_i div W2_j (div b diagnostic)
+  int32_t n3 = 0;
   unsigned long long* d_cross = nullptr;
   double* d_tmp1 = nullptr;  // N1 scratch
   double* d_tmp0 = nullptr;  // N0 scratch
@@ -765,7 +767,7 @@ int field_update(FemPIC* h, double dt, cudaEvent_t ev_pcg0, cudaEvent_t ev_pcg1)
 
 int diagnostics(FemPIC* h) {
   // continuity: (rho - rho_prev) - D^T dg ; Gauss: D^T M e + rho + rho_ion load
-  CK(cudaMemsetAsync(h->d_norms, 0, sizeof(double) * 4, h->stream));
+  CK(cudaMemsetAsync(h->d_norms, 0, sizeof(double) * 6, h->stream));
   int rc = spmv(h, h->DT.view(), h->dg, h->d_tmp0);
   if (rc) return rc;
   int grid = grid_for(h->n0, 256, h->num_sms * 8);
@@ -778,6 +780,15 @@ int diagnostics(FemPIC* h) {
   if (rc) return rc;
   k_norms2<<<grid, 256, 0, h->stream>>>(h->n0, h->int0, h->rho, nullptr, h->d_tmp0, 1.0, h->opts.rho_ion, h->load0,
                                         h->d_norms + 2);
+  h->launches++;
+  // Gauss's magnetic law of the flux the particles see (self plus impressed)
+  const int gt = grid_for(h->n_tets, 256, h->num_sms * 8);
+  if (h->order == 1)
+    k_divb<1><<<gt, 256, 0, h->stream>>>(h->n_tets, h->geom, h->dof2, b_gather(h), h->divref, h->n3, h->d_norms + 4);
+  else if (h->order == 2)
+    k_divb<2><<<gt, 256, 0, h->stream>>>(h->n_tets, h->geom, h->dof2, b_gather(h), h->divref, h->n3, h->d_norms + 4);
+  else
+    k_divb<3><<<gt, 256, 0, h->stream>>>(h->n_tets, h->geom, h->dof2, b_gather(h), h->divref, h->n3, h->d_norms + 4);
   h->launches++;
   CK(cudaGetLastError());
   return FEMPIC_OK;
@@ -988,7 +999,7 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
   if (what == FEMPIC_DIAG) {
     femPIC_diag d;
     memset(&d, 0, sizeof(d));
-    double norms[4];
+    double norms[6];
     CK(cudaMemcpyAsync(norms, h->d_norms, sizeof(norms), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(&d.cg_iterations, h->d_cg_iters, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(&d.cg_residual, h->d_cg_res, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -1002,6 +1013,8 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
     d.continuity_ref = std::sqrt(norms[1]);
     d.gauss_abs = std::sqrt(norms[2]);
     d.gauss_ref = std::sqrt(norms[3]);
+    d.divb_abs = std::sqrt(norms[4]);
+    d.divb_ref = std::sqrt(norms[5]);
     d.crossings = (double)cr;
     d.absorbed = (double)nab;
     if (buf_on_device)
@@ -1328,7 +1341,7 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
   if ((rc = dalloc(h, &h->partials, 8 * (size_t)h->pcg_blocks_w1)) || (rc = dalloc(h, &h->bar, 1)) ||
       (rc = dalloc(h, &h->d_status, 1)) || (rc = dalloc(h, &h->d_cg_iters, 1)) || (rc = dalloc(h, &h->d_cg_res, 1)) ||
       (rc = dalloc(h, &h->d_cg_iters_acc, 1)) ||
-      (rc = dalloc(h, &h->d_norms, 4)) || (rc = dalloc(h, &h->d_cross, 1)))
+      (rc = dalloc(h, &h->d_norms, 6)) || (rc = dalloc(h, &h->d_cross, 1)))
     return rc;
   for (void* p : std::vector<void*>{h->e, h->e_prev, h->e_new, h->dg, h->dg_prev})
     CK(cudaMemset(p, 0, sizeof(double) * h->n1));
@@ -1355,6 +1368,13 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
       (rc = dalloc(h, &h->sort_sums, (h->n_tets + 1023) / 1024 + 1)) ||
       (rc = dalloc(h, &h->sort_sums2, (h->n_tets + 1023) / 1024 / 1024 + 2)))
     return rc;
+  {
+    std::vector<double> dref;
+    int n3 = 0;
+    div_table(order, &dref, &n3);
+    h->n3 = n3;
+    if ((rc = upload(h, &h->divref, dref))) return rc;
+  }
   if ((rc = dalloc(h, &h->d_absorbed, 1))) return rc;
   CK(cudaMemset(h->d_absorbed, 0, sizeof(unsigned long long)));
   if (h->n_absorb_faces > 0 && (rc = dalloc(h, &h->pabs, n))) return rc;

@@ -93,6 +93,10 @@ struct ProjModel {
   HostCSR Asm;                   // N2 x (nt nl2): sums per-tet load vectors into global DOFs
 };
 
+// Exact table Dref [n3][nl2] = int_ref W3_i div W2_j of the order-p volume
+// functions against the W2 divergences on the reference tet (a physical tet's
+// [~div] block is sign(det J) Dref).
+void div_table(int order, std::vector<double>* Dref, int* n3);
 // The load's quadrature on the reference tet: conical product of (p + 3)-point
 // Gauss-Legendre rules, x = u, y = (1-u) v, z = (1-u)(1-v) w, Jacobian
 // (1-u)^2 (1-v); exact for total degree 2p + 3.  Fills nq, qlam, qw.

@@ -89,6 +89,48 @@ __global__ void __launch_bounds__(128) k_w2_load(int32_t nt, int32_t nq, const d
   }
 }
 
+// Divergence diagnostic of a W2 field b: per tet the moments of div b against
+// the order-p volume functions, m_i = s_t sum_j Dref[i][j] b_j (s_t the sign
+// of det J; the W3 span every degree p-1 polynomial, so m = 0 iff div b = 0 on
+// the tet), and the size of their terms a_i = sum_j |Dref[i][j] b_j|:
+// out[0] += sum m_i^2, out[1] += sum a_i^2 (the norms the caller compares).
+template <int P>
+__global__ void __launch_bounds__(256) k_divb(int32_t nt, const double* __restrict__ geom,
+                                              const int32_t* __restrict__ dof2, const double* __restrict__ b,
+                                              const double* __restrict__ dref, int32_t n3, double* out) {
+  constexpr int N2 = Nloc<P>::n2;
+  double s0 = 0.0, s1 = 0.0;
+  for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    const double* g = geom + (size_t)t * 16;
+    const double det = g[3] * (g[7] * g[11] - g[8] * g[10]) - g[4] * (g[6] * g[11] - g[8] * g[9]) +
+                       g[5] * (g[6] * g[10] - g[7] * g[9]);
+    const double sg = det > 0.0 ? 1.0 : -1.0;
+    double bv[N2];
+#pragma unroll
+    for (int j = 0; j < N2; ++j) bv[j] = __ldg(b + __ldg(dof2 + (size_t)t * N2 + j));
+    for (int32_t i = 0; i < n3; ++i) {
+      double m = 0.0, a = 0.0;
+#pragma unroll
+      for (int j = 0; j < N2; ++j) {
+        const double v = __ldg(dref + (size_t)i * N2 + j) * bv[j];
+        m += v;
+        a += fabs(v);
+      }
+      s0 += (sg * m) * (sg * m);
+      s1 += a * a;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(out, s0);
+    atomicAdd(out + 1, s1);
+  }
+}
+
 // sum over the block (fixed shuffle tree, then warps in order); valid in thread 0
 __device__ __forceinline__ double block_sum(double v, double* sh) {
 #pragma unroll

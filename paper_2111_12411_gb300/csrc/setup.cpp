@@ -1324,27 +1324,32 @@ void projection_rule(int p, ProjModel* out) {
       }
 }
 
-std::string build_projection(int p, int32_t nt, int32_t nf, int32_t n2, const double* xyz,
-                             const int32_t* tets, const int32_t* dof2, const HostCSR& M2, ProjModel* out) {
+void div_table(int p, std::vector<double>* Dref, int* n3_out) {
   const int nl2 = nloc2(p);
-  // exact local table: Dref[i][j] = int_ref W3_i div W2_j
   auto f3 = w3_forms(p);
   auto f2 = w2_forms(p);
   const int n3 = (int)f3.size();
-  std::vector<double> Dref((size_t)n3 * nl2, 0.0);
-  {
-    std::vector<Poly> div2;
-    for (auto& f : f2) {
-      Vec v = w2_xyz(f);
-      div2.push_back(padd(padd(deriv(v[0], 0), deriv(v[1], 1)), deriv(v[2], 2)));
-    }
-    for (int i = 0; i < n3; ++i) {
-      // int over the reference tet of x^a y^b z^c = a! b! c! / (a+b+c+3)!: the
-      // barycentric formula with the fourth exponent 0
-      Poly w = to_xyz(f3[i]);
-      for (int j = 0; j < nl2; ++j) Dref[(size_t)i * nl2 + j] = to_double(integrate_bary(pmul(w, div2[j])));
-    }
+  Dref->assign((size_t)n3 * nl2, 0.0);
+  std::vector<Poly> div2;
+  for (auto& f : f2) {
+    Vec v = w2_xyz(f);
+    div2.push_back(padd(padd(deriv(v[0], 0), deriv(v[1], 1)), deriv(v[2], 2)));
   }
+  for (int i = 0; i < n3; ++i) {
+    // int over the reference tet of x^a y^b z^c = a! b! c! / (a+b+c+3)!: the
+    // barycentric formula with the fourth exponent 0
+    Poly w = to_xyz(f3[i]);
+    for (int j = 0; j < nl2; ++j) (*Dref)[(size_t)i * nl2 + j] = to_double(integrate_bary(pmul(w, div2[j])));
+  }
+  *n3_out = n3;
+}
+
+std::string build_projection(int p, int32_t nt, int32_t nf, int32_t n2, const double* xyz,
+                             const int32_t* tets, const int32_t* dof2, const HostCSR& M2, ProjModel* out) {
+  const int nl2 = nloc2(p);
+  int n3 = 0;
+  std::vector<double> Dref;
+  div_table(p, &Dref, &n3);
   out->n3 = n3;
   projection_rule(p, out);
   // per-tet orientation and volume: sign(det J) and 6|V|, J = [x1-x0, x2-x0, x3-x0]

@@ -53,7 +53,8 @@ class femPIC_diag(ctypes.Structure):
                 ("cg_iterations", ctypes.c_int32), ("cg_residual", ctypes.c_double),
                 ("continuity_abs", ctypes.c_double), ("continuity_ref", ctypes.c_double),
                 ("gauss_abs", ctypes.c_double), ("gauss_ref", ctypes.c_double),
-                ("crossings", ctypes.c_double), ("absorbed", ctypes.c_double)]
+                ("crossings", ctypes.c_double), ("absorbed", ctypes.c_double),
+                ("divb_abs", ctypes.c_double), ("divb_ref", ctypes.c_double)]
 
 
 class femPIC_info(ctypes.Structure):

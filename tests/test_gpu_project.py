@@ -125,3 +125,25 @@ def test_projection_errors_and_batch_rejection():
     with pytest.raises(FemPICError):
         Batch([g])
     g.close()
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_divb_diagnostic(order):
+    """The library's Gauss's-magnetic-law diagnostic equals ||[~div] b|| of
+    the oracle's operator (rel 1e-12), and a divergence-free b stays so under
+    the Faraday update (the curl map's range is divergence free)."""
+    g, t, gg, c, vol, x, tet = _setup(order)
+    S3, Dv, M2 = project.matrices(t, gg, vol)
+    b = workloads.random_dof_vector(t.n2, 1e-4, np.random.default_rng(11))
+    g.set("B", b)
+    g.step(5e-8)
+    d = g.diag()
+    want = np.linalg.norm(Dv @ g.get("B"))
+    assert abs(d["divb_abs"] - want) <= 1e-12 * want
+    assert d["divb_ref"] >= d["divb_abs"]
+    bf = project.project(t, gg, vol, _quad, constrained=True)
+    g.set("B", bf)
+    g.step(5e-8)
+    d = g.diag()
+    assert d["divb_ref"] > 0 and d["divb_abs"] <= 1e-12 * d["divb_ref"]
+    g.close()
