@@ -371,3 +371,23 @@ def test_checkpoint_resume(c1small):
     assert rel(b.get("RHO"), a.get("RHO")) < 1e-12
     a.close()
     b.close()
+
+
+def test_gauss_law_over_ten_thousand_steps():
+    """Gauss's law carried over 10^4 steps of the 6^3 box (10^4 electrons,
+    p = 1): the residual may grow only by D^T of each step's CG residual
+    (rtol 1e-12), i.e. at most linearly; continuity holds to 1e-12 on the
+    sampled steps."""
+    from paper_2111_12411_gb300 import Simulation
+    cfg = workloads.make_config(0)
+    g = Simulation.from_config(cfg, diagnostics=True)
+    worst = 0.0
+    for k in range(20):
+        g.step(cfg["dt"], 500)
+        d = g.diag()
+        assert d["continuity_abs"] <= 1e-12 * d["continuity_ref"]
+        worst = max(worst, d["gauss_abs"] / d["gauss_ref"])
+        assert d["gauss_abs"] <= 1e-10 * 500 * (k + 1) * d["gauss_ref"]
+    assert d["steps"] == 10_000
+    print(f"Gauss residual after 1e4 steps: {d['gauss_abs'] / d['gauss_ref']:.3e} (max sampled {worst:.3e})")
+    g.close()
