@@ -107,6 +107,11 @@ struct FemPIC {
   // PEC faces), its Laplacian L_a = D_a^T ([*eps] + c_I [*_I]) D_a formed when
   // dt changes (values LA.v + c_I LAI in LAdt), FP32 copies, Chebyshev
   // coefficients, host copies for the eigenvalue bound
+  // order 3: block Jacobi of A over the W1 DOF groups (edge, face, interior)
+  int32_t n_groups = 0;
+  int32_t* gstart = nullptr;
+  uint8_t* gsize = nullptr;
+  DevCSR Bg;
   DevCSR DA, DAT, LA;
   double *LAI = nullptr, *LAdt = nullptr, *dinvLA = nullptr;
   float *DA32 = nullptr, *DAT32 = nullptr, *LA32 = nullptr, *dinvLA32 = nullptr;
@@ -390,6 +395,7 @@ int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, 
   a.cheb_k = nodal ? h->cheb_k : 1;
   memcpy(a.chebL, imp ? h->chebLA : h->chebL, sizeof(a.chebL));
   memcpy(a.chebV, h->chebV, sizeof(a.chebV));
+  a.Bg = (nodal && h->Bg.nnz > 0) ? h->Bg.view() : CsrView{0, nullptr, nullptr, nullptr};
   a.Ab = (nodal && h->nb > 0) ? BsrView{h->nb, h->brp, h->bci, h->bA} : BsrView{0, nullptr, nullptr, nullptr};
   a.q32 = h->cg_q32;
   a.r32 = h->cg_r32;
@@ -467,6 +473,12 @@ int form_system(FemPIC* h, double dt) {
     k_form_blocks<<<grid_for(h->nb, 256, 1 << 30), 256, 0, h->stream>>>(h->nb, h->brp, h->bci, h->bM, h->bK, c1,
                                                                         h->bA, h->binv, h->bI, ci_imp);
     h->launches++;
+  }
+  if (h->Bg.nnz > 0) {
+    k_group_inverse<<<grid_for(h->n_groups, 128, 1 << 30), 128, 0, h->stream>>>(
+        h->n_groups, h->gstart, h->gsize, h->M.view(h->Aval), h->Bg.rp, h->Bg.v);
+    h->launches++;
+    CK(cudaGetLastError());
   }
   if (h->LA.nnz > 0) {
     // L_a = D_a^T ([*eps] + dt/2 [*_I]) D_a: the gradients of W0 on impedance faces see the boundary term
@@ -1281,6 +1293,34 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
   }
   const size_t nnz = hm.M.col.size();
   if (!hm.Ival.empty() && (rc = upload(h, &h->Iv, hm.Ival))) return rc;
+  if (order == 3) {
+    // W1 DOF groups, contiguous: 3 per edge, 6 per face, 3 per tet interior
+    std::vector<int32_t> gs, rp(1, 0), ci;
+    std::vector<uint8_t> gz;
+    auto add = [&](int32_t start, int size) {
+      gs.push_back(start);
+      gz.push_back((uint8_t)size);
+      for (int r = 0; r < size; ++r) {
+        for (int c = 0; c < size; ++c) ci.push_back(start + c);
+        rp.push_back((int32_t)ci.size());
+      }
+    };
+    for (int32_t e = 0; e < hm.n_edges; ++e) add(3 * e, 3);
+    for (int32_t f = 0; f < hm.n_faces; ++f) add(3 * hm.n_edges + 6 * f, 6);
+    for (int32_t t = 0; t < hm.n_tets; ++t) add(3 * hm.n_edges + 6 * hm.n_faces + 3 * t, 3);
+    if ((int32_t)rp.size() != hm.n1 + 1) {
+      h->err = "order-3 DOF groups do not cover the W1 DOFs";
+      return FEMPIC_ERR_ARG;
+    }
+    HostCSR bg;
+    bg.n_rows = bg.n_cols = hm.n1;
+    bg.rowptr = rp;
+    bg.col = ci;
+    bg.val.assign(ci.size(), 0.0);
+    h->n_groups = (int32_t)gs.size();
+    if ((rc = upload(h, &h->gstart, gs)) || (rc = upload(h, &h->gsize, gz)) || (rc = upload_csr(h, &h->Bg, bg)))
+      return rc;
+  }
   if (!hm.LA.col.empty()) {
     const size_t nl = hm.LA.col.size();
     if ((rc = upload_csr(h, &h->DA, hm.DA)) || (rc = upload_csr(h, &h->DAT, hm.DAT)) ||

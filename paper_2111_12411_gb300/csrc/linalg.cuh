@@ -202,6 +202,61 @@ __global__ void k_inv_diag(int32_t n, const int32_t* rp, const int32_t* ci, cons
   dinv[row] = diag != 0.0 ? 1.0 / diag : 0.0;
 }
 
+// Inverse of each diagonal block of A over a contiguous DOF group (at most 6
+// DOFs: the W1 DOFs of one edge, face or tet interior at order 3) by Cholesky,
+// written to the rows of Bg (each row holds its group's columns in order);
+// a group without a diagonal (PEC rows) gets zeros, a block that is not
+// numerically positive definite its diagonal inverse.
+constexpr int kMaxGroup = 6;
+__global__ void k_group_inverse(int32_t ng, const int32_t* __restrict__ gstart, const uint8_t* __restrict__ gsize,
+                                CsrView A, const int32_t* __restrict__ brp, double* __restrict__ bval) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ng) return;
+  const int s0 = gstart[g], n = gsize[g];
+  double B[kMaxGroup][kMaxGroup], L[kMaxGroup][kMaxGroup], X[kMaxGroup][kMaxGroup];
+  for (int r = 0; r < kMaxGroup; ++r)
+    for (int c = 0; c < kMaxGroup; ++c) B[r][c] = L[r][c] = X[r][c] = 0.0;
+  for (int r = 0; r < n; ++r)
+    for (int k = A.rp[s0 + r]; k < A.rp[s0 + r + 1]; ++k) {
+      const int c = A.ci[k] - s0;
+      if (c >= 0 && c < n) B[r][c] = A.v[k];
+    }
+  bool spd = B[0][0] > 0.0;
+  for (int j = 0; j < n && spd; ++j) {
+    double d = B[j][j];
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+    if (!(d > 0.0)) {
+      spd = false;
+      break;
+    }
+    L[j][j] = sqrt(d);
+    for (int i = j + 1; i < n; ++i) {
+      double t = B[i][j];
+      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+      L[i][j] = t / L[j][j];
+    }
+  }
+  if (spd) {
+    for (int c = 0; c < n; ++c) {  // column c of B^-1 = L^-T L^-1 e_c
+      double y[kMaxGroup];
+      for (int i = 0; i < n; ++i) {
+        double t = i == c ? 1.0 : 0.0;
+        for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
+        y[i] = t / L[i][i];
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        double t = y[i];
+        for (int k = i + 1; k < n; ++k) t -= L[k][i] * X[k][c];
+        X[i][c] = t / L[i][i];
+      }
+    }
+  } else {
+    for (int r = 0; r < n; ++r) X[r][r] = B[r][r] != 0.0 ? 1.0 / B[r][r] : 0.0;
+  }
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) bval[brp[s0 + r] + c] = X[r][c];
+}
+
 // ---- persistent PCG ---------------------------------------------------------
 struct GridBarrier {
   unsigned int count;
@@ -277,6 +332,10 @@ struct PcgArgs {
   // diagonal blocks (block Jacobi); Ab.nb == 0 uses A and dinv
   BsrView Ab;
   const double* binv;
+  // order 3: inverses of A's diagonal blocks over the W1 DOFs of one edge, one
+  // face and one tet interior, as a CSR (rows of a group hold its columns);
+  // n_rows == 0 keeps the point Jacobi dinv
+  CsrView Bg;
   const int32_t* Apart;  // [gridDim.x + 1] per-CTA row ranges of A (block rows at order 2), or null
   const double* rhs;
   double* x;   // in: initial guess, out: solution
@@ -611,6 +670,11 @@ __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, co
         const int k = i >> 1, par = i & 1;
         double r0 = __ldcg(rvec + 2 * k), r1 = __ldcg(rvec + 2 * k + 1);
         zz = fma(__ldg(a.binv + 4 * k + 2 * par), r0, fma(__ldg(a.binv + 4 * k + 2 * par + 1), r1, (double)s));
+      } else if (a.Bg.n_rows > 0) {
+        double t = (double)s;
+        for (int k = __ldg(a.Bg.rp + i); k < __ldg(a.Bg.rp + i + 1); ++k)
+          t = fma(__ldg(a.Bg.v + k), __ldcg(rvec + __ldg(a.Bg.ci + k)), t);
+        zz = t;
       } else {
         zz = fma(__ldg(a.dinv + i), rr, (double)s);
       }

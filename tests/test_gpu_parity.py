@@ -391,3 +391,36 @@ def test_gauss_law_over_ten_thousand_steps():
     assert d["steps"] == 10_000
     print(f"Gauss residual after 1e4 steps: {d['gauss_abs'] / d['gauss_ref']:.3e} (max sampled {worst:.3e})")
     g.close()
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_cavity_mode_discrete_dispersion_on_gpu(order):
+    """The device field update against the trapezoidal rule's closed form: a
+    cavity eigenmode K v = w^2 M v of the PEC box, started from rest with no
+    particles, advances as cos(n Omega dt) with tan(Omega dt / 2) = w dt / 2
+    (amplitude to 1e-9: the CG stops at rel 1e-12)."""
+    import math
+    import scipy.linalg
+    from paper_2111_12411_gb300 import Simulation
+    from oracle import sim as osim
+    xyz, tets = workloads.kuhn_box(3, 3, 3, jitter=0.1, seed=9)
+    o = osim.Sim(xyz, tets, order, -1.6e-19, 9.1e-31, 1.0)
+    fr = np.nonzero(o.topo.free1)[0]
+    lam, vec = scipy.linalg.eigh(o.K[fr][:, fr].toarray(), o.M[fr][:, fr].toarray())
+    k = np.nonzero(lam > 1e-6 * lam.max())[0][0]
+    w = math.sqrt(lam[k])
+    v = np.zeros(o.topo.n1)
+    v[fr] = vec[:, k]
+    dt = 3.0 / w
+    Om = 2.0 * math.atan(w * dt / 2.0) / dt
+    g = Simulation(xyz, tets, order, -1.6e-19, 9.1e-31, 1.0, np.zeros((0, 3)), np.zeros((0, 3)),
+                   np.zeros(0, dtype=np.int32), es_init=False)
+    g.set("E", v)
+    g.set("E_PREV", v)
+    g.set("B", np.zeros(o.topo.n2))
+    vMv = v @ (o.M @ v)
+    for n in range(1, 8):
+        g.step(dt)
+        amp = (v @ (o.M @ g.get("E"))) / vMv
+        assert abs(amp - math.cos(n * Om * dt)) < 1e-9, (n, amp)
+    g.close()
