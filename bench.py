@@ -271,9 +271,16 @@ def run_native(args, rank, world, local_rank):
                 "traffic": traffic, "peak_source": peak_src + " of measured" if "measured" in peak_src else peak_src,
                 "bytes_per_launch": pcg_bytes, "cg_iterations_per_launch": iters,
                 "ms_per_launch": pcg_ms}
+    part_traffic = None
+    if os.path.exists(prof) and info.order == 2 and npart == 1_000_000 and args.precision == "fp64" \
+            and args.walls == "beam" and args.push == "boris":
+        try:
+            part_traffic = json.load(open(prof)).get("k_particle_fast_dram_bytes_per_launch")
+        except (OSError, ValueError):
+            part_traffic = None
     roof_part = {"kernel": "k_particle (gather, push, walk, deposit, charge)", "bound": "hbm",
                  "achieved": push_gbs, "peak": peak, "unit": "GB/s", "frac": push_gbs / peak,
-                 "traffic": None, "bytes_per_launch": pbytes, "ms_per_launch": push_ms,
+                 "traffic": part_traffic, "bytes_per_launch": pbytes, "ms_per_launch": push_ms,
                  "crossings_per_particle": cross_pp, "particles_per_occupied_tet": npart / occupied}
     # arithmetic roofline of the particle kernel: its FP64 thread instructions
     # (DFMA + DMUL + DADD, counted by ncu on this workload) per launch over the
