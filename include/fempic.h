@@ -130,9 +130,12 @@ enum {
   FEMPIC_DIAG = 11,    /* femPIC_diag (get only)                                */
   FEMPIC_PHI = 12,     /* double[N0]  potential of the electrostatic start (get) */
   FEMPIC_SPECIES = 13, /* int32[Np]   species index of each particle (get)      */
-  FEMPIC_B_IMPRESSED = 14 /* double[N2] W2 coefficients of an impressed flux
+  FEMPIC_B_IMPRESSED = 14, /* double[N2] W2 coefficients of an impressed flux
                           density (zeros when none is set): added to b wherever
                           the particles sample B, absent from the field update */
+  FEMPIC_J = 15          /* double[N1]  (g^n - g^{n-1}) / dt of the last step: the
+                          W1 moments <W1_i, J> of the current averaged over the
+                          step (get only; FEMPIC_ERR_STATE before the first step) */
 };
 
 /* ---- operators for femPIC_apply ----------------------------------------- */

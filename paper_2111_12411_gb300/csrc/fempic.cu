@@ -904,6 +904,7 @@ size_t what_bytes(const FemPIC* h, int32_t what) {
   switch (what) {
     case FEMPIC_E:
     case FEMPIC_DG:
+    case FEMPIC_J:
     case FEMPIC_E_PREV:
     case FEMPIC_DG_PREV:
       return sizeof(double) * (size_t)h->n1;
@@ -974,7 +975,7 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
   if (!h) return FEMPIC_ERR_ARG;
   size_t need = what_bytes(h, what);
   if (need == 0 || (to_handle && (what == FEMPIC_DIAG || what == FEMPIC_PHI || what == FEMPIC_NCROSS ||
-                                  what == FEMPIC_SPECIES ||
+                                  what == FEMPIC_SPECIES || what == FEMPIC_J ||
                                   what == FEMPIC_HASH))) {
     h->err = "unknown or read-only quantity";
     return FEMPIC_ERR_ARG;
@@ -1033,6 +1034,19 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
       CK(cudaMemcpy(buf, &d, sizeof(d), cudaMemcpyHostToDevice));
     else
       memcpy(buf, &d, sizeof(d));
+    return FEMPIC_OK;
+  }
+  if (what == FEMPIC_J) {  // Delta g / dt, scaled on the device into the scratch vector
+    if (h->dt_cur <= 0.0) {
+      h->err = "no current before the first step";
+      return FEMPIC_ERR_STATE;
+    }
+    k_lincomb<<<grid_for(h->n1, 256, h->num_sms * 8), 256, 0, h->stream>>>(h->n1, h->dg, h->dg, 1.0 / h->dt_cur, 0.0,
+                                                                           h->d_tmp1);
+    h->launches++;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(buf, h->d_tmp1, need, down, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     return FEMPIC_OK;
   }
   if (what == FEMPIC_B_IMPRESSED) {

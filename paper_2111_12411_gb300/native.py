@@ -22,7 +22,7 @@ PRECISION = {"fp64_strict": 0, "fp64": 1, "mixed": 2}
 SCHEME = {"trapezoid": 0, "wave": 1}
 PUSH = {"boris": 0, "ab4": 1}
 QUANTITY = {"E": 0, "B": 1, "DG": 2, "RHO": 3, "X": 4, "V": 5, "TET": 6, "NCROSS": 7, "HASH": 8,
-            "E_PREV": 9, "DG_PREV": 10, "DIAG": 11, "PHI": 12, "SPECIES": 13, "B_IMPRESSED": 14}
+            "E_PREV": 9, "DG_PREV": 10, "DIAG": 11, "PHI": 12, "SPECIES": 13, "B_IMPRESSED": 14, "J": 15}
 MAX_SPECIES = 8
 OPERATOR = {"M1": 0, "K": 1, "C": 2, "D": 3, "DT": 4, "M2": 5, "A": 6, "L": 7, "PI": 8, "PIT": 9}
 
@@ -381,7 +381,8 @@ class Simulation:
         i = self.info
         n1, n2, n0, npart = i.n1, i.n2, i.n0, self.n_particles
         return {"E": (n1, np.float64), "E_PREV": (n1, np.float64), "DG": (n1, np.float64),
-                "DG_PREV": (n1, np.float64), "B": (n2, np.float64), "B_IMPRESSED": (n2, np.float64),
+                "DG_PREV": (n1, np.float64), "J": (n1, np.float64), "B": (n2, np.float64),
+                "B_IMPRESSED": (n2, np.float64),
                 "RHO": (n0, np.float64),
                 "PHI": (n0, np.float64), "X": ((npart, 3), np.float64),
                 "V": ((npart, 3), np.float64), "TET": (npart, np.int32), "SPECIES": (npart, np.int32),

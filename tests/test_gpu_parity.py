@@ -424,3 +424,14 @@ def test_cavity_mode_discrete_dispersion_on_gpu(order):
         amp = (v @ (o.M @ g.get("E"))) / vMv
         assert abs(amp - math.cos(n * Om * dt)) < 1e-9, (n, amp)
     g.close()
+
+
+def test_current_quantity(c1small):
+    from paper_2111_12411_gb300 import FemPICError, Simulation
+    cfg = c1small
+    g = Simulation.from_config(cfg, es_init=False)
+    with pytest.raises(FemPICError):
+        g.get("J")
+    g.step(cfg["dt"])
+    assert np.allclose(g.get("J"), g.get("DG") / cfg["dt"], rtol=1e-15, atol=0.0)
+    g.close()
