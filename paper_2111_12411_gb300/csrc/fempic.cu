@@ -8,6 +8,7 @@
 //   -> k_bupdate: b^{n+1} = b^n - dt/2 C (e^{n+1} + e^n) -> [diagnostics]
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -815,6 +816,12 @@ cudaEvent_t event_at(FemPIC* h, size_t i) {
   return h->ev[i];
 }
 
+// NVTX range for profilers (a no-op without an attached tool)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 int do_steps(FemPIC* h, double dt, int32_t n) {
   if (!(dt > 0.0) || !std::isfinite(dt) || n < 0) {
     h->err = "dt must be positive and finite, n_steps >= 0";
@@ -847,6 +854,7 @@ int do_steps(FemPIC* h, double dt, int32_t n) {
       }
     }
     CK(cudaEventRecord(e[0], h->stream));
+    NvtxRange step_range("femPIC_step");
     if (h->opts.sort_period > 0 && h->since_sort >= h->opts.sort_period && h->opts.push != FEMPIC_PUSH_AB4) {
       int rc = sort_particles(h);
       if (rc) return rc;
@@ -857,10 +865,14 @@ int do_steps(FemPIC* h, double dt, int32_t n) {
     CK(cudaMemsetAsync(h->dg, 0, sizeof(double) * h->n1, h->stream));
     CK(cudaMemsetAsync(h->rho, 0, sizeof(double) * h->n0, h->stream));
     CK(cudaEventRecord(e[1], h->stream));
+    nvtxRangePushA("particles");
     int rc = launch_particles(h, dt);
+    nvtxRangePop();
     if (rc) return rc;
     CK(cudaEventRecord(e[2], h->stream));
+    nvtxRangePushA("field_update");
     rc = field_update(h, dt, e[3], e[4]);
+    nvtxRangePop();
     if (rc) return rc;
     CK(cudaEventRecord(e[5], h->stream));
     // rotate e: e_prev <- e, e <- e_new
