@@ -40,7 +40,7 @@ def _species(xyz, tets, rng, n_e=3001, n_i=1499):
             dict(q=Q_E, m=M_SR, weight=3e5, x=xi, v=workloads.maxwellian(n_i, 5e4, rng), tet=ti)]
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 @pytest.mark.parametrize("precision", ["fp64_strict", "fp64", "mixed"])
 def test_ions_electrons_and_impedance_step(order, precision):
     from paper_2111_12411_gb300 import Simulation

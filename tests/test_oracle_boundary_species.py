@@ -67,7 +67,7 @@ def test_impedance_faces_and_free_dofs(order):
         assert np.all(t.free1[2 * t.n_edges + 2 * fid])
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_impedance_energy_of_uniform_field(order):
     """E = k (e = D phi, phi = k.x, exact at every order): e^T I e equals
     Y0 |n x k|^2 times the area of the impedance face (the unit square x=1)."""
@@ -77,15 +77,20 @@ def test_impedance_energy_of_uniform_field(order):
     k = np.array([0.3, -1.2, 0.7])
     if order == 1:
         phi = t.xyz @ k
-    else:
+    elif order == 2:
         mid = 0.5 * (t.xyz[t.edges[:, 0]] + t.xyz[t.edges[:, 1]])
         phi = np.concatenate([t.xyz @ k, mid @ k])
+    else:  # the cubic lattice: nodes, two points per edge (nearer the lower vertex first), face centroids
+        a, b = t.xyz[t.edges[:, 0]], t.xyz[t.edges[:, 1]]
+        ep = np.stack([(2 * a + b) / 3, (a + 2 * b) / 3], axis=1).reshape(-1, 3)
+        fc = t.xyz[t.faces].mean(axis=1)
+        phi = np.concatenate([t.xyz @ k, ep @ k, fc @ k])
     e = D @ phi
     want = assemble.Y0 * (k[1] ** 2 + k[2] ** 2) * 1.0
     assert abs(e @ (I @ e) - want) <= 1e-12 * want
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_impedance_energy_of_rotational_field(order):
     """E = (-y, x, 0) / 2 (in the W1 span at every order; its L2 projection is
     exact): on x = 1, |n x E|^2 = E_y^2 + E_z^2 = 1/4, so e^T I e = Y0 / 4."""
