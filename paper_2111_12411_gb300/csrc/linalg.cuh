@@ -1016,8 +1016,9 @@ __global__ void k_hist(int64_t n, const int32_t* __restrict__ tet, int32_t* __re
 }
 
 // exclusive scan of one tile of 1024 values per block; tile totals to sums
-__global__ void k_scan_tiles(int32_t n, const int32_t* __restrict__ in, int32_t* __restrict__ out,
-                             int32_t* __restrict__ sums) {
+// in and out may be the same array (the recursive level scans in place):
+// each thread reads its element before the block's barriers and writes it after
+__global__ void k_scan_tiles(int32_t n, const int32_t* in, int32_t* out, int32_t* __restrict__ sums) {
   __shared__ int32_t warp_tot[32];
   int i = blockIdx.x * 1024 + threadIdx.x;
   int v = i < n ? in[i] : 0;
