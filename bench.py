@@ -630,6 +630,13 @@ def run_project(args, local_rank):
                                   f"p={args.order}, quadrupole lens B = grad((G/k^2) sin(kx) sinh(ky)), "
                                   "G = 1 T/m, k = pi/2cm", "n2": info.n2, "n_points": len(pts),
                       "cg_rtol": args.cg_rtol}}
+    traffic_it = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if args.order == 2 and os.path.exists(prof):
+        try:
+            traffic_it = json.load(open(prof)).get("projection_inner_iteration_dram_bytes_p2")
+        except (OSError, ValueError):
+            traffic_it = None
     for name, con in (("galerkin", False), ("constrained", True)):
         for _ in range(max(1, args.warmup // 3)):
             sim.set_impressed_B(Bv, constrained=con)
@@ -647,7 +654,7 @@ def run_project(args, local_rank):
                      "inner_iteration_us": 1e3 * inner_ms / max(1, inner_it),
                      "roofline_inner_iteration": {
                          "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                         "frac": gbs / peak if gbs else None, "traffic": None,
+                         "frac": gbs / peak if gbs else None, "traffic": traffic_it,
                          "peak_source": peak_src,
                          "bytes_per_iteration": runs[0]["bytes_per_inner_iteration"]}}
     bi = sim.get("B_IMPRESSED")
