@@ -705,6 +705,17 @@ __device__ __forceinline__ void aux_first_u(const PcgArgs& a, int k, float f) {
 }
 
 // lanes per row of L (rows of ~20-70 entries at order 2) and of V
+// lanes per row of the residual's auxiliary products D^T r and Pi^T r
+#ifndef FEMPIC_LPR_DT
+#define FEMPIC_LPR_DT 8
+#endif
+// lanes per W1 row of the preconditioner's z phase (D t + Pi u)
+#ifndef FEMPIC_LPR_Z
+#define FEMPIC_LPR_Z 4
+#endif
+#ifndef FEMPIC_LPR_PIT
+#define FEMPIC_LPR_PIT 16
+#endif
 #ifndef FEMPIC_LPR_L
 #define FEMPIC_LPR_L 8
 #endif
@@ -855,14 +866,14 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
     auto x0 = [&](int c) { return __ldcg(r32_cur + c); };
     auto et = [&](int k, float s) { aux_first_t(a, k, s); };
     auto eu = [&](int k, float s) { aux_first_u(a, k, s); };
-    sc.run<4>(a.DT.n_rows, nullptr, [&](int r, bool act, int lane) { spmv32_row<4>(a.DT, r, act, lane, x0, et); });
+    sc.run<FEMPIC_LPR_DT>(a.DT.n_rows, nullptr, [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_DT>(a.DT, r, act, lane, x0, et); });
     if (a.PiT.n_rows > 0)
-      sc.run<16>(a.PiT.n_rows, nullptr,
-                 [&](int r, bool act, int lane) { spmv32_row<16>(a.PiT, r, act, lane, x0, eu); });
+      sc.run<FEMPIC_LPR_PIT>(a.PiT.n_rows, nullptr,
+                 [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_PIT>(a.PiT, r, act, lane, x0, eu); });
     const float *tv, *uv;
     if (!aux_cheb(a, sc, tv, uv)) return;
     if (!grid_sync(a.bar, a.status)) return;
-    acc[0] += aux_z<4>(a, r_cur, tv, uv, sc);
+    acc[0] += aux_z<FEMPIC_LPR_Z>(a, r_cur, tv, uv, sc);
   }
   grid_sum_add<3>(acc, a.red, kred);
   if (!grid_sync(a.bar, a.status)) return;
@@ -949,10 +960,10 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
       auto xr = [&](int c) { return fmaf(-alpha32, __ldcg(a.q32 + c), __ldcg(r32o + c)); };
       auto et = [&](int k, float s) { aux_first_t(a, k, s); };
       auto eu = [&](int k, float s) { aux_first_u(a, k, s); };
-      sc.run<4>(a.DT.n_rows, nullptr, [&](int r, bool act, int lane) { spmv32_row<4>(a.DT, r, act, lane, xr, et); });
+      sc.run<FEMPIC_LPR_DT>(a.DT.n_rows, nullptr, [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_DT>(a.DT, r, act, lane, xr, et); });
       if (a.PiT.n_rows > 0)
-        sc.run<16>(a.PiT.n_rows, nullptr,
-                   [&](int r, bool act, int lane) { spmv32_row<16>(a.PiT, r, act, lane, xr, eu); });
+        sc.run<FEMPIC_LPR_PIT>(a.PiT.n_rows, nullptr,
+                   [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_PIT>(a.PiT, r, act, lane, xr, eu); });
       PCG_MARK(5);
       const float *tv, *uv;
       if (!aux_cheb(a, sc, tv, uv)) return;
@@ -960,7 +971,7 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
       if (!grid_sync(a.bar, a.status)) return;
       PCG_MARK(6);
       // phase 3: z = dinv r' + D t + Pi u
-      acc2[0] += aux_z<4>(a, r_new, tv, uv, sc);
+      acc2[0] += aux_z<FEMPIC_LPR_Z>(a, r_new, tv, uv, sc);
     }
     grid_sum_add<2>(acc2, a.red, kred);
     PCG_MARK(7);
