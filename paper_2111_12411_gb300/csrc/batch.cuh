@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(256, FEMPIC_BATCH_PCG_MIN_BLOCKS) k_batch_pcg(
     acc[2] += b * b;
   });
   if (!grid_sync(w.bar, w.status)) return;
-  member_rows32<4>(d.DT, tid, tcount, [&](int c) { return __ldcg(r32_cur + c); },
+  member_rows32<FEMPIC_LPR_DT>(d.DT, tid, tcount, [&](int c) { return __ldcg(r32_cur + c); },
                    [&](int k, float s) { member_first_t(d, k, s); });
   member_rows32<16>(d.PiT, tid, tcount, [&](int c) { return __ldcg(r32_cur + c); },
                     [&](int k, float s) { member_first_u(d, k, s); });
@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(256, FEMPIC_BATCH_PCG_MIN_BLOCKS) k_batch_pcg(
       }
       const float a32 = (float)alpha;
       const float* r32o = r32_cur;
-      member_rows32<4>(d.DT, tid, tcount, [&](int c) { return fmaf(-a32, __ldcg(d.q32 + c), __ldcg(r32o + c)); },
+      member_rows32<FEMPIC_LPR_DT>(d.DT, tid, tcount, [&](int c) { return fmaf(-a32, __ldcg(d.q32 + c), __ldcg(r32o + c)); },
                        [&](int k, float s) { member_first_t(d, k, s); });
       member_rows32<16>(d.PiT, tid, tcount, [&](int c) { return fmaf(-a32, __ldcg(d.q32 + c), __ldcg(r32o + c)); },
                         [&](int k, float s) { member_first_u(d, k, s); });
