@@ -55,6 +55,21 @@ def test_struct_layouts_match_c(native, tmp_path):
     assert got == want
 
 
+def test_extension_struct_layouts_match_c(native, tmp_path):
+    prog = tmp_path / "sizes2.c"
+    prog.write_text('#include "fempic.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                    'int main(){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(femPIC_projection),'
+                    ' sizeof(femPIC_injector), sizeof(femPIC_batch_tuning), offsetof(femPIC_injector, v_sigma),'
+                    ' offsetof(femPIC_batch_tuning, particle_ms), offsetof(femPIC_diag, divb_ref));return 0;}\n')
+    exe = tmp_path / "sizes2"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(native.femPIC_projection), ctypes.sizeof(native.femPIC_injector),
+            ctypes.sizeof(native.femPIC_batch_tuning), native.femPIC_injector.v_sigma.offset,
+            native.femPIC_batch_tuning.particle_ms.offset, native.femPIC_diag.divb_ref.offset]
+    assert got == want
+
+
 def test_default_opts(native):
     o = native.default_opts()
     assert o.precision == 1 and o.scheme == 0 and o.cg_rtol == 1e-12 and o.sort_period == 1
@@ -92,6 +107,13 @@ def test_host_validation_errors(native):
     wrong = (tet + 1) % len(tets)
     with pytest.raises(native.FemPICError) as ei:
         native.femPIC_create(xyz, tets, 1, -1.6e-19, 9.1e-31, 1.0, x, v, wrong)
+    assert ei.value.code == native.FEMPIC_ERR_ARG
+    species = [dict(q=-1.6e-19, m=9.1e-31, weight=1.0, x=x, v=v, tet=tet)]
+    with pytest.raises(native.FemPICError) as ei:  # face tags are 0..7
+        native.femPIC_create_ext(xyz, tets, 1, species, np.full((len(tets), 4), 8, dtype=np.int32))
+    assert ei.value.code == native.FEMPIC_ERR_ARG
+    with pytest.raises(native.FemPICError) as ei:  # absorbing walls and the Adams-Bashforth push
+        native.femPIC_create_ext(xyz, tets, 1, species, np.full((len(tets), 4), 2, dtype=np.int32), o)
     assert ei.value.code == native.FEMPIC_ERR_ARG
     nonman = np.vstack([tets, tets[:1]])  # a face shared by three tets
     with pytest.raises(native.FemPICError) as ei:
