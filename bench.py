@@ -323,10 +323,10 @@ def run_native(args, rank, world, local_rank):
             sim.set("V", vh)
             sim.set("TET", th)
             sim.step(dt)
-            xh[:] = sim.get("X")
-            vh[:] = sim.get("V")
-            th[:] = sim.get("TET")
-            eh[:] = sim.get("E")
+            sim.get("X", out=xh)
+            sim.get("V", out=vh)
+            sim.get("TET", out=th)
+            sim.get("E", out=eh)
         barrier()
         t_e2e = time.perf_counter() - t0
         h2d = xh.nbytes + vh.nbytes + th.nbytes
@@ -334,7 +334,8 @@ def run_native(args, rank, world, local_rank):
         e2e = {"value": world * npart * K / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
                "note": "per step: particle state host->device, one full step, particle state "
-                       "and E DOFs device->host, through femPIC_set/step/get (pinned host memory)"}
+                       "and E DOFs device->host, through femPIC_set/step/get straight to and from "
+                       "pinned host buffers"}
 
     result = None
     if rank == 0:

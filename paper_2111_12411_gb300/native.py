@@ -397,9 +397,16 @@ class Simulation:
     def sync(self):
         femPIC_sync(self.h)
 
-    def get(self, what):
+    def get(self, what, out=None):
+        """The quantity as a new array, or written into ``out`` (e.g. pinned
+        host memory: the copy then goes straight to it)."""
         shape, dt = self._shape(what)
-        return femPIC_get(self.h, what, np.empty(shape, dtype=dt))
+        if out is None:
+            return femPIC_get(self.h, what, np.empty(shape, dtype=dt))
+        want = shape if isinstance(shape, tuple) else (shape,)
+        if out.shape != want or out.dtype != np.dtype(dt) or not out.flags.c_contiguous:
+            raise ValueError(f"{what}: out must be a C-contiguous {np.dtype(dt)} array of shape {want}")
+        return femPIC_get(self.h, what, out)
 
     def set(self, what, arr):
         shape, dt = self._shape(what)

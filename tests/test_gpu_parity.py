@@ -435,3 +435,14 @@ def test_current_quantity(c1small):
     g.step(cfg["dt"])
     assert np.allclose(g.get("J"), g.get("DG") / cfg["dt"], rtol=1e-15, atol=0.0)
     g.close()
+
+
+def test_get_into_caller_buffer(c1small):
+    from paper_2111_12411_gb300 import Simulation
+    g = Simulation.from_config(c1small, es_init=False)
+    g.step(c1small["dt"])
+    x = np.empty((g.n_particles, 3))
+    assert g.get("X", out=x) is x and np.array_equal(x, g.get("X"))
+    with pytest.raises(ValueError):
+        g.get("X", out=np.empty((g.n_particles, 3), dtype=np.float32))
+    g.close()
