@@ -111,3 +111,42 @@ def test_wall_errors():
         Simulation(cfg["xyz"], cfg["tets"], 1, cfg["q"], cfg["m"], cfg["weight"], cfg["x"], cfg["v"],
                    cfg["tet"], bface_tag=cfg["bface_tag"], push="ab4")
     assert ei.value.code == native.FEMPIC_ERR_ARG
+
+
+def test_two_species_walls_match_oracle():
+    """Electrons and ions through the beam walls, each species re-injected by
+    its own injector: strict mode bit-exact against the oracle over four
+    steps (fields taken from the oracle every step)."""
+    from paper_2111_12411_gb300 import Simulation
+    cfg = workloads.make_config(1, n_particles=300, walls="beam", tube=(8, 4, 4))
+    cfg["dt"] = 1e-10
+    rng = np.random.default_rng(17)
+    near_end = np.nonzero(cfg["xyz"][cfg["tets"]][:, :, 2].mean(axis=1) > 0.09)[0]
+    xi, ti = workloads.sample_uniform_in_tets(cfg["xyz"], cfg["tets"], 200, rng, subset=near_end)
+    vi = workloads.maxwellian(200, 1e4, rng, drift=(0.0, 0.0, 6e7))
+    sp = [dict(q=-1.602176634e-19, m=9.1093837015e-31, weight=1.0, x=cfg["x"], v=cfg["v"], tet=cfg["tet"]),
+          dict(q=1.602176634e-19, m=1.67262192e-27, weight=1.0, x=xi, v=vi, tet=ti)]
+    inj = [dict(species=0, v_drift=(0.0, 0.0, 3e7), v_sigma=(3e5,) * 3),
+           dict(species=1, v_drift=(0.0, 0.0, 1e5), v_sigma=(1e3,) * 3)]
+    o = osim.Sim(cfg["xyz"], cfg["tets"], 1, sp[0]["q"], sp[0]["m"], 1.0, cfg["B0"], 0.0,
+                 bface_tag=cfg["bface_tag"])
+    o.set_species(sp)
+    o.set_injection(inj, 99)
+    g = Simulation(cfg["xyz"], cfg["tets"], 1, sp[0]["q"], sp[0]["m"], 1.0, cfg["x"], cfg["v"], cfg["tet"],
+                   precision="fp64_strict", B0=cfg["B0"], es_init=False, diagnostics=True, species=sp,
+                   bface_tag=cfg["bface_tag"])
+    g.set_injection(inj, 99)
+    total = 0
+    for _ in range(4):
+        g.set("E", o.e)
+        g.set("E_PREV", o.e_prev)
+        g.set("B", o.b)
+        w = o.step(cfg["dt"])
+        g.step(cfg["dt"])
+        assert g.diag()["absorbed"] == int(w["absorbed"].sum())
+        total += int(w["absorbed"].sum())
+        assert np.array_equal(g.get("X"), w["x"]) and np.array_equal(g.get("V"), w["v"])
+        assert np.array_equal(g.get("TET"), w["tet"]) and np.array_equal(g.get("HASH"), w["hash"])
+        assert rel(g.get("RHO"), o.rho) < 1e-12
+    assert total > 50
+    g.close()

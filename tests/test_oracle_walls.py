@@ -131,3 +131,37 @@ def test_absorbing_walls_need_injectors():
     o.set_particles(cfg["x"], cfg["v"], cfg["tet"])
     with pytest.raises(ValueError):  # 9 mm per step in a 10 cm tube: some reach z = L
         o.push_walk(cfg["dt"])
+
+
+def test_two_species_reinjected_with_their_own_injectors():
+    """Electrons and ions through the beam walls: each absorbed particle
+    comes back with its own species' drift (ions slower, electrons faster),
+    the slot keeps its species, and interior charge is conserved."""
+    cfg = _tube(n_particles=300, nz=4)
+    cfg["dt"] = 1e-10
+    rng = np.random.default_rng(17)
+    xi, ti = workloads.sample_uniform_in_tets(cfg["xyz"], cfg["tets"], 200, rng,
+                                              subset=np.nonzero(cfg["xyz"][cfg["tets"]][:, :, 2].mean(axis=1) > 0.09)[0])
+    vi = workloads.maxwellian(200, 1e4, rng, drift=(0.0, 0.0, 6e7))
+    sp = [dict(q=-1.602176634e-19, m=9.1093837015e-31, weight=1.0, x=cfg["x"], v=cfg["v"], tet=cfg["tet"]),
+          dict(q=1.602176634e-19, m=1.67262192e-27, weight=1.0, x=xi, v=vi, tet=ti)]
+    o = osim.Sim(cfg["xyz"], cfg["tets"], 1, sp[0]["q"], sp[0]["m"], 1.0, cfg["B0"], 0.0,
+                 bface_tag=cfg["bface_tag"])
+    o.set_species(sp)
+    o.set_injection([dict(species=0, v_drift=(0.0, 0.0, 3e7), v_sigma=(3e5,) * 3),
+                     dict(species=1, v_drift=(0.0, 0.0, 1e5), v_sigma=(1e3,) * 3)], 99)
+    t = o.topo
+    seen = [0, 0]
+    for _ in range(4):
+        w = o.step(cfg["dt"])
+        ab = w["absorbed"]
+        for k, sl in enumerate((slice(0, 300), slice(300, 500))):
+            idx = np.nonzero(ab[sl])[0] + sl.start
+            seen[k] += len(idx)
+            if len(idx):
+                vz = o.v[idx, 2]
+                want = 3e7 if k == 0 else 1e5
+                assert np.all(np.abs(vz - want) <= 6 * (3e5 if k == 0 else 1e3) + 1e-6)
+        cont = w["continuity"][t.interior0]
+        assert np.linalg.norm(cont) <= 1e-13 * np.linalg.norm(w["drho"][t.interior0])
+    assert seen[0] > 0 and seen[1] > 50   # ions start near z = L and drift out fast
