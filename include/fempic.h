@@ -304,8 +304,12 @@ int femPIC_set_injection(FemPIC* h, const femPIC_injector* inj, int32_t n, uint6
 
 /* Advance n_steps PIC steps of size dt (s): gather, Lorentz push, walk,
  * charge-conserving deposit, Newmark field solve, b update, rho measurement
- * (Section III-B).  Returns after the device finished; the return value is
- * the latched device status. */
+ * (Section III-B); with absorbing faces, the absorbed particles' slots are
+ * refilled before rho is measured (femPIC_set_injection).  Returns after the
+ * device finished; the return value is the latched device status
+ * (FEMPIC_ERR_WALK crossing cap, FEMPIC_ERR_CG iteration cap,
+ * FEMPIC_ERR_BARRIER grid-barrier timeout), FEMPIC_ERR_ARG for a bad dt, or
+ * FEMPIC_ERR_STATE for absorbing faces with a species that has no injector. */
 int femPIC_step(FemPIC* h, double dt, int32_t n_steps);
 
 /* Same as femPIC_step but returns as soon as the work is enqueued on the
@@ -313,7 +317,10 @@ int femPIC_step(FemPIC* h, double dt, int32_t n_steps);
 int femPIC_step_async(FemPIC* h, double dt, int32_t n_steps);
 int femPIC_sync(FemPIC* h);
 
-/* Copy a quantity to/from caller memory; bytes must equal its size. */
+/* Copy a quantity to/from caller memory; bytes must equal its size
+ * (FEMPIC_ERR_SIZE otherwise), read-only quantities reject femPIC_set
+ * (FEMPIC_ERR_ARG), and a tet id out of range in FEMPIC_TET is rejected
+ * before anything is copied.  Particle quantities are in particle-id order. */
 int femPIC_get(FemPIC* h, int32_t what, void* host_dst, size_t bytes);
 int femPIC_set(FemPIC* h, int32_t what, const void* host_src, size_t bytes);
 
