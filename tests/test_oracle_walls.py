@@ -165,3 +165,16 @@ def test_two_species_reinjected_with_their_own_injectors():
         cont = w["continuity"][t.interior0]
         assert np.linalg.norm(cont) <= 1e-13 * np.linalg.norm(w["drho"][t.interior0])
     assert seen[0] > 0 and seen[1] > 50   # ions start near z = L and drift out fast
+
+
+def test_tube_wall_tags_mark_the_ends():
+    """The workload's tags: every face on z = L absorbs (8 azimuthal x 4
+    radial cells: 8 core triangles + 2 per ring quad = 56), the z = 0 faces
+    inside half the radius inject (24), and all tagged faces are walls."""
+    cfg = _tube(n_particles=10, nz=3)
+    t = topology.Topology(cfg["xyz"], cfg["tets"], 1, cfg["bface_tag"])
+    assert int(t.absorb_face.sum()) == 56 and int(t.inject_face.sum()) == 24
+    assert np.all(t.boundary_face[t.absorb_face | t.inject_face])
+    z = t.xyz[t.faces][:, :, 2]
+    assert np.all(np.abs(z[t.absorb_face] - 0.10) < 1e-12) and np.all(np.abs(z[t.inject_face]) < 1e-12)
+    assert not np.any(t.absorb_face & t.inject_face)
