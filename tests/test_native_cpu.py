@@ -119,3 +119,27 @@ def test_host_validation_errors(native):
     with pytest.raises(native.FemPICError) as ei:
         native.femPIC_create(xyz, nonman, 1, -1.6e-19, 9.1e-31, 1.0, x, v, tet)
     assert ei.value.code == native.FEMPIC_ERR_MESH
+
+
+def test_product_never_reaches_the_oracle():
+    """The library package imports nothing from the oracle (only the tests,
+    smoke() and the benchmark's CPU-baseline and reference arms may), and its
+    binding refuses to run without the built library instead of falling back."""
+    import ast
+    pkg = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2111_12411_gb300")
+    for name in os.listdir(pkg):
+        if not name.endswith(".py"):
+            continue
+        tree = ast.parse(open(os.path.join(pkg, name)).read())
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                assert not any(a.name.split(".")[0] == "oracle" for a in node.names), name
+            elif isinstance(node, ast.ImportFrom):
+                assert (node.module or "").split(".")[0] != "oracle", name
+    from paper_2111_12411_gb300 import native as nat
+    saved, nat._lib = nat._lib, None
+    try:
+        with pytest.raises(ImportError):
+            nat.load(os.path.join(pkg, "no_such_library.so"))
+    finally:
+        nat._lib = saved
