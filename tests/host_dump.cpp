@@ -7,7 +7,9 @@
 //   mesh.bin: int32 n_nodes, n_tets; double xyz[3 n_nodes]; int32 tets[4 n_tets];
 //             int32 tags[4 n_tets]
 //   out.bin:  CSRs M, K, C, D, M2, Ival (on M's pattern), DA, LA, LAI (on LA's
-//             pattern), Dv; then uint8 pec1[n1], bnd0[n0]
+//             pattern), Dv; then uint8 pec1[n1], bnd0[n0]; the load's rule
+//             (int32 nq, double lam[nq][4], w[nq]); the injection faces (int32
+//             F, double xyz[F][9], int32 tet[F], double cum[F])
 #include <cstdio>
 #include <cstdlib>
 #include <string>
@@ -66,6 +68,15 @@ int main(int argc, char** argv) {
   for (const HostCSR* A : {&m.M, &m.K, &m.C, &m.D, &m.M2, &I, &m.DA, &m.LA, &LI, &P.Dv}) dump(o, *A);
   fwrite(m.pec1.data(), 1, m.pec1.size(), o);
   fwrite(m.bnd0.data(), 1, m.bnd0.size(), o);
+  // the load's quadrature rule and the injection faces
+  const int32_t nq = P.nq, nf = (int32_t)m.inj_tet.size();
+  fwrite(&nq, 4, 1, o);
+  fwrite(P.qlam.data(), 8, P.qlam.size(), o);
+  fwrite(P.qw.data(), 8, P.qw.size(), o);
+  fwrite(&nf, 4, 1, o);
+  fwrite(m.inj_xyz.data(), 8, m.inj_xyz.size(), o);
+  fwrite(m.inj_tet.data(), 4, m.inj_tet.size(), o);
+  fwrite(m.inj_cum.data(), 8, m.inj_cum.size(), o);
   fclose(o);
   return 0;
 }

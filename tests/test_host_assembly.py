@@ -7,7 +7,8 @@ Gauss-Legendre rule exact for the integrands in the oracle; only rounding
 differs).  Checked: [*eps], the curl-curl matrix, the curl and gradient maps,
 [*mu^-1], the impedance matrix, the preconditioner's gradient space with the
 impedance wall's W0 DOFs and its Laplacian (mass and impedance parts), the
-projection's [~div], the PEC and boundary masks.
+projection's [~div], the PEC and boundary masks, the load's quadrature rule,
+and the injection table (bit-exact: the re-injection's sampling reads it).
 """
 
 import os
@@ -55,6 +56,7 @@ def _mesh():
     for i in range(4):
         X = xyz[np.delete(tets, i, axis=1)][:, :, 0]
         tag[np.all(np.abs(X - 1.0) < 1e-12, axis=1), i] = 1  # impedance wall x = 1
+        tag[np.all(np.abs(X) < 1e-12, axis=1), i] = 4        # injection faces on x = 0
     return xyz, tets, tag
 
 
@@ -92,6 +94,13 @@ def test_host_operators_match_oracle(harness, tmp_path, order):
         M, K, C, D, M2, I, DA, LA, LI, Dv = (_read(f) for _ in range(10))
         pec1 = np.fromfile(f, np.uint8, t.n1).astype(bool)
         bnd0 = np.fromfile(f, np.uint8, t.n0).astype(bool)
+        nq = int(np.fromfile(f, np.int32, 1)[0])
+        qlam = np.fromfile(f, np.float64, 4 * nq).reshape(nq, 4)
+        qw = np.fromfile(f, np.float64, nq)
+        nf = int(np.fromfile(f, np.int32, 1)[0])
+        ixyz = np.fromfile(f, np.float64, 9 * nf).reshape(nf, 3, 3)
+        itet = np.fromfile(f, np.int32, nf)
+        icum = np.fromfile(f, np.float64, nf)
     assert np.array_equal(pec1, t.pec1) and np.array_equal(bnd0, t.bnd0)
     fr, ii = t.free1, t.interior0
     Mo = assemble.mass1(t, g, vol)[fr][:, fr]
@@ -114,3 +123,12 @@ def test_host_operators_match_oracle(harness, tmp_path, order):
     # the projection's divergence operator against the W3 volume functions
     S3, Dvo, M2o = project.matrices(t, g, vol)
     assert _rel(Dv, Dvo) < 1e-13
+    # the load's conical Gauss rule (nodes from Newton on P_n against numpy's
+    # Legendre-Gauss rule) and the injection table, bit-exact where the
+    # re-injection's sampling reads it
+    from oracle import inject, quadrature
+    ql, qwo = quadrature.tet_rule(order + 3)
+    assert np.abs(qlam - ql).max() < 1e-15 and np.abs(qw - qwo).max() < 1e-16
+    verts, owner, cum = inject.face_table(t)
+    assert nf == len(owner) == 18
+    assert np.array_equal(ixyz, verts) and np.array_equal(itet, owner) and np.array_equal(icum, cum)
