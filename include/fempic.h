@@ -72,7 +72,8 @@ enum {
   FEMPIC_ERR_WALK = 6,   /* a particle hit the face-crossing cap in one step     */
   FEMPIC_ERR_SIZE = 7,   /* caller buffer size does not match the quantity       */
   FEMPIC_ERR_STATE = 8,  /* call not valid in the current state                  */
-  FEMPIC_ERR_BARRIER = 9 /* a device grid barrier timed out                      */
+  FEMPIC_ERR_BARRIER = 9, /* a device grid barrier timed out                     */
+  FEMPIC_ERR_BOUNDS = 10  /* an index out of range (builds with -DFEMPIC_CHECKS=1) */
 };
 
 /* ---- precision modes (set at create) ------------------------------------ */
@@ -327,7 +328,10 @@ int femPIC_set(FemPIC* h, int32_t what, const void* host_src, size_t bytes);
 /* Copy the same quantities to/from device memory the caller owns (same
  * device, ordered on the handle's stream; synchronous on return).  Unlike
  * femPIC_set, femPIC_set_device does not range-check tet ids: the caller
- * guarantees 0 <= tet < n_tets. */
+ * guarantees 0 <= tet < n_tets.  A library built with -DFEMPIC_CHECKS=1
+ * checks them in the particle kernels (the particle is skipped and the step
+ * returns FEMPIC_ERR_BOUNDS) and checks the per-tet DOF and neighbour tables
+ * once at create. */
 int femPIC_get_device(FemPIC* h, int32_t what, void* dev_dst, size_t bytes);
 int femPIC_set_device(FemPIC* h, int32_t what, const void* dev_src, size_t bytes);
 

@@ -274,6 +274,7 @@ __device__ __forceinline__ ParticleArgs member_particle_args(const MemberDesc& d
   a.sp.n = 1;
   a.max_cross = d.max_cross;
   a.status = d.status;
+  a.n_tets = d.nt;
   a.crossings = d.crossings;
   return a;
 }

@@ -341,6 +341,10 @@ int latch_status(FemPIC* h) {
     h->err = "CG reached its iteration cap before the tolerance";
     return FEMPIC_ERR_CG;
   }
+  if (st & kStatusBounds) {
+    h->err = "a tet id or DOF index was out of range (checked build)";
+    return FEMPIC_ERR_BOUNDS;
+  }
   return FEMPIC_OK;
 }
 
@@ -612,6 +616,7 @@ int launch_particles(FemPIC* h, double dt) {
   a.pid = h->pid;
   a.sp = species_table(h, dt);
   a.absorbed = h->pabs;
+  a.n_tets = h->n_tets;
   if (h->np == 0) return FEMPIC_OK;
   if (h->opts.push == FEMPIC_PUSH_AB4) {
     Ab4Args A;
@@ -1415,6 +1420,13 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
   CK(cudaMemset(h->phi, 0, sizeof(double) * h->n0));
   CK(cudaMemset(h->rho_prev, 0, sizeof(double) * h->n0));
   CK(cudaMemset(h->d_status, 0, sizeof(int32_t)));
+#if FEMPIC_CHECKS
+  CK(cudaDeviceSynchronize());
+  k_check_tables<<<grid_for(h->n_tets, 256, 4096), 256, 0, h->stream>>>(
+      h->n_tets, h->nl0, h->nl1, h->nl2, h->dof0, h->dof1, h->dof2, h->nbr, h->n0, h->n1, h->n2, h->d_status);
+  CK(cudaGetLastError());
+  if ((rc = latch_status(h))) return rc;
+#endif
   CK(cudaMemset(h->d_cg_iters, 0, sizeof(int32_t)));
   CK(cudaMemset(h->d_cg_res, 0, sizeof(double)));
   CK(cudaMemset(h->d_norms, 0, 4 * sizeof(double)));

@@ -18,6 +18,39 @@ constexpr uint64_t kFnvPrime = 1099511628211ull;
 constexpr int kStatusWalk = 1;
 constexpr int kStatusCG = 2;
 constexpr int kStatusBarrier = 4;
+constexpr int kStatusBounds = 8;
+
+// Checked builds (-DFEMPIC_CHECKS=1): a tet id outside [0, n) sets the status
+// word (reported as FEMPIC_ERR_BOUNDS) and the particle is skipped instead of
+// reading out of bounds; without the flag the test folds away.
+#ifndef FEMPIC_CHECKS
+#define FEMPIC_CHECKS 0
+#endif
+__device__ __forceinline__ bool index_ok(int64_t i, int64_t n, int32_t* status) {
+  if (!FEMPIC_CHECKS) return true;
+  if (i >= 0 && i < n) return true;
+  atomicOr(status, kStatusBounds);
+  return false;
+}
+
+// Checked builds, once at create: every entry of the per-tet DOF tables within
+// its space and every neighbour record (tet << 2 | face) naming a tet.
+__global__ void k_check_tables(int32_t n_tets, int nl0, int nl1, int nl2, const int32_t* dof0, const int32_t* dof1,
+                               const int32_t* dof2, const int32_t* nbr, int32_t n0, int32_t n1, int32_t n2,
+                               int32_t* status) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tets; t += (int64_t)gridDim.x * blockDim.x) {
+    for (int k = 0; k < nl0; ++k) index_ok(dof0[t * nl0 + k], n0, status);
+    for (int k = 0; k < nl1; ++k) index_ok(dof1[t * nl1 + k], n1, status);
+    for (int k = 0; k < nl2; ++k) index_ok(dof2[t * nl2 + k], n2, status);
+    for (int k = 0; k < 4; ++k) {
+      const int32_t nb = nbr[t * 4 + k];
+      if (nb >= 0)
+        index_ok(nb >> 2, n_tets, status);
+      else if (nb < -2)
+        index_ok(-1, 1, status);
+    }
+  }
+}
 
 // ---- arithmetic policies ----------------------------------------------------
 // Strict: one rounding per operation, in the written order (no contraction).
@@ -460,6 +493,7 @@ struct ParticleArgs {
   const int32_t* pid;  // particle ids in device order (read only with several species)
   SpeciesTable sp;
   uint8_t* absorbed = nullptr;  // [n] 1 where the path ended on an absorbing wall (null: none)
+  int32_t n_tets = 0;           // bound of the tet ids (checked builds)
 };
 
 // q w and q dt / 2m of the particle in device slot i
@@ -481,7 +515,7 @@ __global__ void __launch_bounds__(256) k_particle(ParticleArgs a) {
   constexpr int N0 = Nloc<P>::n0;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long my_cross = 0;
-  if (i < a.n) {
+  if (i < a.n && index_ok(a.tet[i], a.n_tets, a.status)) {
     int T = a.tet[i];
     double x[3] = {a.x[0][i], a.x[1][i], a.x[2][i]};
     double v[3] = {a.v[0][i], a.v[1][i], a.v[2][i]};
@@ -542,6 +576,7 @@ __global__ void __launch_bounds__(256) k_particle(ParticleArgs a) {
       if (nb >= 0) {
         entry = nb & 3;
         T = nb >> 2;
+        if (!index_ok(T, a.n_tets, a.status)) break;
         s0 = s1;
         load_geom(a.geom, T, G);
       } else if (nb == -2) {  // absorbing wall: the path ends at the hit point, no charge left

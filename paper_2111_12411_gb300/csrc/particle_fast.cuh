@@ -325,7 +325,7 @@ __device__ __forceinline__ void particle_step(const ParticleArgs& a, int64_t i) 
   constexpr int N2 = P == 1 ? 4 : 15;
   constexpr int N0 = P == 1 ? 4 : 10;
   const int lane = threadIdx.x & 31;
-  const bool valid = i < a.n;
+  const bool valid = i < a.n && index_ok(a.tet[i], a.n_tets, a.status);
   int T = valid ? a.tet[i] : 0;
   double qw = a.qw, hq = a.h;
   if (valid) particle_consts(a, i, qw, hq);
@@ -381,6 +381,10 @@ __device__ __forceinline__ void particle_step(const ParticleArgs& a, int64_t i) 
     if (nb >= 0) {
       entry = nb & 3;
       T = nb >> 2;
+      if (!index_ok(T, a.n_tets, a.status)) {
+        T = 0;
+        break;
+      }
       s0 = s1;
       load_geom(a.geom, T, G);
     } else if (nb == -2) {  // absorbing wall: the path ends at the hit point, no charge left

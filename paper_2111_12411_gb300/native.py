@@ -16,8 +16,9 @@ LIB_PATH = os.path.join(_HERE, "libfempic.so")
 
 FEMPIC_OK, FEMPIC_ERR_ARG, FEMPIC_ERR_MESH, FEMPIC_ERR_OOM, FEMPIC_ERR_CUDA = 0, 1, 2, 3, 4
 FEMPIC_ERR_CG, FEMPIC_ERR_WALK, FEMPIC_ERR_SIZE, FEMPIC_ERR_STATE, FEMPIC_ERR_BARRIER = 5, 6, 7, 8, 9
+FEMPIC_ERR_BOUNDS = 10
 ERROR_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_MESH", 3: "ERR_OOM", 4: "ERR_CUDA", 5: "ERR_CG",
-               6: "ERR_WALK", 7: "ERR_SIZE", 8: "ERR_STATE", 9: "ERR_BARRIER"}
+               6: "ERR_WALK", 7: "ERR_SIZE", 8: "ERR_STATE", 9: "ERR_BARRIER", 10: "ERR_BOUNDS"}
 PRECISION = {"fp64_strict": 0, "fp64": 1, "mixed": 2}
 SCHEME = {"trapezoid": 0, "wave": 1}
 PUSH = {"boris": 0, "ab4": 1}
