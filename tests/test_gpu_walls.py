@@ -150,3 +150,59 @@ def test_two_species_walls_match_oracle():
         assert rel(g.get("RHO"), o.rho) < 1e-12
     assert total > 50
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64_strict", "fp64"])
+def test_full_size_beam_sampled(precision):
+    """The benchmark's launch configuration: the drift tube at full size
+    (132,480 tets, p = 2, 10^6 particles) with the beam absorbed at z = L and
+    re-injected at z = 0.  One step from a seeded random field; 300 random
+    particles and 200 whose straight path leaves through z = L are recomputed
+    one by one by the oracle: the ones that stay against the walk (strict:
+    bit-exact; contracted FP64: rel 1e-12), the absorbed ones against a fresh
+    sample of the injector for their particle id at step 0 (bit-exact in both
+    modes: the re-injection rounds every operation once).  Charge is
+    conserved over all particles."""
+    from paper_2111_12411_gb300 import Simulation
+    from oracle import geometry, inject, particles as opart, topology as otopo
+    from gpu_helpers import random_state
+    cfg = workloads.make_config(1, walls="beam")
+    g = Simulation.from_config(cfg, precision=precision, diagnostics=True, es_init=False)
+    t = otopo.Topology(cfg["xyz"], cfg["tets"], 2, cfg["bface_tag"])
+    rng = np.random.default_rng(6)
+    e, b = random_state(t, rng, e_scale=1e4, b_scale=1e-3)
+    g.set("E", e)
+    g.set("E_PREV", e)
+    g.set("B", b)
+    g.step(cfg["dt"])
+    d = g.diag()
+    assert d["continuity_abs"] <= 1e-12 * d["continuity_ref"]
+    assert d["absorbed"] > 1000
+    z1 = cfg["x"][:, 2] + cfg["dt"] * cfg["v"][:, 2]
+    leaving = np.nonzero(z1 > 0.1 + 1e-5)[0]
+    idx = np.unique(np.concatenate([rng.choice(len(cfg["x"]), 300, replace=False),
+                                    rng.choice(leaving, 200, replace=False)]))
+    gg, cc, _ = geometry.barycentric_maps(t.xyz, t.tets)
+    x0, v0, t0 = cfg["x"][idx], cfg["v"][idx], cfg["tet"][idx]
+    E, B = opart.gather(t, gg, cc, e, b, cfg["B0"], x0, t0)
+    vn = opart.boris(v0, E, B, cfg["q"], cfg["m"], cfg["dt"])
+    x1 = x0 + cfg["dt"] * vn
+    xe, ve, te, _, _, hs, _, ab = opart.walk_deposit(t, gg, cc, x0, x1, vn, t0, cfg["q"] * cfg["weight"], t.n1,
+                                                     absorb=t.tet_absorb)
+    assert ab.sum() >= 30
+    table = inject.face_table(t)
+    inj = cfg["injectors"][0]
+    for i in np.nonzero(ab)[0]:
+        xe[i], ve[i], te[i] = inject.sample(table, cfg["inject_seed"], 0, int(idx[i]), np.array(inj["v_drift"]),
+                                            np.array(inj["v_sigma"]))
+    xg, vg, tg = g.get("X")[idx], g.get("V")[idx], g.get("TET")[idx]
+    assert np.array_equal(xg[ab], xe[ab]) and np.array_equal(vg[ab], ve[ab]) and np.array_equal(tg[ab], te[ab])
+    k = ~ab
+    if precision == "fp64_strict":
+        assert np.array_equal(xg[k], xe[k]) and np.array_equal(vg[k], ve[k]) and np.array_equal(tg[k], te[k])
+        assert np.array_equal(g.get("HASH")[idx][k], hs[k])
+    else:
+        assert rel(xg[k], xe[k]) < 1e-12 and rel(vg[k], ve[k]) < 1e-12
+        ok = geometry.lam(gg[te[k]], cc[te[k]], xe[k]).min(axis=1) > 1e-9
+        assert ok.mean() > 0.99 and np.array_equal(tg[k][ok], te[k][ok])
+    g.close()
