@@ -309,8 +309,9 @@ int femPIC_set_injection(FemPIC* h, const femPIC_injector* inj, int32_t n, uint6
  * refilled before rho is measured (femPIC_set_injection).  Returns after the
  * device finished; the return value is the latched device status
  * (FEMPIC_ERR_WALK crossing cap, FEMPIC_ERR_CG iteration cap,
- * FEMPIC_ERR_BARRIER grid-barrier timeout), FEMPIC_ERR_ARG for a bad dt, or
- * FEMPIC_ERR_STATE for absorbing faces with a species that has no injector. */
+ * FEMPIC_ERR_BARRIER grid-barrier timeout; FEMPIC_ERR_BOUNDS in a checked
+ * build), FEMPIC_ERR_ARG for a bad dt, or FEMPIC_ERR_STATE for absorbing
+ * faces with a species that has no injector. */
 int femPIC_step(FemPIC* h, double dt, int32_t n_steps);
 
 /* Same as femPIC_step but returns as soon as the work is enqueued on the
