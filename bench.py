@@ -84,6 +84,31 @@ def particle_bytes_per_step(order, n_particles, occupied_tets, crossings_per_par
     return 104.0 + per_tet / ppc * (1.0 + crossings_per_particle)
 
 
+# ---- ranks (N > 1: one independent replica per GPU) ------------------------------------
+def max_over_ranks(x, world, device=None):
+    """The largest x over all ranks: the job takes as long as its slowest
+    replica.  One all-reduce of a scalar, outside the timed region."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def build_in_rank_order(local_rank, world, build_fn, barrier_fn):
+    """Compile the library once per node: local rank 0 builds, the others
+    wait at the barrier and then find it up to date (two ranks compiling the
+    same objects at once would overwrite each other's files)."""
+    if local_rank == 0:
+        build_fn()
+    if world > 1:
+        barrier_fn()
+    if local_rank != 0:
+        build_fn()
+
+
 # ---- clocks -----------------------------------------------------------------------------
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -234,12 +259,7 @@ def run_native(args, rank, world, local_rank):
                 acc[key] += t[key]
             crossings += sim.diag()["crossings"]
         barrier()
-    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world, dev)
     K = args.steps
     value = world * npart * K / (total_ms * 1e-3)
     clocks = clk.summary()
@@ -328,7 +348,7 @@ def run_native(args, rank, world, local_rank):
             sim.get("TET", out=th)
             sim.get("E", out=eh)
         barrier()
-        t_e2e = time.perf_counter() - t0
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
         h2d = xh.nbytes + vh.nbytes + th.nbytes
         d2h = h2d + eh.nbytes
         e2e = {"value": world * npart * K / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -805,7 +825,11 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     from paper_2111_12411_gb300 import build
-    build.build()
+
+    def node_barrier():
+        import torch.distributed as dist
+        dist.barrier()
+    build_in_rank_order(local_rank, world, build.build, node_barrier)
     if args.workload == "batched":
         run_batched(args, local_rank)
     elif args.workload == "serving":
