@@ -44,6 +44,9 @@ class Request:
         self.chunk_steps = chunk_steps
         self.sim = None
         self.done_chunks = 0
+        self.steps_done = 0
+        self.steps_in_chunk = 0  # steps of the current chunk taken so far
+        self.chunk_time = 0.0    # and their device-synchronised wall time
         self.admitted_at = None
         self.finished_at = None
         self.chunk_latency = []
@@ -53,7 +56,13 @@ class Request:
 
 class Server:
     def __init__(self, hbm_budget_bytes, max_slots=64, device=0, precision=None,
-                 result_keys=("X", "E", "RHO"), clock=time.perf_counter):
+                 result_keys=("X", "E", "RHO"), clock=time.perf_counter, sleep=time.sleep,
+                 make_sim=None, make_batch=None):
+        """make_sim(cfg, **kw) and make_batch(sims) default to
+        Simulation.from_config and Batch; clock and sleep to the wall clock."""
+        self.make_sim = make_sim or Simulation.from_config
+        self.make_batch = make_batch or Batch
+        self.sleep = sleep
         self.budget = int(hbm_budget_bytes)
         self.max_slots = max_slots
         self.device = device
@@ -71,6 +80,8 @@ class Server:
         self.t0 = None
 
     def submit(self, req):
+        if req.bytes > self.budget:
+            raise ValueError(f"request {req.id} needs about {req.bytes} bytes, more than the HBM budget")
         self.waiting.append(req)
         self.waiting.sort(key=lambda r: r.arrival)
 
@@ -84,7 +95,7 @@ class Server:
                 kw = {"device": self.device}
                 if self.precision:
                     kw["precision"] = self.precision
-                r.sim = Simulation.from_config(r.cfg, **kw)
+                r.sim = self.make_sim(r.cfg, **kw)
                 real = int(r.sim.info.device_bytes)
                 r.bytes = max(r.bytes, real)
                 self.used += r.bytes
@@ -99,7 +110,7 @@ class Server:
     def _retire(self):
         still = []
         for r in self.active:
-            if r.done_chunks >= r.n_chunks:
+            if r.steps_done >= r.n_chunks * r.chunk_steps:
                 r.result = {k: r.sim.get(k) for k in self.result_keys}
                 r.sim.close()
                 r.sim = None
@@ -125,23 +136,31 @@ class Server:
                 nxt = min(r.arrival for r in self.waiting)
                 if self.used == 0 and all(r.bytes > self.budget for r in self.waiting):
                     raise RuntimeError("a request does not fit the HBM budget")
-                time.sleep(max(0.0, min(0.05, nxt - now)))
+                self.sleep(max(0.0, min(0.05, nxt - now)))
                 continue
             members = [r.sim for r in self.active]
             if changed or self.batch is None or self.batch_members != [id(s) for s in members]:
                 if self.batch is not None:
                     self.batch.close()
-                self.batch = Batch(members)
+                self.batch = self.make_batch(members)
                 self.batch_members = [id(s) for s in members]
-            steps = min(r.chunk_steps for r in self.active)
+            # advance to the nearest chunk boundary among the active requests,
+            # where the ones that arrived meanwhile can join
+            steps = min(r.chunk_steps - r.steps_in_chunk for r in self.active)
             dts = np.array([r.cfg["dt"] for r in self.active])
             t_a = self.clock()
             self.batch.step(dts, steps)
-            dt_chunk = self.clock() - t_a
-            self.busy_s += dt_chunk
+            dt_run = self.clock() - t_a
+            self.busy_s += dt_run
             for r in self.active:
-                r.chunk_latency.append(dt_chunk)
-                r.done_chunks += 1
+                r.steps_done += steps
+                r.steps_in_chunk += steps
+                r.chunk_time += dt_run
+                if r.steps_in_chunk == r.chunk_steps:
+                    r.chunk_latency.append(r.chunk_time)
+                    r.done_chunks += 1
+                    r.steps_in_chunk = 0
+                    r.chunk_time = 0.0
                 self.particle_steps += steps * r.sim.n_particles
             if self._retire() and self.batch is not None:
                 self.batch.close()
