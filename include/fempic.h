@@ -321,8 +321,11 @@ int femPIC_sync(FemPIC* h);
 
 /* Copy a quantity to/from caller memory; bytes must equal its size
  * (FEMPIC_ERR_SIZE otherwise), read-only quantities reject femPIC_set
- * (FEMPIC_ERR_ARG), and a tet id out of range in FEMPIC_TET is rejected
- * before anything is copied.  Particle quantities are in particle-id order. */
+ * (FEMPIC_ERR_ARG), and a tet id out of range in FEMPIC_TET or a non-finite
+ * value in FEMPIC_X or FEMPIC_V is rejected (FEMPIC_ERR_ARG) before anything
+ * is copied.  X and TET are set one at a time: the caller keeps every
+ * position inside its owning tet, as femPIC_create checks (barycentric
+ * coordinates >= -1e-9).  Particle quantities are in particle-id order. */
 int femPIC_get(FemPIC* h, int32_t what, void* host_dst, size_t bytes);
 int femPIC_set(FemPIC* h, int32_t what, const void* host_src, size_t bytes);
 

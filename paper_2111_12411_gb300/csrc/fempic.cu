@@ -1005,6 +1005,14 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
     h->err = "NULL buffer";
     return FEMPIC_ERR_ARG;
   }
+  if (to_handle && (what == FEMPIC_X || what == FEMPIC_V) && !buf_on_device) {
+    const double* d = static_cast<const double*>(buf);
+    for (int64_t i = 0; i < 3 * h->np; ++i)
+      if (!std::isfinite(d[i])) {
+        h->err = "non-finite value at particle " + std::to_string(i / 3);
+        return FEMPIC_ERR_ARG;
+      }
+  }
   if (to_handle && what == FEMPIC_TET && !buf_on_device) {
     const int32_t* t = static_cast<const int32_t*>(buf);
     for (int64_t i = 0; i < h->np; ++i)
@@ -1191,6 +1199,11 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
     }
     const double* g = &hm.geom[(size_t)t * 16];
     const double* x = sp->x_host + 3 * i;
+    const double* v = sp->v_host + 3 * i;
+    if (!std::isfinite(v[0]) || !std::isfinite(v[1]) || !std::isfinite(v[2])) {
+      h->err = "particle " + std::to_string(i) + " has a non-finite velocity";
+      return FEMPIC_ERR_ARG;
+    }
     for (int k = 0; k < 4; ++k) {
       double l = ((g[3 * k] * x[0] + g[3 * k + 1] * x[1]) + g[3 * k + 2] * x[2]) + g[12 + k];
       if (!(l >= -1e-9)) {

@@ -103,6 +103,11 @@ def test_wall_errors():
         g.set_injection([dict(species=1, v_drift=(0, 0, 1), v_sigma=(0, 0, 0))], 1)
     assert ei.value.code == native.FEMPIC_ERR_ARG
     g.set_injection(cfg["injectors"], 5)
+    vbad = g.get("V")
+    vbad[7, 2] = np.inf
+    with pytest.raises(FemPICError) as ei:  # refused on the host before any copy
+        g.set("V", vbad)
+    assert ei.value.code == native.FEMPIC_ERR_ARG
     g.step(cfg["dt"])
     with pytest.raises(FemPICError):
         Batch([g])

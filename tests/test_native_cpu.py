@@ -115,6 +115,16 @@ def test_host_validation_errors(native):
     with pytest.raises(native.FemPICError) as ei:  # absorbing walls and the Adams-Bashforth push
         native.femPIC_create_ext(xyz, tets, 1, species, np.full((len(tets), 4), 2, dtype=np.int32), o)
     assert ei.value.code == native.FEMPIC_ERR_ARG
+    vnan = v.copy()
+    vnan[4, 1] = np.nan  # a non-finite velocity is refused on the host
+    with pytest.raises(native.FemPICError) as ei:
+        native.femPIC_create(xyz, tets, 1, -1.6e-19, 9.1e-31, 1.0, x, vnan, tet)
+    assert ei.value.code == native.FEMPIC_ERR_ARG and "velocity" in str(ei.value)
+    xinf = x.copy()
+    xinf[2, 0] = np.inf  # and a position that is not inside its tet
+    with pytest.raises(native.FemPICError) as ei:
+        native.femPIC_create(xyz, tets, 1, -1.6e-19, 9.1e-31, 1.0, xinf, v, tet)
+    assert ei.value.code == native.FEMPIC_ERR_ARG
     nonman = np.vstack([tets, tets[:1]])  # a face shared by three tets
     with pytest.raises(native.FemPICError) as ei:
         native.femPIC_create(xyz, nonman, 1, -1.6e-19, 9.1e-31, 1.0, x, v, tet)
