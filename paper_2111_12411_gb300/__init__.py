@@ -12,3 +12,4 @@ from .native import (Simulation, Batch, FemPICError, load,  # noqa: F401
                      femPIC_eval_fields, femPIC_get_info, femPIC_last_timing, femPIC_destroy,
                      femPIC_last_error, femPIC_batch_create, femPIC_batch_step,
                      femPIC_batch_timing, femPIC_batch_destroy, femPIC_batch_last_error)
+from .metrics import StepLog, run_logged  # noqa: F401,E402
