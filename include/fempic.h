@@ -333,9 +333,10 @@ int femPIC_set(FemPIC* h, int32_t what, const void* host_src, size_t bytes);
  * device, ordered on the handle's stream; synchronous on return).  Unlike
  * femPIC_set, femPIC_set_device does not range-check tet ids: the caller
  * guarantees 0 <= tet < n_tets.  A library built with -DFEMPIC_CHECKS=1
- * checks them in the particle kernels (the particle is skipped and the step
- * returns FEMPIC_ERR_BOUNDS) and checks the per-tet DOF and neighbour tables
- * once at create. */
+ * checks them on the device before copying (FEMPIC_ERR_BOUNDS, nothing
+ * copied), again in the particle kernels (the particle is skipped and the
+ * step returns FEMPIC_ERR_BOUNDS), and checks the per-tet DOF and neighbour
+ * tables once at create. */
 int femPIC_get_device(FemPIC* h, int32_t what, void* dev_dst, size_t bytes);
 int femPIC_set_device(FemPIC* h, int32_t what, const void* dev_src, size_t bytes);
 

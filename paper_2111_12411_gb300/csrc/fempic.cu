@@ -1022,6 +1022,24 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
       }
   }
   CK(cudaSetDevice(h->device));
+#if FEMPIC_CHECKS
+  if (to_handle && what == FEMPIC_TET && buf_on_device && h->np > 0) {
+    // the device path's tet ids are checked before anything is copied
+    k_check_ids<<<grid_for(h->np, 256, 1 << 20), 256, 0, h->stream>>>(h->np, static_cast<const int32_t*>(buf),
+                                                                     h->n_tets, h->d_status);
+    CK(cudaGetLastError());
+    int32_t st = 0;
+    CK(cudaMemcpyAsync(&st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (st & kStatusBounds) {
+      st &= ~kStatusBounds;
+      CK(cudaMemcpyAsync(h->d_status, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      h->err = "tet id out of range in the device buffer (checked build)";
+      return FEMPIC_ERR_BOUNDS;
+    }
+  }
+#endif
   if (what == FEMPIC_SPECIES) {  // fixed by the particle-id ranges
     std::vector<int32_t> sp((size_t)h->np);
     for (int k = 0; k < h->n_species; ++k)

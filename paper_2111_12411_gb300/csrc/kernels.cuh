@@ -33,6 +33,12 @@ __device__ __forceinline__ bool index_ok(int64_t i, int64_t n, int32_t* status) 
   return false;
 }
 
+// Checked builds: tet ids that arrive from a caller's device buffer.
+__global__ void k_check_ids(int64_t n, const int32_t* ids, int32_t n_tets, int32_t* status) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    index_ok(ids[i], n_tets, status);
+}
+
 // Checked builds, once at create: every entry of the per-tet DOF tables within
 // its space and every neighbour record (tet << 2 | face) naming a tet.
 __global__ void k_check_tables(int32_t n_tets, int nl0, int nl1, int nl2, const int32_t* dof0, const int32_t* dof1,

@@ -1,6 +1,7 @@
 """The bounds-checked build (-DFEMPIC_CHECKS=1) compiles for sm_103a on the
-CPU: tet ids in the particle kernels and the per-tet DOF and neighbour tables
-at create are range-checked, an out-of-range index sets the device status
+CPU: tet ids from a caller's device buffer (before they are copied) and in
+the particle kernels, and the per-tet DOF and neighbour tables at create, are
+range-checked; an out-of-range index sets the device status
 word (FEMPIC_ERR_BOUNDS) instead of being read.  Both the checked and the
 default translation unit export the table check's launch stub."""
 
@@ -24,7 +25,7 @@ def test_checked_build_compiles(tmp_path):
                     os.path.join(ROOT, "paper_2111_12411_gb300", "csrc", "fempic.cu"), "-o", str(obj)],
                    check=True, capture_output=True)
     syms = subprocess.run(["nm", "-C", str(obj)], check=True, capture_output=True, text=True).stdout
-    assert "k_check_tables" in syms and "femPIC_step" in syms
+    assert "k_check_tables" in syms and "k_check_ids" in syms and "femPIC_step" in syms
 
 
 def test_bounds_error_code_is_exported():
