@@ -37,6 +37,8 @@ def estimate_device_bytes(n_tets, order, n_particles):
 
 class Request:
     def __init__(self, rid, cfg, arrival, n_chunks, chunk_steps):
+        if int(n_chunks) < 1 or int(chunk_steps) < 1:
+            raise ValueError(f"request {rid}: n_chunks and chunk_steps must be at least 1")
         self.id = rid
         self.cfg = cfg
         self.arrival = arrival

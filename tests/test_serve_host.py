@@ -105,7 +105,11 @@ def test_slot_limit_and_late_arrival():
     assert [r.result["STEPS"] for r in reqs] == [12, 4, 4, 2]
 
 
-def test_oversize_request_refused():
+def test_oversize_or_empty_request_refused():
     srv = Server(1 << 20)
     with pytest.raises(ValueError):
         srv.submit(Request(0, _cfg(0, 100000, 10), 0.0, 1, 1))
+    with pytest.raises(ValueError):
+        Request(1, _cfg(1, 10, 10), 0.0, 0, 5)
+    with pytest.raises(ValueError):
+        Request(2, _cfg(2, 10, 10), 0.0, 2, 0)
