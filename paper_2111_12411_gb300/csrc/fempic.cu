@@ -1006,12 +1006,22 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
     return FEMPIC_ERR_ARG;
   }
   if (to_handle && (what == FEMPIC_X || what == FEMPIC_V) && !buf_on_device) {
+    // exponent bits all set = infinity or NaN; an OR over the array (integer
+    // work the compiler vectorises), the index only looked up on failure
     const double* d = static_cast<const double*>(buf);
-    for (int64_t i = 0; i < 3 * h->np; ++i)
-      if (!std::isfinite(d[i])) {
-        h->err = "non-finite value at particle " + std::to_string(i / 3);
-        return FEMPIC_ERR_ARG;
-      }
+    const int64_t m = 3 * h->np;
+    uint64_t bad = 0;
+    for (int64_t i = 0; i < m; ++i) {
+      uint64_t u;
+      memcpy(&u, d + i, sizeof(u));
+      bad |= (uint64_t)((u & 0x7FF0000000000000ull) == 0x7FF0000000000000ull);
+    }
+    if (bad) {
+      int64_t i = 0;
+      while (i < m && std::isfinite(d[i])) ++i;
+      h->err = "non-finite value at particle " + std::to_string(i / 3);
+      return FEMPIC_ERR_ARG;
+    }
   }
   if (to_handle && what == FEMPIC_TET && !buf_on_device) {
     const int32_t* t = static_cast<const int32_t*>(buf);
