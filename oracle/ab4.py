@@ -37,6 +37,9 @@ Readings (the paper gives no further detail):
 * Charge: rho^{n+1} from W0 at x^{n+1}, as for the straight chord.
 
 Every float operation is written in a fixed order (one rounding each).
+
+Test infrastructure only: part of the CPU oracle, which the product library
+never imports.
 """
 
 from fractions import Fraction

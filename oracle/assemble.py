@@ -21,6 +21,9 @@
 
 Integrals use the collapsed-cube rule with p + 2 points per direction (exact
 for degree 2p + 1 >= 2p).
+
+Test infrastructure only: part of the CPU oracle, which the product library
+never imports.
 """
 
 import numpy as np

@@ -22,6 +22,9 @@ The Appendix builds each basis as an interpolatory Silvester polynomial
 
 ``lam`` has shape [..., 4], ``g`` (the barycentric gradients) [..., 4, 3].
 All arithmetic is written in a fixed order, one rounding per operation.
+
+Test infrastructure only: part of the CPU oracle, which the product library
+never imports.
 """
 
 import numpy as np

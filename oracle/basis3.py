@@ -34,6 +34,9 @@ interior 3*N_e + 6*N_f + 3*tet + v; W2 faces 6*face + v, interior
 6*N_f + 12*tet + v.
 
 Values and derivatives of the multipliers are formed by the product rule.
+
+Test infrastructure only: part of the CPU oracle, which the product library
+never imports.
 """
 
 from math import factorial

@@ -41,6 +41,9 @@ and the discrete energy W = e.[*eps]e/2 + b.[*mu^-1]b/2 drops by exactly
 dt ebar.I ebar per step (ebar = (e^{n+1} + e^n)/2) without sources.  The
 wave form has no impedance term here.  Linear systems are solved directly
 (sparse LU).
+
+Test infrastructure only: part of the CPU oracle, which the product library
+never imports.
 """
 
 import numpy as np

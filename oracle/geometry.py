@@ -8,6 +8,9 @@ g_0 = -(g_1 + g_2 + g_3), c_i = -g_i . P0 (i >= 1), c_0 = 1 - (c_1 + c_2 + c_3).
 Every operation is written out in a fixed order with one rounding per
 operation (Python/numpy float64, no fused multiply-add), so that the walk's
 decisions, which depend on the signs of lambda, are reproducible.
+
+Test infrastructure only: part of the CPU oracle, which the product library
+never imports.
 """
 
 import numpy as np

@@ -23,6 +23,9 @@
   measured with the nodal basis).
 
 Every float operation is written out in a fixed order (one rounding each).
+
+Test infrastructure only: part of the CPU oracle, which the product library
+never imports.
 """
 
 import numpy as np

@@ -19,6 +19,9 @@ functions W3 (Appendix).  Readings:
   div W2 lives, so [div] b = 0 holds exactly iff div b = 0.
 * [*3] is invertible, so the constraint is imposed as [~div] b = 0.
 * mu^-1 multiplies both sides of the Galerkin system, so it is left out.
+
+Test infrastructure only: part of the CPU oracle, which the product library
+never imports.
 """
 
 import numpy as np

@@ -11,6 +11,9 @@
   {x, y >= 0, x + y <= 1}: x = u, y = (1-u) v, Jacobian (1-u); exact for
   total degree d <= 2n-2.  Returns barycentric points [Q,3] and weights
   summing to 1/2.
+
+Test infrastructure only: part of the CPU oracle, which the product library
+never imports.
 """
 
 import numpy as np

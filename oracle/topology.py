@@ -36,6 +36,9 @@ a boundary face reflects particles specularly unless its tag has bit 2 set
 marks an injection face (particles are re-injected on such faces; an
 injection face reflects unless it is also absorbing).  Bit 1 is the field
 condition above, so a tag is (impedance) | 2 (absorb) | 4 (inject).
+
+Test infrastructure only: part of the CPU oracle, which the product library
+never imports.
 """
 
 import numpy as np
