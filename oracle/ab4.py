@@ -15,18 +15,21 @@ Readings (the paper gives no further detail):
   Lagrange polynomial through (sigma = -j, v^{n-j}), j = 0..k-1: degree k in
   s, x(0) = x^n and x(1) = x^n + dt sum_j beta_j v^{n-j} = x^{n+1}.
   Coefficients x(s) = sum_m C_m s^m, C_0 = x^n, C_m = dt sum_j gam_jm v^{n-j}.
-* Walk: in each tet, lambda_i(x(s)) is a polynomial in s (lambda affine).
-  From the entry parameter s0 the interval [s0, 1] is sampled at 8 equal
-  steps; in the first step where some lambda_i turns negative, each such face
-  gets 8 safeguarded Newton steps inside that bracket (start at its middle;
-  the sign of lambda shrinks the bracket; a Newton step that leaves the
-  closed bracket is replaced by its middle); the last iterate is the
-  crossing.  The
-  exit face is the one with the smallest crossing (ties to the lowest index)
-  and the particle continues in the neighbour from that parameter.  The entry face counts as 0
-  at the entry parameter.  (A grazing excursion shorter than one sample step
-  is not split off; charge stays conserved, since the sub-path's ends are in
-  the tet and W0 is continuous there.)
+* Walk: in each tet, lambda_i(x(s)) is a polynomial in s of degree <= 4
+  (lambda affine).  The particle leaves through face i at
+  t_i = inf{ s in (s0, 1] : lambda_i(x(s)) < 0 }, the first parameter after
+  the entry parameter s0 at which lambda_i changes sign to negative (a
+  touching zero, such as a tangent path, is not a crossing).  t_i is found
+  from all the polynomial's roots (companion-matrix eigenvalues,
+  ``numpy.roots``): the real ones in (s0, 1) split the interval into pieces
+  of constant sign, the sign of each piece is read at its middle, and the
+  left end of the first negative piece is the crossing, polished by Newton
+  steps on the polynomial.  Roots closer together than ROOT_MERGE (a dip
+  that narrow is a graze that stays in the tet) count as one.  On the entry
+  face lambda vanishes at s0 exactly, so its polynomial is divided by
+  (s - s0) first and the quotient's sign decides.  The exit face is the one
+  with the smallest t_i (ties to the lowest index) and the particle
+  continues in the neighbour from that parameter.
 * Walls: the rest of the path is mirrored in the wall plane at the hit point
   (C_0 about the hit point, C_m >= 1 as vectors), and so are v^{n+1}, v^n,
   a^n and the history, so the multistep history stays consistent with the
@@ -49,8 +52,9 @@ import numpy as np
 from . import basis, geometry
 from .particles import FNV_OFFSET, FNV_PRIME
 
-N_SAMPLES = 8
-N_REFINE = 8
+ROOT_MERGE = 1e-9   # roots of one face's polynomial closer than this (in s) are one root
+ROOT_IMAG = 1e-7    # a root whose imaginary part is below this (relative) is read as real
+NEWTON_POLISH = 4
 
 
 def _lagrange_integrals(k):
@@ -107,6 +111,85 @@ def _horner_deriv(coef, s):
     return p
 
 
+def _poly(c, s):
+    """Value at s of the polynomial with ascending coefficients c (Horner)."""
+    p = c[-1]
+    for m in range(len(c) - 2, -1, -1):
+        p = p * s + c[m]
+    return p
+
+
+def _poly_d(c, s):
+    """Derivative at s of the polynomial with ascending coefficients c."""
+    if len(c) < 2:
+        return 0.0
+    p = (len(c) - 1) * c[-1]
+    for m in range(len(c) - 2, 0, -1):
+        p = p * s + m * c[m]
+    return p
+
+
+def _divide_out(c, s0):
+    """Quotient q of c(s) = (s - s0) q(s) + c(s0), ascending coefficients
+    (synthetic division)."""
+    K = len(c) - 1
+    q = np.zeros(max(K, 1))
+    acc = c[K]
+    for m in range(K - 1, -1, -1):
+        q[m] = acc
+        acc = acc * s0 + c[m]
+    return q
+
+
+def real_roots(c):
+    """Sorted real roots of the polynomial with ascending coefficients c: the
+    eigenvalues of its companion matrix (numpy.roots) whose imaginary part is
+    below ROOT_IMAG of their size.  Zero leading coefficients are dropped."""
+    c = np.trim_zeros(np.asarray(c, dtype=np.float64), "b")
+    if len(c) < 2:
+        return np.zeros(0)
+    r = np.roots(c[::-1])
+    keep = np.abs(r.imag) <= ROOT_IMAG * (1.0 + np.abs(r.real))
+    return np.sort(r.real[keep])
+
+
+def first_exit(c, s0, entry):
+    """inf{ s in (s0, 1] : f(s) < 0 } for f the polynomial lambda_i(x(s)) with
+    ascending coefficients c, or inf when f stays non-negative.
+
+    entry: face i is the one the path entered through at s0, where f vanishes;
+    f is divided by (s - s0) and the quotient (same sign on (s0, 1]) is used.
+    The real roots in (s0, 1) cut the interval into pieces of one sign; roots
+    within ROOT_MERGE of each other or of the ends count once (a narrower
+    excursion is a graze).  The first piece whose middle is negative starts
+    the crossing: s0 itself for the first piece, else a root, polished by
+    Newton steps that stay between its neighbours."""
+    c = np.asarray(c, dtype=np.float64)
+    f = _divide_out(c, s0) if entry else c
+    pts = [s0]
+    for r in real_roots(f):
+        if r - pts[-1] > ROOT_MERGE and r < 1.0 - ROOT_MERGE:
+            pts.append(float(r))
+    pts.append(1.0)
+    for k in range(len(pts) - 1):
+        mid = 0.5 * (pts[k] + pts[k + 1])
+        if _poly(f, mid) < 0.0:
+            if k == 0:
+                return s0
+            r = pts[k]
+            lo, hi = 0.5 * (pts[k - 1] + r), mid
+            for _ in range(NEWTON_POLISH):
+                d = _poly_d(f, r)
+                if d == 0.0:
+                    break
+                rn = r - _poly(f, r) / d
+                if not (lo < rn < hi):
+                    break
+                r = rn
+            return r
+    return np.inf
+
+
 def path_coeffs(x, vhist, dt, k):
     """C [n, k+1, 3] of x(s) from x^n and vhist [k, n, 3] (v^n, v^{n-1}, ...)."""
     beta, gam = ab_tables(k)
@@ -159,12 +242,16 @@ def _mirror(vec, gw, gg):
     return vec - ((2.0 * geometry.dot3(vec, gw)) / gg)[..., None] * gw
 
 
-def step(topo, g_all, c_all, x, v, tet, vh, ah, hcount, E, B, q, m, qw, dt, n1, max_cross=4096):
+def step(topo, g_all, c_all, x, v, tet, vh, ah, hcount, E, B, q, m, qw, dt, n1, max_cross=4096,
+         trace=None, dg_abs=None):
     """One AB step of every particle.
 
     vh, ah [3, n, 3]: v^{n-1..n-3}, a^{n-1..n-3} (valid: the first hcount);
     E, B gathered at x.  Returns dict with x, v, tet, vh, ah (shifted), dg,
-    ncross, hash, status and the order k used.
+    ncross, hash, status and the order k used.  trace (a list, optional)
+    receives one (particle, tet, face, s) per crossing, in walk order;
+    dg_abs (optional, [n1]) the sum of the absolute values of the terms added
+    into each DOF.
     """
     n = len(x)
     k = min(4, hcount + 1)
@@ -196,52 +283,30 @@ def step(topo, g_all, c_all, x, v, tet, vh, ah, hcount, E, B, q, m, qw, dt, n1, 
         Ta = T[act]
         A = lam_coeffs(g_all[Ta], c_all[Ta], C[act])
         s0 = s_in[act]
-        span = 1.0 - s0
-        prev = _horner(A, s0)
         ent = entry[act]
-        for i in range(4):
-            prev[ent == i, i] = 0.0
         found = np.zeros(act.size, dtype=bool)
         best = np.full(act.size, -1, dtype=np.int64)
         s1 = np.ones(act.size)
-        for j in range(1, N_SAMPLES + 1):
-            lo_s = s0 + span * ((j - 1) / N_SAMPLES)
-            hi_s = s0 + span * (j / N_SAMPLES)
-            cur = _horner(A, hi_s)
-            look = ~found
-            sbest = np.full(act.size, np.inf)
+        for r in range(act.size):
+            tbest = np.inf
             for i in range(4):
-                cand = look & (cur[:, i] < 0.0)
-                if not cand.any():
-                    continue
-                lo = lo_s.copy()
-                hi = hi_s.copy()
-                Ai = A[:, :, i:i + 1]
-                sx = (lo + hi) * 0.5
-                with np.errstate(divide="ignore", invalid="ignore"):
-                    for _ in range(N_REFINE):
-                        f = _horner(Ai, sx)[:, 0]
-                        neg = f < 0.0
-                        hi = np.where(neg, sx, hi)
-                        lo = np.where(neg, lo, sx)
-                        d = _horner_deriv(Ai, sx)[:, 0]
-                        sn = sx - f / d
-                        ok = (sn >= lo) & (sn <= hi)
-                        sx = np.where(ok, sn, (lo + hi) * 0.5)
-                upd = cand & (sx < sbest)
-                sbest[upd] = sx[upd]
-                best[upd] = i
-            hit = look & (best >= 0)
-            s1[hit] = sbest[hit]
-            found |= hit
-            prev = cur
+                ti = first_exit(A[r, :, i], s0[r], ent[r] == i)
+                if ti < tbest:                   # strict: ties keep the lowest face
+                    tbest, best[r] = ti, i
+            if best[r] >= 0:
+                found[r] = True
+                s1[r] = tbest
         contrib = _segment_currents(topo.order, A, s0, s1, qw)
         np.add.at(dg, topo.dof1[Ta].ravel(), contrib.ravel())
+        if dg_abs is not None:
+            np.add.at(dg_abs, topo.dof1[Ta].ravel(), np.abs(contrib).ravel())
 
         go = np.nonzero(found)[0]
         if go.size:
             p = act[go]
             f = best[go]
+            if trace is not None:
+                trace.extend(zip(p.tolist(), T[p].tolist(), f.tolist(), s1[go].tolist()))
             nb = topo.tet2tet[T[p], f]
             wall = nb < 0
             code = np.where(wall, np.int64(0x80000000) | f, nb).astype(np.uint64)
