@@ -86,7 +86,7 @@ def _segment_currents(order, la, lb, s0, s1, qw):
 
 
 
-def walk_deposit(topo, g_all, c_all, x0, x1, v, tet, qw, n1, max_cross=4096, absorb=None):
+def walk_deposit(topo, g_all, c_all, x0, x1, v, tet, qw, n1, max_cross=4096, absorb=None, dg_abs=None):
     """Walk every chord [x0, x1] through the mesh and deposit its current.
 
     Returns (x_end, v_end, tet_end, dg, n_cross, hash, status, absorbed)
@@ -96,7 +96,9 @@ def walk_deposit(topo, g_all, c_all, x0, x1, v, tet, qw, n1, max_cross=4096, abs
     crossing cap was hit and ``absorbed`` marks paths that ended on an
     absorbing wall (``absorb`` [n_tets, 4] bool per local face of the sorted
     tet; None: every wall reflects).  An absorbed path ends at the hit point,
-    its current deposited up to there.
+    its current deposited up to there.  ``dg_abs`` (optional, [n1]) receives
+    the sum of the absolute values of the terms added into each DOF (the
+    scale of that DOF's rounding error; the sum itself is unchanged).
     """
     n = len(x0)
     a = x0.copy()
@@ -130,6 +132,8 @@ def walk_deposit(topo, g_all, c_all, x0, x1, v, tet, qw, n1, max_cross=4096, abs
             s1 = np.where(done, 1.0, np.minimum(np.maximum(sbest, s0), 1.0))
             contrib = _segment_currents(topo.order, la, lb, s0, s1, qw)
             np.add.at(dg, topo.dof1[Ta].ravel(), contrib.ravel())
+            if dg_abs is not None:
+                np.add.at(dg_abs, topo.dof1[Ta].ravel(), np.abs(contrib).ravel())
 
             go = np.nonzero(~done)[0]
             if go.size:
@@ -176,11 +180,17 @@ def walk_deposit(topo, g_all, c_all, x0, x1, v, tet, qw, n1, max_cross=4096, abs
     return b, v, T, dg, ncross, hsh, status, absorbed
 
 
-def measure_rho(topo, g_all, c_all, x, tet, qw):
-    """rho_k = q w sum_p W0_k(x_p)."""
+def measure_rho(topo, g_all, c_all, x, tet, qw, rho_abs=None, rho_cnt=None):
+    """rho_k = q w sum_p W0_k(x_p); rho_abs (optional, [n0]) receives the sum
+    of the absolute values of the terms of each rho_k, rho_cnt (optional) the
+    sum of |q w| over the particles whose tet carries DOF k."""
     g, c = g_all[tet], c_all[tet]
     lam = geometry.lam(g, c, x)
     w0 = basis.w0(topo.order, lam)
     rho = np.zeros(topo.n0)
     np.add.at(rho, topo.dof0[tet].ravel(), (qw * w0).ravel())
+    if rho_abs is not None:
+        np.add.at(rho_abs, topo.dof0[tet].ravel(), np.abs(qw * w0).ravel())
+    if rho_cnt is not None:
+        np.add.at(rho_cnt, topo.dof0[tet].ravel(), np.full(w0.size, abs(qw)))
     return rho

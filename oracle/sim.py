@@ -105,9 +105,15 @@ class Sim:
             yield slice(self.offsets[k], self.offsets[k + 1]), q, m, w
 
     def _measure_rho(self, x, tet):
+        """rho of every species; self.rho_abs gets the sums of the absolute
+        values of its terms, self.rho_cnt the sums of |q w| of the particles
+        that contribute to each DOF."""
         rho = np.zeros(self.topo.n0)
+        self.rho_abs = np.zeros(self.topo.n0)
+        self.rho_cnt = np.zeros(self.topo.n0)
         for sl, q, m, w in self._slices():
-            rho += particles.measure_rho(self.topo, self.g, self.c, x[sl], tet[sl], q * w)
+            rho += particles.measure_rho(self.topo, self.g, self.c, x[sl], tet[sl], q * w, self.rho_abs,
+                                         self.rho_cnt)
         return rho
 
     def electrostatic_init(self):
@@ -129,6 +135,7 @@ class Sim:
         t = self.topo
         parts = []
         dg = np.zeros(t.n1)
+        dg_abs = np.zeros(t.n1)
         if self.push == "ab4":
             return self._push_walk_ab4(dt)
         for sl, q, m, w in self._slices():
@@ -137,7 +144,7 @@ class Sim:
             x1 = self.x[sl] + dt * vn
             xe, ve, te, d, ncross, hsh, st, ab = particles.walk_deposit(
                 t, self.g, self.c, self.x[sl], x1, vn, self.tet[sl], q * w, t.n1, self.max_cross,
-                absorb=t.tet_absorb if t.tet_absorb.any() else None)
+                absorb=t.tet_absorb if t.tet_absorb.any() else None, dg_abs=dg_abs)
             dg += d
             k = len(parts)
             if ab.any():
@@ -151,6 +158,7 @@ class Sim:
                               status=st, absorbed=ab))
         out = {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
         out["dg"] = dg
+        out["dg_abs"] = dg_abs
         return out
 
     def _push_walk_ab4(self, dt):
@@ -158,16 +166,19 @@ class Sim:
         t = self.topo
         parts = []
         dg = np.zeros(t.n1)
+        dg_abs = np.zeros(t.n1)
         for sl, q, m, w in self._slices():
             E, B = particles.gather(t, self.g, self.c, self.e, self.b, self.B0, self.x[sl], self.tet[sl])
             r = ab4.step(t, self.g, self.c, self.x[sl], self.v[sl], self.tet[sl], self.vh[:, sl],
-                         self.ah[:, sl], self.hcount, E, B, q, m, q * w, dt, t.n1, self.max_cross)
+                         self.ah[:, sl], self.hcount, E, B, q, m, q * w, dt, t.n1, self.max_cross,
+                         dg_abs=dg_abs)
             dg += r["dg"]
             parts.append(r)
         out = {k: np.concatenate([p[k] for p in parts]) for k in ("x", "v", "tet", "ncross", "hash", "status")}
         out["vh"] = np.concatenate([p["vh"] for p in parts], axis=1)
         out["ah"] = np.concatenate([p["ah"] for p in parts], axis=1)
         out["dg"] = dg
+        out["dg_abs"] = dg_abs
         out["order"] = parts[0]["order"] if parts else min(4, self.hcount + 1)
         return out
 
