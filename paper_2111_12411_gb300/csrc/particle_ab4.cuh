@@ -9,9 +9,10 @@
 //   x(s) = sum_m C_m s^m, C_0 = x^n, C_m = dt sum_j gam_jm v^{n-j}, s in [0, 1]
 // (the integral of the Lagrange polynomial through the last k velocities,
 // so x(1) is the Adams-Bashforth position update).  In each tet lambda(x(s))
-// is a polynomial in s: [s0, 1] is sampled at 8 equal steps, the faces that
-// turn negative in the first such step get 8 safeguarded Newton steps in that
-// bracket, the smallest crossing wins (ties to the lowest face).  Walls mirror the rest of the path
+// is a polynomial in s: each face's first sign change to negative after the
+// entry parameter is isolated by Bernstein subdivision (Descartes' rule of
+// signs on the Bernstein coefficients) and polished by safeguarded Newton
+// steps; the smallest crossing wins (ties to the lowest face).  Walls mirror the rest of the path
 // and the velocity history.  The current of each sub-path is
 // q w int W1_i(x(s)) . x'(s) ds by the (2p + 2)-point Gauss-Legendre rule,
 // exact for the degree pk + k - 1 integrand.  Every operation is rounded
@@ -24,8 +25,11 @@
 namespace fempic {
 namespace dev {
 
-constexpr int kAbSamples = 8;
-constexpr int kAbRefine = 8;
+// A sign pattern that is still ambiguous on a parameter interval shorter than
+// this (in s) is a graze: the path stays in the tet unless it ends negative.
+constexpr double kAbGraze = 9.313225746154785e-10;  // 2^-30
+constexpr int kAbMaxChecks = 256;                   // interval checks per face and sub-path
+constexpr int kAbNewton = 48;                       // safeguarded Newton steps at most
 
 // beta_j of order k (exact fractions, rounded once)
 __host__ __device__ constexpr double ab_beta(int k, int j) {
@@ -109,6 +113,113 @@ __device__ __forceinline__ void ab_mirror(double* vec, const double* gw, double 
   for (int c = 0; c < 3; ++c) vec[c] = __dsub_rn(vec[c], __dmul_rn(f, gw[c]));
 }
 
+// First s in [s0, 1] after which the polynomial c[0..n] (ascending powers of
+// s, n a compile-time degree) is negative: the crossing of a face whose lambda is c along the path.
+// Returns 2.0 when it stays non-negative (a graze included).  The interval
+// [s0, 1] is mapped to u in [0, 1]; a window [ua, ua + w] is examined through
+// the Bernstein coefficients of the polynomial on it: no sign change means no
+// root there (the window moves on and widens), one sign change with a positive
+// start means exactly one crossing (refined by Newton steps kept inside the
+// window), more sign changes halve the window.
+template <int n>
+__device__ __forceinline__ double ab_first_negative(const double (&c)[5], double s0) {
+  constexpr double binom[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0}, {1, 3, 3, 1, 0},
+                                  {1, 4, 6, 4, 1}};
+  const double span = 1.0 - s0;
+  // P(u) = c(s0 + span u): Taylor shift to s0, then scale u^k by span^k
+  double P[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) P[k] = k <= n ? c[k] : 0.0;
+#pragma unroll
+  for (int i = 0; i < n; ++i)
+#pragma unroll
+    for (int k = n - 1; k >= i; --k) P[k] = fma(s0, P[k + 1], P[k]);
+  {
+    double sc = span;
+#pragma unroll
+    for (int k = 1; k <= n; ++k) {
+      P[k] *= sc;
+      sc *= span;
+    }
+  }
+  if (n == 0) return P[0] < 0.0 ? s0 : 2.0;  // constant
+  const double wmin = kAbGraze / span;
+  double ua = 0.0, w = 1.0;
+  for (int it = 0; it < kAbMaxChecks; ++it) {
+    // q(t) = P(ua + w t), monomial then Bernstein coefficients
+    double q[5], b[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) q[k] = P[k];
+#pragma unroll
+    for (int i = 0; i < n; ++i)
+#pragma unroll
+      for (int k = n - 1; k >= i; --k) q[k] = fma(ua, q[k + 1], q[k]);
+    {
+      double sc = w;
+#pragma unroll
+      for (int k = 1; k <= n; ++k) {
+        q[k] *= sc;
+        sc *= w;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k <= n; ++k) {
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j <= k; ++j) acc = fma(binom[k][j] / binom[n][j], q[j], acc);
+      b[k] = acc;
+    }
+    // sign changes (zeros skipped) and the first nonzero sign
+    int changes = 0, first = 0, last = 0;
+#pragma unroll
+    for (int k = 0; k <= n; ++k) {
+      const int sg = b[k] > 0.0 ? 1 : (b[k] < 0.0 ? -1 : 0);
+      if (sg == 0) continue;
+      if (first == 0) first = sg;
+      if (last != 0 && sg != last) ++changes;
+      last = sg;
+    }
+    if (first < 0) return s0 + span * ua;  // negative from the window's start
+    const bool ends_negative = last < 0;
+    if (changes == 0 || (changes >= 2 && w <= wmin && !ends_negative)) {
+      ua += w;  // no root, or a graze
+      if (ua >= 1.0) return 2.0;
+      w = fmin(2.0 * w, 1.0 - ua);
+      continue;
+    }
+    if (changes >= 2 && w > wmin) {
+      w *= 0.5;
+      continue;
+    }
+    // one crossing to negative in (0, 1] of t (or a cluster narrower than the
+    // graze width that ends negative): q(0) > 0, q(1) <= 0
+    double lo = 0.0, hi = 1.0;
+    double t = b[0] / (b[0] - b[n]);
+    if (!(t > 0.0 && t < 1.0)) t = 0.5;
+    for (int k = 0; k < kAbNewton; ++k) {
+      double f = q[n], d = 0.0;
+#pragma unroll
+      for (int m = n - 1; m >= 0; --m) {
+        d = fma(d, t, f);
+        f = fma(f, t, q[m]);
+      }
+      if (f < 0.0)
+        hi = t;
+      else
+        lo = t;
+      double tn = d != 0.0 ? t - f / d : 0.5 * (lo + hi);
+      if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+      if (tn == t || hi - lo <= 2.220446049250313e-16) {
+        t = tn;
+        break;
+      }
+      t = tn;
+    }
+    return s0 + span * (ua + w * t);
+  }
+  return 2.0;
+}
+
 // K: the Adams-Bashforth order of the step (a template parameter, so the path
 // and lambda coefficients stay in registers)
 template <int P, int K>
@@ -188,34 +299,36 @@ __global__ void __launch_bounds__(128) k_particle_ab4(Ab4Args A) {
                                      __dmul_rn(G.g[f][2], C[m][2]));
           L[m][f] = m == 0 ? __dadd_rn(t, G.c[f]) : t;
         }
-      const double span = __dsub_rn(1.0, s0);
       int best = -1;
       double s1 = 1.0;
-      for (int j = 1; j <= kAbSamples && best < 0; ++j) {
-        const double lo_s = __dadd_rn(s0, __dmul_rn(span, (double)(j - 1) / kAbSamples));
-        const double hi_s = __dadd_rn(s0, __dmul_rn(span, (double)j / kAbSamples));
-        double sbest = __longlong_as_double(0x7ff0000000000000ll);
+      {
+        double sbest = 2.0;
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-          if (!(ab_horner<K>(L, f, hi_s) < 0.0)) continue;
-          double lo = lo_s, hi = hi_s;
-          double sx = __dmul_rn(__dadd_rn(lo, hi), 0.5);
-          for (int it = 0; it < kAbRefine; ++it) {
-            const double fv = ab_horner<K>(L, f, sx);
-            if (fv < 0.0)
-              hi = sx;
-            else
-              lo = sx;
-            const double dv = ab_horner_d<K>(L, f, sx);
-            const double sn = __dsub_rn(sx, __ddiv_rn(fv, dv));
-            sx = (sn >= lo && sn <= hi) ? sn : __dmul_rn(__dadd_rn(lo, hi), 0.5);
+          double cf[5];
+#pragma unroll
+          for (int m = 0; m < 5; ++m) cf[m] = m <= K ? L[m][f] : 0.0;
+          double sf;
+          if (f == entry) {
+            // lambda of the entry face vanishes at s0: divide out (s - s0)
+            double acc = cf[K];
+#pragma unroll
+            for (int m = K - 1; m >= 0; --m) {
+              const double nx = fma(acc, s0, cf[m]);
+              cf[m] = acc;
+              acc = nx;
+            }
+            cf[K] = 0.0;
+            sf = ab_first_negative<K - 1>(cf, s0);
+          } else {
+            sf = ab_first_negative<K>(cf, s0);
           }
-          if (sx < sbest) {
-            sbest = sx;
+          if (sf < sbest) {
+            sbest = sf;
             best = f;
           }
         }
-        if (best >= 0) s1 = sbest;
+        if (best >= 0) s1 = fmin(fmax(sbest, s0), 1.0);
       }
       // current of the sub-path [s0, s1]
       {
@@ -311,7 +424,6 @@ __global__ void __launch_bounds__(128) k_particle_ab4(Ab4Args A) {
         s0 = s1;
         entry = best;
       }
-      (void)entry;
       if (nc >= a.max_cross) {
         atomicOr(a.status, kStatusWalk);
         break;

@@ -3,11 +3,18 @@ against the oracle, through the C ABI.
 
 Every step starts both sides from the same fields (the oracle's e, b are set
 on the device), so the particle half of each step is compared on its own
-across the AB1 -> AB4 start-up: positions, velocities, owning tets and
-crossing-sequence hashes bit-exact (one rounding per operation on both
-sides), the current rel 1e-12 (atomics reorder the sums; the Gauss-Legendre
-abscissae are written independently on each side), charge conserved on the
-device to 1e-12.
+across the AB1 -> AB4 start-up.  The two sides find a face crossing
+independently (the oracle from the roots of lambda_i(x(s)), the kernel by
+Bernstein subdivision), so the decisions must agree exactly: owning tets,
+crossing counts and crossing-sequence hashes bit-exact.  Velocities do not
+depend on a crossing parameter (a wall mirrors them by its face alone):
+bit-exact after the first step.  Positions depend on it only through wall
+hit points: within 1e-12 of the unit box; those ~1e-16 differences feed the
+next step's field gather, so later velocities are held to 1e-12 per
+element.  The current per DOF within 1e-12 of the sum of the
+absolute values of its terms (the crossing parameters agree to about 1e-12
+in the worst-conditioned case and to rounding otherwise; atomics reorder the
+sums), charge conserved on the device to 1e-12.
 """
 
 import numpy as np
@@ -15,7 +22,7 @@ import pytest
 
 import workloads
 from oracle import sim as osim
-from gpu_helpers import build_lib, rel
+from gpu_helpers import assert_close_to_scale, assert_elementwise, build_lib
 from test_oracle_boundary_species import M_E, M_SR, Q_E
 
 pytestmark = pytest.mark.gpu
@@ -60,13 +67,15 @@ def test_ab4_steps_match_oracle(order, species):
         w = o.step(dt)
         g.step(dt)
         assert w["order"] == min(4, k + 1)
-        assert np.array_equal(g.get("X"), w["x"])
-        assert np.array_equal(g.get("V"), w["v"])
         assert np.array_equal(g.get("TET"), w["tet"])
         assert np.array_equal(g.get("NCROSS"), w["ncross"])
         assert np.array_equal(g.get("HASH"), w["hash"])
-        assert rel(g.get("DG"), w["dg"]) < 1e-12
-        assert rel(g.get("RHO"), o.rho) < 1e-12
+        if k == 0:
+            assert np.array_equal(g.get("V"), w["v"])
+        assert_close_to_scale(g.get("V"), w["v"], 1e-12, "v")
+        assert np.abs(g.get("X") - w["x"]).max() <= 1e-12
+        assert_elementwise(g.get("DG"), w["dg"], w["dg_abs"], 1e-12, "dg")
+        assert_elementwise(g.get("RHO"), o.rho, o.rho_abs, 1e-12, "rho")
         d = g.diag()
         assert d["continuity_abs"] <= 1e-12 * d["continuity_ref"]
     assert w["ncross"].sum() > 1000 and w["ncross"].max() < 50
@@ -97,5 +106,5 @@ def test_ab4_restarts_history_on_set():
     w = fresh.step(dt)
     g.step(dt)
     assert w["order"] == 1
-    assert np.array_equal(g.get("X"), w["x"]) and np.array_equal(g.get("TET"), w["tet"])
+    assert np.abs(g.get("X") - w["x"]).max() <= 1e-12 and np.array_equal(g.get("TET"), w["tet"])
     g.close()
