@@ -8,7 +8,7 @@
  * Finite Element Particle in Cell Method" (arXiv 2111.12411):
  *
  *   - E is expanded in order-p interpolatory Whitney edge functions W1 and B in
- *     face functions W2 (Section III-A, Appendix), p = 1 or 2;
+ *     face functions W2 (Section III-A, Appendix), p = 1, 2 or 3;
  *   - each step gathers E and B at every particle, applies the Lorentz force
  *     (Section II), moves the particle on a straight chord, walks the chord
  *     through the tets by ray-face intersection, and deposits the exact path
@@ -49,7 +49,13 @@
  *     (lattice point nearer the lower vertex first), then N_n + 2*N_e + face.
  *   - Units are SI.  Boundary faces are perfect electric conductors (W1 DOFs
  *     on them held at 0) unless femPIC_create_ext tags them impedance
- *     (first-order absorbing); particles reflect specularly at every wall.
+ *     (first-order absorbing).  Particles reflect specularly at a wall unless
+ *     femPIC_create_ext tags its face absorbing: there the path ends at the
+ *     wall and the particle is re-injected on the faces tagged injecting
+ *     (femPIC_set_injection).
+ *   - Besides the Boris push on a straight chord (the default), opts.push
+ *     selects the paper's Adams-Bashforth 4 push on a polynomial path
+ *     (Section III-B), orders 1 and 2.
  */
 #ifndef FEMPIC_H
 #define FEMPIC_H
@@ -194,7 +200,11 @@ typedef struct {
   int32_t push;         /* FEMPIC_PUSH_* (default FEMPIC_PUSH_BORIS)           */
 } femPIC_opts;
 
-/* Per-step diagnostics (Section IV-D): continuity and Gauss residuals. */
+/* Per-step diagnostics (Section IV-D): continuity and Gauss residuals.
+   femPIC_get(FEMPIC_DIAG) computes the continuity, Gauss and div b residuals
+   of the state as it is at the call (after the first step; zeros before it),
+   so a state changed by femPIC_set shows in them; the CG figures, crossings
+   and absorbed counts are those of the last step. */
 typedef struct {
   int64_t steps;            /* steps taken since create                        */
   int32_t status;           /* latched FEMPIC_* status of the device            */
@@ -232,6 +242,9 @@ typedef struct {
   int32_t n_impedance_faces; /* boundary faces with the absorbing condition   */
   int32_t n_absorb_faces;   /* boundary faces that absorb particles            */
   int32_t n_inject_faces;   /* boundary faces particles are re-injected on     */
+  int64_t device_allocations; /* device allocations (cudaMalloc) this library has
+                               made in the process so far, all handles and
+                               batches together (not a per-handle figure)     */
 } femPIC_info;
 
 /* Fill *opts with defaults: FP64, trapezoid, cg_rtol 1e-12, cg_max_it 2000,
@@ -362,8 +375,15 @@ int femPIC_eval_fields(FemPIC* h, int64_t n, const double* x_host, const int32_t
  *   - at most FEMPIC_PROBE_MAX_POINTS points per call; larger n returns
  *     FEMPIC_ERR_SIZE and touches nothing;
  *   - the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture starts;
+ *     (cudaGetSymbolAddress) with that device current, and so does the first
+ *     call after that device's context was created anew (a cudaDeviceReset,
+ *     say): the address is cached with the id of the context it belongs to;
+ *     under CUDA's lazy module loading the first call per device, order and
+ *     precision mode also loads the field kernel, which may allocate and
+ *     synchronise inside the CUDA runtime: make these first calls before any
+ *     stream capture or latency-critical work starts;
+ *   - femPIC_info.device_allocations does not change across a call after
+ *     those first ones;
  *   - all calls share the array and it keeps the last call's contents; every
  *     output value is rewritten by each call, so nothing needs clearing.
  *     Calls that overlap on the GPU (from several host threads or handles at

@@ -7,10 +7,12 @@
 //   -> k_rhs: Newmark right-hand side -> k_pcg: ([*eps] + dt^2/4 K) e^{n+1} = rhs
 //   -> k_bupdate: b^{n+1} = b^n - dt/2 C (e^{n+1} + e^n) -> [diagnostics]
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -28,6 +30,20 @@
 #include "particle_ab4.cuh"
 #include "project.cuh"
 #include "inject.cuh"
+
+namespace {
+// Device allocations made by this library in this process (all handles and
+// batches): reported by femPIC_get_info, so a caller can check that a call
+// allocated nothing.
+std::atomic<long long> g_device_allocations{0};
+
+template <typename T>
+cudaError_t counted_malloc(T** p, size_t bytes) {
+  const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  if (e == cudaSuccess) g_device_allocations.fetch_add(1, std::memory_order_relaxed);
+  return e;
+}
+}  // namespace
 
 using namespace fempic;
 using namespace fempic::dev;
@@ -197,7 +213,7 @@ template <class T>
 int dalloc(FemPIC* h, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  cudaError_t e = counted_malloc((void**)p, count * sizeof(T));
   if (e != cudaSuccess) {
     h->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
     *p = nullptr;
@@ -1065,6 +1081,10 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
   if (what == FEMPIC_DIAG) {
     femPIC_diag d;
     memset(&d, 0, sizeof(d));
+    if (h->steps > 0) {  // residuals of the state as it is now (after any femPIC_set)
+      const int rc = diagnostics(h);
+      if (rc) return rc;
+    }
     double norms[6];
     CK(cudaMemcpyAsync(norms, h->d_norms, sizeof(norms), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(&d.cg_iterations, h->d_cg_iters, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
@@ -1725,8 +1745,8 @@ int femPIC_apply(FemPIC* h, int32_t op, const double* x_host, size_t nx, double*
   }
   CK(cudaSetDevice(h->device));
   double *dx = nullptr, *dy = nullptr;
-  CK(cudaMalloc(&dx, sizeof(double) * std::max<size_t>(nx, 1)));
-  if (cudaMalloc(&dy, sizeof(double) * std::max<size_t>(ny, 1)) != cudaSuccess) {
+  CK(counted_malloc(&dx, sizeof(double) * std::max<size_t>(nx, 1)));
+  if (counted_malloc(&dy, sizeof(double) * std::max<size_t>(ny, 1)) != cudaSuccess) {
     cudaFree(dx);
     h->err = "cudaMalloc failed";
     return FEMPIC_ERR_OOM;
@@ -1755,10 +1775,10 @@ int femPIC_eval_fields(FemPIC* h, int64_t n, const double* x_host, const int32_t
   CK(cudaSetDevice(h->device));
   double *dx = nullptr, *dE = nullptr, *dB = nullptr;
   int32_t* dt = nullptr;
-  CK(cudaMalloc(&dx, sizeof(double) * 3 * n));
-  CK(cudaMalloc(&dE, sizeof(double) * 3 * n));
-  CK(cudaMalloc(&dB, sizeof(double) * 3 * n));
-  CK(cudaMalloc(&dt, sizeof(int32_t) * n));
+  CK(counted_malloc(&dx, sizeof(double) * 3 * n));
+  CK(counted_malloc(&dE, sizeof(double) * 3 * n));
+  CK(counted_malloc(&dB, sizeof(double) * 3 * n));
+  CK(counted_malloc(&dt, sizeof(int32_t) * n));
   CK(cudaMemcpy(dx, x_host, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(dt, tet_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice));
   int grid = grid_for(n, 128, 1 << 30);
@@ -1787,25 +1807,64 @@ static __device__ __align__(256) unsigned char g_probe_scratch[kProbeBytes];
 
 constexpr int kProbeMaxDevices = 64;
 std::mutex g_probe_mutex;
-void* g_probe_ptr[kProbeMaxDevices] = {};
+struct ProbeSlot {
+  unsigned long long ctx_id = 0;  // context the address belongs to (0: none yet)
+  void* ptr = nullptr;
+};
+ProbeSlot g_probe_slot[kProbeMaxDevices];
 
-// device address of g_probe_scratch on the current device (nullptr on error)
+// Unique id of the calling thread's current CUDA context, through the driver
+// entry points the runtime hands out (the library does not link libcuda);
+// 0 when it cannot be read.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    looked_up = true;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// device address of g_probe_scratch in the current context of `device`
+// (nullptr on error).  The address is cached per device together with the
+// context it was read in, and read again when the context changed (after a
+// cudaDeviceReset, say), or every time if the context id cannot be read.
 void* probe_scratch(int device, std::string* err) {
   if (device < 0 || device >= kProbeMaxDevices) {
     *err = "device ordinal out of range for the probe scratch table";
     return nullptr;
   }
   std::lock_guard<std::mutex> lock(g_probe_mutex);
-  if (!g_probe_ptr[device]) {
+  const unsigned long long ctx = current_context_id();
+  ProbeSlot& slot = g_probe_slot[device];
+  if (!slot.ptr || ctx == 0 || slot.ctx_id != ctx) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_probe_scratch);
     if (e != cudaSuccess || !p) {
       *err = std::string("cudaGetSymbolAddress(probe scratch): ") + cudaGetErrorString(e);
+      slot = ProbeSlot();
       return nullptr;
     }
-    g_probe_ptr[device] = p;
+    slot.ptr = p;
+    slot.ctx_id = ctx;
   }
-  return g_probe_ptr[device];
+  return slot.ptr;
 }
 }  // namespace
 
@@ -1860,6 +1919,7 @@ int femPIC_get_info(const FemPIC* h, femPIC_info* info) {
   info->nl1 = h->nl1;
   info->nl2 = h->nl2;
   info->n_particles = h->np;
+  info->device_allocations = g_device_allocations.load(std::memory_order_relaxed);
   info->nnz_A = h->M.nnz;
   info->nnz_C = h->C.nnz;
   info->nnz_Q = h->Q.nnz;
@@ -1947,7 +2007,7 @@ namespace {
 
 template <class T>
 int balloc(FemPICBatch* b, T** p, size_t n) {
-  cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T));
+  cudaError_t e = counted_malloc((void**)p, std::max<size_t>(n, 1) * sizeof(T));
   if (e != cudaSuccess) {
     b->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? FEMPIC_ERR_OOM : FEMPIC_ERR_CUDA;
@@ -2508,7 +2568,7 @@ extern "C" int femPIC_measure_alu(int32_t device, int32_t kind, double* ops_per_
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return FEMPIC_ERR_CUDA;
   const int blocks = prop.multiProcessorCount * 4, threads = 256;
   void* buf = nullptr;
-  if (cudaMalloc(&buf, 64) != cudaSuccess) return FEMPIC_ERR_CUDA;
+  if (counted_malloc(&buf, 64) != cudaSuccess) return FEMPIC_ERR_CUDA;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = FEMPIC_OK;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = FEMPIC_ERR_CUDA;

@@ -12,7 +12,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfempic.so")
+# FEMPIC_LIB selects another build of the library (the test variants of build.py)
+LIB_PATH = os.environ.get("FEMPIC_LIB") or os.path.join(_HERE, "libfempic.so")
 
 FEMPIC_OK, FEMPIC_ERR_ARG, FEMPIC_ERR_MESH, FEMPIC_ERR_OOM, FEMPIC_ERR_CUDA = 0, 1, 2, 3, 4
 FEMPIC_ERR_CG, FEMPIC_ERR_WALK, FEMPIC_ERR_SIZE, FEMPIC_ERR_STATE, FEMPIC_ERR_BARRIER = 5, 6, 7, 8, 9
@@ -69,7 +70,8 @@ class femPIC_info(ctypes.Structure):
                 ("n_boundary_faces", ctypes.c_int32), ("device_bytes", ctypes.c_size_t),
                 ("nnz_L", ctypes.c_int64), ("nnz_V", ctypes.c_int64), ("aux_cheb_degree", ctypes.c_int32),
                 ("n_species", ctypes.c_int32), ("n_impedance_faces", ctypes.c_int32),
-                ("n_absorb_faces", ctypes.c_int32), ("n_inject_faces", ctypes.c_int32)]
+                ("n_absorb_faces", ctypes.c_int32), ("n_inject_faces", ctypes.c_int32),
+                ("device_allocations", ctypes.c_int64)]
 
 
 # (name, restype, argtypes) of every exported symbol declared in include/fempic.h

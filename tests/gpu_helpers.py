@@ -37,3 +37,50 @@ def rel(a, b):
     a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
     den = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def assert_elementwise(a, b, scale, tol, what):
+    """|a_k - b_k| <= tol * scale_k for every element k.
+
+    For a deposited vector, scale_k is the oracle's sum of the absolute
+    values of the terms added into element k (the size of its rounding error
+    whatever the order of the sum), so a small element is held to its own
+    terms and not to the vector's norm; an element with no terms must be
+    exactly zero on both sides."""
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    err = np.abs(a - b)
+    bound = tol * np.asarray(scale, dtype=np.float64)
+    bad = np.nonzero(~(err <= bound))[0]
+    assert bad.size == 0, (f"{what}: {bad.size} of {a.size} elements off; first {bad[:4].tolist()} "
+                           f"err {err[bad[:4]].tolist()} bound {bound[bad[:4]].tolist()}")
+
+
+def assert_close_to_scale(a, b, tol, what, floor=1e-3):
+    """|a_k - b_k| <= tol * max(|b_k|, floor * max|b|) for every element:
+    per-element relative error, with a floor for elements near zero."""
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    scale = np.maximum(np.abs(b), floor * (np.abs(b).max() if b.size else 0.0))
+    assert_elementwise(a, b, scale, tol, what)
+
+
+def assert_rho(g_rho, o, precision, what="rho"):
+    """Charge per W0 DOF against the oracle.  Strict mode evaluates every W0
+    term with the oracle's formulas: 1e-12 of the sum of the terms' absolute
+    values.  A contracted kernel (fused multiply-adds) evaluates W0 at
+    barycentric coordinates that differ by a few ulps; the order-p Lagrange
+    function amplifies an absolute difference in lambda by its derivative
+    (at most ~2 p^2), so each term may differ by ~1e-14 |q w| whatever its own
+    size: 1e-12 of the terms plus 1e-14 |q w| per contributing particle."""
+    scale = o.rho_abs if precision == "fp64_strict" else o.rho_abs + 1e-2 * o.rho_cnt
+    assert_elementwise(g_rho, o.rho, scale, 1e-12, what)
+
+
+def assert_solves_system(A, e, rhs, rhs_terms, rtol, what="e"):
+    """||A e - rhs|| <= 10 rtol ||rhs|| + 256 eps ||rhs_terms||: the device
+    solved its own right-hand side to rtol, which differs from the oracle's by
+    the rounding of the terms that make it up (rhs_terms: the sum of their
+    absolute values per row; they cancel when e is a gradient field)."""
+    eps = np.finfo(np.float64).eps
+    res = np.linalg.norm(A @ e - rhs)
+    bound = 10 * rtol * np.linalg.norm(rhs) + 256 * eps * np.linalg.norm(rhs_terms)
+    assert res <= bound, f"{what}: residual {res:.3e} > bound {bound:.3e}"

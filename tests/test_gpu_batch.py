@@ -6,14 +6,18 @@ FP64 (same arithmetic; only the order of the FP64 atomic current sums
 differs, and it feeds the field solve), 2e-6 with the FP32 push (a last-bit
 field difference can flip an FP32 rounding); fields rel 1e-6 (CG stopped at
 rel 1e-12 residual on systems with condition numbers up to ~1e6); charge
-conservation 1e-12."""
+conservation 1e-12.  After one step from the same field state the batched
+particle kernel (the single-instance kernel's step, run per member) must give
+bit-identical positions, velocities, tets and crossing hashes; and one batched
+step of each member is checked against the oracle."""
 
 import numpy as np
 import pytest
 
 import workloads
-from oracle import topology as otopo
-from gpu_helpers import build_lib, rel
+from oracle import fields as ofields, geometry, sim as osim, topology as otopo
+from gpu_helpers import (assert_close_to_scale, assert_elementwise, assert_rho, assert_solves_system,
+                         build_lib, random_state, rel)
 
 pytestmark = pytest.mark.gpu
 
@@ -36,12 +40,24 @@ def test_batch_matches_members_alone():
     assert len({c["order"] for c in cfgs}) == 2  # both orders in the mix
     alone = [Simulation.from_config(c) for c in cfgs]
     mixed = [Simulation.from_config(c) for c in cfgs]
+    rng = np.random.default_rng(21)
+    for a, m, c in zip(alone, mixed, cfgs):      # one field state for both (a kick of about v_th per step)
+        e, b = random_state(otopo.Topology(c["xyz"], c["tets"], c["order"]), rng, e_scale=10.0, b_scale=1e-5)
+        for s in (a, m):
+            s.set("E", e)
+            s.set("E_PREV", e)
+            s.set("B", b)
     batch = Batch(mixed)
     dts = np.array([c["dt"] for c in cfgs])
-    rho0 = [s.get("RHO") for s in mixed]
     for s, c in zip(alone, cfgs):
-        s.step(c["dt"], 3)
-    batch.step(dts, 3)
+        s.step(c["dt"])
+    batch.step(dts)
+    for k, (a, m) in enumerate(zip(alone, mixed)):
+        for q in ("X", "V", "TET", "HASH", "NCROSS"):
+            assert np.array_equal(m.get(q), a.get(q)), (k, q)
+    for s, c in zip(alone, cfgs):
+        s.step(c["dt"], 2)
+    batch.step(dts, 2)
     t = batch.timing()
     assert t["launches_per_step"] > 0
     for k, (a, m, c) in enumerate(zip(alone, mixed, cfgs)):
@@ -104,3 +120,68 @@ def test_autotune_picks_a_candidate_and_keeps_results():
     batch.close()
     for s in alone + mixed:
         s.close()
+
+
+def test_batch_member_one_step_matches_oracle():
+    """One batched step (Section III-B cycle) of an order-1 and an order-2 FP64
+    member and an order-2 mixed member, each from a random field state set on
+    both sides, against the oracle.  FP64 (contracted) members: positions
+    within 1e-12 of the unit box, velocities per element within 1e-12 of their
+    size, tets, crossing counts
+    and hashes equal, the current per DOF within 1e-11 of its terms (midpoint
+    against 2-point Gauss rule), the field solve satisfying the oracle's
+    system, b^{n+1} equal to the oracle's Faraday update of the member's own
+    e^{n+1}.  Mixed member (FP32 gather and push): positions and velocities
+    within 2e-6, tets equal where the end point is not within 1e-5 of a face.
+    Charge conserved on the device for every member."""
+    from paper_2111_12411_gb300 import Batch, Simulation
+    cfgs = workloads.make_batch(n_instances=3, np_range=(4e3, 8e3), nt_range=(2e3, 4e3), steps=1,
+                                seed=77, precision="fp64")
+    cfgs[0]["order"], cfgs[1]["order"], cfgs[2]["order"] = 1, 2, 2
+    cfgs[2]["precision"] = "mixed"
+    rng = np.random.default_rng(22)
+    sims, oracles = [], []
+    for c in cfgs:
+        o = osim.Sim(c["xyz"], c["tets"], c["order"], c["q"], c["m"], c["weight"], c["B0"], c["rho_ion"])
+        o.set_particles(c["x"], c["v"], c["tet"])
+        e, b = random_state(o.topo, rng, e_scale=10.0, b_scale=1e-5)
+        o.e, o.e_prev, o.b = e.copy(), e.copy(), b.copy()
+        g = Simulation.from_config(c, es_init=False, diagnostics=True)
+        g.set("E", e)
+        g.set("E_PREV", e)
+        g.set("B", b)
+        sims.append(g)
+        oracles.append((o, e, b))
+    batch = Batch(sims)
+    batch.step(np.array([c["dt"] for c in cfgs]))
+    for k, (g, (o, e, b), c) in enumerate(zip(sims, oracles, cfgs)):
+        w = o.step(c["dt"])
+        d = g.diag()
+        assert d["continuity_abs"] <= 1e-12 * d["continuity_ref"], k
+        if c["precision"] == "mixed":
+            assert_close_to_scale(g.get("X"), w["x"], 2e-6, f"x[{k}]")
+            assert_close_to_scale(g.get("V"), w["v"], 2e-6, f"v[{k}]")
+            ok = geometry.lam(o.g[w["tet"]], o.c[w["tet"]], w["x"]).min(axis=1) > 1e-5
+            assert ok.mean() > 0.98
+            assert np.array_equal(g.get("TET")[ok], w["tet"][ok]), k
+            continue
+        assert np.abs(g.get("X") - w["x"]).max() <= 1e-12      # unit box
+        assert_close_to_scale(g.get("V"), w["v"], 1e-12, f"v[{k}]")
+        for q, key in (("TET", "tet"), ("NCROSS", "ncross"), ("HASH", "hash")):
+            assert np.array_equal(g.get(q), w[key]), (k, q)
+        assert_elementwise(g.get("DG"), w["dg"], w["dg_abs"], 1e-11, f"dg[{k}]")
+        assert_rho(g.get("RHO"), o, "fp64", f"rho[{k}]")
+        A = ofields.system_matrix(o.M, o.K, c["dt"], "trapezoid")
+        eg = g.get("E")
+        fr = o.topo.free1
+        dgg = g.get("DG")                    # the member's own current, as on the device
+        rhs = ofields.rhs_trapezoid(o.M, o.K, o.CtM2, e, b, dgg, c["dt"])
+        terms = abs(o.M) @ np.abs(e) + (0.25 * c["dt"] ** 2) * (abs(o.K) @ np.abs(e)) \
+            + c["dt"] * (abs(o.CtM2) @ np.abs(b)) + np.abs(dgg)
+        assert_solves_system(A[fr][:, fr], eg[fr], rhs[fr], terms[fr], 1e-12, f"e[{k}]")
+        want = ofields.update_b(o.C, b, eg, e, c["dt"])
+        scale = np.abs(b) + (0.5 * c["dt"]) * (abs(o.C) @ (np.abs(eg) + np.abs(e)))
+        assert_elementwise(g.get("B"), want, scale, 1e-13, f"b[{k}]")
+    batch.close()
+    for g in sims:
+        g.close()

@@ -19,7 +19,7 @@ import pytest
 
 import workloads
 from oracle import particles as opart, sim as osim
-from gpu_helpers import build_lib, random_state, rel
+from gpu_helpers import assert_elementwise, build_lib, random_state, rel, assert_rho
 
 pytestmark = pytest.mark.gpu
 
@@ -105,8 +105,8 @@ def test_one_step_parity_order3(cfg, o3, precision):
     else:
         assert rel(xg, w["x"]) < 1e-12 and rel(vg, w["v"]) < 1e-12
     assert w["ncross"].mean() > 0.5
-    assert rel(g.get("DG"), w["dg"]) < 1e-12
-    assert rel(g.get("RHO"), o.rho) < 1e-12
+    assert_elementwise(g.get("DG"), w["dg"], w["dg_abs"], 1e-12 if precision == "fp64_strict" else 1e-11, "dg")
+    assert_rho(g.get("RHO"), o, precision)
     from oracle import fields as ofields
     A = ofields.system_matrix(o.M, o.K, dt, "trapezoid")
     eg = g.get("E")

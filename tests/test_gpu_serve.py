@@ -53,3 +53,60 @@ def test_serving_continuous_batching_results_match_alone():
         assert rel(r.result["E"], alone.get("E")) < 1e-6, r.id
         assert rel(r.result["RHO"], alone.get("RHO")) < tol, r.id
         alone.close()
+
+
+def test_served_requests_match_oracle():
+    """Four requests (orders 1 and 2, FP64 and FP32 push) admitted together
+    and advanced in one batch by one step each; each result is checked
+    against the oracle's step (Section III-B cycle) of the request's own inputs
+    from the device's electrostatic start e^0 (read back as E_PREV).  FP64:
+    positions within 1e-12 of the unit box, velocities per element within
+    1e-12 of their size, tets,
+    crossing counts and hashes equal, current per DOF within 1e-11 of its
+    terms; FP32 push: positions and velocities within 2e-6, tets equal where
+    the end point is not within 1e-5 of a face.  Every request's e^{n+1}
+    satisfies the oracle's trapezoidal system built from its own e^0 and
+    Delta g to 10 cg_rtol plus the rounding of the right-hand side's terms."""
+    from oracle import fields as ofields, geometry, sim as osim
+    from paper_2111_12411_gb300.serve import Request, Server
+    from gpu_helpers import assert_close_to_scale, assert_elementwise, assert_rho, assert_solves_system
+
+    reqs = []
+    for i, (order, prec) in enumerate([(1, "fp64"), (2, "fp64"), (1, "mixed"), (2, "mixed")]):
+        cfg = workloads.configs._box_instance(6, order, 3000 + 500 * i, 1.0e6, 0.3, 2000 + i,
+                                              precision=prec, steps=1)
+        reqs.append(Request(i, cfg, arrival=0.0, n_chunks=1, chunk_steps=1))
+    server = Server(sum(r.bytes for r in reqs), max_slots=4,
+                    result_keys=("X", "V", "TET", "NCROSS", "HASH", "E", "E_PREV", "DG", "RHO"))
+    for r in reqs:
+        server.submit(r)
+    done = server.run(max_wall_s=600)
+    assert len(done) == len(reqs)
+    for r in done:
+        c, res = r.cfg, r.result
+        o = osim.Sim(c["xyz"], c["tets"], c["order"], c["q"], c["m"], c["weight"], c["B0"], c["rho_ion"])
+        o.set_particles(c["x"], c["v"], c["tet"])
+        e0 = res["E_PREV"]
+        o.e, o.e_prev = e0.copy(), e0.copy()
+        w = o.step(c["dt"])
+        if c["precision"] == "mixed":
+            assert_close_to_scale(res["X"], w["x"], 2e-6, f"x[{r.id}]")
+            assert_close_to_scale(res["V"], w["v"], 2e-6, f"v[{r.id}]")
+            ok = geometry.lam(o.g[w["tet"]], o.c[w["tet"]], w["x"]).min(axis=1) > 1e-5
+            assert ok.mean() > 0.98
+            assert np.array_equal(res["TET"][ok], w["tet"][ok]), r.id
+        else:
+            assert np.abs(res["X"] - w["x"]).max() <= 1e-12      # unit box
+            assert_close_to_scale(res["V"], w["v"], 1e-12, f"v[{r.id}]")
+            assert np.array_equal(res["TET"], w["tet"]), r.id
+            assert np.array_equal(res["NCROSS"], w["ncross"]), r.id
+            assert np.array_equal(res["HASH"], w["hash"]), r.id
+            assert_elementwise(res["DG"], w["dg"], w["dg_abs"], 1e-11, f"dg[{r.id}]")
+            assert_rho(res["RHO"], o, "fp64", f"rho[{r.id}]")
+        A = ofields.system_matrix(o.M, o.K, c["dt"], "trapezoid")
+        rhs = ofields.rhs_trapezoid(o.M, o.K, o.CtM2, e0, np.zeros(o.topo.n2), res["DG"], c["dt"])
+        fr = o.topo.free1
+        # e^0 is a gradient field, so M e^0 - dt^2/4 K e^0 cancels: the check allows the
+        # rounding of those terms (assert_solves_system)
+        terms = abs(o.M) @ np.abs(e0) + (0.25 * c["dt"] ** 2) * (abs(o.K) @ np.abs(e0)) + np.abs(res["DG"])
+        assert_solves_system(A[fr][:, fr], res["E"][fr], rhs[fr], terms[fr], 1e-12, f"e[{r.id}]")

@@ -42,16 +42,17 @@ def test_exports_every_declared_symbol(native):
 def test_struct_layouts_match_c(native, tmp_path):
     prog = tmp_path / "sizes.c"
     prog.write_text('#include "fempic.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                    'int main(){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(femPIC_mesh),'
+                    'int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(femPIC_mesh),'
                     ' sizeof(femPIC_species), sizeof(femPIC_opts), sizeof(femPIC_diag),'
-                    ' sizeof(femPIC_info), offsetof(femPIC_opts, stream), offsetof(femPIC_info, device_bytes));return 0;}\n')
+                    ' sizeof(femPIC_info), offsetof(femPIC_opts, stream), offsetof(femPIC_info, device_bytes),'
+                    ' offsetof(femPIC_info, device_allocations));return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(native.femPIC_mesh), ctypes.sizeof(native.femPIC_species),
             ctypes.sizeof(native.femPIC_opts), ctypes.sizeof(native.femPIC_diag),
             ctypes.sizeof(native.femPIC_info), native.femPIC_opts.stream.offset,
-            native.femPIC_info.device_bytes.offset]
+            native.femPIC_info.device_bytes.offset, native.femPIC_info.device_allocations.offset]
     assert got == want
 
 
@@ -68,6 +69,17 @@ def test_extension_struct_layouts_match_c(native, tmp_path):
             ctypes.sizeof(native.femPIC_batch_tuning), native.femPIC_injector.v_sigma.offset,
             native.femPIC_batch_tuning.particle_ms.offset, native.femPIC_diag.divb_ref.offset]
     assert got == want
+
+
+def test_constants_match_header(native):
+    src = open(HEADER).read()
+    m = re.search(r"#define\s+FEMPIC_PROBE_MAX_POINTS\s+(\d+)", src)
+    assert m and int(m.group(1)) == native.FEMPIC_PROBE_MAX_POINTS
+    codes = dict(re.findall(r"#define\s+(FEMPIC_ERR_\w+)\s+\(?(-?\d+)\)?", src))
+    codes.update(re.findall(r"(FEMPIC_ERR_\w+)\s*=\s*(-?\d+)", src))
+    for name, val in codes.items():
+        if hasattr(native, name):
+            assert getattr(native, name) == int(val), name
 
 
 def test_default_opts(native):

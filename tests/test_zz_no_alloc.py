@@ -39,12 +39,19 @@ def test_noalloc_probe_matches_eval_fields(nat, order, precision):
     sim.set("B", workloads.random_dof_vector(t.n2, 1e-4, rng))
     # two calls in a row: different sizes and points; the second call reuses the
     # array that still holds the first call's data
+    allocs = lambda: nat.femPIC_get_info(sim.h).device_allocations
     for lo, hi in ((0, 1_000), (3_000, 17_777)):
         x, tet = cfg["x"][lo:hi], cfg["tet"][lo:hi]
+        a0 = allocs()
         E_ref, B_ref = nat.femPIC_eval_fields(sim.h, x, tet)
+        a1 = allocs()
         E, B = nat.femPIC_eval_fields_noalloc(sim.h, x, tet)
+        a2 = allocs()
         assert np.array_equal(E, E_ref) and np.array_equal(B, B_ref)
         assert np.abs(E).max() > 0 and np.abs(B).max() > 0
+        # the library's device-allocation count: the allocating probe raises it,
+        # this one leaves it where it was
+        assert a1 > a0 and a2 == a1
     sim.close()
 
 
