@@ -31,10 +31,10 @@ def _sources():
     return [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC))] + [os.path.join(INCLUDE, "fempic.h")]
 
 
-def _stale():
-    if not os.path.exists(LIB):
+def _stale(lib=LIB):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(s) > t for s in _sources())
 
 
@@ -47,30 +47,49 @@ def _run(cmd, verbose):
     return p.stdout + p.stderr
 
 
-def build(force=False, verbose=False, ptxas_info=False):
-    """Compile the library if any source is newer than it; returns its path."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+# Test variants of the library, built beside the default one:
+# * "checked": every index taken from a caller or a table is range-checked
+#   (FEMPIC_ERR_BOUNDS instead of an out-of-range access);
+# * "barrier_test": the grid barrier's spin limit lowered to 2e5 polls and one
+#   CTA of every persistent CG launch made absent from its barriers, so the
+#   others' bounded waits run out and the launch returns FEMPIC_ERR_BARRIER.
+VARIANTS = {
+    "checked": ["-DFEMPIC_CHECKS=1"],
+    "barrier_test": ["-DFEMPIC_BARRIER_SPIN_LIMIT=200000", "-DFEMPIC_TEST_ABSENT_CTA=1"],
+}
+
+
+def variant_path(variant):
+    return LIB if variant is None else os.path.join(HERE, f"libfempic_{variant}.so")
+
+
+def build(force=False, verbose=False, ptxas_info=False, variant=None):
+    """Compile the library (or one of its test variants) if any source is newer
+    than it; returns its path."""
+    lib_path = variant_path(variant)
+    if not force and not _stale(lib_path):
+        return lib_path
+    bdir = BUILD if variant is None else os.path.join(BUILD, variant)
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
-    host_o = os.path.join(BUILD, "setup.o")
-    dev_o = os.path.join(BUILD, "fempic.o")
+    host_o = os.path.join(bdir, "setup.o")
+    dev_o = os.path.join(bdir, "fempic.o")
     cmds = [
         ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I" + INCLUDE, "-c",
          os.path.join(CSRC, "setup.cpp"), "-o", host_o],
         [nvcc, "-O3", "-std=c++17", "-lineinfo", ARCH, "-Xcompiler", "-fPIC,-ffp-contract=off",
          "-I" + INCLUDE, "-c", os.path.join(CSRC, "fempic.cu"), "-o", dev_o]
-        + os.environ.get("FEMPIC_NVCC_FLAGS", "").split()
+        + (VARIANTS[variant] if variant else os.environ.get("FEMPIC_NVCC_FLAGS", "").split())
         + (["-Xptxas", "-v"] if ptxas_info else []),
     ]
     with ThreadPoolExecutor(2) as ex:
         outs = list(ex.map(lambda c: _run(c, verbose), cmds))
     if ptxas_info:
         print(outs[1])
-    tmp = LIB + ".tmp"
+    tmp = lib_path + ".tmp"
     _run([nvcc, "-shared", ARCH, "-o", tmp, host_o, dev_o, "-lpthread"], verbose)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -263,14 +263,23 @@ struct GridBarrier {
   unsigned int gen;
 };
 
-constexpr long long kBarrierSpinLimit = 20000000;  // ~1-2 s with the backoff below
+#ifndef FEMPIC_BARRIER_SPIN_LIMIT
+#define FEMPIC_BARRIER_SPIN_LIMIT 20000000  // ~1-2 s with the backoff below
+#endif
+constexpr long long kBarrierSpinLimit = FEMPIC_BARRIER_SPIN_LIMIT;
 
 __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) { return *(volatile const unsigned*)p; }
 
 // Returns false (and latches kStatusBarrier) if the barrier timed out.
+// Test builds with FEMPIC_TEST_ABSENT_CTA = b: CTA b never arrives (it leaves
+// the kernel at its first barrier), so every other CTA's wait runs into the
+// spin limit; nothing else changes.
 __device__ bool grid_sync(GridBarrier* bar, int32_t* status) {
   __shared__ int ok;
   __syncthreads();
+#ifdef FEMPIC_TEST_ABSENT_CTA
+  if (blockIdx.x == FEMPIC_TEST_ABSENT_CTA) return false;
+#endif
   if (threadIdx.x == 0) {
     ok = 1;
     unsigned gen = ld_volatile(&bar->gen);

@@ -63,16 +63,37 @@ def assert_close_to_scale(a, b, tol, what, floor=1e-3):
     assert_elementwise(a, b, scale, tol, what)
 
 
-def assert_rho(g_rho, o, precision, what="rho"):
-    """Charge per W0 DOF against the oracle.  Strict mode evaluates every W0
-    term with the oracle's formulas: 1e-12 of the sum of the terms' absolute
-    values.  A contracted kernel (fused multiply-adds) evaluates W0 at
-    barycentric coordinates that differ by a few ulps; the order-p Lagrange
-    function amplifies an absolute difference in lambda by its derivative
-    (at most ~2 p^2), so each term may differ by ~1e-14 |q w| whatever its own
-    size: 1e-12 of the terms plus 1e-14 |q w| per contributing particle."""
-    scale = o.rho_abs if precision == "fp64_strict" else o.rho_abs + 1e-2 * o.rho_cnt
-    assert_elementwise(g_rho, o.rho, scale, 1e-12, what)
+def assert_rho(g_rho, o, precision, what="rho", gx=None, gtet=None):
+    """Charge per W0 DOF against the oracle.  Strict mode: the same end points
+    and the same formulas, so 1e-12 of the sum of the terms' absolute values.
+    A contracted kernel (fused multiply-adds) ends its particles within its
+    position tolerance of the oracle's and evaluates W0 at barycentrics a few
+    ulps apart: its charge is compared with the oracle's measurement at the
+    device's own end points (gx, gtet), to 1e-12 of the terms plus 1e-14
+    |q w| per contributing particle (an order-p Lagrange function amplifies
+    an absolute difference in lambda by its derivative, at most ~2 p^2)."""
+    if precision == "fp64_strict" or gx is None:
+        scale = o.rho_abs if precision == "fp64_strict" else o.rho_abs + 1e-2 * o.rho_cnt
+        assert_elementwise(g_rho, o.rho, scale, 1e-12, what)
+        return
+    keep = (o.rho_abs, o.rho_cnt)
+    ref = o._measure_rho(np.asarray(gx, dtype=np.float64).reshape(-1, 3), np.asarray(gtet, dtype=np.int64))
+    scale = o.rho_abs + 1e-2 * o.rho_cnt
+    o.rho_abs, o.rho_cnt = keep
+    assert_elementwise(g_rho, ref, scale, 1e-12, what)
+
+
+def assert_particles_close(gx, gv, wx, wv, tol, extent, what=""):
+    """Per particle: |x_g - x_o| <= tol * extent (a position's rounding scales
+    with the chord and the domain, not with its own coordinates) and
+    |v_g - v_o| <= tol * |v_o| (the particle's speed)."""
+    dx = np.linalg.norm(np.asarray(gx) - wx, axis=1)
+    dv = np.linalg.norm(np.asarray(gv) - wv, axis=1)
+    sv = np.linalg.norm(wv, axis=1)
+    bx = np.nonzero(~(dx <= tol * extent))[0]
+    bv = np.nonzero(~(dv <= tol * sv))[0]
+    assert bx.size == 0, f"x{what}: {bx.size} particles off, first {bx[:4].tolist()} |dx| {dx[bx[:4]].tolist()}"
+    assert bv.size == 0, f"v{what}: {bv.size} particles off, first {bv[:4].tolist()} |dv|/|v| {(dv / sv)[bv[:4]].tolist()}"
 
 
 def assert_solves_system(A, e, rhs, rhs_terms, rtol, what="e"):

@@ -76,7 +76,7 @@ def test_ions_electrons_and_impedance_step(order, precision):
     dg = g.get("DG")
     if precision != "mixed":
         assert_elementwise(dg, w["dg"], w["dg_abs"], 1e-12 if precision == "fp64_strict" else 1e-11, "dg")
-        assert_rho(g.get("RHO"), o, precision)
+        assert_rho(g.get("RHO"), o, precision, "rho", g.get("X"), g.get("TET"))
     d = g.diag()
     assert d["continuity_abs"] <= 1e-12 * d["continuity_ref"]
     # the GPU's e^{n+1} solves the oracle's impedance system for the GPU's own current

@@ -106,7 +106,7 @@ def test_one_step_parity_order3(cfg, o3, precision):
         assert rel(xg, w["x"]) < 1e-12 and rel(vg, w["v"]) < 1e-12
     assert w["ncross"].mean() > 0.5
     assert_elementwise(g.get("DG"), w["dg"], w["dg_abs"], 1e-12 if precision == "fp64_strict" else 1e-11, "dg")
-    assert_rho(g.get("RHO"), o, precision)
+    assert_rho(g.get("RHO"), o, precision, "rho", g.get("X"), g.get("TET"))
     from oracle import fields as ofields
     A = ofields.system_matrix(o.M, o.K, dt, "trapezoid")
     eg = g.get("E")

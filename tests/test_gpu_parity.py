@@ -124,7 +124,7 @@ def test_one_step_parity(c1small, order, precision):
     # sign their rounding differs by up to ~1e-13 of the DOF's terms)
     tol_dg = 1e-12 if precision == "fp64_strict" else 1e-11
     assert_elementwise(g.get("DG"), w["dg"], w["dg_abs"], tol_dg, "dg")
-    assert_rho(g.get("RHO"), o, precision)
+    assert_rho(g.get("RHO"), o, precision, "rho", g.get("X"), g.get("TET"))
     # field solve: the GPU e^{n+1} satisfies the oracle's system
     from oracle import fields as ofields
     A = ofields.system_matrix(o.M, o.K, dt, "trapezoid")

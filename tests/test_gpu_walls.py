@@ -70,7 +70,7 @@ def test_beam_walls_match_oracle(order, precision):
             assert rel(xg, w["x"]) < 1e-12 and rel(vg, w["v"]) < 1e-12
         assert_elementwise(g.get("DG"), w["dg"], w["dg_abs"], 1e-12 if precision == "fp64_strict" else 1e-11,
                            "dg")
-        assert_rho(g.get("RHO"), o, precision)
+        assert_rho(g.get("RHO"), o, precision, "rho", g.get("X"), g.get("TET"))
         assert d["continuity_abs"] <= 1e-12 * d["continuity_ref"]
     assert total >= 20
     g.close()
