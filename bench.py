@@ -191,24 +191,85 @@ def oracle_particle_sample(cfg, n_sample, steps=1):
     return times
 
 
+def _oracle_worker(job):
+    """One worker of the multi-core oracle baseline: builds the drift-tube
+    workload from its seed, steps its slice of the particles with the oracle's
+    particle loop and returns the per-step times and its summed current."""
+    walls, lo, hi, steps = job
+    import workloads
+    from oracle import particles as opart, sim as osim
+    cfg = workloads.make_config(1, walls=walls)
+    s = osim.Sim(cfg["xyz"], cfg["tets"], cfg["order"], cfg["q"], cfg["m"], cfg["weight"],
+                 cfg["B0"], cfg["rho_ion"], matrices=False, bface_tag=cfg.get("bface_tag"))
+    s.set_particles(cfg["x"][lo:hi], cfg["v"][lo:hi], cfg["tet"][lo:hi])
+    if cfg.get("injectors"):
+        s.set_injection(cfg["injectors"], cfg["inject_seed"])
+    times, dg = [], None
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        w = s.push_walk(cfg["dt"])
+        opart.measure_rho(s.topo, s.g, s.c, w["x"], w["tet"], s.qw)
+        times.append(time.perf_counter() - t0)
+        s.x, s.v, s.tet = w["x"], w["v"], w["tet"]
+        dg = w["dg"]
+    return times, dg
+
+
+def oracle_particle_parallel(walls, n_sample, steps, workers=None):
+    """The oracle's particle loop split by particles over the host's cores
+    (spawned processes, each with its own copy of the mesh), the per-worker
+    currents summed at the end.  Returns (seconds per step, workers): a step
+    lasts as long as its slowest worker plus the reduction of the currents."""
+    import multiprocessing as mp
+    workers = workers or os.cpu_count() or 1
+    bounds = np.linspace(0, n_sample, workers + 1).astype(int)
+    jobs = [(walls, int(bounds[k]), int(bounds[k + 1]), steps) for k in range(workers)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    t0 = time.perf_counter()
+    total = res[0][1].copy()
+    for _, dg in res[1:]:
+        total += dg
+    t_red = time.perf_counter() - t0
+    per_step = [max(r[0][k] for r in res) + t_red / steps for k in range(steps)]
+    return per_step, workers
+
+
+ARM_PARTS = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1"}
+
+
+def host_cpu():
+    """The host CPU's model name (x86) or Arm core part."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":", 1)[0].strip().lower()
+            if key == "model name":
+                return line.split(":", 1)[1].strip()
+            if key == "cpu part":
+                part = line.split(":", 1)[1].strip()
+                return f"{ARM_PARTS.get(part, 'Arm core')} (CPU part {part})"
+    except OSError:
+        pass
+    return None
+
+
 def run_reference(args, rank, world):
     import workloads
     if rank != 0:
         return
-    cfg = workloads.make_config(1, walls=args.walls)
     n_sample = args.ref_sample
-    times = oracle_particle_sample(cfg, n_sample, steps=args.warmup + args.steps)
+    times, cores = oracle_particle_parallel(args.walls, n_sample, args.warmup + args.steps)
     timed = times[args.warmup:]
     total = sum(timed)
     value = n_sample * len(timed) / total
     sample = (f"oracle particle loop (gather, push, walk, deposit, charge) over the first "
-              f"{n_sample} of the 1e6 particles per step; the oracle's direct field solve "
-              "is not run at this size")
+              f"{n_sample} of the 1e6 particles per step, split by particles over {cores} host processes "
+              f"({host_cpu()}), currents summed; the oracle's direct field solve is not run at this size")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(timed),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": workload_name(2, 1_000_000, args.walls), "sample": sample},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -361,12 +422,17 @@ def run_native(args, rank, world, local_rank):
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            n_s = args.cpu_sample
-            ts = oracle_particle_sample(cfg, n_s, steps=1)
-            cpu = {"value": n_s / ts[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+            n_s = min(args.cpu_sample, npart)
+            ts, cores = oracle_particle_parallel(args.walls, n_s, 1)
+            t1 = oracle_particle_sample(cfg, args.cpu_sample_1core, steps=1)
+            cpu = {"value": n_s / ts[0], "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "cpu": host_cpu(),
                    "sample": f"one particle-loop step (gather, push, walk, deposit, charge) of the "
-                             f"first {n_s} of the {npart} particles on the same mesh and seed; the "
-                             "oracle's direct field solve is not timed at this size"}
+                             f"first {n_s} of the {npart} particles on the same mesh and seed, split by "
+                             f"particles over {cores} host processes, currents summed; the oracle's direct "
+                             "field solve is not timed at this size",
+                   "single_core": {"value": args.cpu_sample_1core / t1[0], "cores": 1,
+                                   "sample": f"the first {args.cpu_sample_1core} particles, one step"}}
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
@@ -394,23 +460,35 @@ def run_native(args, rank, world, local_rank):
             "alu_peaks_ops_per_s": alu,
             "clocks": clocks,
         }
-        print(json.dumps(result), flush=True)
     sim.close()
+    if result is not None and world == 1 and not args.no_extras:
+        # the other single-GPU workloads, each a compact sub-record of the same line
+        extras_t0 = time.perf_counter()
+        result["c3_precision"] = precision_record(args, local_rank, workloads.make_config(2), args.c3_steps, 3,
+                                                  args.c3_steps)
+        result["batched"] = batched_record(local_rank, args.batched_instances, args.batched_steps, 3)
+        result["batched"]["config"]["reduction"] = (
+            f"{args.batched_instances} instances x {args.batched_steps} steps of the 64 x 200 batched workload")
+        result["serving"] = serving_record(local_rank, args.serving_requests, args.serving_rate, 50, 16, 200.0)
+        result["serving"]["config"]["reduction"] = (
+            f"{args.serving_requests} of the 512 Poisson requests of the serving workload")
+        result["extras_wall_s"] = time.perf_counter() - extras_t0
+    if result is not None:
+        print(json.dumps(result), flush=True)
     return result
 
 
-def run_batched(args, local_rank):
+def batched_record(local_rank, n_instances, K, W):
     """Batched workload: uneven box instances advanced together (mixed
-    precision, one launch per kernel for all) against the plain per-instance
-    FP64 path (each instance stepped alone, one after the other)."""
+    precision, one launch per kernel for all, autotuned launch shapes,
+    replayed as one CUDA graph per step) against the plain per-instance FP64
+    path (each instance stepped alone, one after the other)."""
     import torch
     import workloads
     from paper_2111_12411_gb300 import Batch, Simulation
 
-    torch.cuda.set_device(local_rank)
-    cfgs = workloads.make_batch(n_instances=args.instances, steps=args.steps)
+    cfgs = workloads.make_batch(n_instances=n_instances, steps=K)
     total_np = sum(len(c["x"]) for c in cfgs)
-    K, W = args.steps, args.warmup
     out = {"metric": "aggregate particle-steps/s, batched mixed precision vs per-instance FP64",
            "unit": UNIT, "steps": K, "warmup": W, "data": "synthetic",
            "config": {"workload": f"{len(cfgs)} Kuhn-box instances, tets log-uniform 2e3-5e4, p in {{1,2}}, "
@@ -456,20 +534,23 @@ def run_batched(args, local_rank):
     batch.close()
     for sm in sims:
         sm.close()
-    print(json.dumps(out), flush=True)
+    return out
 
 
-def run_serving(args, local_rank):
+def run_batched(args, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    print(json.dumps(batched_record(local_rank, args.instances, args.steps, args.warmup)), flush=True)
+
+
+def serving_record(local_rank, n_requests, rate, chunk_steps, max_slots, hbm_budget_gb):
     """Serving workload: a Poisson stream of box simulations admitted by HBM
     budget and advanced in chunks with continuous batching."""
-    import torch
     import workloads
     from paper_2111_12411_gb300.serve import Request, Server
 
-    torch.cuda.set_device(local_rank)
-    reqs = workloads.make_requests(n_requests=args.requests, rate_hz=args.rate,
-                                   chunk_steps=args.chunk_steps, chunks=(1, 2))
-    server = Server(args.hbm_budget_gb * (1 << 30), max_slots=args.instances, device=local_rank,
+    reqs = workloads.make_requests(n_requests=n_requests, rate_hz=rate, chunk_steps=chunk_steps, chunks=(1, 2))
+    server = Server(hbm_budget_gb * (1 << 30), max_slots=max_slots, device=local_rank,
                     precision="mixed", result_keys=("E",))
     t_build = time.perf_counter()
     for r in reqs:
@@ -478,33 +559,59 @@ def run_serving(args, local_rank):
     t_build = time.perf_counter() - t_build
     server.run()
     rep = server.report()
-    out = {"metric": "serving: p50/p99 chunk latency and aggregate particle-steps/s", "unit": UNIT,
-           "value": rep["particle_steps_per_s_busy"], "data": "synthetic",
-           "config": {"workload": f"{len(reqs)} Poisson requests at {args.rate} Hz, Kuhn boxes 2e3-5e4 "
-                                  "tets, p in {1,2}, particles 1e4-4e6, mixed precision",
-                      "chunk_steps": args.chunk_steps, "hbm_budget_gb": args.hbm_budget_gb,
-                      "max_slots": args.instances, "host_input_generation_s": t_build},
-           "serving": rep}
-    print(json.dumps(out), flush=True)
+    return {"metric": "serving: p50/p99 chunk latency and aggregate particle-steps/s", "unit": UNIT,
+            "value": rep["particle_steps_per_s_busy"], "data": "synthetic",
+            "config": {"workload": f"{len(reqs)} Poisson requests at {rate} Hz, Kuhn boxes 2e3-5e4 "
+                                   "tets, p in {1,2}, particles 1e4-4e6, mixed precision",
+                       "chunk_steps": chunk_steps, "hbm_budget_gb": hbm_budget_gb,
+                       "max_slots": max_slots, "host_input_generation_s": t_build},
+            "serving": rep}
 
 
-def run_precision(args, local_rank):
-    """Mixed precision against FP64 on the same GPU: the jittered Kuhn box of
-    37^3 hexes (303,918 tets) at p = 2 with 10^7 electrons in two
-    counter-streaming beams (+-2e7 m/s along z, v_th = 1e6 m/s), both forms
-    stepped from the same state.  Reports each form's throughput, the
-    relative errors of E, B, x and v of the mixed form against the FP64 form
-    after every step, and both forms' Gauss and continuity residuals."""
+def run_serving(args, local_rank):
     import torch
-    import workloads
+    torch.cuda.set_device(local_rank)
+    print(json.dumps(serving_record(local_rank, args.requests, args.rate, args.chunk_steps, args.instances,
+                                    args.hbm_budget_gb)), flush=True)
+
+
+def _rooflines(info, acc, crossings, npart, occupied, K, peak, peak_src):
+    """HBM rooflines of the CG solve and the particle kernel from K steps of
+    library timings (acc: summed last_timing fields) and crossings."""
+    iters = acc["cg_iterations"] / K
+    pcg_bytes = pcg_bytes_per_iteration(info) * (iters + 1.0)
+    pcg_ms = acc["pcg_ms"] / K
+    pcg_gbs = pcg_bytes / (pcg_ms * 1e-3) / 1e9
+    cross_pp = crossings / (K * max(1, npart))
+    pbytes = particle_bytes_per_step(info.order, npart, occupied, cross_pp) * npart
+    push_ms = acc["push_ms"] / K
+    push_gbs = pbytes / (push_ms * 1e-3) / 1e9
+    src = peak_src + " of measured" if "measured" in peak_src else peak_src
+    cg = {"kernel": "k_pcg (device PCG, one cooperative launch per step)", "bound": "hbm",
+          "achieved": pcg_gbs, "peak": peak, "unit": "GB/s", "frac": pcg_gbs / peak, "traffic": None,
+          "peak_source": src, "bytes_per_launch": pcg_bytes, "cg_iterations_per_launch": iters,
+          "ms_per_launch": pcg_ms}
+    part = {"kernel": "k_particle (gather, push, walk, deposit, charge)", "bound": "hbm",
+            "achieved": push_gbs, "peak": peak, "unit": "GB/s", "frac": push_gbs / peak, "traffic": None,
+            "peak_source": src, "bytes_per_launch": pbytes, "ms_per_launch": push_ms,
+            "crossings_per_particle": cross_pp, "particles_per_occupied_tet": npart / max(1, occupied)}
+    return cg, part
+
+
+def precision_record(args, local_rank, cfg, K, W, err_steps):
+    """Mixed precision against FP64 on the same GPU, both forms stepped from the
+    same state: each form's throughput (whole step and particle loop, with
+    both rooflines), then the relative errors of E, B, x and v of the mixed
+    form against the FP64 form after each of err_steps steps, and both forms'
+    Gauss and continuity residuals."""
+    import torch
     from paper_2111_12411_gb300 import Simulation
 
-    torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
-    cfg = workloads.make_config(2, n_particles=args.particles)
-    K, W = args.steps, args.warmup
     npart = len(cfg["x"])
+    occupied = len(np.unique(cfg["tet"]))
+    peak, peak_src = measured_peaks()
 
     def rel(a, b):
         nb = float(np.linalg.norm(b))
@@ -513,15 +620,17 @@ def run_precision(args, local_rank):
     sims = {p: Simulation.from_config(cfg, precision=p, device=local_rank, stream=stream.cuda_stream,
                                       cg_rtol=args.cg_rtol, diagnostics=True) for p in ("fp64", "mixed")}
     info = sims["fp64"].info
-    # W warm-up steps of each form alone (throughput only), then restart both from the initial state
     state0 = {k: sims["fp64"].get(k) for k in ("X", "V", "TET", "E", "E_PREV", "B", "DG", "DG_PREV", "RHO")}
     out_forms = {}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for p, sm in sims.items():
         sm.step(cfg["dt"], W)
         torch.cuda.synchronize(dev)
         t_ms = []
-        part_ms = 0.0
+        acc = {k: 0.0 for k in ("particle_ms", "field_ms", "push_ms", "pcg_ms", "cg_iterations", "launches")}
+        cross = 0.0
         for _ in range(K):
+            flush.zero_()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -529,15 +638,25 @@ def run_precision(args, local_rank):
             b.record(stream)
             b.synchronize()
             t_ms.append(a.elapsed_time(b))
-            part_ms += sm.last_timing()["particle_ms"]
+            t = sm.last_timing()
+            for k in acc:
+                acc[k] += t[k]
+            cross += sm.diag()["crossings"]
         d = sm.diag()
+        roof_cg, roof_part = _rooflines(info, acc, cross, npart, occupied, K, peak, peak_src)
         out_forms[p] = {"value": npart * K / (1e-3 * sum(t_ms)), "ms_per_step": sum(t_ms) / K,
-                        "particle_loop": npart * K / (1e-3 * part_ms),
+                        "particle_loop": {"value": npart * K / (1e-3 * acc["particle_ms"]),
+                                          "ms_per_step": acc["particle_ms"] / K,
+                                          "note": "sort + gather/push/walk/deposit/charge"},
+                        "field_update": {"ms_per_step": acc["field_ms"] / K, "pcg_ms": acc["pcg_ms"] / K,
+                                         "cg_iterations_per_step": acc["cg_iterations"] / K},
+                        "roofline_particle_kernel": roof_part, "roofline_cg_kernel": roof_cg,
+                        "gpu_launches": int(acc["launches"]),
                         "cg_iterations_last_step": d["cg_iterations"]}
         for k, v in state0.items():
             sm.set(k, v)
     errs = []
-    for step in range(1, K + 1):
+    for step in range(1, err_steps + 1):
         for sm in sims.values():
             sm.step(cfg["dt"])
         f, m = sims["fp64"], sims["mixed"]
@@ -553,11 +672,12 @@ def run_precision(args, local_rank):
         errs.append(row)
     out = {"metric": "mixed precision vs FP64 on one GPU: particle-steps/s and per-field relative error",
            "unit": UNIT, "value": out_forms["mixed"]["value"], "steps": K, "warmup": W, "data": "synthetic",
-           "config": {"workload": "jittered Kuhn box 37^3 (303918 tets), p=2, 1e7 electrons in two "
-                                  "counter-streaming beams +-2e7 m/s, v_th=1e6 m/s, B0=0",
+           "config": {"workload": "jittered Kuhn box 37^3 (303918 tets), p=2, "
+                                  f"{npart:.0e} electrons in two counter-streaming beams +-2e7 m/s, "
+                                  "v_th=1e6 m/s, B0=0".replace("e+0", "e"),
                       "n_particles": npart, "n_tets": info.n_tets, "n1": info.n1, "n2": info.n2,
                       "cg_rtol": args.cg_rtol, "dt": cfg["dt"],
-                      "l2": "inputs larger than L2 (particle state alone 0.56 GB)"},
+                      "l2": "flushed between timed steps (256 MiB write); particle state alone 0.56 GB"},
            "fp64": out_forms["fp64"], "mixed": out_forms["mixed"],
            "speedup_mixed_vs_fp64": out_forms["mixed"]["value"] / out_forms["fp64"]["value"],
            "errors_mixed_vs_fp64": errs,
@@ -565,7 +685,18 @@ def run_precision(args, local_rank):
                    "initial state; the FP64 form itself matches the oracle to 1e-12 (parity tests)"}
     for sm in sims.values():
         sm.close()
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def run_precision(args, local_rank):
+    """Mixed precision against FP64 on the jittered 37^3 Kuhn box (303,918
+    tets, p = 2, 10^7 electrons in two counter-streaming beams +-2e7 m/s
+    along z, v_th = 1e6 m/s); see precision_record."""
+    import torch
+    import workloads
+    torch.cuda.set_device(local_rank)
+    cfg = workloads.make_config(2, n_particles=args.particles)
+    print(json.dumps(precision_record(args, local_rank, cfg, args.steps, args.warmup, args.steps)), flush=True)
 
 
 def run_push(args, local_rank):
@@ -793,10 +924,18 @@ def main():
                     help="particle push: Boris on the straight chord, or the paper's Adams-Bashforth 4 "
                          "on the quartic path")
     ap.add_argument("--cg-rtol", type=float, default=1e-12)
-    ap.add_argument("--cpu-sample", type=int, default=250_000)
-    ap.add_argument("--ref-sample", type=int, default=50_000)
+    ap.add_argument("--cpu-sample", type=int, default=1_000_000)
+    ap.add_argument("--cpu-sample-1core", type=int, default=100_000)
+    ap.add_argument("--ref-sample", type=int, default=400_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the sub-records of the default run (37^3 box mixed vs FP64, batched, serving)")
+    ap.add_argument("--c3-steps", type=int, default=3)
+    ap.add_argument("--batched-instances", type=int, default=32)
+    ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--serving-requests", type=int, default=128)
+    ap.add_argument("--serving-rate", type=float, default=8.0)
     ap.add_argument("--workload", choices=("tube", "batched", "serving", "precision", "push", "project",
                                            "schemes", "species"),
                     default="tube")
