@@ -54,21 +54,33 @@ def measured_peaks():
 def pcg_bytes_per_iteration(info):
     """Bytes one preconditioned CG iteration must move: the A arrays (8 B per
     value; at order 2 in 2x2 blocks with one 4 B column per block, else 4 B per
-    entry), the FP32 D, D^T, Pi and Pi^T arrays of the preconditioner (4 B
-    value + 4 B column), 4 B row pointers, the vector passes (SpMV: p gather +
-    q write; update: x, p, q, r read, x, r write; auxiliary corrections: r,
-    t, u, dinv, dinv_L, dinv_V reads, t, u, z writes; direction update: p, z
-    read, p write), and for each of the cheb_k - 1 Chebyshev steps of the
-    auxiliary problems the FP32 L and V arrays plus five FP32 vector passes
-    (right side, step and iterate read; step and iterate written)."""
+    entry; 4 B per value when the direction products are FP32, plus one FP64
+    residual product every cg_replace_period iterations), the FP32 D, D^T, Pi
+    and Pi^T arrays of the preconditioner (4 B value + 4 B column), 4 B row
+    pointers, the vector passes (SpMV: p gather + q write; update: x, p, q, r
+    read, x, r write; auxiliary corrections: r, t, u, dinv, dinv_L, dinv_V
+    reads, t, u, z writes; direction update: p, z read, p write), and for each
+    of the cheb_k - 1 Chebyshev steps of the auxiliary problems the FP32 L and
+    V arrays plus five FP32 vector passes (right side, step and iterate read;
+    step and iterate written)."""
     n1, n0 = info.n1, info.n0
     nv = 3 * info.n_nodes
-    a_bytes = (8 * info.nnz_A + info.nnz_A) if info.order == 2 else 12 * info.nnz_A
-    mats = a_bytes + 8 * (info.nnz_D + info.nnz_DT + 2 * info.nnz_Pi) + 4 * (3 * n1 + n0 + nv)
-    vec = 8 * (2 * n1 + 6 * n1 + (2 * n1 + 2 * n0 + n1 + n0) + (2 * nv + nv) + n1 + 3 * n1)
+    a64 = (8 * info.nnz_A + info.nnz_A) if info.order == 2 else 12 * info.nnz_A
+    mats = 8 * (info.nnz_D + info.nnz_DT + 2 * info.nnz_Pi) + 4 * (3 * n1 + n0 + nv)
+    aux = 8 * ((2 * n1 + 2 * n0 + n1 + n0) + (2 * nv + nv))
     k = max(1, int(info.aux_cheb_degree))
     cheb = (k - 1) * (8 * (info.nnz_L + info.nnz_V) + 4 * (n0 + nv) + 20 * (n0 + nv))
-    return mats + vec + cheb
+    if getattr(info, "cg_fp32_products", 0):
+        # FP32 A (4 B value + a 4 B column per 2x2 block) gathering the FP32 p
+        # and writing the FP32 q; update x, r from x, p, r (8 B) and q (4 B);
+        # direction update reads p, z, writes p and its FP32 copy; plus, every
+        # cg_replace_period iterations, one FP64 product rhs - A x
+        a32 = 4 * info.nnz_A + info.nnz_A
+        vec = 4 * n1 + 4 * n1 + (8 * 3 + 4 + 16) * n1 + (16 + 8 + 4) * n1
+        repl = (a64 + (8 + 8 + 8 + 4) * n1) / max(1, int(info.cg_replace_period))
+        return a32 + mats + vec + aux + cheb + repl
+    vec = 8 * (2 * n1 + 6 * n1 + n1 + 3 * n1)
+    return a64 + mats + vec + aux + cheb
 
 
 def particle_bytes_per_step(order, n_particles, occupied_tets, crossings_per_particle):
@@ -341,7 +353,9 @@ def run_native(args, rank, world, local_rank):
         try:
             per_it = json.load(open(prof)).get("k_pcg_bytes_per_iteration")
             # counters taken on an earlier build of k_pcg are not carried over
-            if json.load(open(prof)).get("aux_cheb_degree", 1) != info.aux_cheb_degree:
+            tj = json.load(open(prof))
+            if (tj.get("aux_cheb_degree", 1) != info.aux_cheb_degree
+                    or tj.get("cg_fp32_products", 0) != getattr(info, "cg_fp32_products", 0)):
                 per_it = None
             traffic = per_it * (iters + 1.0) if per_it else None
         except (OSError, ValueError):
@@ -912,6 +926,58 @@ def run_species(args, local_rank):
     print(json.dumps(out), flush=True)
 
 
+def run_oracle_baseline(args):
+    """The oracle timed on the host cores, for the CPU baseline table: the
+    6^3 box (C1: 1296 tets, p = 1, 10^4 electrons) for all its steps with the
+    field solve (single core, numpy/scipy as they stand), and the particle
+    loops of the drift tube (10^6 electrons, p = 2) and of the 37^3 box (a
+    10^6-particle sample of its 10^7, extrapolated per particle) on one core
+    and split over every core.  No GPU is used."""
+    import workloads
+    from oracle import sim as osim
+    out = {"metric": "oracle on the host cores (CPU baseline)", "unit": UNIT, "cpu": host_cpu(),
+           "cores": os.cpu_count(), "data": "synthetic"}
+    cfg = workloads.make_config(0)
+    t0 = time.perf_counter()
+    s = osim.Sim(cfg["xyz"], cfg["tets"], cfg["order"], cfg["q"], cfg["m"], cfg["weight"], cfg["B0"],
+                 cfg["rho_ion"])
+    s.set_particles(cfg["x"], cfg["v"], cfg["tet"])
+    s.electrostatic_init()
+    t_setup = time.perf_counter() - t0
+    steps = cfg["steps"] if args.oracle_c1_steps is None else args.oracle_c1_steps
+    t_part = t_field = 0.0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        w = s.push_walk(cfg["dt"])
+        t1 = time.perf_counter()
+        from oracle import fields
+        A = fields.system_matrix(s.M, s.K, cfg["dt"], s.scheme, s.gamma, s.beta, s.I)
+        r = fields.rhs_trapezoid(s.M, s.K, s.CtM2, s.e, s.b, w["dg"], cfg["dt"], s.I)
+        e_new = fields.solve(A, r, s.topo.free1)
+        s.b = fields.update_b(s.C, s.b, e_new, s.e, cfg["dt"])
+        s.e_prev, s.e = s.e, e_new
+        s.x, s.v, s.tet = w["x"], w["v"], w["tet"]
+        s.rho = s._measure_rho(s.x, s.tet)
+        t_field += time.perf_counter() - t1
+        t_part += t1 - t0
+    n = len(cfg["x"])
+    out["c1"] = {"workload": "6^3 Kuhn box, 1296 tets, p=1, 1e4 electrons", "steps": steps, "cores": 1,
+                 "setup_s": t_setup, "particle_loop": n * steps / t_part, "field_solve_s_per_step": t_field / steps,
+                 "whole_step": n * steps / (t_part + t_field)}
+    for name, idx, n_s in (("c2", 1, 1_000_000), ("c3", 2, 1_000_000)):
+        c = workloads.make_config(idx, n_particles=n_s) if idx == 2 else workloads.make_config(idx)
+        t1 = oracle_particle_sample(c, min(100_000, n_s), steps=1)[0]
+        if idx == 1:
+            tp, cores = oracle_particle_parallel("beam", n_s, 1)
+        else:
+            tp, cores = None, os.cpu_count()
+        out[name] = {"workload": c["name"], "particle_loop_1core": min(100_000, n_s) / t1,
+                     "particle_loop_all_cores": (n_s / tp[0]) if tp else None, "cores": cores,
+                     "sample": f"one step of the first {min(100_000, n_s)} particles (1 core)"
+                               + (f"; all {n_s} particles over {cores} processes" if tp else "")}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -932,12 +998,13 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sub-records of the default run (37^3 box mixed vs FP64, batched, serving)")
     ap.add_argument("--c3-steps", type=int, default=3)
+    ap.add_argument("--oracle-c1-steps", type=int, default=None)
     ap.add_argument("--batched-instances", type=int, default=32)
     ap.add_argument("--batched-steps", type=int, default=20)
     ap.add_argument("--serving-requests", type=int, default=128)
     ap.add_argument("--serving-rate", type=float, default=8.0)
     ap.add_argument("--workload", choices=("tube", "batched", "serving", "precision", "push", "project",
-                                           "schemes", "species"),
+                                           "schemes", "species", "oracle"),
                     default="tube")
     ap.add_argument("--order", type=int, default=2, choices=(1, 2, 3),
                     help="basis order p of the tube and project workloads")
@@ -957,6 +1024,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "oracle":
+        run_oracle_baseline(args)
         return
     if world > 1:
         import torch

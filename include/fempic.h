@@ -245,6 +245,11 @@ typedef struct {
   int64_t device_allocations; /* device allocations (cudaMalloc) this library has
                                made in the process so far, all handles and
                                batches together (not a per-handle figure)     */
+  int32_t cg_fp32_products; /* 1: the field solve's direction products run in
+                               FP32, the residual recomputed in FP64 every
+                               cg_replace_period iterations and before a solve
+                               is accepted (order 2); 0: FP64 products        */
+  int32_t cg_replace_period;
 } femPIC_info;
 
 /* Fill *opts with defaults: FP64, trapezoid, cg_rtol 1e-12, cg_max_it 2000,

@@ -88,6 +88,10 @@ struct FemPIC {
   int64_t nnzb = 0;
   int32_t *brp = nullptr, *bci = nullptr;
   double *bM = nullptr, *bK = nullptr, *bA = nullptr, *binv = nullptr;
+  float* bA32 = nullptr;   // FP32 copy of bA: the CG's direction products (FEMPIC_PCG_FP32A)
+  double kdiag_med = 0.0;  // median over W1 rows of K_ii / (4 M_ii): dt^2 times it is the
+                           // typical ratio of the curl-curl to the mass term of A
+  bool pcg_fp32 = false;   // this dt's solves use the FP32 direction products
   double *dvM = nullptr, *dvK = nullptr;
   // FP32 copies for the preconditioner's auxiliary-space corrections
   float *D32 = nullptr, *DT32 = nullptr, *Pi32 = nullptr, *PiT32 = nullptr;
@@ -113,6 +117,7 @@ struct FemPIC {
   double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *partials = nullptr;
   double *cg_r2 = nullptr, *cg_p2 = nullptr, *cg_red = nullptr;
   float *cg_q32 = nullptr, *cg_r32 = nullptr;
+  float* cg_p32 = nullptr;  // FP32 copy of the search direction (FEMPIC_PCG_FP32A)
   GridBarrier* bar = nullptr;
   int pcg_blocks_w1 = 0, pcg_blocks_w0 = 0;
   int32_t* apart = nullptr;  // [pcg_blocks_w1 + 1] per-CTA row ranges of A in the CG
@@ -418,6 +423,10 @@ int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, 
   memcpy(a.chebV, h->chebV, sizeof(a.chebV));
   a.Bg = (nodal && h->Bg.nnz > 0) ? h->Bg.view() : CsrView{0, nullptr, nullptr, nullptr};
   a.Ab = (nodal && h->nb > 0) ? BsrView{h->nb, h->brp, h->bci, h->bA} : BsrView{0, nullptr, nullptr, nullptr};
+  a.Ab32 = (nodal && h->nb > 0 && h->pcg_fp32) ? BsrView32{h->nb, h->brp, h->bci, h->bA32}
+                                               : BsrView32{0, nullptr, nullptr, nullptr};
+  a.p32 = h->cg_p32;
+  a.repl = kPcgReplacePeriod;
   a.q32 = h->cg_q32;
   a.r32 = h->cg_r32;
   a.red = h->cg_red;
@@ -494,6 +503,15 @@ int form_system(FemPIC* h, double dt) {
     k_form_blocks<<<grid_for(h->nb, 256, 1 << 30), 256, 0, h->stream>>>(h->nb, h->brp, h->bci, h->bM, h->bK, c1,
                                                                         h->bA, h->binv, h->bI, ci_imp);
     h->launches++;
+    // FP32 direction products only while the curl-curl term stays within
+    // kPcgFp32MaxRatio of the mass term (median over the rows): beyond it the
+    // cancellation in A x of gradient fields outgrows what FP32 products and
+    // the FP64 residual replacement can follow
+    h->pcg_fp32 = h->bA32 && h->kdiag_med * dt * dt <= kPcgFp32MaxRatio;
+    if (h->pcg_fp32) {
+      k_to_f32<<<grid_for(4 * h->nnzb, 256, 4096), 256, 0, h->stream>>>(4 * h->nnzb, h->bA, h->bA32);
+      h->launches++;
+    }
   }
   if (h->Bg.nnz > 0) {
     k_group_inverse<<<grid_for(h->n_groups, 128, 1 << 30), 128, 0, h->stream>>>(
@@ -1307,6 +1325,23 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
   }
   UP(h->load0, hm.load0);
 #undef UP
+  {  // typical curl-curl to mass ratio per unit dt^2 (decides the FP32 direction products)
+    std::vector<double> ratio;
+    ratio.reserve(hm.M.n_rows);
+    for (int32_t i = 0; i < hm.M.n_rows; ++i) {
+      double m = 0.0, k = 0.0;
+      for (int32_t j = hm.M.rowptr[i]; j < hm.M.rowptr[i + 1]; ++j)
+        if (hm.M.col[j] == i) {
+          m = hm.M.val[j];
+          k = hm.K.val[j];
+        }
+      if (m > 0.0) ratio.push_back(0.25 * k / m);
+    }
+    if (!ratio.empty()) {
+      std::nth_element(ratio.begin(), ratio.begin() + ratio.size() / 2, ratio.end());
+      h->kdiag_med = ratio[ratio.size() / 2];
+    }
+  }
   if ((rc = upload_csr(h, &h->M, hm.M)) || (rc = upload_csr(h, &h->K, hm.K)) || (rc = upload_csr(h, &h->Q, hm.Q)) ||
       (rc = upload_csr(h, &h->C, hm.C)) || (rc = upload_csr(h, &h->M2, hm.M2)) || (rc = upload_csr(h, &h->D, hm.D)) ||
       (rc = upload_csr(h, &h->DT, hm.DT)) || (rc = upload_csr(h, &h->L, hm.L)) ||
@@ -1378,7 +1413,8 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
       h->nb = nb;
       h->nnzb = (int64_t)bci.size();
       if ((rc = upload(h, &h->brp, brp)) || (rc = upload(h, &h->bci, bci)) || (rc = upload(h, &h->bM, bM)) ||
-          (rc = upload(h, &h->bK, bK)) || (rc = dalloc(h, &h->bA, bM.size())) || (rc = dalloc(h, &h->binv, 4 * (size_t)nb)))
+          (rc = upload(h, &h->bK, bK)) || (rc = dalloc(h, &h->bA, bM.size())) || (rc = dalloc(h, &h->binv, 4 * (size_t)nb)) ||
+          (FEMPIC_PCG_FP32A && (rc = dalloc(h, &h->bA32, bM.size()))))
         return rc;
       if (imp && (rc = upload(h, &h->bI, bI))) return rc;
     }
@@ -1468,7 +1504,7 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
     if ((rc = upload(h, &h->apart, part))) return rc;
   }
   if ((rc = dalloc(h, &h->cg_q32, nmax)) || (rc = dalloc(h, &h->cg_r32, 2 * (size_t)nmax)) ||
-      (rc = dalloc(h, &h->cg_red, 12)))
+      (rc = dalloc(h, &h->cg_p32, nmax)) || (rc = dalloc(h, &h->cg_red, 12)))
     return rc;
   if ((rc = dalloc(h, &h->partials, 8 * (size_t)h->pcg_blocks_w1)) || (rc = dalloc(h, &h->bar, 1)) ||
       (rc = dalloc(h, &h->d_status, 1)) || (rc = dalloc(h, &h->d_cg_iters, 1)) || (rc = dalloc(h, &h->d_cg_res, 1)) ||
@@ -1920,6 +1956,8 @@ int femPIC_get_info(const FemPIC* h, femPIC_info* info) {
   info->nl2 = h->nl2;
   info->n_particles = h->np;
   info->device_allocations = g_device_allocations.load(std::memory_order_relaxed);
+  info->cg_fp32_products = h->pcg_fp32 ? 1 : 0;
+  info->cg_replace_period = kPcgReplacePeriod;
   info->nnz_A = h->M.nnz;
   info->nnz_C = h->C.nnz;
   info->nnz_Q = h->Q.nnz;

@@ -28,6 +28,14 @@ struct BsrView {
   const double* v;
 };
 
+// 2x2-block CSR with FP32 values (the CG's direction products)
+struct BsrView32 {
+  int32_t nb;
+  const int32_t* rp;
+  const int32_t* ci;
+  const float* v;
+};
+
 // FP32 values: used for the preconditioner's auxiliary-space operators
 struct CsrView32 {
   int32_t n_rows;
@@ -341,6 +349,13 @@ struct PcgArgs {
   // diagonal blocks (block Jacobi); Ab.nb == 0 uses A and dinv
   BsrView Ab;
   const double* binv;
+  // FP32 direction products (order 2): q = A p with A and p rounded to FP32
+  // and summed in FP32; every `repl` iterations, and before convergence is
+  // accepted, the residual is recomputed in FP64 as rhs - A x.  Ab32.nb == 0
+  // keeps the FP64 products.
+  BsrView32 Ab32;
+  float* p32;
+  int repl;
   // order 3: inverses of A's diagonal blocks over the W1 DOFs of one edge, one
   // face and one tet interior, as a CSR (rows of a group hold its columns);
   // n_rows == 0 keeps the point Jacobi dinv
@@ -512,6 +527,41 @@ __device__ __forceinline__ void bspmv_row(const BsrView& A, const double* x, int
       s1 = fma(a23.x, xv.x, fma(a23.y, xv.y, s1));
     }
 #endif
+  }
+#pragma unroll
+  for (int o = LPR / 2; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o, LPR);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o, LPR);
+  }
+  if (act && lane == 0) emit(k0, s0, s1);
+}
+
+// block row k0 of the FP32 2x2-block matrix times an FP32 vector, summed in
+// FP32 (two blocks per lane and pass, as bspmv_row)
+template <int LPR, class F>
+__device__ __forceinline__ void bspmv32_row(const BsrView32& A, const float* x, int k0, bool act, int lane, F emit) {
+  const float2* x2 = reinterpret_cast<const float2*>(x);
+  const float4* v4 = reinterpret_cast<const float4*>(A.v);
+  float s0 = 0.f, s1 = 0.f;
+  if (act) {
+    const int beg = __ldg(A.rp + k0), end = __ldg(A.rp + k0 + 1);
+    int j = beg + lane;
+    for (; j + LPR < end; j += 2 * LPR) {
+      const int c0 = __ldg(A.ci + j), c1 = __ldg(A.ci + j + LPR);
+      const float2 x0 = __ldcg(x2 + c0), x1 = __ldcg(x2 + c1);
+      const float4 a = __ldg(v4 + j), b = __ldg(v4 + j + LPR);
+      s0 = fmaf(a.x, x0.x, fmaf(a.y, x0.y, s0));
+      s1 = fmaf(a.z, x0.x, fmaf(a.w, x0.y, s1));
+      s0 = fmaf(b.x, x1.x, fmaf(b.y, x1.y, s0));
+      s1 = fmaf(b.z, x1.x, fmaf(b.w, x1.y, s1));
+    }
+    if (j < end) {
+      const int c = __ldg(A.ci + j);
+      const float2 xv = __ldcg(x2 + c);
+      const float4 a = __ldg(v4 + j);
+      s0 = fmaf(a.x, xv.x, fmaf(a.y, xv.y, s0));
+      s1 = fmaf(a.z, xv.x, fmaf(a.w, xv.y, s1));
+    }
   }
 #pragma unroll
   for (int o = LPR / 2; o > 0; o >>= 1) {
@@ -807,7 +857,8 @@ __device__ unsigned long long g_pcg_stamp[4096][4];
 #endif
 
 // Preconditioned CG; with the auxiliary-space preconditioner, 3 + cheb_k grid
-// barriers per iteration (three without it):
+// barriers per iteration (three without it; two more on the iterations that
+// replace the residual when the direction products are FP32):
 //   phase 0: p_k = z + beta p_{k-1}; barrier
 //   phase 1: q = A p_k; barrier; alpha = rz / (p.q)
 //   phase 2: x += alpha p, r' = r - alpha q; right-hand sides D^T r' and
@@ -816,6 +867,24 @@ __device__ unsigned long long g_pcg_stamp[4096][4];
 //            after a barrier; barrier
 //   phase 3: z = B r' + D t + Pi u (B: block or point Jacobi); barrier;
 //            rz', r'.r' -> convergence, beta
+// Direction products in FP32 (FEMPIC_PCG_FP32A, order 2): the product q = A p
+// is the heaviest phase and, in FP64, bound by the FP64 pipe (one DFMA per
+// stored value at GB300's FP64 rate); in FP32 it reads half the bytes and runs
+// on the FP32 pipe.  Its rounding (~1e-7 of |A||p|) enters the recursive
+// residual, so every kPcgReplacePeriod iterations the residual is replaced by
+// rhs - A x computed in FP64 (two more barriers and one FP64 product), and a
+// solve ends only on a replaced residual below the tolerance: the stopping
+// test is on the true residual, as with FP64 products.
+#ifndef FEMPIC_PCG_FP32A
+#define FEMPIC_PCG_FP32A 1
+#endif
+constexpr int kPcgReplacePeriod = 16;
+// largest median ratio of the curl-curl to the mass diagonal, (dt^2/4) K_ii /
+// M_ii, at which the FP32 products are used (drift tube at 33.3 ps: 880;
+// 37^3 box at its dt: 600; the 6^3-20^3 boxes at theirs: 2.4e5, where they
+// fail to converge)
+constexpr double kPcgFp32MaxRatio = 1.0e4;
+
 // Launch shape of the persistent CG kernel: with dynamic row scheduling one
 // CTA of 1024 threads (the most a CTA can have) per SM; with the static
 // stride, 6 co-resident 256-thread CTAs per SM measured fastest (5 and 8 were
@@ -896,14 +965,25 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
   bool conv = rnorm <= thresh || bnorm == 0.0;
   double beta = 0.0;
   int pb = 0;  // p_{k-1} lives in p[pb], p_k is written to p[pb ^ 1]
+  bool f32a = a.Ab32.nb > 0;
+  bool verify = false;  // FP32 products: the recursive residual reached the tolerance
+  double last_true = rnorm;  // FP32 products: the last FP64 (true) residual norm
   while (!conv && it < a.max_it) {
     const double* p_old = a.p[pb];
     double* p_new = a.p[pb ^ 1];
     const bool first = it == 0;
     // phase 0: p_k = z + beta p_{k-1} (elementwise), then q = A p_k
     PCG_MARK(0);
-    if (!first) {
-      for (int i = gid; i < n; i += tpg) p_new[i] = fma(beta, __ldcg(p_old + i), __ldcg(a.z + i));
+    if (!first || f32a) {
+      if (f32a) {
+        for (int i = gid; i < n; i += tpg) {
+          const double pv = first ? __ldcg(a.z + i) : fma(beta, __ldcg(p_old + i), __ldcg(a.z + i));
+          p_new[i] = pv;
+          a.p32[i] = (float)pv;
+        }
+      } else {
+        for (int i = gid; i < n; i += tpg) p_new[i] = fma(beta, __ldcg(p_old + i), __ldcg(a.z + i));
+      }
       PCG_MARK(1);
       if (!grid_sync(a.bar, a.status)) return;
       PCG_MARK(2);
@@ -912,10 +992,18 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
       // iteration's product reads z itself, so no barrier is needed here
       for (int i = gid; i < n; i += tpg) p_new[i] = __ldcg(a.z + i);
     }
-    const double* pk_vec = first ? a.z : p_new;
+    const double* pk_vec = (first && !f32a) ? a.z : p_new;
     double acc1[1] = {0.0};
     PCG_STAMP(0, it);
-    if (a.Ab.nb > 0) {
+    if (f32a) {
+      auto em = [&](int k, float s0, float s1) {
+        a.q32[2 * k] = s0;
+        a.q32[2 * k + 1] = s1;
+        acc1[0] += __ldcg(pk_vec + 2 * k) * (double)s0 + __ldcg(pk_vec + 2 * k + 1) * (double)s1;
+      };
+      sc.run<LPR>(a.Ab32.nb, apart,
+                  [&](int k, bool act, int lane) { bspmv32_row<LPR>(a.Ab32, a.p32, k, act, lane, em); });
+    } else if (a.Ab.nb > 0) {
       auto em = [&](int k, double s0, double s1) {
         a.q[2 * k] = s0;
         a.q[2 * k + 1] = s1;
@@ -951,22 +1039,44 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
     double* r_new = a.r[(it + 1) & 1];
     const double* r_old = r_cur;
     double acc2[2] = {0.0, 0.0};  // r'.z', r'.r'
-    for (int i = gid; i < n; i += tpg) {
-      a.x[i] = fma(alpha, __ldcg(pk_vec + i), __ldcg(a.x + i));
-      double rr = fma(-alpha, __ldcg(a.q + i), __ldcg(r_old + i));
-      r_new[i] = rr;
-      if (nodal) r32_alt[i] = (float)rr;
-      acc2[1] += rr * rr;
-      if (!nodal) {
-        double zz = a.dinv[i] * rr;
-        a.z[i] = zz;
-        acc2[0] += rr * zz;
+    // FP32 products: every repl-th iteration, and once the recursive residual
+    // has reached the tolerance, r' = rhs - A x' in FP64
+    const bool replace = f32a && (verify || (it + 1) % a.repl == 0);
+    if (replace) {
+      for (int i = gid; i < n; i += tpg) a.x[i] = fma(alpha, __ldcg(pk_vec + i), __ldcg(a.x + i));
+      if (!grid_sync(a.bar, a.status)) return;
+      auto em = [&](int k, double s0, double s1) {
+        const double r0 = a.rhs[2 * k] - s0, r1 = a.rhs[2 * k + 1] - s1;
+        r_new[2 * k] = r0;
+        r_new[2 * k + 1] = r1;
+        r32_alt[2 * k] = (float)r0;
+        r32_alt[2 * k + 1] = (float)r1;
+        acc2[1] += r0 * r0 + r1 * r1;
+      };
+      sc.run<LPR>(a.Ab.nb, apart, [&](int k, bool act, int lane) { bspmv_row<LPR>(a.Ab, a.x, k, act, lane, em); });
+      if (!grid_sync(a.bar, a.status)) return;
+    } else {
+      for (int i = gid; i < n; i += tpg) {
+        a.x[i] = fma(alpha, __ldcg(pk_vec + i), __ldcg(a.x + i));
+        const double qi = f32a ? (double)__ldcg(a.q32 + i) : __ldcg(a.q + i);
+        double rr = fma(-alpha, qi, __ldcg(r_old + i));
+        r_new[i] = rr;
+        if (nodal) r32_alt[i] = (float)rr;
+        acc2[1] += rr * rr;
+        if (!nodal) {
+          double zz = a.dinv[i] * rr;
+          a.z[i] = zz;
+          acc2[0] += rr * zz;
+        }
       }
     }
     if (nodal) {
       const float alpha32 = (float)alpha;
       const float* r32o = r32_cur;
-      auto xr = [&](int c) { return fmaf(-alpha32, __ldcg(a.q32 + c), __ldcg(r32o + c)); };
+      const float* r32n = r32_alt;
+      auto xr = [&](int c) {
+        return replace ? __ldcg(r32n + c) : fmaf(-alpha32, __ldcg(a.q32 + c), __ldcg(r32o + c));
+      };
       auto et = [&](int k, float s) { aux_first_t(a, k, s); };
       auto eu = [&](int k, float s) { aux_first_u(a, k, s); };
       sc.run<FEMPIC_LPR_DT>(a.DT.n_rows, nullptr, [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_DT>(a.DT, r, act, lane, xr, et); });
@@ -994,7 +1104,21 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
     r32_alt = tmp32;
     pb ^= 1;
     rnorm = sqrt(t2[1]);
-    conv = rnorm <= thresh;
+    if (f32a) {  // accept only a replaced (true) residual; otherwise check it next iteration
+      conv = replace && rnorm <= thresh;
+      verify = !conv && rnorm <= thresh;
+      if (replace && !conv) {
+        // safeguard: a true residual that has not halved since the last one
+        // means the FP32 products no longer lead; go on in FP64
+        if (rnorm > 0.5 * last_true) {
+          f32a = false;
+          verify = false;
+        }
+        last_true = rnorm;
+      }
+    } else {
+      conv = rnorm <= thresh;
+    }
     beta = rz != 0.0 ? t2[0] / rz : 0.0;
     rz = t2[0];
   }
