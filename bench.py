@@ -316,6 +316,10 @@ def run_native(args, rank, world, local_rank):
     for _ in range(args.warmup):
         sim.step(dt)
     barrier()
+    # read again after a step: the field solve's product precision is set when
+    # the system is formed for this dt
+    from paper_2111_12411_gb300.native import femPIC_get_info
+    info = femPIC_get_info(sim.h)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     acc = {k: 0.0 for k in ("particle_ms", "field_ms", "launches", "sort_ms", "push_ms", "rhs_ms",
@@ -458,7 +462,10 @@ def run_native(args, rank, world, local_rank):
                        "(256 MiB write)", "parallelism": "replicas" if world > 1 else "single GPU",
                        "n_particles": npart, "n_tets": info.n_tets, "n1": info.n1, "n2": info.n2,
                        "device_bytes": int(info.device_bytes),
-                       "cg_rtol": args.cg_rtol},
+                       "cg_rtol": args.cg_rtol,
+                       "cg_direction_products": "fp32, residual recomputed in fp64 every "
+                                                f"{info.cg_replace_period} iterations"
+                       if info.cg_fp32_products else "fp64"},
             "roofline": roof_pcg if dominant_is_pcg else roof_part,
             "roofline_particle_kernel": roof_part,
             "roofline_cg_kernel": roof_pcg,
@@ -657,7 +664,8 @@ def precision_record(args, local_rank, cfg, K, W, err_steps):
                 acc[k] += t[k]
             cross += sm.diag()["crossings"]
         d = sm.diag()
-        roof_cg, roof_part = _rooflines(info, acc, cross, npart, occupied, K, peak, peak_src)
+        from paper_2111_12411_gb300.native import femPIC_get_info
+        roof_cg, roof_part = _rooflines(femPIC_get_info(sm.h), acc, cross, npart, occupied, K, peak, peak_src)
         out_forms[p] = {"value": npart * K / (1e-3 * sum(t_ms)), "ms_per_step": sum(t_ms) / K,
                         "particle_loop": {"value": npart * K / (1e-3 * acc["particle_ms"]),
                                           "ms_per_step": acc["particle_ms"] / K,

@@ -201,10 +201,11 @@ typedef struct {
 } femPIC_opts;
 
 /* Per-step diagnostics (Section IV-D): continuity and Gauss residuals.
-   femPIC_get(FEMPIC_DIAG) computes the continuity, Gauss and div b residuals
-   of the state as it is at the call (after the first step; zeros before it),
-   so a state changed by femPIC_set shows in them; the CG figures, crossings
-   and absorbed counts are those of the last step. */
+   With opts.diagnostics set, femPIC_get(FEMPIC_DIAG) computes the continuity,
+   Gauss and div b residuals of the state as it is at the call (after the first
+   step; zeros before it), so a state changed by femPIC_set shows in them;
+   without it they are zero.  The CG figures, crossings and absorbed counts are
+   those of the last step. */
 typedef struct {
   int64_t steps;            /* steps taken since create                        */
   int32_t status;           /* latched FEMPIC_* status of the device            */

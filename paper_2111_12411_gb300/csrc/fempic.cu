@@ -1099,7 +1099,7 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
   if (what == FEMPIC_DIAG) {
     femPIC_diag d;
     memset(&d, 0, sizeof(d));
-    if (h->steps > 0) {  // residuals of the state as it is now (after any femPIC_set)
+    if (h->steps > 0 && h->opts.diagnostics) {  // residuals of the state as it is now (after any femPIC_set)
       const int rc = diagnostics(h);
       if (rc) return rc;
     }
