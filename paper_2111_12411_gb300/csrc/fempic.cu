@@ -89,8 +89,8 @@ struct FemPIC {
   int32_t *brp = nullptr, *bci = nullptr;
   double *bM = nullptr, *bK = nullptr, *bA = nullptr, *binv = nullptr;
   float* bA32 = nullptr;   // FP32 copy of bA: the CG's direction products (FEMPIC_PCG_FP32A)
-  double kdiag_med = 0.0;  // median over W1 rows of K_ii / (4 M_ii): dt^2 times it is the
-                           // typical ratio of the curl-curl to the mass term of A
+  double kdiag_med = 0.0;  // median over W1 rows of K_ii / M_ii: the coefficient of K in A
+                           // times it is the typical ratio of the curl-curl to the mass term
   bool pcg_fp32 = false;   // this dt's solves use the FP32 direction products
   double *dvM = nullptr, *dvK = nullptr;
   // FP32 copies for the preconditioner's auxiliary-space corrections
@@ -475,6 +475,11 @@ int form_system(FemPIC* h, double dt) {
   int grid = grid_for(h->n1, 256, 1 << 30);
   // impedance faces (trapezoid only): A += dt/2 I, R1 -= dt/2 I
   const double ci_imp = h->Iv ? 0.5 * dt : 0.0;
+  // FP32 direction products only while the curl-curl term stays within
+  // kPcgFp32MaxRatio of the mass term (median over the rows): beyond it the
+  // cancellation in A x of gradient fields outgrows what FP32 products and
+  // the FP64 residual replacement can follow
+  h->pcg_fp32 = h->bA32 && h->kdiag_med * c1 <= kPcgFp32MaxRatio;
   k_form_system<<<grid, 256, 0, h->stream>>>(h->n1, h->M.rp, h->M.ci, h->M.v, h->K.v, c1, cr1, h->Aval, h->R1val,
                                              h->dinvA, h->Iv, ci_imp, -ci_imp);
   h->launches++;
@@ -503,11 +508,6 @@ int form_system(FemPIC* h, double dt) {
     k_form_blocks<<<grid_for(h->nb, 256, 1 << 30), 256, 0, h->stream>>>(h->nb, h->brp, h->bci, h->bM, h->bK, c1,
                                                                         h->bA, h->binv, h->bI, ci_imp);
     h->launches++;
-    // FP32 direction products only while the curl-curl term stays within
-    // kPcgFp32MaxRatio of the mass term (median over the rows): beyond it the
-    // cancellation in A x of gradient fields outgrows what FP32 products and
-    // the FP64 residual replacement can follow
-    h->pcg_fp32 = h->bA32 && h->kdiag_med * dt * dt <= kPcgFp32MaxRatio;
     if (h->pcg_fp32) {
       k_to_f32<<<grid_for(4 * h->nnzb, 256, 4096), 256, 0, h->stream>>>(4 * h->nnzb, h->bA, h->bA32);
       h->launches++;
@@ -1335,7 +1335,7 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
           m = hm.M.val[j];
           k = hm.K.val[j];
         }
-      if (m > 0.0) ratio.push_back(0.25 * k / m);
+      if (m > 0.0) ratio.push_back(k / m);
     }
     if (!ratio.empty()) {
       std::nth_element(ratio.begin(), ratio.begin() + ratio.size() / 2, ratio.end());
