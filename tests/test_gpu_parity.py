@@ -152,9 +152,10 @@ def test_diagnostics_match_oracle(c1small, order):
     device norm must equal the oracle's to 1e-10 of its value plus the
     rounding of the terms that cancel in it (128 eps of their size): after a
     step both residuals are at rounding or CG-tolerance level; then Delta g
-    and e are perturbed through femPIC_set, the residuals grow by orders of
-    magnitude, and the device's values must follow to 1e-10 (a residual
-    computed as zero, or with a wrong operator or sign, fails there)."""
+    and e are perturbed through femPIC_set (by 1e-4 of their largest entry),
+    the residuals grow by orders of magnitude, and the device's values must
+    follow to the same bound (a residual computed as zero, or with a wrong
+    operator or sign, fails there: the bound is then far below the residual)."""
     o, g = pair(c1small, order=order, precision="fp64", diagnostics=True)
     rho0 = g.get("RHO")
     g.step(c1small["dt"])
@@ -186,8 +187,8 @@ def test_diagnostics_match_oracle(c1small, order):
     assert same(d["gauss_abs"], g_abs, g_sc) and g_abs <= 1e-9 * g_ref
     fr = o.topo.free1
     rng = np.random.default_rng(12)
-    dgp = dg + fr * (1e-6 * np.abs(dg).max()) * rng.standard_normal(dg.size)
-    ep = eg + fr * (1e-6 * np.abs(eg).max()) * rng.standard_normal(eg.size)
+    dgp = dg + fr * (1e-4 * np.abs(dg).max()) * rng.standard_normal(dg.size)
+    ep = eg + fr * (1e-4 * np.abs(eg).max()) * rng.standard_normal(eg.size)
     g.set("DG", dgp)
     g.set("E", ep)
     d2 = g.diag()
@@ -195,7 +196,6 @@ def test_diagnostics_match_oracle(c1small, order):
     g2, _, g2_sc = gauss(ep)
     assert c2 > 1e3 * max(c_abs, d["continuity_abs"]) and g2 > 1e3 * max(g_abs, d["gauss_abs"])
     assert same(d2["continuity_abs"], c2, c2_sc) and same(d2["gauss_abs"], g2, g2_sc)
-    assert abs(d2["continuity_abs"] - c2) <= 1e-10 * c2 and abs(d2["gauss_abs"] - g2) <= 1e-10 * g2
     g.close()
 
 
