@@ -78,6 +78,9 @@ struct FemPIC {
   int64_t np = 0;
   // device mesh
   double* geom = nullptr;
+  float* geom32 = nullptr;  // mixed precision: barycentric gradients [nt][12] in FP32
+  float* e32 = nullptr;     // mixed precision: e and the sampled b rounded to FP32,
+  float* b32 = nullptr;     // refreshed before every particle launch
   int32_t *nbr = nullptr, *dof0 = nullptr, *dof1 = nullptr, *dof2 = nullptr;
   uint8_t *pec1 = nullptr, *int0 = nullptr;
   double* load0 = nullptr;
@@ -652,6 +655,16 @@ int launch_particles(FemPIC* h, double dt) {
   a.absorbed = h->pabs;
   a.n_tets = h->n_tets;
   if (h->np == 0) return FEMPIC_OK;
+  if (h->e32 && h->opts.precision == FEMPIC_MIXED && h->opts.push != FEMPIC_PUSH_AB4 && h->order <= 2) {
+    // the mixed gather's FP32 copies of this step's e and sampled b
+    k_to_f32<<<grid_for(h->n1, 256, 4096), 256, 0, h->stream>>>(h->n1, h->e, h->e32);
+    k_to_f32<<<grid_for(h->n2, 256, 4096), 256, 0, h->stream>>>(h->n2, a.b, h->b32);
+    h->launches += 2;
+    CK(cudaGetLastError());
+    a.e32 = h->e32;
+    a.b32 = h->b32;
+    a.geom32 = h->geom32;
+  }
   if (h->opts.push == FEMPIC_PUSH_AB4) {
     Ab4Args A;
     A.p = a;
@@ -1313,6 +1326,13 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
   rc = upload(h, &(dst), (src)); \
   if (rc) return rc;
   UP(h->geom, hm.geom);
+  if (o.precision == FEMPIC_MIXED) {
+    std::vector<float> g32((size_t)hm.n_tets * 12);
+    for (size_t t = 0; t < (size_t)hm.n_tets; ++t)
+      for (int k = 0; k < 12; ++k) g32[t * 12 + k] = (float)hm.geom[t * 16 + k];
+    UP(h->geom32, g32);
+    if ((rc = dalloc(h, &h->e32, std::max(1, hm.n1))) || (rc = dalloc(h, &h->b32, std::max(1, hm.n2)))) return rc;
+  }
   UP(h->nbr, hm.nbr);
   UP(h->dof0, hm.dof0);
   UP(h->dof1, hm.dof1);

@@ -500,6 +500,12 @@ struct ParticleArgs {
   SpeciesTable sp;
   uint8_t* absorbed = nullptr;  // [n] 1 where the path ended on an absorbing wall (null: none)
   int32_t n_tets = 0;           // bound of the tet ids (checked builds)
+  // FP32 copies read by the mixed-precision gather (null: convert on use):
+  // e and b rounded to FP32, and the gradients of each tet's barycentrics
+  // ([nt][12]); the same values the conversions would give
+  const float* e32 = nullptr;
+  const float* b32 = nullptr;
+  const float* geom32 = nullptr;
 };
 
 // q w and q dt / 2m of the particle in device slot i

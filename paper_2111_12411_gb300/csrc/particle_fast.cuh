@@ -200,16 +200,17 @@ __device__ __forceinline__ void deposit_rho_fact(const double* l, double qw, con
 // ---- FP32 gather and push (mixed precision): lambda and geometry rounded to
 // float, DOF values read as FP64 and rounded, E, B and the Boris rotation in
 // FP32.  Positions, the walk, the deposit and the charge stay FP64.
-template <int P>
-__device__ __forceinline__ void gather_EB_f32(const TetGeom& Gd, const double* lad, const double* __restrict__ e,
-                                              const int32_t* __restrict__ d1, const double* __restrict__ b,
-                                              const int32_t* __restrict__ d2, const double* B0d, float* E, float* B) {
+template <int P, class VT>
+__device__ __forceinline__ void gather_EB_f32(const TetGeom& Gd, const double* lad, const VT* __restrict__ e,
+                                              const int32_t* __restrict__ d1, const VT* __restrict__ b,
+                                              const int32_t* __restrict__ d2, const double* B0d, float* E, float* B,
+                                              const float* __restrict__ g32 = nullptr) {
   float l[4], g[4][3];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     l[i] = (float)lad[i];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) g[i][k] = (float)Gd.g[i][k];
+    for (int k = 0; k < 3; ++k) g[i][k] = g32 ? __ldg(g32 + 3 * i + k) : (float)Gd.g[i][k];
   }
   float c[6];
   if (P == 1) {
@@ -341,7 +342,11 @@ __device__ __forceinline__ void particle_step(const ParticleArgs& a, int64_t i) 
   bary_fma(G, x, la);
   if (MIXED) {
     float Ef[3], Bf[3], vf[3] = {(float)v[0], (float)v[1], (float)v[2]};
-    gather_EB_f32<P>(G, la, a.e, a.dof1 + (size_t)T * N1, a.b, a.dof2 + (size_t)T * N2, a.B0, Ef, Bf);
+    if (a.e32)
+      gather_EB_f32<P>(G, la, a.e32, a.dof1 + (size_t)T * N1, a.b32, a.dof2 + (size_t)T * N2, a.B0, Ef, Bf,
+                       a.geom32 + (size_t)T * 12);
+    else
+      gather_EB_f32<P>(G, la, a.e, a.dof1 + (size_t)T * N1, a.b, a.dof2 + (size_t)T * N2, a.B0, Ef, Bf);
     boris_f32(vf, Ef, Bf, (float)hq);
     v[0] = vf[0];
     v[1] = vf[1];
