@@ -108,3 +108,48 @@ def test_ab4_restarts_history_on_set():
     assert w["order"] == 1
     assert np.abs(g.get("X") - w["x"]).max() <= 1e-12 and np.array_equal(g.get("TET"), w["tet"])
     g.close()
+
+
+def test_ab4_finds_a_crossing_pair_inside_one_eighth_of_the_step():
+    """A path that leaves its tet through a face and comes back within one
+    eighth of the step (the kind of excursion an eight-sample search misses):
+    one electron in a uniform E field on an unjittered Kuhn box, started so
+    that its second step (Adams-Bashforth 2) is the parabola
+    z(s) = 0.5 + beta (s - 0.3)(s - 0.34) across the plane z = 0.5.  Device and
+    oracle both count two crossings, end in the starting tet and agree on the
+    crossing hash."""
+    from paper_2111_12411_gb300 import Simulation
+    from oracle import geometry, topology
+    xyz, tets = workloads.kuhn_box(4, 4, 4)
+    t = topology.Topology(xyz, tets, 1)
+    g_all, c_all, _ = geometry.barycentric_maps(t.xyz, t.tets)
+    dt, beta = 1e-9, 0.0375
+    a_z = 2.0 * beta / dt ** 2
+    v1 = np.array([0.0, 0.0, -0.64 * beta / dt])
+    v0 = v1 - np.array([0.0, 0.0, dt * a_z])
+    x1 = np.array([0.35, 0.30, 0.5 + 0.102 * beta])
+    x0 = x1 - dt * v0
+    E = np.array([0.0, 0.0, a_z * M_E / -Q_E])                 # electron: a = -(e/m) E
+    e_dof = (t.xyz[t.edges[:, 1]] - t.xyz[t.edges[:, 0]]) @ E  # Whitney DOFs of the uniform field
+    zs = [0.5 + beta * (s - 0.3) * (s - 0.34) for s in np.arange(9) / 8.0]
+    assert min(zs) > 0.5                                        # every eighth of the step is above the plane
+    lam = np.einsum("tik,k->ti", g_all, x0) + c_all
+    tet0 = np.array([int(np.argmax(lam.min(axis=1)))])
+    o = osim.Sim(xyz, tets, 1, -Q_E, M_E, 1.0, push="ab4")
+    o.set_particles(x0[None], v0[None], tet0)
+    g = Simulation(xyz, tets, 1, -Q_E, M_E, 1.0, x0[None], v0[None], tet0, push="ab4", es_init=False)
+    for k in range(2):
+        tet1 = int(o.tet[0])                                    # the tet the step starts in
+        o.e, o.e_prev, o.b = e_dof.copy(), e_dof.copy(), np.zeros(t.n2)
+        g.set("E", o.e)
+        g.set("E_PREV", o.e_prev)
+        g.set("B", o.b)
+        w = o.step(dt)
+        g.step(dt)
+    assert w["order"] == 2
+    assert w["ncross"][0] == 2 and w["tet"][0] == tet1          # out through z = 0.5 and back
+    assert np.array_equal(g.get("NCROSS"), w["ncross"])
+    assert np.array_equal(g.get("TET"), w["tet"])
+    assert np.array_equal(g.get("HASH"), w["hash"])
+    assert np.abs(g.get("X")[0] - w["x"][0]).max() <= 1e-12
+    g.close()
