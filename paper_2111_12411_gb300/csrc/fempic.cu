@@ -169,6 +169,7 @@ struct FemPIC {
   double* divref = nullptr;   // [n3][nl2] int_ref W3_i div W2_j (div b diagnostic)
   int32_t n3 = 0;
   unsigned long long* d_cross = nullptr;
+  unsigned long long* d_first = nullptr;  // first bad element of a staged host transfer (all ones: none)
   double* d_tmp1 = nullptr;  // N1 scratch
   double* d_tmp0 = nullptr;  // N0 scratch
   double dt_cur = -1.0;
@@ -1052,32 +1053,6 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
     h->err = "NULL buffer";
     return FEMPIC_ERR_ARG;
   }
-  if (to_handle && (what == FEMPIC_X || what == FEMPIC_V) && !buf_on_device) {
-    // exponent bits all set = infinity or NaN; an OR over the array (integer
-    // work the compiler vectorises), the index only looked up on failure
-    const double* d = static_cast<const double*>(buf);
-    const int64_t m = 3 * h->np;
-    uint64_t bad = 0;
-    for (int64_t i = 0; i < m; ++i) {
-      uint64_t u;
-      memcpy(&u, d + i, sizeof(u));
-      bad |= (uint64_t)((u & 0x7FF0000000000000ull) == 0x7FF0000000000000ull);
-    }
-    if (bad) {
-      int64_t i = 0;
-      while (i < m && std::isfinite(d[i])) ++i;
-      h->err = "non-finite value at particle " + std::to_string(i / 3);
-      return FEMPIC_ERR_ARG;
-    }
-  }
-  if (to_handle && what == FEMPIC_TET && !buf_on_device) {
-    const int32_t* t = static_cast<const int32_t*>(buf);
-    for (int64_t i = 0; i < h->np; ++i)
-      if (t[i] < 0 || t[i] >= h->n_tets) {
-        h->err = "tet id out of range at particle " + std::to_string(i);
-        return FEMPIC_ERR_ARG;
-      }
-  }
   CK(cudaSetDevice(h->device));
 #if FEMPIC_CHECKS
   if (to_handle && what == FEMPIC_TET && buf_on_device && h->np > 0) {
@@ -1187,12 +1162,18 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
   if (h->np == 0) return FEMPIC_OK;
   int grid = grid_for(h->np, 256, 1 << 30);
   double* stage = h->stage;
-  if (to_handle && (what == FEMPIC_X || what == FEMPIC_V || what == FEMPIC_TET)) h->ab_count = 0;
+  // Host X, V and TET are validated on the device after the staging copy: the
+  // first non-finite value or out-of-range tet id vetoes the gather into the
+  // particle state, so a refused transfer leaves the state as it was.
+  const bool check = to_handle && !buf_on_device && (what == FEMPIC_X || what == FEMPIC_V || what == FEMPIC_TET);
+  const unsigned long long* veto = check ? h->d_first : nullptr;
+  const int vgrid = grid_for(3 * h->np, 256, h->num_sms * 8);
   if (what == FEMPIC_X || what == FEMPIC_V) {
     double** dst = what == FEMPIC_X ? h->px : h->pv;
     if (to_handle) {
       CK(cudaMemcpyAsync(stage, buf, need, up, h->stream));
-      k_gather_by_id<<<grid, 256, 0, h->stream>>>(h->np, h->pid, stage, dst[0], dst[1], dst[2]);
+      if (check) k_first_nonfinite<<<vgrid, 256, 0, h->stream>>>(3 * h->np, stage, h->d_first);
+      k_gather_by_id<<<grid, 256, 0, h->stream>>>(h->np, h->pid, stage, dst[0], dst[1], dst[2], veto);
     } else {
       k_scatter_by_id<<<grid, 256, 0, h->stream>>>(h->np, h->pid, dst[0], dst[1], dst[2], stage);
       CK(cudaMemcpyAsync(buf, stage, need, down, h->stream));
@@ -1202,7 +1183,8 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
     int32_t* st = reinterpret_cast<int32_t*>(stage);
     if (to_handle) {
       CK(cudaMemcpyAsync(st, buf, need, up, h->stream));
-      k_gather1_by_id<int32_t><<<grid, 256, 0, h->stream>>>(h->np, h->pid, st, src);
+      if (check) k_first_bad_tet<<<vgrid, 256, 0, h->stream>>>(h->np, st, h->n_tets, h->d_first);
+      k_gather1_by_id<int32_t><<<grid, 256, 0, h->stream>>>(h->np, h->pid, st, src, veto);
     } else {
       k_scatter1_by_id<int32_t><<<grid, 256, 0, h->stream>>>(h->np, h->pid, src, st);
       CK(cudaMemcpyAsync(buf, st, need, down, h->stream));
@@ -1213,7 +1195,17 @@ int transfer(FemPIC* h, int32_t what, void* buf, size_t bytes, bool to_handle, b
     CK(cudaMemcpyAsync(buf, st, need, down, h->stream));
   }
   CK(cudaGetLastError());
+  unsigned long long first = ~0ull;
+  if (check) CK(cudaMemcpyAsync(&first, h->d_first, sizeof(first), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (first != ~0ull) {
+    CK(cudaMemsetAsync(h->d_first, 0xFF, sizeof(unsigned long long), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->err = what == FEMPIC_TET ? "tet id out of range at particle " + std::to_string(first)
+                                : "non-finite value at particle " + std::to_string(first / 3);
+    return FEMPIC_ERR_ARG;
+  }
+  if (to_handle && (what == FEMPIC_X || what == FEMPIC_V || what == FEMPIC_TET)) h->ab_count = 0;
   if (to_handle && (what == FEMPIC_X || what == FEMPIC_TET)) {
     int rc = measure_rho(h, h->rho);
     if (rc) return rc;
@@ -1529,8 +1521,9 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
   if ((rc = dalloc(h, &h->partials, 8 * (size_t)h->pcg_blocks_w1)) || (rc = dalloc(h, &h->bar, 1)) ||
       (rc = dalloc(h, &h->d_status, 1)) || (rc = dalloc(h, &h->d_cg_iters, 1)) || (rc = dalloc(h, &h->d_cg_res, 1)) ||
       (rc = dalloc(h, &h->d_cg_iters_acc, 1)) ||
-      (rc = dalloc(h, &h->d_norms, 6)) || (rc = dalloc(h, &h->d_cross, 1)))
+      (rc = dalloc(h, &h->d_norms, 6)) || (rc = dalloc(h, &h->d_cross, 1)) || (rc = dalloc(h, &h->d_first, 1)))
     return rc;
+  CK(cudaMemset(h->d_first, 0xFF, sizeof(unsigned long long)));
   for (void* p : std::vector<void*>{h->e, h->e_prev, h->e_new, h->dg, h->dg_prev})
     CK(cudaMemset(p, 0, sizeof(double) * h->n1));
   CK(cudaMemset(h->b, 0, sizeof(double) * h->n2));

@@ -1216,11 +1216,26 @@ __global__ void k_sort_scatter(SortArgs a) {
   a.to[1][pos] = a.ti[1][i];
 }
 
-// particle-id order <-> device order
+// Validation of a staged transfer: the lowest index of an element that is not
+// finite (exponent bits all set) or, for tet ids, outside [0, n_tets), kept by
+// atomicMin in *first (all ones = none found).
+__global__ void k_first_nonfinite(int64_t m, const double* v, unsigned long long* first) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v[i]);
+    if ((u & 0x7FF0000000000000ull) == 0x7FF0000000000000ull) atomicMin(first, (unsigned long long)i);
+  }
+}
+__global__ void k_first_bad_tet(int64_t m, const int32_t* t, int32_t n_tets, unsigned long long* first) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    if (t[i] < 0 || t[i] >= n_tets) atomicMin(first, (unsigned long long)i);
+}
+
+// particle-id order <-> device order; a gather with a veto word writes nothing
+// once the validation above found a bad element
 __global__ void k_gather_by_id(int64_t n, const int32_t* pid, const double* src_il, double* d0, double* d1,
-                               double* d2) {
+                               double* d2, const unsigned long long* veto = nullptr) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || (veto && *veto != ~0ull)) return;
   int64_t p = pid[i];
   d0[i] = src_il[3 * p];
   d1[i] = src_il[3 * p + 1];
@@ -1241,9 +1256,10 @@ __global__ void k_scatter1_by_id(int64_t n, const int32_t* pid, const T* s, T* d
   if (i < n) dst[pid[i]] = s[i];
 }
 template <class T>
-__global__ void k_gather1_by_id(int64_t n, const int32_t* pid, const T* s, T* dst) {
+__global__ void k_gather1_by_id(int64_t n, const int32_t* pid, const T* s, T* dst,
+                                const unsigned long long* veto = nullptr) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = s[pid[i]];
+  if (i < n && !(veto && *veto != ~0ull)) dst[i] = s[pid[i]];
 }
 
 // ---- diagnostics ----------------------------------------------------------------

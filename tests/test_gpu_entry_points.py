@@ -5,6 +5,9 @@ need a test build of the library.
   buffer equals femPIC_get's host copy; state loaded from device buffers
   gives the same next step (strict mode, bit-exact) as the same state loaded
   from host buffers.
+* femPIC_set from host buffers refuses non-finite X or V and out-of-range
+  tet ids (checked on the device after the staging copy) and leaves the
+  particle state untouched.
 * The bounds-checked build (-DFEMPIC_CHECKS=1): an out-of-range tet id handed
   over through femPIC_set_device is refused with FEMPIC_ERR_BOUNDS before it
   is copied or read; the handle keeps working with valid ids.
@@ -72,6 +75,54 @@ def test_device_buffer_transfers_round_trip():
     assert ei.value.code == native.FEMPIC_ERR_SIZE
     for s in (a, b, c):
         s.close()
+
+
+def test_host_set_refuses_bad_particle_state():
+    """femPIC_set validates host X, V and TET on the device after the staging
+    copy: a non-finite value or a tet id outside [0, n_tets) is refused with
+    FEMPIC_ERR_ARG naming the first bad particle, and nothing of it reaches
+    the particle state (X, V, TET and the measured RHO unchanged, the next
+    step bit-identical to a handle that saw no refused call)."""
+    from paper_2111_12411_gb300 import Simulation, native
+    cfg = workloads.make_config(0, n_particles=5003)
+    a = Simulation.from_config(cfg, precision="fp64_strict", es_init=False)
+    b = Simulation.from_config(cfg, precision="fp64_strict", es_init=False)
+    a.step(cfg["dt"])
+    b.step(cfg["dt"])
+    before = {q: a.get(q) for q in ("X", "V", "TET", "RHO")}
+    n_tets = a.info.n_tets
+    cases = []
+    for q, val in (("X", np.nan), ("X", np.inf), ("V", -np.inf), ("V", np.nan)):
+        for p in (0, 2711, a.n_particles - 1):
+            cases.append((q, p, val))
+    for val in (-1, n_tets, np.iinfo(np.int32).min):
+        for p in (0, 4999):
+            cases.append(("TET", p, val))
+    for q, p, val in cases:
+        bad = before[q].copy()
+        bad[p] = val
+        if q != "TET":
+            bad[p + 1:] = np.nan  # later bad elements: the first is named
+        with pytest.raises(native.FemPICError) as ei:
+            a.set(q, bad)
+        assert ei.value.code == native.FEMPIC_ERR_ARG, (q, p)
+        assert f"particle {p}" in str(ei.value), (q, p, str(ei.value))
+        for k, v in before.items():
+            assert np.array_equal(a.get(k), v), (q, p, k)
+    # a valid set after the refusals is taken; the field state is copied from
+    # one handle to both (each handle's own first step summed its deposit with
+    # FP64 atomics, in an order that may differ in the last bits)
+    state = {q: a.get(q) for q in ("E", "E_PREV", "B", "DG", "DG_PREV")}
+    state.update({q: before[q] for q in ("X", "V", "TET")})
+    for q, v in state.items():
+        a.set(q, v)
+        b.set(q, v)
+    a.step(cfg["dt"])
+    b.step(cfg["dt"])
+    for q in ("X", "V", "TET", "HASH"):
+        assert np.array_equal(a.get(q), b.get(q)), q
+    a.close()
+    b.close()
 
 
 def _child(variant, body):
