@@ -1515,7 +1515,7 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
     std::vector<int32_t> part = balanced_ranges(pre, h->pcg_blocks_w1);
     if ((rc = upload(h, &h->apart, part))) return rc;
   }
-  if ((rc = dalloc(h, &h->cg_q32, nmax)) || (rc = dalloc(h, &h->cg_r32, 2 * (size_t)nmax)) ||
+  if ((rc = dalloc(h, &h->cg_q32, nmax)) || (rc = dalloc(h, &h->cg_r32, 4 * (size_t)nmax)) ||
       (rc = dalloc(h, &h->cg_p32, nmax)) || (rc = dalloc(h, &h->cg_red, 12)))
     return rc;
   if ((rc = dalloc(h, &h->partials, 8 * (size_t)h->pcg_blocks_w1)) || (rc = dalloc(h, &h->bar, 1)) ||

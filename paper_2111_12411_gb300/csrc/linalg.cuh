@@ -342,8 +342,8 @@ struct PcgArgs {
   int cheb_k;
   float chebL[3][kMaxCheb];  // [0][0] = 1/theta; [1][i], [2][i]: step i coefficients
   float chebV[3][kMaxCheb];
-  float* q32;  // FP32 shadows of q and r (inputs of the auxiliary products)
-  float* r32;
+  float* q32;  // unused by k_pcg (its q shadow lives in r32)
+  float* r32;  // [2][n] pairs (r_i, q_i): FP32 shadows of r and q, the inputs of the auxiliary products
   double* red; // [3][4] reduction slots, zeroed before the launch
   // order 2: the system matrix in 2x2 blocks and the inverses of its
   // diagonal blocks (block Jacobi); Ab.nb == 0 uses A and dinv
@@ -907,8 +907,11 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
   PcgSched sc{gid, tpg, ring, 0};
   const int32_t* apart = a.Apart;
   double* r_cur = a.r[0];
-  float* r32_cur = a.r32;        // FP32 shadow of r, double-buffered like r
-  float* r32_alt = a.r32 + n;
+  // FP32 shadows of r and q for the auxiliary products, the pair (r_i, q_i)
+  // of one buffer side by side so that r - alpha q, formed on the fly in the
+  // restriction products, takes one 8-byte gather; double-buffered like r
+  float2* rq_cur = reinterpret_cast<float2*>(a.r32);
+  float2* rq_alt = rq_cur + n;
   int kred = 0;  // reductions so far (slot of the ring)
 #ifdef FEMPIC_PCG_PROFILE
   unsigned long long prof_acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -920,7 +923,7 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
     double b = a.rhs[r0];
     double rr = b - s;
     r_cur[r0] = rr;
-    if (nodal) r32_cur[r0] = (float)rr;
+    if (nodal) rq_cur[r0].x = (float)rr;
     acc[1] += rr * rr;
     acc[2] += b * b;
     if (!nodal) {
@@ -941,7 +944,7 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
   }
   if (nodal) {
     if (!grid_sync(a.bar, a.status)) return;
-    auto x0 = [&](int c) { return __ldcg(r32_cur + c); };
+    auto x0 = [&](int c) { return __ldcg(&rq_cur[c].x); };
     auto et = [&](int k, float s) { aux_first_t(a, k, s); };
     auto eu = [&](int k, float s) { aux_first_u(a, k, s); };
     sc.run<FEMPIC_LPR_DT>(a.DT.n_rows, nullptr, [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_DT>(a.DT, r, act, lane, x0, et); });
@@ -997,8 +1000,8 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
     PCG_STAMP(0, it);
     if (f32a) {
       auto em = [&](int k, float s0, float s1) {
-        a.q32[2 * k] = s0;
-        a.q32[2 * k + 1] = s1;
+        rq_cur[2 * k].y = s0;
+        rq_cur[2 * k + 1].y = s1;
         acc1[0] += __ldcg(pk_vec + 2 * k) * (double)s0 + __ldcg(pk_vec + 2 * k + 1) * (double)s1;
       };
       sc.run<LPR>(a.Ab32.nb, apart,
@@ -1008,8 +1011,8 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
         a.q[2 * k] = s0;
         a.q[2 * k + 1] = s1;
         if (nodal) {
-          a.q32[2 * k] = (float)s0;
-          a.q32[2 * k + 1] = (float)s1;
+          rq_cur[2 * k].y = (float)s0;
+          rq_cur[2 * k + 1].y = (float)s1;
         }
         acc1[0] += __ldcg(pk_vec + 2 * k) * s0 + __ldcg(pk_vec + 2 * k + 1) * s1;
       };
@@ -1019,7 +1022,7 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
       auto xo = [&](int c) { return __ldcg(pk_vec + c); };
       auto em = [&](int r0, double s) {
         a.q[r0] = s;
-        if (nodal) a.q32[r0] = (float)s;
+        if (nodal) rq_cur[r0].y = (float)s;
         acc1[0] += __ldcg(pk_vec + r0) * s;
       };
       sc.run<LPR>(n, apart, [&](int r, bool act, int lane) { spmv_row<LPR>(a.A, r, act, lane, xo, em); });
@@ -1049,8 +1052,8 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
         const double r0 = a.rhs[2 * k] - s0, r1 = a.rhs[2 * k + 1] - s1;
         r_new[2 * k] = r0;
         r_new[2 * k + 1] = r1;
-        r32_alt[2 * k] = (float)r0;
-        r32_alt[2 * k + 1] = (float)r1;
+        rq_alt[2 * k].x = (float)r0;
+        rq_alt[2 * k + 1].x = (float)r1;
         acc2[1] += r0 * r0 + r1 * r1;
       };
       sc.run<LPR>(a.Ab.nb, apart, [&](int k, bool act, int lane) { bspmv_row<LPR>(a.Ab, a.x, k, act, lane, em); });
@@ -1058,10 +1061,10 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
     } else {
       for (int i = gid; i < n; i += tpg) {
         a.x[i] = fma(alpha, __ldcg(pk_vec + i), __ldcg(a.x + i));
-        const double qi = f32a ? (double)__ldcg(a.q32 + i) : __ldcg(a.q + i);
+        const double qi = f32a ? (double)__ldcg(&rq_cur[i].y) : __ldcg(a.q + i);
         double rr = fma(-alpha, qi, __ldcg(r_old + i));
         r_new[i] = rr;
-        if (nodal) r32_alt[i] = (float)rr;
+        if (nodal) rq_alt[i].x = (float)rr;
         acc2[1] += rr * rr;
         if (!nodal) {
           double zz = a.dinv[i] * rr;
@@ -1072,10 +1075,12 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
     }
     if (nodal) {
       const float alpha32 = (float)alpha;
-      const float* r32o = r32_cur;
-      const float* r32n = r32_alt;
+      const float2* rqo = rq_cur;
+      const float2* rqn = rq_alt;
       auto xr = [&](int c) {
-        return replace ? __ldcg(r32n + c) : fmaf(-alpha32, __ldcg(a.q32 + c), __ldcg(r32o + c));
+        if (replace) return __ldcg(&rqn[c].x);
+        const float2 v = __ldcg(rqo + c);
+        return fmaf(-alpha32, v.y, v.x);
       };
       auto et = [&](int k, float s) { aux_first_t(a, k, s); };
       auto eu = [&](int k, float s) { aux_first_u(a, k, s); };
@@ -1099,9 +1104,9 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
     grid_sum_read<2>(a.red, kred++, t2);
     ++it;
     r_cur = r_new;
-    float* tmp32 = r32_cur;
-    r32_cur = r32_alt;
-    r32_alt = tmp32;
+    float2* tmp32 = rq_cur;
+    rq_cur = rq_alt;
+    rq_alt = tmp32;
     pb ^= 1;
     rnorm = sqrt(t2[1]);
     if (f32a) {  // accept only a replaced (true) residual; otherwise check it next iteration
