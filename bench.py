@@ -62,7 +62,11 @@ def pcg_bytes_per_iteration(info):
     reads, t, u, z writes; direction update: p, z read, p write), and for each
     of the cheb_k - 1 Chebyshev steps of the auxiliary problems the FP32 L and
     V arrays plus five FP32 vector passes (right side, step and iterate read;
-    step and iterate written)."""
+    step and iterate written).  With the Chebyshev smoother of degree ks on
+    B^-1 A (cg_smooth_degree > 1): its first iterate (2x2 block inverse read,
+    iterate and step written) and ks - 1 more FP32 A products, each with the
+    residual, the block inverse, the step (read and written), the iterate
+    read and the next one written."""
     n1, n0 = info.n1, info.n0
     nv = 3 * info.n_nodes
     a64 = (8 * info.nnz_A + info.nnz_A) if info.order == 2 else 12 * info.nnz_A
@@ -78,7 +82,9 @@ def pcg_bytes_per_iteration(info):
         a32 = 4 * info.nnz_A + info.nnz_A
         vec = 4 * n1 + 4 * n1 + (8 * 3 + 4 + 16) * n1 + (16 + 8 + 4) * n1
         repl = (a64 + (8 + 8 + 8 + 4) * n1) / max(1, int(info.cg_replace_period))
-        return a32 + mats + vec + aux + cheb + repl
+        ks = max(1, int(getattr(info, "cg_smooth_degree", 1)))
+        smooth = 0 if ks == 1 else (16 + 8) * n1 + (ks - 1) * (a32 + (8 + 16 + 8 + 4 + 4) * n1)
+        return a32 + mats + vec + aux + cheb + repl + smooth
     vec = 8 * (2 * n1 + 6 * n1 + n1 + 3 * n1)
     return a64 + mats + vec + aux + cheb
 
@@ -465,7 +471,10 @@ def run_native(args, rank, world, local_rank):
                        "cg_rtol": args.cg_rtol,
                        "cg_direction_products": "fp32, residual recomputed in fp64 every "
                                                 f"{info.cg_replace_period} iterations"
-                       if info.cg_fp32_products else "fp64"},
+                       if info.cg_fp32_products else "fp64",
+                       "cg_preconditioner": (f"Chebyshev smoother of degree {info.cg_smooth_degree} on B^-1 A"
+                                             if info.cg_smooth_degree > 1 else "block Jacobi")
+                       + f" + auxiliary spaces, {info.aux_cheb_degree} Chebyshev steps"},
             "roofline": roof_pcg if dominant_is_pcg else roof_part,
             "roofline_particle_kernel": roof_part,
             "roofline_cg_kernel": roof_pcg,

@@ -92,6 +92,12 @@ struct FemPIC {
   int32_t *brp = nullptr, *bci = nullptr;
   double *bM = nullptr, *bK = nullptr, *bA = nullptr, *binv = nullptr;
   float* bA32 = nullptr;   // FP32 copy of bA: the CG's direction products (FEMPIC_PCG_FP32A)
+  // Chebyshev smoother on B^-1 A (order 2, FP32 A): degree, whether it is in
+  // use for the current system, its coefficients and its vectors
+  int smooth_k = 1;
+  bool smooth_on = false;
+  float* chebS = nullptr;  // [3 * kMaxCheb] coefficients, written on the device
+  float *sy = nullptr, *sd = nullptr;
   double kdiag_med = 0.0;  // median over W1 rows of K_ii / M_ii: the coefficient of K in A
                            // times it is the typical ratio of the curl-curl to the mass term
   bool pcg_fp32 = false;   // this dt's solves use the FP32 direction products
@@ -143,6 +149,11 @@ struct FemPIC {
   std::vector<int32_t> hLA_rp, hLA_ci;
   std::vector<double> hLA_m, hLA_i;
   float chebLA[3][kMaxCheb] = {};
+  // with the smoother: the degree of the auxiliary Chebyshev steps and their
+  // coefficients (same bounds, more steps), and the bounds they come from
+  int cheb_k_sm = 1;
+  float chebL_sm[3][kMaxCheb] = {}, chebV_sm[3][kMaxCheb] = {}, chebLA_sm[3][kMaxCheb] = {};
+  double lmaxL = 0.0;
   // species: ids [sp_off[k], sp_off[k+1]) belong to species k
   // Adams-Bashforth push: history v^{n-1-j}, a^{n-1-j} per particle (device
   // order; the particles are not re-sorted), entries filled so far
@@ -269,18 +280,37 @@ inline int grid_for(int64_t work, int block, int cap) {
 #endif
 constexpr double kChebRatio = 100.0;
 
+// Chebyshev smoother on B^-1 A (order 2): degree (1 = block Jacobi alone),
+// power-iteration steps for its largest eigenvalue, the margin put on that
+// estimate (the power iteration approaches it from below) and the ratio of
+// the damped interval.  Each degree above 1 costs one FP32 A product per
+// iteration, run in a phase of the auxiliary Chebyshev steps.  Drift tube at
+// p = 2 (full size, live timing): block Jacobi with 4 auxiliary steps 173.8
+// iterations, 53.4 ms per solve; degree 2, 4 steps: 136.0, 48.6 ms; degree 3
+// with 6 auxiliary steps: 100.5, 47.7 ms.
+#ifndef FEMPIC_SMOOTH_DEG
+#define FEMPIC_SMOOTH_DEG 3
+#endif
+// auxiliary Chebyshev degree while the smoother is in use
+#ifndef FEMPIC_AUX_CHEB_SMOOTH
+#define FEMPIC_AUX_CHEB_SMOOTH 6
+#endif
+constexpr int kSmoothPower = 40;
+constexpr double kSmoothMargin = 1.1;
+constexpr double kSmoothRatio = 10.0;
+
 // Chebyshev iteration for a Jacobi-scaled SPD matrix whose scaled spectrum is
 // taken as [lmax / kChebRatio, lmax]: step 0 sets y = dinv f / theta; step i
 // sets d <- c1_i d + c2_i dinv (f - A y), y <- y + d.  Degree 1 (or no bound)
 // leaves the diagonal scaling y = dinv f.
-void cheb_coeffs(double lmax, int k, float (&c)[3][kMaxCheb]) {
+void cheb_coeffs(double lmax, int k, float (&c)[3][kMaxCheb], double ratio = kChebRatio) {
   for (auto& row : c)
     for (float& v : row) v = 0.f;
   if (k <= 1 || !(lmax > 0.0)) {
     c[0][0] = 1.f;
     return;
   }
-  const double lmin = lmax / kChebRatio, th = 0.5 * (lmax + lmin), de = 0.5 * (lmax - lmin);
+  const double lmin = lmax / ratio, th = 0.5 * (lmax + lmin), de = 0.5 * (lmax - lmin);
   const double sig = th / de;
   double rho = 1.0 / sig;
   c[0][0] = (float)(1.0 / th);
@@ -422,15 +452,21 @@ int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, 
   a.uf = h->aux_uf;
   a.ud = h->aux_ud;
   a.u2 = h->aux_u2;
-  a.cheb_k = nodal ? h->cheb_k : 1;
-  memcpy(a.chebL, imp ? h->chebLA : h->chebL, sizeof(a.chebL));
-  memcpy(a.chebV, h->chebV, sizeof(a.chebV));
+  // the smoother runs with cheb_k_sm auxiliary steps (its products share their phases)
+  const bool smooth = nodal && h->nb > 0 && h->pcg_fp32 && h->smooth_on;
+  a.cheb_k = !nodal ? 1 : smooth ? h->cheb_k_sm : h->cheb_k;
+  memcpy(a.chebL, imp ? (smooth ? h->chebLA_sm : h->chebLA) : (smooth ? h->chebL_sm : h->chebL), sizeof(a.chebL));
+  memcpy(a.chebV, smooth ? h->chebV_sm : h->chebV, sizeof(a.chebV));
   a.Bg = (nodal && h->Bg.nnz > 0) ? h->Bg.view() : CsrView{0, nullptr, nullptr, nullptr};
   a.Ab = (nodal && h->nb > 0) ? BsrView{h->nb, h->brp, h->bci, h->bA} : BsrView{0, nullptr, nullptr, nullptr};
   a.Ab32 = (nodal && h->nb > 0 && h->pcg_fp32) ? BsrView32{h->nb, h->brp, h->bci, h->bA32}
                                                : BsrView32{0, nullptr, nullptr, nullptr};
   a.p32 = h->cg_p32;
   a.repl = kPcgReplacePeriod;
+  a.smooth_k = (smooth && a.Ab32.nb > 0 && a.cheb_k >= h->smooth_k) ? h->smooth_k : 1;
+  a.chebS = h->chebS;
+  a.sy = h->sy;
+  a.sd = h->sd;
   a.q32 = h->cg_q32;
   a.r32 = h->cg_r32;
   a.red = h->cg_red;
@@ -460,6 +496,34 @@ int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, 
   else
     CK(cudaLaunchCooperativeKernel((void*)k_pcg<FEMPIC_LPR_P2>, blocks, FEMPIC_PCG_THREADS, args, 0, h->stream));
   h->launches++;
+  return FEMPIC_OK;
+}
+
+// Coefficients of the Chebyshev smoother for the current system, all on the
+// device: the largest eigenvalue of B^-1 A (B: A's 2x2 diagonal blocks) by
+// kSmoothPower steps of the power iteration from a hashed start vector, as
+// the Rayleigh quotient x.(A x) / x.(B x) of the last iterate (B x is the
+// A x_prev of the step before, since x = B^-1 (A x_prev)), then the
+// coefficients from it.  Uses the CG's scratch vectors; no host synchronisation.
+int smoother_coeffs(FemPIC* h) {
+  const int32_t n = 2 * h->nb;
+  const CsrView A = h->M.view(h->Aval);
+  double* x = h->cg_z;
+  double* yp = h->cg_q;
+  double* yc = h->cg_r;
+  const int g = grid_for(n, 256, h->num_sms * 8);
+  k_hash_vector<<<g, 256, 0, h->stream>>>(n, x);
+  int rc = 0;
+  for (int it = 0; it < kSmoothPower; ++it) {
+    if ((rc = spmv(h, A, x, yp))) return rc;
+    k_block_apply<<<g, 256, 0, h->stream>>>(h->nb, h->binv, yp, x);
+  }
+  if ((rc = spmv(h, A, x, yc))) return rc;
+  CK(cudaMemsetAsync(h->cg_red, 0, 2 * sizeof(double), h->stream));
+  k_dot2<<<g, 256, 0, h->stream>>>(n, x, yc, yp, h->cg_red);
+  k_smooth_coeffs<<<1, 32, 0, h->stream>>>(h->cg_red, h->smooth_k, kSmoothMargin, kSmoothRatio, h->chebS);
+  CK(cudaGetLastError());
+  h->launches += 2 * kSmoothPower + 3;
   return FEMPIC_OK;
 }
 
@@ -506,7 +570,9 @@ int form_system(FemPIC* h, double dt) {
   if (h->V.nnz > 0) {
     k_axpy_to_f32<<<grid_for(h->V.nnz, 256, 4096), 256, 0, h->stream>>>(h->V.nnz, h->V.v, h->VKv, c1, h->V32);
     h->launches++;
-    cheb_coeffs(gershgorin_scaled(h->hV_rp, h->hV_ci, h->hV_m.data(), h->hV_k.data(), c1), h->cheb_k, h->chebV);
+    const double lv = gershgorin_scaled(h->hV_rp, h->hV_ci, h->hV_m.data(), h->hV_k.data(), c1);
+    cheb_coeffs(lv, h->cheb_k, h->chebV);
+    cheb_coeffs(lv, h->cheb_k_sm, h->chebV_sm);
   }
   if (h->nb > 0) {
     k_form_blocks<<<grid_for(h->nb, 256, 1 << 30), 256, 0, h->stream>>>(h->nb, h->brp, h->bci, h->bM, h->bK, c1,
@@ -516,6 +582,11 @@ int form_system(FemPIC* h, double dt) {
       k_to_f32<<<grid_for(4 * h->nnzb, 256, 4096), 256, 0, h->stream>>>(4 * h->nnzb, h->bA, h->bA32);
       h->launches++;
     }
+  }
+  h->smooth_on = h->pcg_fp32 && h->smooth_k > 1 && h->sy;
+  if (h->smooth_on) {
+    int rc = smoother_coeffs(h);
+    if (rc) return rc;
   }
   if (h->Bg.nnz > 0) {
     k_group_inverse<<<grid_for(h->n_groups, 128, 1 << 30), 128, 0, h->stream>>>(
@@ -532,11 +603,14 @@ int form_system(FemPIC* h, double dt) {
     k_to_f32<<<grid_for(h->n0, 256, 4096), 256, 0, h->stream>>>(h->n0, h->dinvLA, h->dinvLA32);
     h->launches += 4;
     CK(cudaGetLastError());
-    if (h->cheb_k > 1)
-      cheb_coeffs(gershgorin_scaled(h->hLA_rp, h->hLA_ci, h->hLA_m.data(), h->hLA_i.data(), ci_imp), h->cheb_k,
-                  h->chebLA);
-    else
+    if (h->cheb_k > 1) {
+      const double la = gershgorin_scaled(h->hLA_rp, h->hLA_ci, h->hLA_m.data(), h->hLA_i.data(), ci_imp);
+      cheb_coeffs(la, h->cheb_k, h->chebLA);
+      cheb_coeffs(la, h->cheb_k_sm, h->chebLA_sm);
+    } else {
       cheb_coeffs(0.0, 1, h->chebLA);
+      cheb_coeffs(0.0, 1, h->chebLA_sm);
+    }
   }
   h->launches++;
   CK(cudaGetLastError());
@@ -1379,7 +1453,8 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
     h->hV_ci = hm.VM.col;
     h->hV_m = hm.VM.val;
     h->hV_k = hm.VK;
-    cheb_coeffs(gershgorin_scaled(hm.L.rowptr, hm.L.col, hm.L.val.data(), nullptr, 0.0), h->cheb_k, h->chebL);
+    h->lmaxL = gershgorin_scaled(hm.L.rowptr, hm.L.col, hm.L.val.data(), nullptr, 0.0);
+    cheb_coeffs(h->lmaxL, h->cheb_k, h->chebL);
   } else {
     cheb_coeffs(0.0, 1, h->chebL);
   }
@@ -1427,6 +1502,13 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
       if ((rc = upload(h, &h->brp, brp)) || (rc = upload(h, &h->bci, bci)) || (rc = upload(h, &h->bM, bM)) ||
           (rc = upload(h, &h->bK, bK)) || (rc = dalloc(h, &h->bA, bM.size())) || (rc = dalloc(h, &h->binv, 4 * (size_t)nb)) ||
           (FEMPIC_PCG_FP32A && (rc = dalloc(h, &h->bA32, bM.size()))))
+        return rc;
+      h->cheb_k_sm = h->cheb_k > 1 ? std::max(h->cheb_k, std::min(FEMPIC_AUX_CHEB_SMOOTH, kMaxCheb)) : 1;
+      h->smooth_k = std::max(1, std::min(FEMPIC_SMOOTH_DEG, h->cheb_k_sm));
+      cheb_coeffs(h->lmaxL, h->cheb_k_sm, h->chebL_sm);
+      if (FEMPIC_PCG_FP32A && h->smooth_k > 1 &&
+          ((rc = dalloc(h, &h->sy, 4 * (size_t)nb)) || (rc = dalloc(h, &h->sd, 2 * (size_t)nb)) ||
+           (rc = dalloc(h, &h->chebS, 3 * kMaxCheb))))
         return rc;
       if (imp && (rc = upload(h, &h->bI, bI))) return rc;
     }
@@ -1971,6 +2053,7 @@ int femPIC_get_info(const FemPIC* h, femPIC_info* info) {
   info->device_allocations = g_device_allocations.load(std::memory_order_relaxed);
   info->cg_fp32_products = h->pcg_fp32 ? 1 : 0;
   info->cg_replace_period = kPcgReplacePeriod;
+  info->cg_smooth_degree = h->smooth_on ? h->smooth_k : 1;
   info->nnz_A = h->M.nnz;
   info->nnz_C = h->C.nnz;
   info->nnz_Q = h->Q.nnz;
@@ -1981,7 +2064,7 @@ int femPIC_get_info(const FemPIC* h, femPIC_info* info) {
   info->device_bytes = h->bytes;
   info->nnz_L = h->L.nnz;
   info->nnz_V = h->V.nnz;
-  info->aux_cheb_degree = h->cheb_k;
+  info->aux_cheb_degree = h->smooth_on ? h->cheb_k_sm : h->cheb_k;
   info->n_species = h->n_species;
   info->n_impedance_faces = h->n_imp_faces;
   info->n_absorb_faces = h->n_absorb_faces;

@@ -36,6 +36,9 @@ struct BsrView32 {
   const float* v;
 };
 
+// largest Chebyshev degree of the preconditioner's polynomial parts
+constexpr int kMaxCheb = 8;
+
 // FP32 values: used for the preconditioner's auxiliary-space operators
 struct CsrView32 {
   int32_t n_rows;
@@ -43,6 +46,68 @@ struct CsrView32 {
   const int32_t* ci;
   const float* v;
 };
+
+// Power iteration for the largest eigenvalue of B^-1 A (B: the 2x2 diagonal
+// blocks of A, inverted in binv): a start vector from an integer hash
+// (SplitMix64 finaliser), x <- B^-1 y block by block, and the two dot
+// products of the Rayleigh quotient x.(A x) / x.(B x).
+__global__ void k_hash_vector(int32_t n, double* __restrict__ x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long z = (unsigned long long)i + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[i] = (double)(z >> 11) * 0x1.0p-52 - 1.0;
+  }
+}
+// Chebyshev coefficients of the smoother from the Rayleigh quotient rq[0] /
+// rq[1] (one thread): the interval [l / ratio, l] with l = margin * lambda, as
+// for the auxiliary problems; a quotient that is not positive and finite
+// leaves 1/theta = 1 and no further steps, i.e. the block Jacobi B^-1 r.
+__global__ void k_smooth_coeffs(const double* rq, int k, double margin, double ratio, float* c) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int i = 0; i < 3 * kMaxCheb; ++i) c[i] = 0.f;
+  const double lam = rq[1] > 0.0 ? rq[0] / rq[1] : 0.0;
+  if (!(lam > 0.0) || !isfinite(lam) || k <= 1) {
+    c[0] = 1.f;
+    return;
+  }
+  const double lmax = margin * lam, lmin = lmax / ratio, th = 0.5 * (lmax + lmin), de = 0.5 * (lmax - lmin);
+  const double sig = th / de;
+  double rho = 1.0 / sig;
+  c[0] = (float)(1.0 / th);
+  for (int i = 1; i < k && i < kMaxCheb; ++i) {
+    const double rn = 1.0 / (2.0 * sig - rho);
+    c[kMaxCheb + i] = (float)(rn * rho);
+    c[2 * kMaxCheb + i] = (float)(2.0 * rn / de);
+    rho = rn;
+  }
+}
+__global__ void k_block_apply(int32_t nb, const double* __restrict__ binv, const double* __restrict__ y,
+                              double* __restrict__ x) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += (int64_t)gridDim.x * blockDim.x) {
+    const double y0 = y[2 * k], y1 = y[2 * k + 1];
+    x[2 * k] = fma(binv[4 * k], y0, binv[4 * k + 1] * y1);
+    x[2 * k + 1] = fma(binv[4 * k + 2], y0, binv[4 * k + 3] * y1);
+  }
+}
+__global__ void k_dot2(int32_t n, const double* __restrict__ x, const double* __restrict__ y0,
+                       const double* __restrict__ y1, double* out) {
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    s0 = fma(x[i], y0[i], s0);
+    s1 = fma(x[i], y1[i], s1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(out, s0);
+    atomicAdd(out + 1, s1);
+  }
+}
 
 __global__ void k_to_f32(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -314,7 +379,6 @@ __device__ bool grid_sync(GridBarrier* bar, int32_t* status) {
   return ok != 0;
 }
 
-constexpr int kMaxCheb = 8;
 
 struct PcgArgs {
   CsrView A;
@@ -356,6 +420,17 @@ struct PcgArgs {
   BsrView32 Ab32;
   float* p32;
   int repl;
+  // Chebyshev smoother of degree smooth_k on B^-1 A in place of the block
+  // Jacobi term B^-1 r (order 2 with an FP32 copy of A; smooth_k = 1 keeps
+  // B^-1 r): y_1 = B^-1 r / theta, y_{i+1} = y_i + d_{i+1} with
+  // d_{i+1} = c1_i d_i + c2_i B^-1 (r - A y_i), the FP32 product A y_i run in
+  // the i-th further phase of the auxiliary Chebyshev steps (no barrier of its
+  // own); a fixed polynomial in B^-1 A times B^-1, so the preconditioner stays
+  // symmetric.  sy: [2][n] iterate (double-buffered), sd: [n] last step.
+  int smooth_k;
+  const float* chebS;  // [3 * kMaxCheb] on the device: [0] = 1/theta; [kMaxCheb + i], [2 kMaxCheb + i]: step i
+  float* sy;
+  float* sd;
   // order 3: inverses of A's diagonal blocks over the W1 DOFs of one edge, one
   // face and one tet interior, as a CSR (rows of a group hold its columns);
   // n_rows == 0 keeps the point Jacobi dinv
@@ -725,7 +800,9 @@ __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, co
     if (act && lane == 0) {
       double rr = __ldcg(rvec + i);
       double zz;
-      if (a.Ab.nb > 0) {
+      if (a.smooth_k > 1) {
+        zz = (double)__ldcg(a.sy + (size_t)((a.smooth_k - 1) & 1) * a.D.n_rows + i) + (double)s;
+      } else if (a.Ab.nb > 0) {
         const int k = i >> 1, par = i & 1;
         double r0 = __ldcg(rvec + 2 * k), r1 = __ldcg(rvec + 2 * k + 1);
         zz = fma(__ldg(a.binv + 4 * k + 2 * par), r0, fma(__ldg(a.binv + 4 * k + 2 * par + 1), r1, (double)s));
@@ -742,6 +819,19 @@ __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, co
     }
   });
   return rz;
+}
+
+// First iterate of the smoother for block k from the residual (r0, r1) of its
+// two rows: y_1 = d_1 = B_k^-1 r / theta.
+__device__ __forceinline__ void smooth_first(const PcgArgs& a, int k, double r0, double r1) {
+  const double* bi = a.binv + 4 * k;
+  const float th = __ldg(a.chebS);
+  const float y0 = th * (float)fma(__ldg(bi), r0, __ldg(bi + 1) * r1);
+  const float y1 = th * (float)fma(__ldg(bi + 2), r0, __ldg(bi + 3) * r1);
+  a.sy[2 * k] = y0;
+  a.sy[2 * k + 1] = y1;
+  a.sd[2 * k] = y0;
+  a.sd[2 * k + 1] = y1;
 }
 
 // Store the first Chebyshev iterate of the auxiliary problems from their
@@ -786,7 +876,7 @@ __device__ __forceinline__ void aux_first_u(const PcgArgs& a, int k, float f) {
 // barrier before each (the step gathers the whole previous iterate):
 //   d <- c1 d + c2 dinv (f - A y),  y <- y + d  (y double-buffered).
 // Returns the buffers holding the final iterates; false if a barrier timed out.
-__device__ bool aux_cheb(const PcgArgs& a, PcgSched& sc, const float*& tfin, const float*& ufin) {
+__device__ bool aux_cheb(const PcgArgs& a, PcgSched& sc, const double* rvec, const float*& tfin, const float*& ufin) {
   float* ty[2] = {a.t, a.t2};
   float* uy[2] = {a.u, a.u2};
   int cur = 0;
@@ -816,6 +906,23 @@ __device__ bool aux_cheb(const PcgArgs& a, PcgSched& sc, const float*& tfin, con
       };
       sc.run<FEMPIC_LPR_V>(a.V.n_rows, nullptr,
                            [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_V>(a.V, r, act, lane, xv, ev); });
+    }
+    if (i < a.smooth_k) {  // smoother step i + 1 on the same phase
+      const int n = a.Ab32.nb * 2;
+      const float* syc = a.sy + (size_t)((i - 1) & 1) * n;
+      float* syn = a.sy + (size_t)(i & 1) * n;
+      const float s1 = __ldg(a.chebS + kMaxCheb + i), s2 = __ldg(a.chebS + 2 * kMaxCheb + i);
+      auto es = [&](int k, float w0, float w1) {
+        const double g0 = __ldcg(rvec + 2 * k) - (double)w0, g1 = __ldcg(rvec + 2 * k + 1) - (double)w1;
+        const double* bi = a.binv + 4 * k;
+        const float d0 = fmaf(s1, __ldcg(a.sd + 2 * k), s2 * (float)fma(__ldg(bi), g0, __ldg(bi + 1) * g1));
+        const float d1 = fmaf(s1, __ldcg(a.sd + 2 * k + 1), s2 * (float)fma(__ldg(bi + 2), g0, __ldg(bi + 3) * g1));
+        a.sd[2 * k] = d0;
+        a.sd[2 * k + 1] = d1;
+        syn[2 * k] = __ldcg(syc + 2 * k) + d0;
+        syn[2 * k + 1] = __ldcg(syc + 2 * k + 1) + d1;
+      };
+      sc.run<4>(a.Ab32.nb, nullptr, [&](int k, bool act, int lane) { bspmv32_row<4>(a.Ab32, syc, k, act, lane, es); });
     }
     cur ^= 1;
   }
@@ -919,7 +1026,7 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
 #endif
   // ---- start: r = rhs - A x; z = M^-1 r
   double acc[3] = {0.0, 0.0, 0.0};  // r.z, r.r, rhs.rhs
-  auto start_row = [&](int r0, double s) {
+  auto start_row = [&](int r0, double s) -> double {
     double b = a.rhs[r0];
     double rr = b - s;
     r_cur[r0] = rr;
@@ -931,11 +1038,13 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
       a.z[r0] = zz;
       acc[0] += rr * zz;
     }
+    return rr;
   };
   if (a.Ab.nb > 0) {
     auto em = [&](int k, double s0, double s1) {
-      start_row(2 * k, s0);
-      start_row(2 * k + 1, s1);
+      const double r0 = start_row(2 * k, s0);
+      const double r1 = start_row(2 * k + 1, s1);
+      if (a.smooth_k > 1) smooth_first(a, k, r0, r1);
     };
     sc.run<LPR>(a.Ab.nb, apart, [&](int k, bool act, int lane) { bspmv_row<LPR>(a.Ab, a.x, k, act, lane, em); });
   } else {
@@ -952,7 +1061,7 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
       sc.run<FEMPIC_LPR_PIT>(a.PiT.n_rows, nullptr,
                  [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_PIT>(a.PiT, r, act, lane, x0, eu); });
     const float *tv, *uv;
-    if (!aux_cheb(a, sc, tv, uv)) return;
+    if (!aux_cheb(a, sc, r_cur, tv, uv)) return;
     if (!grid_sync(a.bar, a.status)) return;
     acc[0] += aux_z<FEMPIC_LPR_Z>(a, r_cur, tv, uv, sc);
   }
@@ -1055,11 +1164,12 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
         rq_alt[2 * k].x = (float)r0;
         rq_alt[2 * k + 1].x = (float)r1;
         acc2[1] += r0 * r0 + r1 * r1;
+        if (a.smooth_k > 1) smooth_first(a, k, r0, r1);
       };
       sc.run<LPR>(a.Ab.nb, apart, [&](int k, bool act, int lane) { bspmv_row<LPR>(a.Ab, a.x, k, act, lane, em); });
       if (!grid_sync(a.bar, a.status)) return;
     } else {
-      for (int i = gid; i < n; i += tpg) {
+      auto upd = [&](int i) -> double {
         a.x[i] = fma(alpha, __ldcg(pk_vec + i), __ldcg(a.x + i));
         const double qi = f32a ? (double)__ldcg(&rq_cur[i].y) : __ldcg(a.q + i);
         double rr = fma(-alpha, qi, __ldcg(r_old + i));
@@ -1071,6 +1181,16 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
           a.z[i] = zz;
           acc2[0] += rr * zz;
         }
+        return rr;
+      };
+      if (a.smooth_k > 1) {  // by blocks: the smoother's first iterate needs both rows
+        for (int k = gid; k < (n >> 1); k += tpg) {
+          const double r0 = upd(2 * k);
+          const double r1 = upd(2 * k + 1);
+          smooth_first(a, k, r0, r1);
+        }
+      } else {
+        for (int i = gid; i < n; i += tpg) upd(i);
       }
     }
     if (nodal) {
@@ -1090,7 +1210,7 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
                    [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_PIT>(a.PiT, r, act, lane, xr, eu); });
       PCG_MARK(5);
       const float *tv, *uv;
-      if (!aux_cheb(a, sc, tv, uv)) return;
+      if (!aux_cheb(a, sc, r_new, tv, uv)) return;
       PCG_MARK(8);
       if (!grid_sync(a.bar, a.status)) return;
       PCG_MARK(6);

@@ -72,7 +72,7 @@ class femPIC_info(ctypes.Structure):
                 ("n_species", ctypes.c_int32), ("n_impedance_faces", ctypes.c_int32),
                 ("n_absorb_faces", ctypes.c_int32), ("n_inject_faces", ctypes.c_int32),
                 ("device_allocations", ctypes.c_int64), ("cg_fp32_products", ctypes.c_int32),
-                ("cg_replace_period", ctypes.c_int32)]
+                ("cg_replace_period", ctypes.c_int32), ("cg_smooth_degree", ctypes.c_int32)]
 
 
 # (name, restype, argtypes) of every exported symbol declared in include/fempic.h

@@ -526,7 +526,9 @@ def test_get_into_caller_buffer(c1small):
 def test_field_solve_with_fp32_direction_products(order):
     """The drift tube at its 33.3 ps step, where at order 2 the CG's direction
     products run in FP32 (femPIC_info.cg_fp32_products) with the residual
-    recomputed in FP64 (orders 1 and 3: FP64 products): from a random field state the device's e^{n+1} satisfies the
+    recomputed in FP64 and the preconditioner smooths with a Chebyshev
+    polynomial in B^-1 A (orders 1 and 3: FP64 products, block or point
+    Jacobi): from a random field state the device's e^{n+1} satisfies the
     oracle's trapezoidal system, built from the device's own Delta g, to
     10 cg_rtol plus the rounding of the right-hand side's terms, and the
     solve reports convergence (its stopping test is on an FP64 residual)."""
@@ -547,7 +549,11 @@ def test_field_solve_with_fp32_direction_products(order):
     g.step(dt)
     # order 2 only: at order 3 the FP32 products raised the iteration count
     # (436 against 268 on the drift tube), so orders 1 and 3 keep FP64 ones
-    assert native.femPIC_get_info(g.h).cg_fp32_products == (1 if order == 2 else 0)
+    info = native.femPIC_get_info(g.h)
+    assert info.cg_fp32_products == (1 if order == 2 else 0)
+    # with the FP32 copy of A, a Chebyshev smoother on B^-1 A replaces the
+    # block-Jacobi term of the preconditioner
+    assert (info.cg_smooth_degree > 1) == (order == 2)
     d = g.diag()
     assert d["cg_residual"] <= 1e-12 and d["continuity_abs"] <= 1e-12 * d["continuity_ref"]
     A = ofields.system_matrix(o.M, o.K, dt, "trapezoid")

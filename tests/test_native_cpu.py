@@ -42,17 +42,19 @@ def test_exports_every_declared_symbol(native):
 def test_struct_layouts_match_c(native, tmp_path):
     prog = tmp_path / "sizes.c"
     prog.write_text('#include "fempic.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                    'int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(femPIC_mesh),'
+                    'int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(femPIC_mesh),'
                     ' sizeof(femPIC_species), sizeof(femPIC_opts), sizeof(femPIC_diag),'
                     ' sizeof(femPIC_info), offsetof(femPIC_opts, stream), offsetof(femPIC_info, device_bytes),'
-                    ' offsetof(femPIC_info, device_allocations));return 0;}\n')
+                    ' offsetof(femPIC_info, device_allocations), offsetof(femPIC_info, cg_smooth_degree));'
+                    'return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(native.femPIC_mesh), ctypes.sizeof(native.femPIC_species),
             ctypes.sizeof(native.femPIC_opts), ctypes.sizeof(native.femPIC_diag),
             ctypes.sizeof(native.femPIC_info), native.femPIC_opts.stream.offset,
-            native.femPIC_info.device_bytes.offset, native.femPIC_info.device_allocations.offset]
+            native.femPIC_info.device_bytes.offset, native.femPIC_info.device_allocations.offset,
+            native.femPIC_info.cg_smooth_degree.offset]
     assert got == want
 
 
