@@ -64,7 +64,8 @@ def pcg_bytes_per_iteration(info):
     V arrays plus five FP32 vector passes (right side, step and iterate read;
     step and iterate written).  With the Chebyshev smoother of degree ks on
     B^-1 A (cg_smooth_degree > 1): its first iterate (2x2 block inverse read,
-    iterate and step written) and ks - 1 more FP32 A products, each with the
+    iterate and step written) and ks - 1 more A products (bfloat16 values,
+    FP32 sums), each with the
     residual, the block inverse, the step (read and written), the iterate
     read and the next one written."""
     n1, n0 = info.n1, info.n0
@@ -83,7 +84,8 @@ def pcg_bytes_per_iteration(info):
         vec = 4 * n1 + 4 * n1 + (8 * 3 + 4 + 16) * n1 + (16 + 8 + 4) * n1
         repl = (a64 + (8 + 8 + 8 + 4) * n1) / max(1, int(info.cg_replace_period))
         ks = max(1, int(getattr(info, "cg_smooth_degree", 1)))
-        smooth = 0 if ks == 1 else (16 + 8) * n1 + (ks - 1) * (a32 + (8 + 16 + 8 + 4 + 4) * n1)
+        a16 = 2 * info.nnz_A + info.nnz_A  # bfloat16 values, a 4 B column per 2x2 block
+        smooth = 0 if ks == 1 else (16 + 8) * n1 + (ks - 1) * (a16 + (8 + 16 + 8 + 4 + 4) * n1)
         return a32 + mats + vec + aux + cheb + repl + smooth
     vec = 8 * (2 * n1 + 6 * n1 + n1 + 3 * n1)
     return a64 + mats + vec + aux + cheb

@@ -36,6 +36,23 @@ struct BsrView32 {
   const float* v;
 };
 
+// 2x2-block matrix with bfloat16 values (the upper 16 bits of the FP32
+// value, rounded to nearest even), four per block: the smoother's products
+struct BsrView16 {
+  int32_t nb;
+  const int32_t* rp;
+  const int32_t* ci;
+  const uint16_t* v;
+};
+
+// FP32 -> bfloat16 bits, rounded to nearest even (finite values)
+__global__ void k_to_bf16(int64_t n, const float* __restrict__ in, uint16_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t u = __float_as_uint(in[i]);
+    out[i] = (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+  }
+}
+
 // largest Chebyshev degree of the preconditioner's polynomial parts
 constexpr int kMaxCheb = 8;
 
@@ -425,9 +442,11 @@ struct PcgArgs {
   // B^-1 r): y_1 = B^-1 r / theta, y_{i+1} = y_i + d_{i+1} with
   // d_{i+1} = c1_i d_i + c2_i B^-1 (r - A y_i), the FP32 product A y_i run in
   // the i-th further phase of the auxiliary Chebyshev steps (no barrier of its
-  // own); a fixed polynomial in B^-1 A times B^-1, so the preconditioner stays
+  // own) with A's values rounded to bfloat16 (host study: the same iteration
+  // count as with FP64 values); a fixed polynomial in B^-1 A times B^-1, so the preconditioner stays
   // symmetric.  sy: [2][n] iterate (double-buffered), sd: [n] last step.
   int smooth_k;
+  BsrView16 As16;      // A with bfloat16 values for the smoother's products
   const float* chebS;  // [3 * kMaxCheb] on the device: [0] = 1/theta; [kMaxCheb + i], [2 kMaxCheb + i]: step i
   float* sy;
   float* sd;
@@ -637,6 +656,37 @@ __device__ __forceinline__ void bspmv32_row(const BsrView32& A, const float* x, 
       s0 = fmaf(a.x, xv.x, fmaf(a.y, xv.y, s0));
       s1 = fmaf(a.z, xv.x, fmaf(a.w, xv.y, s1));
     }
+  }
+#pragma unroll
+  for (int o = LPR / 2; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o, LPR);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o, LPR);
+  }
+  if (act && lane == 0) emit(k0, s0, s1);
+}
+
+// block row k0 of the bfloat16 2x2-block matrix times an FP32 vector, summed
+// in FP32 (as bspmv32_row; the four values of a block are one 8-byte load)
+template <int LPR, class F>
+__device__ __forceinline__ void bspmv16_row(const BsrView16& A, const float* x, int k0, bool act, int lane, F emit) {
+  const float2* x2 = reinterpret_cast<const float2*>(x);
+  const uint2* v2 = reinterpret_cast<const uint2*>(A.v);
+  float s0 = 0.f, s1 = 0.f;
+  auto acc = [&](const uint2 w, const float2 xv) {
+    s0 = fmaf(__uint_as_float(w.x << 16), xv.x, fmaf(__uint_as_float(w.x & 0xFFFF0000u), xv.y, s0));
+    s1 = fmaf(__uint_as_float(w.y << 16), xv.x, fmaf(__uint_as_float(w.y & 0xFFFF0000u), xv.y, s1));
+  };
+  if (act) {
+    const int beg = __ldg(A.rp + k0), end = __ldg(A.rp + k0 + 1);
+    int j = beg + lane;
+    for (; j + LPR < end; j += 2 * LPR) {
+      const int c0 = __ldg(A.ci + j), c1 = __ldg(A.ci + j + LPR);
+      const float2 x0 = __ldcg(x2 + c0), x1 = __ldcg(x2 + c1);
+      const uint2 a = __ldg(v2 + j), b = __ldg(v2 + j + LPR);
+      acc(a, x0);
+      acc(b, x1);
+    }
+    if (j < end) acc(__ldg(v2 + j), __ldcg(x2 + __ldg(A.ci + j)));
   }
 #pragma unroll
   for (int o = LPR / 2; o > 0; o >>= 1) {
@@ -908,7 +958,7 @@ __device__ bool aux_cheb(const PcgArgs& a, PcgSched& sc, const double* rvec, con
                            [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_V>(a.V, r, act, lane, xv, ev); });
     }
     if (i < a.smooth_k) {  // smoother step i + 1 on the same phase
-      const int n = a.Ab32.nb * 2;
+      const int n = a.As16.nb * 2;
       const float* syc = a.sy + (size_t)((i - 1) & 1) * n;
       float* syn = a.sy + (size_t)(i & 1) * n;
       const float s1 = __ldg(a.chebS + kMaxCheb + i), s2 = __ldg(a.chebS + 2 * kMaxCheb + i);
@@ -922,7 +972,7 @@ __device__ bool aux_cheb(const PcgArgs& a, PcgSched& sc, const double* rvec, con
         syn[2 * k] = __ldcg(syc + 2 * k) + d0;
         syn[2 * k + 1] = __ldcg(syc + 2 * k + 1) + d1;
       };
-      sc.run<4>(a.Ab32.nb, nullptr, [&](int k, bool act, int lane) { bspmv32_row<4>(a.Ab32, syc, k, act, lane, es); });
+      sc.run<4>(a.As16.nb, nullptr, [&](int k, bool act, int lane) { bspmv16_row<4>(a.As16, syc, k, act, lane, es); });
     }
     cur ^= 1;
   }
