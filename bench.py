@@ -367,7 +367,8 @@ def run_native(args, rank, world, local_rank):
             # counters taken on an earlier build of k_pcg are not carried over
             tj = json.load(open(prof))
             if (tj.get("aux_cheb_degree", 1) != info.aux_cheb_degree
-                    or tj.get("cg_fp32_products", 0) != getattr(info, "cg_fp32_products", 0)):
+                    or tj.get("cg_fp32_products", 0) != getattr(info, "cg_fp32_products", 0)
+                    or tj.get("cg_smooth_degree", 1) != getattr(info, "cg_smooth_degree", 1)):
                 per_it = None
             traffic = per_it * (iters + 1.0) if per_it else None
         except (OSError, ValueError):
