@@ -98,6 +98,7 @@ struct FemPIC {
   bool smooth_on = false;
   float* chebS = nullptr;  // [3 * kMaxCheb] coefficients, written on the device
   uint16_t* bA16 = nullptr;  // bfloat16 copy of bA for the smoother's products
+  float* binv32 = nullptr;   // FP32 copy of binv for the smoother
   float *sy = nullptr, *sd = nullptr;
   double kdiag_med = 0.0;  // median over W1 rows of K_ii / M_ii: the coefficient of K in A
                            // times it is the typical ratio of the curl-curl to the mass term
@@ -467,6 +468,7 @@ int run_pcg(FemPIC* h, const CsrView& A, const double* dinv, const double* rhs, 
   a.smooth_k = (smooth && a.Ab32.nb > 0 && a.cheb_k >= h->smooth_k) ? h->smooth_k : 1;
   a.chebS = h->chebS;
   a.As16 = a.smooth_k > 1 ? BsrView16{h->nb, h->brp, h->bci, h->bA16} : BsrView16{0, nullptr, nullptr, nullptr};
+  a.binv32 = h->binv32;
   a.sy = h->sy;
   a.sd = h->sd;
   a.q32 = h->cg_q32;
@@ -588,7 +590,8 @@ int form_system(FemPIC* h, double dt) {
   h->smooth_on = h->pcg_fp32 && h->smooth_k > 1 && h->sy;
   if (h->smooth_on) {
     k_to_bf16<<<grid_for(4 * h->nnzb, 256, 4096), 256, 0, h->stream>>>(4 * h->nnzb, h->bA32, h->bA16);
-    h->launches++;
+    k_to_f32<<<grid_for(4 * h->nb, 256, 4096), 256, 0, h->stream>>>(4 * h->nb, h->binv, h->binv32);
+    h->launches += 2;
     int rc = smoother_coeffs(h);
     if (rc) return rc;
   }
@@ -1512,7 +1515,8 @@ int create_impl(const femPIC_mesh* mesh, int32_t order, const femPIC_species* sp
       cheb_coeffs(h->lmaxL, h->cheb_k_sm, h->chebL_sm);
       if (FEMPIC_PCG_FP32A && h->smooth_k > 1 &&
           ((rc = dalloc(h, &h->sy, 4 * (size_t)nb)) || (rc = dalloc(h, &h->sd, 2 * (size_t)nb)) ||
-           (rc = dalloc(h, &h->chebS, 3 * kMaxCheb)) || (rc = dalloc(h, &h->bA16, bM.size()))))
+           (rc = dalloc(h, &h->chebS, 3 * kMaxCheb)) || (rc = dalloc(h, &h->bA16, bM.size())) ||
+           (rc = dalloc(h, &h->binv32, 4 * (size_t)nb))))
         return rc;
       if (imp && (rc = upload(h, &h->bI, bI))) return rc;
     }

@@ -447,6 +447,7 @@ struct PcgArgs {
   // symmetric.  sy: [2][n] iterate (double-buffered), sd: [n] last step.
   int smooth_k;
   BsrView16 As16;      // A with bfloat16 values for the smoother's products
+  const float* binv32; // FP32 copy of binv (the smoother runs in FP32 throughout)
   const float* chebS;  // [3 * kMaxCheb] on the device: [0] = 1/theta; [kMaxCheb + i], [2 kMaxCheb + i]: step i
   float* sy;
   float* sd;
@@ -851,7 +852,7 @@ __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, co
       double rr = __ldcg(rvec + i);
       double zz;
       if (a.smooth_k > 1) {
-        zz = (double)__ldcg(a.sy + (size_t)((a.smooth_k - 1) & 1) * a.D.n_rows + i) + (double)s;
+        zz = (double)(__ldcg(a.sy + (size_t)((a.smooth_k - 1) & 1) * a.D.n_rows + i) + s);
       } else if (a.Ab.nb > 0) {
         const int k = i >> 1, par = i & 1;
         double r0 = __ldcg(rvec + 2 * k), r1 = __ldcg(rvec + 2 * k + 1);
@@ -871,13 +872,13 @@ __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, co
   return rz;
 }
 
-// First iterate of the smoother for block k from the residual (r0, r1) of its
-// two rows: y_1 = d_1 = B_k^-1 r / theta.
-__device__ __forceinline__ void smooth_first(const PcgArgs& a, int k, double r0, double r1) {
-  const double* bi = a.binv + 4 * k;
+// First iterate of the smoother for block k from the FP32 residual (r0, r1)
+// of its two rows: y_1 = d_1 = B_k^-1 r / theta.
+__device__ __forceinline__ void smooth_first(const PcgArgs& a, int k, float r0, float r1) {
+  const float4 bi = __ldg(reinterpret_cast<const float4*>(a.binv32) + k);
   const float th = __ldg(a.chebS);
-  const float y0 = th * (float)fma(__ldg(bi), r0, __ldg(bi + 1) * r1);
-  const float y1 = th * (float)fma(__ldg(bi + 2), r0, __ldg(bi + 3) * r1);
+  const float y0 = th * fmaf(bi.x, r0, bi.y * r1);
+  const float y1 = th * fmaf(bi.z, r0, bi.w * r1);
   a.sy[2 * k] = y0;
   a.sy[2 * k + 1] = y1;
   a.sd[2 * k] = y0;
@@ -926,7 +927,7 @@ __device__ __forceinline__ void aux_first_u(const PcgArgs& a, int k, float f) {
 // barrier before each (the step gathers the whole previous iterate):
 //   d <- c1 d + c2 dinv (f - A y),  y <- y + d  (y double-buffered).
 // Returns the buffers holding the final iterates; false if a barrier timed out.
-__device__ bool aux_cheb(const PcgArgs& a, PcgSched& sc, const double* rvec, const float*& tfin, const float*& ufin) {
+__device__ bool aux_cheb(const PcgArgs& a, PcgSched& sc, const float2* rqs, const float*& tfin, const float*& ufin) {
   float* ty[2] = {a.t, a.t2};
   float* uy[2] = {a.u, a.u2};
   int cur = 0;
@@ -963,10 +964,10 @@ __device__ bool aux_cheb(const PcgArgs& a, PcgSched& sc, const double* rvec, con
       float* syn = a.sy + (size_t)(i & 1) * n;
       const float s1 = __ldg(a.chebS + kMaxCheb + i), s2 = __ldg(a.chebS + 2 * kMaxCheb + i);
       auto es = [&](int k, float w0, float w1) {
-        const double g0 = __ldcg(rvec + 2 * k) - (double)w0, g1 = __ldcg(rvec + 2 * k + 1) - (double)w1;
-        const double* bi = a.binv + 4 * k;
-        const float d0 = fmaf(s1, __ldcg(a.sd + 2 * k), s2 * (float)fma(__ldg(bi), g0, __ldg(bi + 1) * g1));
-        const float d1 = fmaf(s1, __ldcg(a.sd + 2 * k + 1), s2 * (float)fma(__ldg(bi + 2), g0, __ldg(bi + 3) * g1));
+        const float g0 = __ldcg(&rqs[2 * k].x) - w0, g1 = __ldcg(&rqs[2 * k + 1].x) - w1;
+        const float4 bi = __ldg(reinterpret_cast<const float4*>(a.binv32) + k);
+        const float d0 = fmaf(s1, __ldcg(a.sd + 2 * k), s2 * fmaf(bi.x, g0, bi.y * g1));
+        const float d1 = fmaf(s1, __ldcg(a.sd + 2 * k + 1), s2 * fmaf(bi.z, g0, bi.w * g1));
         a.sd[2 * k] = d0;
         a.sd[2 * k + 1] = d1;
         syn[2 * k] = __ldcg(syc + 2 * k) + d0;
@@ -1076,11 +1077,12 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
 #endif
   // ---- start: r = rhs - A x; z = M^-1 r
   double acc[3] = {0.0, 0.0, 0.0};  // r.z, r.r, rhs.rhs
-  auto start_row = [&](int r0, double s) -> double {
+  auto start_row = [&](int r0, double s) -> float {
     double b = a.rhs[r0];
     double rr = b - s;
     r_cur[r0] = rr;
-    if (nodal) rq_cur[r0].x = (float)rr;
+    const float rf = (float)rr;
+    if (nodal) rq_cur[r0].x = rf;
     acc[1] += rr * rr;
     acc[2] += b * b;
     if (!nodal) {
@@ -1088,12 +1090,12 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
       a.z[r0] = zz;
       acc[0] += rr * zz;
     }
-    return rr;
+    return rf;
   };
   if (a.Ab.nb > 0) {
     auto em = [&](int k, double s0, double s1) {
-      const double r0 = start_row(2 * k, s0);
-      const double r1 = start_row(2 * k + 1, s1);
+      const float r0 = start_row(2 * k, s0);
+      const float r1 = start_row(2 * k + 1, s1);
       if (a.smooth_k > 1) smooth_first(a, k, r0, r1);
     };
     sc.run<LPR>(a.Ab.nb, apart, [&](int k, bool act, int lane) { bspmv_row<LPR>(a.Ab, a.x, k, act, lane, em); });
@@ -1111,7 +1113,7 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
       sc.run<FEMPIC_LPR_PIT>(a.PiT.n_rows, nullptr,
                  [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_PIT>(a.PiT, r, act, lane, x0, eu); });
     const float *tv, *uv;
-    if (!aux_cheb(a, sc, r_cur, tv, uv)) return;
+    if (!aux_cheb(a, sc, rq_cur, tv, uv)) return;
     if (!grid_sync(a.bar, a.status)) return;
     acc[0] += aux_z<FEMPIC_LPR_Z>(a, r_cur, tv, uv, sc);
   }
@@ -1211,32 +1213,34 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
         const double r0 = a.rhs[2 * k] - s0, r1 = a.rhs[2 * k + 1] - s1;
         r_new[2 * k] = r0;
         r_new[2 * k + 1] = r1;
-        rq_alt[2 * k].x = (float)r0;
-        rq_alt[2 * k + 1].x = (float)r1;
+        const float r0f = (float)r0, r1f = (float)r1;
+        rq_alt[2 * k].x = r0f;
+        rq_alt[2 * k + 1].x = r1f;
         acc2[1] += r0 * r0 + r1 * r1;
-        if (a.smooth_k > 1) smooth_first(a, k, r0, r1);
+        if (a.smooth_k > 1) smooth_first(a, k, r0f, r1f);
       };
       sc.run<LPR>(a.Ab.nb, apart, [&](int k, bool act, int lane) { bspmv_row<LPR>(a.Ab, a.x, k, act, lane, em); });
       if (!grid_sync(a.bar, a.status)) return;
     } else {
-      auto upd = [&](int i) -> double {
+      auto upd = [&](int i) -> float {
         a.x[i] = fma(alpha, __ldcg(pk_vec + i), __ldcg(a.x + i));
         const double qi = f32a ? (double)__ldcg(&rq_cur[i].y) : __ldcg(a.q + i);
         double rr = fma(-alpha, qi, __ldcg(r_old + i));
         r_new[i] = rr;
-        if (nodal) rq_alt[i].x = (float)rr;
+        const float rf = (float)rr;
+        if (nodal) rq_alt[i].x = rf;
         acc2[1] += rr * rr;
         if (!nodal) {
           double zz = a.dinv[i] * rr;
           a.z[i] = zz;
           acc2[0] += rr * zz;
         }
-        return rr;
+        return rf;
       };
       if (a.smooth_k > 1) {  // by blocks: the smoother's first iterate needs both rows
         for (int k = gid; k < (n >> 1); k += tpg) {
-          const double r0 = upd(2 * k);
-          const double r1 = upd(2 * k + 1);
+          const float r0 = upd(2 * k);
+          const float r1 = upd(2 * k + 1);
           smooth_first(a, k, r0, r1);
         }
       } else {
@@ -1260,7 +1264,7 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
                    [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_PIT>(a.PiT, r, act, lane, xr, eu); });
       PCG_MARK(5);
       const float *tv, *uv;
-      if (!aux_cheb(a, sc, r_new, tv, uv)) return;
+      if (!aux_cheb(a, sc, rq_alt, tv, uv)) return;
       PCG_MARK(8);
       if (!grid_sync(a.bar, a.status)) return;
       PCG_MARK(6);
