@@ -285,17 +285,21 @@ constexpr double kChebRatio = 100.0;
 // Chebyshev smoother on B^-1 A (order 2): degree (1 = block Jacobi alone),
 // power-iteration steps for its largest eigenvalue, the margin put on that
 // estimate (the power iteration approaches it from below) and the ratio of
-// the damped interval.  Each degree above 1 costs one FP32 A product per
-// iteration, run in a phase of the auxiliary Chebyshev steps.  Drift tube at
-// p = 2 (full size, live timing): block Jacobi with 4 auxiliary steps 173.8
-// iterations, 53.4 ms per solve; degree 2, 4 steps: 136.0, 48.6 ms; degree 3
-// with 6 auxiliary steps: 100.5, 47.7 ms.
+// the damped interval.  Each degree above 1 costs one A product per
+// iteration (bfloat16 values), run in a phase of the auxiliary Chebyshev
+// steps.  The degree is odd: the smoother's polynomial p(lambda) then stays
+// positive for every lambda > 0, beyond the damped interval too, so the
+// preconditioner is positive definite whatever the eigenvalue estimate (at
+// even degrees p turns negative just above the interval).  Drift tube at
+// p = 2 (full size, live timing, ms per step): block Jacobi with 4 auxiliary
+// steps 55.3 (173.8 iterations); degree 3, 6 steps 46.1 (100.5); degree 5,
+// 8 steps 45.0 (73.5); degree 4, 8 steps 45.0 (79.5).
 #ifndef FEMPIC_SMOOTH_DEG
-#define FEMPIC_SMOOTH_DEG 3
+#define FEMPIC_SMOOTH_DEG 5
 #endif
 // auxiliary Chebyshev degree while the smoother is in use
 #ifndef FEMPIC_AUX_CHEB_SMOOTH
-#define FEMPIC_AUX_CHEB_SMOOTH 6
+#define FEMPIC_AUX_CHEB_SMOOTH 8
 #endif
 constexpr int kSmoothPower = 40;
 constexpr double kSmoothMargin = 1.1;

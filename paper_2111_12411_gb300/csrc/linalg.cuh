@@ -1299,6 +1299,13 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
       conv = rnorm <= thresh;
     }
     beta = rz != 0.0 ? t2[0] / rz : 0.0;
+    // A replaced residual can carry far more in the preconditioner's norm than
+    // the recursive one did (the FP32 products' rounding in the near-kernel
+    // directions the auxiliary spaces amplify), and beta > 1 formed from it no
+    // longer continues the conjugate directions: restart from z (on a
+    // 3 x 3 x 3 cavity box at p = 2 the CG otherwise stalled near 1e-6; on the
+    // drift tube the iteration count is unchanged, host emulation)
+    if (replace && beta > 1.0) beta = 0.0;
     rz = t2[0];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
