@@ -253,8 +253,8 @@ typedef struct {
   int32_t cg_replace_period;
   int32_t cg_smooth_degree; /* degree of the Chebyshev smoother on B^-1 A that
                                replaces the block-Jacobi term of the CG
-                               preconditioner (1: block Jacobi; > 1 only with
-                               FP32 direction products, order 2)              */
+                               preconditioner (1: block Jacobi; > 1 at order 2,
+                               whose 2x2 blocks it works on)                  */
 } femPIC_info;
 
 /* Fill *opts with defaults: FP64, trapezoid, cg_rtol 1e-12, cg_max_it 2000,
