@@ -732,6 +732,21 @@ __device__ __forceinline__ void spmv32_row(const CsrView32& A, int r0, bool act,
   if (act && lane == 0) emit(r0, s);
 }
 
+// As spmv32_row, with the row's epilogue operands loaded before its entries:
+// pre(r0) (lane 0 of the row's group) returns them and emit(r0, sum, pre
+// values) uses them, so their loads overlap the row's index -> vector loads
+// instead of following the reduction.
+#ifndef FEMPIC_CHEB_PREFETCH
+#define FEMPIC_CHEB_PREFETCH 1
+#endif
+template <int LPR, class X, class P, class F>
+__device__ __forceinline__ void spmv32_row_pre(const CsrView32& A, int r0, bool act, int lane, X x_of, P pre,
+                                               F emit) {
+  decltype(pre(0)) pv{};
+  if (act && lane == 0) pv = pre(r0);
+  spmv32_row<LPR>(A, r0, act, lane, x_of, [&](int r, float s) { emit(r, s, pv); });
+}
+
 // static driver: the groups of the grid stride through rows [0, n)
 template <int LPR, class Body>
 __device__ __forceinline__ void rows_static(int n, int gid, int groups, Body body) {
@@ -938,6 +953,17 @@ __device__ bool aux_cheb(const PcgArgs& a, PcgSched& sc, const float2* rqs, cons
     float* yn = ty[cur ^ 1];
     const float c1 = a.chebL[1][i], c2 = a.chebL[2][i];
     auto xl = [&](int c) { return __ldcg(yc + c); };
+#if FEMPIC_CHEB_PREFETCH
+    auto pl = [&](int k) { return make_float4(__ldcg(a.td + k), __ldcg(a.tf + k), __ldg(a.dinvL + k), __ldcg(yc + k)); };
+    auto elp = [&](int k, float s, float4 p) {
+      const float d = fmaf(c1, p.x, c2 * p.z * (p.y - s));
+      a.td[k] = d;
+      yn[k] = p.w + d;
+    };
+    sc.run<FEMPIC_LPR_L>(a.L.n_rows, nullptr, [&](int r, bool act, int lane) {
+      spmv32_row_pre<FEMPIC_LPR_L>(a.L, r, act, lane, xl, pl, elp);
+    });
+#else
     auto el = [&](int k, float s) {
       const float d = fmaf(c1, __ldcg(a.td + k), c2 * __ldg(a.dinvL + k) * (__ldcg(a.tf + k) - s));
       a.td[k] = d;
@@ -945,11 +971,23 @@ __device__ bool aux_cheb(const PcgArgs& a, PcgSched& sc, const float2* rqs, cons
     };
     sc.run<FEMPIC_LPR_L>(a.L.n_rows, nullptr,
                          [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_L>(a.L, r, act, lane, xl, el); });
+#endif
     if (vec) {
       const float* vc = uy[cur];
       float* vn = uy[cur ^ 1];
       const float e1 = a.chebV[1][i], e2 = a.chebV[2][i];
       auto xv = [&](int c) { return __ldcg(vc + c); };
+#if FEMPIC_CHEB_PREFETCH
+      auto pv = [&](int k) { return make_float4(__ldcg(a.ud + k), __ldcg(a.uf + k), __ldg(a.dinvV + k), __ldcg(vc + k)); };
+      auto evp = [&](int k, float s, float4 p) {
+        const float d = fmaf(e1, p.x, e2 * p.z * (p.y - s));
+        a.ud[k] = d;
+        vn[k] = p.w + d;
+      };
+      sc.run<FEMPIC_LPR_V>(a.V.n_rows, nullptr, [&](int r, bool act, int lane) {
+        spmv32_row_pre<FEMPIC_LPR_V>(a.V, r, act, lane, xv, pv, evp);
+      });
+#else
       auto ev = [&](int k, float s) {
         const float d = fmaf(e1, __ldcg(a.ud + k), e2 * __ldg(a.dinvV + k) * (__ldcg(a.uf + k) - s));
         a.ud[k] = d;
@@ -957,6 +995,7 @@ __device__ bool aux_cheb(const PcgArgs& a, PcgSched& sc, const float2* rqs, cons
       };
       sc.run<FEMPIC_LPR_V>(a.V.n_rows, nullptr,
                            [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_V>(a.V, r, act, lane, xv, ev); });
+#endif
     }
     if (i < a.smooth_k) {  // smoother step i + 1 on the same phase
       const int n = a.As16.nb * 2;
