@@ -739,6 +739,12 @@ __device__ __forceinline__ void spmv32_row(const CsrView32& A, int r0, bool act,
 #ifndef FEMPIC_CHEB_PREFETCH
 #define FEMPIC_CHEB_PREFETCH 1
 #endif
+#ifndef FEMPIC_RESTRICT_PREFETCH
+#define FEMPIC_RESTRICT_PREFETCH 1
+#endif
+#ifndef FEMPIC_APROD_PREFETCH
+#define FEMPIC_APROD_PREFETCH 1
+#endif
 template <int LPR, class X, class P, class F>
 __device__ __forceinline__ void spmv32_row_pre(const CsrView32& A, int r0, bool act, int lane, X x_of, P pre,
                                                F emit) {
@@ -831,6 +837,9 @@ struct PcgSched {
 #ifndef FEMPIC_AUXZ_FUSED
 #define FEMPIC_AUXZ_FUSED 1
 #endif
+#ifndef FEMPIC_AUXZ_PREFETCH
+#define FEMPIC_AUXZ_PREFETCH 1
+#endif
 template <int LPR>
 __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, const float* tv, const float* uv,
                                         PcgSched& sc) {
@@ -838,6 +847,13 @@ __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, co
   double rz = 0.0;
   sc.run<LPR>(a.D.n_rows, nullptr, [&](int i, bool act, int lane) {
     float s = 0.f;
+    // the row's residual and smoother value, loaded ahead of its products
+    double rr_pre = 0.0;
+    float sy_pre = 0.f;
+    if (FEMPIC_AUXZ_PREFETCH && act && lane == 0) {
+      rr_pre = __ldcg(rvec + i);
+      if (a.smooth_k > 1) sy_pre = __ldcg(a.sy + (size_t)((a.smooth_k - 1) & 1) * a.D.n_rows + i);
+    }
     if (act) {
       if (FEMPIC_AUXZ_FUSED) {
         const int db = __ldg(a.D.rp + i), de = __ldg(a.D.rp + i + 1);
@@ -864,10 +880,10 @@ __device__ __forceinline__ double aux_z(const PcgArgs& a, const double* rvec, co
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
     if (act && lane == 0) {
-      double rr = __ldcg(rvec + i);
+      double rr = FEMPIC_AUXZ_PREFETCH ? rr_pre : __ldcg(rvec + i);
       double zz;
       if (a.smooth_k > 1) {
-        zz = (double)(__ldcg(a.sy + (size_t)((a.smooth_k - 1) & 1) * a.D.n_rows + i) + s);
+        zz = (double)((FEMPIC_AUXZ_PREFETCH ? sy_pre : __ldcg(a.sy + (size_t)((a.smooth_k - 1) & 1) * a.D.n_rows + i)) + s);
       } else if (a.Ab.nb > 0) {
         const int k = i >> 1, par = i & 1;
         double r0 = __ldcg(rvec + 2 * k), r1 = __ldcg(rvec + 2 * k + 1);
@@ -901,7 +917,24 @@ __device__ __forceinline__ void smooth_first(const PcgArgs& a, int k, float r0, 
 }
 
 // Store the first Chebyshev iterate of the auxiliary problems from their
-// right-hand sides f = (D^T r)_k or (Pi^T r)_k.
+// right-hand sides f = (D^T r)_k or (Pi^T r)_k (the _d forms take the row's
+// Jacobi scaling already loaded).
+__device__ __forceinline__ void aux_first_t_d(const PcgArgs& a, int k, float f, float dl) {
+  const float y = a.chebL[0][0] * dl * f;
+  a.t[k] = y;
+  if (a.cheb_k > 1) {
+    a.tf[k] = f;
+    a.td[k] = y;
+  }
+}
+__device__ __forceinline__ void aux_first_u_d(const PcgArgs& a, int k, float f, float dv) {
+  const float y = a.chebV[0][0] * dv * f;
+  a.u[k] = y;
+  if (a.cheb_k > 1) {
+    a.uf[k] = f;
+    a.ud[k] = y;
+  }
+}
 __device__ __forceinline__ void aux_first_t(const PcgArgs& a, int k, float f) {
   const float y = a.chebL[0][0] * __ldg(a.dinvL + k) * f;
   a.t[k] = y;
@@ -1199,6 +1232,20 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
     double acc1[1] = {0.0};
     PCG_STAMP(0, it);
     if (f32a) {
+#if FEMPIC_APROD_PREFETCH
+      // the block row's direction values (for p.q) loaded ahead of the product
+      auto pp = [&](int k) { return __ldcg(reinterpret_cast<const double2*>(pk_vec) + k); };
+      auto emp = [&](int k, float s0, float s1, double2 pv) {
+        rq_cur[2 * k].y = s0;
+        rq_cur[2 * k + 1].y = s1;
+        acc1[0] += pv.x * (double)s0 + pv.y * (double)s1;
+      };
+      sc.run<LPR>(a.Ab32.nb, apart, [&](int k, bool act, int lane) {
+        double2 pv{0.0, 0.0};
+        if (act && lane == 0) pv = pp(k);
+        bspmv32_row<LPR>(a.Ab32, a.p32, k, act, lane, [&](int kk, float s0, float s1) { emp(kk, s0, s1, pv); });
+      });
+#else
       auto em = [&](int k, float s0, float s1) {
         rq_cur[2 * k].y = s0;
         rq_cur[2 * k + 1].y = s1;
@@ -1206,6 +1253,7 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
       };
       sc.run<LPR>(a.Ab32.nb, apart,
                   [&](int k, bool act, int lane) { bspmv32_row<LPR>(a.Ab32, a.p32, k, act, lane, em); });
+#endif
     } else if (a.Ab.nb > 0) {
       auto em = [&](int k, double s0, double s1) {
         a.q[2 * k] = s0;
@@ -1295,12 +1343,27 @@ __global__ void __launch_bounds__(FEMPIC_PCG_THREADS, FEMPIC_PCG_MIN_BLOCKS) k_p
         const float2 v = __ldcg(rqo + c);
         return fmaf(-alpha32, v.y, v.x);
       };
+#if FEMPIC_RESTRICT_PREFETCH
+      // the rows' Jacobi scalings loaded ahead of their products
+      auto pt = [&](int k) { return __ldg(a.dinvL + k); };
+      auto pu = [&](int k) { return __ldg(a.dinvV + k); };
+      auto et = [&](int k, float s, float dl) { aux_first_t_d(a, k, s, dl); };
+      auto eu = [&](int k, float s, float dv) { aux_first_u_d(a, k, s, dv); };
+      sc.run<FEMPIC_LPR_DT>(a.DT.n_rows, nullptr, [&](int r, bool act, int lane) {
+        spmv32_row_pre<FEMPIC_LPR_DT>(a.DT, r, act, lane, xr, pt, et);
+      });
+      if (a.PiT.n_rows > 0)
+        sc.run<FEMPIC_LPR_PIT>(a.PiT.n_rows, nullptr, [&](int r, bool act, int lane) {
+          spmv32_row_pre<FEMPIC_LPR_PIT>(a.PiT, r, act, lane, xr, pu, eu);
+        });
+#else
       auto et = [&](int k, float s) { aux_first_t(a, k, s); };
       auto eu = [&](int k, float s) { aux_first_u(a, k, s); };
       sc.run<FEMPIC_LPR_DT>(a.DT.n_rows, nullptr, [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_DT>(a.DT, r, act, lane, xr, et); });
       if (a.PiT.n_rows > 0)
         sc.run<FEMPIC_LPR_PIT>(a.PiT.n_rows, nullptr,
                    [&](int r, bool act, int lane) { spmv32_row<FEMPIC_LPR_PIT>(a.PiT, r, act, lane, xr, eu); });
+#endif
       PCG_MARK(5);
       const float *tv, *uv;
       if (!aux_cheb(a, sc, rq_alt, tv, uv)) return;
