@@ -25,6 +25,9 @@
 #ifndef FEMPIC_PARTICLE_AGG
 #define FEMPIC_PARTICLE_AGG 0
 #endif
+#ifndef FEMPIC_DEPOSIT_SCALED
+#define FEMPIC_DEPOSIT_SCALED 1
+#endif
 
 namespace fempic {
 namespace dev {
@@ -157,11 +160,24 @@ __device__ __forceinline__ void deposit_fact(const double* la, const double* lb,
   for (int i = 0; i < 4; ++i) d[i] = lb[i] - la[i];
   const double sc = qw * (s1 - s0);
   double w[6];
+#if FEMPIC_DEPOSIT_SCALED
+  // the sub-segment's weight folded into the direction once (4 products
+  // instead of one per edge pair)
+  double ds[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) ds[i] = sc * d[i];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const int s = edge_s(j), t = edge_t(j);
+    w[j] = fma(la[s], ds[t], -la[t] * ds[s]);
+  }
+#else
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     const int s = edge_s(j), t = edge_t(j);
     w[j] = sc * fma(la[s], d[t], -la[t] * d[s]);
   }
+#endif
   if (P == 1) {
 #pragma unroll
     for (int j = 0; j < 6; ++j) run_add(dg + __ldg(dofs + j), w[j], agg, runs, lane, valid);
@@ -294,9 +310,32 @@ __device__ __forceinline__ void boris_f32(float* v, const float* E, const float*
   v[2] = vm[2] + (vp[0] * sv[1] - vp[1] * sv[0]) + eh[2];
 }
 
-// exit face of the chord in the current tet (entry face excluded); -1 if it ends here
+// exit face of the chord in the current tet (entry face excluded); -1 if it ends here.
+// The candidates' parameters s_f = la_f / (la_f - lb_f) are compared as
+// cross products (one division, for the winner): with lb_f < 0 the
+// denominator is positive unless the start lies outside face f by more than
+// the end does, where s_f >= 1 and the candidate counts as s = 1.
+#ifndef FEMPIC_EXIT_NODIV
+#define FEMPIC_EXIT_NODIV 1
+#endif
 __device__ __forceinline__ int exit_face(const double* la, const double* lb, int entry, double s0, double& s1) {
   int best = -1;
+#if FEMPIC_EXIT_NODIV
+  double num = 1.0, den = 1.0;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    if (f != entry && lb[f] < 0.0) {
+      double nf = la[f], df = la[f] - lb[f];
+      if (!(df > 0.0)) nf = df = 1.0;
+      if (best < 0 || nf * den < num * df) {
+        num = nf;
+        den = df;
+        best = f;
+      }
+    }
+  }
+  s1 = best < 0 ? 1.0 : fmin(fmax(num / den, s0), 1.0);
+#else
   double sbest = __longlong_as_double(0x7ff0000000000000ll);
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
@@ -309,6 +348,7 @@ __device__ __forceinline__ int exit_face(const double* la, const double* lb, int
     }
   }
   s1 = best < 0 ? 1.0 : fmin(fmax(sbest, s0), 1.0);
+#endif
   return best;
 }
 
